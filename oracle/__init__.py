@@ -1,0 +1,223 @@
+"""FP64 CPU oracle for two-stage Gauss-Seidel (GS2), GS/SOR, JR, GMRES and CG.
+
+TEST INFRASTRUCTURE ONLY.  Only the test suite, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py`` may import this package.  The GPU
+library never imports it and shares no code with it.
+
+The arithmetic lives in ``oracle.c`` (plain C, one loop per formula of the
+paper); this module compiles it with gcc on first use and wraps it with
+ctypes.  All arrays are numpy: CSR rowptr int64, col int32, val float64.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+FORWARD, BACKWARD, SYMMETRIC = 0, 1, 2
+PC_NONE, PC_GS2, PC_JR, PC_GS = 0, 1, 2, 3
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so next to it (gcc, -O2, no -march)."""
+    stale = (not os.path.exists(_LIB)) or (
+        os.path.getmtime(_LIB) < max(os.path.getmtime(_SRC),
+                                     os.path.getmtime(os.path.join(_HERE, "oracle.h"))))
+    if force or stale:
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+               _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("cycles", ctypes.c_int),
+                ("status", ctypes.c_int), ("true_relres", ctypes.c_double)]
+
+
+@dataclass
+class SolveInfo:
+    iters: int
+    cycles: int
+    status: int
+    true_relres: float
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            P = ctypes.c_void_p
+            I64, I32, D = ctypes.c_int64, ctypes.c_int, ctypes.c_double
+            csr = [I64, P, P, P]
+            lib.ora_spmv.argtypes = csr + [P, P]
+            lib.ora_spmv.restype = None
+            lib.ora_diag.argtypes = csr + [P]
+            lib.ora_gs2.argtypes = csr + [P, P, I32, I32, D, D, I32]
+            lib.ora_gs.argtypes = csr + [P, P, I32, D, I32]
+            lib.ora_jr.argtypes = csr + [P, P, I32, D]
+            lib.ora_levels.argtypes = [I64, P, P, I32, P]
+            lib.ora_precond.argtypes = csr + [P, P, I32, I32, I32, D, D, I32]
+            lib.ora_gmres.argtypes = csr + [P, P, I32, D, I32, I32, I32, I32, D, D,
+                                            I32, ctypes.POINTER(_Info), P]
+            lib.ora_cg.argtypes = csr + [P, P, D, I32, I32, I32, I32, D, D, I32,
+                                         ctypes.POINTER(_Info)]
+            lib.ora_gs2_compact.argtypes = csr + [P, P, I32, I32, I32]
+            for f in ("ora_diag", "ora_gs2", "ora_gs", "ora_jr", "ora_levels",
+                      "ora_precond", "ora_gmres", "ora_cg", "ora_gs2_compact"):
+                getattr(lib, f).restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _csr(A):
+    rp, ci, va = A
+    rp = np.ascontiguousarray(rp, dtype=np.int64)
+    ci = np.ascontiguousarray(ci, dtype=np.int32)
+    va = np.ascontiguousarray(va, dtype=np.float64)
+    n = rp.shape[0] - 1
+    return n, rp, ci, va
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _vec(v, n):
+    v = np.array(v, dtype=np.float64, copy=True, order="C")
+    if v.shape != (n,):
+        raise OracleError(f"vector of length {n} expected, got {v.shape}")
+    return v
+
+
+def _check(st, what):
+    if st != 0:
+        raise OracleError(f"{what} returned status {st}")
+
+
+def spmv(A, x):
+    n, rp, ci, va = _csr(A)
+    x = _vec(x, n)
+    y = np.empty(n)
+    _load().ora_spmv(n, _p(rp), _p(ci), _p(va), _p(x), _p(y))
+    return y
+
+
+def diag(A):
+    n, rp, ci, va = _csr(A)
+    d = np.empty(n)
+    _check(_load().ora_diag(n, _p(rp), _p(ci), _p(va), _p(d)), "ora_diag")
+    return d
+
+
+def gs2(A, b, x, outer=1, inner=1, omega=1.0, gamma=1.0, direction=FORWARD):
+    """Non-compact GS2 sweeps (Eq. 4-7, damped); returns the new x."""
+    n, rp, ci, va = _csr(A)
+    b, x = _vec(b, n), _vec(x, n)
+    _check(_load().ora_gs2(n, _p(rp), _p(ci), _p(va), _p(b), _p(x), outer, inner,
+                           omega, gamma, direction), "ora_gs2")
+    return x
+
+
+def gs(A, b, x, sweeps=1, omega=1.0, direction=FORWARD):
+    """Exact GS / SOR by the compact row recurrence; returns the new x."""
+    n, rp, ci, va = _csr(A)
+    b, x = _vec(b, n), _vec(x, n)
+    _check(_load().ora_gs(n, _p(rp), _p(ci), _p(va), _p(b), _p(x), sweeps, omega,
+                          direction), "ora_gs")
+    return x
+
+
+def jr(A, b, x, sweeps=1, omega=1.0):
+    """Damped Jacobi-Richardson; returns the new x."""
+    n, rp, ci, va = _csr(A)
+    b, x = _vec(b, n), _vec(x, n)
+    _check(_load().ora_jr(n, _p(rp), _p(ci), _p(va), _p(b), _p(x), sweeps, omega),
+           "ora_jr")
+    return x
+
+
+def levels(A, lower=True):
+    """(level per row, number of levels) of the strict lower/upper triangle."""
+    n, rp, ci, _ = _csr(A)
+    lev = np.zeros(n, dtype=np.int32)
+    nlev = _load().ora_levels(n, _p(rp), _p(ci), 1 if lower else 0, _p(lev))
+    return lev, int(nlev)
+
+
+def precond(A, v, kind=PC_GS2, outer=1, inner=1, omega=1.0, gamma=1.0,
+            direction=FORWARD):
+    """z = M^{-1} v from a zero start."""
+    n, rp, ci, va = _csr(A)
+    v = _vec(v, n)
+    z = np.empty(n)
+    _check(_load().ora_precond(n, _p(rp), _p(ci), _p(va), _p(v), _p(z), kind, outer,
+                               inner, omega, gamma, direction), "ora_precond")
+    return z
+
+
+def gmres(A, b, x0=None, restart=30, tol=1e-8, max_iters=10000, pc_kind=PC_GS2,
+          pc_outer=1, pc_inner=1, pc_omega=1.0, pc_gamma=1.0,
+          pc_direction=FORWARD, history=False):
+    """Restarted right-preconditioned GMRES with CGS2.
+
+    Returns (x, SolveInfo[, history]).  A non-converged solve is returned with
+    its status rather than raised, so tests can check the status.
+    """
+    n, rp, ci, va = _csr(A)
+    b = _vec(b, n)
+    x = np.zeros(n) if x0 is None else _vec(x0, n)
+    info = _Info()
+    hist = np.full(max(max_iters, 1), np.nan)
+    st = _load().ora_gmres(n, _p(rp), _p(ci), _p(va), _p(b), _p(x), restart, tol,
+                           max_iters, pc_kind, pc_outer, pc_inner, pc_omega,
+                           pc_gamma, pc_direction, ctypes.byref(info),
+                           _p(hist) if history else None)
+    if st == 1:
+        raise OracleError("ora_gmres: invalid argument")
+    si = SolveInfo(info.iters, info.cycles, info.status, info.true_relres)
+    if history:
+        return x, si, hist[: info.iters].copy()
+    return x, si
+
+
+def cg(A, b, x0=None, tol=1e-8, max_iters=10000, pc_kind=PC_GS2, pc_outer=1,
+       pc_inner=1, pc_omega=1.0, pc_gamma=1.0, pc_direction=SYMMETRIC):
+    """Preconditioned CG; returns (x, SolveInfo)."""
+    n, rp, ci, va = _csr(A)
+    b = _vec(b, n)
+    x = np.zeros(n) if x0 is None else _vec(x0, n)
+    info = _Info()
+    st = _load().ora_cg(n, _p(rp), _p(ci), _p(va), _p(b), _p(x), tol, max_iters,
+                        pc_kind, pc_outer, pc_inner, pc_omega, pc_gamma,
+                        pc_direction, ctypes.byref(info))
+    if st == 1:
+        raise OracleError("ora_cg: invalid argument")
+    return x, SolveInfo(info.iters, info.cycles, info.status, info.true_relres)
+
+
+def gs2_compact(A, b, x, outer=1, inner=1, direction=FORWARD):
+    """Compact GS2 (Eq. 11); returns the new x."""
+    n, rp, ci, va = _csr(A)
+    b, x = _vec(b, n), _vec(x, n)
+    _check(_load().ora_gs2_compact(n, _p(rp), _p(ci), _p(va), _p(b), _p(x), outer,
+                                   inner, direction), "ora_gs2_compact")
+    return x

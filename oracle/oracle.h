@@ -1,0 +1,111 @@
+/*
+ * Plain, slow, single-threaded FP64 CPU oracle for two-stage Gauss-Seidel
+ * (GS2), exact Gauss-Seidel (GS/SOR), Jacobi-Richardson (JR) and restarted
+ * right-preconditioned GMRES with CGS2 orthogonalisation.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load this library.  The GPU library
+ * shares no code with it and never calls it.
+ *
+ * Matrices are CSR: rowptr[n+1] (int64), col[nnz] (int32), val[nnz] (f64).
+ * Column order inside a row is arbitrary; the split A = L + D + U is taken by
+ * comparing the column index with the row index (Sec. 3, splitting before
+ * Eq. (1)).
+ *
+ * Return codes follow the library's status enumeration: 0 = OK,
+ * 1 = invalid argument, 2 = zero/missing diagonal, 5 = not converged,
+ * 6 = breakdown, 7 = NaN/Inf detected.
+ */
+#ifndef GS2_ORACLE_H
+#define GS2_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORA_FORWARD = 0, ORA_BACKWARD = 1, ORA_SYMMETRIC = 2 };
+enum { ORA_PC_NONE = 0, ORA_PC_GS2 = 1, ORA_PC_JR = 2, ORA_PC_GS = 3 };
+
+typedef struct {
+  int iters;          /* total Arnoldi steps over all cycles */
+  int cycles;         /* restart cycles started */
+  int status;         /* 0 converged, 5 not converged, 6 breakdown, 7 NaN */
+  double true_relres; /* ||b - A x|| / ||b|| at exit */
+} ora_info;
+
+/* y = A x */
+void ora_spmv(int64_t n, const int64_t* rp, const int32_t* ci,
+              const double* va, const double* x, double* y);
+
+/* Diagonal a_ii of every row; returns 2 if some a_ii is zero or absent. */
+int ora_diag(int64_t n, const int64_t* rp, const int32_t* ci,
+             const double* va, double* d);
+
+/* Non-compact two-stage GS, Eq. (4)-(7) with the damping factors of the
+ * "Damping factor" paragraph of Sec. 3: per outer sweep
+ *   r = b - A x;  g0 = D^{-1} r;
+ *   g_{j+1} = (1-gamma) g_j + gamma D^{-1} (r - omega T g_j),  j < inner;
+ *   x += omega g_inner,
+ * with T = L (forward) or U (backward); symmetric = forward then backward.
+ * x is updated in place. */
+int ora_gs2(int64_t n, const int64_t* rp, const int32_t* ci, const double* va,
+            const double* b, double* x, int outer, int inner, double omega,
+            double gamma, int dir);
+
+/* Exact GS / SOR by the compact row recurrence (Sec. 5.1.1, sequential GS):
+ * x_i <- (1-omega) x_i + omega (b_i - sum_{j != i} a_ij x_j) / a_ii in
+ * ascending (forward) or descending (backward) row order; symmetric =
+ * forward then backward.  x in place. */
+int ora_gs(int64_t n, const int64_t* rp, const int32_t* ci, const double* va,
+           const double* b, double* x, int sweeps, double omega, int dir);
+
+/* Damped Jacobi-Richardson: x += omega D^{-1} (b - A x), `sweeps` times
+ * (Sec. 3, zero-inner-sweep special case). */
+int ora_jr(int64_t n, const int64_t* rp, const int32_t* ci, const double* va,
+           const double* b, double* x, int sweeps, double omega);
+
+/* Level sets of the strict lower (lower=1) or strict upper (lower=0)
+ * triangle: level(i) = 1 + max level(j) over dependencies j, level 0 for
+ * rows with none.  Returns the number of levels. */
+int ora_levels(int64_t n, const int64_t* rp, const int32_t* ci, int lower,
+               int32_t* level);
+
+/* Apply a preconditioner from a zero start: z = M^{-1} v.
+ * kind: ORA_PC_NONE (z = v), ORA_PC_GS2, ORA_PC_JR (outer = sweeps),
+ * ORA_PC_GS (exact GS, outer = sweeps). */
+int ora_precond(int64_t n, const int64_t* rp, const int32_t* ci,
+                const double* va, const double* v, double* z, int kind,
+                int outer, int inner, double omega, double gamma, int dir);
+
+/* Restarted GMRES(m), right preconditioned, CGS2 Arnoldi, Givens rotations.
+ * x holds x0 on entry and the solution on exit.  Stops when the implicit
+ * residual |g_{j+1}| <= tol ||b|| inside a cycle and the recomputed true
+ * residual confirms it, or when max_iters Arnoldi steps have run.
+ * resid_hist (may be NULL) receives |g_{j+1}|/||b|| after every step, so it
+ * needs max_iters entries. */
+int ora_gmres(int64_t n, const int64_t* rp, const int32_t* ci,
+              const double* va, const double* b, double* x, int restart,
+              double tol, int max_iters, int pc_kind, int pc_outer,
+              int pc_inner, double pc_omega, double pc_gamma, int pc_dir,
+              ora_info* info, double* resid_hist);
+
+/* Preconditioned conjugate gradients for SPD A (Sec. 6.2 uses CG with an
+ * SGS2 preconditioner).  Same stopping rule on the recursively updated
+ * residual, confirmed by the true residual. */
+int ora_cg(int64_t n, const int64_t* rp, const int32_t* ci, const double* va,
+           const double* b, double* x, double tol, int max_iters, int pc_kind,
+           int pc_outer, int pc_inner, double pc_omega, double pc_gamma,
+           int pc_dir, ora_info* info);
+
+/* Compact two-stage GS, Eq. (11): x <- Mhat^{-1} (b + N x) where
+ * N = -U (forward) or -L (backward) and Mhat^{-1} is `inner` JR sweeps on
+ * (D + T) from g0 = D^{-1}(b + N x).  Undamped (omega = gamma = 1). */
+int ora_gs2_compact(int64_t n, const int64_t* rp, const int32_t* ci,
+                    const double* va, const double* b, double* x, int outer,
+                    int inner, int dir);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,444 @@
+"""Pins of the FP64 oracle to facts the paper and the mathematics fix.
+
+Every check here is independent of the oracle's own loops: dense linear
+algebra from numpy, closed-form spectra, a hand-worked example, level sets
+from a graph library, and invariances the paper's tables show.  A dropped
+term, a wrong sign, a transposed triangle or an in-place inner sweep in the
+oracle fails at least one of them.
+"""
+import math
+import os
+
+import networkx as nx
+import numpy as np
+import pytest
+
+import oracle
+from paper_2104_01196_gb300 import problems as P
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def dense_parts(A):
+    M = P.csr_to_dense(A)
+    D = np.diag(np.diag(M))
+    L = np.tril(M, -1)
+    U = np.triu(M, 1)
+    return M, D, L, U
+
+
+def tiny_nonsym(n=7, seed=5):
+    rng = np.random.default_rng(seed)
+    M = rng.uniform(-1, 1, (n, n)) * (rng.uniform(0, 1, (n, n)) < 0.5)
+    np.fill_diagonal(M, np.abs(M).sum(1) + rng.uniform(0.5, 1.5, n))
+    return P.dense_to_csr(M)
+
+
+# ---------------------------------------------------------------------------
+# A hand-worked example (Eq. 5-7 applied by hand to a 3x3 tridiagonal system)
+# ---------------------------------------------------------------------------
+
+def test_hand_worked_gs2_and_gs():
+    M = np.array([[4.0, -1, 0], [-1, 4, -1], [0, -1, 4]])
+    A = P.dense_to_csr(M)
+    b = np.array([1.0, 2.0, 3.0])
+    # g0 = D^-1 r = [1/4, 1/2, 3/4]; g1 = D^-1 (r - L g0) = [1/4, 9/16, 7/8]
+    x1 = oracle.gs2(A, b, np.zeros(3), outer=1, inner=1)
+    assert x1.tolist() == [0.25, 0.5625, 0.875]
+    # g2 = D^-1 (r - L g1) = [1/4, 9/16, 57/64] = exact forward GS (depth 2)
+    x2 = oracle.gs2(A, b, np.zeros(3), outer=1, inner=2)
+    assert x2.tolist() == [0.25, 0.5625, 0.890625]
+    xg = oracle.gs(A, b, np.zeros(3), sweeps=1)
+    assert xg.tolist() == [0.25, 0.5625, 0.890625]
+    # zero inner sweeps = Jacobi-Richardson: D^-1 b
+    x0 = oracle.gs2(A, b, np.zeros(3), outer=1, inner=0)
+    assert x0.tolist() == [0.25, 0.5, 0.75]
+
+
+# ---------------------------------------------------------------------------
+# Exact GS / SOR against a dense triangular solve
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("omega", [1.0, 0.7, 1.3])
+def test_gs_equals_dense_sor(omega):
+    A = tiny_nonsym()
+    M, D, L, U = dense_parts(A)
+    rng = np.random.default_rng(1)
+    b, x0 = rng.standard_normal(7), rng.standard_normal(7)
+    # non-compact SOR form of the damping paragraph: x + w (D + w L)^-1 (b - A x)
+    fwd = x0 + omega * np.linalg.solve(D + omega * L, b - M @ x0)
+    assert np.allclose(oracle.gs(A, b, x0, 1, omega, oracle.FORWARD), fwd,
+                       rtol=1e-13, atol=1e-13)
+    # compact form of the same paragraph: w (D + w L)^-1 (b - [U + (1 - 1/w) D] x)
+    cmp_ = omega * np.linalg.solve(D + omega * L, b - (U + (1 - 1 / omega) * D) @ x0)
+    assert np.allclose(fwd, cmp_, rtol=1e-12, atol=1e-12)
+    bwd = x0 + omega * np.linalg.solve(D + omega * U, b - M @ x0)
+    assert np.allclose(oracle.gs(A, b, x0, 1, omega, oracle.BACKWARD), bwd,
+                       rtol=1e-13, atol=1e-13)
+    sym = fwd + omega * np.linalg.solve(D + omega * U, b - M @ fwd)
+    assert np.allclose(oracle.gs(A, b, x0, 1, omega, oracle.SYMMETRIC), sym,
+                       rtol=1e-12, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# GS2 against the closed forms of Sec. 3
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("inner", [0, 1, 2, 3])
+@pytest.mark.parametrize("omega", [1.0, 0.8])
+def test_gs2_equals_neumann_series(inner, omega):
+    """x + w sum_{j<=s} (-w D^-1 L)^j D^-1 r  (degree-s Neumann expansion)."""
+    A = tiny_nonsym()
+    M, D, L, U = dense_parts(A)
+    rng = np.random.default_rng(2)
+    b, x0 = rng.standard_normal(7), rng.standard_normal(7)
+    Di = np.diag(1 / np.diag(M))
+    r = b - M @ x0
+    for T, d in ((L, oracle.FORWARD), (U, oracle.BACKWARD)):
+        S = sum(np.linalg.matrix_power(-omega * Di @ T, j) for j in range(inner + 1))
+        expect = x0 + omega * S @ Di @ r
+        got = oracle.gs2(A, b, x0, 1, inner, omega, 1.0, d)
+        assert np.allclose(got, expect, rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("gamma", [0.5, 0.9, 1.2])
+def test_gs2_inner_damping_closed_form(gamma):
+    """Damped inner JR: g_s = g* + T^s (g_0 - g*), T = (1-gamma) I - gamma w D^-1 L,
+    g* = (D + w L)^-1 r, g_0 = D^-1 r."""
+    A = tiny_nonsym(6, 9)
+    M, D, L, U = dense_parts(A)
+    rng = np.random.default_rng(3)
+    b, x0 = rng.standard_normal(6), rng.standard_normal(6)
+    omega = 0.9
+    Di = np.diag(1 / np.diag(M))
+    r = b - M @ x0
+    gstar = np.linalg.solve(D + omega * L, r)
+    T = (1 - gamma) * np.eye(6) - gamma * omega * Di @ L
+    for s in (1, 2, 4):
+        g = gstar + np.linalg.matrix_power(T, s) @ (Di @ r - gstar)
+        got = oracle.gs2(A, b, x0, 1, s, omega, gamma, oracle.FORWARD)
+        assert np.allclose(got, x0 + omega * g, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("N", [6, 16])
+def test_gs2_with_depth_inner_sweeps_is_exact_gs(N):
+    """D^-1 L is nilpotent: with inner sweeps >= depth(L) GS2 is exact GS,
+    with one fewer it is not (checked where the missing Neumann term,
+    (1/4)^depth times a path count, is far above rounding)."""
+    A = P.poisson2d_matrix(N)
+    _, nlev = oracle.levels(A, lower=True)
+    depth = nlev - 1
+    assert depth == 2 * N - 2
+    rng = np.random.default_rng(4)
+    b, x0 = rng.standard_normal(N * N), rng.standard_normal(N * N)
+    for d in (oracle.FORWARD, oracle.BACKWARD, oracle.SYMMETRIC):
+        for omega in (1.0, 0.8):
+            ex = oracle.gs(A, b, x0, 1, omega, d)
+            got = oracle.gs2(A, b, x0, 1, depth, omega, 1.0, d)
+            assert np.linalg.norm(got - ex) <= 1e-13 * np.linalg.norm(ex)
+            if N <= 8 and d != oracle.SYMMETRIC:
+                # (in a symmetric sweep the backward half absorbs most of it)
+                short = oracle.gs2(A, b, x0, 1, depth - 1, omega, 1.0, d)
+                assert np.linalg.norm(short - ex) > 1e-6 * np.linalg.norm(ex)
+
+
+def test_gs2_zero_inner_is_jacobi_richardson():
+    pr = P.random_system(300, 17)
+    rng = np.random.default_rng(5)
+    x0 = rng.standard_normal(pr.n)
+    for omega in (1.0, 0.6):
+        a = oracle.gs2(pr.A, pr.b, x0, 3, 0, omega, 1.0, oracle.FORWARD)
+        j = oracle.jr(pr.A, pr.b, x0, 3, omega)
+        assert np.allclose(a, j, rtol=1e-14, atol=1e-14)
+
+
+def test_diagonal_matrix_collapses_everything():
+    n = 40
+    d = 1.0 + np.arange(n) % 7
+    A = (np.arange(n + 1, dtype=np.int64), np.arange(n, dtype=np.int32), d.copy())
+    b = np.linspace(-1, 1, n)
+    for omega in (1.0, 0.7):
+        expect = omega * b / d
+        for got in (oracle.gs2(A, b, np.zeros(n), 1, 3, omega, 1.0, oracle.SYMMETRIC * 0),
+                    oracle.gs(A, b, np.zeros(n), 1, omega),
+                    oracle.jr(A, b, np.zeros(n), 1, omega)):
+            assert np.allclose(got, expect, rtol=1e-15, atol=0)
+    # omega = 1: one sweep solves the system exactly
+    assert np.array_equal(oracle.gs2(A, b, np.zeros(n), 1, 1), b / d)
+
+
+def test_residual_propagators_of_sec4():
+    """Sec. 4: one GS2(1) sweep maps r to (I - A D^-1 [I - L D^-1]) r, two JR
+    sweeps to (I - A D^-1)^2 r = (I - A D^-1 [I - (L+U) D^-1]) r, SGS2(1) to
+    (I - A D^-1 [I - U D^-1])(I - A D^-1 [I - L D^-1]) r."""
+    A = tiny_nonsym(8, 13)
+    M, D, L, U = dense_parts(A)
+    Di = np.diag(1 / np.diag(M))
+    I = np.eye(8)
+    rng = np.random.default_rng(6)
+    b, x0 = rng.standard_normal(8), rng.standard_normal(8)
+    r0 = b - M @ x0
+    Pg = I - M @ Di @ (I - L @ Di)
+    Pb = I - M @ Di @ (I - U @ Di)
+    Pj = I - M @ Di
+    x = oracle.gs2(A, b, x0, 1, 1, 1.0, 1.0, oracle.FORWARD)
+    assert np.allclose(b - M @ x, Pg @ r0, rtol=1e-12, atol=1e-12)
+    x = oracle.gs2(A, b, x0, 1, 1, 1.0, 1.0, oracle.SYMMETRIC)
+    assert np.allclose(b - M @ x, Pb @ Pg @ r0, rtol=1e-12, atol=1e-12)
+    x = oracle.jr(A, b, x0, 2, 1.0)
+    assert np.allclose(b - M @ x, Pj @ Pj @ r0, rtol=1e-12, atol=1e-12)
+    assert np.allclose(Pj @ Pj, I - M @ Di @ (I - (L + U) @ Di), atol=1e-13)
+    x = oracle.jr(A, b, x0, 3, 1.0)
+    assert np.allclose(b - M @ x, Pj @ Pj @ Pj @ r0, rtol=1e-12, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Closed-form spectra of the 2D Dirichlet Laplacian (textbook)
+# ---------------------------------------------------------------------------
+
+def iteration_matrix(step, n):
+    """Columns T e_i of a stationary iteration x -> T x (b = 0)."""
+    return np.stack([step(np.eye(n)[:, i]) for i in range(n)], axis=1)
+
+
+@pytest.mark.parametrize("omega", [1.0, 0.8])
+def test_jacobi_spectrum_2d_laplacian(omega):
+    N = 8
+    A = P.poisson2d_matrix(N)
+    n = N * N
+    T = iteration_matrix(lambda e: oracle.jr(A, np.zeros(n), e, 1, omega), n)
+    ev = np.sort(np.linalg.eigvals(T).real)
+    k = np.arange(1, N + 1)
+    mu = (np.cos(np.pi * k / (N + 1))[:, None] + np.cos(np.pi * k / (N + 1))[None, :]) / 2
+    expect = np.sort((1 - omega * (1 - mu)).ravel())
+    assert np.allclose(ev, expect, atol=1e-12)
+    rho = np.abs(ev).max()
+    rho_cf = max(abs(1 - omega * (1 - math.cos(math.pi / (N + 1)))),
+                 abs(1 - omega * (1 + math.cos(math.pi / (N + 1)))))
+    assert abs(rho - rho_cf) < 1e-12
+
+
+def test_jacobi_rho_for_64_grid_closed_form():
+    # rho_J = cos(pi/65) for the 64 x 64 grid of the small workload
+    assert abs(math.cos(math.pi / 65) - 0.998832) < 5e-7
+
+
+def test_gs_and_sor_spectral_radius_young():
+    """Lexicographic 5-point Laplacian is consistently ordered: rho(GS) =
+    rho_J^2 and rho(SOR at w_opt) = w_opt - 1 (Young)."""
+    N = 8
+    A = P.poisson2d_matrix(N)
+    n = N * N
+    muJ = math.cos(math.pi / (N + 1))
+    Tgs = iteration_matrix(lambda e: oracle.gs(A, np.zeros(n), e, 1, 1.0), n)
+    assert abs(np.abs(np.linalg.eigvals(Tgs)).max() - muJ ** 2) < 1e-10
+    wopt = 2 / (1 + math.sqrt(1 - muJ ** 2))
+    Tsor = iteration_matrix(lambda e: oracle.gs(A, np.zeros(n), e, 1, wopt), n)
+    # a 2x2 Jordan block sits at w_opt - 1: eigenvalues move by ~sqrt(eps)
+    assert abs(np.abs(np.linalg.eigvals(Tsor)).max() - (wopt - 1)) < 1e-6
+    # GS2 with inner sweeps >= depth has the same iteration matrix as GS
+    Tgs2 = iteration_matrix(lambda e: oracle.gs2(A, np.zeros(n), e, 1, 2 * N - 2), n)
+    assert np.allclose(Tgs2, Tgs, atol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# Level sets
+# ---------------------------------------------------------------------------
+
+def test_levels_of_structured_grids():
+    N = 9
+    lev, nlev = oracle.levels(P.poisson2d_matrix(N), lower=True)
+    i = np.arange(N * N)
+    assert nlev == 2 * N - 1
+    assert np.array_equal(lev, (i % N) + (i // N))
+    lev, nlev = oracle.levels(P.poisson2d_matrix(N), lower=False)
+    assert np.array_equal(lev, (N - 1 - i % N) + (N - 1 - i // N))
+    N = 6
+    lev, nlev = oracle.levels(P.poisson3d_matrix(N), lower=True)
+    i = np.arange(N ** 3)
+    assert nlev == 3 * N - 2
+    assert np.array_equal(lev, i % N + (i // N) % N + i // (N * N))
+
+
+def test_levels_equal_longest_path_brute_force():
+    A = P.random_csr(120, 21, mean_offdiag=3.0)
+    rp, ci, _ = A
+    G = nx.DiGraph()
+    G.add_nodes_from(range(120))
+    for i in range(120):
+        for k in range(rp[i], rp[i + 1]):
+            if ci[k] < i:
+                G.add_edge(int(ci[k]), i)
+    lev, nlev = oracle.levels(A, lower=True)
+    longest = {v: 0 for v in G.nodes}
+    for v in nx.topological_sort(G):
+        for w in G.successors(v):
+            longest[w] = max(longest[w], longest[v] + 1)
+    assert [longest[v] for v in range(120)] == lev.tolist()
+    assert nlev - 1 == nx.dag_longest_path_length(G)
+
+
+# ---------------------------------------------------------------------------
+# GMRES against the Krylov least-squares minimiser
+# ---------------------------------------------------------------------------
+
+def precond_matrix(A, n, **kw):
+    return iteration_matrix(lambda e: oracle.precond(A, e, **kw), n)
+
+
+@pytest.mark.parametrize("pc", [dict(kind=oracle.PC_NONE),
+                                dict(kind=oracle.PC_GS2, inner=1, omega=0.9),
+                                dict(kind=oracle.PC_GS2, inner=2,
+                                     direction=oracle.SYMMETRIC),
+                                dict(kind=oracle.PC_JR, outer=2, omega=0.7)])
+def test_gmres_residuals_are_krylov_minima(pc):
+    n = 7
+    A = tiny_nonsym(n, 31)
+    M = P.csr_to_dense(A)
+    b = np.random.default_rng(7).standard_normal(n)
+    Minv = precond_matrix(A, n, **pc)
+    AM = M @ Minv
+    x, info, hist = oracle.gmres(A, b, restart=n, tol=1e-14, max_iters=n,
+                                 pc_kind=pc["kind"], pc_outer=pc.get("outer", 1),
+                                 pc_inner=pc.get("inner", 1),
+                                 pc_omega=pc.get("omega", 1.0),
+                                 pc_direction=pc.get("direction", 0), history=True)
+    K = np.stack([np.linalg.matrix_power(AM, j) @ b for j in range(n)], axis=1)
+    for k in range(1, info.iters + 1):
+        y, *_ = np.linalg.lstsq(AM @ K[:, :k], b, rcond=None)
+        best = np.linalg.norm(b - AM @ K[:, :k] @ y) / np.linalg.norm(b)
+        # the power basis K is ill-conditioned, hence the absolute floor
+        assert abs(hist[k - 1] - best) <= max(1e-9 * best, 1e-10), (k, hist[k - 1], best)
+    assert info.iters <= n
+    assert info.status == 0
+    assert np.allclose(x, np.linalg.solve(M, b), rtol=1e-10, atol=1e-12)
+
+
+def test_gmres_restart_and_true_residual():
+    pr = P.poisson2d(24, seed=P.SEED_BASE)
+    x, info = oracle.gmres(pr.A, pr.b, restart=5, tol=1e-8, max_iters=5000,
+                           pc_kind=oracle.PC_GS2, pc_inner=1)
+    assert info.status == 0 and info.cycles > 1
+    r = pr.b - P.csr_matvec(pr.A, x)
+    assert np.linalg.norm(r) / np.linalg.norm(pr.b) == pytest.approx(info.true_relres, rel=1e-6)
+    assert info.true_relres <= 1e-8
+
+
+def test_gmres_small_workload_converges():
+    """2D 5-point Poisson 64x64, GMRES(30), one forward GS2 sweep with one
+    inner sweep, rel. residual 1e-8."""
+    pr = P.poisson2d(64)
+    x, info = oracle.gmres(pr.A, pr.b, restart=30, tol=1e-8, max_iters=2000,
+                           pc_kind=oracle.PC_GS2, pc_inner=1)
+    assert info.status == 0 and info.true_relres <= 1e-8
+    assert np.linalg.norm(x - pr.x_true) / np.linalg.norm(pr.x_true) < 1e-4
+    # unpreconditioned GMRES(30) needs more iterations, symmetric GS2 fewer
+    _, info0 = oracle.gmres(pr.A, pr.b, restart=30, tol=1e-8, max_iters=20000,
+                            pc_kind=oracle.PC_NONE)
+    _, info2 = oracle.gmres(pr.A, pr.b, restart=30, tol=1e-8, max_iters=20000,
+                            pc_kind=oracle.PC_GS2, pc_inner=1,
+                            pc_direction=oracle.SYMMETRIC)
+    assert info0.iters > info.iters > info2.iters
+
+
+def _golden(key):
+    with open(os.path.join(GOLDEN, "paper_tables.txt")) as f:
+        for line in f:
+            if line.startswith(key + " "):
+                return dict(kv.split("=") for kv in line.split()[1:])
+    raise KeyError(key)
+
+
+def test_jr1_iteration_count_independent_of_omega():
+    """Table ela3d-omega prints 213 GMRES iterations for JR(1) at every omega:
+    one JR sweep from zero is omega D^-1, and GMRES does not see a scalar
+    factor on the preconditioner."""
+    g = _golden("jr1_vs_omega")
+    assert len(set(g["iters"].split(","))) == 1
+    A, clamped = P.elasticity_matrix(5)
+    b = P.elasticity_body_load(5, clamped)
+    counts = []
+    for om in [float(w) for w in g["omega"].split(",")]:
+        _, info = oracle.gmres(A, b, restart=30, tol=1e-8, max_iters=3000,
+                               pc_kind=oracle.PC_JR, pc_outer=1, pc_omega=om)
+        assert info.status == 0
+        counts.append(info.iters)
+    assert len(set(counts)) == 1, counts
+
+
+def test_sgs2_enough_inner_sweeps_matches_sgs_iterations():
+    """Table ela3d-omega: SGS2(1,10) takes the SGS count (61 = 61 at omega=1)."""
+    g = _golden("sgs_vs_sgs2_1_10")
+    assert g["sgs"] == g["sgs2_1_10"]
+    A = P.poisson3d_matrix(6)
+    b = P.csr_matvec(A, P.uniform_pm1(3, 216))
+    _, nlev = oracle.levels(A)
+    _, i_gs = oracle.gmres(A, b, restart=30, tol=1e-10, pc_kind=oracle.PC_GS,
+                           pc_direction=oracle.SYMMETRIC)
+    _, i_gs2 = oracle.gmres(A, b, restart=30, tol=1e-10, pc_kind=oracle.PC_GS2,
+                            pc_inner=nlev - 1, pc_direction=oracle.SYMMETRIC)
+    assert i_gs.iters == i_gs2.iters
+
+
+# ---------------------------------------------------------------------------
+# CG and compact GS2
+# ---------------------------------------------------------------------------
+
+def test_cg_iterates_minimise_energy_norm():
+    M = P.csr_to_dense(P.poisson2d_matrix(3))
+    A = P.dense_to_csr(M)
+    b = np.arange(1.0, 10.0)
+    xs = np.linalg.solve(M, b)
+    K = np.stack([np.linalg.matrix_power(M, j) @ b for j in range(9)], axis=1)
+    for k in range(1, 4):
+        x, info = oracle.cg(A, b, tol=1e-300, max_iters=k, pc_kind=oracle.PC_NONE)
+        # min over y of ||K y - x*||_A
+        Q = K[:, :k]
+        y = np.linalg.solve(Q.T @ M @ Q, Q.T @ M @ xs)
+        assert np.allclose(x, Q @ y, rtol=1e-9, atol=1e-11)
+
+
+def test_cg_with_sgs2_converges_and_sgs2_is_symmetric():
+    pr = P.poisson2d(20)
+    x, info = oracle.cg(pr.A, pr.b, tol=1e-8, pc_kind=oracle.PC_GS2, pc_inner=1,
+                        pc_direction=oracle.SYMMETRIC)
+    assert info.status == 0 and info.true_relres <= 1e-8
+    Minv = precond_matrix(P.poisson2d_matrix(6), 36, kind=oracle.PC_GS2, inner=1,
+                          direction=oracle.SYMMETRIC)
+    assert np.allclose(Minv, Minv.T, atol=1e-14)
+
+
+def test_compact_gs2_closed_form_and_exact_limit():
+    A = tiny_nonsym(7, 41)
+    M, D, L, U = dense_parts(A)
+    Di = np.diag(1 / np.diag(M))
+    rng = np.random.default_rng(8)
+    b, x0 = rng.standard_normal(7), rng.standard_normal(7)
+    for s in (0, 1, 2):
+        S = sum(np.linalg.matrix_power(-Di @ L, j) for j in range(s + 1))
+        expect = S @ Di @ (b - U @ x0)
+        got = oracle.gs2_compact(A, b, x0, 1, s, oracle.FORWARD)
+        assert np.allclose(got, expect, rtol=1e-13, atol=1e-13)
+    # exact inner solve: compact and non-compact GS coincide (Eq. 1 vs Eq. 10)
+    Ap = P.poisson2d_matrix(7)
+    bb, xx = rng.standard_normal(49), rng.standard_normal(49)
+    assert np.allclose(oracle.gs2_compact(Ap, bb, xx, 1, 12), oracle.gs(Ap, bb, xx, 1),
+                       rtol=1e-13, atol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# Error statuses
+# ---------------------------------------------------------------------------
+
+def test_statuses():
+    A = P.dense_to_csr(np.array([[1.0, 2.0], [3.0, 0.0]]))
+    with pytest.raises(oracle.OracleError):
+        oracle.gs2(A, np.ones(2), np.zeros(2))
+    pr = P.poisson2d(16)
+    _, info = oracle.gmres(pr.A, pr.b, restart=10, tol=1e-12, max_iters=3,
+                           pc_kind=oracle.PC_NONE)
+    assert info.status == 5 and info.iters == 3
+    b = pr.b.copy()
+    b[3] = np.nan
+    _, info = oracle.gmres(pr.A, b, restart=10, tol=1e-8, max_iters=30)
+    assert info.status == 7
