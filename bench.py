@@ -1,0 +1,412 @@
+"""Benchmark: GS2-preconditioned restarted GMRES on one GB300.
+
+One step = one full solve A x = b from x0 = 0 of the 3D 7-point Laplacian
+on a 128^3 grid (n = 2,097,152, nnz = 14,581,760, FP64 CSR, b = A x_true,
+x_true ~ U[-1,1] from the seed), GMRES(30) right preconditioned by one
+symmetric GS2 sweep with one inner JR sweep (SGS2(1,1)), relative residual
+1e-8.  Inputs are synthetic (the paper's Galeri Laplacian, re-synthesised).
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+on the host cores on a bounded sample of the same workload instead.
+With torchrun (N > 1) every rank solves its own copy on its own GPU
+(replicas; the method has no data-path exchange on one matrix per GPU).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GS2 sweep HBM GB/s (% peak); GMRES solves/s, p50/p99 latency vs plain FP64"
+WORKLOAD = ("3D 7-point Laplacian 128^3 (n=2,097,152, nnz=14,581,760), CSR FP64, "
+            "b = A x_true, x_true ~ U[-1,1]; GMRES(30) + SGS2(1,1), rel. residual 1e-8")
+COUNTS_FILE = os.path.join(ROOT, "tests", "golden", "oracle_counts.txt")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.txt")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--grid", type=int, default=128, help="N of the N^3 Laplacian")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the baseline/precision comparison solves")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--no-profile", action="store_true",
+                    help="do not time kernels with events inside the timed region")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def stored_count(key):
+    """Full-solve iteration counts written by tests/golden/make_oracle_counts.py
+    (the oracle only)."""
+    if not os.path.exists(COUNTS_FILE):
+        return None
+    with open(COUNTS_FILE) as f:
+        for line in f:
+            if line.startswith(key + " "):
+                return int(line.split("iters=")[1].split()[0])
+    return None
+
+
+def stored_traffic(kernel, grid):
+    """Per-launch DRAM bytes of a kernel from the committed ncu summary."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    with open(TRAFFIC_FILE) as f:
+        for line in f:
+            parts = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
+            if parts.get("kernel") == kernel and parts.get("grid") == str(grid):
+                return float(parts["dram_bytes_per_launch"])
+    return None
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle
+# ---------------------------------------------------------------------------
+
+def oracle_sample(pr, n_steps_sample=3):
+    """Time the oracle's GMRES(30)+SGS2(1,1) for a few Arnoldi steps and scale
+    to one full solve by the oracle's own full-solve iteration count."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    _, info = oracle.gmres(pr.A, pr.b, restart=30, tol=1e-8, max_iters=n_steps_sample,
+                           pc_kind=oracle.PC_GS2, pc_inner=1, pc_direction=oracle.SYMMETRIC)
+    dt = time.perf_counter() - t0
+    per_iter = dt / max(info.iters, 1)
+    full = stored_count(f"poisson3d_{int(round(pr.n ** (1 / 3)))}_gmres30_sgs2_1_1")
+    return per_iter, full, dt, info.iters
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2104_01196_gb300 import problems as P
+    pr = P.poisson3d(args.grid)
+    times = []
+    per_iter_all = []
+    full = None
+    for s in range(args.warmup + args.steps):
+        per_iter, full, dt, its = oracle_sample(pr)
+        if s >= args.warmup:
+            times.append(dt)
+            per_iter_all.append(per_iter)
+    per_iter = float(np.mean(per_iter_all))
+    iters_full = full if full else 1
+    value = 1.0 / (per_iter * iters_full)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": args.grid},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                         "sample": f"3 Arnoldi steps of GMRES(30)+SGS2(1,1) per step, "
+                                   f"scaled by the oracle's full-solve count {iters_full}"},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+
+    import paper_2104_01196_gb300 as gs2
+    from paper_2104_01196_gb300 import build as B
+    from paper_2104_01196_gb300 import problems as P
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0 or not os.path.exists(B.LIB):
+        B.build()
+    if dist:
+        dist.barrier()
+    gs2.load()
+
+    pr = P.poisson3d(args.grid)
+    n = pr.n
+    stream = torch.cuda.Stream()
+    h = gs2.gs2_setup(pr.A, stream=stream.cuda_stream)
+    pc = gs2.params("gs2", 1, 1, direction="symmetric")
+    with torch.cuda.stream(stream):
+        b = torch.from_numpy(pr.b).cuda()
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    stream.synchronize()
+
+    def solve():
+        x.zero_()
+        return gs2.gmres_solve(h, b, x, 30, 1e-8, 5000, pc)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            info = solve()
+    stream.synchronize()
+    if info.status != 0:
+        raise RuntimeError(f"warm-up solve failed: {info}")
+
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    if not args.no_profile:
+        h.profile(True)
+        h.profile_reset()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    iters = []
+    launches0 = gs2.launch_count()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        t_start.record(stream)
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            info = solve()
+            ev[k][1].record(stream)
+            iters.append(info.iters)
+            if info.status != 0:
+                raise RuntimeError(f"timed solve failed: {info}")
+        t_end.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = gs2.launch_count() - launches0
+    total_ms = t_start.elapsed_time(t_end)
+    step_ms = [a.elapsed_time(bb) for a, bb in ev]
+    kstats = h.profile_read() if not args.no_profile else {}
+    h.profile(False)
+    clocks = sampler.stop() if sampler else None
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps / (total_ms / 1000.0)
+
+    hbm, peak_kind = peaks()
+    roof = None
+    kernels = {}
+    if kstats:
+        for name, s in kstats.items():
+            if s["launches"]:
+                gbs = s["bytes"] / (s["total_ms"] / 1000.0) / 1e9 if s["total_ms"] > 0 else 0.0
+                kernels[name] = {"launches": s["launches"], "ms": round(s["total_ms"], 3),
+                                 "share": None, "gbs": round(gbs, 1),
+                                 "frac": round(gbs / hbm, 3)}
+        ksum = sum(v["ms"] for v in kernels.values())
+        for v in kernels.values():
+            v["share"] = round(v["ms"] / ksum, 3) if ksum else None
+        top = max(kernels, key=lambda k: kernels[k]["ms"])
+        s = kstats[top]
+        per_launch_bytes = s["bytes"] / s["launches"]
+        per_launch_ms = s["total_ms"] / s["launches"]
+        achieved = per_launch_bytes / (per_launch_ms / 1000.0) / 1e9
+        traffic = stored_traffic(top, args.grid)
+        roof = {"bound": "hbm", "kernel": top, "achieved": round(achieved, 1), "peak": hbm,
+                "unit": "GB/s", "frac": round(achieved / hbm, 3),
+                "traffic": traffic, "algorithmic_bytes_per_launch": per_launch_bytes,
+                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"}
+        # the GS2 sweep kernels named by the metric
+        sweep = {k: kernels[k] for k in ("resid", "inner64") if k in kernels}
+    else:
+        sweep = {}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": args.grid, "n": n, "nnz": pr.nnz,
+                   "restart": 30, "tol": 1e-8, "precond": "SGS2(1,1) FP64",
+                   "parallelism": f"replicas x{world}",
+                   "l2": "no flush: per-step working set (A 175 MB, D^-1L/D^-1U 2x75 MB, "
+                         "Krylov basis 520 MB) exceeds the 129 MB L2"},
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
+                       "p99": float(np.percentile(step_ms, 99)),
+                       "per_step": [round(t, 3) for t in step_ms]},
+        "iters": iters,
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "sweep_kernels": sweep,
+        "kernels": kernels,
+        "clocks": clocks,
+    }
+
+    # ---- e2e: the public C-ABI call with host (pinned) buffers ------------
+    bh = torch.from_numpy(pr.b.copy()).pin_memory().numpy()
+    xh = torch.zeros(n, dtype=torch.float64).pin_memory().numpy()
+    for _ in range(1):
+        xh[:] = 0.0
+        gs2.gmres_solve(h, bh, xh, 30, 1e-8, 5000, pc)
+    e2e_t = []
+    for _ in range(max(1, min(args.steps, 3))):
+        xh[:] = 0.0
+        t0 = time.perf_counter()
+        inf = gs2.gmres_solve(h, bh, xh, 30, 1e-8, 5000, pc)
+        e2e_t.append(time.perf_counter() - t0)
+        assert inf.status == 0
+    out["e2e"] = {"value": world / float(np.mean(e2e_t)), "unit": "solves/s",
+                  "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 8 * n,
+                  "note": "gmres_solve with pinned host b and x: H2D of b and x0, "
+                          "solve, D2H of x inside each timed call"}
+
+    if rank == 0 and not args.no_extras and world == 1:
+        out["comparisons"] = comparisons(gs2, torch, pr, stream, b)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        per_iter, full, dt, its = oracle_sample(pr)
+        if full:
+            v = 1.0 / (per_iter * full)
+            out["cpu_baseline"] = {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                   "sample": f"{its} Arnoldi steps of the same GMRES(30)+"
+                                             f"SGS2(1,1) solve ({dt:.1f} s), scaled by the "
+                                             f"oracle's full-solve count {full}"}
+        else:
+            out["cpu_baseline"] = {"value": None, "unit": "solves/s", "cores": 1,
+                                   "kind": "oracle", "sample": "full-solve count not stored"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def comparisons(gs2, torch, pr, stream, b):
+    """One solve each of the paper's baselines and the precision variants on
+    the same workload (untimed by the headline; device-timed here)."""
+    res = {}
+    variants = {
+        "sgs2_1_2": gs2.params("gs2", 1, 2, direction="symmetric"),
+        "sgs2_1_3": gs2.params("gs2", 1, 3, direction="symmetric"),
+        "sgs2_1_1_fp32": gs2.params("gs2", 1, 1, direction="symmetric", precision="fp32"),
+        "sgs2_1_1_fp16": gs2.params("gs2", 1, 1, direction="symmetric", precision="fp16"),
+        "gs_levels_sym": gs2.params("gs", 1, direction="symmetric"),
+        "jr3_w1.0": gs2.params("jr", 3, omega=1.0),
+        "jr3_w0.8": gs2.params("jr", 3, omega=0.8),
+    }
+    h = gs2.gs2_setup(pr.A, precisions=("fp32", "fp16"), stream=stream.cuda_stream)
+    with torch.cuda.stream(stream):
+        x = torch.zeros(pr.n, dtype=torch.float64, device="cuda")
+        for name, p in variants.items():
+            x.zero_()
+            gs2.gmres_solve(h, b, x, 30, 1e-8, 3000, p)  # warm (levels, workspace)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            x.zero_()
+            e0.record(stream)
+            info = gs2.gmres_solve(h, b, x, 30, 1e-8, 3000, p)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            err = float(torch.linalg.norm(x - torch.from_numpy(pr.x_true).cuda()) /
+                        math.sqrt(pr.n))
+            res[name] = {"status": info.status, "iters": info.iters, "ms": round(ms, 2),
+                         "solves_per_s": round(1000.0 / ms, 3),
+                         "true_relres": info.true_relres, "rms_err_vs_x_true": err}
+    h.close()
+    return res
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,228 @@
+/*
+ * gs2.h -- C ABI of the GB300 two-stage Gauss-Seidel library.
+ *
+ * Two-stage Gauss-Seidel (GS2) replaces the sparse triangular solve of a
+ * Gauss-Seidel sweep by a fixed number of inner Jacobi-Richardson (JR)
+ * sweeps (Sec. 3, Eq. (4)-(7)); it is used here as a relaxation and as the
+ * preconditioner of restarted GMRES.  Exact GS through a level-scheduled
+ * triangular solve and damped JR are provided beside it as baselines.
+ *
+ * Conventions shared by every call:
+ *  - Status: every call returns a gs2_status and never throws across the
+ *    ABI.  On failure gs2_last_error() returns a message for the calling
+ *    thread.
+ *  - Matrix: CSR with rowptr int64[n+1], col int32[nnz], val double[nnz].
+ *    Columns may appear in any order inside a row; duplicates are rejected.
+ *    A = L + D + U is split by comparing column and row index (Sec. 3,
+ *    splitting before Eq. (1)).  Every row needs a nonzero diagonal entry.
+ *  - Vectors b and x: double[n].  They may be device pointers (of the
+ *    handle's device) or host pointers (pageable or pinned); host vectors
+ *    are staged through device buffers by the call, which then synchronises
+ *    the stream before returning.  With device vectors a call only enqueues
+ *    work on the handle's stream, except gmres_solve/cg_solve, which read
+ *    back a small status word once per restart cycle.
+ *  - Ownership: gs2_setup copies the matrix; no call keeps a pointer to the
+ *    caller's vectors after it returns.
+ *  - Threads: a handle belongs to one stream and is not thread-safe.
+ *    A server (gs2_server_*) is thread-safe.
+ *  - Results of one handle are bitwise reproducible run to run on the same
+ *    GPU: no floating-point atomics are used.
+ */
+#ifndef GS2_H
+#define GS2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GS2_OK = 0,
+  GS2_ERR_INVALID_ARG = 1,
+  GS2_ERR_ZERO_DIAGONAL = 2,
+  GS2_ERR_OOM = 3,
+  GS2_ERR_CUDA = 4,
+  GS2_ERR_NOT_CONVERGED = 5,
+  GS2_ERR_BREAKDOWN = 6,
+  GS2_ERR_NAN = 7,
+  GS2_ERR_TIMEOUT = 8,
+  GS2_ERR_BUSY = 9,
+  GS2_ERR_NOT_FOUND = 10
+} gs2_status;
+
+typedef enum { GS2_FORWARD = 0, GS2_BACKWARD = 1, GS2_SYMMETRIC = 2 } gs2_direction;
+
+/* Storage and arithmetic of the inner sweeps (the triangles D^{-1}L and
+ * D^{-1}U and the inner iterate g).  The residual r = b - A x (outer
+ * iteration) is always FP64.  Sec. 6.3 runs the preconditioner in single
+ * precision; FP16 with a per-row FP32 scale is an extension of that. */
+typedef enum {
+  GS2_FP64 = 0,
+  GS2_FP32 = 1,
+  GS2_FP16_ROWSCALED = 2
+} gs2_precision;
+
+/* Non-compact form Eq. (4) is the paper's default (Sec. 6 setup); the
+ * compact form Eq. (11) is x <- Mhat^{-1}(b + N x) (undamped). */
+typedef enum { GS2_NONCOMPACT = 0, GS2_COMPACT = 1 } gs2_form;
+
+typedef enum {
+  GS2_PC_NONE = 0, /* identity */
+  GS2_PC_GS2 = 1,  /* two-stage GS, Eq. (4)-(7) with damping */
+  GS2_PC_JR = 2,   /* damped Jacobi-Richardson, `outer` sweeps */
+  GS2_PC_GS = 3    /* exact GS/SOR, level-scheduled, `outer` sweeps */
+} gs2_pc_kind;
+
+/* Relaxation / preconditioner parameters in the paper's notation:
+ * GS2(n_t, n_j) = `outer` global sweeps with `inner` JR sweeps each (Sec. 6
+ * setup; the local sweep count n_k is 1 on one GPU).  omega is the outer
+ * (SOR-like) damping factor and gamma the inner one (Sec. 3, "Damping
+ * factor"): an outer sweep computes r = b - A x, g_0 = D^{-1} r,
+ *   g_{j+1} = (1 - gamma) g_j + gamma D^{-1} (r - omega T g_j),
+ * and x += omega g_{inner}, with T = L (forward) or U (backward).
+ * As a preconditioner the sweeps start from x = 0. */
+typedef struct {
+  int kind;      /* gs2_pc_kind */
+  int outer;     /* n_t >= 1 (sweeps for JR / GS) */
+  int inner;     /* n_j >= 0 */
+  double omega;  /* outer damping, > 0 */
+  double gamma;  /* inner damping, > 0; 1 = undamped */
+  int direction; /* gs2_direction */
+  int precision; /* gs2_precision */
+  int form;      /* gs2_form */
+} gs2_params;
+
+typedef struct {
+  int iters;          /* total Krylov iterations (Arnoldi steps for GMRES) */
+  int cycles;         /* restart cycles (GMRES) / direction restarts (CG) */
+  int status;         /* gs2_status of the solve */
+  double true_relres; /* ||b - A x|| / ||b|| recomputed at exit */
+} gs2_solve_info;
+
+typedef struct {
+  int64_t n, nnz, nnz_lower, nnz_upper;
+  int levels_lower, levels_upper; /* 0 until a level-scheduled call */
+  int64_t device_bytes;           /* device memory held by the handle */
+  int tpr_a, tpr_tri;             /* threads per row of the CSR kernels */
+} gs2_handle_stats;
+
+typedef struct gs2_handle gs2_handle;
+
+/* Create a handle for A (Sec. 3 splitting; Sec. 5.1.3 keeps D^{-1}L and
+ * D^{-1}U prescaled and explicit; Sec. 5.2 keeps the temporaries resident
+ * with A).  Copies A to the current CUDA device, checks it (rowptr
+ * monotone with rowptr[0] = 0 and rowptr[n] = nnz, 0 <= col < n, no
+ * duplicate (i, j), nonzero a_ii in every row) and prepares the inner-sweep
+ * storage for every precision bit set in `precisions` (bit p for
+ * gs2_precision p; FP64 is always prepared, other precisions are also
+ * prepared on first use).
+ *   on_device: 1 if rowptr/col/val are device pointers, 0 if host.
+ *   stream: cudaStream_t the handle enqueues on (NULL = legacy default).
+ * Errors: INVALID_ARG (bad sizes or structure, n or nnz above 2^31 - 1),
+ * ZERO_DIAGONAL, OOM, CUDA. */
+gs2_status gs2_setup(int64_t n, int64_t nnz, const int64_t* rowptr,
+                     const int32_t* col, const double* val, int on_device,
+                     unsigned precisions, void* stream, gs2_handle** out);
+
+/* Release every device and host resource of the handle (NULL is a no-op). */
+void gs2_destroy(gs2_handle* h);
+
+/* Change the stream later calls enqueue on. */
+gs2_status gs2_set_stream(gs2_handle* h, void* stream);
+
+gs2_status gs2_get_stats(const gs2_handle* h, gs2_handle_stats* out);
+
+/* Non-compact GS2 relaxation, Eq. (4) with inner JR sweeps Eq. (5)-(7):
+ * x is read and overwritten (in/out), b is read.  outer_sweeps = n_t >= 0,
+ * inner_sweeps = n_j >= 0 (0 gives JR), damping = omega > 0, direction as
+ * gs2_direction (symmetric = forward then backward, Sec. 3).  FP64,
+ * gamma = 1. */
+gs2_status gs2_apply(gs2_handle* h, const double* b, double* x,
+                     int outer_sweeps, int inner_sweeps, double damping,
+                     int direction);
+
+/* GS2 with every parameter: gamma, precision and compact form.
+ * p->kind is ignored (taken as GS2_PC_GS2). */
+gs2_status gs2_apply_ex(gs2_handle* h, const double* b, double* x,
+                        const gs2_params* p);
+
+/* Exact GS / SOR baseline: x + omega (D + omega T)^{-1} (b - A x) per half
+ * sweep (Sec. 3, "Damping factor"), the triangular solve scheduled by
+ * level sets of T (Sec. 3, level-set scheduling).  Levels are computed on
+ * the first call. x in/out. */
+gs2_status gs_apply(gs2_handle* h, const double* b, double* x, int sweeps,
+                    double omega, int direction);
+
+/* Damped JR baseline: x += omega D^{-1} (b - A x), `sweeps` times (Sec. 3,
+ * zero-inner-sweep case). x in/out. */
+gs2_status jr_apply(gs2_handle* h, const double* b, double* x, int sweeps,
+                    double omega);
+
+/* y = A x (FP64). */
+gs2_status gs2_spmv(gs2_handle* h, const double* x, double* y);
+
+/* Restarted GMRES(restart), right preconditioned by `precond` (NULL = no
+ * preconditioner) applied from a zero start, Arnoldi by classical
+ * Gram-Schmidt applied twice (CGS2) in FP64, Givens rotations in FP64 on
+ * the device (Sec. 6 uses GMRES with GS2; the paper's stopping rule is a
+ * relative residual reduction).  x holds x0 on entry and the solution on
+ * exit.  Stops when the implicit residual |g_{j+1}| <= tol ||b|| and the
+ * recomputed true residual confirms it, or after max_iters Arnoldi steps.
+ * Returns OK, NOT_CONVERGED, BREAKDOWN or NAN (also stored in info->status);
+ * info may be NULL.  1 <= restart <= 64. */
+gs2_status gmres_solve(gs2_handle* h, const double* b, double* x, int restart,
+                       double tol, int max_iters, const gs2_params* precond,
+                       gs2_solve_info* info);
+
+/* Preconditioned CG for SPD A (Sec. 6.2 runs CG with SGS2), same
+ * conventions as gmres_solve; the preconditioner must be symmetric
+ * (GS2/GS with direction SYMMETRIC, JR, or none). */
+gs2_status cg_solve(gs2_handle* h, const double* b, double* x, double tol,
+                    int max_iters, const gs2_params* precond,
+                    gs2_solve_info* info);
+
+/* Many independent systems in one call: system i is solved on hs[i] with
+ * bs[i], xs[i] (device pointers), all with the same restart, tol,
+ * max_iters and preconditioner.  The systems' kernels are interleaved on
+ * the first handle's stream so that small systems share the GPU.
+ * infos[count] receives each system's result; the return value is OK if
+ * every system converged, else the first failing status. */
+gs2_status gs2_batch_solve(gs2_handle* const* hs, const double* const* bs,
+                           double* const* xs, int count, int restart,
+                           double tol, int max_iters, const gs2_params* precond,
+                           gs2_solve_info* infos);
+
+/* ---- per-kernel device timing (CUDA events on the handle's stream) ---- */
+
+typedef struct {
+  char name[32];
+  int64_t launches;
+  double total_ms;
+  double bytes; /* algorithmic bytes summed over the timed launches */
+} gs2_kernel_stat;
+
+/* enable = 1 records an event pair around every launch of the library's
+ * kernels on this handle until disabled; 0 stops and keeps the totals. */
+gs2_status gs2_profile_enable(gs2_handle* h, int enable);
+/* Resolves pending events (synchronising the stream) and copies up to
+ * `cap` per-kernel totals into out; *count receives the number written. */
+gs2_status gs2_profile_read(gs2_handle* h, gs2_kernel_stat* out, int cap,
+                            int* count);
+gs2_status gs2_profile_reset(gs2_handle* h);
+
+/* Thread-local message of the last failing call on this thread. */
+const char* gs2_last_error(void);
+
+/* Library version string. */
+const char* gs2_version(void);
+
+/* Number of CUDA kernel launches this library has made in the process
+ * (all handles, all threads), for accounting of launch counts. */
+int64_t gs2_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GS2_H */

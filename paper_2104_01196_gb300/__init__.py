@@ -1,0 +1,352 @@
+"""GB300 two-stage Gauss-Seidel (GS2) library: Python binding.
+
+Thin ctypes marshalling over the C ABI in ``include/gs2.h`` (libgs2.so, built
+in-tree by ``paper_2104_01196_gb300.build``).  Every step of every solve runs
+in the library's CUDA kernels; this module only turns arrays into pointers.
+There is no CPU fallback: if libgs2.so is missing, loading fails loudly.
+
+Vectors may be torch CUDA tensors (float64, contiguous; used in place) or
+numpy float64 arrays (host memory, staged by the library).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+__all__ = [
+    "GS2Error", "Params", "SolveInfo", "Handle", "load", "gs2_setup", "gs2_apply",
+    "gs2_apply_ex", "gs_apply", "jr_apply", "gs2_spmv", "gmres_solve", "cg_solve",
+    "gs2_batch_solve", "params", "FORWARD", "BACKWARD", "SYMMETRIC", "FP64", "FP32",
+    "FP16_ROWSCALED", "PC_NONE", "PC_GS2", "PC_JR", "PC_GS", "NONCOMPACT", "COMPACT",
+    "STATUS",
+]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgs2.so")
+
+FORWARD, BACKWARD, SYMMETRIC = 0, 1, 2
+FP64, FP32, FP16_ROWSCALED = 0, 1, 2
+PC_NONE, PC_GS2, PC_JR, PC_GS = 0, 1, 2, 3
+NONCOMPACT, COMPACT = 0, 1
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "ZERO_DIAGONAL", 3: "OOM", 4: "CUDA",
+          5: "NOT_CONVERGED", 6: "BREAKDOWN", 7: "NAN", 8: "TIMEOUT", 9: "BUSY",
+          10: "NOT_FOUND"}
+_DIR = {"forward": FORWARD, "backward": BACKWARD, "symmetric": SYMMETRIC}
+_PREC = {"fp64": FP64, "fp32": FP32, "fp16": FP16_ROWSCALED}
+_KIND = {"none": PC_NONE, "gs2": PC_GS2, "jr": PC_JR, "gs": PC_GS}
+
+
+class GS2Error(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("outer", ctypes.c_int), ("inner", ctypes.c_int),
+                ("omega", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("direction", ctypes.c_int), ("precision", ctypes.c_int),
+                ("form", ctypes.c_int)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("cycles", ctypes.c_int), ("status", ctypes.c_int),
+                ("true_relres", ctypes.c_double)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("nnz_lower", ctypes.c_int64),
+                ("nnz_upper", ctypes.c_int64), ("levels_lower", ctypes.c_int),
+                ("levels_upper", ctypes.c_int), ("device_bytes", ctypes.c_int64),
+                ("tpr_a", ctypes.c_int), ("tpr_tri", ctypes.c_int)]
+
+
+class _KStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64),
+                ("total_ms", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
+@dataclass
+class SolveInfo:
+    iters: int
+    cycles: int
+    status: int
+    true_relres: float
+
+    @property
+    def ok(self) -> bool:
+        return self.status == 0
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libgs2.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} is missing: build it with "
+                           "`python -m paper_2104_01196_gb300.build` (needs nvcc)")
+    lib = ctypes.CDLL(p)
+    P, I, I64, D, U = (ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double,
+                       ctypes.c_uint)
+    sig = {
+        "gs2_setup": [I64, I64, P, P, P, I, U, P, ctypes.POINTER(P)],
+        "gs2_set_stream": [P, P],
+        "gs2_get_stats": [P, ctypes.POINTER(_Stats)],
+        "gs2_apply": [P, P, P, I, I, D, I],
+        "gs2_apply_ex": [P, P, P, ctypes.POINTER(Params)],
+        "gs_apply": [P, P, P, I, D, I],
+        "jr_apply": [P, P, P, I, D],
+        "gs2_spmv": [P, P, P],
+        "gmres_solve": [P, P, P, I, D, I, ctypes.POINTER(Params), ctypes.POINTER(_Info)],
+        "cg_solve": [P, P, P, D, I, ctypes.POINTER(Params), ctypes.POINTER(_Info)],
+        "gs2_batch_solve": [P, P, P, I, I, D, I, ctypes.POINTER(Params), ctypes.POINTER(_Info)],
+        "gs2_profile_enable": [P, I],
+        "gs2_profile_read": [P, ctypes.POINTER(_KStat), I, ctypes.POINTER(I)],
+        "gs2_profile_reset": [P],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.gs2_destroy.argtypes = [P]
+    lib.gs2_destroy.restype = None
+    lib.gs2_last_error.restype = ctypes.c_char_p
+    lib.gs2_version.restype = ctypes.c_char_p
+    lib.gs2_launch_count.restype = ctypes.c_int64
+    _lib = lib
+    return lib
+
+
+def _err(st: int):
+    msg = load().gs2_last_error().decode(errors="replace")
+    raise GS2Error(st, msg)
+
+
+def _check(st: int):
+    if st != 0:
+        _err(st)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(a, writable=False):
+    """(pointer, keepalive) of a float64 vector: torch CUDA tensor or numpy."""
+    if a is None:
+        return None, None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags.c_contiguous:
+            raise TypeError("numpy vectors must be contiguous float64")
+        if writable and not a.flags.writeable:
+            raise TypeError("output vector is read-only")
+        return a.ctypes.data, a
+    t = a
+    if t.dtype != _torch().float64 or not t.is_contiguous():
+        raise TypeError("torch vectors must be contiguous float64")
+    return t.data_ptr(), t
+
+
+def params(kind="gs2", outer=1, inner=1, omega=1.0, gamma=1.0, direction="forward",
+           precision="fp64", form="noncompact") -> Params:
+    """gs2_params in the paper's notation: GS2(n_t = outer, n_j = inner)."""
+    k = _KIND[kind] if isinstance(kind, str) else int(kind)
+    d = _DIR[direction] if isinstance(direction, str) else int(direction)
+    p = _PREC[precision] if isinstance(precision, str) else int(precision)
+    f = {"noncompact": NONCOMPACT, "compact": COMPACT}[form] if isinstance(form, str) else int(form)
+    return Params(k, outer, inner, omega, gamma, d, p, f)
+
+
+class Handle:
+    """A matrix resident on the device with its split, triangles and
+    temporaries (library-owned)."""
+
+    def __init__(self, ptr, n, nnz, stream):
+        self._ptr = ptr
+        self.n = n
+        self.nnz = nnz
+        self.stream = stream
+
+    @property
+    def ptr(self):
+        if not self._ptr:
+            raise RuntimeError("handle destroyed")
+        return self._ptr
+
+    def stats(self) -> dict:
+        s = _Stats()
+        _check(load().gs2_get_stats(self.ptr, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in _Stats._fields_}
+
+    def set_stream(self, stream):
+        self.stream = stream
+        _check(load().gs2_set_stream(self.ptr, stream or None))
+
+    def profile(self, enable: bool):
+        _check(load().gs2_profile_enable(self.ptr, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        arr = (_KStat * 64)()
+        cnt = ctypes.c_int(0)
+        _check(load().gs2_profile_read(self.ptr, arr, 64, ctypes.byref(cnt)))
+        return {arr[i].name.decode(): dict(launches=arr[i].launches, total_ms=arr[i].total_ms,
+                                           bytes=arr[i].bytes) for i in range(cnt.value)}
+
+    def profile_reset(self):
+        _check(load().gs2_profile_reset(self.ptr))
+
+    def close(self):
+        if self._ptr:
+            load().gs2_destroy(self._ptr)
+            self._ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _current_stream():
+    try:
+        torch = _torch()
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return 0
+
+
+def gs2_setup(A, precisions=(), stream=None) -> Handle:
+    """Create a handle for CSR A = (rowptr int64, col int32, val float64);
+    arrays may be numpy (host) or torch tensors (host or CUDA)."""
+    rp, ci, va = A
+    keep = []
+    on_dev = 0
+    ptrs = []
+    for arr, dt in ((rp, "int64"), (ci, "int32"), (va, "float64")):
+        if isinstance(arr, np.ndarray):
+            arr = np.ascontiguousarray(arr, dtype=dt)
+            keep.append(arr)
+            ptrs.append(arr.ctypes.data)
+        else:
+            torch = _torch()
+            t = arr.to(getattr(torch, dt)).contiguous()
+            keep.append(t)
+            ptrs.append(t.data_ptr())
+            on_dev = 1 if t.is_cuda else 0
+    n = len(rp) - 1
+    nnz = int(rp[-1])
+    mask = 0
+    for p in precisions:
+        mask |= 1 << (_PREC[p] if isinstance(p, str) else int(p))
+    s = _current_stream() if stream is None else stream
+    out = ctypes.c_void_p()
+    _check(load().gs2_setup(n, nnz, ptrs[0], ptrs[1], ptrs[2], on_dev, mask, s or None,
+                            ctypes.byref(out)))
+    return Handle(out.value, n, nnz, s)
+
+
+def gs2_apply(h, b, x, outer_sweeps=1, inner_sweeps=1, damping=1.0, direction=FORWARD):
+    pb, _kb = _ptr(b)
+    px, _kx = _ptr(x, True)
+    d = _DIR[direction] if isinstance(direction, str) else direction
+    _check(load().gs2_apply(h.ptr, pb, px, outer_sweeps, inner_sweeps, damping, d))
+    return x
+
+
+def gs2_apply_ex(h, b, x, p: Params):
+    pb, _kb = _ptr(b)
+    px, _kx = _ptr(x, True)
+    _check(load().gs2_apply_ex(h.ptr, pb, px, ctypes.byref(p)))
+    return x
+
+
+def gs_apply(h, b, x, sweeps=1, omega=1.0, direction=FORWARD):
+    pb, _kb = _ptr(b)
+    px, _kx = _ptr(x, True)
+    d = _DIR[direction] if isinstance(direction, str) else direction
+    _check(load().gs_apply(h.ptr, pb, px, sweeps, omega, d))
+    return x
+
+
+def jr_apply(h, b, x, sweeps=1, omega=1.0):
+    pb, _kb = _ptr(b)
+    px, _kx = _ptr(x, True)
+    _check(load().jr_apply(h.ptr, pb, px, sweeps, omega))
+    return x
+
+
+def gs2_spmv(h, x, y):
+    px, _kx = _ptr(x)
+    py, _ky = _ptr(y, True)
+    _check(load().gs2_spmv(h.ptr, px, py))
+    return y
+
+
+_SOLVER_STATUSES = (0, 5, 6, 7)
+
+
+def gmres_solve(h, b, x, restart=30, tol=1e-8, max_iters=10000, precond: Params | None = None):
+    """Restarted right-preconditioned GMRES; returns SolveInfo (the solver
+    statuses NOT_CONVERGED / BREAKDOWN / NAN are returned, not raised)."""
+    pb, _kb = _ptr(b)
+    px, _kx = _ptr(x, True)
+    info = _Info()
+    st = load().gmres_solve(h.ptr, pb, px, restart, tol, max_iters,
+                            ctypes.byref(precond) if precond is not None else None,
+                            ctypes.byref(info))
+    if st not in _SOLVER_STATUSES:
+        _err(st)
+    return SolveInfo(info.iters, info.cycles, info.status, info.true_relres)
+
+
+def cg_solve(h, b, x, tol=1e-8, max_iters=10000, precond: Params | None = None):
+    pb, _kb = _ptr(b)
+    px, _kx = _ptr(x, True)
+    info = _Info()
+    st = load().cg_solve(h.ptr, pb, px, tol, max_iters,
+                         ctypes.byref(precond) if precond is not None else None,
+                         ctypes.byref(info))
+    if st not in _SOLVER_STATUSES:
+        _err(st)
+    return SolveInfo(info.iters, info.cycles, info.status, info.true_relres)
+
+
+def gs2_batch_solve(handles, bs, xs, restart=30, tol=1e-8, max_iters=10000,
+                    precond: Params | None = None):
+    """Solve independent systems together; returns a list of SolveInfo."""
+    cnt = len(handles)
+    H = (ctypes.c_void_p * cnt)(*[h.ptr for h in handles])
+    keep = []
+    B = (ctypes.c_void_p * cnt)()
+    X = (ctypes.c_void_p * cnt)()
+    for i in range(cnt):
+        pb, kb = _ptr(bs[i])
+        px, kx = _ptr(xs[i], True)
+        keep += [kb, kx]
+        B[i], X[i] = pb, px
+    infos = (_Info * cnt)()
+    st = load().gs2_batch_solve(H, B, X, cnt, restart, tol, max_iters,
+                                ctypes.byref(precond) if precond is not None else None, infos)
+    if st not in _SOLVER_STATUSES:
+        _err(st)
+    return [SolveInfo(i.iters, i.cycles, i.status, i.true_relres) for i in infos]
+
+
+def version() -> str:
+    return load().gs2_version().decode()
+
+
+def launch_count() -> int:
+    """Kernel launches made by the library in this process so far."""
+    return int(load().gs2_launch_count())

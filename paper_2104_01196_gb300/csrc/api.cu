@@ -1,0 +1,698 @@
+// Host runtime of the GS2 library: handle setup (validation, the A = L + D + U
+// split with prescaled triangles, row tiles, precision copies), the C ABI
+// entry points, host-vector staging and per-kernel event timing.
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <mutex>
+#include <new>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace gs2 {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// ---------------------------------------------------------------------------
+// profiler
+// ---------------------------------------------------------------------------
+
+struct Profiler {
+  bool enabled = false;
+  std::vector<std::string> names;
+  std::unordered_map<std::string, int> ids;
+  std::vector<gs2_kernel_stat> stats;
+  struct Pending {
+    int id;
+    cudaEvent_t a, b;
+    double bytes;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  int id_of(const char* name) {
+    auto it = ids.find(name);
+    if (it != ids.end()) return it->second;
+    const int id = (int)stats.size();
+    ids[name] = id;
+    gs2_kernel_stat s{};
+    std::strncpy(s.name, name, sizeof(s.name) - 1);
+    stats.push_back(s);
+    return id;
+  }
+  void resolve(cudaStream_t st) {
+    if (pending.empty()) return;
+    cudaStreamSynchronize(st);
+    for (auto& p : pending) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+        stats[p.id].launches += 1;
+        stats[p.id].total_ms += ms;
+        stats[p.id].bytes += p.bytes;
+      }
+      pool.push_back(p.a);
+      pool.push_back(p.b);
+    }
+    pending.clear();
+  }
+  ~Profiler() {
+    for (auto& p : pending) {
+      cudaEventDestroy(p.a);
+      cudaEventDestroy(p.b);
+    }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+KernelTimer::KernelTimer(gs2_handle* h_, const char* name, double bytes_)
+    : h(h_), id(-1), bytes(bytes_) {
+  if (h->prof && h->prof->enabled) {
+    id = h->prof->id_of(name);
+    e0 = h->prof->get();
+    cudaEventRecord(e0, h->stream);
+  }
+}
+
+KernelTimer::~KernelTimer() {
+  if (id >= 0 && e0) {
+    cudaEvent_t e1 = h->prof->get();
+    cudaEventRecord(e1, h->stream);
+    h->prof->pending.push_back({id, e0, e1, bytes});
+    // keep the pending list bounded on long runs
+    if (h->prof->pending.size() > 4096) h->prof->resolve(h->stream);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// setup helpers
+// ---------------------------------------------------------------------------
+
+constexpr int kHardCap = 6144;  // staged entries per tile at most
+constexpr int kPad = 16;        // padding entries after every CSR array
+
+static int choose_lanes(double mean) {
+  int K = 1;
+  while (K < 16 && mean / K > 24.0) K *= 2;
+  return K;
+}
+
+static void build_tiles(const std::vector<int>& rp, int n, int K, std::vector<int>& tiles,
+                        int& cap) {
+  const int R = kRowThreads / K;
+  tiles.clear();
+  tiles.push_back(0);
+  int maxnz = 0;
+  int r = 0;
+  while (r < n) {
+    int len = rp[r + 1] - rp[r];
+    if (len > kHardCap) {
+      ++r;
+      tiles.push_back(r);
+      continue;
+    }
+    int cnt = 0, nz = 0;
+    while (r < n && cnt < R) {
+      len = rp[r + 1] - rp[r];
+      if (len > kHardCap || nz + len > kHardCap) break;
+      nz += len;
+      ++cnt;
+      ++r;
+    }
+    maxnz = std::max(maxnz, nz);
+    tiles.push_back(r);
+  }
+  cap = ((maxnz + 7) / 8) * 8;
+  if (cap < 8) cap = 8;
+}
+
+static void upload_csr(gs2_handle* h, DevCsr& M, int n, const std::vector<int>& rp,
+                       const std::vector<int>& ci, const std::vector<double>& va) {
+  M.n = n;
+  M.nnz = (int)ci.size();
+  M.mean_row = n ? (double)M.nnz / n : 0.0;
+  M.tpr = choose_lanes(M.mean_row);
+  const size_t nz = (size_t)M.nnz + kPad;
+  M.rp = (int*)h->dalloc(sizeof(int) * (n + 1));
+  M.ci = (int*)h->dalloc(sizeof(int) * nz);
+  M.va = (double*)h->dalloc(sizeof(double) * nz);
+  GS2_CUDA(cudaMemcpy(M.rp, rp.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
+  GS2_CUDA(cudaMemset(M.ci, 0, sizeof(int) * nz));
+  GS2_CUDA(cudaMemset(M.va, 0, sizeof(double) * nz));
+  if (M.nnz) {
+    GS2_CUDA(cudaMemcpy(M.ci, ci.data(), sizeof(int) * M.nnz, cudaMemcpyHostToDevice));
+    GS2_CUDA(cudaMemcpy(M.va, va.data(), sizeof(double) * M.nnz, cudaMemcpyHostToDevice));
+  }
+  std::vector<int> tiles;
+  build_tiles(rp, n, M.tpr, tiles, M.cap);
+  M.ntiles = (int)tiles.size() - 1;
+  M.tile_row = (int*)h->dalloc(sizeof(int) * tiles.size());
+  GS2_CUDA(cudaMemcpy(M.tile_row, tiles.data(), sizeof(int) * tiles.size(),
+                      cudaMemcpyHostToDevice));
+}
+
+// FP32 copy and FP16 copy with per-row scale s_i = max_j |v_ij| of a
+// triangle (Sec. 6.3 single-precision preconditioner; FP16 with row scale
+// is an extension of it).
+struct HostTri {
+  std::vector<int> rp, ci;
+  std::vector<double> va;
+};
+
+static void prepare_lowprec(gs2_handle* h, DevCsr& M, const HostTri& T, int prec) {
+  const size_t nz = (size_t)M.nnz + kPad;
+  if (prec == GS2_FP32 && !M.va32) {
+    std::vector<float> v(nz, 0.f);
+    for (int k = 0; k < M.nnz; ++k) v[k] = (float)T.va[k];
+    M.va32 = (float*)h->dalloc(sizeof(float) * nz);
+    GS2_CUDA(cudaMemcpy(M.va32, v.data(), sizeof(float) * nz, cudaMemcpyHostToDevice));
+  }
+  if (prec == GS2_FP16_ROWSCALED && !M.va16) {
+    std::vector<__half> v(nz, __float2half(0.f));
+    std::vector<float> s(M.n, 0.f);
+    for (int i = 0; i < M.n; ++i) {
+      double m = 0.0;
+      for (int k = T.rp[i]; k < T.rp[i + 1]; ++k) m = std::max(m, std::fabs(T.va[k]));
+      s[i] = (float)m;
+      for (int k = T.rp[i]; k < T.rp[i + 1]; ++k)
+        v[k] = __float2half(m > 0 ? (float)(T.va[k] / m) : 0.f);
+    }
+    M.va16 = (__half*)h->dalloc(sizeof(__half) * nz);
+    M.scale16 = (float*)h->dalloc(sizeof(float) * std::max(M.n, 1));
+    GS2_CUDA(cudaMemcpy(M.va16, v.data(), sizeof(__half) * nz, cudaMemcpyHostToDevice));
+    if (M.n)
+      GS2_CUDA(cudaMemcpy(M.scale16, s.data(), sizeof(float) * M.n, cudaMemcpyHostToDevice));
+  }
+}
+
+}  // namespace gs2
+
+// host copies of the triangles, kept for lazy precision / level setup
+struct gs2_host_side {
+  gs2::HostTri L, U;
+};
+static std::mutex g_host_mu;
+static std::unordered_map<const gs2_handle*, gs2_host_side*> g_host;
+
+void* gs2_handle::dalloc(size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    GS2_THROW(e == cudaErrorMemoryAllocation ? GS2_ERR_OOM : GS2_ERR_CUDA,
+              std::string("cudaMalloc(") + std::to_string(bytes) + "): " +
+                  cudaGetErrorString(e));
+  }
+  allocs.push_back(p);
+  dev_bytes += (int64_t)bytes;
+  return p;
+}
+
+namespace gs2 {
+
+static gs2_host_side* host_side(const gs2_handle* h) {
+  std::lock_guard<std::mutex> g(g_host_mu);
+  auto it = g_host.find(h);
+  return it == g_host.end() ? nullptr : it->second;
+}
+
+void ensure_precision(gs2_handle* h, int prec) {
+  if (prec == GS2_FP64) return;
+  if (prec != GS2_FP32 && prec != GS2_FP16_ROWSCALED)
+    GS2_THROW(GS2_ERR_INVALID_ARG, "unknown precision");
+  gs2_host_side* hs = host_side(h);
+  prepare_lowprec(h, h->L, hs->L, prec);
+  prepare_lowprec(h, h->U, hs->U, prec);
+  if (!h->rhat32) {
+    const size_t n = std::max<int64_t>(h->n, 1);
+    h->rhat32 = (float*)h->dalloc(sizeof(float) * n);
+    h->g32a = (float*)h->dalloc(sizeof(float) * n);
+    h->g32b = (float*)h->dalloc(sizeof(float) * n);
+  }
+}
+
+// Level sets of the triangles (level-set scheduling, Sec. 3): level(i) =
+// 1 + max level over row i's dependencies; rows are grouped by level.
+void ensure_levels(gs2_handle* h) {
+  if (h->levels_ready) return;
+  gs2_host_side* hs = host_side(h);
+  const int n = (int)h->n;
+  auto build = [&](const HostTri& T, bool lower, std::vector<int>& ptr, int*& rows_dev) {
+    std::vector<int> lev(n, 0);
+    int nlev = n ? 1 : 0;
+    for (int s = 0; s < n; ++s) {
+      const int i = lower ? s : n - 1 - s;
+      int lv = 0;
+      for (int k = T.rp[i]; k < T.rp[i + 1]; ++k) lv = std::max(lv, lev[T.ci[k]] + 1);
+      lev[i] = lv;
+      nlev = std::max(nlev, lv + 1);
+    }
+    ptr.assign(nlev + 1, 0);
+    for (int i = 0; i < n; ++i) ptr[lev[i] + 1]++;
+    for (int l = 0; l < nlev; ++l) ptr[l + 1] += ptr[l];
+    std::vector<int> fill(ptr.begin(), ptr.end() - 1), rows(std::max(n, 1));
+    for (int i = 0; i < n; ++i) rows[fill[lev[i]]++] = i;
+    rows_dev = (int*)h->dalloc(sizeof(int) * std::max(n, 1));
+    GS2_CUDA(cudaMemcpy(rows_dev, rows.data(), sizeof(int) * std::max(n, 1),
+                        cudaMemcpyHostToDevice));
+  };
+  build(hs->L, true, h->lev_ptr_L, h->lev_rows_L);
+  build(hs->U, false, h->lev_ptr_U, h->lev_rows_U);
+  h->levels_ready = true;
+}
+
+static bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Host-vector staging: device pointers pass through; host vectors are
+// copied to the handle's staging buffers and x is copied back at the end.
+struct Staged {
+  gs2_handle* h;
+  const double* b;
+  double* x;
+  double* x_user;
+  bool host_x = false;
+  Staged(gs2_handle* h_, const double* b_user, double* x_user_, bool x_in)
+      : h(h_), b(b_user), x(x_user_), x_user(x_user_) {
+    const size_t bytes = sizeof(double) * h->n;
+    if (b_user && !is_device_ptr(b_user)) {
+      GS2_CUDA(cudaMemcpyAsync(h->bstage, b_user, bytes, cudaMemcpyHostToDevice, h->stream));
+      b = h->bstage;
+    }
+    if (x_user_ && !is_device_ptr(x_user_)) {
+      host_x = true;
+      if (x_in)
+        GS2_CUDA(cudaMemcpyAsync(h->xstage, x_user_, bytes, cudaMemcpyHostToDevice,
+                                 h->stream));
+      x = h->xstage;
+    }
+  }
+  void finish() {
+    if (host_x) {
+      GS2_CUDA(cudaMemcpyAsync(x_user, h->xstage, sizeof(double) * h->n,
+                               cudaMemcpyDeviceToHost, h->stream));
+      GS2_CUDA(cudaStreamSynchronize(h->stream));
+    } else if (b != nullptr && b == h->bstage) {
+      GS2_CUDA(cudaStreamSynchronize(h->stream));
+    }
+  }
+};
+
+static void check_params(const gs2_params* p) {
+  if (!p) return;
+  if (p->kind < GS2_PC_NONE || p->kind > GS2_PC_GS)
+    GS2_THROW(GS2_ERR_INVALID_ARG, "unknown preconditioner kind");
+  if (p->kind == GS2_PC_NONE) return;
+  if (p->outer < 1 || p->outer > 1000) GS2_THROW(GS2_ERR_INVALID_ARG, "outer sweeps < 1");
+  if (p->inner < 0 || p->inner > 100000) GS2_THROW(GS2_ERR_INVALID_ARG, "inner sweeps < 0");
+  if (!(p->omega > 0.0) || !std::isfinite(p->omega))
+    GS2_THROW(GS2_ERR_INVALID_ARG, "omega must be > 0");
+  if (!(p->gamma > 0.0) || !std::isfinite(p->gamma))
+    GS2_THROW(GS2_ERR_INVALID_ARG, "gamma must be > 0");
+  if (p->direction < 0 || p->direction > 2) GS2_THROW(GS2_ERR_INVALID_ARG, "direction");
+  if (p->precision < 0 || p->precision > 2) GS2_THROW(GS2_ERR_INVALID_ARG, "precision");
+  if (p->form != GS2_NONCOMPACT && p->form != GS2_COMPACT)
+    GS2_THROW(GS2_ERR_INVALID_ARG, "form");
+  if (p->form == GS2_COMPACT && (p->kind != GS2_PC_GS2 || p->omega != 1.0 || p->gamma != 1.0))
+    GS2_THROW(GS2_ERR_INVALID_ARG, "the compact form is undamped GS2 (omega = gamma = 1)");
+}
+
+}  // namespace gs2
+
+using namespace gs2;
+
+#define API_BEGIN try {
+#define API_END                                        \
+  }                                                    \
+  catch (const gs2::Error& e) {                        \
+    gs2::set_error(e.msg);                             \
+    return e.st;                                       \
+  }                                                    \
+  catch (const std::bad_alloc&) {                      \
+    gs2::set_error("host allocation failed");          \
+    return GS2_ERR_OOM;                                \
+  }                                                    \
+  catch (...) {                                        \
+    gs2::set_error("unexpected C++ exception");        \
+    return GS2_ERR_CUDA;                               \
+  }
+
+static void destroy_impl(gs2_handle* h) {
+  if (!h) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  delete h->prof;
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->st_host) cudaFreeHost(h->st_host);
+  if (h->stop_mapped) cudaFreeHost((void*)h->stop_mapped);
+  {
+    std::lock_guard<std::mutex> g(g_host_mu);
+    auto it = g_host.find(h);
+    if (it != g_host.end()) {
+      delete it->second;
+      g_host.erase(it);
+    }
+  }
+  delete h;
+  cudaSetDevice(cur);
+}
+
+extern "C" {
+
+const char* gs2_last_error(void) { return g_last_error.c_str(); }
+
+const char* gs2_version(void) { return "gs2-gb300 0.1 (sm_103a)"; }
+
+int64_t gs2_launch_count(void) { return (int64_t)g_launches.load(); }
+
+gs2_status gs2_setup(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col,
+                     const double* val, int on_device, unsigned precisions, void* stream,
+                     gs2_handle** out) {
+  if (!out) {
+    set_error("out is NULL");
+    return GS2_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  gs2_handle* h = nullptr;
+  API_BEGIN
+  if (n < 0 || nnz < 0) GS2_THROW(GS2_ERR_INVALID_ARG, "negative size");
+  if (n > std::numeric_limits<int>::max() - 1 || nnz > std::numeric_limits<int>::max() - 64)
+    GS2_THROW(GS2_ERR_INVALID_ARG, "n or nnz above 2^31 - 1");
+  if (!rowptr || (nnz > 0 && (!col || !val)))
+    GS2_THROW(GS2_ERR_INVALID_ARG, "NULL CSR array");
+  // host copies of the input
+  std::vector<int64_t> rp64(n + 1);
+  std::vector<int32_t> ci(nnz);
+  std::vector<double> va(nnz);
+  if (on_device) {
+    GS2_CUDA(cudaMemcpy(rp64.data(), rowptr, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost));
+    if (nnz) {
+      GS2_CUDA(cudaMemcpy(ci.data(), col, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost));
+      GS2_CUDA(cudaMemcpy(va.data(), val, sizeof(double) * nnz, cudaMemcpyDeviceToHost));
+    }
+  } else {
+    std::memcpy(rp64.data(), rowptr, sizeof(int64_t) * (n + 1));
+    if (nnz) {
+      std::memcpy(ci.data(), col, sizeof(int32_t) * nnz);
+      std::memcpy(va.data(), val, sizeof(double) * nnz);
+    }
+  }
+  // validation
+  if (rp64[0] != 0 || rp64[n] != nnz)
+    GS2_THROW(GS2_ERR_INVALID_ARG, "rowptr[0] must be 0 and rowptr[n] must be nnz");
+  for (int64_t i = 0; i < n; ++i)
+    if (rp64[i + 1] < rp64[i]) GS2_THROW(GS2_ERR_INVALID_ARG, "rowptr is not monotone");
+  std::vector<int> seen(n, -1);
+  std::vector<double> diag(n, 0.0);
+  for (int64_t i = 0; i < n; ++i) {
+    bool has_diag = false;
+    for (int64_t k = rp64[i]; k < rp64[i + 1]; ++k) {
+      const int64_t j = ci[k];
+      if (j < 0 || j >= n)
+        GS2_THROW(GS2_ERR_INVALID_ARG, "column index out of range in row " + std::to_string(i));
+      if (seen[j] == (int)i)
+        GS2_THROW(GS2_ERR_INVALID_ARG, "duplicate entry in row " + std::to_string(i));
+      seen[j] = (int)i;
+      if (j == i) {
+        has_diag = true;
+        diag[i] = va[k];
+      }
+    }
+    if (!has_diag || diag[i] == 0.0 || !std::isfinite(diag[i]))
+      GS2_THROW(GS2_ERR_ZERO_DIAGONAL, "zero or missing diagonal in row " + std::to_string(i));
+  }
+  // split A = L + D + U, triangles prescaled by D^{-1} (Sec. 5.1.3)
+  std::vector<int> rp32(n + 1);
+  for (int64_t i = 0; i <= n; ++i) rp32[i] = (int)rp64[i];
+  auto* hs = new gs2_host_side();
+  HostTri& L = hs->L;
+  HostTri& U = hs->U;
+  L.rp.assign(n + 1, 0);
+  U.rp.assign(n + 1, 0);
+  for (int64_t i = 0; i < n; ++i) {
+    const double di = 1.0 / diag[i];
+    for (int64_t k = rp64[i]; k < rp64[i + 1]; ++k) {
+      const int j = ci[k];
+      if (j < i) {
+        L.ci.push_back(j);
+        L.va.push_back(va[k] * di);
+      } else if (j > i) {
+        U.ci.push_back(j);
+        U.va.push_back(va[k] * di);
+      }
+    }
+    L.rp[i + 1] = (int)L.ci.size();
+    U.rp[i + 1] = (int)U.ci.size();
+  }
+  h = new gs2_handle();
+  {
+    std::lock_guard<std::mutex> g(g_host_mu);
+    g_host[h] = hs;
+  }
+  GS2_CUDA(cudaGetDevice(&h->device));
+  GS2_CUDA(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device));
+  h->stream = (cudaStream_t)stream;
+  h->n = n;
+  h->nnz = nnz;
+  upload_csr(h, h->A, (int)n, rp32, std::vector<int>(ci.begin(), ci.end()), va);
+  upload_csr(h, h->L, (int)n, L.rp, L.ci, L.va);
+  upload_csr(h, h->U, (int)n, U.rp, U.ci, U.va);
+  std::vector<double> dinv(n);
+  for (int64_t i = 0; i < n; ++i) dinv[i] = 1.0 / diag[i];
+  const size_t nv = (size_t)std::max<int64_t>(n, 1);
+  h->dinv = (double*)h->dalloc(sizeof(double) * nv);
+  if (n) GS2_CUDA(cudaMemcpy(h->dinv, dinv.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+  h->r = (double*)h->dalloc(sizeof(double) * nv);
+  h->rhat = (double*)h->dalloc(sizeof(double) * nv);
+  h->g0 = (double*)h->dalloc(sizeof(double) * nv);
+  h->g1 = (double*)h->dalloc(sizeof(double) * nv);
+  h->z = (double*)h->dalloc(sizeof(double) * nv);
+  h->t = (double*)h->dalloc(sizeof(double) * nv);
+  h->bstage = (double*)h->dalloc(sizeof(double) * nv);
+  h->xstage = (double*)h->dalloc(sizeof(double) * nv);
+  h->nblk = vec_blocks(h, n);
+  h->part_cap = h->nblk * (kMaxRestart + 2);
+  h->part = (double*)h->dalloc(sizeof(double) * h->part_cap);
+  for (int p = 1; p <= 2; ++p)
+    if (precisions & (1u << p)) ensure_precision(h, p);
+  GS2_CUDA(cudaDeviceSynchronize());
+  *out = h;
+  return GS2_OK;
+  }
+  catch (const gs2::Error& e) {
+    gs2::set_error(e.msg);
+    destroy_impl(h);
+    return e.st;
+  }
+  catch (const std::bad_alloc&) {
+    gs2::set_error("host allocation failed");
+    destroy_impl(h);
+    return GS2_ERR_OOM;
+  }
+  catch (...) {
+    gs2::set_error("unexpected C++ exception");
+    destroy_impl(h);
+    return GS2_ERR_CUDA;
+  }
+}
+
+void gs2_destroy(gs2_handle* h) { destroy_impl(h); }
+
+gs2_status gs2_set_stream(gs2_handle* h, void* stream) {
+  if (!h) return GS2_ERR_INVALID_ARG;
+  h->stream = (cudaStream_t)stream;
+  return GS2_OK;
+}
+
+gs2_status gs2_get_stats(const gs2_handle* h, gs2_handle_stats* out) {
+  if (!h || !out) return GS2_ERR_INVALID_ARG;
+  out->n = h->n;
+  out->nnz = h->nnz;
+  out->nnz_lower = h->L.nnz;
+  out->nnz_upper = h->U.nnz;
+  out->levels_lower = h->levels_ready ? (int)h->lev_ptr_L.size() - 1 : 0;
+  out->levels_upper = h->levels_ready ? (int)h->lev_ptr_U.size() - 1 : 0;
+  out->device_bytes = h->dev_bytes;
+  out->tpr_a = h->A.tpr;
+  out->tpr_tri = h->L.tpr;
+  return GS2_OK;
+}
+
+gs2_status gs2_apply_ex(gs2_handle* h, const double* b, double* x, const gs2_params* p) {
+  if (!h || !p || (h->n && (!b || !x))) {
+    set_error("NULL argument");
+    return GS2_ERR_INVALID_ARG;
+  }
+  API_BEGIN
+  gs2_params q = *p;
+  q.kind = GS2_PC_GS2;
+  check_params(&q);
+  if (q.outer == 0 || h->n == 0) return GS2_OK;
+  ensure_precision(h, q.precision);
+  Staged s(h, b, x, true);
+  gs2_relax(h, s.b, s.x, &q);
+  s.finish();
+  return GS2_OK;
+  API_END
+}
+
+gs2_status gs2_apply(gs2_handle* h, const double* b, double* x, int outer_sweeps,
+                     int inner_sweeps, double damping, int direction) {
+  if (outer_sweeps == 0) return h ? GS2_OK : GS2_ERR_INVALID_ARG;
+  gs2_params p{GS2_PC_GS2, outer_sweeps, inner_sweeps, damping, 1.0, direction,
+               GS2_FP64, GS2_NONCOMPACT};
+  return gs2_apply_ex(h, b, x, &p);
+}
+
+gs2_status gs_apply(gs2_handle* h, const double* b, double* x, int sweeps, double omega,
+                    int direction) {
+  if (!h || (h->n && (!b || !x))) return GS2_ERR_INVALID_ARG;
+  API_BEGIN
+  if (sweeps < 0 || !(omega > 0.0) || direction < 0 || direction > 2)
+    GS2_THROW(GS2_ERR_INVALID_ARG, "bad sweeps/omega/direction");
+  if (sweeps == 0 || h->n == 0) return GS2_OK;
+  ensure_levels(h);
+  Staged s(h, b, x, true);
+  gs_relax(h, s.b, s.x, sweeps, omega, direction);
+  s.finish();
+  return GS2_OK;
+  API_END
+}
+
+gs2_status jr_apply(gs2_handle* h, const double* b, double* x, int sweeps, double omega) {
+  if (!h || (h->n && (!b || !x))) return GS2_ERR_INVALID_ARG;
+  API_BEGIN
+  if (sweeps < 0 || !(omega > 0.0)) GS2_THROW(GS2_ERR_INVALID_ARG, "bad sweeps/omega");
+  if (sweeps == 0 || h->n == 0) return GS2_OK;
+  Staged s(h, b, x, true);
+  jr_relax(h, s.b, s.x, sweeps, omega);
+  s.finish();
+  return GS2_OK;
+  API_END
+}
+
+gs2_status gs2_spmv(gs2_handle* h, const double* x, double* y) {
+  if (!h || (h->n && (!x || !y))) return GS2_ERR_INVALID_ARG;
+  API_BEGIN
+  if (h->n == 0) return GS2_OK;
+  Staged s(h, x, y, false);
+  launch_spmv(h, s.b, s.x, nullptr);
+  s.finish();
+  return GS2_OK;
+  API_END
+}
+
+gs2_status gmres_solve(gs2_handle* h, const double* b, double* x, int restart, double tol,
+                       int max_iters, const gs2_params* precond, gs2_solve_info* info) {
+  if (!h || (h->n && (!b || !x))) return GS2_ERR_INVALID_ARG;
+  API_BEGIN
+  if (restart < 1 || restart > kMaxRestart || !(tol >= 0.0) || max_iters < 0)
+    GS2_THROW(GS2_ERR_INVALID_ARG, "restart must be in [1, 64], tol >= 0, max_iters >= 0");
+  check_params(precond);
+  if (precond && precond->kind == GS2_PC_GS2) ensure_precision(h, precond->precision);
+  if (precond && precond->kind == GS2_PC_GS) ensure_levels(h);
+  Staged s(h, b, x, true);
+  gs2_status st = gmres_run(h, s.b, s.x, restart, tol, max_iters, precond, info);
+  s.finish();
+  return st;
+  API_END
+}
+
+gs2_status cg_solve(gs2_handle* h, const double* b, double* x, double tol, int max_iters,
+                    const gs2_params* precond, gs2_solve_info* info) {
+  if (!h || (h->n && (!b || !x))) return GS2_ERR_INVALID_ARG;
+  API_BEGIN
+  if (!(tol >= 0.0) || max_iters < 0) GS2_THROW(GS2_ERR_INVALID_ARG, "tol/max_iters");
+  check_params(precond);
+  if (precond && precond->kind == GS2_PC_GS2) ensure_precision(h, precond->precision);
+  if (precond && precond->kind == GS2_PC_GS) ensure_levels(h);
+  Staged s(h, b, x, true);
+  gs2_status st = cg_run(h, s.b, s.x, tol, max_iters, precond, info);
+  s.finish();
+  return st;
+  API_END
+}
+
+gs2_status gs2_batch_solve(gs2_handle* const* hs, const double* const* bs, double* const* xs,
+                           int count, int restart, double tol, int max_iters,
+                           const gs2_params* precond, gs2_solve_info* infos) {
+  if (count < 0 || (count > 0 && (!hs || !bs || !xs))) return GS2_ERR_INVALID_ARG;
+  API_BEGIN
+  if (restart < 1 || restart > kMaxRestart || !(tol >= 0.0) || max_iters < 0)
+    GS2_THROW(GS2_ERR_INVALID_ARG, "restart must be in [1, 64], tol >= 0, max_iters >= 0");
+  check_params(precond);
+  for (int i = 0; i < count; ++i) {
+    if (!hs[i]) GS2_THROW(GS2_ERR_INVALID_ARG, "NULL handle in batch");
+    if (hs[i]->n && (!is_device_ptr(bs[i]) || !is_device_ptr(xs[i])))
+      GS2_THROW(GS2_ERR_INVALID_ARG, "batch vectors must be device pointers");
+    for (int k = 0; k < i; ++k)
+      if (hs[k] == hs[i]) GS2_THROW(GS2_ERR_INVALID_ARG, "a handle appears twice in a batch");
+    if (precond && precond->kind == GS2_PC_GS2) ensure_precision(hs[i], precond->precision);
+    if (precond && precond->kind == GS2_PC_GS) ensure_levels(hs[i]);
+  }
+  return gmres_batch(hs, bs, xs, count, restart, tol, max_iters, precond, infos);
+  API_END
+}
+
+gs2_status gs2_profile_enable(gs2_handle* h, int enable) {
+  if (!h) return GS2_ERR_INVALID_ARG;
+  if (!h->prof) h->prof = new gs2::Profiler();
+  h->prof->enabled = enable != 0;
+  return GS2_OK;
+}
+
+gs2_status gs2_profile_read(gs2_handle* h, gs2_kernel_stat* out, int cap, int* count) {
+  if (!h || !count || (cap > 0 && !out)) return GS2_ERR_INVALID_ARG;
+  *count = 0;
+  if (!h->prof) return GS2_OK;
+  h->prof->resolve(h->stream);
+  const int m = std::min<int>(cap, (int)h->prof->stats.size());
+  for (int i = 0; i < m; ++i) out[i] = h->prof->stats[i];
+  *count = m;
+  return GS2_OK;
+}
+
+gs2_status gs2_profile_reset(gs2_handle* h) {
+  if (!h) return GS2_ERR_INVALID_ARG;
+  if (!h->prof) return GS2_OK;
+  h->prof->resolve(h->stream);
+  for (auto& s : h->prof->stats) {
+    s.launches = 0;
+    s.total_ms = 0;
+    s.bytes = 0;
+  }
+  return GS2_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,220 @@
+// Internal declarations of the GS2 library: handle layout, error plumbing,
+// kernel launchers.  Not part of the public ABI (include/gs2.h is).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/gs2.h"
+
+namespace gs2 {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+
+void set_error(const std::string& msg);
+
+struct Error {
+  gs2_status st;
+  std::string msg;
+};
+
+#define GS2_THROW(st, msg) throw ::gs2::Error{(st), (msg)}
+#define GS2_CUDA(call)                                                      \
+  do {                                                                      \
+    cudaError_t e_ = (call);                                                \
+    if (e_ != cudaSuccess)                                                  \
+      GS2_THROW(e_ == cudaErrorMemoryAllocation ? GS2_ERR_OOM : GS2_ERR_CUDA, \
+                std::string(#call) + ": " + cudaGetErrorString(e_));         \
+  } while (0)
+// every kernel launch of the library is followed by this check, which also
+// counts it (gs2_launch_count)
+void count_launch();
+#define GS2_LAUNCH_CHECK()          \
+  do {                              \
+    ::gs2::count_launch();          \
+    GS2_CUDA(cudaGetLastError());   \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// device storage
+// ---------------------------------------------------------------------------
+
+// A CSR matrix on the device with 32-bit indices.  `va` is FP64; the
+// triangles also carry FP32 values and FP16 values with an FP32 per-row
+// scale (s_i = max_j |v_ij|, stored v_ij / s_i) once prepared.
+struct DevCsr {
+  int n = 0;
+  int nnz = 0;
+  int* rp = nullptr;       // n + 1
+  int* ci = nullptr;       // nnz (padded)
+  double* va = nullptr;    // nnz (padded)
+  float* va32 = nullptr;   // FP32 copy (triangles)
+  __half* va16 = nullptr;  // FP16 scaled copy (triangles)
+  float* scale16 = nullptr;
+  int tpr = 1;             // lanes per row (K) of the tile kernels
+  // row tiles: rows [tile_row[t], tile_row[t+1]); a tile with more than
+  // `cap` entries holds exactly one (long) row
+  int ntiles = 0;
+  int cap = 0;
+  int* tile_row = nullptr;  // ntiles + 1
+  double mean_row = 0.0;
+};
+
+// Device-resident GMRES / CG state, one per handle.
+struct KrylovState {
+  int stop;      // 1: the current cycle has ended (converged/limit/breakdown)
+  int status;    // gs2_status seen by the device
+  int k;         // Arnoldi steps taken in the current cycle
+  int iters;     // total Arnoldi steps
+  int max_iters;
+  int pad_;
+  double tol_abs;  // tol * ||b||
+  double bnorm;
+  double beta;     // ||r0|| of the cycle
+  double hn;       // last H(j+1, j)
+  double inv_hn;
+  double rz;       // CG: r.z
+  double alpha;
+};
+
+struct Profiler;
+
+}  // namespace gs2
+
+struct gs2_handle {
+  int device = 0;
+  int nsm = 0;
+  cudaStream_t stream = nullptr;
+  int64_t n = 0, nnz = 0;
+  gs2::DevCsr A, L, U;  // L, U prescaled: D^{-1} L and D^{-1} U
+  double* dinv = nullptr;
+  int64_t dev_bytes = 0;
+  std::vector<void*> allocs;
+
+  // resident temporaries (Sec. 5.2: allocated once per matrix)
+  double *r = nullptr, *rhat = nullptr, *g0 = nullptr, *g1 = nullptr;
+  double *z = nullptr, *t = nullptr, *bstage = nullptr, *xstage = nullptr;
+  float *rhat32 = nullptr, *g32a = nullptr, *g32b = nullptr;
+  double* part = nullptr;  // per-block partial sums
+  int nblk = 0;            // blocks of the vector kernels
+  int part_cap = 0;        // doubles in `part`
+
+  // level sets (lazy)
+  bool levels_ready = false;
+  std::vector<int> lev_ptr_L, lev_ptr_U;  // host, nlev + 1
+  int* lev_rows_L = nullptr;
+  int* lev_rows_U = nullptr;
+
+  // Krylov workspace (lazy, grows with restart)
+  int kry_m = 0;
+  double *V = nullptr, *w = nullptr, *H = nullptr, *hbuf = nullptr;
+  double *gvec = nullptr, *cs = nullptr, *sn = nullptr, *y = nullptr;
+  double *p = nullptr, *q = nullptr;
+  gs2::KrylovState* st = nullptr;       // device
+  gs2::KrylovState* st_host = nullptr;  // pinned mirror
+  volatile int* stop_mapped = nullptr;  // pinned, device-mapped stop flag
+  int* stop_mapped_dev = nullptr;
+
+  gs2::Profiler* prof = nullptr;
+
+  void* dalloc(size_t bytes);
+};
+
+namespace gs2 {
+
+// ---------------------------------------------------------------------------
+// profiling: optional event pairs around launches
+// ---------------------------------------------------------------------------
+
+struct KernelTimer {
+  gs2_handle* h;
+  int id;
+  double bytes;
+  cudaEvent_t e0 = nullptr;
+  KernelTimer(gs2_handle* h_, const char* name, double bytes_);
+  ~KernelTimer();
+};
+
+// ---------------------------------------------------------------------------
+// launchers (kernels.cu)
+// ---------------------------------------------------------------------------
+
+// r-hat (and optionally r) from r = b - A x in FP64; rhat written in the
+// sweep precision (rhat64 or rhat32, whichever is non-null).
+void launch_resid(gs2_handle* h, const double* b, const double* x,
+                  double* r_out, double* rhat64, float* rhat32,
+                  const int* skip);
+
+// Elementwise r-hat = D^{-1} v (v FP64) in the sweep precision.
+void launch_prep_rhat(gs2_handle* h, const double* v, double* rhat64,
+                      float* rhat32, const int* skip);
+
+enum InnerMode { INNER_MID = 0, INNER_LAST_ADD = 1, INNER_LAST_SET = 2 };
+
+// One inner JR sweep on triangle T (h->L or h->U):
+//   g_out = (1-gamma) g_in + gamma (rhat - omega T g_in)
+// MID writes g_out; LAST_ADD does x += omega g_out; LAST_SET does
+// x = omega g_out.  Vectors are FP64 for prec == GS2_FP64, else FP32.
+void launch_inner(gs2_handle* h, const DevCsr& T, int prec, const void* rhat,
+                  const void* g_in, void* g_out, double* x, double omega,
+                  double gamma, int mode, const int* skip);
+
+// x = omega * rhat (zero inner sweeps from a zero start) or x += omega*rhat.
+void launch_rhat_update(gs2_handle* h, int prec, const void* rhat, double* x,
+                        double omega, bool add, const int* skip);
+
+void launch_spmv(gs2_handle* h, const double* x, double* y, const int* skip);
+void launch_jr(gs2_handle* h, const double* b, const double* x_in,
+               double* x_out, double omega, const int* skip);
+void launch_level(gs2_handle* h, const DevCsr& T, const int* rows, int r0,
+                  int r1, const double* rhat, double* g, double* x,
+                  double omega, const int* skip);
+
+void launch_axpy(gs2_handle* h, double* y, double a, const double* x,
+                 const int* skip);
+void launch_copy(gs2_handle* h, double* dst, const double* src);
+
+// Krylov kernels (krylov.cu)
+void ensure_krylov(gs2_handle* h, int m);
+
+// Preconditioner application from a zero start: z = M^{-1} v.  If
+// rhat_ready, the sweep-precision D^{-1} v is already in place.
+void precond_apply(gs2_handle* h, const gs2_params* p, const double* v,
+                   double* z, bool rhat_ready, const int* skip);
+// The buffer that must hold D^{-1} v when rhat_ready is passed.
+void* precond_rhat_buffer(gs2_handle* h, const gs2_params* p);
+bool precond_wants_rhat(const gs2_params* p);
+
+// relaxations (relax.cu)
+void gs2_relax(gs2_handle* h, const double* b, double* x, const gs2_params* p);
+void gs_relax(gs2_handle* h, const double* b, double* x, int sweeps,
+              double omega, int direction);
+void jr_relax(gs2_handle* h, const double* b, double* x, int sweeps,
+              double omega);
+void ensure_levels(gs2_handle* h);
+void ensure_precision(gs2_handle* h, int prec);
+
+// solvers (krylov.cu)
+gs2_status gmres_run(gs2_handle* h, const double* b, double* x, int m,
+                     double tol, int max_iters, const gs2_params* p,
+                     gs2_solve_info* info);
+gs2_status cg_run(gs2_handle* h, const double* b, double* x, double tol,
+                  int max_iters, const gs2_params* p, gs2_solve_info* info);
+gs2_status gmres_batch(gs2_handle* const* hs, const double* const* bs,
+                       double* const* xs, int count, int m, double tol,
+                       int max_iters, const gs2_params* p, gs2_solve_info* infos);
+void read_state(gs2_handle* h);
+
+// geometry helpers
+int vec_blocks(gs2_handle* h, int64_t n);
+constexpr int kVecThreads = 256;
+constexpr int kRowThreads = 256;
+constexpr int kMaxRestart = 64;
+
+}  // namespace gs2

@@ -1,0 +1,764 @@
+// Krylov solvers on the device: restarted GMRES(m), right preconditioned,
+// CGS2 Arnoldi, Givens rotations; preconditioned CG.
+//
+// All scalars stay on the device (KrylovState); the host launches a whole
+// restart cycle and reads back one status word per cycle.  Every kernel of
+// a step checks the device `stop` flag and returns at once after the cycle
+// has ended, so the host may launch a full cycle without knowing when it
+// converges.  Reductions are two-level and fixed-order (per-block partials,
+// then one block per coefficient), so results are bitwise reproducible.
+#include <algorithm>
+#include <cmath>
+#include <thread>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace gs2 {
+
+// ---------------------------------------------------------------------------
+// reductions
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double warp_sum(double s) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+// Block-wide sums of NV per-thread values, written to part[v * nblk + blk].
+template <int NV>
+__device__ __forceinline__ void block_partials(const double (&acc)[NV], int nv, double* part,
+                                               int nblk) {
+  __shared__ double red[kVecThreads / 32][NV];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    if (v < nv) {
+      const double s = warp_sum(acc[v]);
+      if (lane == 0) red[wid][v] = s;
+    }
+  }
+  __syncthreads();
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kVecThreads / 32; ++w) s += red[w][v];
+    part[(size_t)v * nblk + blockIdx.x] = s;
+  }
+}
+
+// out[v] = sum over blocks of part[v * nblk + b], one block per v, fixed
+// order.  mode 0: H(v, j) = s; mode 1: H(v, j) += s; both also hbuf[v] = s.
+__global__ void k_reduce_cols(const double* __restrict__ part, int nblk, double* H, int ldh,
+                              int j, double* hbuf, int mode, const int* skip) {
+  if (skip && *skip) return;
+  const int v = blockIdx.x;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part[(size_t)v * nblk + b];
+  __shared__ double red[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  s = warp_sum(s);
+  if (lane == 0) red[wid] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    double* hv = H + (size_t)j * ldh + v;
+    if (mode == 0) *hv = t;
+    else *hv += t;
+    hbuf[v] = t;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// CGS2 passes over the basis V (row-major by vector, ld = n)
+// ---------------------------------------------------------------------------
+
+// pass 1: part = V[0..jc)^T w
+template <int MAXK>
+__global__ void __launch_bounds__(kVecThreads)
+k_dots(int n, const double* __restrict__ V, int jc, const double* __restrict__ w,
+       double* part, int nblk, const int* skip) {
+  if (skip && *skip) return;
+  double acc[MAXK];
+#pragma unroll
+  for (int k = 0; k < MAXK; ++k) acc[k] = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double wi = w[i];
+#pragma unroll
+    for (int k = 0; k < MAXK; ++k)
+      if (k < jc) acc[k] = fma(__ldg(V + (size_t)k * n + i), wi, acc[k]);
+  }
+  block_partials<MAXK>(acc, jc, part, nblk);
+}
+
+// pass 2: w -= V h ; part = V^T w          (NORM = false)
+// pass 3: w -= V h ; part[0] = w^T w       (NORM = true)
+template <int MAXK, bool NORM>
+__global__ void __launch_bounds__(kVecThreads)
+k_update(int n, const double* __restrict__ V, int jc, const double* __restrict__ hcoef,
+         double* w, double* part, int nblk, const int* skip) {
+  if (skip && *skip) return;
+  __shared__ double hs[MAXK];
+  for (int k = threadIdx.x; k < MAXK; k += blockDim.x) hs[k] = k < jc ? hcoef[k] : 0.0;
+  __syncthreads();
+  constexpr int NA = NORM ? 1 : MAXK;
+  double acc[NA];
+#pragma unroll
+  for (int k = 0; k < NA; ++k) acc[k] = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < MAXK; ++k)
+      if (k < jc) s = fma(__ldg(V + (size_t)k * n + i), hs[k], s);
+    const double wn = w[i] - s;
+    w[i] = wn;
+    if (NORM) {
+      acc[0] = fma(wn, wn, acc[0]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < NA; ++k)
+        if (k < jc) acc[k] = fma(__ldg(V + (size_t)k * n + i), wn, acc[k]);
+    }
+  }
+  block_partials<NA>(acc, NORM ? 1 : jc, part, nblk);
+}
+
+// Givens step j (one thread): H(j+1, j) = ||w||, earlier rotations applied
+// to column j, new rotation from (H(j,j), H(j+1,j)) with
+//   d = sqrt(f^2 + g^2), c = |f|/d, r = sign(f) d, s = g/r
+// (f = 0: c = 0, s = sign(g), r = |g|; g = 0: c = 1, s = 0, r = f),
+// residual estimate |g_{j+1}|, and the stop decision of the cycle.
+__global__ void k_givens(const double* __restrict__ part, int nblk, double* H, int ldh, int j,
+                         double* cs, double* sn, double* gv, KrylovState* st,
+                         volatile int* stop_host) {
+  if (st->stop) return;
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part[b];
+  s = warp_sum(s);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = s;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double nrm2 = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) nrm2 += red[w];
+  const double hn = sqrt(nrm2);
+  double* col = H + (size_t)j * ldh;
+  col[j + 1] = hn;
+  for (int i = 0; i < j; ++i) {
+    const double a = col[i], c = col[i + 1];
+    col[i] = cs[i] * a + sn[i] * c;
+    col[i + 1] = -sn[i] * a + cs[i] * c;
+  }
+  const double f = col[j], g = col[j + 1];
+  double c, sgv, r;
+  if (g == 0.0) {
+    c = 1.0; sgv = 0.0; r = f;
+  } else if (f == 0.0) {
+    c = 0.0; sgv = g > 0.0 ? 1.0 : -1.0; r = fabs(g);
+  } else {
+    const double d = sqrt(f * f + g * g);
+    c = fabs(f) / d;
+    r = f > 0.0 ? d : -d;
+    sgv = g / r;
+  }
+  cs[j] = c;
+  sn[j] = sgv;
+  col[j] = r;
+  col[j + 1] = 0.0;
+  gv[j + 1] = -sgv * gv[j];
+  gv[j] = c * gv[j];
+  st->iters += 1;
+  st->k = j + 1;
+  st->hn = hn;
+  st->inv_hn = 1.0 / hn;
+  const double est = fabs(gv[j + 1]);
+  int stop = 0;
+  if (isnan(est) || isnan(hn) || isinf(hn)) {
+    st->status = GS2_ERR_NAN;
+    stop = 1;
+  } else if (hn == 0.0) {
+    st->status = GS2_ERR_BREAKDOWN;
+    stop = 1;
+  } else if (est <= st->tol_abs || st->iters >= st->max_iters) {
+    stop = 1;
+  }
+  if (stop) {
+    st->stop = 1;
+    *stop_host = 1;
+  }
+}
+
+// v_{j+1} = w / H(j+1, j), and the preconditioner's D^{-1} v_{j+1}
+__global__ void k_scale_next(int n, const double* __restrict__ w, double* vnext,
+                             const double* __restrict__ dinv, double* rhat64, float* rhat32,
+                             const KrylovState* st) {
+  if (st->stop) return;
+  const double a = st->inv_hn;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double v = w[i] * a;
+    vnext[i] = v;
+    if (rhat64) rhat64[i] = dinv[i] * v;
+    if (rhat32) rhat32[i] = (float)(dinv[i] * v);
+  }
+}
+
+// y = R^{-1} g over the k steps of the cycle (back substitution, one thread)
+__global__ void k_backsolve(const double* __restrict__ H, int ldh, const double* gv, double* y,
+                            const KrylovState* st) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int k = st->k;
+  for (int i = k - 1; i >= 0; --i) {
+    double s = gv[i];
+    for (int l = i + 1; l < k; ++l) s -= H[(size_t)l * ldh + i] * y[l];
+    y[i] = s / H[(size_t)i * ldh + i];
+  }
+}
+
+// u = V[0..k) y and the preconditioner's D^{-1} u
+template <int MAXK>
+__global__ void __launch_bounds__(kVecThreads)
+k_combine(int n, const double* __restrict__ V, const double* __restrict__ y, double* u,
+          const double* __restrict__ dinv, double* rhat64, float* rhat32,
+          const KrylovState* st) {
+  __shared__ double ys[MAXK];
+  const int k = st->k;
+  for (int i = threadIdx.x; i < MAXK; i += blockDim.x) ys[i] = i < k ? y[i] : 0.0;
+  __syncthreads();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double s = 0.0;
+#pragma unroll
+    for (int l = 0; l < MAXK; ++l)
+      if (l < k) s = fma(__ldg(V + (size_t)l * n + i), ys[l], s);
+    u[i] = s;
+    if (rhat64) rhat64[i] = dinv[i] * s;
+    if (rhat32) rhat32[i] = (float)(dinv[i] * s);
+  }
+}
+
+// per-block partial sums of x^T x
+__global__ void __launch_bounds__(kVecThreads)
+k_norm_part(int n, const double* __restrict__ x, double* part, int nblk) {
+  double acc[1] = {0.0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    acc[0] = fma(x[i], x[i], acc[0]);
+  block_partials<1>(acc, 1, part, nblk);
+}
+
+// beta = sqrt(sum part) into st->beta (which = 0) or st->bnorm (which = 1)
+__global__ void k_norm_final(const double* __restrict__ part, int nblk, KrylovState* st,
+                             int which) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part[b];
+  s = warp_sum(s);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    if (which == 0) st->beta = sqrt(t);
+    else st->bnorm = sqrt(t);
+  }
+}
+
+// cycle start: v_0 = r / beta, D^{-1} v_0, g = (beta, 0, ...), state reset
+__global__ void k_cycle_start(int n, const double* __restrict__ r, double* v0,
+                              const double* __restrict__ dinv, double* rhat64, float* rhat32,
+                              double* gv, int m, KrylovState* st) {
+  const double beta = st->beta;
+  const double a = 1.0 / beta;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double v = r[i] * a;
+    v0[i] = v;
+    if (rhat64) rhat64[i] = dinv[i] * v;
+    if (rhat32) rhat32[i] = (float)(dinv[i] * v);
+  }
+  if (blockIdx.x == 0)
+    for (int i = threadIdx.x; i <= m; i += blockDim.x) gv[i] = i == 0 ? beta : 0.0;
+}
+
+__global__ void k_state_init(KrylovState* st, double tol, int max_iters) {
+  st->stop = 0;
+  st->status = GS2_OK;
+  st->k = 0;
+  st->iters = 0;
+  st->max_iters = max_iters;
+  st->tol_abs = tol * st->bnorm;
+}
+
+__global__ void k_cycle_reset(KrylovState* st) {
+  st->stop = 0;
+  st->k = 0;
+}
+
+// ---------------------------------------------------------------------------
+// workspace
+// ---------------------------------------------------------------------------
+
+void ensure_krylov(gs2_handle* h, int m) {
+  if (!h->st) {
+    h->st = (KrylovState*)h->dalloc(sizeof(KrylovState));
+    GS2_CUDA(cudaMemset(h->st, 0, sizeof(KrylovState)));
+    GS2_CUDA(cudaHostAlloc((void**)&h->st_host, sizeof(KrylovState), cudaHostAllocDefault));
+    int* f = nullptr;
+    GS2_CUDA(cudaHostAlloc((void**)&f, sizeof(int), cudaHostAllocMapped));
+    *f = 0;
+    h->stop_mapped = f;
+    GS2_CUDA(cudaHostGetDevicePointer((void**)&h->stop_mapped_dev, f, 0));
+    const size_t n = std::max<int64_t>(h->n, 1);
+    h->w = (double*)h->dalloc(sizeof(double) * n);
+    h->p = (double*)h->dalloc(sizeof(double) * n);
+    h->q = (double*)h->dalloc(sizeof(double) * n);
+  }
+  if (h->kry_m >= m) return;
+  const size_t n = std::max<int64_t>(h->n, 1);
+  // grow: new basis and Hessenberg storage (old ones stay owned until destroy)
+  h->V = (double*)h->dalloc(sizeof(double) * n * (m + 1));
+  h->H = (double*)h->dalloc(sizeof(double) * (size_t)(m + 1) * m);
+  h->hbuf = (double*)h->dalloc(sizeof(double) * (m + 1));
+  h->gvec = (double*)h->dalloc(sizeof(double) * (m + 1));
+  h->cs = (double*)h->dalloc(sizeof(double) * (m + 1));
+  h->sn = (double*)h->dalloc(sizeof(double) * (m + 1));
+  h->y = (double*)h->dalloc(sizeof(double) * (m + 1));
+  h->kry_m = m;
+}
+
+// ---------------------------------------------------------------------------
+// launch helpers
+// ---------------------------------------------------------------------------
+
+static int maxk_for(int jc) {
+  if (jc <= 8) return 8;
+  if (jc <= 16) return 16;
+  if (jc <= 32) return 32;
+  return 64;
+}
+
+static void launch_dots(gs2_handle* h, int jc, const double* w, const int* skip) {
+  KernelTimer tm(h, "cgs2_dots", 8.0 * h->n * (jc + 1));
+  const int n = (int)h->n, nb = h->nblk;
+  switch (maxk_for(jc)) {
+    case 8: k_dots<8><<<nb, kVecThreads, 0, h->stream>>>(n, h->V, jc, w, h->part, nb, skip); break;
+    case 16: k_dots<16><<<nb, kVecThreads, 0, h->stream>>>(n, h->V, jc, w, h->part, nb, skip); break;
+    case 32: k_dots<32><<<nb, kVecThreads, 0, h->stream>>>(n, h->V, jc, w, h->part, nb, skip); break;
+    default: k_dots<64><<<nb, kVecThreads, 0, h->stream>>>(n, h->V, jc, w, h->part, nb, skip); break;
+  }
+  GS2_LAUNCH_CHECK();
+}
+
+template <bool NORM>
+static void launch_update(gs2_handle* h, int jc, double* w, const int* skip) {
+  KernelTimer tm(h, NORM ? "cgs2_upd_norm" : "cgs2_upd_dots", 8.0 * h->n * (jc + 2));
+  const int n = (int)h->n, nb = h->nblk;
+  switch (maxk_for(jc)) {
+    case 8: k_update<8, NORM><<<nb, kVecThreads, 0, h->stream>>>(n, h->V, jc, h->hbuf, w, h->part, nb, skip); break;
+    case 16: k_update<16, NORM><<<nb, kVecThreads, 0, h->stream>>>(n, h->V, jc, h->hbuf, w, h->part, nb, skip); break;
+    case 32: k_update<32, NORM><<<nb, kVecThreads, 0, h->stream>>>(n, h->V, jc, h->hbuf, w, h->part, nb, skip); break;
+    default: k_update<64, NORM><<<nb, kVecThreads, 0, h->stream>>>(n, h->V, jc, h->hbuf, w, h->part, nb, skip); break;
+  }
+  GS2_LAUNCH_CHECK();
+}
+
+static void launch_combine(gs2_handle* h, int m, double* u, double* r64, float* r32) {
+  KernelTimer tm(h, "combine", 8.0 * h->n * (m + 1));
+  const int n = (int)h->n, nb = h->nblk;
+  switch (maxk_for(m)) {
+    case 8: k_combine<8><<<nb, kVecThreads, 0, h->stream>>>(n, h->V, h->y, u, h->dinv, r64, r32, h->st); break;
+    case 16: k_combine<16><<<nb, kVecThreads, 0, h->stream>>>(n, h->V, h->y, u, h->dinv, r64, r32, h->st); break;
+    case 32: k_combine<32><<<nb, kVecThreads, 0, h->stream>>>(n, h->V, h->y, u, h->dinv, r64, r32, h->st); break;
+    default: k_combine<64><<<nb, kVecThreads, 0, h->stream>>>(n, h->V, h->y, u, h->dinv, r64, r32, h->st); break;
+  }
+  GS2_LAUNCH_CHECK();
+}
+
+static void launch_norm(gs2_handle* h, const double* x, int which) {
+  KernelTimer tm(h, "norm", 8.0 * h->n);
+  k_norm_part<<<h->nblk, kVecThreads, 0, h->stream>>>((int)h->n, x, h->part, h->nblk);
+  GS2_LAUNCH_CHECK();
+  k_norm_final<<<1, 256, 0, h->stream>>>(h->part, h->nblk, h->st, which);
+  GS2_LAUNCH_CHECK();
+}
+
+void read_state(gs2_handle* h) {
+  GS2_CUDA(cudaMemcpyAsync(h->st_host, h->st, sizeof(KrylovState), cudaMemcpyDeviceToHost,
+                           h->stream));
+  GS2_CUDA(cudaStreamSynchronize(h->stream));
+}
+
+// ---------------------------------------------------------------------------
+// GMRES(m)
+// ---------------------------------------------------------------------------
+
+// One GMRES solve as a resumable state machine: `launch_*` only enqueue work
+// on the handle's stream and end with an asynchronous copy of the device
+// state; `advance` is called after that stream has been synchronised, reads
+// the state and either finishes or enqueues the next restart cycle.  Single
+// solves drive one machine; the batch call drives many, one stream each.
+struct GmresRun {
+  gs2_handle* h = nullptr;
+  const double* b = nullptr;
+  double* x = nullptr;
+  int m = 0;
+  double tol = 0.0;
+  int max_iters = 0;
+  const gs2_params* pc = nullptr;
+  bool wants = false;
+  double* r64 = nullptr;
+  float* r32 = nullptr;
+  double bnorm = 0.0;
+  bool first = true;
+  bool breakdown = false;
+  bool done = false;
+  gs2_status st = GS2_OK;
+  gs2_solve_info loc{0, 0, GS2_OK, 0.0};
+
+  void start(gs2_handle* h_, const double* b_, double* x_, int m_, double tol_, int maxit,
+             const gs2_params* p) {
+    h = h_; b = b_; x = x_; m = m_; tol = tol_; max_iters = maxit;
+    pc = (p && p->kind != GS2_PC_NONE) ? p : nullptr;
+    if (h->n == 0) {
+      done = true;
+      return;
+    }
+    ensure_krylov(h, m);
+    wants = precond_wants_rhat(pc);
+    if (wants) {
+      void* rb = precond_rhat_buffer(h, pc);
+      if (rb == (void*)h->rhat32) r32 = h->rhat32;
+      else r64 = (double*)rb;
+    }
+    launch_norm(h, b, 1);
+    k_state_init<<<1, 1, 0, h->stream>>>(h->st, tol, max_iters);
+    GS2_LAUNCH_CHECK();
+    launch_true_residual();
+  }
+
+  // r = b - A x, ||r|| -> st->beta, then the state copy to the host
+  void launch_true_residual() {
+    launch_resid(h, b, x, h->r, nullptr, nullptr, nullptr);
+    launch_norm(h, h->r, 0);
+    GS2_CUDA(cudaMemcpyAsync(h->st_host, h->st, sizeof(KrylovState), cudaMemcpyDeviceToHost,
+                             h->stream));
+  }
+
+  void finish(gs2_status s) {
+    st = s;
+    loc.status = s;
+    done = true;
+  }
+
+  // Called with the stream synchronised.
+  void advance() {
+    if (done) return;
+    const KrylovState& hs = *h->st_host;
+    if (first) {
+      first = false;
+      bnorm = hs.bnorm;
+      if (bnorm == 0.0) {
+        GS2_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * h->n, h->stream));
+        loc.true_relres = 0.0;
+        finish(GS2_OK);
+        return;
+      }
+      if (std::isnan(bnorm) || std::isinf(bnorm)) {
+        loc.true_relres = NAN;
+        finish(GS2_ERR_NAN);
+        return;
+      }
+    }
+    const double beta = hs.beta;
+    loc.true_relres = beta / bnorm;
+    loc.iters = hs.iters;
+    if (std::isnan(beta) || std::isinf(beta) || hs.status == GS2_ERR_NAN)
+      return finish(GS2_ERR_NAN);
+    if (loc.true_relres <= tol) return finish(GS2_OK);
+    if (hs.status == GS2_ERR_BREAKDOWN) breakdown = true;
+    if (breakdown) return finish(GS2_ERR_BREAKDOWN);
+    if (loc.iters >= max_iters) return finish(GS2_ERR_NOT_CONVERGED);
+    loc.cycles++;
+    launch_cycle();
+  }
+
+  void launch_cycle() {
+    const int n = (int)h->n;
+    const int nb = h->nblk;
+    const int ldh = m + 1;
+    const int* skip = &h->st->stop;
+    *h->stop_mapped = 0;
+    k_cycle_reset<<<1, 1, 0, h->stream>>>(h->st);
+    GS2_LAUNCH_CHECK();
+    k_cycle_start<<<vec_blocks(h, n), kVecThreads, 0, h->stream>>>(n, h->r, h->V, h->dinv, r64,
+                                                                  r32, h->gvec, m, h->st);
+    GS2_LAUNCH_CHECK();
+    for (int j = 0; j < m; ++j) {
+      if (*h->stop_mapped) break;  // the device has already ended the cycle
+      const double* vj = h->V + (size_t)j * n;
+      precond_apply(h, pc, vj, h->z, wants, skip);
+      launch_spmv(h, h->z, h->w, skip);
+      const int jc = j + 1;
+      launch_dots(h, jc, h->w, skip);
+      k_reduce_cols<<<jc, 256, 0, h->stream>>>(h->part, nb, h->H, ldh, j, h->hbuf, 0, skip);
+      GS2_LAUNCH_CHECK();
+      launch_update<false>(h, jc, h->w, skip);
+      k_reduce_cols<<<jc, 256, 0, h->stream>>>(h->part, nb, h->H, ldh, j, h->hbuf, 1, skip);
+      GS2_LAUNCH_CHECK();
+      launch_update<true>(h, jc, h->w, skip);
+      k_givens<<<1, 256, 0, h->stream>>>(h->part, nb, h->H, ldh, j, h->cs, h->sn, h->gvec, h->st,
+                                         h->stop_mapped_dev);
+      GS2_LAUNCH_CHECK();
+      if (j + 1 < m) {
+        k_scale_next<<<vec_blocks(h, n), kVecThreads, 0, h->stream>>>(
+            n, h->w, h->V + (size_t)(j + 1) * n, h->dinv, r64, r32, h->st);
+        GS2_LAUNCH_CHECK();
+      }
+    }
+    // x += M^{-1} V y
+    k_backsolve<<<1, 32, 0, h->stream>>>(h->H, ldh, h->gvec, h->y, h->st);
+    GS2_LAUNCH_CHECK();
+    launch_combine(h, m, h->w, r64, r32);
+    precond_apply(h, pc, h->w, h->z, wants, nullptr);
+    launch_axpy(h, x, 1.0, h->z, nullptr);
+    launch_true_residual();
+  }
+};
+
+gs2_status gmres_run(gs2_handle* h, const double* b, double* x, int m, double tol,
+                     int max_iters, const gs2_params* p, gs2_solve_info* info) {
+  GmresRun g;
+  g.start(h, b, x, m, tol, max_iters, p);
+  while (!g.done) {
+    GS2_CUDA(cudaStreamSynchronize(h->stream));
+    g.advance();
+  }
+  if (info) *info = g.loc;
+  return g.st;
+}
+
+gs2_status gmres_batch(gs2_handle* const* hs, const double* const* bs, double* const* xs,
+                       int count, int m, double tol, int max_iters, const gs2_params* p,
+                       gs2_solve_info* infos) {
+  std::vector<GmresRun> runs(count);
+  for (int i = 0; i < count; ++i) runs[i].start(hs[i], bs[i], xs[i], m, tol, max_iters, p);
+  for (;;) {
+    bool any = false;
+    for (int i = 0; i < count; ++i) {
+      if (runs[i].done) continue;
+      // poll first so that finished systems are served while others run
+      if (cudaStreamQuery(hs[i]->stream) == cudaErrorNotReady) {
+        any = true;
+        continue;
+      }
+      GS2_CUDA(cudaStreamSynchronize(hs[i]->stream));
+      runs[i].advance();
+      any = any || !runs[i].done;
+    }
+    if (!any) break;
+    std::this_thread::yield();
+  }
+  gs2_status first_bad = GS2_OK;
+  for (int i = 0; i < count; ++i) {
+    GS2_CUDA(cudaStreamSynchronize(hs[i]->stream));
+    if (infos) infos[i] = runs[i].loc;
+    if (runs[i].st != GS2_OK && first_bad == GS2_OK) first_bad = runs[i].st;
+  }
+  return first_bad;
+}
+
+// ---------------------------------------------------------------------------
+// preconditioned CG
+// ---------------------------------------------------------------------------
+
+// part = [p.q partials]
+__global__ void __launch_bounds__(kVecThreads)
+k_dot_part(int n, const double* __restrict__ a, const double* __restrict__ b, double* part,
+           int nblk, const int* skip) {
+  if (skip && *skip) return;
+  double acc[1] = {0.0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    acc[0] = fma(a[i], b[i], acc[0]);
+  block_partials<1>(acc, 1, part, nblk);
+}
+
+// reduce part into a scalar: what = 0 -> alpha = rz / (p.q) (breakdown if
+// p.q == 0); what = 1 -> beta_cg = rz_new / rz, rz = rz_new (stored in hn)
+__global__ void k_cg_scalar(const double* __restrict__ part, int nblk, KrylovState* st,
+                            int what, const int* skip) {
+  if (skip && *skip) return;
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part[b];
+  s = warp_sum(s);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = s;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double t = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+  if (what == 0) {
+    if (t == 0.0) {
+      st->status = GS2_ERR_BREAKDOWN;
+      st->stop = 1;
+      return;
+    }
+    st->alpha = st->rz / t;
+  } else if (what == 1) {
+    st->hn = t / st->rz;  // beta of CG
+    st->rz = t;
+  } else {
+    st->rz = t;
+  }
+}
+
+// x += alpha p ; r -= alpha q ; part = r.r
+__global__ void __launch_bounds__(kVecThreads)
+k_cg_xr(int n, double* x, double* r, const double* __restrict__ p, const double* __restrict__ q,
+        double* part, int nblk, const KrylovState* st, const int* skip) {
+  if (skip && *skip) return;
+  const double a = st->alpha;
+  double acc[1] = {0.0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    x[i] = fma(a, p[i], x[i]);
+    const double ri = fma(-a, q[i], r[i]);
+    r[i] = ri;
+    acc[0] = fma(ri, ri, acc[0]);
+  }
+  block_partials<1>(acc, 1, part, nblk);
+}
+
+// ||r|| test after an iteration: stop the loop of launches when converged
+__global__ void k_cg_check(const double* __restrict__ part, int nblk, KrylovState* st,
+                           volatile int* stop_host, const int* skip) {
+  if (skip && *skip) return;
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part[b];
+  s = warp_sum(s);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = s;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double t = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+  const double rn = sqrt(t);
+  st->iters += 1;
+  st->beta = rn;
+  if (isnan(rn) || isinf(rn)) {
+    st->status = GS2_ERR_NAN;
+    st->stop = 1;
+  } else if (rn <= st->tol_abs || st->iters >= st->max_iters) {
+    st->stop = 1;
+  }
+  if (st->stop) *stop_host = 1;
+}
+
+// p = z + beta p
+__global__ void k_cg_p(int n, double* p, const double* __restrict__ z, const KrylovState* st,
+                       const int* skip) {
+  if (skip && *skip) return;
+  const double bt = st->hn;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    p[i] = fma(bt, p[i], z[i]);
+}
+
+gs2_status cg_run(gs2_handle* h, const double* b, double* x, double tol, int max_iters,
+                  const gs2_params* p, gs2_solve_info* info) {
+  gs2_solve_info loc{0, 0, GS2_OK, 0.0};
+  if (h->n == 0) {
+    if (info) *info = loc;
+    return GS2_OK;
+  }
+  ensure_krylov(h, 1);
+  const gs2_params* pc = (p && p->kind != GS2_PC_NONE) ? p : nullptr;
+  const int n = (int)h->n, nb = h->nblk;
+  const int* skip = &h->st->stop;
+  double* r = h->r;
+  double* z = h->z;
+  double* pv = h->p;
+  double* q = h->q;
+
+  launch_norm(h, b, 1);
+  k_state_init<<<1, 1, 0, h->stream>>>(h->st, tol, max_iters);
+  GS2_LAUNCH_CHECK();
+  read_state(h);
+  const double bnorm = h->st_host->bnorm;
+  if (bnorm == 0.0) {
+    GS2_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, h->stream));
+    if (info) *info = loc;
+    return GS2_OK;
+  }
+  gs2_status st = GS2_OK;
+  launch_resid(h, b, x, r, nullptr, nullptr, nullptr);
+  constexpr int kCheckEvery = 16;
+  for (;;) {
+    // (re)start the search direction from the current residual
+    launch_norm(h, r, 0);
+    read_state(h);
+    double rn = h->st_host->beta;
+    loc.iters = h->st_host->iters;
+    if (std::isnan(rn) || std::isinf(rn)) {
+      st = GS2_ERR_NAN;
+      break;
+    }
+    if (rn <= tol * bnorm) {
+      // confirm on the true residual
+      launch_resid(h, b, x, h->t, nullptr, nullptr, nullptr);
+      launch_norm(h, h->t, 0);
+      read_state(h);
+      if (h->st_host->beta <= tol * bnorm) break;
+      launch_copy(h, r, h->t);
+      rn = h->st_host->beta;
+    }
+    if (loc.iters >= max_iters) {
+      st = GS2_ERR_NOT_CONVERGED;
+      break;
+    }
+    loc.cycles++;
+    *h->stop_mapped = 0;
+    k_cycle_reset<<<1, 1, 0, h->stream>>>(h->st);
+    precond_apply(h, pc, r, z, false, nullptr);
+    launch_copy(h, pv, z);
+    k_dot_part<<<nb, kVecThreads, 0, h->stream>>>(n, r, z, h->part, nb, nullptr);
+    k_cg_scalar<<<1, 256, 0, h->stream>>>(h->part, nb, h->st, 2, nullptr);
+    GS2_LAUNCH_CHECK();
+    for (;;) {
+      for (int it = 0; it < kCheckEvery; ++it) {
+        if (*h->stop_mapped) break;
+        launch_spmv(h, pv, q, skip);
+        k_dot_part<<<nb, kVecThreads, 0, h->stream>>>(n, pv, q, h->part, nb, skip);
+        k_cg_scalar<<<1, 256, 0, h->stream>>>(h->part, nb, h->st, 0, skip);
+        k_cg_xr<<<nb, kVecThreads, 0, h->stream>>>(n, x, r, pv, q, h->part, nb, h->st, skip);
+        k_cg_check<<<1, 256, 0, h->stream>>>(h->part, nb, h->st, h->stop_mapped_dev, skip);
+        precond_apply(h, pc, r, z, false, skip);
+        k_dot_part<<<nb, kVecThreads, 0, h->stream>>>(n, r, z, h->part, nb, skip);
+        k_cg_scalar<<<1, 256, 0, h->stream>>>(h->part, nb, h->st, 1, skip);
+        k_cg_p<<<vec_blocks(h, n), kVecThreads, 0, h->stream>>>(n, pv, z, h->st, skip);
+        GS2_LAUNCH_CHECK();
+      }
+      read_state(h);
+      if (h->st_host->stop) break;
+    }
+    if (h->st_host->status == GS2_ERR_NAN) {
+      st = GS2_ERR_NAN;
+      loc.iters = h->st_host->iters;
+      break;
+    }
+    if (h->st_host->status == GS2_ERR_BREAKDOWN) {
+      st = GS2_ERR_BREAKDOWN;
+      loc.iters = h->st_host->iters;
+      break;
+    }
+  }
+  launch_resid(h, b, x, h->t, nullptr, nullptr, nullptr);
+  launch_norm(h, h->t, 0);
+  read_state(h);
+  loc.true_relres = h->st_host->beta / bnorm;
+  loc.status = st;
+  if (info) *info = loc;
+  return st;
+}
+
+}  // namespace gs2

@@ -1,0 +1,251 @@
+// Relaxation drivers: GS2 (non-compact Eq. 4 and compact Eq. 11), exact
+// GS/SOR by level-scheduled triangular solves, damped JR, and the
+// zero-start preconditioner application used by the Krylov solvers.
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace gs2 {
+
+// ---------------------------------------------------------------------------
+// compact right-hand side: rhat = D^{-1} (b - T_other x)  (Eq. 11 with
+// N = -U for a forward sweep and N = -L for a backward one)
+// ---------------------------------------------------------------------------
+
+__global__ void k_compact_rhs(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                              const double* __restrict__ va, const double* __restrict__ b,
+                              const double* __restrict__ x, const double* __restrict__ dinv,
+                              double* rhat64, float* rhat32, const int* skip) {
+  if (skip && *skip) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int k = rp[i]; k < rp[i + 1]; ++k) s = fma(va[k], __ldg(x + ci[k]), s);
+    // the triangle is prescaled: sum = (D^{-1} T x)_i
+    const double rh = dinv[i] * b[i] - s;
+    if (rhat64) rhat64[i] = rh;
+    if (rhat32) rhat32[i] = (float)rh;
+  }
+}
+
+__global__ void k_fill(int n, double* y, double v, const int* skip) {
+  if (skip && *skip) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    y[i] = v;
+}
+
+__global__ void k_copy(int n, double* y, const double* __restrict__ x, const int* skip) {
+  if (skip && *skip) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    y[i] = x[i];
+}
+
+static void launch_compact_rhs(gs2_handle* h, const DevCsr& Tother, const double* b,
+                               const double* x, double* rhat64, float* rhat32,
+                               const int* skip) {
+  KernelTimer tm(h, "compact_rhs",
+                 Tother.nnz * 12.0 + 4.0 * (h->n + 1) + 24.0 * h->n + (rhat64 ? 8.0 : 4.0) * h->n);
+  k_compact_rhs<<<vec_blocks(h, h->n), kVecThreads, 0, h->stream>>>(
+      (int)h->n, Tother.rp, Tother.ci, Tother.va, b, x, h->dinv, rhat64, rhat32, skip);
+  GS2_LAUNCH_CHECK();
+}
+
+static void launch_fill(gs2_handle* h, double* y, double v, const int* skip) {
+  k_fill<<<vec_blocks(h, h->n), kVecThreads, 0, h->stream>>>((int)h->n, y, v, skip);
+  GS2_LAUNCH_CHECK();
+}
+
+static void launch_copy_skip(gs2_handle* h, double* y, const double* x, const int* skip) {
+  KernelTimer tm(h, "copy", 16.0 * h->n);
+  k_copy<<<vec_blocks(h, h->n), kVecThreads, 0, h->stream>>>((int)h->n, y, x, skip);
+  GS2_LAUNCH_CHECK();
+}
+
+// ---------------------------------------------------------------------------
+// GS2 pieces
+// ---------------------------------------------------------------------------
+
+static void* rhat_buf(gs2_handle* h, int prec) {
+  return prec == GS2_FP64 ? (void*)h->rhat : (void*)h->rhat32;
+}
+
+// n_j inner JR sweeps (Eq. 6-7, damped), the last one fused with the update
+// of x in `last_mode` (x += omega g or x = omega g).
+static void inner_sweeps(gs2_handle* h, const DevCsr& T, int prec, const void* rhat,
+                         double* x, double omega, double gamma, int inner, int last_mode,
+                         const int* skip) {
+  void* bufA = prec == GS2_FP64 ? (void*)h->g0 : (void*)h->g32a;
+  void* bufB = prec == GS2_FP64 ? (void*)h->g1 : (void*)h->g32b;
+  const void* gin = rhat;  // g_0 = D^{-1} r  (Eq. 5)
+  for (int j = 0; j < inner; ++j) {
+    const bool last = j == inner - 1;
+    void* gout = last ? nullptr : (j % 2 == 0 ? bufA : bufB);
+    launch_inner(h, T, prec, rhat, gin, gout, x, omega, gamma, last ? last_mode : INNER_MID,
+                 skip);
+    gin = gout;
+  }
+}
+
+static void resid_into(gs2_handle* h, int prec, const double* b, const double* x,
+                       const int* skip) {
+  if (prec == GS2_FP64)
+    launch_resid(h, b, x, nullptr, h->rhat, nullptr, skip);
+  else
+    launch_resid(h, b, x, nullptr, nullptr, h->rhat32, skip);
+}
+
+static void compact_rhs_into(gs2_handle* h, int prec, const DevCsr& Tother, const double* b,
+                             const double* x, const int* skip) {
+  if (prec == GS2_FP64)
+    launch_compact_rhs(h, Tother, b, x, h->rhat, nullptr, skip);
+  else
+    launch_compact_rhs(h, Tother, b, x, nullptr, h->rhat32, skip);
+}
+
+// One half sweep of GS2 on triangle T.  x_zero: x is known to be 0 and the
+// sweep-precision D^{-1} b is already in the rhat buffer.
+static void gs2_half(gs2_handle* h, const gs2_params* p, const DevCsr& T, const DevCsr& Tother,
+                     const double* b, double* x, bool x_zero, const int* skip) {
+  const int prec = p->precision;
+  void* rh = rhat_buf(h, prec);
+  if (p->form == GS2_COMPACT) {
+    // x <- Mhat^{-1} (b + N x): every half sweep overwrites x
+    if (!x_zero) compact_rhs_into(h, prec, Tother, b, x, skip);
+    if (p->inner == 0)
+      launch_rhat_update(h, prec, rh, x, 1.0, false, skip);
+    else
+      inner_sweeps(h, T, prec, rh, x, 1.0, 1.0, p->inner, INNER_LAST_SET, skip);
+    return;
+  }
+  // non-compact: x += omega Mhat^{-1} (b - A x)
+  if (!x_zero) resid_into(h, prec, b, x, skip);
+  const int mode = x_zero ? INNER_LAST_SET : INNER_LAST_ADD;
+  if (p->inner == 0)
+    launch_rhat_update(h, prec, rh, x, p->omega, !x_zero, skip);
+  else
+    inner_sweeps(h, T, prec, rh, x, p->omega, p->gamma, p->inner, mode, skip);
+}
+
+void gs2_relax(gs2_handle* h, const double* b, double* x, const gs2_params* p) {
+  for (int s = 0; s < p->outer; ++s) {
+    if (p->direction == GS2_FORWARD || p->direction == GS2_SYMMETRIC)
+      gs2_half(h, p, h->L, h->U, b, x, false, nullptr);
+    if (p->direction == GS2_BACKWARD || p->direction == GS2_SYMMETRIC)
+      gs2_half(h, p, h->U, h->L, b, x, false, nullptr);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// exact GS / SOR baseline: x += omega (D + omega T)^{-1} (b - A x), the
+// triangular solve by level sets (one launch per level)
+// ---------------------------------------------------------------------------
+
+static void gs_half(gs2_handle* h, bool lower, const double* b, double* x, double omega,
+                    bool x_zero, const int* skip) {
+  const DevCsr& T = lower ? h->L : h->U;
+  const std::vector<int>& ptr = lower ? h->lev_ptr_L : h->lev_ptr_U;
+  const int* rows = lower ? h->lev_rows_L : h->lev_rows_U;
+  if (x_zero) {
+    launch_fill(h, x, 0.0, skip);
+  } else {
+    launch_resid(h, b, x, nullptr, h->rhat, nullptr, skip);
+  }
+  KernelTimer tm(h, "levels", T.nnz * 12.0 + 4.0 * (h->n + 1) + 32.0 * h->n);
+  for (size_t l = 0; l + 1 < ptr.size(); ++l)
+    launch_level(h, T, rows, ptr[l], ptr[l + 1], h->rhat, h->g0, x, omega, skip);
+}
+
+void gs_relax(gs2_handle* h, const double* b, double* x, int sweeps, double omega,
+              int direction) {
+  for (int s = 0; s < sweeps; ++s) {
+    if (direction == GS2_FORWARD || direction == GS2_SYMMETRIC)
+      gs_half(h, true, b, x, omega, false, nullptr);
+    if (direction == GS2_BACKWARD || direction == GS2_SYMMETRIC)
+      gs_half(h, false, b, x, omega, false, nullptr);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// damped JR baseline, ping-pong between x and a resident temporary
+// ---------------------------------------------------------------------------
+
+void jr_relax(gs2_handle* h, const double* b, double* x, int sweeps, double omega) {
+  const double* xin = x;
+  double* xout = h->t;
+  for (int s = 0; s < sweeps; ++s) {
+    launch_jr(h, b, xin, xout, omega, nullptr);
+    xin = xout;
+    xout = (xout == h->t) ? x : h->t;
+  }
+  if (xin != x) launch_copy(h, x, xin);
+}
+
+// ---------------------------------------------------------------------------
+// preconditioner from a zero start: z = M^{-1} v
+// ---------------------------------------------------------------------------
+
+bool precond_wants_rhat(const gs2_params* p) {
+  return p && (p->kind == GS2_PC_GS2 || p->kind == GS2_PC_JR || p->kind == GS2_PC_GS);
+}
+
+void* precond_rhat_buffer(gs2_handle* h, const gs2_params* p) {
+  if (!precond_wants_rhat(p)) return nullptr;
+  if (p->kind == GS2_PC_GS2) return rhat_buf(h, p->precision);
+  return h->rhat;
+}
+
+void precond_apply(gs2_handle* h, const gs2_params* p, const double* v, double* z,
+                   bool rhat_ready, const int* skip) {
+  if (!p || p->kind == GS2_PC_NONE) {
+    launch_copy_skip(h, z, v, skip);
+    return;
+  }
+  if (p->kind == GS2_PC_GS2) {
+    const int prec = p->precision;
+    if (!rhat_ready) {
+      if (prec == GS2_FP64)
+        launch_prep_rhat(h, v, h->rhat, nullptr, skip);
+      else
+        launch_prep_rhat(h, v, nullptr, h->rhat32, skip);
+    }
+    bool zero = true;
+    for (int s = 0; s < p->outer; ++s) {
+      if (p->direction == GS2_FORWARD || p->direction == GS2_SYMMETRIC) {
+        gs2_half(h, p, h->L, h->U, v, z, zero, skip);
+        zero = false;
+      }
+      if (p->direction == GS2_BACKWARD || p->direction == GS2_SYMMETRIC) {
+        gs2_half(h, p, h->U, h->L, v, z, zero, skip);
+        zero = false;
+      }
+    }
+    return;
+  }
+  if (p->kind == GS2_PC_JR) {
+    if (!rhat_ready) launch_prep_rhat(h, v, h->rhat, nullptr, skip);
+    launch_rhat_update(h, GS2_FP64, h->rhat, z, p->omega, false, skip);
+    const double* xin = z;
+    double* xout = h->t;
+    for (int s = 1; s < p->outer; ++s) {
+      launch_jr(h, v, xin, xout, p->omega, skip);
+      xin = xout;
+      xout = (xout == h->t) ? z : h->t;
+    }
+    if (xin != z) launch_copy_skip(h, z, xin, skip);
+    return;
+  }
+  // exact GS: the first half sweep from z = 0 solves with r = v
+  if (!rhat_ready) launch_prep_rhat(h, v, h->rhat, nullptr, skip);
+  bool zero = true;
+  for (int s = 0; s < p->outer; ++s) {
+    if (p->direction == GS2_FORWARD || p->direction == GS2_SYMMETRIC) {
+      gs_half(h, true, v, z, p->omega, zero, skip);
+      zero = false;
+    }
+    if (p->direction == GS2_BACKWARD || p->direction == GS2_SYMMETRIC) {
+      gs_half(h, false, v, z, p->omega, zero, skip);
+      zero = false;
+    }
+  }
+}
+
+}  // namespace gs2
