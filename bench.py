@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the baseline/precision comparison solves")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer e2e timing")
     ap.add_argument("--no-profile", action="store_true",
                     help="do not time kernels with events inside the timed region")
     return ap.parse_args()
@@ -190,6 +191,67 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12  # 2 FMA/clk/SM x 2 flop x 152 SMs x 2.07 GHz
+
+
+def kernel_flops(name, st, n):
+    """FP64 flops of a kernel's timed launches, from its algorithmic bytes
+    (the CGS2 passes read 8n bytes per basis vector)."""
+    L, B = st["launches"], st["bytes"]
+    if name == "cgs2_dots":        # bytes 8n(jc+1), 2 jc n flops
+        return 2.0 * n * (B / (8.0 * n) - L)
+    if name == "cgs2_upd_dots":    # bytes 8n(jc+2), 4 jc n flops
+        return 4.0 * n * (B / (8.0 * n) - 2 * L)
+    if name == "cgs2_upd_norm":    # bytes 8n(jc+2), 2 (jc+1) n flops
+        return 2.0 * n * (B / (8.0 * n) - L)
+    return None
+
+
+def kernel_table(stats, n, hbm):
+    out = {}
+    for name, s in stats.items():
+        if not s["launches"] or s["total_ms"] <= 0:
+            continue
+        gbs = s["bytes"] / (s["total_ms"] / 1000.0) / 1e9
+        row = {"launches": s["launches"], "ms": round(s["total_ms"], 3), "share": None,
+               "gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 3)}
+        fl = kernel_flops(name, s, n)
+        if fl is not None:
+            tf = fl / (s["total_ms"] / 1000.0) / 1e12
+            row["fp64_tflops"] = round(tf, 3)
+            row["fp64_frac"] = round(tf / FP64_PEAK_TFLOPS, 3)
+        out[name] = row
+    tot = sum(v["ms"] for v in out.values())
+    for v in out.values():
+        v["share"] = round(v["ms"] / tot, 3) if tot else None
+    return out
+
+
+def roofline(name, s, n, hbm, peak_kind, grid):
+    per_launch_bytes = s["bytes"] / s["launches"]
+    per_launch_ms = s["total_ms"] / s["launches"]
+    gbs = per_launch_bytes / (per_launch_ms / 1000.0) / 1e9
+    fl = kernel_flops(name, s, n)
+    traffic = stored_traffic(name, grid)
+    if fl is not None:
+        tf = fl / s["launches"] / (per_launch_ms / 1000.0) / 1e12
+        return {"bound": "alu", "kernel": name, "achieved": round(tf, 4),
+                "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
+                "frac": round(tf / FP64_PEAK_TFLOPS, 3), "traffic": traffic,
+                "algorithmic_flops_per_launch": fl / s["launches"],
+                "algorithmic_bytes_per_launch": per_launch_bytes,
+                "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 3),
+                "peak_source": "FP64 FMA rate: 2 FMA/clk/SM x 152 SMs x 2.07 GHz "
+                               "(nominal 1.25 TFLOP/s); HBM from MEASURED_PEAKS.json "
+                               f"({peak_kind})",
+                "launches_timed": s["launches"]}
+    return {"bound": "hbm", "kernel": name, "achieved": round(gbs, 1), "peak": hbm,
+            "unit": "GB/s", "frac": round(gbs / hbm, 3), "traffic": traffic,
+            "algorithmic_bytes_per_launch": per_launch_bytes,
+            "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
+            "launches_timed": s["launches"]}
+
+
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
@@ -229,20 +291,36 @@ def run_ours(args):
         x.zero_()
         return gs2.gmres_solve(h, b, x, 30, 1e-8, 5000, pc)
 
+    # warm-up; the last warm-up solve is timed kernel by kernel (event pair
+    # around every launch) for the table of shares
     with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
+        for w in range(args.warmup):
+            if w == args.warmup - 1 and not args.no_profile:
+                h.profile_filter(None)
+                h.profile(True)
+                h.profile_reset()
             info = solve()
     stream.synchronize()
     if info.status != 0:
         raise RuntimeError(f"warm-up solve failed: {info}")
+    hbm, peak_kind = peaks()
+    kernels = {}
+    top = None
+    if not args.no_profile:
+        warm = h.profile_read()
+        h.profile(False)
+        kernels = kernel_table(warm, n, hbm)
+        top = max(kernels, key=lambda k: kernels[k]["ms"]) if kernels else None
 
     sampler = ClockSampler(local) if rank == 0 else None
     if sampler:
         sampler.start()
         time.sleep(0.3)
-    if not args.no_profile:
-        h.profile(True)
+    if top:
+        # inside the timed region only the dominant kernel is bracketed
+        h.profile_filter(top)
         h.profile_reset()
+        h.profile(True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     iters = []
@@ -268,8 +346,9 @@ def run_ours(args):
     launches = gs2.launch_count() - launches0
     total_ms = t_start.elapsed_time(t_end)
     step_ms = [a.elapsed_time(bb) for a, bb in ev]
-    kstats = h.profile_read() if not args.no_profile else {}
+    timed = h.profile_read() if top else {}
     h.profile(False)
+    h.profile_filter(None)
     clocks = sampler.stop() if sampler else None
     if dist:
         t = torch.tensor([total_ms], device="cuda")
@@ -278,33 +357,10 @@ def run_ours(args):
     ms_per_step = total_ms / args.steps
     value = world * args.steps / (total_ms / 1000.0)
 
-    hbm, peak_kind = peaks()
     roof = None
-    kernels = {}
-    if kstats:
-        for name, s in kstats.items():
-            if s["launches"]:
-                gbs = s["bytes"] / (s["total_ms"] / 1000.0) / 1e9 if s["total_ms"] > 0 else 0.0
-                kernels[name] = {"launches": s["launches"], "ms": round(s["total_ms"], 3),
-                                 "share": None, "gbs": round(gbs, 1),
-                                 "frac": round(gbs / hbm, 3)}
-        ksum = sum(v["ms"] for v in kernels.values())
-        for v in kernels.values():
-            v["share"] = round(v["ms"] / ksum, 3) if ksum else None
-        top = max(kernels, key=lambda k: kernels[k]["ms"])
-        s = kstats[top]
-        per_launch_bytes = s["bytes"] / s["launches"]
-        per_launch_ms = s["total_ms"] / s["launches"]
-        achieved = per_launch_bytes / (per_launch_ms / 1000.0) / 1e9
-        traffic = stored_traffic(top, args.grid)
-        roof = {"bound": "hbm", "kernel": top, "achieved": round(achieved, 1), "peak": hbm,
-                "unit": "GB/s", "frac": round(achieved / hbm, 3),
-                "traffic": traffic, "algorithmic_bytes_per_launch": per_launch_bytes,
-                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"}
-        # the GS2 sweep kernels named by the metric
-        sweep = {k: kernels[k] for k in ("resid", "inner64") if k in kernels}
-    else:
-        sweep = {}
+    if top and top in timed and timed[top]["launches"]:
+        roof = roofline(top, timed[top], n, hbm, peak_kind, args.grid)
+    sweep = {k: kernels[k] for k in ("resid", "inner64") if k in kernels}
 
     out = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
@@ -328,22 +384,29 @@ def run_ours(args):
     }
 
     # ---- e2e: the public C-ABI call with host (pinned) buffers ------------
-    bh = torch.from_numpy(pr.b.copy()).pin_memory().numpy()
-    xh = torch.zeros(n, dtype=torch.float64).pin_memory().numpy()
-    for _ in range(1):
+    # the library copies b and x0 to the device, solves and copies x back
+    # inside every timed call
+    out["e2e"] = None
+    if not args.no_e2e:
+        bh = torch.from_numpy(pr.b.copy()).pin_memory().numpy()
+        xh = torch.zeros(n, dtype=torch.float64).pin_memory().numpy()
         xh[:] = 0.0
         gs2.gmres_solve(h, bh, xh, 30, 1e-8, 5000, pc)
-    e2e_t = []
-    for _ in range(max(1, min(args.steps, 3))):
-        xh[:] = 0.0
-        t0 = time.perf_counter()
-        inf = gs2.gmres_solve(h, bh, xh, 30, 1e-8, 5000, pc)
-        e2e_t.append(time.perf_counter() - t0)
-        assert inf.status == 0
-    out["e2e"] = {"value": world / float(np.mean(e2e_t)), "unit": "solves/s",
-                  "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 8 * n,
-                  "note": "gmres_solve with pinned host b and x: H2D of b and x0, "
-                          "solve, D2H of x inside each timed call"}
+        e2e_t = []
+        for _ in range(max(1, min(args.steps, 3))):
+            xh[:] = 0.0
+            t0 = time.perf_counter()
+            inf = gs2.gmres_solve(h, bh, xh, 30, 1e-8, 5000, pc)
+            e2e_t.append(time.perf_counter() - t0)
+            assert inf.status == 0
+        if dist:
+            t = torch.tensor([float(np.mean(e2e_t))], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_t = [float(t.item())]
+        out["e2e"] = {"value": world / float(np.mean(e2e_t)), "unit": "solves/s",
+                      "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 8 * n,
+                      "note": "gmres_solve with pinned host b and x: H2D of b and x0, "
+                              "solve, D2H of x inside each timed call"}
 
     if rank == 0 and not args.no_extras and world == 1:
         out["comparisons"] = comparisons(gs2, torch, pr, stream, b)

@@ -194,6 +194,13 @@ gs2_status gs2_batch_solve(gs2_handle* const* hs, const double* const* bs,
                            double tol, int max_iters, const gs2_params* precond,
                            gs2_solve_info* infos);
 
+/* Synchronise the handle's stream and report a sticky device-side error:
+ * TIMEOUT if a kernel's bounded wait on its own shared-memory copies gave
+ * up (the kernel then returned without touching its outputs further).  The
+ * word is cleared by this call.  gmres_solve and cg_solve check it once per
+ * restart cycle and return the status themselves. */
+gs2_status gs2_check(gs2_handle* h);
+
 /* ---- per-kernel device timing (CUDA events on the handle's stream) ---- */
 
 typedef struct {
@@ -206,6 +213,9 @@ typedef struct {
 /* enable = 1 records an event pair around every launch of the library's
  * kernels on this handle until disabled; 0 stops and keeps the totals. */
 gs2_status gs2_profile_enable(gs2_handle* h, int enable);
+/* Time only the kernels named `name` (as reported by gs2_profile_read);
+ * NULL or "" times every kernel.  Fewer event pairs perturb a run less. */
+gs2_status gs2_profile_filter(gs2_handle* h, const char* name);
 /* Resolves pending events (synchronising the stream) and copies up to
  * `cap` per-kernel totals into out; *count receives the number written. */
 gs2_status gs2_profile_read(gs2_handle* h, gs2_kernel_stat* out, int cap,

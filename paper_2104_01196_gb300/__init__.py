@@ -109,6 +109,8 @@ def load(path: str | None = None):
         "cg_solve": [P, P, P, D, I, ctypes.POINTER(Params), ctypes.POINTER(_Info)],
         "gs2_batch_solve": [P, P, P, I, I, D, I, ctypes.POINTER(Params), ctypes.POINTER(_Info)],
         "gs2_profile_enable": [P, I],
+        "gs2_profile_filter": [P, ctypes.c_char_p],
+        "gs2_check": [P],
         "gs2_profile_read": [P, ctypes.POINTER(_KStat), I, ctypes.POINTER(I)],
         "gs2_profile_reset": [P],
     }
@@ -193,6 +195,14 @@ class Handle:
 
     def profile(self, enable: bool):
         _check(load().gs2_profile_enable(self.ptr, 1 if enable else 0))
+
+    def check(self):
+        """Synchronise and raise if a kernel reported a device-side error."""
+        _check(load().gs2_check(self.ptr))
+
+    def profile_filter(self, name: str | None):
+        """Time only kernels called `name` (None: all)."""
+        _check(load().gs2_profile_filter(self.ptr, name.encode() if name else None))
 
     def profile_read(self) -> dict:
         arr = (_KStat * 64)()

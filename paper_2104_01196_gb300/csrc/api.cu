@@ -30,6 +30,7 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 struct Profiler {
   bool enabled = false;
+  std::string only;  // non-empty: time only kernels of this name
   std::vector<std::string> names;
   std::unordered_map<std::string, int> ids;
   std::vector<gs2_kernel_stat> stats;
@@ -87,7 +88,7 @@ struct Profiler {
 
 KernelTimer::KernelTimer(gs2_handle* h_, const char* name, double bytes_)
     : h(h_), id(-1), bytes(bytes_) {
-  if (h->prof && h->prof->enabled) {
+  if (h->prof && h->prof->enabled && (h->prof->only.empty() || h->prof->only == name)) {
     id = h->prof->id_of(name);
     e0 = h->prof->get();
     cudaEventRecord(e0, h->stream);
@@ -152,10 +153,13 @@ static void upload_csr(gs2_handle* h, DevCsr& M, int n, const std::vector<int>& 
   M.nnz = (int)ci.size();
   M.mean_row = n ? (double)M.nnz / n : 0.0;
   M.tpr = choose_lanes(M.mean_row);
+  // every array is padded by kPad entries so that the 16-byte-rounded bulk
+  // copies of a tile's slices never leave the allocation
   const size_t nz = (size_t)M.nnz + kPad;
-  M.rp = (int*)h->dalloc(sizeof(int) * (n + 1));
+  M.rp = (int*)h->dalloc(sizeof(int) * (n + 1 + kPad));
   M.ci = (int*)h->dalloc(sizeof(int) * nz);
   M.va = (double*)h->dalloc(sizeof(double) * nz);
+  GS2_CUDA(cudaMemset(M.rp, 0, sizeof(int) * (n + 1 + kPad)));
   GS2_CUDA(cudaMemcpy(M.rp, rp.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
   GS2_CUDA(cudaMemset(M.ci, 0, sizeof(int) * nz));
   GS2_CUDA(cudaMemset(M.va, 0, sizeof(double) * nz));
@@ -166,9 +170,15 @@ static void upload_csr(gs2_handle* h, DevCsr& M, int n, const std::vector<int>& 
   std::vector<int> tiles;
   build_tiles(rp, n, M.tpr, tiles, M.cap);
   M.ntiles = (int)tiles.size() - 1;
-  M.tile_row = (int*)h->dalloc(sizeof(int) * tiles.size());
-  GS2_CUDA(cudaMemcpy(M.tile_row, tiles.data(), sizeof(int) * tiles.size(),
-                      cudaMemcpyHostToDevice));
+  std::vector<int4> desc(std::max(M.ntiles, 1));
+  for (int t = 0; t < M.ntiles; ++t) {
+    const int r0 = tiles[t], r1 = tiles[t + 1];
+    const int a = rp[r0], b = rp[r1];
+    const bool longrow = (r1 - r0 == 1) && (b - a > kHardCap);
+    desc[t] = make_int4(r0, r1, longrow ? -1 - a : (a & ~7), b);
+  }
+  M.desc = (int4*)h->dalloc(sizeof(int4) * desc.size());
+  GS2_CUDA(cudaMemcpy(M.desc, desc.data(), sizeof(int4) * desc.size(), cudaMemcpyHostToDevice));
 }
 
 // FP32 copy and FP16 copy with per-row scale s_i = max_j |v_ij| of a
@@ -375,6 +385,7 @@ static void destroy_impl(gs2_handle* h) {
   delete h->prof;
   for (void* p : h->allocs) cudaFree(p);
   if (h->st_host) cudaFreeHost(h->st_host);
+  if (h->err_host) cudaFreeHost(h->err_host);
   if (h->stop_mapped) cudaFreeHost((void*)h->stop_mapped);
   {
     std::lock_guard<std::mutex> g(g_host_mu);
@@ -492,6 +503,8 @@ gs2_status gs2_setup(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_
   for (int64_t i = 0; i < n; ++i) dinv[i] = 1.0 / diag[i];
   const size_t nv = (size_t)std::max<int64_t>(n, 1);
   h->dinv = (double*)h->dalloc(sizeof(double) * nv);
+  h->dev_err = (int*)h->dalloc(sizeof(int));
+  GS2_CUDA(cudaMemset(h->dev_err, 0, sizeof(int)));
   if (n) GS2_CUDA(cudaMemcpy(h->dinv, dinv.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
   h->r = (double*)h->dalloc(sizeof(double) * nv);
   h->rhat = (double*)h->dalloc(sizeof(double) * nv);
@@ -502,6 +515,11 @@ gs2_status gs2_setup(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_
   h->bstage = (double*)h->dalloc(sizeof(double) * nv);
   h->xstage = (double*)h->dalloc(sizeof(double) * nv);
   h->nblk = vec_blocks(h, n);
+  // reductions: at least ~16 rows per thread and one block per SM (the
+  // widest CGS2 kernels hold ~150 registers per thread, one 256-thread block
+  // per SM), so the per-block reduction stays small next to the FP64 work
+  h->nblk_dot = (int)std::max<int64_t>(
+      1, std::min<int64_t>((n + kVecThreads * 16 - 1) / (kVecThreads * 16), h->nsm));
   h->part_cap = h->nblk * (kMaxRestart + 2);
   h->part = (double*)h->dalloc(sizeof(double) * h->part_cap);
   for (int p = 1; p <= 2; ++p)
@@ -669,6 +687,27 @@ gs2_status gs2_profile_enable(gs2_handle* h, int enable) {
   if (!h) return GS2_ERR_INVALID_ARG;
   if (!h->prof) h->prof = new gs2::Profiler();
   h->prof->enabled = enable != 0;
+  return GS2_OK;
+}
+
+gs2_status gs2_check(gs2_handle* h) {
+  if (!h) return GS2_ERR_INVALID_ARG;
+  API_BEGIN
+  GS2_CUDA(cudaStreamSynchronize(h->stream));
+  int e = 0;
+  GS2_CUDA(cudaMemcpy(&e, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e) {
+    GS2_CUDA(cudaMemset(h->dev_err, 0, sizeof(int)));
+    GS2_THROW((gs2_status)e, "a device-side bounded wait gave up (copy never completed)");
+  }
+  return GS2_OK;
+  API_END
+}
+
+gs2_status gs2_profile_filter(gs2_handle* h, const char* name) {
+  if (!h) return GS2_ERR_INVALID_ARG;
+  if (!h->prof) h->prof = new gs2::Profiler();
+  h->prof->only = name ? name : "";
   return GS2_OK;
 }
 

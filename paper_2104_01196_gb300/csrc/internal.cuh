@@ -58,11 +58,12 @@ struct DevCsr {
   __half* va16 = nullptr;  // FP16 scaled copy (triangles)
   float* scale16 = nullptr;
   int tpr = 1;             // lanes per row (K) of the tile kernels
-  // row tiles: rows [tile_row[t], tile_row[t+1]); a tile with more than
-  // `cap` entries holds exactly one (long) row
+  // row tiles: desc[t] = {first row, end row, first staged entry (rowptr
+  // rounded down to 8), end entry}; a tile with more than `cap` entries
+  // holds exactly one (long) row and has desc.z = -1 - rowptr[first row]
   int ntiles = 0;
   int cap = 0;
-  int* tile_row = nullptr;  // ntiles + 1
+  int4* desc = nullptr;  // ntiles
   double mean_row = 0.0;
 };
 
@@ -94,6 +95,7 @@ struct gs2_handle {
   int64_t n = 0, nnz = 0;
   gs2::DevCsr A, L, U;  // L, U prescaled: D^{-1} L and D^{-1} U
   double* dinv = nullptr;
+  int* dev_err = nullptr;  // sticky device error word (bounded waits)
   int64_t dev_bytes = 0;
   std::vector<void*> allocs;
 
@@ -102,7 +104,8 @@ struct gs2_handle {
   double *z = nullptr, *t = nullptr, *bstage = nullptr, *xstage = nullptr;
   float *rhat32 = nullptr, *g32a = nullptr, *g32b = nullptr;
   double* part = nullptr;  // per-block partial sums
-  int nblk = 0;            // blocks of the vector kernels
+  int nblk = 0;            // blocks of the elementwise vector kernels
+  int nblk_dot = 0;        // blocks of the reduction kernels (<= nblk)
   int part_cap = 0;        // doubles in `part`
 
   // level sets (lazy)
@@ -118,6 +121,7 @@ struct gs2_handle {
   double *p = nullptr, *q = nullptr;
   gs2::KrylovState* st = nullptr;       // device
   gs2::KrylovState* st_host = nullptr;  // pinned mirror
+  int* err_host = nullptr;              // pinned mirror of dev_err
   volatile int* stop_mapped = nullptr;  // pinned, device-mapped stop flag
   int* stop_mapped_dev = nullptr;
 

@@ -18,6 +18,7 @@
 // read-only path and stay L2-resident.
 #include <cuda_fp16.h>
 
+#include <cstdint>
 #include <map>
 #include <mutex>
 #include <utility>
@@ -73,93 +74,224 @@ struct ValTraits<__half> {
   __device__ static float get(const __half* p, int k) { return __half2float(p[k]); }
 };
 
-// streaming 16-byte load (read once: evict-first in L2, no L1 allocation)
-__device__ __forceinline__ int4 ld_stream(const int4* p) { return __ldcs(p); }
+// ---------------------------------------------------------------------------
+// TMA bulk copies and mbarriers (inline PTX, sm_90+ / sm_103a)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// order this thread's (and, after a barrier, the block's) generic-proxy
+// accesses of shared memory before later async-proxy (TMA) writes
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t tx) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(tx)
+               : "memory");
+}
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+// 1-D bulk copy global -> shared, completion counted on `bar` in bytes;
+// src and dst 16-byte aligned, bytes a positive multiple of 16
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes,
+                                            uint64_t* bar, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
+      "[%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: gives up after ~2 s of SM clock so that a wrong transaction
+// count can never hang the GPU; the caller reports GS2_ERR_TIMEOUT.
+constexpr long long kWaitBudgetCycles = 4LL << 30;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > kWaitBudgetCycles) return false;
+  return true;
+}
 
 // ---------------------------------------------------------------------------
 // tile engine
 // ---------------------------------------------------------------------------
 
-// Matrix view for the engine.  Tiles: rows [tile_row[t], tile_row[t+1]);
-// a tile holding one row longer than `cap` entries is processed from global
-// memory by the whole block.
+// Matrix view for the engine.  Tile t = rows [d.x, d.y) with d = desc[t];
+// d.z = first staged entry (rowptr[d.x] rounded down to 8) and d.w =
+// rowptr[d.y]; a tile holding one row longer than `cap` entries has
+// d.z = -1 - rowptr[d.x] and is processed from global memory by the block.
 template <typename VT>
 struct TileMat {
   int n;
   int ntiles;
-  int cap;  // max staged entries of a normal tile (multiple of 8)
+  int cap;   // max staged entries of a normal tile (multiple of 8)
+  int rcap;  // max rows of a tile
   const int* __restrict__ rp;
   const int* __restrict__ ci;
   const VT* __restrict__ va;
-  const int* __restrict__ tile_row;
+  const int4* __restrict__ desc;
+  int* err;  // set to GS2_ERR_TIMEOUT if a copy never completes
+};
+
+__host__ __device__ constexpr int round16(int b) { return (b + 15) & ~15; }
+
+template <typename VT>
+struct StageLayout {
+  int rp_off, ci_off, va_off, bytes;
+  __host__ __device__ StageLayout(int rcap, int cap) {
+    rp_off = 0;
+    ci_off = round16((rcap + 8) * 4);
+    va_off = ci_off + round16((cap + 8) * 4);
+    bytes = ((va_off + round16((cap + 8) * (int)sizeof(VT))) + 127) & ~127;
+  }
 };
 
 // Engine: for every row i, acc_i = sum_k va[k] * epi.gather(ci[k]), then
-// epi.finish(i, acc_i).  K lanes per row, each summing one contiguous
-// segment of the row, combined by a K-wide shuffle tree.
+// epi.finish(i, acc_i).  Double-buffered: while the block reduces tile t
+// from one shared-memory stage, one thread has TMA fill the other stage
+// with tile t + grid (its rowptr slice, columns and values), completion
+// tracked by one mbarrier per stage.  Rows are reduced by one thread each
+// (K = 1) or by K contiguous segments and a K-wide shuffle tree.  The
+// epilogue's per-row operands are loaded before the gathers.
 template <int K, typename VT, class Epi>
 __global__ void __launch_bounds__(kRowThreads)
 k_tiles(TileMat<VT> M, Epi epi, const int* skip) {
   using AT = typename ValTraits<VT>::AT;
   if (skip && *skip) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  int* s_ci = reinterpret_cast<int*>(smem_raw);
-  VT* s_va = reinterpret_cast<VT*>(smem_raw + (size_t)(M.cap + 8) * sizeof(int));
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bars[2];
   __shared__ AT red[kRowThreads / 32];
-
+  const StageLayout<VT> L(M.rcap, M.cap);
   const int q = threadIdx.x / K;  // row slot inside the tile
   const int l = threadIdx.x % K;  // segment of the row
+  uint64_t policy = 0;
 
-  for (int t = blockIdx.x; t < M.ntiles; t += gridDim.x) {
-    const int r0 = M.tile_row[t], r1 = M.tile_row[t + 1];
-    const int a = M.rp[r0], b = M.rp[r1];
-    if (b - a > M.cap) {
+  // thread 0: describe and start the copies of tile t into stage st
+  auto issue = [&](int t, int st) {
+    const int4 d = M.desc[t];
+    unsigned char* base = smem_raw + (size_t)st * L.bytes;
+    uint32_t tx = 0;
+    uint32_t brp = 0, bci = 0, bva = 0;
+    if (d.z >= 0) {
+      const int rpb = d.x & ~3;
+      brp = (uint32_t)round16((d.y + 1 - rpb) * 4);
+      const int cnt = d.w - d.z;
+      bci = (uint32_t)round16(cnt * 4);
+      bva = cnt > 0 ? (uint32_t)round16(cnt * (int)sizeof(VT)) : 0u;
+      if (cnt == 0) bci = 0;
+      tx = brp + bci + bva;
+    }
+    mbar_arrive_expect_tx(&bars[st], tx);
+    if (d.z >= 0) {
+      tma_load_1d(base + L.rp_off, M.rp + (d.x & ~3), brp, &bars[st], policy);
+      if (bci) tma_load_1d(base + L.ci_off, M.ci + d.z, bci, &bars[st], policy);
+      if (bva) tma_load_1d(base + L.va_off, M.va + d.z, bva, &bars[st], policy);
+    }
+  };
+
+  if (threadIdx.x == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_mbar_init();
+    policy = l2_evict_first_policy();
+    if ((int)blockIdx.x < M.ntiles) issue(blockIdx.x, 0);
+  }
+  __syncthreads();
+
+  int it = 0;
+  for (int t = blockIdx.x; t < M.ntiles; t += gridDim.x, ++it) {
+    const int st = it & 1;
+    const int tn = t + gridDim.x;
+    if (threadIdx.x == 0 && tn < M.ntiles) {
+      fence_proxy_async_smem();
+      issue(tn, st ^ 1);
+    }
+    const int4 d = M.desc[t];
+    const bool ok = mbar_wait_bounded(&bars[st], (it >> 1) & 1);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0 && M.err) atomicExch(M.err, (int)GS2_ERR_TIMEOUT);
+      return;
+    }
+    if (d.z < 0) {
       // one long row: whole block, straight from global memory
+      const int a = -1 - d.z;
       AT s = AT(0);
-      for (int k = a + threadIdx.x; k < b; k += blockDim.x)
+      for (int k = a + threadIdx.x; k < d.w; k += blockDim.x)
         s = fma((AT)ValTraits<VT>::get(M.va, k), (AT)epi.gather(M.ci[k]), s);
       s = block_sum<AT>(s, red);
-      if (threadIdx.x == 0) epi.finish(r0, s);
+      if (threadIdx.x == 0) epi.finish(d.x, s, epi.pre(d.x));
       __syncthreads();
       continue;
     }
-    // stage col and val of the tile, aligned down to 8 entries so that
-    // every 16-byte vector load is aligned (arrays are padded at the end)
-    const int a0 = a & ~7;
-    const int cnt = b - a0;
-    {
-      const int nci = (cnt + 3) >> 2;
-      const int4* src = reinterpret_cast<const int4*>(M.ci + a0);
-      int4* dst = reinterpret_cast<int4*>(s_ci);
-      for (int v = threadIdx.x; v < nci; v += blockDim.x) dst[v] = ld_stream(src + v);
-      constexpr int per = 16 / sizeof(VT);
-      const int nva = (cnt + per - 1) / per;
-      const int4* srcv = reinterpret_cast<const int4*>(M.va + a0);
-      int4* dstv = reinterpret_cast<int4*>(s_va);
-      for (int v = threadIdx.x; v < nva; v += blockDim.x) dstv[v] = ld_stream(srcv + v);
-    }
-    __syncthreads();
-    const int row = r0 + q;
+    const unsigned char* base = smem_raw + (size_t)st * L.bytes;
+    const int* s_rp = reinterpret_cast<const int*>(base + L.rp_off);
+    const int* s_ci = reinterpret_cast<const int*>(base + L.ci_off);
+    const VT* s_va = reinterpret_cast<const VT*>(base + L.va_off);
+    const int rpb = d.x & ~3;
+    const int row = d.x + q;
     AT s = AT(0);
-    if (row < r1) {
-      const int rs = M.rp[row] - a0, re = M.rp[row + 1] - a0;
+    typename Epi::Pre pv{};
+    if (row < d.y) {
+      pv = epi.pre(row);
+      const int rs = s_rp[row - rpb] - d.z, re = s_rp[row + 1 - rpb] - d.z;
       int ks = rs, ke = re;
       if (K > 1) {
         const int seg = (re - rs + K - 1) / K;
         ks = min(rs + l * seg, re);
         ke = min(ks + seg, re);
       }
-      for (int k = ks; k < ke; ++k)
-        s = fma((AT)ValTraits<VT>::get(s_va, k), (AT)epi.gather(s_ci[k]), s);
+      int k = ks;
+      // groups of four: all four gathers are in flight before the FMAs
+      for (; k + 4 <= ke; k += 4) {
+        const AT x0 = (AT)epi.gather(s_ci[k]), x1 = (AT)epi.gather(s_ci[k + 1]);
+        const AT x2 = (AT)epi.gather(s_ci[k + 2]), x3 = (AT)epi.gather(s_ci[k + 3]);
+        s = fma((AT)ValTraits<VT>::get(s_va, k), x0, s);
+        s = fma((AT)ValTraits<VT>::get(s_va, k + 1), x1, s);
+        s = fma((AT)ValTraits<VT>::get(s_va, k + 2), x2, s);
+        s = fma((AT)ValTraits<VT>::get(s_va, k + 3), x3, s);
+      }
+      const int rem = ke - k;
+      if (rem > 0) {
+        const AT x0 = (AT)epi.gather(s_ci[k]);
+        const AT x1 = rem > 1 ? (AT)epi.gather(s_ci[k + 1]) : AT(0);
+        const AT x2 = rem > 2 ? (AT)epi.gather(s_ci[k + 2]) : AT(0);
+        s = fma((AT)ValTraits<VT>::get(s_va, k), x0, s);
+        if (rem > 1) s = fma((AT)ValTraits<VT>::get(s_va, k + 1), x1, s);
+        if (rem > 2) s = fma((AT)ValTraits<VT>::get(s_va, k + 2), x2, s);
+      }
     }
     if (K > 1) s = group_sum<K, AT>(s);
-    if (row < r1 && l == 0) epi.finish(row, s);
+    if (row < d.y && l == 0) epi.finish(row, s, pv);
     __syncthreads();
   }
 }
 
 // ---------------------------------------------------------------------------
-// epilogues
+// epilogues: pre(i) loads the row's operands before the gathers, finish(i,
+// s, pre) consumes the row sum
 // ---------------------------------------------------------------------------
 
 // r = b - A x;  rhat = D^{-1} r   (Eq. 4 residual and Eq. 5 initial guess)
@@ -170,10 +302,14 @@ struct EpiResid {
   double* __restrict__ r;
   double* __restrict__ rhat64;
   float* __restrict__ rhat32;
+  struct Pre {
+    double b, d;
+  };
+  __device__ Pre pre(int i) const { return Pre{b[i], dinv[i]}; }
   __device__ double gather(int c) const { return __ldg(x + c); }
-  __device__ void finish(int i, double s) const {
-    const double ri = b[i] - s;
-    const double rh = dinv[i] * ri;
+  __device__ void finish(int i, double s, const Pre& p) const {
+    const double ri = p.b - s;
+    const double rh = p.d * ri;
     if (r) r[i] = ri;
     if (rhat64) rhat64[i] = rh;
     if (rhat32) rhat32[i] = (float)rh;
@@ -183,8 +319,10 @@ struct EpiResid {
 struct EpiSpmv {
   const double* __restrict__ x;
   double* __restrict__ y;
+  struct Pre {};
+  __device__ Pre pre(int) const { return Pre{}; }
   __device__ double gather(int c) const { return __ldg(x + c); }
-  __device__ void finish(int i, double s) const { y[i] = s; }
+  __device__ void finish(int i, double s, const Pre&) const { y[i] = s; }
 };
 
 // x_out = x_in + omega D^{-1} (b - A x_in)   (damped JR, ping-pong buffers)
@@ -194,9 +332,13 @@ struct EpiJr {
   const double* __restrict__ dinv;
   double* __restrict__ x_out;
   double omega;
+  struct Pre {
+    double x, b, d;
+  };
+  __device__ Pre pre(int i) const { return Pre{x[i], b[i], dinv[i]}; }
   __device__ double gather(int c) const { return __ldg(x + c); }
-  __device__ void finish(int i, double s) const {
-    x_out[i] = x[i] + omega * (dinv[i] * (b[i] - s));
+  __device__ void finish(int i, double s, const Pre& p) const {
+    x_out[i] = p.x + omega * (p.d * (p.b - s));
   }
 };
 
@@ -213,13 +355,25 @@ struct EpiInner {
   double omega64;
   int mode;
   int damped;
+  struct Pre {
+    AT rh, gi, sc;
+    double xi;
+  };
+  __device__ Pre pre(int i) const {
+    Pre p;
+    p.rh = (AT)rhat[i];
+    p.gi = damped ? (AT)g_in[i] : AT(0);
+    p.sc = rowscale ? (AT)rowscale[i] : AT(1);
+    p.xi = mode == INNER_LAST_ADD ? x[i] : 0.0;
+    return p;
+  }
   __device__ AT gather(int c) const { return (AT)__ldg(g_in + c); }
-  __device__ void finish(int i, AT s) const {
-    if (rowscale) s *= (AT)rowscale[i];
-    AT go = (AT)rhat[i] - omega * s;
-    if (damped) go = (AT(1) - gamma) * (AT)g_in[i] + gamma * go;
+  __device__ void finish(int i, AT s, const Pre& p) const {
+    if (rowscale) s *= p.sc;
+    AT go = p.rh - omega * s;
+    if (damped) go = (AT(1) - gamma) * p.gi + gamma * go;
     if (mode == INNER_MID) g_out[i] = (GT)go;
-    else if (mode == INNER_LAST_ADD) x[i] += omega64 * (double)go;
+    else if (mode == INNER_LAST_ADD) x[i] = p.xi + omega64 * (double)go;
     else x[i] = omega64 * (double)go;
   }
 };
@@ -230,16 +384,21 @@ struct EpiInner {
 
 // Resident blocks per SM of a tile kernel at a dynamic shared-memory size,
 // queried once per (kernel, size) and cached (the query and the attribute
-// call cost microseconds of host time per launch otherwise).
+// call cost microseconds of host time per launch otherwise).  The dynamic
+// shared-memory limit is one attribute per kernel, so it is only ever
+// raised: matrices with smaller tiles keep launching under the larger limit.
 static int blocks_per_sm(const void* fn, size_t smem) {
   static std::mutex mu;
   static std::map<std::pair<const void*, size_t>, int> cache;
+  static std::map<const void*, size_t> attr;
   std::lock_guard<std::mutex> g(mu);
   auto key = std::make_pair(fn, smem);
   auto it = cache.find(key);
   if (it != cache.end()) return it->second;
-  if (smem > 48 * 1024)
+  if (smem > 48 * 1024 && smem > attr[fn]) {
     GS2_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr[fn] = smem;
+  }
   int per_sm = 0;
   GS2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kRowThreads, smem));
   if (per_sm < 1) per_sm = 1;
@@ -248,15 +407,17 @@ static int blocks_per_sm(const void* fn, size_t smem) {
 }
 
 template <typename VT>
-static TileMat<VT> view(const DevCsr& M, const VT* va) {
+static TileMat<VT> view(gs2_handle* h, const DevCsr& M, const VT* va) {
   TileMat<VT> t;
   t.n = M.n;
   t.ntiles = M.ntiles;
   t.cap = M.cap;
+  t.rcap = kRowThreads / M.tpr;
   t.rp = M.rp;
   t.ci = M.ci;
   t.va = va;
-  t.tile_row = M.tile_row;
+  t.desc = M.desc;
+  t.err = h->dev_err;
   return t;
 }
 
@@ -264,11 +425,11 @@ template <int K, typename VT, class Epi>
 static void launch_k(gs2_handle* h, const DevCsr& M, const VT* va, const Epi& epi,
                      const int* skip) {
   if (M.n == 0 || M.ntiles == 0) return;
-  const size_t smem = (size_t)(M.cap + 8) * (sizeof(int) + sizeof(VT)) + 16;
+  const size_t smem = 2 * (size_t)StageLayout<VT>(kRowThreads / K, M.cap).bytes;
   auto fn = k_tiles<K, VT, Epi>;
   const int per_sm = blocks_per_sm((const void*)fn, smem);
   const int grid = std::min(M.ntiles, per_sm * h->nsm);
-  fn<<<grid, kRowThreads, smem, h->stream>>>(view<VT>(M, va), epi, skip);
+  fn<<<grid, kRowThreads, smem, h->stream>>>(view<VT>(h, M, va), epi, skip);
   GS2_LAUNCH_CHECK();
 }
 

@@ -9,6 +9,8 @@
 // then one block per coefficient), so results are bitwise reproducible.
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <thread>
 #include <vector>
 
@@ -26,7 +28,8 @@ __device__ __forceinline__ double warp_sum(double s) {
   return s;
 }
 
-// Block-wide sums of NV per-thread values, written to part[v * nblk + blk].
+// Block-wide sums of NV per-thread values, written to part[v * nblk + blk]
+// (general form: one shuffle tree per value; used for NV > 32).
 template <int NV>
 __device__ __forceinline__ void block_partials(const double (&acc)[NV], int nv, double* part,
                                                int nblk) {
@@ -45,6 +48,66 @@ __device__ __forceinline__ void block_partials(const double (&acc)[NV], int nv, 
 #pragma unroll
     for (int w = 0; w < kVecThreads / 32; ++w) s += red[w][v];
     part[(size_t)v * nblk + blockIdx.x] = s;
+  }
+}
+
+template <int N>
+struct Pow2 {
+  static constexpr int value = N <= 1 ? 1 : 2 * Pow2<(N + 1) / 2>::value;
+};
+template <>
+struct Pow2<1> {
+  static constexpr int value = 1;
+};
+template <int P>
+struct Log2 {
+  static constexpr int value = P <= 1 ? 0 : 1 + Log2<P / 2>::value;
+};
+template <>
+struct Log2<1> {
+  static constexpr int value = 0;
+};
+
+// Block-wide sums of NV <= 32 per-thread values.  Inside a warp a butterfly
+// transpose-reduction halves the values each lane holds at every exchange,
+// P - 1 adds per lane for P = NV rounded up to a power of two, instead of
+// 5 adds per value of a shuffle tree -- the FP64 pipe is the bottleneck of
+// these kernels.  After it lane l holds the warp's sum of value l >> (5 - p).
+template <int NV>
+__device__ __forceinline__ void block_partials_bf(const double (&acc)[NV], double* part,
+                                                  int nblk) {
+  constexpr int P = Pow2<NV>::value;
+  constexpr int p = Log2<P>::value;
+  static_assert(P <= 32, "butterfly reduction holds at most 32 values");
+  __shared__ double red[kVecThreads / 32][P];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double a[P];
+#pragma unroll
+  for (int k = 0; k < P; ++k) a[k] = k < NV ? acc[k] : 0.0;
+#pragma unroll
+  for (int s = 0; s < p; ++s) {
+    const int off = 16 >> s;
+    const int half = (P >> s) / 2;
+    const bool upper = (lane & off) != 0;
+#pragma unroll
+    for (int j = 0; j < half; ++j) {
+      const double send = upper ? a[j] : a[j + half];
+      const double recv = __shfl_xor_sync(0xffffffffu, send, off);
+      a[j] = (upper ? a[j + half] : a[j]) + recv;
+    }
+  }
+  // lanes that differ only in their low 5 - p bits hold parts of the same
+  // value: finish with a plain tree over those bits
+#pragma unroll
+  for (int o = 16 >> p; o > 0; o >>= 1) a[0] += __shfl_xor_sync(0xffffffffu, a[0], o);
+  const int k = lane >> (5 - p);
+  if ((lane & ((1 << (5 - p)) - 1)) == 0) red[wid][k] = a[0];
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kVecThreads / 32; ++w) s += red[w][threadIdx.x];
+    part[(size_t)threadIdx.x * nblk + blockIdx.x] = s;
   }
 }
 
@@ -73,9 +136,61 @@ __global__ void k_reduce_cols(const double* __restrict__ part, int nblk, double*
 
 // ---------------------------------------------------------------------------
 // CGS2 passes over the basis V (row-major by vector, ld = n)
+//
+// For j + 1 <= 32 basis vectors the kernels are instantiated for the exact
+// count JC, so no predicated-off FP64 instruction takes an issue slot; larger
+// restarts use the MAXK = 64 forms with a runtime bound.
 // ---------------------------------------------------------------------------
 
-// pass 1: part = V[0..jc)^T w
+// pass 1: part = V[0..JC)^T w
+template <int JC>
+__global__ void __launch_bounds__(kVecThreads)
+k_dots_x(int n, const double* __restrict__ V, const double* __restrict__ w, double* part,
+         int nblk, const int* skip) {
+  if (skip && *skip) return;
+  double acc[JC];
+#pragma unroll
+  for (int k = 0; k < JC; ++k) acc[k] = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double wi = w[i];
+#pragma unroll
+    for (int k = 0; k < JC; ++k) acc[k] = fma(__ldg(V + (size_t)k * n + i), wi, acc[k]);
+  }
+  block_partials_bf<JC>(acc, part, nblk);
+}
+
+// pass 2: w -= V h ; part = V^T w          (NORM = false)
+// pass 3: w -= V h ; part[0] = w^T w       (NORM = true)
+// V h is summed in four interleaved partial sums to shorten the FMA chain.
+template <int JC, bool NORM>
+__global__ void __launch_bounds__(kVecThreads)
+k_update_x(int n, const double* __restrict__ V, const double* __restrict__ hcoef,
+           double* __restrict__ w, double* part, int nblk, const int* skip) {
+  if (skip && *skip) return;
+  __shared__ double hs[JC];
+  for (int k = threadIdx.x; k < JC; k += blockDim.x) hs[k] = hcoef[k];
+  __syncthreads();
+  constexpr int NA = NORM ? 1 : JC;
+  double acc[NA];
+#pragma unroll
+  for (int k = 0; k < NA; ++k) acc[k] = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double sp[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int k = 0; k < JC; ++k) sp[k & 3] = fma(__ldg(V + (size_t)k * n + i), hs[k], sp[k & 3]);
+    const double wn = w[i] - ((sp[0] + sp[1]) + (sp[2] + sp[3]));
+    w[i] = wn;
+    if (NORM) {
+      acc[0] = fma(wn, wn, acc[0]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < NA; ++k) acc[k] = fma(__ldg(V + (size_t)k * n + i), wn, acc[k]);
+    }
+  }
+  block_partials_bf<NA>(acc, part, nblk);
+}
+
+// runtime-bounded forms for 32 < j + 1 <= 64
 template <int MAXK>
 __global__ void __launch_bounds__(kVecThreads)
 k_dots(int n, const double* __restrict__ V, int jc, const double* __restrict__ w,
@@ -93,8 +208,6 @@ k_dots(int n, const double* __restrict__ V, int jc, const double* __restrict__ w
   block_partials<MAXK>(acc, jc, part, nblk);
 }
 
-// pass 2: w -= V h ; part = V^T w          (NORM = false)
-// pass 3: w -= V h ; part[0] = w^T w       (NORM = true)
 template <int MAXK, bool NORM>
 __global__ void __launch_bounds__(kVecThreads)
 k_update(int n, const double* __restrict__ V, int jc, const double* __restrict__ hcoef,
@@ -125,70 +238,82 @@ k_update(int n, const double* __restrict__ V, int jc, const double* __restrict__
   block_partials<NA>(acc, NORM ? 1 : jc, part, nblk);
 }
 
-// Givens step j (one thread): H(j+1, j) = ||w||, earlier rotations applied
-// to column j, new rotation from (H(j,j), H(j+1,j)) with
+// Givens step j: H(j+1, j) = ||w||, earlier rotations applied to column j,
+// new rotation from (H(j,j), H(j+1,j)) with
 //   d = sqrt(f^2 + g^2), c = |f|/d, r = sign(f) d, s = g/r
 // (f = 0: c = 0, s = sign(g), r = |g|; g = 0: c = 1, s = 0, r = f),
-// residual estimate |g_{j+1}|, and the stop decision of the cycle.
+// residual estimate |g_{j+1}|, and the stop decision of the cycle.  The
+// column and the earlier rotations are staged in shared memory by all
+// threads; the sequential rotation chain then runs on shared memory.
 __global__ void k_givens(const double* __restrict__ part, int nblk, double* H, int ldh, int j,
                          double* cs, double* sn, double* gv, KrylovState* st,
                          volatile int* stop_host) {
   if (st->stop) return;
   __shared__ double red[32];
+  __shared__ double col_s[kMaxRestart + 2], cs_s[kMaxRestart + 1], sn_s[kMaxRestart + 1];
+  double* col = H + (size_t)j * ldh;
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) col_s[i] = col[i];
+  for (int i = threadIdx.x; i < j; i += blockDim.x) {
+    cs_s[i] = cs[i];
+    sn_s[i] = sn[i];
+  }
   double s = 0.0;
   for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part[b];
   s = warp_sum(s);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) red[wid] = s;
   __syncthreads();
-  if (threadIdx.x != 0) return;
-  double nrm2 = 0.0;
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) nrm2 += red[w];
-  const double hn = sqrt(nrm2);
-  double* col = H + (size_t)j * ldh;
-  col[j + 1] = hn;
-  for (int i = 0; i < j; ++i) {
-    const double a = col[i], c = col[i + 1];
-    col[i] = cs[i] * a + sn[i] * c;
-    col[i + 1] = -sn[i] * a + cs[i] * c;
+  if (threadIdx.x == 0) {
+    double nrm2 = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) nrm2 += red[w];
+    const double hn = sqrt(nrm2);
+    col_s[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {
+      const double a = col_s[i], c = col_s[i + 1];
+      col_s[i] = cs_s[i] * a + sn_s[i] * c;
+      col_s[i + 1] = -sn_s[i] * a + cs_s[i] * c;
+    }
+    const double f = col_s[j], g = col_s[j + 1];
+    double c, sgv, r;
+    if (g == 0.0) {
+      c = 1.0; sgv = 0.0; r = f;
+    } else if (f == 0.0) {
+      c = 0.0; sgv = g > 0.0 ? 1.0 : -1.0; r = fabs(g);
+    } else {
+      const double d = sqrt(f * f + g * g);
+      c = fabs(f) / d;
+      r = f > 0.0 ? d : -d;
+      sgv = g / r;
+    }
+    cs[j] = c;
+    sn[j] = sgv;
+    col_s[j] = r;
+    col_s[j + 1] = 0.0;
+    const double gj = gv[j];
+    gv[j + 1] = -sgv * gj;
+    gv[j] = c * gj;
+    st->iters += 1;
+    st->k = j + 1;
+    st->hn = hn;
+    st->inv_hn = 1.0 / hn;
+    const double est = fabs(-sgv * gj);
+    int stop = 0;
+    if (isnan(est) || isnan(hn) || isinf(hn)) {
+      st->status = GS2_ERR_NAN;
+      stop = 1;
+    } else if (hn == 0.0) {
+      st->status = GS2_ERR_BREAKDOWN;
+      stop = 1;
+    } else if (est <= st->tol_abs || st->iters >= st->max_iters) {
+      stop = 1;
+    }
+    if (stop) {
+      st->stop = 1;
+      *stop_host = 1;
+    }
   }
-  const double f = col[j], g = col[j + 1];
-  double c, sgv, r;
-  if (g == 0.0) {
-    c = 1.0; sgv = 0.0; r = f;
-  } else if (f == 0.0) {
-    c = 0.0; sgv = g > 0.0 ? 1.0 : -1.0; r = fabs(g);
-  } else {
-    const double d = sqrt(f * f + g * g);
-    c = fabs(f) / d;
-    r = f > 0.0 ? d : -d;
-    sgv = g / r;
-  }
-  cs[j] = c;
-  sn[j] = sgv;
-  col[j] = r;
-  col[j + 1] = 0.0;
-  gv[j + 1] = -sgv * gv[j];
-  gv[j] = c * gv[j];
-  st->iters += 1;
-  st->k = j + 1;
-  st->hn = hn;
-  st->inv_hn = 1.0 / hn;
-  const double est = fabs(gv[j + 1]);
-  int stop = 0;
-  if (isnan(est) || isnan(hn) || isinf(hn)) {
-    st->status = GS2_ERR_NAN;
-    stop = 1;
-  } else if (hn == 0.0) {
-    st->status = GS2_ERR_BREAKDOWN;
-    stop = 1;
-  } else if (est <= st->tol_abs || st->iters >= st->max_iters) {
-    stop = 1;
-  }
-  if (stop) {
-    st->stop = 1;
-    *stop_host = 1;
-  }
+  __syncthreads();
+  for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) col[i] = col_s[i];
 }
 
 // v_{j+1} = w / H(j+1, j), and the preconditioner's D^{-1} v_{j+1}
@@ -205,15 +330,26 @@ __global__ void k_scale_next(int n, const double* __restrict__ w, double* vnext,
   }
 }
 
-// y = R^{-1} g over the k steps of the cycle (back substitution, one thread)
+// y = R^{-1} g over the k steps of the cycle: column-oriented back
+// substitution, y_i = g_i / R_ii, then every g_l (l < i) -= R_li y_i in
+// parallel; g lives in shared memory.
 __global__ void k_backsolve(const double* __restrict__ H, int ldh, const double* gv, double* y,
                             const KrylovState* st) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  __shared__ double g_s[kMaxRestart + 1];
+  __shared__ double yi_s;
   const int k = st->k;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) g_s[i] = gv[i];
+  __syncthreads();
   for (int i = k - 1; i >= 0; --i) {
-    double s = gv[i];
-    for (int l = i + 1; l < k; ++l) s -= H[(size_t)l * ldh + i] * y[l];
-    y[i] = s / H[(size_t)i * ldh + i];
+    const double* ci = H + (size_t)i * ldh;
+    if (threadIdx.x == 0) {
+      yi_s = g_s[i] / ci[i];
+      y[i] = yi_s;
+    }
+    __syncthreads();
+    const double yi = yi_s;
+    for (int l = threadIdx.x; l < i; l += blockDim.x) g_s[l] -= ci[l] * yi;
+    __syncthreads();
   }
 }
 
@@ -304,6 +440,8 @@ void ensure_krylov(gs2_handle* h, int m) {
     h->st = (KrylovState*)h->dalloc(sizeof(KrylovState));
     GS2_CUDA(cudaMemset(h->st, 0, sizeof(KrylovState)));
     GS2_CUDA(cudaHostAlloc((void**)&h->st_host, sizeof(KrylovState), cudaHostAllocDefault));
+    GS2_CUDA(cudaHostAlloc((void**)&h->err_host, sizeof(int), cudaHostAllocDefault));
+    *h->err_host = 0;
     int* f = nullptr;
     GS2_CUDA(cudaHostAlloc((void**)&f, sizeof(int), cudaHostAllocMapped));
     *f = 0;
@@ -338,29 +476,77 @@ static int maxk_for(int jc) {
   return 64;
 }
 
-static void launch_dots(gs2_handle* h, int jc, const double* w, const int* skip) {
+#define GS2_JC_CASES(X)                                                                  \
+  X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16) \
+  X(17) X(18) X(19) X(20) X(21) X(22) X(23) X(24) X(25) X(26) X(27) X(28) X(29) X(30)  \
+  X(31) X(32)
+
+// Grid of a reduction kernel: as many blocks as stay resident on all SMs
+// (queried once per instantiation), but at least ~8 rows per thread and no
+// more blocks than the partial-sum buffer holds.
+static int reduction_grid(gs2_handle* h, const void* fn) {
+  static std::mutex mu;
+  static std::map<const void*, int> occ;
+  int per_sm;
+  {
+    std::lock_guard<std::mutex> g(mu);
+    auto it = occ.find(fn);
+    if (it == occ.end()) {
+      int b = 0;
+      GS2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, kVecThreads, 0));
+      it = occ.emplace(fn, std::max(b, 1)).first;
+    }
+    per_sm = it->second;
+  }
+  const int64_t want = (h->n + kVecThreads * 8 - 1) / (kVecThreads * 8);
+  return (int)std::max<int64_t>(1, std::min<int64_t>({want, (int64_t)per_sm * h->nsm,
+                                                      (int64_t)h->nblk}));
+}
+
+// Each launcher returns the number of blocks, i.e. of partial sums per value.
+static int launch_dots(gs2_handle* h, int jc, const double* w, const int* skip) {
   KernelTimer tm(h, "cgs2_dots", 8.0 * h->n * (jc + 1));
-  const int n = (int)h->n, nb = h->nblk;
-  switch (maxk_for(jc)) {
-    case 8: k_dots<8><<<nb, kVecThreads, 0, h->stream>>>(n, h->V, jc, w, h->part, nb, skip); break;
-    case 16: k_dots<16><<<nb, kVecThreads, 0, h->stream>>>(n, h->V, jc, w, h->part, nb, skip); break;
-    case 32: k_dots<32><<<nb, kVecThreads, 0, h->stream>>>(n, h->V, jc, w, h->part, nb, skip); break;
-    default: k_dots<64><<<nb, kVecThreads, 0, h->stream>>>(n, h->V, jc, w, h->part, nb, skip); break;
+  const int n = (int)h->n;
+  cudaStream_t s = h->stream;
+  int nb = 1;
+  switch (jc) {
+#define GS2_DOTS_CASE(J)                                                          \
+  case J:                                                                         \
+    nb = reduction_grid(h, (const void*)k_dots_x<J>);                             \
+    k_dots_x<J><<<nb, kVecThreads, 0, s>>>(n, h->V, w, h->part, nb, skip);        \
+    break;
+    GS2_JC_CASES(GS2_DOTS_CASE)
+#undef GS2_DOTS_CASE
+    default:
+      nb = reduction_grid(h, (const void*)k_dots<64>);
+      k_dots<64><<<nb, kVecThreads, 0, s>>>(n, h->V, jc, w, h->part, nb, skip);
+      break;
   }
   GS2_LAUNCH_CHECK();
+  return nb;
 }
 
 template <bool NORM>
-static void launch_update(gs2_handle* h, int jc, double* w, const int* skip) {
+static int launch_update(gs2_handle* h, int jc, double* w, const int* skip) {
   KernelTimer tm(h, NORM ? "cgs2_upd_norm" : "cgs2_upd_dots", 8.0 * h->n * (jc + 2));
-  const int n = (int)h->n, nb = h->nblk;
-  switch (maxk_for(jc)) {
-    case 8: k_update<8, NORM><<<nb, kVecThreads, 0, h->stream>>>(n, h->V, jc, h->hbuf, w, h->part, nb, skip); break;
-    case 16: k_update<16, NORM><<<nb, kVecThreads, 0, h->stream>>>(n, h->V, jc, h->hbuf, w, h->part, nb, skip); break;
-    case 32: k_update<32, NORM><<<nb, kVecThreads, 0, h->stream>>>(n, h->V, jc, h->hbuf, w, h->part, nb, skip); break;
-    default: k_update<64, NORM><<<nb, kVecThreads, 0, h->stream>>>(n, h->V, jc, h->hbuf, w, h->part, nb, skip); break;
+  const int n = (int)h->n;
+  cudaStream_t s = h->stream;
+  int nb = 1;
+  switch (jc) {
+#define GS2_UPD_CASE(J)                                                                 \
+  case J:                                                                               \
+    nb = reduction_grid(h, (const void*)k_update_x<J, NORM>);                           \
+    k_update_x<J, NORM><<<nb, kVecThreads, 0, s>>>(n, h->V, h->hbuf, w, h->part, nb, skip); \
+    break;
+    GS2_JC_CASES(GS2_UPD_CASE)
+#undef GS2_UPD_CASE
+    default:
+      nb = reduction_grid(h, (const void*)k_update<64, NORM>);
+      k_update<64, NORM><<<nb, kVecThreads, 0, s>>>(n, h->V, jc, h->hbuf, w, h->part, nb, skip);
+      break;
   }
   GS2_LAUNCH_CHECK();
+  return nb;
 }
 
 static void launch_combine(gs2_handle* h, int m, double* u, double* r64, float* r32) {
@@ -377,16 +563,32 @@ static void launch_combine(gs2_handle* h, int m, double* u, double* r64, float* 
 
 static void launch_norm(gs2_handle* h, const double* x, int which) {
   KernelTimer tm(h, "norm", 8.0 * h->n);
-  k_norm_part<<<h->nblk, kVecThreads, 0, h->stream>>>((int)h->n, x, h->part, h->nblk);
+  k_norm_part<<<h->nblk_dot, kVecThreads, 0, h->stream>>>((int)h->n, x, h->part, h->nblk_dot);
   GS2_LAUNCH_CHECK();
-  k_norm_final<<<1, 256, 0, h->stream>>>(h->part, h->nblk, h->st, which);
+  k_norm_final<<<1, 256, 0, h->stream>>>(h->part, h->nblk_dot, h->st, which);
   GS2_LAUNCH_CHECK();
 }
 
-void read_state(gs2_handle* h) {
+// Copy the device state and the sticky error word to pinned host memory.
+static void copy_state_async(gs2_handle* h) {
   GS2_CUDA(cudaMemcpyAsync(h->st_host, h->st, sizeof(KrylovState), cudaMemcpyDeviceToHost,
                            h->stream));
+  GS2_CUDA(cudaMemcpyAsync(h->err_host, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost,
+                           h->stream));
+}
+
+// A kernel gave up a bounded wait: clear the word and fail the call.
+static void raise_device_error(gs2_handle* h) {
+  const int e = *h->err_host;
+  *h->err_host = 0;
+  GS2_CUDA(cudaMemsetAsync(h->dev_err, 0, sizeof(int), h->stream));
+  GS2_THROW((gs2_status)e, "a device-side bounded wait gave up (copy never completed)");
+}
+
+void read_state(gs2_handle* h) {
+  copy_state_async(h);
   GS2_CUDA(cudaStreamSynchronize(h->stream));
+  if (*h->err_host) raise_device_error(h);
 }
 
 // ---------------------------------------------------------------------------
@@ -441,8 +643,7 @@ struct GmresRun {
   void launch_true_residual() {
     launch_resid(h, b, x, h->r, nullptr, nullptr, nullptr);
     launch_norm(h, h->r, 0);
-    GS2_CUDA(cudaMemcpyAsync(h->st_host, h->st, sizeof(KrylovState), cudaMemcpyDeviceToHost,
-                             h->stream));
+    copy_state_async(h);
   }
 
   void finish(gs2_status s) {
@@ -470,6 +671,7 @@ struct GmresRun {
         return;
       }
     }
+    if (*h->err_host) raise_device_error(h);
     const double beta = hs.beta;
     loc.true_relres = beta / bnorm;
     loc.iters = hs.iters;
@@ -485,7 +687,6 @@ struct GmresRun {
 
   void launch_cycle() {
     const int n = (int)h->n;
-    const int nb = h->nblk;
     const int ldh = m + 1;
     const int* skip = &h->st->stop;
     *h->stop_mapped = 0;
@@ -500,14 +701,14 @@ struct GmresRun {
       precond_apply(h, pc, vj, h->z, wants, skip);
       launch_spmv(h, h->z, h->w, skip);
       const int jc = j + 1;
-      launch_dots(h, jc, h->w, skip);
-      k_reduce_cols<<<jc, 256, 0, h->stream>>>(h->part, nb, h->H, ldh, j, h->hbuf, 0, skip);
+      int nbr = launch_dots(h, jc, h->w, skip);
+      k_reduce_cols<<<jc, 256, 0, h->stream>>>(h->part, nbr, h->H, ldh, j, h->hbuf, 0, skip);
       GS2_LAUNCH_CHECK();
-      launch_update<false>(h, jc, h->w, skip);
-      k_reduce_cols<<<jc, 256, 0, h->stream>>>(h->part, nb, h->H, ldh, j, h->hbuf, 1, skip);
+      nbr = launch_update<false>(h, jc, h->w, skip);
+      k_reduce_cols<<<jc, 256, 0, h->stream>>>(h->part, nbr, h->H, ldh, j, h->hbuf, 1, skip);
       GS2_LAUNCH_CHECK();
-      launch_update<true>(h, jc, h->w, skip);
-      k_givens<<<1, 256, 0, h->stream>>>(h->part, nb, h->H, ldh, j, h->cs, h->sn, h->gvec, h->st,
+      nbr = launch_update<true>(h, jc, h->w, skip);
+      k_givens<<<1, 256, 0, h->stream>>>(h->part, nbr, h->H, ldh, j, h->cs, h->sn, h->gvec, h->st,
                                          h->stop_mapped_dev);
       GS2_LAUNCH_CHECK();
       if (j + 1 < m) {
@@ -517,7 +718,7 @@ struct GmresRun {
       }
     }
     // x += M^{-1} V y
-    k_backsolve<<<1, 32, 0, h->stream>>>(h->H, ldh, h->gvec, h->y, h->st);
+    k_backsolve<<<1, 64, 0, h->stream>>>(h->H, ldh, h->gvec, h->y, h->st);
     GS2_LAUNCH_CHECK();
     launch_combine(h, m, h->w, r64, r32);
     precond_apply(h, pc, h->w, h->z, wants, nullptr);
@@ -673,7 +874,7 @@ gs2_status cg_run(gs2_handle* h, const double* b, double* x, double tol, int max
   }
   ensure_krylov(h, 1);
   const gs2_params* pc = (p && p->kind != GS2_PC_NONE) ? p : nullptr;
-  const int n = (int)h->n, nb = h->nblk;
+  const int n = (int)h->n, nb = h->nblk_dot;
   const int* skip = &h->st->stop;
   double* r = h->r;
   double* z = h->z;

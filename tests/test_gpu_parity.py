@@ -374,3 +374,38 @@ def test_full_size_gmres_true_residual(g, big):
     r = np.linalg.norm(big.b - oracle.spmv(big.A, xg)) / np.linalg.norm(big.b)
     assert r <= 1e-8 and abs(r - info.true_relres) <= 1e-12
     assert rel(xg, big.x_true) <= 1e-3
+
+
+def _oracle_counts():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "oracle_counts.txt")
+    out = {}
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            key, *kv = line.split()
+            out[key] = dict(x.split("=") for x in kv)
+    return out
+
+
+FULL_PCS = {
+    "sgs2_1_1": dict(kind="gs2", outer=1, inner=1, direction="symmetric"),
+    "sgs2_1_2": dict(kind="gs2", outer=1, inner=2, direction="symmetric"),
+    "sgs2_1_3": dict(kind="gs2", outer=1, inner=3, direction="symmetric"),
+    "sgs_exact": dict(kind="gs", outer=1, direction="symmetric"),
+    "jr3_w1.0": dict(kind="jr", outer=3, omega=1.0),
+    "jr3_w0.8": dict(kind="jr", outer=3, omega=0.8),
+}
+
+
+@pytest.mark.parametrize("pc", list(FULL_PCS))
+def test_full_size_iteration_counts_match_oracle(g, big, pc):
+    """3D Laplacian 128^3, GMRES(30) to 1e-8: the GPU's iteration count is
+    within +-1 of the oracle's (stored by tests/golden/make_oracle_counts.py)."""
+    ref = _oracle_counts()[f"poisson3d_128_gmres30_{pc}"]
+    h = g.gs2_setup(big.A)
+    x = dev(np.zeros(big.n))
+    info = g.gmres_solve(h, dev(big.b), x, 30, 1e-8, 5000, g.params(**FULL_PCS[pc]))
+    assert info.status == 0 and info.true_relres <= 1e-8
+    assert abs(info.iters - int(ref["iters"])) <= 1, (info.iters, ref)
