@@ -395,7 +395,9 @@ static int blocks_per_sm(const void* fn, size_t smem) {
   auto key = std::make_pair(fn, smem);
   auto it = cache.find(key);
   if (it != cache.end()) return it->second;
-  if (smem > 48 * 1024 && smem > attr[fn]) {
+  // the default 48 KB limit covers static + dynamic shared memory, so opt in
+  // well before the dynamic part alone reaches it
+  if (smem > 32 * 1024 && smem > attr[fn]) {
     GS2_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr[fn] = smem;
   }
