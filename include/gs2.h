@@ -148,6 +148,26 @@ gs2_status gs2_apply(gs2_handle* h, const double* b, double* x,
 gs2_status gs2_apply_ex(gs2_handle* h, const double* b, double* x,
                         const gs2_params* p);
 
+/* The gs2_apply relaxation for callers that cannot allocate device memory
+ * (an application that owns all GPU memory through its own allocator, code
+ * that must not allocate after start-up).  The paper has no counterpart:
+ * this is a library convenience.  No handle is needed and the call
+ * allocates nothing: its working memory (D^{-1}, r-hat and two inner
+ * iterates) is a fixed 8 MiB array inside the library's device image, held
+ * by every GPU that loads the library until the process exits.
+ *   n <= 262,144 rows, else GS2_ERR_INVALID_ARG; rowptr int64[n+1],
+ *   col int32[nnz], val, b (read) and x (read and overwritten) are device
+ *   pointers of the current device; stream as in gs2_setup.  The matrix is
+ *   not validated: a zero or missing diagonal gives inf/NaN in x.
+ * Every call uses the same array, so calls that overlap on the GPU race:
+ * serialise them.  The first call on a device looks the array up (with that
+ * device current); make it before any stream capture.  Results match
+ * gs2_apply to rounding (FP64, gamma = 1). */
+gs2_status gs2_apply_noalloc(int64_t n, const int64_t* rowptr, const int32_t* col,
+                             const double* val, const double* b, double* x,
+                             int outer_sweeps, int inner_sweeps, double damping,
+                             int direction, void* stream);
+
 /* Exact GS / SOR baseline: x + omega (D + omega T)^{-1} (b - A x) per half
  * sweep (Sec. 3, "Damping factor"), the triangular solve scheduled by
  * level sets of T (Sec. 3, level-set scheduling).  Levels are computed on
