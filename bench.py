@@ -45,6 +45,9 @@ def parse():
                     help="skip the baseline/precision comparison solves")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer e2e timing")
+    ap.add_argument("--no-serve", action="store_true", help="skip the request-stream run")
+    ap.add_argument("--serve-requests", type=int, default=40,
+                    help="requests of the served stream (bounded sample of 2000)")
     ap.add_argument("--no-profile", action="store_true",
                     help="do not time kernels with events inside the timed region")
     return ap.parse_args()
@@ -410,6 +413,8 @@ def run_ours(args):
 
     if rank == 0 and not args.no_extras and world == 1:
         out["comparisons"] = comparisons(gs2, torch, pr, stream, b)
+    if rank == 0 and not args.no_serve and world == 1:
+        out["serving"] = serving(gs2, torch, args.serve_requests)
     if rank == 0 and world == 1 and not args.no_cpu:
         per_iter, full, dt, its = oracle_sample(pr)
         if full:
@@ -425,6 +430,68 @@ def run_ours(args):
         print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def serving(gs2, torch, count):
+    """The request stream: 2D/3D Poisson and 3D convection-diffusion systems,
+    n log-uniform in [1e3, 2e6], lognormal(0,1) coefficients, GMRES(30) +
+    SGS2(1,1) to 1e-8 (a bounded sample of `count` requests).  Measured:
+    one-at-a-time gmres_solve, the server saturated (all submitted at once:
+    solves/s) and the server under open-loop Poisson arrivals at 60% of that
+    rate (p50/p99 submit-to-done latency), with FP64 and FP32 inner sweeps."""
+    from paper_2104_01196_gb300 import problems as P
+    recipe = P.request_stream(count, rate_hz=1.0, build=False)
+    probs = [P.variable_coefficient_problem(kind, N, seed) for _, kind, N, seed in recipe]
+    res = {"requests": count, "n_total": int(sum(p.n for p in probs)),
+           "n_range": [int(min(p.n for p in probs)), int(max(p.n for p in probs))]}
+    torch.cuda.synchronize()
+    # one at a time, FP64, through gmres_solve on fresh handles
+    t0 = time.perf_counter()
+    seq_fail = 0
+    for p in probs:
+        h = gs2.gs2_setup(p.A)
+        x = np.zeros(p.n)
+        info = gs2.gmres_solve(h, p.b.copy(), x, 30, 1e-8, 4000,
+                               gs2.params("gs2", 1, 1, direction="symmetric"))
+        seq_fail += info.status != 0
+        h.close()
+    res["sequential_fp64"] = {"solves_per_s": count / (time.perf_counter() - t0),
+                              "failed": int(seq_fail)}
+    for prec in ("fp64", "fp32"):
+        pc = gs2.params("gs2", 1, 1, direction="symmetric", precision=prec)
+        srv = gs2.Server(restart=30, tol=1e-8, max_iters=4000, precond=pc, max_slots=8,
+                         prep_threads=4)
+        t0 = time.perf_counter()
+        tickets = [srv.submit(p.A, p.b) for p in probs]
+        lat, worst = [], 0.0
+        for t, p in zip(tickets, probs):
+            info, x, ms = srv.wait(t, p.n)
+            lat.append(ms)
+            worst = max(worst, info.true_relres if info.status == 0 else float("inf"))
+        dt = time.perf_counter() - t0
+        st = srv.stats()
+        rate = count / dt
+        # open loop: Poisson arrivals at 60% of the saturated rate
+        gaps = -np.log(1.0 - P.uniform01(P.SEED_BASE + 77, count)) / (0.6 * rate)
+        arrivals = np.cumsum(gaps)
+        t0 = time.perf_counter()
+        tickets = []
+        for a, p in zip(arrivals, probs):
+            delay = a - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(srv.submit(p.A, p.b))
+        olat = [srv.wait(t, p.n)[2] for t, p in zip(tickets, probs)]
+        srv.close()
+        res[f"served_{prec}"] = {
+            "solves_per_s": rate, "max_active": st["max_active"], "failed": st["failed"],
+            "worst_true_relres": worst,
+            "saturated_latency_ms": {"p50": float(np.percentile(lat, 50)),
+                                     "p99": float(np.percentile(lat, 99))},
+            "open_loop_rate_hz": 0.6 * rate,
+            "open_loop_latency_ms": {"p50": float(np.percentile(olat, 50)),
+                                     "p99": float(np.percentile(olat, 99))}}
+    return res
 
 
 def comparisons(gs2, torch, pr, stream, b):

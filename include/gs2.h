@@ -221,6 +221,68 @@ gs2_status gs2_batch_solve(gs2_handle* const* hs, const double* const* bs,
  * restart cycle and return the status themselves. */
 gs2_status gs2_check(gs2_handle* h);
 
+/* ---- solve server: continuous batching of independent systems ---------- */
+
+/* A server owns one GPU (the device current at creation) and solves
+ * submitted systems A x = b with restarted GMRES and the configured
+ * preconditioner.  Requests are admitted in arrival order as soon as a slot
+ * is free and their estimated device footprint fits both the server's
+ * budget and the device's free memory; each admitted request gets its own
+ * stream, handle and resident Krylov state, so the work of requests that
+ * arrive while others are running overlaps on the GPU.  A result is the
+ * same, bit for bit, as the same solve run alone through gmres_solve. */
+typedef struct gs2_server gs2_server;
+
+typedef struct {
+  int64_t hbm_budget_bytes; /* device bytes the server may reserve for admitted
+                               requests; 0 = 90% of the free memory at creation */
+  int max_slots;            /* requests on the GPU at once, >= 1 */
+  int prep_threads;         /* host threads preparing admitted requests, >= 1 */
+  int restart;              /* GMRES restart, 1..64 */
+  double tol;               /* relative residual */
+  int max_iters;
+  int has_precond;          /* 0: no preconditioner */
+  gs2_params precond;
+  uint64_t fail_ticket;     /* fault-injection hook for tests: the request with
+                               this ticket fails its admission with GS2_ERR_OOM
+                               as if its allocation had failed (0 = none) */
+} gs2_server_cfg;
+
+typedef struct {
+  int64_t n, nnz;
+  const int64_t* rowptr; /* host CSR, copied by gs2_server_submit */
+  const int32_t* col;
+  const double* val;
+  const double* b;  /* host, copied */
+  const double* x0; /* host initial guess, copied; NULL = zero */
+} gs2_request;
+
+typedef struct {
+  int64_t submitted, admitted, completed, failed;
+  int64_t pending, active, max_active;
+  int64_t reserved_bytes, budget_bytes;
+} gs2_server_stats;
+
+gs2_status gs2_server_create(const gs2_server_cfg* cfg, gs2_server** out);
+/* Queue a request (inputs are copied); *ticket identifies it.  OOM if it can
+ * never fit the budget, INVALID_ARG for a malformed request. */
+gs2_status gs2_server_submit(gs2_server* s, const gs2_request* req, uint64_t* ticket);
+/* Non-blocking: BUSY while the request is queued or running, NOT_FOUND for an
+ * unknown or already collected ticket; otherwise the request's status, with
+ * its solve info, x (n doubles, may be NULL) and the submit-to-done latency
+ * in milliseconds (may be NULL).  A collected result is released. */
+gs2_status gs2_server_poll(gs2_server* s, uint64_t ticket, gs2_solve_info* info,
+                           double* x_out, double* latency_ms);
+/* Blocking form of poll: waits at most timeout_s seconds (TIMEOUT). */
+gs2_status gs2_server_wait(gs2_server* s, uint64_t ticket, double timeout_s,
+                           gs2_solve_info* info, double* x_out, double* latency_ms);
+gs2_status gs2_server_get_stats(gs2_server* s, gs2_server_stats* out);
+/* Device bytes the server reserves for a request of this size (the
+ * admission estimate). */
+int64_t gs2_server_footprint(const gs2_server_cfg* cfg, int64_t n, int64_t nnz);
+/* Finish running requests, drop queued ones, release everything. */
+void gs2_server_destroy(gs2_server* s);
+
 /* ---- per-kernel device timing (CUDA events on the handle's stream) ---- */
 
 typedef struct {

@@ -69,6 +69,26 @@ class _KStat(ctypes.Structure):
                 ("total_ms", ctypes.c_double), ("bytes", ctypes.c_double)]
 
 
+class _ServerCfg(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_slots", ctypes.c_int),
+                ("prep_threads", ctypes.c_int), ("restart", ctypes.c_int),
+                ("tol", ctypes.c_double), ("max_iters", ctypes.c_int),
+                ("has_precond", ctypes.c_int), ("precond", Params),
+                ("fail_ticket", ctypes.c_uint64)]
+
+
+class _Request(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("rowptr", ctypes.c_void_p),
+                ("col", ctypes.c_void_p), ("val", ctypes.c_void_p), ("b", ctypes.c_void_p),
+                ("x0", ctypes.c_void_p)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in
+                ("submitted", "admitted", "completed", "failed", "pending", "active",
+                 "max_active", "reserved_bytes", "budget_bytes")]
+
+
 @dataclass
 class SolveInfo:
     iters: int
@@ -123,6 +143,22 @@ def load(path: str | None = None):
     lib.gs2_last_error.restype = ctypes.c_char_p
     lib.gs2_version.restype = ctypes.c_char_p
     lib.gs2_launch_count.restype = ctypes.c_int64
+    lib.gs2_server_create.argtypes = [ctypes.POINTER(_ServerCfg), ctypes.POINTER(P)]
+    lib.gs2_server_create.restype = I
+    lib.gs2_server_submit.argtypes = [P, ctypes.POINTER(_Request), ctypes.POINTER(ctypes.c_uint64)]
+    lib.gs2_server_submit.restype = I
+    lib.gs2_server_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(_Info), P,
+                                    ctypes.POINTER(D)]
+    lib.gs2_server_poll.restype = I
+    lib.gs2_server_wait.argtypes = [P, ctypes.c_uint64, D, ctypes.POINTER(_Info), P,
+                                    ctypes.POINTER(D)]
+    lib.gs2_server_wait.restype = I
+    lib.gs2_server_get_stats.argtypes = [P, ctypes.POINTER(_ServerStats)]
+    lib.gs2_server_get_stats.restype = I
+    lib.gs2_server_footprint.argtypes = [ctypes.POINTER(_ServerCfg), I64, I64]
+    lib.gs2_server_footprint.restype = I64
+    lib.gs2_server_destroy.argtypes = [P]
+    lib.gs2_server_destroy.restype = None
     _lib = lib
     return lib
 
@@ -351,6 +387,83 @@ def gs2_batch_solve(handles, bs, xs, restart=30, tol=1e-8, max_iters=10000,
     if st not in _SOLVER_STATUSES:
         _err(st)
     return [SolveInfo(i.iters, i.cycles, i.status, i.true_relres) for i in infos]
+
+
+class Server:
+    """Continuous-batching solve server on the current CUDA device (see
+    gs2_server_* in include/gs2.h).  Matrices and vectors are host numpy."""
+
+    def __init__(self, restart=30, tol=1e-8, max_iters=10000, precond: Params | None = None,
+                 max_slots=4, prep_threads=2, hbm_budget_bytes=0, fail_ticket=0):
+        self._cfg = _ServerCfg(hbm_budget_bytes, max_slots, prep_threads, restart, tol,
+                               max_iters, 1 if precond is not None else 0,
+                               precond if precond is not None else Params(), fail_ticket)
+        out = ctypes.c_void_p()
+        _check(load().gs2_server_create(ctypes.byref(self._cfg), ctypes.byref(out)))
+        self._ptr = out.value
+
+    def footprint(self, n: int, nnz: int) -> int:
+        return int(load().gs2_server_footprint(ctypes.byref(self._cfg), n, nnz))
+
+    def submit(self, A, b, x0=None) -> int:
+        rp = np.ascontiguousarray(A[0], dtype=np.int64)
+        ci = np.ascontiguousarray(A[1], dtype=np.int32)
+        va = np.ascontiguousarray(A[2], dtype=np.float64)
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x0 = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64)
+        q = _Request(len(rp) - 1, int(rp[-1]), rp.ctypes.data, ci.ctypes.data, va.ctypes.data,
+                     b.ctypes.data, x0.ctypes.data if x0 is not None else None)
+        t = ctypes.c_uint64()
+        _check(load().gs2_server_submit(self._ptr, ctypes.byref(q), ctypes.byref(t)))
+        return int(t.value)
+
+    def _collect(self, fn, ticket, n, *extra):
+        info = _Info()
+        x = np.empty(n) if n else None
+        lat = ctypes.c_double()
+        st = fn(self._ptr, ticket, *extra, ctypes.byref(info),
+                x.ctypes.data if x is not None else None, ctypes.byref(lat))
+        return st, SolveInfo(info.iters, info.cycles, info.status, info.true_relres), x, lat.value
+
+    def poll(self, ticket: int, n: int = 0):
+        """None while busy, else (SolveInfo, x or None, latency_ms)."""
+        st, info, x, lat = self._collect(load().gs2_server_poll, ticket, n)
+        if st == 9:
+            return None
+        if st == 10:
+            _err(st)
+        return info, x, lat
+
+    def wait(self, ticket: int, n: int = 0, timeout: float = 600.0):
+        """Block until done: (SolveInfo, x or None, latency_ms)."""
+        st, info, x, lat = self._collect(load().gs2_server_wait, ticket, n,
+                                         ctypes.c_double(timeout))
+        if st in (8, 10):
+            _err(st)
+        return info, x, lat
+
+    def stats(self) -> dict:
+        s = _ServerStats()
+        _check(load().gs2_server_get_stats(self._ptr, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in _ServerStats._fields_}
+
+    def close(self):
+        if self._ptr:
+            load().gs2_server_destroy(self._ptr)
+            self._ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def server_footprint(n: int, nnz: int, restart: int = 30, precond: Params | None = None) -> int:
+    """Device bytes the server reserves for a request of this size."""
+    cfg = _ServerCfg(0, 1, 1, restart, 1e-8, 100, 1 if precond is not None else 0,
+                     precond if precond is not None else Params(), 0)
+    return int(load().gs2_server_footprint(ctypes.byref(cfg), n, nnz))
 
 
 def version() -> str:

@@ -159,14 +159,12 @@ static void upload_csr(gs2_handle* h, DevCsr& M, int n, const std::vector<int>& 
   M.rp = (int*)h->dalloc(sizeof(int) * (n + 1 + kPad));
   M.ci = (int*)h->dalloc(sizeof(int) * nz);
   M.va = (double*)h->dalloc(sizeof(double) * nz);
-  GS2_CUDA(cudaMemset(M.rp, 0, sizeof(int) * (n + 1 + kPad)));
-  GS2_CUDA(cudaMemcpy(M.rp, rp.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
-  GS2_CUDA(cudaMemset(M.ci, 0, sizeof(int) * nz));
-  GS2_CUDA(cudaMemset(M.va, 0, sizeof(double) * nz));
-  if (M.nnz) {
-    GS2_CUDA(cudaMemcpy(M.ci, ci.data(), sizeof(int) * M.nnz, cudaMemcpyHostToDevice));
-    GS2_CUDA(cudaMemcpy(M.va, va.data(), sizeof(double) * M.nnz, cudaMemcpyHostToDevice));
-  }
+  h->dzero(M.rp, sizeof(int) * (n + 1 + kPad));
+  h->h2d(M.rp, rp.data(), sizeof(int) * (n + 1));
+  h->dzero(M.ci, sizeof(int) * nz);
+  h->dzero(M.va, sizeof(double) * nz);
+  h->h2d(M.ci, ci.data(), sizeof(int) * M.nnz);
+  h->h2d(M.va, va.data(), sizeof(double) * M.nnz);
   std::vector<int> tiles;
   build_tiles(rp, n, M.tpr, tiles, M.cap);
   M.ntiles = (int)tiles.size() - 1;
@@ -178,7 +176,7 @@ static void upload_csr(gs2_handle* h, DevCsr& M, int n, const std::vector<int>& 
     desc[t] = make_int4(r0, r1, longrow ? -1 - a : (a & ~7), b);
   }
   M.desc = (int4*)h->dalloc(sizeof(int4) * desc.size());
-  GS2_CUDA(cudaMemcpy(M.desc, desc.data(), sizeof(int4) * desc.size(), cudaMemcpyHostToDevice));
+  h->h2d(M.desc, desc.data(), sizeof(int4) * desc.size());
 }
 
 // FP32 copy and FP16 copy with per-row scale s_i = max_j |v_ij| of a
@@ -195,7 +193,7 @@ static void prepare_lowprec(gs2_handle* h, DevCsr& M, const HostTri& T, int prec
     std::vector<float> v(nz, 0.f);
     for (int k = 0; k < M.nnz; ++k) v[k] = (float)T.va[k];
     M.va32 = (float*)h->dalloc(sizeof(float) * nz);
-    GS2_CUDA(cudaMemcpy(M.va32, v.data(), sizeof(float) * nz, cudaMemcpyHostToDevice));
+    h->h2d(M.va32, v.data(), sizeof(float) * nz);
   }
   if (prec == GS2_FP16_ROWSCALED && !M.va16) {
     std::vector<__half> v(nz, __float2half(0.f));
@@ -209,9 +207,8 @@ static void prepare_lowprec(gs2_handle* h, DevCsr& M, const HostTri& T, int prec
     }
     M.va16 = (__half*)h->dalloc(sizeof(__half) * nz);
     M.scale16 = (float*)h->dalloc(sizeof(float) * std::max(M.n, 1));
-    GS2_CUDA(cudaMemcpy(M.va16, v.data(), sizeof(__half) * nz, cudaMemcpyHostToDevice));
-    if (M.n)
-      GS2_CUDA(cudaMemcpy(M.scale16, s.data(), sizeof(float) * M.n, cudaMemcpyHostToDevice));
+    h->h2d(M.va16, v.data(), sizeof(__half) * nz);
+    h->h2d(M.scale16, s.data(), sizeof(float) * M.n);
   }
 }
 
@@ -227,17 +224,57 @@ static std::unordered_map<const gs2_handle*, gs2_host_side*> g_host;
 void* gs2_handle::dalloc(size_t bytes) {
   void* p = nullptr;
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMalloc(&p, bytes);
+  cudaError_t e = async_alloc ? cudaMallocAsync(&p, bytes, stream) : cudaMalloc(&p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     GS2_THROW(e == cudaErrorMemoryAllocation ? GS2_ERR_OOM : GS2_ERR_CUDA,
-              std::string("cudaMalloc(") + std::to_string(bytes) + "): " +
-                  cudaGetErrorString(e));
+              std::string("device allocation of ") + std::to_string(bytes) +
+                  " bytes: " + cudaGetErrorString(e));
   }
   allocs.push_back(p);
   dev_bytes += (int64_t)bytes;
   return p;
 }
+
+// setup copies are ordered on the handle's stream (pageable sources are
+// staged by the driver before the call returns)
+void gs2_handle::h2d(void* dst, const void* src, size_t bytes) {
+  if (bytes) GS2_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, stream));
+}
+
+void gs2_handle::dzero(void* dst, size_t bytes) {
+  if (bytes) GS2_CUDA(cudaMemsetAsync(dst, 0, bytes, stream));
+}
+
+namespace gs2 {
+
+static std::mutex g_pinned_mu;
+static std::unordered_map<size_t, std::vector<void*>> g_pinned_free;
+
+void* pinned_get(size_t bytes) {
+  {
+    std::lock_guard<std::mutex> g(g_pinned_mu);
+    auto& v = g_pinned_free[bytes];
+    if (!v.empty()) {
+      void* p = v.back();
+      v.pop_back();
+      std::memset(p, 0, bytes);
+      return p;
+    }
+  }
+  void* p = nullptr;
+  GS2_CUDA(cudaHostAlloc(&p, bytes, cudaHostAllocMapped | cudaHostAllocPortable));
+  std::memset(p, 0, bytes);
+  return p;
+}
+
+void pinned_put(void* p, size_t bytes) {
+  if (!p) return;
+  std::lock_guard<std::mutex> g(g_pinned_mu);
+  g_pinned_free[bytes].push_back(p);
+}
+
+}  // namespace gs2
 
 namespace gs2 {
 
@@ -284,8 +321,7 @@ void ensure_levels(gs2_handle* h) {
     std::vector<int> fill(ptr.begin(), ptr.end() - 1), rows(std::max(n, 1));
     for (int i = 0; i < n; ++i) rows[fill[lev[i]]++] = i;
     rows_dev = (int*)h->dalloc(sizeof(int) * std::max(n, 1));
-    GS2_CUDA(cudaMemcpy(rows_dev, rows.data(), sizeof(int) * std::max(n, 1),
-                        cudaMemcpyHostToDevice));
+    h->h2d(rows_dev, rows.data(), sizeof(int) * std::max(n, 1));
   };
   build(hs->L, true, h->lev_ptr_L, h->lev_rows_L);
   build(hs->U, false, h->lev_ptr_U, h->lev_rows_U);
@@ -376,17 +412,23 @@ using namespace gs2;
     return GS2_ERR_CUDA;                               \
   }
 
-static void destroy_impl(gs2_handle* h) {
+// Release a handle.  Stream-ordered handles free their device memory on
+// their own stream (no device-wide synchronisation); the small pinned
+// mirrors go back to the process-wide pool.
+void gs2::destroy_handle(gs2_handle* h) {
   if (!h) return;
   int cur = 0;
   cudaGetDevice(&cur);
   cudaSetDevice(h->device);
   if (h->stream) cudaStreamSynchronize(h->stream);
   delete h->prof;
-  for (void* p : h->allocs) cudaFree(p);
-  if (h->st_host) cudaFreeHost(h->st_host);
-  if (h->err_host) cudaFreeHost(h->err_host);
-  if (h->stop_mapped) cudaFreeHost((void*)h->stop_mapped);
+  for (void* p : h->allocs) {
+    if (h->async_alloc) cudaFreeAsync(p, h->stream);
+    else cudaFree(p);
+  }
+  pinned_put(h->st_host, sizeof(KrylovState));
+  pinned_put(h->err_host, sizeof(int));
+  pinned_put((void*)h->stop_mapped, sizeof(int));
   {
     std::lock_guard<std::mutex> g(g_host_mu);
     auto it = g_host.find(h);
@@ -398,6 +440,8 @@ static void destroy_impl(gs2_handle* h) {
   delete h;
   cudaSetDevice(cur);
 }
+
+static void destroy_impl(gs2_handle* h) { gs2::destroy_handle(h); }
 
 extern "C" {
 
@@ -415,8 +459,22 @@ gs2_status gs2_setup(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_
     return GS2_ERR_INVALID_ARG;
   }
   *out = nullptr;
-  gs2_handle* h = nullptr;
   API_BEGIN
+  *out = setup_handle(n, nnz, rowptr, col, val, on_device, precisions, (cudaStream_t)stream,
+                      false);
+  return GS2_OK;
+  API_END
+}
+
+}  // extern "C"
+
+// Validate A, split it, upload everything and allocate the resident
+// temporaries.  Throws gs2::Error; a partly built handle is released.
+gs2_handle* gs2::setup_handle(int64_t n, int64_t nnz, const int64_t* rowptr,
+                              const int32_t* col, const double* val, int on_device,
+                              unsigned precisions, cudaStream_t stream, bool async_alloc) {
+  gs2_handle* h = nullptr;
+  try {
   if (n < 0 || nnz < 0) GS2_THROW(GS2_ERR_INVALID_ARG, "negative size");
   if (n > std::numeric_limits<int>::max() - 1 || nnz > std::numeric_limits<int>::max() - 64)
     GS2_THROW(GS2_ERR_INVALID_ARG, "n or nnz above 2^31 - 1");
@@ -493,7 +551,8 @@ gs2_status gs2_setup(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_
   }
   GS2_CUDA(cudaGetDevice(&h->device));
   GS2_CUDA(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device));
-  h->stream = (cudaStream_t)stream;
+  h->stream = stream;
+  h->async_alloc = async_alloc;
   h->n = n;
   h->nnz = nnz;
   upload_csr(h, h->A, (int)n, rp32, std::vector<int>(ci.begin(), ci.end()), va);
@@ -504,8 +563,8 @@ gs2_status gs2_setup(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_
   const size_t nv = (size_t)std::max<int64_t>(n, 1);
   h->dinv = (double*)h->dalloc(sizeof(double) * nv);
   h->dev_err = (int*)h->dalloc(sizeof(int));
-  GS2_CUDA(cudaMemset(h->dev_err, 0, sizeof(int)));
-  if (n) GS2_CUDA(cudaMemcpy(h->dinv, dinv.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+  h->dzero(h->dev_err, sizeof(int));
+  h->h2d(h->dinv, dinv.data(), sizeof(double) * n);
   h->r = (double*)h->dalloc(sizeof(double) * nv);
   h->rhat = (double*)h->dalloc(sizeof(double) * nv);
   h->g0 = (double*)h->dalloc(sizeof(double) * nv);
@@ -524,26 +583,15 @@ gs2_status gs2_setup(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_
   h->part = (double*)h->dalloc(sizeof(double) * h->part_cap);
   for (int p = 1; p <= 2; ++p)
     if (precisions & (1u << p)) ensure_precision(h, p);
-  GS2_CUDA(cudaDeviceSynchronize());
-  *out = h;
-  return GS2_OK;
-  }
-  catch (const gs2::Error& e) {
-    gs2::set_error(e.msg);
-    destroy_impl(h);
-    return e.st;
-  }
-  catch (const std::bad_alloc&) {
-    gs2::set_error("host allocation failed");
-    destroy_impl(h);
-    return GS2_ERR_OOM;
-  }
-  catch (...) {
-    gs2::set_error("unexpected C++ exception");
-    destroy_impl(h);
-    return GS2_ERR_CUDA;
+  GS2_CUDA(cudaStreamSynchronize(h->stream));
+  return h;
+  } catch (...) {
+    destroy_handle(h);
+    throw;
   }
 }
+
+extern "C" {
 
 void gs2_destroy(gs2_handle* h) { destroy_impl(h); }
 

@@ -127,7 +127,14 @@ struct gs2_handle {
 
   gs2::Profiler* prof = nullptr;
 
+  // stream-ordered allocation (cudaMallocAsync / cudaFreeAsync on `stream`):
+  // used by server-owned handles so that freeing one request's memory never
+  // synchronises the device under the other requests
+  bool async_alloc = false;
+
   void* dalloc(size_t bytes);
+  void h2d(void* dst, const void* src, size_t bytes);
+  void dzero(void* dst, size_t bytes);
 };
 
 namespace gs2 {
@@ -214,6 +221,27 @@ gs2_status gmres_batch(gs2_handle* const* hs, const double* const* bs,
                        double* const* xs, int count, int m, double tol,
                        int max_iters, const gs2_params* p, gs2_solve_info* infos);
 void read_state(gs2_handle* h);
+
+// A GMRES solve as a resumable job (used by the server): start enqueues
+// the first work on the handle's stream; advance must be called only once
+// that stream is idle and returns true when the solve has finished.
+struct GmresJob;
+GmresJob* gmres_job_start(gs2_handle* h, const double* b, double* x, int m, double tol,
+                          int max_iters, const gs2_params* p);
+bool gmres_job_advance(GmresJob* j);
+gs2_solve_info gmres_job_info(const GmresJob* j);
+void gmres_job_free(GmresJob* j);
+
+// handle creation / destruction shared by gs2_setup and the server
+gs2_handle* setup_handle(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col,
+                         const double* val, int on_device, unsigned precisions,
+                         cudaStream_t stream, bool async_alloc);
+void destroy_handle(gs2_handle* h);
+
+// small pinned, device-mapped host buffers, recycled process-wide (freeing
+// pinned memory synchronises the device)
+void* pinned_get(size_t bytes);
+void pinned_put(void* p, size_t bytes);
 
 // geometry helpers
 int vec_blocks(gs2_handle* h, int64_t n);

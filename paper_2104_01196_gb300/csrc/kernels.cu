@@ -344,7 +344,10 @@ struct EpiJr {
 
 // inner JR sweep on the prescaled triangle T = D^{-1} L or D^{-1} U:
 //   g' = (1-gamma) g + gamma (rhat - omega T g)
-template <typename GT, typename AT>
+// DAMPED and SCALED (FP16 triangles with a per-row scale) are compile-time:
+// a runtime flag on a uniform kernel argument is predicated, and its FP64
+// instructions would then issue on every row.
+template <typename GT, typename AT, bool DAMPED, bool SCALED>
 struct EpiInner {
   const GT* __restrict__ g_in;
   const GT* __restrict__ rhat;
@@ -354,7 +357,6 @@ struct EpiInner {
   AT omega, gamma;
   double omega64;
   int mode;
-  int damped;
   struct Pre {
     AT rh, gi, sc;
     double xi;
@@ -362,16 +364,16 @@ struct EpiInner {
   __device__ Pre pre(int i) const {
     Pre p;
     p.rh = (AT)rhat[i];
-    p.gi = damped ? (AT)g_in[i] : AT(0);
-    p.sc = rowscale ? (AT)rowscale[i] : AT(1);
+    p.gi = DAMPED ? (AT)g_in[i] : AT(0);
+    p.sc = SCALED ? (AT)rowscale[i] : AT(1);
     p.xi = mode == INNER_LAST_ADD ? x[i] : 0.0;
     return p;
   }
   __device__ AT gather(int c) const { return (AT)__ldg(g_in + c); }
   __device__ void finish(int i, AT s, const Pre& p) const {
-    if (rowscale) s *= p.sc;
+    if (SCALED) s *= p.sc;
     AT go = p.rh - omega * s;
-    if (damped) go = (AT(1) - gamma) * p.gi + gamma * go;
+    if (DAMPED) go = (AT(1) - gamma) * p.gi + gamma * go;
     if (mode == INNER_MID) g_out[i] = (GT)go;
     else if (mode == INNER_LAST_ADD) x[i] = p.xi + omega64 * (double)go;
     else x[i] = omega64 * (double)go;
@@ -485,17 +487,41 @@ void launch_inner(gs2_handle* h, const DevCsr& T, int prec, const void* rhat,
   KernelTimer tm(h, prec == GS2_FP64 ? "inner64" : (prec == GS2_FP32 ? "inner32" : "inner16"),
                  bytes);
   if (prec == GS2_FP64) {
-    EpiInner<double, double> e{(const double*)g_in, (const double*)rhat, (double*)g_out, x,
-                               nullptr, omega, gamma, omega, mode, damped};
-    dispatch<double>(h, T, T.va, e, skip);
+    if (damped) {
+      EpiInner<double, double, true, false> e{(const double*)g_in, (const double*)rhat,
+                                              (double*)g_out, x, nullptr, omega, gamma, omega,
+                                              mode};
+      dispatch<double>(h, T, T.va, e, skip);
+    } else {
+      EpiInner<double, double, false, false> e{(const double*)g_in, (const double*)rhat,
+                                               (double*)g_out, x, nullptr, omega, gamma, omega,
+                                               mode};
+      dispatch<double>(h, T, T.va, e, skip);
+    }
   } else if (prec == GS2_FP32) {
-    EpiInner<float, float> e{(const float*)g_in, (const float*)rhat, (float*)g_out, x,
-                             nullptr, (float)omega, (float)gamma, omega, mode, damped};
-    dispatch<float>(h, T, T.va32, e, skip);
+    if (damped) {
+      EpiInner<float, float, true, false> e{(const float*)g_in, (const float*)rhat,
+                                            (float*)g_out, x, nullptr, (float)omega,
+                                            (float)gamma, omega, mode};
+      dispatch<float>(h, T, T.va32, e, skip);
+    } else {
+      EpiInner<float, float, false, false> e{(const float*)g_in, (const float*)rhat,
+                                             (float*)g_out, x, nullptr, (float)omega,
+                                             (float)gamma, omega, mode};
+      dispatch<float>(h, T, T.va32, e, skip);
+    }
   } else {
-    EpiInner<float, float> e{(const float*)g_in, (const float*)rhat, (float*)g_out, x,
-                             T.scale16, (float)omega, (float)gamma, omega, mode, damped};
-    dispatch<__half>(h, T, T.va16, e, skip);
+    if (damped) {
+      EpiInner<float, float, true, true> e{(const float*)g_in, (const float*)rhat,
+                                           (float*)g_out, x, T.scale16, (float)omega,
+                                           (float)gamma, omega, mode};
+      dispatch<__half>(h, T, T.va16, e, skip);
+    } else {
+      EpiInner<float, float, false, true> e{(const float*)g_in, (const float*)rhat,
+                                            (float*)g_out, x, T.scale16, (float)omega,
+                                            (float)gamma, omega, mode};
+      dispatch<__half>(h, T, T.va16, e, skip);
+    }
   }
 }
 

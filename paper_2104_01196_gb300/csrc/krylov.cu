@@ -438,13 +438,10 @@ __global__ void k_cycle_reset(KrylovState* st) {
 void ensure_krylov(gs2_handle* h, int m) {
   if (!h->st) {
     h->st = (KrylovState*)h->dalloc(sizeof(KrylovState));
-    GS2_CUDA(cudaMemset(h->st, 0, sizeof(KrylovState)));
-    GS2_CUDA(cudaHostAlloc((void**)&h->st_host, sizeof(KrylovState), cudaHostAllocDefault));
-    GS2_CUDA(cudaHostAlloc((void**)&h->err_host, sizeof(int), cudaHostAllocDefault));
-    *h->err_host = 0;
-    int* f = nullptr;
-    GS2_CUDA(cudaHostAlloc((void**)&f, sizeof(int), cudaHostAllocMapped));
-    *f = 0;
+    h->dzero(h->st, sizeof(KrylovState));
+    h->st_host = (KrylovState*)pinned_get(sizeof(KrylovState));
+    h->err_host = (int*)pinned_get(sizeof(int));
+    int* f = (int*)pinned_get(sizeof(int));
     h->stop_mapped = f;
     GS2_CUDA(cudaHostGetDevicePointer((void**)&h->stop_mapped_dev, f, 0));
     const size_t n = std::max<int64_t>(h->n, 1);
@@ -738,6 +735,43 @@ gs2_status gmres_run(gs2_handle* h, const double* b, double* x, int m, double to
   if (info) *info = g.loc;
   return g.st;
 }
+
+// Resumable job: owns a copy of the preconditioner parameters so that the
+// caller's struct need not outlive the call that started it.
+struct GmresJob {
+  gs2_params params{};
+  bool has_params = false;
+  GmresRun run;
+};
+
+GmresJob* gmres_job_start(gs2_handle* h, const double* b, double* x, int m, double tol,
+                          int max_iters, const gs2_params* p) {
+  GmresJob* j = new GmresJob();
+  if (p) {
+    j->params = *p;
+    j->has_params = true;
+  }
+  try {
+    j->run.start(h, b, x, m, tol, max_iters, j->has_params ? &j->params : nullptr);
+  } catch (...) {
+    delete j;
+    throw;
+  }
+  return j;
+}
+
+bool gmres_job_advance(GmresJob* j) {
+  if (!j->run.done) j->run.advance();
+  return j->run.done;
+}
+
+gs2_solve_info gmres_job_info(const GmresJob* j) {
+  gs2_solve_info i = j->run.loc;
+  i.status = j->run.st;
+  return i;
+}
+
+void gmres_job_free(GmresJob* j) { delete j; }
 
 gs2_status gmres_batch(gs2_handle* const* hs, const double* const* bs, double* const* xs,
                        int count, int m, double tol, int max_iters, const gs2_params* p,

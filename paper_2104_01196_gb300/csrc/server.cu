@@ -1,0 +1,411 @@
+// Solve server: continuous batching of independent systems on one GPU.
+//
+// Requests are queued on submission and admitted in arrival order as soon as
+// a slot is free and their estimated device footprint fits the server's
+// budget (by default 90% of the device memory free when the server starts).
+// A preparation thread builds an admitted request's handle on a stream of
+// its own, with stream-ordered allocations, and starts its GMRES job; the
+// progress thread then polls every running job's stream and advances the
+// job by one restart cycle whenever that stream is idle.  Requests that
+// arrive while others run are therefore admitted as slots and memory free
+// up, and their kernels overlap on the GPU.  Every request runs the same
+// kernels with the same launch geometry as a lone gmres_solve, so its
+// result is bitwise the same alone and in the mix.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace gs2 {
+
+using Clock = std::chrono::steady_clock;
+
+enum ReqState { REQ_PENDING = 0, REQ_PREPARING = 1, REQ_ACTIVE = 2, REQ_DONE = 3 };
+
+struct Request {
+  uint64_t ticket = 0;
+  int state = REQ_PENDING;
+  int64_t n = 0, nnz = 0;
+  std::vector<int64_t> rp;
+  std::vector<int32_t> ci;
+  std::vector<double> va, b, x0;
+  int64_t footprint = 0;
+  Clock::time_point t_submit, t_done;
+  cudaStream_t stream = nullptr;
+  gs2_handle* h = nullptr;
+  GmresJob* job = nullptr;
+  gs2_solve_info info{0, 0, GS2_OK, 0.0};
+  gs2_status status = GS2_OK;
+  std::vector<double> x;
+};
+
+// Device bytes a request of this size holds once admitted: the matrix, its
+// two prescaled triangles, the resident vectors, the Krylov basis and the
+// optional lower-precision and level-set storage (mirrors setup_handle,
+// ensure_precision, ensure_levels and ensure_krylov).
+static int64_t footprint(const gs2_server_cfg& c, int64_t n, int64_t nnz) {
+  const int64_t off = std::max<int64_t>(nnz - n, 0);
+  const int64_t m = std::max(c.restart, 1);
+  int64_t b = 12 * nnz + 12 * off + 3 * 4 * (n + 17) + 3 * (n / 16 + 16) * 16;
+  b += 8 * n * 9;                     // D^{-1} and eight resident temporaries
+  b += 8 * (int64_t)8 * 152 * 66;     // per-block partial sums (upper bound)
+  b += 8 * n * (m + 1) + 3 * 8 * n;   // Krylov basis, w, p, q
+  b += 8 * (m + 1) * (m + 6);         // Hessenberg, rotations, y
+  if (c.has_precond && c.precond.kind == GS2_PC_GS2) {
+    if (c.precond.precision == GS2_FP32) b += 4 * off + 12 * n;
+    if (c.precond.precision == GS2_FP16_ROWSCALED) b += 2 * off + 8 * n + 12 * n;
+  }
+  if (c.has_precond && c.precond.kind == GS2_PC_GS) b += 8 * n;
+  return b + (1 << 20);
+}
+
+}  // namespace gs2
+
+struct gs2_server {
+  gs2_server_cfg cfg{};
+  int device = 0;
+  int64_t budget = 0;
+  std::mutex mu;
+  std::condition_variable cv_prep;  // preparation threads wait for admissible work
+  std::condition_variable cv_done;  // gs2_server_wait callers
+  std::condition_variable cv_loop;  // the progress thread, when idle
+  std::deque<gs2::Request*> pending;
+  std::vector<gs2::Request*> active;
+  std::unordered_map<uint64_t, gs2::Request*> table;
+  uint64_t next_ticket = 1;
+  int64_t reserved = 0;
+  int64_t slots_used = 0;  // preparing + active
+  int64_t submitted = 0, admitted = 0, completed = 0, failed = 0, max_active = 0;
+  bool stopping = false;
+  std::vector<std::thread> prep;
+  std::thread loop;
+};
+
+using namespace gs2;
+
+static bool admissible(gs2_server* s) {
+  if (s->pending.empty() || s->slots_used >= s->cfg.max_slots) return false;
+  return s->reserved + s->pending.front()->footprint <= s->budget;
+}
+
+// Called with the lock held: release the request's reservation, record its
+// end and wake everybody who may be waiting on it or on free capacity.
+static void retire_locked(gs2_server* s, Request* r, bool ok) {
+  r->state = REQ_DONE;
+  r->t_done = Clock::now();
+  s->reserved -= r->footprint;
+  s->slots_used -= 1;
+  if (ok) s->completed += 1;
+  else s->failed += 1;
+  s->cv_done.notify_all();
+  s->cv_prep.notify_all();
+}
+
+// Release the device resources of a request (its stream-ordered memory is
+// freed on its own stream; the stream goes once its work has drained).
+static void release_device(Request* r) {
+  if (r->job) gmres_job_free(r->job);
+  r->job = nullptr;
+  if (r->h) destroy_handle(r->h);
+  r->h = nullptr;
+  if (r->stream) cudaStreamDestroy(r->stream);
+  r->stream = nullptr;
+}
+
+// Build the handle and start the GMRES job of an admitted request.
+static void prepare(gs2_server* s, Request* r) {
+  gs2_status st = GS2_OK;
+  try {
+    if (s->cfg.fail_ticket && r->ticket == s->cfg.fail_ticket)
+      GS2_THROW(GS2_ERR_OOM, "injected allocation failure");
+    GS2_CUDA(cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking));
+    unsigned prec = 0;
+    const gs2_params* pc = s->cfg.has_precond ? &s->cfg.precond : nullptr;
+    if (pc && pc->kind == GS2_PC_GS2) prec = 1u << pc->precision;
+    r->h = setup_handle(r->n, r->nnz, r->rp.data(), r->ci.data(), r->va.data(), 0, prec,
+                        r->stream, true);
+    if (pc && pc->kind == GS2_PC_GS) ensure_levels(r->h);
+    r->h->h2d(r->h->bstage, r->b.data(), sizeof(double) * r->n);
+    if (r->x0.empty()) r->h->dzero(r->h->xstage, sizeof(double) * r->n);
+    else r->h->h2d(r->h->xstage, r->x0.data(), sizeof(double) * r->n);
+    r->job = gmres_job_start(r->h, r->h->bstage, r->h->xstage, s->cfg.restart, s->cfg.tol,
+                             s->cfg.max_iters, pc);
+  } catch (const Error& e) {
+    st = e.st;
+  } catch (const std::bad_alloc&) {
+    st = GS2_ERR_OOM;
+  } catch (...) {
+    st = GS2_ERR_CUDA;
+  }
+  // the host copies of the matrix are no longer needed
+  std::vector<int64_t>().swap(r->rp);
+  std::vector<int32_t>().swap(r->ci);
+  std::vector<double>().swap(r->va);
+  std::lock_guard<std::mutex> g(s->mu);
+  if (st != GS2_OK) {
+    release_device(r);
+    r->status = st;
+    r->info.status = st;
+    retire_locked(s, r, false);
+    return;
+  }
+  r->state = REQ_ACTIVE;
+  s->active.push_back(r);
+  s->cv_loop.notify_one();
+}
+
+static void prep_thread(gs2_server* s) {
+  cudaSetDevice(s->device);
+  for (;;) {
+    Request* r = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->cv_prep.wait(lk, [&] { return s->stopping || admissible(s); });
+      if (s->stopping) return;
+      r = s->pending.front();
+      s->pending.pop_front();
+      r->state = REQ_PREPARING;
+      s->reserved += r->footprint;
+      s->slots_used += 1;
+      s->admitted += 1;
+      s->max_active = std::max(s->max_active, s->slots_used);
+    }
+    prepare(s, r);
+  }
+}
+
+// Copy the solution back and retire a finished request.
+static void finish(gs2_server* s, Request* r, gs2_status err) {
+  bool ok = err == GS2_OK;
+  if (ok) {
+    r->info = gmres_job_info(r->job);
+    r->status = (gs2_status)r->info.status;
+    r->x.resize(r->n);
+    if (r->n &&
+        cudaMemcpyAsync(r->x.data(), r->h->xstage, sizeof(double) * r->n,
+                        cudaMemcpyDeviceToHost, r->stream) != cudaSuccess) {
+      cudaGetLastError();
+      r->status = GS2_ERR_CUDA;
+    }
+    cudaStreamSynchronize(r->stream);
+  } else {
+    r->status = err;
+    r->info.status = err;
+  }
+  release_device(r);
+  std::lock_guard<std::mutex> g(s->mu);
+  s->active.erase(std::find(s->active.begin(), s->active.end(), r));
+  retire_locked(s, r, ok && r->status == GS2_OK);
+}
+
+static void progress_thread(gs2_server* s) {
+  cudaSetDevice(s->device);
+  std::vector<Request*> snap;
+  for (;;) {
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      if (s->active.empty()) {
+        if (s->stopping && s->slots_used == 0) return;
+        s->cv_loop.wait_for(lk, std::chrono::milliseconds(2));
+        continue;
+      }
+      snap = s->active;
+    }
+    bool progressed = false;
+    for (Request* r : snap) {
+      const cudaError_t q = cudaStreamQuery(r->stream);
+      if (q == cudaErrorNotReady) continue;
+      progressed = true;
+      if (q != cudaSuccess) {
+        cudaGetLastError();
+        finish(s, r, GS2_ERR_CUDA);
+        continue;
+      }
+      gs2_status err = GS2_OK;
+      bool done = false;
+      try {
+        done = gmres_job_advance(r->job);
+      } catch (const Error& e) {
+        err = e.st;
+        done = true;
+      } catch (...) {
+        err = GS2_ERR_CUDA;
+        done = true;
+      }
+      if (done) finish(s, r, err);
+    }
+    if (!progressed) std::this_thread::yield();
+  }
+}
+
+static gs2_status collect_locked(gs2_server* s, Request* r, gs2_solve_info* info, double* x_out,
+                                 double* latency_ms) {
+  if (info) *info = r->info;
+  if (x_out && !r->x.empty()) std::memcpy(x_out, r->x.data(), sizeof(double) * r->x.size());
+  if (latency_ms)
+    *latency_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+  const gs2_status st = r->status;
+  s->table.erase(r->ticket);
+  delete r;
+  return st;
+}
+
+extern "C" {
+
+int64_t gs2_server_footprint(const gs2_server_cfg* cfg, int64_t n, int64_t nnz) {
+  if (!cfg || n < 0 || nnz < 0) return -1;
+  return footprint(*cfg, n, nnz);
+}
+
+gs2_status gs2_server_create(const gs2_server_cfg* cfg, gs2_server** out) {
+  if (!cfg || !out) return GS2_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (cfg->max_slots < 1 || cfg->restart < 1 || cfg->restart > kMaxRestart ||
+      !(cfg->tol >= 0.0) || cfg->max_iters < 0 || cfg->hbm_budget_bytes < 0) {
+    set_error("bad server configuration");
+    return GS2_ERR_INVALID_ARG;
+  }
+  if (cfg->has_precond) {
+    const gs2_params& p = cfg->precond;
+    if (p.kind < GS2_PC_NONE || p.kind > GS2_PC_GS || p.outer < 1 || p.inner < 0 ||
+        !(p.omega > 0.0) || !(p.gamma > 0.0) || p.direction < 0 || p.direction > 2 ||
+        p.precision < 0 || p.precision > 2) {
+      set_error("bad preconditioner parameters");
+      return GS2_ERR_INVALID_ARG;
+    }
+  }
+  auto* s = new gs2_server();
+  s->cfg = *cfg;
+  if (s->cfg.prep_threads < 1) s->cfg.prep_threads = 1;
+  if (cudaGetDevice(&s->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete s;
+    set_error("no CUDA device");
+    return GS2_ERR_CUDA;
+  }
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    cudaGetLastError();
+    delete s;
+    set_error("cudaMemGetInfo failed");
+    return GS2_ERR_CUDA;
+  }
+  s->budget = cfg->hbm_budget_bytes > 0 ? cfg->hbm_budget_bytes : (int64_t)(0.9 * (double)fr);
+  for (int i = 0; i < s->cfg.prep_threads; ++i) s->prep.emplace_back(prep_thread, s);
+  s->loop = std::thread(progress_thread, s);
+  *out = s;
+  return GS2_OK;
+}
+
+gs2_status gs2_server_submit(gs2_server* s, const gs2_request* q, uint64_t* ticket) {
+  if (!s || !q || !ticket || q->n < 0 || q->nnz < 0 || !q->rowptr || !q->b ||
+      (q->nnz > 0 && (!q->col || !q->val))) {
+    set_error("bad request");
+    return GS2_ERR_INVALID_ARG;
+  }
+  if (q->rowptr[0] != 0 || q->rowptr[q->n] != q->nnz) {
+    set_error("rowptr[0] must be 0 and rowptr[n] must be nnz");
+    return GS2_ERR_INVALID_ARG;
+  }
+  const int64_t fp = footprint(s->cfg, q->n, q->nnz);
+  if (fp > s->budget) {
+    set_error("request needs " + std::to_string(fp) + " device bytes, budget is " +
+              std::to_string(s->budget));
+    return GS2_ERR_OOM;
+  }
+  auto* r = new Request();
+  try {
+    r->n = q->n;
+    r->nnz = q->nnz;
+    r->rp.assign(q->rowptr, q->rowptr + q->n + 1);
+    r->ci.assign(q->col, q->col + q->nnz);
+    r->va.assign(q->val, q->val + q->nnz);
+    r->b.assign(q->b, q->b + q->n);
+    if (q->x0) r->x0.assign(q->x0, q->x0 + q->n);
+  } catch (const std::bad_alloc&) {
+    delete r;
+    set_error("host allocation failed");
+    return GS2_ERR_OOM;
+  }
+  r->footprint = fp;
+  r->t_submit = Clock::now();
+  std::lock_guard<std::mutex> g(s->mu);
+  if (s->stopping) {
+    delete r;
+    return GS2_ERR_BUSY;
+  }
+  r->ticket = s->next_ticket++;
+  s->table[r->ticket] = r;
+  s->pending.push_back(r);
+  s->submitted += 1;
+  *ticket = r->ticket;
+  s->cv_prep.notify_one();
+  return GS2_OK;
+}
+
+gs2_status gs2_server_poll(gs2_server* s, uint64_t ticket, gs2_solve_info* info, double* x_out,
+                           double* latency_ms) {
+  if (!s) return GS2_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> g(s->mu);
+  auto it = s->table.find(ticket);
+  if (it == s->table.end()) return GS2_ERR_NOT_FOUND;
+  if (it->second->state != REQ_DONE) return GS2_ERR_BUSY;
+  return collect_locked(s, it->second, info, x_out, latency_ms);
+}
+
+gs2_status gs2_server_wait(gs2_server* s, uint64_t ticket, double timeout_s, gs2_solve_info* info,
+                           double* x_out, double* latency_ms) {
+  if (!s) return GS2_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->table.find(ticket);
+  if (it == s->table.end()) return GS2_ERR_NOT_FOUND;
+  Request* r = it->second;
+  const auto deadline = Clock::now() + std::chrono::duration<double>(std::max(timeout_s, 0.0));
+  if (!s->cv_done.wait_until(lk, deadline, [&] { return r->state == REQ_DONE; }))
+    return GS2_ERR_TIMEOUT;
+  return collect_locked(s, r, info, x_out, latency_ms);
+}
+
+gs2_status gs2_server_get_stats(gs2_server* s, gs2_server_stats* out) {
+  if (!s || !out) return GS2_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> g(s->mu);
+  out->submitted = s->submitted;
+  out->admitted = s->admitted;
+  out->completed = s->completed;
+  out->failed = s->failed;
+  out->pending = (int64_t)s->pending.size();
+  out->active = s->slots_used;
+  out->max_active = s->max_active;
+  out->reserved_bytes = s->reserved;
+  out->budget_bytes = s->budget;
+  return GS2_OK;
+}
+
+void gs2_server_destroy(gs2_server* s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> g(s->mu);
+    s->stopping = true;
+    for (Request* r : s->pending) {
+      s->table.erase(r->ticket);
+      delete r;
+    }
+    s->pending.clear();
+    s->cv_prep.notify_all();
+    s->cv_loop.notify_all();
+  }
+  for (auto& t : s->prep) t.join();
+  s->loop.join();
+  for (auto& kv : s->table) delete kv.second;
+  delete s;
+}
+
+}  // extern "C"

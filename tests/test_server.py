@@ -1,0 +1,135 @@
+"""The solve server: continuous batching of independent systems.
+
+GPU tests check that every result is the same, bit for bit, alone and in the
+mix; that admission follows the memory budget; and that a failure injected
+on the host (a request whose allocation "fails") is reported for that
+request while the others complete.  The CPU test checks the admission
+estimate, which needs no GPU.
+"""
+import numpy as np
+import pytest
+
+import paper_2104_01196_gb300 as gs2
+from paper_2104_01196_gb300 import build as B
+from paper_2104_01196_gb300 import problems as P
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return gs2.load()
+
+
+def test_footprint_covers_matrix_triangles_and_basis(lib):
+    n, nnz = 100_000, 700_000
+    fp = gs2.server_footprint(n, nnz, restart=30)
+    # A (12 B/entry), the two prescaled triangles, the 31-vector basis
+    assert fp >= 12 * nnz + 12 * (nnz - n) + 8 * n * 31
+    assert fp < 2 * (24 * nnz + 8 * n * 60)
+    assert gs2.server_footprint(2 * n, 2 * nnz) > fp
+    assert gs2.server_footprint(n, nnz, restart=60) > fp
+    lowp = gs2.server_footprint(n, nnz, precond=gs2.params("gs2", precision="fp32"))
+    assert lowp > gs2.server_footprint(n, nnz, precond=gs2.params("gs2"))
+
+
+def _mix():
+    reqs = [P.variable_coefficient_problem("poisson2d", 30, 11),
+            P.variable_coefficient_problem("poisson3d", 14, 12),
+            P.variable_coefficient_problem("convdiff3d", 12, 13),
+            P.poisson2d(50),
+            P.variable_coefficient_problem("poisson3d", 22, 14),
+            P.random_system(3000, 15, dominance=1.1),
+            P.variable_coefficient_problem("convdiff3d", 18, 16),
+            P.poisson3d(16)]
+    return reqs
+
+
+def _alone(pr, pc):
+    import torch
+    h = gs2.gs2_setup(pr.A)
+    x = torch.zeros(pr.n, dtype=torch.float64, device="cuda")
+    b = torch.from_numpy(pr.b).cuda()
+    info = gs2.gmres_solve(h, b, x, 30, 1e-8, 4000, pc)
+    torch.cuda.synchronize()
+    out = x.cpu().numpy()
+    h.close()
+    return info, out
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_results_equal_alone_and_in_the_mix(lib, prec):
+    pc = gs2.params("gs2", 1, 1, direction="symmetric", precision=prec)
+    probs = _mix()
+    srv = gs2.Server(restart=30, tol=1e-8, max_iters=4000, precond=pc, max_slots=3,
+                     prep_threads=2)
+    tickets = [srv.submit(p.A, p.b) for p in probs]
+    got = [srv.wait(t, p.n) for t, p in zip(tickets, probs)]
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(probs) and st["failed"] == 0
+    assert 1 < st["max_active"] <= 3
+    for p, (info, x, lat) in zip(probs, got):
+        ainfo, ax = _alone(p, pc)
+        assert info.status == 0 and info.true_relres <= 1e-8
+        assert info.iters == ainfo.iters
+        assert np.array_equal(x, ax), p.name
+        assert lat > 0.0
+
+
+@pytest.mark.gpu
+def test_admission_follows_the_memory_budget(lib):
+    probs = [P.poisson3d(20) for _ in range(6)]
+    pc = gs2.params("gs2", 1, 1, direction="symmetric")
+    probe = gs2.Server(precond=pc, max_slots=8)
+    fp = probe.footprint(probs[0].n, probs[0].nnz)
+    probe.close()
+    # room for two requests at a time, although eight slots are free
+    srv = gs2.Server(precond=pc, max_slots=8, hbm_budget_bytes=int(2.5 * fp))
+    tickets = [srv.submit(p.A, p.b) for p in probs]
+    for t, p in zip(tickets, probs):
+        info, x, _ = srv.wait(t, p.n)
+        assert info.status == 0
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == 6 and st["max_active"] <= 2
+    assert st["reserved_bytes"] == 0
+    # a request that can never fit is refused at submission
+    small = gs2.Server(precond=pc, hbm_budget_bytes=fp // 2)
+    with pytest.raises(gs2.GS2Error) as e:
+        small.submit(probs[0].A, probs[0].b)
+    assert e.value.status == 3
+    small.close()
+
+
+@pytest.mark.gpu
+def test_injected_allocation_failure_is_reported_and_others_complete(lib):
+    probs = [P.poisson2d(40), P.poisson2d(41), P.poisson2d(42)]
+    srv = gs2.Server(precond=gs2.params("gs2", 1, 1), max_slots=2, fail_ticket=2)
+    tickets = [srv.submit(p.A, p.b) for p in probs]
+    assert tickets == [1, 2, 3]
+    out = [srv.wait(t, p.n) for t, p in zip(tickets, probs)]
+    st = srv.stats()
+    srv.close()
+    assert out[1][0].status == 3
+    assert out[0][0].status == 0 and out[2][0].status == 0
+    assert st["failed"] == 1 and st["completed"] == 2
+
+
+@pytest.mark.gpu
+def test_poll_busy_unknown_and_invalid_requests(lib):
+    pr = P.poisson3d(24)
+    srv = gs2.Server(precond=gs2.params("gs2", 1, 1, direction="symmetric"))
+    t = srv.submit(pr.A, pr.b)
+    r = srv.poll(t, pr.n)
+    while r is None:
+        r = srv.poll(t, pr.n)
+    assert r[0].status == 0
+    with pytest.raises(gs2.GS2Error):
+        srv.poll(t, pr.n)  # already collected
+    # a zero diagonal fails in preparation and is reported for the request
+    bad = P.dense_to_csr(np.array([[1.0, 2.0], [3.0, 0.0]]))
+    tb = srv.submit(bad, np.ones(2))
+    info, _, _ = srv.wait(tb, 2)
+    assert info.status == 2
+    srv.close()
