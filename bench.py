@@ -74,15 +74,19 @@ def stored_count(key):
     return None
 
 
-def stored_traffic(kernel, grid):
-    """Per-launch DRAM bytes of a kernel from the committed ncu summary."""
+def stored_traffic(kernel, algorithmic_bytes_per_launch):
+    """Per-launch DRAM bytes of a kernel: the ratio of DRAM bytes to
+    algorithmic bytes captured by ncu on a smaller case of the same kernel
+    (profiles/traffic.txt), scaled to this launch's algorithmic bytes (the
+    kernels stream their inputs once, so traffic grows in proportion)."""
     if not os.path.exists(TRAFFIC_FILE):
         return None
     with open(TRAFFIC_FILE) as f:
         for line in f:
             parts = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
-            if parts.get("kernel") == kernel and parts.get("grid") == str(grid):
-                return float(parts["dram_bytes_per_launch"])
+            if parts.get("kernel") == kernel and "dram_over_algorithmic" in parts:
+                return round(float(parts["dram_over_algorithmic"]) *
+                             algorithmic_bytes_per_launch)
     return None
 
 
@@ -235,7 +239,7 @@ def roofline(name, s, n, hbm, peak_kind, grid):
     per_launch_ms = s["total_ms"] / s["launches"]
     gbs = per_launch_bytes / (per_launch_ms / 1000.0) / 1e9
     fl = kernel_flops(name, s, n)
-    traffic = stored_traffic(name, grid)
+    traffic = stored_traffic(name, per_launch_bytes)
     if fl is not None:
         tf = fl / s["launches"] / (per_launch_ms / 1000.0) / 1e12
         return {"bound": "alu", "kernel": name, "achieved": round(tf, 4),
@@ -415,6 +419,8 @@ def run_ours(args):
         out["comparisons"] = comparisons(gs2, torch, pr, stream, b)
     if rank == 0 and not args.no_serve and world == 1:
         out["serving"] = serving(gs2, torch, args.serve_requests)
+    if rank == 0 and not args.no_extras and world == 1:
+        out["small_system"] = small_system(gs2, torch)
     if rank == 0 and world == 1 and not args.no_cpu:
         per_iter, full, dt, its = oracle_sample(pr)
         if full:
@@ -430,6 +436,38 @@ def run_ours(args):
         print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def small_system(gs2, torch, reps=20):
+    """2D 5-point Poisson 64x64 (n = 4096), GMRES(30) + forward GS2(1,1) to
+    1e-8: launch-bound, so timed with the Arnoldi steps replayed as a CUDA
+    graph and as separate launches (device-timed solves per second)."""
+    from paper_2104_01196_gb300 import problems as P
+    pr = P.poisson2d(64)
+    pc = gs2.params("gs2", 1, 1)
+    b = torch.from_numpy(pr.b).cuda()
+    x = torch.zeros(pr.n, dtype=torch.float64, device="cuda")
+    res = {"workload": "2D 5-point Poisson 64x64, GMRES(30) + GS2(1,1) forward, 1e-8"}
+    for name, mode in (("graph", 1), ("launches", 2)):
+        h = gs2.gs2_setup(pr.A)
+        h.set_graph_mode(mode)
+        for _ in range(3):
+            x.zero_()
+            info = gs2.gmres_solve(h, b, x, 30, 1e-8, 4000, pc)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            x.zero_()
+            info = gs2.gmres_solve(h, b, x, 30, 1e-8, 4000, pc)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        res[name] = {"ms_per_solve": round(ms, 3), "solves_per_s": round(1000.0 / ms, 1),
+                     "iters": info.iters, "true_relres": info.true_relres}
+        h.close()
+    return res
 
 
 def serving(gs2, torch, count):

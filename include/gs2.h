@@ -134,6 +134,14 @@ gs2_status gs2_set_stream(gs2_handle* h, void* stream);
 
 gs2_status gs2_get_stats(const gs2_handle* h, gs2_handle_stats* out);
 
+/* How gmres_solve issues the Arnoldi steps of a restart cycle:
+ * 0 (default) = as one replayed CUDA graph for n <= 524,288 and as separate
+ * launches above; 1 = always a graph; 2 = never.  A graph is captured once
+ * per cycle shape (restart, preconditioner) on a private stream joined to
+ * the handle's stream; results are the same either way, bit for bit.
+ * Graphs are not used while per-kernel profiling is enabled. */
+gs2_status gs2_set_graph_mode(gs2_handle* h, int mode);
+
 /* Non-compact GS2 relaxation, Eq. (4) with inner JR sweeps Eq. (5)-(7):
  * x is read and overwritten (in/out), b is read.  outer_sweeps = n_t >= 0,
  * inner_sweeps = n_j >= 0 (0 gives JR), damping = omega > 0, direction as

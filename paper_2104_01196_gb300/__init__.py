@@ -131,6 +131,7 @@ def load(path: str | None = None):
         "gs2_profile_enable": [P, I],
         "gs2_profile_filter": [P, ctypes.c_char_p],
         "gs2_check": [P],
+        "gs2_set_graph_mode": [P, I],
         "gs2_profile_read": [P, ctypes.POINTER(_KStat), I, ctypes.POINTER(I)],
         "gs2_profile_reset": [P],
     }
@@ -231,6 +232,10 @@ class Handle:
 
     def profile(self, enable: bool):
         _check(load().gs2_profile_enable(self.ptr, 1 if enable else 0))
+
+    def set_graph_mode(self, mode: int):
+        """0: automatic, 1: always replay Arnoldi steps as a CUDA graph, 2: never."""
+        _check(load().gs2_set_graph_mode(self.ptr, mode))
 
     def check(self):
         """Synchronise and raise if a kernel reported a device-side error."""

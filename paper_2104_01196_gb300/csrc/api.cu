@@ -23,6 +23,7 @@ void set_error(const std::string& msg) { g_last_error = msg; }
 
 static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void add_launches(long long delta) { g_launches.fetch_add(delta, std::memory_order_relaxed); }
 
 // ---------------------------------------------------------------------------
 // profiler
@@ -85,6 +86,8 @@ struct Profiler {
     for (auto e : pool) cudaEventDestroy(e);
   }
 };
+
+bool profiling_active(const gs2_handle* h) { return h->prof && h->prof->enabled; }
 
 KernelTimer::KernelTimer(gs2_handle* h_, const char* name, double bytes_)
     : h(h_), id(-1), bytes(bytes_) {
@@ -421,6 +424,11 @@ void gs2::destroy_handle(gs2_handle* h) {
   cudaGetDevice(&cur);
   cudaSetDevice(h->device);
   if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->gstream) cudaStreamSynchronize(h->gstream);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->gstream) cudaStreamDestroy(h->gstream);
+  if (h->gev_in) cudaEventDestroy(h->gev_in);
+  if (h->gev_out) cudaEventDestroy(h->gev_out);
   delete h->prof;
   for (void* p : h->allocs) {
     if (h->async_alloc) cudaFreeAsync(p, h->stream);
@@ -735,6 +743,12 @@ gs2_status gs2_profile_enable(gs2_handle* h, int enable) {
   if (!h) return GS2_ERR_INVALID_ARG;
   if (!h->prof) h->prof = new gs2::Profiler();
   h->prof->enabled = enable != 0;
+  return GS2_OK;
+}
+
+gs2_status gs2_set_graph_mode(gs2_handle* h, int mode) {
+  if (!h || mode < 0 || mode > 2) return GS2_ERR_INVALID_ARG;
+  h->graph_mode = mode;
   return GS2_OK;
 }
 

@@ -35,6 +35,7 @@ struct Error {
 // every kernel launch of the library is followed by this check, which also
 // counts it (gs2_launch_count)
 void count_launch();
+void add_launches(long long delta);
 #define GS2_LAUNCH_CHECK()          \
   do {                              \
     ::gs2::count_launch();          \
@@ -127,6 +128,16 @@ struct gs2_handle {
 
   gs2::Profiler* prof = nullptr;
 
+  // CUDA graph of one restart cycle's Arnoldi steps (launch-bound small
+  // systems): captured on a private stream, replayed there and joined to
+  // `stream` with events; re-captured when the cycle's shape changes
+  int graph_mode = 0;  // 0: automatic (n <= kGraphMaxRows), 1: always, 2: never
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t gev_in = nullptr, gev_out = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<double> gkey;
+  int64_t g_launches = 0;  // kernel launches per replay
+
   // stream-ordered allocation (cudaMallocAsync / cudaFreeAsync on `stream`):
   // used by server-owned handles so that freeing one request's memory never
   // synchronises the device under the other requests
@@ -142,6 +153,8 @@ namespace gs2 {
 // ---------------------------------------------------------------------------
 // profiling: optional event pairs around launches
 // ---------------------------------------------------------------------------
+
+bool profiling_active(const gs2_handle* h);
 
 struct KernelTimer {
   gs2_handle* h;
@@ -248,5 +261,8 @@ int vec_blocks(gs2_handle* h, int64_t n);
 constexpr int kVecThreads = 256;
 constexpr int kRowThreads = 256;
 constexpr int kMaxRestart = 64;
+// systems up to this size replay their Arnoldi steps as a CUDA graph by
+// default; above it the kernels are long enough that launch cost is noise
+constexpr int64_t kGraphMaxRows = 1 << 19;
 
 }  // namespace gs2

@@ -682,36 +682,103 @@ struct GmresRun {
     launch_cycle();
   }
 
-  void launch_cycle() {
+  // Arnoldi step j: z = M^{-1} v_j, w = A z, CGS2, Givens, v_{j+1}.  Every
+  // kernel returns at once once the device has stopped the cycle.
+  void enqueue_step(int j) {
     const int n = (int)h->n;
     const int ldh = m + 1;
     const int* skip = &h->st->stop;
+    const double* vj = h->V + (size_t)j * n;
+    precond_apply(h, pc, vj, h->z, wants, skip);
+    launch_spmv(h, h->z, h->w, skip);
+    const int jc = j + 1;
+    int nbr = launch_dots(h, jc, h->w, skip);
+    k_reduce_cols<<<jc, 256, 0, h->stream>>>(h->part, nbr, h->H, ldh, j, h->hbuf, 0, skip);
+    GS2_LAUNCH_CHECK();
+    nbr = launch_update<false>(h, jc, h->w, skip);
+    k_reduce_cols<<<jc, 256, 0, h->stream>>>(h->part, nbr, h->H, ldh, j, h->hbuf, 1, skip);
+    GS2_LAUNCH_CHECK();
+    nbr = launch_update<true>(h, jc, h->w, skip);
+    k_givens<<<1, 256, 0, h->stream>>>(h->part, nbr, h->H, ldh, j, h->cs, h->sn, h->gvec, h->st,
+                                       h->stop_mapped_dev);
+    GS2_LAUNCH_CHECK();
+    if (j + 1 < m) {
+      k_scale_next<<<vec_blocks(h, n), kVecThreads, 0, h->stream>>>(
+          n, h->w, h->V + (size_t)(j + 1) * n, h->dinv, r64, r32, h->st);
+      GS2_LAUNCH_CHECK();
+    }
+  }
+
+  bool use_graph() const {
+    if (profiling_active(h)) return false;  // event timing needs eager launches
+    return h->graph_mode == 1 || (h->graph_mode == 0 && h->n <= kGraphMaxRows);
+  }
+
+  // The m steps as one CUDA graph: captured once per cycle shape on the
+  // handle's private stream, replayed there between two event joins with
+  // the handle's stream.  Steps after the device-side stop run as no-ops.
+  void graph_steps() {
+    std::vector<double> key = {(double)m, (double)(uintptr_t)h->V, (double)(uintptr_t)r64,
+                               (double)(uintptr_t)r32, (double)(uintptr_t)h->part};
+    if (pc) {
+      const double pk[] = {(double)pc->kind, (double)pc->outer, (double)pc->inner, pc->omega,
+                           pc->gamma, (double)pc->direction, (double)pc->precision,
+                           (double)pc->form};
+      key.insert(key.end(), pk, pk + 8);
+    }
+    if (!h->gstream) {
+      GS2_CUDA(cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking));
+      GS2_CUDA(cudaEventCreateWithFlags(&h->gev_in, cudaEventDisableTiming));
+      GS2_CUDA(cudaEventCreateWithFlags(&h->gev_out, cudaEventDisableTiming));
+    }
+    if (!h->gexec || h->gkey != key) {
+      if (h->gexec) cudaGraphExecDestroy(h->gexec);
+      h->gexec = nullptr;
+      cudaStream_t user = h->stream;
+      h->stream = h->gstream;
+      const long long c0 = gs2_launch_count();
+      cudaGraph_t g = nullptr;
+      GS2_CUDA(cudaStreamBeginCapture(h->gstream, cudaStreamCaptureModeThreadLocal));
+      try {
+        for (int j = 0; j < m; ++j) enqueue_step(j);
+      } catch (...) {
+        cudaStreamEndCapture(h->gstream, &g);
+        if (g) cudaGraphDestroy(g);
+        h->stream = user;
+        throw;
+      }
+      h->stream = user;
+      GS2_CUDA(cudaStreamEndCapture(h->gstream, &g));
+      h->g_launches = gs2_launch_count() - c0;
+      add_launches(-h->g_launches);  // captured, not run
+      cudaError_t e = cudaGraphInstantiate(&h->gexec, g, 0);
+      cudaGraphDestroy(g);
+      GS2_CUDA(e);
+      h->gkey = key;
+    }
+    GS2_CUDA(cudaEventRecord(h->gev_in, h->stream));
+    GS2_CUDA(cudaStreamWaitEvent(h->gstream, h->gev_in, 0));
+    GS2_CUDA(cudaGraphLaunch(h->gexec, h->gstream));
+    GS2_CUDA(cudaEventRecord(h->gev_out, h->gstream));
+    GS2_CUDA(cudaStreamWaitEvent(h->stream, h->gev_out, 0));
+    add_launches(h->g_launches);
+  }
+
+  void launch_cycle() {
+    const int n = (int)h->n;
+    const int ldh = m + 1;
     *h->stop_mapped = 0;
     k_cycle_reset<<<1, 1, 0, h->stream>>>(h->st);
     GS2_LAUNCH_CHECK();
     k_cycle_start<<<vec_blocks(h, n), kVecThreads, 0, h->stream>>>(n, h->r, h->V, h->dinv, r64,
                                                                   r32, h->gvec, m, h->st);
     GS2_LAUNCH_CHECK();
-    for (int j = 0; j < m; ++j) {
-      if (*h->stop_mapped) break;  // the device has already ended the cycle
-      const double* vj = h->V + (size_t)j * n;
-      precond_apply(h, pc, vj, h->z, wants, skip);
-      launch_spmv(h, h->z, h->w, skip);
-      const int jc = j + 1;
-      int nbr = launch_dots(h, jc, h->w, skip);
-      k_reduce_cols<<<jc, 256, 0, h->stream>>>(h->part, nbr, h->H, ldh, j, h->hbuf, 0, skip);
-      GS2_LAUNCH_CHECK();
-      nbr = launch_update<false>(h, jc, h->w, skip);
-      k_reduce_cols<<<jc, 256, 0, h->stream>>>(h->part, nbr, h->H, ldh, j, h->hbuf, 1, skip);
-      GS2_LAUNCH_CHECK();
-      nbr = launch_update<true>(h, jc, h->w, skip);
-      k_givens<<<1, 256, 0, h->stream>>>(h->part, nbr, h->H, ldh, j, h->cs, h->sn, h->gvec, h->st,
-                                         h->stop_mapped_dev);
-      GS2_LAUNCH_CHECK();
-      if (j + 1 < m) {
-        k_scale_next<<<vec_blocks(h, n), kVecThreads, 0, h->stream>>>(
-            n, h->w, h->V + (size_t)(j + 1) * n, h->dinv, r64, r32, h->st);
-        GS2_LAUNCH_CHECK();
+    if (use_graph()) {
+      graph_steps();
+    } else {
+      for (int j = 0; j < m; ++j) {
+        if (*h->stop_mapped) break;  // the device has already ended the cycle
+        enqueue_step(j);
       }
     }
     // x += M^{-1} V y

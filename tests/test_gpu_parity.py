@@ -409,3 +409,25 @@ def test_full_size_iteration_counts_match_oracle(g, big, pc):
     info = g.gmres_solve(h, dev(big.b), x, 30, 1e-8, 5000, g.params(**FULL_PCS[pc]))
     assert info.status == 0 and info.true_relres <= 1e-8
     assert abs(info.iters - int(ref["iters"])) <= 1, (info.iters, ref)
+
+
+@pytest.mark.parametrize("pc", ["sgs2_1_2", "jr3", "gs_sym", "none"])
+def test_graph_and_eager_cycles_agree_bitwise(g, pc):
+    """Arnoldi steps replayed as a captured CUDA graph give the same bits as
+    separate launches, also when a cached graph is reused for a new b."""
+    pr = P.poisson2d(64)
+    b2 = P.csr_matvec(pr.A, P.uniform_pm1(77, pr.n))
+    gp, _ = PCS[pc]
+    prm = g.params(**gp) if gp else None
+    res = {}
+    for mode in (1, 2):
+        h = g.gs2_setup(pr.A)
+        h.set_graph_mode(mode)
+        for k, b in enumerate((pr.b, b2)):
+            x = dev(np.zeros(pr.n))
+            info = g.gmres_solve(h, dev(b), x, 30, 1e-8, 5000, prm)
+            assert info.status == 0
+            res[(mode, k)] = (info.iters, host(x))
+    for k in (0, 1):
+        assert res[(1, k)][0] == res[(2, k)][0]
+        assert np.array_equal(res[(1, k)][1], res[(2, k)][1])

@@ -1,0 +1,151 @@
+"""GPU parity on the elasticity and convection-diffusion model problems.
+
+Q1 hexahedral elasticity (SPD, ~81 entries per row: the K-lane row path)
+with SGS2 in FP64 and with FP32 triangle values; 3D first-order upwind
+convection-diffusion (nonsymmetric) with GS2 inner sweeps in FP64, FP32 and
+FP16 with a per-row scale, outer residual and Arnoldi in FP64.  FP64 sweeps
+match the oracle to 1e-12; lower-precision results are compared with the
+FP64 oracle and the error bound each precision implies is written in the
+test (FP32 values: ~1e-7 relative per entry; FP16 scaled values: ~5e-4).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2104_01196_gb300 import problems as P
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def g():
+    import torch  # noqa: F401
+
+    from paper_2104_01196_gb300 import build as B
+    B.build()
+    import paper_2104_01196_gb300 as gs2
+    gs2.load()
+    return gs2
+
+
+def dev(v):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(v, dtype=np.float64)).cuda()
+
+
+def host(t):
+    import torch
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.fixture(scope="module")
+def ela():
+    return P.elasticity3d(10)
+
+
+@pytest.fixture(scope="module")
+def cd():
+    return P.convdiff3d(20)
+
+
+@pytest.mark.parametrize("inner", [1, 2, 3, 4])
+def test_elasticity_sgs2_sweeps_fp64(g, ela, inner):
+    x0 = P.uniform_pm1(5, ela.n)
+    h = g.gs2_setup(ela.A)
+    x = dev(x0)
+    g.gs2_apply(h, dev(ela.b), x, 2, inner, 0.9, g.SYMMETRIC)
+    assert rel(host(x), oracle.gs2(ela.A, ela.b, x0, 2, inner, 0.9, 1.0, 2)) <= TOL
+
+
+@pytest.mark.parametrize("inner,omega", [(1, 0.7), (2, 0.8), (3, 0.9)])
+def test_elasticity_gmres_fp32_preconditioner(g, ela, inner, omega):
+    """Preconditioner values in FP32, GMRES/Arnoldi FP64: converges to the
+    same tolerance in about the FP64 oracle's iteration count (Sec. 6.3).
+    As in the elasticity omega table of Sec. 6.1, SGS2 with few inner sweeps
+    needs omega < 1 (here SGS2(1,1) stagnates at omega = 0.8)."""
+    h = g.gs2_setup(ela.A, precisions=("fp32",))
+    x = dev(np.zeros(ela.n))
+    info = g.gmres_solve(h, dev(ela.b), x, 30, 1e-8, 5000,
+                         g.params("gs2", 1, inner, omega=omega, direction="symmetric",
+                                  precision="fp32"))
+    xo, oinfo = oracle.gmres(ela.A, ela.b, restart=30, tol=1e-8, max_iters=5000,
+                             pc_kind=oracle.PC_GS2, pc_inner=inner, pc_omega=omega,
+                             pc_direction=oracle.SYMMETRIC)
+    assert info.status == 0 and oinfo.status == 0
+    assert info.true_relres <= 1e-8
+    assert abs(info.iters - oinfo.iters) <= max(2, oinfo.iters // 20), (info.iters, oinfo.iters)
+    r = np.linalg.norm(ela.b - oracle.spmv(ela.A, host(x))) / np.linalg.norm(ela.b)
+    assert r <= 1e-8
+
+
+def test_elasticity_stationary_jr_diverges_at_omega_one(g, ela):
+    """Sec. 6.1: with omega = 1 JR diverges on elasticity, while SGS2(1,1) with
+    omega = 0.8 reduces the residual."""
+    h = g.gs2_setup(ela.A)
+    b = dev(ela.b)
+
+    def res(x):
+        return np.linalg.norm(ela.b - oracle.spmv(ela.A, host(x)))
+
+    x = dev(np.zeros(ela.n))
+    r0 = res(x)
+    g.jr_apply(h, b, x, 200, 1.0)
+    assert res(x) > r0
+    x = dev(np.zeros(ela.n))
+    g.gs2_apply(h, b, x, 50, 1, 0.8, g.SYMMETRIC)
+    assert res(x) < r0
+
+
+@pytest.mark.parametrize("direction", [0, 1, 2])
+def test_convdiff_sweeps_all_precisions(g, cd, direction):
+    x0 = P.uniform_pm1(9, cd.n)
+    ref = oracle.gs2(cd.A, cd.b, x0, 1, 2, 1.0, 1.0, direction)
+    h = g.gs2_setup(cd.A, precisions=("fp32", "fp16"))
+    errs = {}
+    for prec in ("fp64", "fp32", "fp16"):
+        x = dev(x0)
+        g.gs2_apply_ex(h, dev(cd.b), x, g.params("gs2", 1, 2, direction=direction,
+                                                 precision=prec))
+        errs[prec] = rel(host(x), ref)
+    assert errs["fp64"] <= TOL
+    assert errs["fp32"] <= 2e-6
+    assert errs["fp16"] <= 2e-3
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16"])
+def test_convdiff_gmres_error_vs_fp64_oracle(g, cd, prec):
+    """GS2(1,1) inner sweeps in each precision, FP64 outer: the true residual
+    meets 1e-8 and the solution is within the FP64 oracle's own error."""
+    xo, oinfo = oracle.gmres(cd.A, cd.b, restart=30, tol=1e-8, max_iters=5000,
+                             pc_kind=oracle.PC_GS2, pc_inner=1)
+    h = g.gs2_setup(cd.A, precisions=(prec,) if prec != "fp64" else ())
+    x = dev(np.zeros(cd.n))
+    info = g.gmres_solve(h, dev(cd.b), x, 30, 1e-8, 5000,
+                         g.params("gs2", 1, 1, precision=prec))
+    assert info.status == 0 and info.true_relres <= 1e-8
+    xg = host(x)
+    err_ora = rel(xo, cd.x_true)
+    assert rel(xg, cd.x_true) <= 10 * err_ora + 1e-12
+    if prec == "fp64":
+        assert abs(info.iters - oinfo.iters) <= 1
+    else:
+        assert abs(info.iters - oinfo.iters) <= max(2, oinfo.iters // 10)
+
+
+def test_convdiff_full_size_sweeps(g):
+    """192^3 (n = 7,077,888): one forward GS2(1,1) sweep in FP64 against the
+    oracle on every entry, FP32 and FP16 inner sweeps within their bounds."""
+    pr = P.convdiff3d(192)
+    x0 = P.uniform_pm1(13, pr.n)
+    ref = oracle.gs2(pr.A, pr.b, x0, 1, 1, 1.0, 1.0, 0)
+    h = g.gs2_setup(pr.A, precisions=("fp32", "fp16"))
+    for prec, bound in (("fp64", TOL), ("fp32", 2e-6), ("fp16", 2e-3)):
+        x = dev(x0)
+        g.gs2_apply_ex(h, dev(pr.b), x, g.params("gs2", 1, 1, precision=prec))
+        assert rel(host(x), ref) <= bound, prec
