@@ -105,7 +105,8 @@ typedef struct {
   int64_t n, nnz, nnz_lower, nnz_upper;
   int levels_lower, levels_upper; /* 0 until a level-scheduled call */
   int64_t device_bytes;           /* device memory held by the handle */
-  int tpr_a, tpr_tri;             /* threads per row of the CSR kernels */
+  int tpr_a, tpr_tri;             /* lanes per row of the tile kernels (A, D^-1 L) */
+  int rpt_a, rpt_tri;             /* rows per lane group of the tile kernels */
 } gs2_handle_stats;
 
 typedef struct gs2_handle gs2_handle;
@@ -133,6 +134,15 @@ void gs2_destroy(gs2_handle* h);
 gs2_status gs2_set_stream(gs2_handle* h, void* stream);
 
 gs2_status gs2_get_stats(const gs2_handle* h, gs2_handle_stats* out);
+
+/* Autotune the tile shape of A, D^{-1}L and D^{-1}U: for each matrix, time an
+ * SpMV-shaped pass for every candidate (lanes per row K around the row-length
+ * heuristic, rows per lane group 1 or 2) and keep the fastest.  Results are
+ * cached by matrix class (size to a factor sqrt(2), mean row length), so
+ * matrices of a class already measured are re-tiled without timing.  The
+ * numerical results do not change (rows are reduced in the same order for
+ * K = 1 and in a different segment split otherwise, within rounding). */
+gs2_status gs2_autotune(gs2_handle* h);
 
 /* How gmres_solve issues the Arnoldi steps of a restart cycle:
  * 0 (default) = as one replayed CUDA graph for n <= 524,288 and as separate

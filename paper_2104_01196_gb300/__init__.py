@@ -61,7 +61,8 @@ class _Stats(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("nnz_lower", ctypes.c_int64),
                 ("nnz_upper", ctypes.c_int64), ("levels_lower", ctypes.c_int),
                 ("levels_upper", ctypes.c_int), ("device_bytes", ctypes.c_int64),
-                ("tpr_a", ctypes.c_int), ("tpr_tri", ctypes.c_int)]
+                ("tpr_a", ctypes.c_int), ("tpr_tri", ctypes.c_int),
+                ("rpt_a", ctypes.c_int), ("rpt_tri", ctypes.c_int)]
 
 
 class _KStat(ctypes.Structure):
@@ -132,6 +133,7 @@ def load(path: str | None = None):
         "gs2_profile_filter": [P, ctypes.c_char_p],
         "gs2_check": [P],
         "gs2_set_graph_mode": [P, I],
+        "gs2_autotune": [P],
         "gs2_profile_read": [P, ctypes.POINTER(_KStat), I, ctypes.POINTER(I)],
         "gs2_profile_reset": [P],
     }
@@ -232,6 +234,10 @@ class Handle:
 
     def profile(self, enable: bool):
         _check(load().gs2_profile_enable(self.ptr, 1 if enable else 0))
+
+    def autotune(self):
+        """Pick the fastest tile shape of each matrix (cached by matrix class)."""
+        _check(load().gs2_autotune(self.ptr))
 
     def set_graph_mode(self, mode: int):
         """0: automatic, 1: always replay Arnoldi steps as a CUDA graph, 2: never."""

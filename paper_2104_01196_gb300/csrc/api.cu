@@ -8,7 +8,9 @@
 #include <cmath>
 #include <cstring>
 #include <limits>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <new>
 #include <string>
 #include <unordered_map>
@@ -121,9 +123,9 @@ static int choose_lanes(double mean) {
   return K;
 }
 
-static void build_tiles(const std::vector<int>& rp, int n, int K, std::vector<int>& tiles,
-                        int& cap) {
-  const int R = kRowThreads / K;
+static void build_tiles(const std::vector<int>& rp, int n, int K, int RPT,
+                        std::vector<int>& tiles, int& cap) {
+  const int R = RPT * kRowThreads / K;
   tiles.clear();
   tiles.push_back(0);
   int maxnz = 0;
@@ -150,6 +152,8 @@ static void build_tiles(const std::vector<int>& rp, int n, int K, std::vector<in
   if (cap < 8) cap = 8;
 }
 
+void retile(gs2_handle* h, DevCsr& M, const std::vector<int>& rp, int K, int RPT);
+
 static void upload_csr(gs2_handle* h, DevCsr& M, int n, const std::vector<int>& rp,
                        const std::vector<int>& ci, const std::vector<double>& va) {
   M.n = n;
@@ -168,8 +172,16 @@ static void upload_csr(gs2_handle* h, DevCsr& M, int n, const std::vector<int>& 
   h->dzero(M.va, sizeof(double) * nz);
   h->h2d(M.ci, ci.data(), sizeof(int) * M.nnz);
   h->h2d(M.va, va.data(), sizeof(double) * M.nnz);
+  retile(h, M, rp, M.tpr, 1);
+}
+
+// (Re)build the row tiles of M for K lanes per row and RPT rows per lane
+// group, and upload their descriptors.
+void retile(gs2_handle* h, DevCsr& M, const std::vector<int>& rp, int K, int RPT) {
   std::vector<int> tiles;
-  build_tiles(rp, n, M.tpr, tiles, M.cap);
+  build_tiles(rp, M.n, K, RPT, tiles, M.cap);
+  M.tpr = K;
+  M.rpt = RPT;
   M.ntiles = (int)tiles.size() - 1;
   std::vector<int4> desc(std::max(M.ntiles, 1));
   for (int t = 0; t < M.ntiles; ++t) {
@@ -220,6 +232,7 @@ static void prepare_lowprec(gs2_handle* h, DevCsr& M, const HostTri& T, int prec
 // host copies of the triangles, kept for lazy precision / level setup
 struct gs2_host_side {
   gs2::HostTri L, U;
+  std::vector<int> Arp;  // rowptr of A (re-tiling)
 };
 static std::mutex g_host_mu;
 static std::unordered_map<const gs2_handle*, gs2_host_side*> g_host;
@@ -329,6 +342,51 @@ void ensure_levels(gs2_handle* h) {
   build(hs->L, true, h->lev_ptr_L, h->lev_rows_L);
   build(hs->U, false, h->lev_ptr_U, h->lev_rows_U);
   h->levels_ready = true;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner: tile shape (lanes per row K, rows per lane group RPT) per matrix
+// ---------------------------------------------------------------------------
+
+// Best shapes found so far, by (matrix role, n to a factor sqrt(2), mean row
+// length to a quarter): matrices of the same class reuse a measurement.
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int>, std::pair<int, int>> g_tune;
+
+static void tune_matrix(gs2_handle* h, DevCsr& M, const std::vector<int>& rp, int role) {
+  if (M.n == 0 || M.nnz == 0) return;
+  const auto key = std::make_tuple(role, (int)std::lround(2.0 * std::log2((double)M.n)),
+                                   (int)std::lround(4.0 * M.mean_row));
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      if (it->second != std::make_pair(M.tpr, M.rpt))
+        retile(h, M, rp, it->second.first, it->second.second);
+      return;
+    }
+  }
+  // candidates around the mean-row-length heuristic
+  const int kh = choose_lanes(M.mean_row);
+  std::vector<std::pair<int, int>> cand;
+  for (int K : {1, 2, 4, 8, 16}) {
+    if (2 * K < kh || K > 2 * kh) continue;
+    cand.emplace_back(K, 1);
+    if (K <= 2) cand.emplace_back(K, 2);
+  }
+  std::pair<int, int> best{M.tpr, M.rpt};
+  float best_ms = 1e30f;
+  for (const auto& c : cand) {
+    retile(h, M, rp, c.first, c.second);
+    const float ms = time_tile_probe(h, M, 5);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  retile(h, M, rp, best.first, best.second);
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  g_tune[key] = best;
 }
 
 static bool is_device_ptr(const void* p) {
@@ -564,6 +622,7 @@ gs2_handle* gs2::setup_handle(int64_t n, int64_t nnz, const int64_t* rowptr,
   h->n = n;
   h->nnz = nnz;
   upload_csr(h, h->A, (int)n, rp32, std::vector<int>(ci.begin(), ci.end()), va);
+  hs->Arp = rp32;
   upload_csr(h, h->L, (int)n, L.rp, L.ci, L.va);
   upload_csr(h, h->U, (int)n, U.rp, U.ci, U.va);
   std::vector<double> dinv(n);
@@ -620,6 +679,8 @@ gs2_status gs2_get_stats(const gs2_handle* h, gs2_handle_stats* out) {
   out->device_bytes = h->dev_bytes;
   out->tpr_a = h->A.tpr;
   out->tpr_tri = h->L.tpr;
+  out->rpt_a = h->A.rpt;
+  out->rpt_tri = h->L.rpt;
   return GS2_OK;
 }
 
@@ -744,6 +805,27 @@ gs2_status gs2_profile_enable(gs2_handle* h, int enable) {
   if (!h->prof) h->prof = new gs2::Profiler();
   h->prof->enabled = enable != 0;
   return GS2_OK;
+}
+
+gs2_status gs2_autotune(gs2_handle* h) {
+  if (!h) return GS2_ERR_INVALID_ARG;
+  API_BEGIN
+  if (h->n == 0) return GS2_OK;
+  gs2_host_side* hs = host_side(h);
+  h->dzero(h->t, sizeof(double) * h->n);
+  h->dzero(h->z, sizeof(double) * h->n);
+  tune_matrix(h, h->A, hs->Arp, 0);
+  tune_matrix(h, h->L, hs->L.rp, 1);
+  tune_matrix(h, h->U, hs->U.rp, 2);
+  GS2_CUDA(cudaStreamSynchronize(h->stream));
+  // cached CUDA graphs hold the old tile shapes
+  if (h->gexec) {
+    cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+    h->gkey.clear();
+  }
+  return GS2_OK;
+  API_END
 }
 
 gs2_status gs2_set_graph_mode(gs2_handle* h, int mode) {

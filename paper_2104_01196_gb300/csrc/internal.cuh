@@ -59,6 +59,7 @@ struct DevCsr {
   __half* va16 = nullptr;  // FP16 scaled copy (triangles)
   float* scale16 = nullptr;
   int tpr = 1;             // lanes per row (K) of the tile kernels
+  int rpt = 1;             // rows per group of K lanes (RPT), 1 or 2 (K <= 2)
   // row tiles: desc[t] = {first row, end row, first staged entry (rowptr
   // rounded down to 8), end entry}; a tile with more than `cap` entries
   // holds exactly one (long) row and has desc.z = -1 - rowptr[first row]
@@ -194,6 +195,7 @@ void launch_rhat_update(gs2_handle* h, int prec, const void* rhat, double* x,
                         double omega, bool add, const int* skip);
 
 void launch_spmv(gs2_handle* h, const double* x, double* y, const int* skip);
+float time_tile_probe(gs2_handle* h, const DevCsr& M, int reps);
 void launch_jr(gs2_handle* h, const double* b, const double* x_in,
                double* x_out, double omega, const int* skip);
 void launch_level(gs2_handle* h, const DevCsr& T, const int* rows, int r0,
@@ -242,6 +244,8 @@ struct GmresJob;
 GmresJob* gmres_job_start(gs2_handle* h, const double* b, double* x, int m, double tol,
                           int max_iters, const gs2_params* p);
 bool gmres_job_advance(GmresJob* j);
+// capture the job's cycle graph now (host work only) when it will use one
+void gmres_job_prepare(GmresJob* j);
 gs2_solve_info gmres_job_info(const GmresJob* j);
 void gmres_job_free(GmresJob* j);
 

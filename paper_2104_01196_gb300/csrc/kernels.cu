@@ -174,9 +174,10 @@ struct StageLayout {
 // from one shared-memory stage, one thread has TMA fill the other stage
 // with tile t + grid (its rowptr slice, columns and values), completion
 // tracked by one mbarrier per stage.  Rows are reduced by one thread each
-// (K = 1) or by K contiguous segments and a K-wide shuffle tree.  The
+// (K = 1) or by K contiguous segments and a K-wide shuffle tree; each group
+// of K lanes takes RPT rows of a tile (RPT * 256 / K rows per tile).  The
 // epilogue's per-row operands are loaded before the gathers.
-template <int K, typename VT, class Epi>
+template <int K, int RPT, typename VT, class Epi>
 __global__ void __launch_bounds__(kRowThreads)
 k_tiles(TileMat<VT> M, Epi epi, const int* skip) {
   using AT = typename ValTraits<VT>::AT;
@@ -251,40 +252,43 @@ k_tiles(TileMat<VT> M, Epi epi, const int* skip) {
     const int* s_ci = reinterpret_cast<const int*>(base + L.ci_off);
     const VT* s_va = reinterpret_cast<const VT*>(base + L.va_off);
     const int rpb = d.x & ~3;
-    const int row = d.x + q;
-    AT s = AT(0);
-    typename Epi::Pre pv{};
-    if (row < d.y) {
-      pv = epi.pre(row);
-      const int rs = s_rp[row - rpb] - d.z, re = s_rp[row + 1 - rpb] - d.z;
-      int ks = rs, ke = re;
-      if (K > 1) {
-        const int seg = (re - rs + K - 1) / K;
-        ks = min(rs + l * seg, re);
-        ke = min(ks + seg, re);
+#pragma unroll
+    for (int rr = 0; rr < RPT; ++rr) {
+      const int row = d.x + q + rr * (kRowThreads / K);
+      AT s = AT(0);
+      typename Epi::Pre pv{};
+      if (row < d.y) {
+        pv = epi.pre(row);
+        const int rs = s_rp[row - rpb] - d.z, re = s_rp[row + 1 - rpb] - d.z;
+        int ks = rs, ke = re;
+        if (K > 1) {
+          const int seg = (re - rs + K - 1) / K;
+          ks = min(rs + l * seg, re);
+          ke = min(ks + seg, re);
+        }
+        int k = ks;
+        // groups of four: all four gathers are in flight before the FMAs
+        for (; k + 4 <= ke; k += 4) {
+          const AT x0 = (AT)epi.gather(s_ci[k]), x1 = (AT)epi.gather(s_ci[k + 1]);
+          const AT x2 = (AT)epi.gather(s_ci[k + 2]), x3 = (AT)epi.gather(s_ci[k + 3]);
+          s = fma((AT)ValTraits<VT>::get(s_va, k), x0, s);
+          s = fma((AT)ValTraits<VT>::get(s_va, k + 1), x1, s);
+          s = fma((AT)ValTraits<VT>::get(s_va, k + 2), x2, s);
+          s = fma((AT)ValTraits<VT>::get(s_va, k + 3), x3, s);
+        }
+        const int rem = ke - k;
+        if (rem > 0) {
+          const AT x0 = (AT)epi.gather(s_ci[k]);
+          const AT x1 = rem > 1 ? (AT)epi.gather(s_ci[k + 1]) : AT(0);
+          const AT x2 = rem > 2 ? (AT)epi.gather(s_ci[k + 2]) : AT(0);
+          s = fma((AT)ValTraits<VT>::get(s_va, k), x0, s);
+          if (rem > 1) s = fma((AT)ValTraits<VT>::get(s_va, k + 1), x1, s);
+          if (rem > 2) s = fma((AT)ValTraits<VT>::get(s_va, k + 2), x2, s);
+        }
       }
-      int k = ks;
-      // groups of four: all four gathers are in flight before the FMAs
-      for (; k + 4 <= ke; k += 4) {
-        const AT x0 = (AT)epi.gather(s_ci[k]), x1 = (AT)epi.gather(s_ci[k + 1]);
-        const AT x2 = (AT)epi.gather(s_ci[k + 2]), x3 = (AT)epi.gather(s_ci[k + 3]);
-        s = fma((AT)ValTraits<VT>::get(s_va, k), x0, s);
-        s = fma((AT)ValTraits<VT>::get(s_va, k + 1), x1, s);
-        s = fma((AT)ValTraits<VT>::get(s_va, k + 2), x2, s);
-        s = fma((AT)ValTraits<VT>::get(s_va, k + 3), x3, s);
-      }
-      const int rem = ke - k;
-      if (rem > 0) {
-        const AT x0 = (AT)epi.gather(s_ci[k]);
-        const AT x1 = rem > 1 ? (AT)epi.gather(s_ci[k + 1]) : AT(0);
-        const AT x2 = rem > 2 ? (AT)epi.gather(s_ci[k + 2]) : AT(0);
-        s = fma((AT)ValTraits<VT>::get(s_va, k), x0, s);
-        if (rem > 1) s = fma((AT)ValTraits<VT>::get(s_va, k + 1), x1, s);
-        if (rem > 2) s = fma((AT)ValTraits<VT>::get(s_va, k + 2), x2, s);
-      }
+      if (K > 1) s = group_sum<K, AT>(s);
+      if (row < d.y && l == 0) epi.finish(row, s, pv);
     }
-    if (K > 1) s = group_sum<K, AT>(s);
-    if (row < d.y && l == 0) epi.finish(row, s, pv);
     __syncthreads();
   }
 }
@@ -416,7 +420,7 @@ static TileMat<VT> view(gs2_handle* h, const DevCsr& M, const VT* va) {
   t.n = M.n;
   t.ntiles = M.ntiles;
   t.cap = M.cap;
-  t.rcap = kRowThreads / M.tpr;
+  t.rcap = M.rpt * kRowThreads / M.tpr;
   t.rp = M.rp;
   t.ci = M.ci;
   t.va = va;
@@ -425,27 +429,31 @@ static TileMat<VT> view(gs2_handle* h, const DevCsr& M, const VT* va) {
   return t;
 }
 
-template <int K, typename VT, class Epi>
+template <int K, int RPT, typename VT, class Epi>
 static void launch_k(gs2_handle* h, const DevCsr& M, const VT* va, const Epi& epi,
                      const int* skip) {
   if (M.n == 0 || M.ntiles == 0) return;
-  const size_t smem = 2 * (size_t)StageLayout<VT>(kRowThreads / K, M.cap).bytes;
-  auto fn = k_tiles<K, VT, Epi>;
+  const size_t smem = 2 * (size_t)StageLayout<VT>(RPT * kRowThreads / K, M.cap).bytes;
+  auto fn = k_tiles<K, RPT, VT, Epi>;
   const int per_sm = blocks_per_sm((const void*)fn, smem);
   const int grid = std::min(M.ntiles, per_sm * h->nsm);
   fn<<<grid, kRowThreads, smem, h->stream>>>(view<VT>(h, M, va), epi, skip);
   GS2_LAUNCH_CHECK();
 }
 
+// (K, RPT) shapes: RPT = 2 only for short rows (K <= 2), where the per-tile
+// barrier and stage overhead is largest relative to the work per row
 template <typename VT, class Epi>
 static void dispatch(gs2_handle* h, const DevCsr& M, const VT* va, const Epi& epi,
                      const int* skip) {
-  switch (M.tpr) {
-    case 1: launch_k<1, VT, Epi>(h, M, va, epi, skip); break;
-    case 2: launch_k<2, VT, Epi>(h, M, va, epi, skip); break;
-    case 4: launch_k<4, VT, Epi>(h, M, va, epi, skip); break;
-    case 8: launch_k<8, VT, Epi>(h, M, va, epi, skip); break;
-    default: launch_k<16, VT, Epi>(h, M, va, epi, skip); break;
+  switch (M.tpr * 4 + (M.rpt == 2 ? 1 : 0)) {
+    case 1 * 4 + 1: launch_k<1, 2, VT, Epi>(h, M, va, epi, skip); break;
+    case 2 * 4 + 1: launch_k<2, 2, VT, Epi>(h, M, va, epi, skip); break;
+    case 1 * 4: launch_k<1, 1, VT, Epi>(h, M, va, epi, skip); break;
+    case 2 * 4: launch_k<2, 1, VT, Epi>(h, M, va, epi, skip); break;
+    case 4 * 4: launch_k<4, 1, VT, Epi>(h, M, va, epi, skip); break;
+    case 8 * 4: launch_k<8, 1, VT, Epi>(h, M, va, epi, skip); break;
+    default: launch_k<16, 1, VT, Epi>(h, M, va, epi, skip); break;
   }
 }
 
@@ -466,6 +474,29 @@ void launch_spmv(gs2_handle* h, const double* x, double* y, const int* skip) {
   KernelTimer tm(h, "spmv", bytes_csr(h->A, 8) + 16.0 * h->n);
   EpiSpmv e{x, y};
   dispatch<double>(h, h->A, h->A.va, e, skip);
+}
+
+// Autotuner probe: milliseconds per launch of y = M x over M's FP64 values
+// with M's current tile shape (x = h->t, y = h->z), best of `reps`.
+float time_tile_probe(gs2_handle* h, const DevCsr& M, int reps) {
+  EpiSpmv e{h->t, h->z};
+  cudaEvent_t e0, e1;
+  GS2_CUDA(cudaEventCreate(&e0));
+  GS2_CUDA(cudaEventCreate(&e1));
+  dispatch<double>(h, M, M.va, e, nullptr);  // warm-up (occupancy query, L2)
+  float best = 1e30f;
+  for (int r = 0; r < reps; ++r) {
+    GS2_CUDA(cudaEventRecord(e0, h->stream));
+    dispatch<double>(h, M, M.va, e, nullptr);
+    GS2_CUDA(cudaEventRecord(e1, h->stream));
+    GS2_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    GS2_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    best = std::min(best, ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return best;
 }
 
 void launch_jr(gs2_handle* h, const double* b, const double* x_in, double* x_out,

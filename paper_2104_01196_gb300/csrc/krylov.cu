@@ -718,6 +718,18 @@ struct GmresRun {
   // handle's private stream, replayed there between two event joins with
   // the handle's stream.  Steps after the device-side stop run as no-ops.
   void graph_steps() {
+    ensure_graph();
+    GS2_CUDA(cudaEventRecord(h->gev_in, h->stream));
+    GS2_CUDA(cudaStreamWaitEvent(h->gstream, h->gev_in, 0));
+    GS2_CUDA(cudaGraphLaunch(h->gexec, h->gstream));
+    GS2_CUDA(cudaEventRecord(h->gev_out, h->gstream));
+    GS2_CUDA(cudaStreamWaitEvent(h->stream, h->gev_out, 0));
+    add_launches(h->g_launches);
+  }
+
+  // Capture (once per cycle shape) without running anything: host work
+  // only, so a server can do it on a preparation thread.
+  void ensure_graph() {
     std::vector<double> key = {(double)m, (double)(uintptr_t)h->V, (double)(uintptr_t)r64,
                                (double)(uintptr_t)r32, (double)(uintptr_t)h->part};
     if (pc) {
@@ -756,12 +768,6 @@ struct GmresRun {
       GS2_CUDA(e);
       h->gkey = key;
     }
-    GS2_CUDA(cudaEventRecord(h->gev_in, h->stream));
-    GS2_CUDA(cudaStreamWaitEvent(h->gstream, h->gev_in, 0));
-    GS2_CUDA(cudaGraphLaunch(h->gexec, h->gstream));
-    GS2_CUDA(cudaEventRecord(h->gev_out, h->gstream));
-    GS2_CUDA(cudaStreamWaitEvent(h->stream, h->gev_out, 0));
-    add_launches(h->g_launches);
   }
 
   void launch_cycle() {
@@ -825,6 +831,10 @@ GmresJob* gmres_job_start(gs2_handle* h, const double* b, double* x, int m, doub
     throw;
   }
   return j;
+}
+
+void gmres_job_prepare(GmresJob* j) {
+  if (!j->run.done && j->run.use_graph()) j->run.ensure_graph();
 }
 
 bool gmres_job_advance(GmresJob* j) {

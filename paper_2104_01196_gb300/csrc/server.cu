@@ -133,11 +133,16 @@ static void prepare(gs2_server* s, Request* r) {
     r->h = setup_handle(r->n, r->nnz, r->rp.data(), r->ci.data(), r->va.data(), 0, prec,
                         r->stream, true);
     if (pc && pc->kind == GS2_PC_GS) ensure_levels(r->h);
+    // every request replays its cycles as a graph captured by this thread,
+    // so the single progress thread only ever launches whole cycles
+    r->h->graph_mode = 1;
     r->h->h2d(r->h->bstage, r->b.data(), sizeof(double) * r->n);
     if (r->x0.empty()) r->h->dzero(r->h->xstage, sizeof(double) * r->n);
     else r->h->h2d(r->h->xstage, r->x0.data(), sizeof(double) * r->n);
     r->job = gmres_job_start(r->h, r->h->bstage, r->h->xstage, s->cfg.restart, s->cfg.tol,
                              s->cfg.max_iters, pc);
+    // capture the cycle graph here, off the progress thread
+    gmres_job_prepare(r->job);
   } catch (const Error& e) {
     st = e.st;
   } catch (const std::bad_alloc&) {

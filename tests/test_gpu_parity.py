@@ -411,6 +411,26 @@ def test_full_size_iteration_counts_match_oracle(g, big, pc):
     assert abs(info.iters - int(ref["iters"])) <= 1, (info.iters, ref)
 
 
+@pytest.mark.parametrize("name", ["poisson3d_11", "random_5000", "rows_35", "elasticity_6"])
+def test_autotuned_shapes_keep_parity(g, name):
+    """After the autotuner re-tiles A and the triangles, sweeps still match
+    the oracle to 1e-12 and the chosen shapes are valid."""
+    A = MATS[name]
+    b, x0 = rhs_and_x0(A, 51)
+    h = g.gs2_setup(A)
+    h.autotune()
+    st = h.stats()
+    assert st["tpr_a"] in (1, 2, 4, 8, 16) and st["rpt_a"] in (1, 2)
+    assert st["rpt_a"] == 1 or st["tpr_a"] <= 2
+    for d in (0, 1, 2):
+        x = dev(x0)
+        g.gs2_apply(h, dev(b), x, 1, 2, 0.9, d)
+        assert rel(host(x), oracle.gs2(A, b, x0, 1, 2, 0.9, 1.0, d)) <= TOL
+    y = dev(np.zeros(len(b)))
+    g.gs2_spmv(h, dev(x0), y)
+    assert rel(host(y), oracle.spmv(A, x0)) <= TOL
+
+
 @pytest.mark.parametrize("pc", ["sgs2_1_2", "jr3", "gs_sym", "none"])
 def test_graph_and_eager_cycles_agree_bitwise(g, pc):
     """Arnoldi steps replayed as a captured CUDA graph give the same bits as
