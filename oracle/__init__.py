@@ -25,7 +25,7 @@ _lock = threading.Lock()
 _lib = None
 
 FORWARD, BACKWARD, SYMMETRIC = 0, 1, 2
-PC_NONE, PC_GS2, PC_JR, PC_GS = 0, 1, 2, 3
+PC_NONE, PC_GS2, PC_JR, PC_GS, PC_MTGS = 0, 1, 2, 3, 4
 
 
 class OracleError(RuntimeError):
@@ -81,8 +81,11 @@ def _load():
             lib.ora_cg.argtypes = csr + [P, P, D, I32, I32, I32, I32, D, D, I32,
                                          ctypes.POINTER(_Info)]
             lib.ora_gs2_compact.argtypes = csr + [P, P, I32, I32, I32]
+            lib.ora_coloring.argtypes = [I64, P, P, P]
+            lib.ora_mtgs.argtypes = csr + [P, P, I32, D, I32]
             for f in ("ora_diag", "ora_gs2", "ora_gs", "ora_jr", "ora_levels",
-                      "ora_precond", "ora_gmres", "ora_cg", "ora_gs2_compact"):
+                      "ora_precond", "ora_gmres", "ora_cg", "ora_gs2_compact",
+                      "ora_coloring", "ora_mtgs"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -161,6 +164,23 @@ def levels(A, lower=True):
     lev = np.zeros(n, dtype=np.int32)
     nlev = _load().ora_levels(n, _p(rp), _p(ci), 1 if lower else 0, _p(lev))
     return lev, int(nlev)
+
+
+def coloring(A):
+    """(colour per row, number of colours): first fit on the symmetrised pattern."""
+    n, rp, ci, _ = _csr(A)
+    col = np.zeros(n, dtype=np.int32)
+    nc = _load().ora_coloring(n, _p(rp), _p(ci), _p(col))
+    return col, int(nc)
+
+
+def mtgs(A, b, x, sweeps=1, omega=1.0, direction=FORWARD):
+    """Multicolour GS / SOR (rows colour by colour); returns the new x."""
+    n, rp, ci, va = _csr(A)
+    b, x = _vec(b, n), _vec(x, n)
+    _check(_load().ora_mtgs(n, _p(rp), _p(ci), _p(va), _p(b), _p(x), sweeps, omega,
+                            direction), "ora_mtgs")
+    return x
 
 
 def precond(A, v, kind=PC_GS2, outer=1, inner=1, omega=1.0, gamma=1.0,

@@ -162,6 +162,67 @@ int ora_gs(int64_t n, const int64_t* rp, const int32_t* ci, const double* va,
 }
 
 /* ------------------------------------------------------------------ */
+/* Multicolour GS (Sec. 5.1.2): greedy colouring, then the sequential   */
+/* row update visiting the rows colour by colour.                       */
+/* ------------------------------------------------------------------ */
+
+int ora_coloring(int64_t n, const int64_t* rp, const int32_t* ci, int32_t* color) {
+  /* transpose pattern: for every row j, the rows i with a_ij != 0 */
+  int64_t* tp = calloc((size_t)n + 1, sizeof(int64_t));
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) tp[ci[k] + 1]++;
+  for (int64_t j = 0; j < n; ++j) tp[j + 1] += tp[j];
+  int64_t* fill = malloc(((size_t)n + 1) * sizeof(int64_t));
+  memcpy(fill, tp, ((size_t)n + 1) * sizeof(int64_t));
+  int64_t* ti = malloc(((size_t)rp[n] + 1) * sizeof(int64_t));
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) ti[fill[ci[k]]++] = i;
+  /* first fit: forbidden[c] == i marks colour c as used by a neighbour of i */
+  int64_t* forbidden = malloc(((size_t)n + 1) * sizeof(int64_t));
+  for (int64_t c = 0; c <= n; ++c) forbidden[c] = -1;
+  int32_t ncolors = 0;
+  for (int64_t i = 0; i < n; ++i) color[i] = -1;
+  for (int64_t i = 0; i < n; ++i) {
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k)
+      if (ci[k] != i && color[ci[k]] >= 0) forbidden[color[ci[k]]] = i;
+    for (int64_t k = tp[i]; k < tp[i + 1]; ++k)
+      if (ti[k] != i && color[ti[k]] >= 0) forbidden[color[ti[k]]] = i;
+    int32_t c = 0;
+    while (forbidden[c] == i) ++c;
+    color[i] = c;
+    if (c + 1 > ncolors) ncolors = c + 1;
+  }
+  free(tp); free(fill); free(ti); free(forbidden);
+  return ncolors;
+}
+
+int ora_mtgs(int64_t n, const int64_t* rp, const int32_t* ci, const double* va,
+             const double* b, double* x, int sweeps, double omega, int dir) {
+  if (n < 0 || sweeps < 0) return 1;
+  if (dir != ORA_FORWARD && dir != ORA_BACKWARD && dir != ORA_SYMMETRIC)
+    return 1;
+  if (n == 0) return 0;
+  double* d = malloc((size_t)n * sizeof(double));
+  int st = ora_diag(n, rp, ci, va, d);
+  free(d);
+  if (st) return st;
+  int32_t* color = malloc((size_t)n * sizeof(int32_t));
+  const int32_t nc = ora_coloring(n, rp, ci, color);
+  for (int s = 0; s < sweeps; ++s) {
+    if (dir == ORA_FORWARD || dir == ORA_SYMMETRIC)
+      for (int32_t c = 0; c < nc; ++c)
+        for (int64_t i = 0; i < n; ++i)
+          if (color[i] == c) gs_row(i, rp, ci, va, b, x, omega);
+    if (dir == ORA_BACKWARD || dir == ORA_SYMMETRIC)
+      for (int32_t c = nc - 1; c >= 0; --c)
+        for (int64_t i = 0; i < n; ++i)
+          if (color[i] == c) gs_row(i, rp, ci, va, b, x, omega);
+  }
+  free(color);
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
 /* Jacobi-Richardson: GS2 with zero inner sweeps (Sec. 3), damped.      */
 /* ------------------------------------------------------------------ */
 
@@ -223,6 +284,8 @@ int ora_precond(int64_t n, const int64_t* rp, const int32_t* ci,
       return ora_jr(n, rp, ci, va, v, z, outer, omega);
     case ORA_PC_GS:
       return ora_gs(n, rp, ci, va, v, z, outer, omega, dir);
+    case ORA_PC_MTGS:
+      return ora_mtgs(n, rp, ci, va, v, z, outer, omega, dir);
     default:
       return 1;
   }

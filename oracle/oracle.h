@@ -25,7 +25,8 @@ extern "C" {
 #endif
 
 enum { ORA_FORWARD = 0, ORA_BACKWARD = 1, ORA_SYMMETRIC = 2 };
-enum { ORA_PC_NONE = 0, ORA_PC_GS2 = 1, ORA_PC_JR = 2, ORA_PC_GS = 3 };
+enum { ORA_PC_NONE = 0, ORA_PC_GS2 = 1, ORA_PC_JR = 2, ORA_PC_GS = 3,
+       ORA_PC_MTGS = 4 };
 
 typedef struct {
   int iters;          /* total Arnoldi steps over all cycles */
@@ -71,9 +72,22 @@ int ora_jr(int64_t n, const int64_t* rp, const int32_t* ci, const double* va,
 int ora_levels(int64_t n, const int64_t* rp, const int32_t* ci, int lower,
                int32_t* level);
 
+/* First-fit colouring of the symmetrised pattern of A in natural row order:
+ * rows i and j with a_ij != 0 or a_ji != 0 (i != j) get different colours.
+ * Returns the number of colours. */
+int ora_coloring(int64_t n, const int64_t* rp, const int32_t* ci, int32_t* color);
+
+/* Multicolour GS / SOR (Sec. 5.1.2, multi-threaded GS): the compact row
+ * update of ora_gs applied colour by colour, colours ascending (forward) or
+ * descending (backward), rows of one colour in natural order; symmetric =
+ * forward then backward.  x in place. */
+int ora_mtgs(int64_t n, const int64_t* rp, const int32_t* ci, const double* va,
+             const double* b, double* x, int sweeps, double omega, int dir);
+
 /* Apply a preconditioner from a zero start: z = M^{-1} v.
  * kind: ORA_PC_NONE (z = v), ORA_PC_GS2, ORA_PC_JR (outer = sweeps),
- * ORA_PC_GS (exact GS, outer = sweeps). */
+ * ORA_PC_GS (exact GS, outer = sweeps), ORA_PC_MTGS (multicolour GS,
+ * outer = sweeps). */
 int ora_precond(int64_t n, const int64_t* rp, const int32_t* ci,
                 const double* va, const double* v, double* z, int kind,
                 int outer, int inner, double omega, double gamma, int dir);

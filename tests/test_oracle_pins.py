@@ -279,6 +279,79 @@ def test_levels_equal_longest_path_brute_force():
 
 
 # ---------------------------------------------------------------------------
+# Multicolour GS (Sec. 5.1.2) against a dense solve in the colour ordering
+# ---------------------------------------------------------------------------
+
+def test_coloring_red_black_on_stencils_and_valid_on_random():
+    N = 7
+    col, nc = oracle.coloring(P.poisson2d_matrix(N))
+    i = np.arange(N * N)
+    assert nc == 2 and np.array_equal(col, (i % N + i // N) % 2)
+    col, nc = oracle.coloring(P.poisson3d_matrix(5))
+    i = np.arange(125)
+    assert nc == 2 and np.array_equal(col, (i % 5 + (i // 5) % 5 + i // 25) % 2)
+    A = P.random_csr(150, 9, mean_offdiag=4.0)
+    rp, ci, _ = A
+    col, nc = oracle.coloring(A)
+    G = nx.Graph()
+    G.add_nodes_from(range(150))
+    for r in range(150):
+        for k in range(rp[r], rp[r + 1]):
+            if ci[k] != r:
+                G.add_edge(r, int(ci[k]))
+    assert all(col[u] != col[v] for u, v in G.edges)
+    # first fit in natural order: every colour c > 0 of row i has an earlier
+    # neighbour of each smaller colour, and the count equals the largest + 1
+    for v in range(150):
+        seen = {int(col[u]) for u in G.neighbors(v) if u < v}
+        assert set(range(col[v])) <= seen
+    assert nc == col.max() + 1
+    greedy = nx.greedy_color(G, strategy=lambda g, c: range(150))
+    assert [greedy[v] for v in range(150)] == col.tolist()
+
+
+@pytest.mark.parametrize("omega", [1.0, 0.8])
+def test_mtgs_equals_dense_sor_in_colour_order(omega):
+    """MT-GS is SOR on P A P^T with rows sorted (stably) by colour."""
+    A = P.random_csr(60, 4, mean_offdiag=3.0)
+    M = P.csr_to_dense(A)
+    col, nc = oracle.coloring(A)
+    assert nc >= 3
+    perm = np.argsort(col, kind="stable")
+    Mp = M[np.ix_(perm, perm)]
+    D, L, U = np.diag(np.diag(Mp)), np.tril(Mp, -1), np.triu(Mp, 1)
+    rng = np.random.default_rng(3)
+    b, x0 = rng.standard_normal(60), rng.standard_normal(60)
+    bp, xp = b[perm], x0[perm]
+    fwd = xp + omega * np.linalg.solve(D + omega * L, bp - Mp @ xp)
+    bwd = xp + omega * np.linalg.solve(D + omega * U, bp - Mp @ xp)
+    sym = fwd + omega * np.linalg.solve(D + omega * U, bp - Mp @ fwd)
+    for d, want in ((oracle.FORWARD, fwd), (oracle.BACKWARD, bwd),
+                    (oracle.SYMMETRIC, sym)):
+        got = oracle.mtgs(A, b, x0, 1, omega, d)
+        assert np.allclose(got[perm], want, rtol=1e-12, atol=1e-12)
+
+
+def test_mtgs_red_black_poisson_is_two_jacobi_half_steps():
+    """On a red-black grid each colour's rows see only the other colour."""
+    N = 6
+    A = P.poisson2d_matrix(N)
+    M = P.csr_to_dense(A)
+    col, _ = oracle.coloring(A)
+    rng = np.random.default_rng(8)
+    b, x = rng.standard_normal(N * N), rng.standard_normal(N * N)
+    y = x.copy()
+    for c in (0, 1):
+        m = col == c
+        y[m] = (b[m] - (M[m] @ y - np.diag(M)[m] * y[m])) / np.diag(M)[m]
+    assert np.allclose(oracle.mtgs(A, b, x, 1, 1.0, oracle.FORWARD), y,
+                       rtol=1e-13, atol=1e-13)
+    # a multicolour preconditioner from zero equals one sweep from zero
+    z = oracle.precond(A, b, kind=oracle.PC_MTGS, outer=1, omega=1.0)
+    assert np.allclose(z, oracle.mtgs(A, b, np.zeros(N * N), 1, 1.0), atol=0)
+
+
+# ---------------------------------------------------------------------------
 # GMRES against the Krylov least-squares minimiser
 # ---------------------------------------------------------------------------
 
