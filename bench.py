@@ -558,6 +558,7 @@ def comparisons(gs2, torch, pr, stream, b):
         "sgs2_1_1_fp32": gs2.params("gs2", 1, 1, direction="symmetric", precision="fp32"),
         "sgs2_1_1_fp16": gs2.params("gs2", 1, 1, direction="symmetric", precision="fp16"),
         "gs_levels_sym": gs2.params("gs", 1, direction="symmetric"),
+        "mtsgs": gs2.params("mtgs", 1, direction="symmetric"),
         "jr3_w1.0": gs2.params("jr", 3, omega=1.0),
         "jr3_w0.8": gs2.params("jr", 3, omega=0.8),
     }

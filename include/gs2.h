@@ -72,7 +72,8 @@ typedef enum {
   GS2_PC_NONE = 0, /* identity */
   GS2_PC_GS2 = 1,  /* two-stage GS, Eq. (4)-(7) with damping */
   GS2_PC_JR = 2,   /* damped Jacobi-Richardson, `outer` sweeps */
-  GS2_PC_GS = 3    /* exact GS/SOR, level-scheduled, `outer` sweeps */
+  GS2_PC_GS = 3,   /* exact GS/SOR, level-scheduled, `outer` sweeps */
+  GS2_PC_MTGS = 4  /* multicolour GS/SOR, `outer` sweeps (Sec. 5.1.2) */
 } gs2_pc_kind;
 
 /* Relaxation / preconditioner parameters in the paper's notation:
@@ -107,6 +108,7 @@ typedef struct {
   int64_t device_bytes;           /* device memory held by the handle */
   int tpr_a, tpr_tri;             /* lanes per row of the tile kernels (A, D^-1 L) */
   int rpt_a, rpt_tri;             /* rows per lane group of the tile kernels */
+  int colors;                     /* 0 until a multicolour call */
 } gs2_handle_stats;
 
 typedef struct gs2_handle gs2_handle;
@@ -193,6 +195,21 @@ gs2_status gs2_apply_noalloc(int64_t n, const int64_t* rowptr, const int32_t* co
 gs2_status gs_apply(gs2_handle* h, const double* b, double* x, int sweeps,
                     double omega, int direction);
 
+/* Multicolour GS / SOR baseline (Sec. 5.1.2, multi-threaded GS): rows are
+ * coloured on the host on the first call, first fit in natural row order
+ * on the symmetrised pattern (rows i and j differ in colour whenever a_ij
+ * or a_ji is stored, i != j); the paper's greedy colouring is parallel and
+ * leaves the order open, this one is deterministic.  A forward sweep
+ * relaxes the colours in ascending order, each colour in one parallel
+ * launch with
+ *   x_i <- (1 - omega) x_i + omega (b_i - sum_{j != i} a_ij x_j) / a_ii,
+ * a backward sweep takes the colours in descending order, and symmetric is
+ * forward then backward.  Equal to SOR on A with its rows and columns
+ * permuted by colour.  x in/out.  Errors: INVALID_ARG (sweeps < 0,
+ * omega <= 0, bad direction), OOM and CUDA on the first call. */
+gs2_status mtgs_apply(gs2_handle* h, const double* b, double* x, int sweeps,
+                      double omega, int direction);
+
 /* Damped JR baseline: x += omega D^{-1} (b - A x), `sweeps` times (Sec. 3,
  * zero-inner-sweep case). x in/out. */
 gs2_status jr_apply(gs2_handle* h, const double* b, double* x, int sweeps,
@@ -216,7 +233,7 @@ gs2_status gmres_solve(gs2_handle* h, const double* b, double* x, int restart,
 
 /* Preconditioned CG for SPD A (Sec. 6.2 runs CG with SGS2), same
  * conventions as gmres_solve; the preconditioner must be symmetric
- * (GS2/GS with direction SYMMETRIC, JR, or none). */
+ * (GS2/GS/MTGS with direction SYMMETRIC, JR, or none). */
 gs2_status cg_solve(gs2_handle* h, const double* b, double* x, double tol,
                     int max_iters, const gs2_params* precond,
                     gs2_solve_info* info);

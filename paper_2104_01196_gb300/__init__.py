@@ -18,9 +18,9 @@ import numpy as np
 
 __all__ = [
     "GS2Error", "Params", "SolveInfo", "Handle", "load", "gs2_setup", "gs2_apply",
-    "gs2_apply_ex", "gs_apply", "jr_apply", "gs2_spmv", "gmres_solve", "cg_solve",
+    "gs2_apply_ex", "gs_apply", "mtgs_apply", "jr_apply", "gs2_spmv", "gmres_solve", "cg_solve",
     "gs2_batch_solve", "params", "FORWARD", "BACKWARD", "SYMMETRIC", "FP64", "FP32",
-    "FP16_ROWSCALED", "PC_NONE", "PC_GS2", "PC_JR", "PC_GS", "NONCOMPACT", "COMPACT",
+    "FP16_ROWSCALED", "PC_NONE", "PC_GS2", "PC_JR", "PC_GS", "PC_MTGS", "NONCOMPACT", "COMPACT",
     "STATUS",
 ]
 
@@ -29,14 +29,14 @@ LIB_PATH = os.path.join(_HERE, "libgs2.so")
 
 FORWARD, BACKWARD, SYMMETRIC = 0, 1, 2
 FP64, FP32, FP16_ROWSCALED = 0, 1, 2
-PC_NONE, PC_GS2, PC_JR, PC_GS = 0, 1, 2, 3
+PC_NONE, PC_GS2, PC_JR, PC_GS, PC_MTGS = 0, 1, 2, 3, 4
 NONCOMPACT, COMPACT = 0, 1
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "ZERO_DIAGONAL", 3: "OOM", 4: "CUDA",
           5: "NOT_CONVERGED", 6: "BREAKDOWN", 7: "NAN", 8: "TIMEOUT", 9: "BUSY",
           10: "NOT_FOUND"}
 _DIR = {"forward": FORWARD, "backward": BACKWARD, "symmetric": SYMMETRIC}
 _PREC = {"fp64": FP64, "fp32": FP32, "fp16": FP16_ROWSCALED}
-_KIND = {"none": PC_NONE, "gs2": PC_GS2, "jr": PC_JR, "gs": PC_GS}
+_KIND = {"none": PC_NONE, "gs2": PC_GS2, "jr": PC_JR, "gs": PC_GS, "mtgs": PC_MTGS}
 
 
 class GS2Error(RuntimeError):
@@ -62,7 +62,7 @@ class _Stats(ctypes.Structure):
                 ("nnz_upper", ctypes.c_int64), ("levels_lower", ctypes.c_int),
                 ("levels_upper", ctypes.c_int), ("device_bytes", ctypes.c_int64),
                 ("tpr_a", ctypes.c_int), ("tpr_tri", ctypes.c_int),
-                ("rpt_a", ctypes.c_int), ("rpt_tri", ctypes.c_int)]
+                ("rpt_a", ctypes.c_int), ("rpt_tri", ctypes.c_int), ("colors", ctypes.c_int)]
 
 
 class _KStat(ctypes.Structure):
@@ -124,6 +124,7 @@ def load(path: str | None = None):
         "gs2_apply": [P, P, P, I, I, D, I],
         "gs2_apply_ex": [P, P, P, ctypes.POINTER(Params)],
         "gs_apply": [P, P, P, I, D, I],
+        "mtgs_apply": [P, P, P, I, D, I],
         "jr_apply": [P, P, P, I, D],
         "gs2_spmv": [P, P, P],
         "gmres_solve": [P, P, P, I, D, I, ctypes.POINTER(Params), ctypes.POINTER(_Info)],
@@ -333,6 +334,14 @@ def gs_apply(h, b, x, sweeps=1, omega=1.0, direction=FORWARD):
     px, _kx = _ptr(x, True)
     d = _DIR[direction] if isinstance(direction, str) else direction
     _check(load().gs_apply(h.ptr, pb, px, sweeps, omega, d))
+    return x
+
+
+def mtgs_apply(h, b, x, sweeps=1, omega=1.0, direction=FORWARD):
+    pb, _kb = _ptr(b)
+    px, _kx = _ptr(x, True)
+    d = _DIR[direction] if isinstance(direction, str) else direction
+    _check(load().mtgs_apply(h.ptr, pb, px, sweeps, omega, d))
     return x
 
 

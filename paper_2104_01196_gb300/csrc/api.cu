@@ -344,6 +344,69 @@ void ensure_levels(gs2_handle* h) {
   h->levels_ready = true;
 }
 
+// First-fit colouring in natural row order of the symmetrised pattern
+// (rows i, j adjacent if a_ij or a_ji is stored, i != j), then one matrix
+// per colour: its rows ascending, their off-diagonal entries prescaled by
+// D^{-1} (the L part, then the U part of each row).  Only neighbours j < i
+// are coloured when row i is, so the earlier neighbours are the columns of
+// row i of L and the rows j < i whose U row holds column i.
+void ensure_colors(gs2_handle* h) {
+  if (h->colors_ready) return;
+  gs2_host_side* hs = host_side(h);
+  const int n = (int)h->n;
+  const HostTri& L = hs->L;
+  const HostTri& U = hs->U;
+  std::vector<int> utp(n + 1, 0), uti(U.ci.size());
+  for (int k = 0; k < (int)U.ci.size(); ++k) utp[U.ci[k] + 1]++;
+  for (int i = 0; i < n; ++i) utp[i + 1] += utp[i];
+  {
+    std::vector<int> fill(utp.begin(), utp.end() - 1);
+    for (int j = 0; j < n; ++j)
+      for (int k = U.rp[j]; k < U.rp[j + 1]; ++k) uti[fill[U.ci[k]]++] = j;
+  }
+  std::vector<int> color(n, -1), mark(n + 1, -1);
+  int nc = 0;
+  for (int i = 0; i < n; ++i) {
+    for (int k = L.rp[i]; k < L.rp[i + 1]; ++k) mark[color[L.ci[k]]] = i;
+    for (int k = utp[i]; k < utp[i + 1]; ++k) mark[color[uti[k]]] = i;
+    int c = 0;
+    while (mark[c] == i) ++c;
+    color[i] = c;
+    nc = std::max(nc, c + 1);
+  }
+  h->colors.assign(nc, DevCsr{});
+  h->color_rows.assign(nc, nullptr);
+  std::vector<std::vector<int>> rows(nc);
+  for (int i = 0; i < n; ++i) rows[color[i]].push_back(i);
+  for (int c = 0; c < nc; ++c) {
+    const std::vector<int>& rr = rows[c];
+    std::vector<int> rp(rr.size() + 1, 0), ci;
+    std::vector<double> va;
+    for (size_t q = 0; q < rr.size(); ++q) {
+      const int i = rr[q];
+      for (int k = L.rp[i]; k < L.rp[i + 1]; ++k) {
+        ci.push_back(L.ci[k]);
+        va.push_back(L.va[k]);
+      }
+      for (int k = U.rp[i]; k < U.rp[i + 1]; ++k) {
+        ci.push_back(U.ci[k]);
+        va.push_back(U.va[k]);
+      }
+      rp[q + 1] = (int)ci.size();
+    }
+    upload_csr(h, h->colors[c], (int)rr.size(), rp, ci, va);
+    h->color_rows[c] = (int*)h->dalloc(sizeof(int) * std::max<size_t>(rr.size(), 1));
+    h->h2d(h->color_rows[c], rr.data(), sizeof(int) * rr.size());
+  }
+  h->colors_ready = true;
+}
+
+void ensure_precond(gs2_handle* h, const gs2_params* p) {
+  if (!p) return;
+  if (p->kind == GS2_PC_GS) ensure_levels(h);
+  if (p->kind == GS2_PC_MTGS) ensure_colors(h);
+}
+
 // ---------------------------------------------------------------------------
 // autotuner: tile shape (lanes per row K, rows per lane group RPT) per matrix
 // ---------------------------------------------------------------------------
@@ -436,7 +499,7 @@ struct Staged {
 
 static void check_params(const gs2_params* p) {
   if (!p) return;
-  if (p->kind < GS2_PC_NONE || p->kind > GS2_PC_GS)
+  if (p->kind < GS2_PC_NONE || p->kind > GS2_PC_MTGS)
     GS2_THROW(GS2_ERR_INVALID_ARG, "unknown preconditioner kind");
   if (p->kind == GS2_PC_NONE) return;
   if (p->outer < 1 || p->outer > 1000) GS2_THROW(GS2_ERR_INVALID_ARG, "outer sweeps < 1");
@@ -681,6 +744,7 @@ gs2_status gs2_get_stats(const gs2_handle* h, gs2_handle_stats* out) {
   out->tpr_tri = h->L.tpr;
   out->rpt_a = h->A.rpt;
   out->rpt_tri = h->L.rpt;
+  out->colors = h->colors_ready ? (int)h->colors.size() : 0;
   return GS2_OK;
 }
 
@@ -725,6 +789,21 @@ gs2_status gs_apply(gs2_handle* h, const double* b, double* x, int sweeps, doubl
   API_END
 }
 
+gs2_status mtgs_apply(gs2_handle* h, const double* b, double* x, int sweeps, double omega,
+                      int direction) {
+  if (!h || (h->n && (!b || !x))) return GS2_ERR_INVALID_ARG;
+  API_BEGIN
+  if (sweeps < 0 || !(omega > 0.0) || direction < 0 || direction > 2)
+    GS2_THROW(GS2_ERR_INVALID_ARG, "bad sweeps/omega/direction");
+  if (sweeps == 0 || h->n == 0) return GS2_OK;
+  ensure_colors(h);
+  Staged s(h, b, x, true);
+  mtgs_relax(h, s.b, s.x, sweeps, omega, direction);
+  s.finish();
+  return GS2_OK;
+  API_END
+}
+
 gs2_status jr_apply(gs2_handle* h, const double* b, double* x, int sweeps, double omega) {
   if (!h || (h->n && (!b || !x))) return GS2_ERR_INVALID_ARG;
   API_BEGIN
@@ -756,7 +835,7 @@ gs2_status gmres_solve(gs2_handle* h, const double* b, double* x, int restart, d
     GS2_THROW(GS2_ERR_INVALID_ARG, "restart must be in [1, 64], tol >= 0, max_iters >= 0");
   check_params(precond);
   if (precond && precond->kind == GS2_PC_GS2) ensure_precision(h, precond->precision);
-  if (precond && precond->kind == GS2_PC_GS) ensure_levels(h);
+  ensure_precond(h, precond);
   Staged s(h, b, x, true);
   gs2_status st = gmres_run(h, s.b, s.x, restart, tol, max_iters, precond, info);
   s.finish();
@@ -771,7 +850,7 @@ gs2_status cg_solve(gs2_handle* h, const double* b, double* x, double tol, int m
   if (!(tol >= 0.0) || max_iters < 0) GS2_THROW(GS2_ERR_INVALID_ARG, "tol/max_iters");
   check_params(precond);
   if (precond && precond->kind == GS2_PC_GS2) ensure_precision(h, precond->precision);
-  if (precond && precond->kind == GS2_PC_GS) ensure_levels(h);
+  ensure_precond(h, precond);
   Staged s(h, b, x, true);
   gs2_status st = cg_run(h, s.b, s.x, tol, max_iters, precond, info);
   s.finish();
@@ -794,7 +873,7 @@ gs2_status gs2_batch_solve(gs2_handle* const* hs, const double* const* bs, doubl
     for (int k = 0; k < i; ++k)
       if (hs[k] == hs[i]) GS2_THROW(GS2_ERR_INVALID_ARG, "a handle appears twice in a batch");
     if (precond && precond->kind == GS2_PC_GS2) ensure_precision(hs[i], precond->precision);
-    if (precond && precond->kind == GS2_PC_GS) ensure_levels(hs[i]);
+    ensure_precond(hs[i], precond);
   }
   return gmres_batch(hs, bs, xs, count, restart, tol, max_iters, precond, infos);
   API_END

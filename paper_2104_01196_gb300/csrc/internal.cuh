@@ -116,6 +116,12 @@ struct gs2_handle {
   int* lev_rows_L = nullptr;
   int* lev_rows_U = nullptr;
 
+  // multicolour GS (lazy): colour c holds the rows color_rows[c] (ascending)
+  // and their off-diagonal entries prescaled by D^{-1}, as its own matrix
+  bool colors_ready = false;
+  std::vector<gs2::DevCsr> colors;
+  std::vector<int*> color_rows;
+
   // Krylov workspace (lazy, grows with restart)
   int kry_m = 0;
   double *V = nullptr, *w = nullptr, *H = nullptr, *hbuf = nullptr;
@@ -202,6 +208,11 @@ void launch_level(gs2_handle* h, const DevCsr& T, const int* rows, int r0,
                   int r1, const double* rhat, double* g, double* x,
                   double omega, const int* skip);
 
+// one colour of a multicolour GS sweep: for each row i of the colour matrix
+// C (original row rows[i]), x_r = (1 - omega) x_r + omega (bhat_r - (C x)_i)
+void launch_color(gs2_handle* h, const DevCsr& C, const int* rows, const double* bhat,
+                  double* x, double omega, const int* skip);
+
 void launch_axpy(gs2_handle* h, double* y, double a, const double* x,
                  const int* skip);
 void launch_copy(gs2_handle* h, double* dst, const double* src);
@@ -223,7 +234,12 @@ void gs_relax(gs2_handle* h, const double* b, double* x, int sweeps,
               double omega, int direction);
 void jr_relax(gs2_handle* h, const double* b, double* x, int sweeps,
               double omega);
+void mtgs_relax(gs2_handle* h, const double* b, double* x, int sweeps,
+                double omega, int direction);
 void ensure_levels(gs2_handle* h);
+void ensure_colors(gs2_handle* h);
+// level sets or colours a preconditioner needs, built on first use
+void ensure_precond(gs2_handle* h, const gs2_params* p);
 void ensure_precision(gs2_handle* h, int prec);
 
 // solvers (krylov.cu)

@@ -384,6 +384,35 @@ struct EpiInner {
   }
 };
 
+// one colour of multicolour GS (Sec. 5.1.2): the colour matrix holds only
+// off-diagonal entries prescaled by D^{-1}, none of them inside the colour,
+// so every x_j gathered here belongs to another colour and is not written
+// by this launch; row i of the colour is row rows[i] of A.
+//   x_r = (1 - omega) x_r + omega (bhat_r - sum_j (a_rj / a_rr) x_j)
+template <bool DAMPED>
+struct EpiColor {
+  const int* __restrict__ rows;
+  const double* __restrict__ bhat;
+  double* x;
+  double omega;
+  struct Pre {
+    int r;
+    double bh, xr;
+  };
+  __device__ Pre pre(int i) const {
+    Pre p;
+    p.r = rows[i];
+    p.bh = bhat[p.r];
+    p.xr = DAMPED ? x[p.r] : 0.0;
+    return p;
+  }
+  __device__ double gather(int c) const { return __ldg(x + c); }
+  __device__ void finish(int, double s, const Pre& p) const {
+    const double gs = p.bh - s;
+    x[p.r] = DAMPED ? p.xr + omega * (gs - p.xr) : gs;
+  }
+};
+
 // ---------------------------------------------------------------------------
 // launch plumbing
 // ---------------------------------------------------------------------------
@@ -553,6 +582,21 @@ void launch_inner(gs2_handle* h, const DevCsr& T, int prec, const void* rhat,
                                             (float)gamma, omega, mode};
       dispatch<__half>(h, T, T.va16, e, skip);
     }
+  }
+}
+
+void launch_color(gs2_handle* h, const DevCsr& C, const int* rows, const double* bhat,
+                  double* x, double omega, const int* skip) {
+  const bool damped = omega != 1.0;
+  // colour matrix once; per row its index, bhat, the written x and (lower
+  // bound) one gathered x of another colour; damping re-reads x_r
+  KernelTimer tm(h, "color", bytes_csr(C, 8) + C.n * (28.0 + (damped ? 8.0 : 0.0)));
+  if (damped) {
+    EpiColor<true> e{rows, bhat, x, omega};
+    dispatch<double>(h, C, C.va, e, skip);
+  } else {
+    EpiColor<false> e{rows, bhat, x, omega};
+    dispatch<double>(h, C, C.va, e, skip);
   }
 }
 

@@ -165,6 +165,33 @@ void gs_relax(gs2_handle* h, const double* b, double* x, int sweeps, double omeg
 }
 
 // ---------------------------------------------------------------------------
+// multicolour GS / SOR baseline (Sec. 5.1.2): the compact row update of
+// exact GS, colour by colour (ascending forward, descending backward); rows
+// of one colour are independent, so each colour is one parallel launch.
+// bhat = D^{-1} b must be in h->rhat.
+// ---------------------------------------------------------------------------
+
+static void mtgs_half(gs2_handle* h, bool forward, double* x, double omega,
+                      const int* skip) {
+  const int nc = (int)h->colors.size();
+  for (int s = 0; s < nc; ++s) {
+    const int c = forward ? s : nc - 1 - s;
+    launch_color(h, h->colors[c], h->color_rows[c], h->rhat, x, omega, skip);
+  }
+}
+
+void mtgs_relax(gs2_handle* h, const double* b, double* x, int sweeps, double omega,
+                int direction) {
+  launch_prep_rhat(h, b, h->rhat, nullptr, nullptr);
+  for (int s = 0; s < sweeps; ++s) {
+    if (direction == GS2_FORWARD || direction == GS2_SYMMETRIC)
+      mtgs_half(h, true, x, omega, nullptr);
+    if (direction == GS2_BACKWARD || direction == GS2_SYMMETRIC)
+      mtgs_half(h, false, x, omega, nullptr);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // damped JR baseline, ping-pong between x and a resident temporary
 // ---------------------------------------------------------------------------
 
@@ -184,7 +211,8 @@ void jr_relax(gs2_handle* h, const double* b, double* x, int sweeps, double omeg
 // ---------------------------------------------------------------------------
 
 bool precond_wants_rhat(const gs2_params* p) {
-  return p && (p->kind == GS2_PC_GS2 || p->kind == GS2_PC_JR || p->kind == GS2_PC_GS);
+  return p && (p->kind == GS2_PC_GS2 || p->kind == GS2_PC_JR || p->kind == GS2_PC_GS ||
+               p->kind == GS2_PC_MTGS);
 }
 
 void* precond_rhat_buffer(gs2_handle* h, const gs2_params* p) {
@@ -231,6 +259,17 @@ void precond_apply(gs2_handle* h, const gs2_params* p, const double* v, double* 
       xout = (xout == h->t) ? z : h->t;
     }
     if (xin != z) launch_copy_skip(h, z, xin, skip);
+    return;
+  }
+  if (p->kind == GS2_PC_MTGS) {
+    if (!rhat_ready) launch_prep_rhat(h, v, h->rhat, nullptr, skip);
+    launch_fill(h, z, 0.0, skip);
+    for (int s = 0; s < p->outer; ++s) {
+      if (p->direction == GS2_FORWARD || p->direction == GS2_SYMMETRIC)
+        mtgs_half(h, true, z, p->omega, skip);
+      if (p->direction == GS2_BACKWARD || p->direction == GS2_SYMMETRIC)
+        mtgs_half(h, false, z, p->omega, skip);
+    }
     return;
   }
   // exact GS: the first half sweep from z = 0 solves with r = v

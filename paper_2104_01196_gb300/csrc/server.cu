@@ -49,8 +49,9 @@ struct Request {
 
 // Device bytes a request of this size holds once admitted: the matrix, its
 // two prescaled triangles, the resident vectors, the Krylov basis and the
-// optional lower-precision and level-set storage (mirrors setup_handle,
-// ensure_precision, ensure_levels and ensure_krylov).
+// optional lower-precision, level-set and colour storage (mirrors
+// setup_handle, ensure_precision, ensure_levels, ensure_colors and
+// ensure_krylov).
 static int64_t footprint(const gs2_server_cfg& c, int64_t n, int64_t nnz) {
   const int64_t off = std::max<int64_t>(nnz - n, 0);
   const int64_t m = std::max(c.restart, 1);
@@ -64,6 +65,10 @@ static int64_t footprint(const gs2_server_cfg& c, int64_t n, int64_t nnz) {
     if (c.precond.precision == GS2_FP16_ROWSCALED) b += 2 * off + 8 * n + 12 * n;
   }
   if (c.has_precond && c.precond.kind == GS2_PC_GS) b += 8 * n;
+  // colour matrices: the off-diagonal entries again, row lists, row
+  // pointers and tile descriptors, plus per-colour allocation slack
+  if (c.has_precond && c.precond.kind == GS2_PC_MTGS)
+    b += 12 * off + 8 * n + 4 * (n / 16 + 16) * 16 + (1 << 18);
   return b + (1 << 20);
 }
 
@@ -132,7 +137,7 @@ static void prepare(gs2_server* s, Request* r) {
     if (pc && pc->kind == GS2_PC_GS2) prec = 1u << pc->precision;
     r->h = setup_handle(r->n, r->nnz, r->rp.data(), r->ci.data(), r->va.data(), 0, prec,
                         r->stream, true);
-    if (pc && pc->kind == GS2_PC_GS) ensure_levels(r->h);
+    ensure_precond(r->h, pc);
     // every request replays its cycles as a graph captured by this thread,
     // so the single progress thread only ever launches whole cycles
     r->h->graph_mode = 1;
@@ -280,7 +285,7 @@ gs2_status gs2_server_create(const gs2_server_cfg* cfg, gs2_server** out) {
   }
   if (cfg->has_precond) {
     const gs2_params& p = cfg->precond;
-    if (p.kind < GS2_PC_NONE || p.kind > GS2_PC_GS || p.outer < 1 || p.inner < 0 ||
+    if (p.kind < GS2_PC_NONE || p.kind > GS2_PC_MTGS || p.outer < 1 || p.inner < 0 ||
         !(p.omega > 0.0) || !(p.gamma > 0.0) || p.direction < 0 || p.direction > 2 ||
         p.precision < 0 || p.precision > 2) {
       set_error("bad preconditioner parameters");

@@ -29,6 +29,8 @@ CASES = [
      dict(pc_kind=oracle.PC_GS2, pc_inner=3, pc_direction=oracle.SYMMETRIC)),
     ("poisson3d_128_gmres30_sgs_exact", lambda: P.poisson3d(128),
      dict(pc_kind=oracle.PC_GS, pc_direction=oracle.SYMMETRIC)),
+    ("poisson3d_128_gmres30_mtsgs", lambda: P.poisson3d(128),
+     dict(pc_kind=oracle.PC_MTGS, pc_direction=oracle.SYMMETRIC)),
     ("poisson3d_128_gmres30_jr3_w1.0", lambda: P.poisson3d(128),
      dict(pc_kind=oracle.PC_JR, pc_outer=3, pc_omega=1.0)),
     ("poisson3d_128_gmres30_jr3_w0.8", lambda: P.poisson3d(128),

@@ -139,6 +139,22 @@ def test_level_scheduled_gs(g, name, direction):
 
 
 @pytest.mark.parametrize("name", list(MATS))
+@pytest.mark.parametrize("direction", [0, 1, 2])
+def test_multicolor_gs(g, name, direction):
+    """Multicolour GS/SOR (Sec. 5.1.2): same colouring as the oracle's first
+    fit, sweeps equal to the oracle's colour-by-colour recurrence."""
+    A = MATS[name]
+    b, x0 = rhs_and_x0(A, 29)
+    h = g.gs2_setup(A)
+    assert h.stats()["colors"] == 0
+    for sweeps, omega in ((2, 1.0), (1, 0.7), (2, 1.2)):
+        x = dev(x0)
+        g.mtgs_apply(h, dev(b), x, sweeps, omega, direction)
+        assert rel(host(x), oracle.mtgs(A, b, x0, sweeps, omega, direction)) <= TOL
+    assert h.stats()["colors"] == oracle.coloring(A)[1]
+
+
+@pytest.mark.parametrize("name", list(MATS))
 def test_jr(g, name):
     A = MATS[name]
     b, x0 = rhs_and_x0(A, 19)
@@ -197,6 +213,10 @@ PCS = {
                                                       pc_omega=0.8)),
     "gs_sym": (dict(kind="gs", outer=1, direction="symmetric"),
                dict(pc_kind=oracle.PC_GS, pc_direction=2)),
+    "mtsgs": (dict(kind="mtgs", outer=1, direction="symmetric"),
+              dict(pc_kind=oracle.PC_MTGS, pc_direction=2)),
+    "mtgs_2_w0.9": (dict(kind="mtgs", outer=2, omega=0.9),
+                    dict(pc_kind=oracle.PC_MTGS, pc_outer=2, pc_omega=0.9)),
 }
 
 
@@ -271,6 +291,8 @@ def test_cg_matches_oracle(g):
     h = g.gs2_setup(pr.A)
     for gp, op in ((dict(kind="gs2", outer=1, inner=1, direction="symmetric"),
                     dict(pc_kind=oracle.PC_GS2, pc_direction=2)),
+                   (dict(kind="mtgs", outer=1, direction="symmetric"),
+                    dict(pc_kind=oracle.PC_MTGS, pc_direction=2)),
                    (None, dict(pc_kind=oracle.PC_NONE))):
         x = dev(np.zeros(pr.n))
         info = g.cg_solve(h, dev(pr.b), x, tol=1e-8, max_iters=5000,
@@ -396,6 +418,7 @@ FULL_PCS = {
     "sgs_exact": dict(kind="gs", outer=1, direction="symmetric"),
     "jr3_w1.0": dict(kind="jr", outer=3, omega=1.0),
     "jr3_w0.8": dict(kind="jr", outer=3, omega=0.8),
+    "mtsgs": dict(kind="mtgs", outer=1, direction="symmetric"),
 }
 
 
@@ -431,7 +454,7 @@ def test_autotuned_shapes_keep_parity(g, name):
     assert rel(host(y), oracle.spmv(A, x0)) <= TOL
 
 
-@pytest.mark.parametrize("pc", ["sgs2_1_2", "jr3", "gs_sym", "none"])
+@pytest.mark.parametrize("pc", ["sgs2_1_2", "jr3", "gs_sym", "mtsgs", "none"])
 def test_graph_and_eager_cycles_agree_bitwise(g, pc):
     """Arnoldi steps replayed as a captured CUDA graph give the same bits as
     separate launches, also when a cached graph is reused for a new b."""

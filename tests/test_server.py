@@ -30,6 +30,9 @@ def test_footprint_covers_matrix_triangles_and_basis(lib):
     assert gs2.server_footprint(n, nnz, restart=60) > fp
     lowp = gs2.server_footprint(n, nnz, precond=gs2.params("gs2", precision="fp32"))
     assert lowp > gs2.server_footprint(n, nnz, precond=gs2.params("gs2"))
+    # multicolour GS keeps a colour-ordered copy of the off-diagonal entries
+    mc = gs2.server_footprint(n, nnz, precond=gs2.params("mtgs"))
+    assert mc >= gs2.server_footprint(n, nnz, precond=gs2.params("gs2")) + 12 * (nnz - n)
 
 
 def _mix():
@@ -57,9 +60,12 @@ def _alone(pr, pc):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "mtsgs"])
 def test_results_equal_alone_and_in_the_mix(lib, prec):
-    pc = gs2.params("gs2", 1, 1, direction="symmetric", precision=prec)
+    if prec == "mtsgs":
+        pc = gs2.params("mtgs", 1, direction="symmetric")
+    else:
+        pc = gs2.params("gs2", 1, 1, direction="symmetric", precision=prec)
     probs = _mix()
     srv = gs2.Server(restart=30, tol=1e-8, max_iters=4000, precond=pc, max_slots=3,
                      prep_threads=2)
