@@ -161,7 +161,8 @@ k_dots_x(int n, const double* __restrict__ V, const double* __restrict__ w, doub
 
 // pass 2: w -= V h ; part = V^T w          (NORM = false)
 // pass 3: w -= V h ; part[0] = w^T w       (NORM = true)
-// V h is summed in four interleaved partial sums to shorten the FMA chain.
+// V h is summed in two interleaved partial sums: a shorter FMA chain, and
+// only one extra FP64 add per row (the FP64 pipe is the limit here).
 template <int JC, bool NORM>
 __global__ void __launch_bounds__(kVecThreads)
 k_update_x(int n, const double* __restrict__ V, const double* __restrict__ hcoef,
@@ -175,10 +176,10 @@ k_update_x(int n, const double* __restrict__ V, const double* __restrict__ hcoef
 #pragma unroll
   for (int k = 0; k < NA; ++k) acc[k] = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    double sp[4] = {0.0, 0.0, 0.0, 0.0};
+    double sp[2] = {0.0, 0.0};
 #pragma unroll
-    for (int k = 0; k < JC; ++k) sp[k & 3] = fma(__ldg(V + (size_t)k * n + i), hs[k], sp[k & 3]);
-    const double wn = w[i] - ((sp[0] + sp[1]) + (sp[2] + sp[3]));
+    for (int k = 0; k < JC; ++k) sp[k & 1] = fma(__ldg(V + (size_t)k * n + i), hs[k], sp[k & 1]);
+    const double wn = w[i] - (sp[0] + sp[1]);
     w[i] = wn;
     if (NORM) {
       acc[0] = fma(wn, wn, acc[0]);
@@ -478,10 +479,17 @@ static int maxk_for(int jc) {
   X(17) X(18) X(19) X(20) X(21) X(22) X(23) X(24) X(25) X(26) X(27) X(28) X(29) X(30)  \
   X(31) X(32)
 
-// Grid of a reduction kernel: as many blocks as stay resident on all SMs
-// (queried once per instantiation), but at least ~8 rows per thread and no
-// more blocks than the partial-sum buffer holds.
-static int reduction_grid(gs2_handle* h, const void* fn) {
+// Grid of a reduction kernel: at most `per_sm_max` blocks per SM (0 = as
+// many as stay resident, queried once per instantiation), at least ~8 rows
+// per thread, no more blocks than the partial-sum buffer holds, and a whole
+// multiple of the SM count when there are at least that many (even load per
+// SM).  The dot-product pass (one FMA per loaded value) is latency-bound and
+// wants every resident warp; the update passes (two FMAs per value for
+// w -= Vh, V^T w) are bound by the FP64 pipe and ran fastest at two blocks
+// per SM, the update-and-norm pass at three (measured at n = 2.1M), where the
+// per-block butterfly reductions stay a few percent of the work.
+constexpr int kDotBlocksPerSm = 0, kUpdBlocksPerSm = 2, kNormBlocksPerSm = 3;
+static int reduction_grid(gs2_handle* h, const void* fn, int per_sm_max) {
   static std::mutex mu;
   static std::map<const void*, int> occ;
   int per_sm;
@@ -495,9 +503,11 @@ static int reduction_grid(gs2_handle* h, const void* fn) {
     }
     per_sm = it->second;
   }
+  if (per_sm_max > 0) per_sm = std::min(per_sm, per_sm_max);
   const int64_t want = (h->n + kVecThreads * 8 - 1) / (kVecThreads * 8);
-  return (int)std::max<int64_t>(1, std::min<int64_t>({want, (int64_t)per_sm * h->nsm,
-                                                      (int64_t)h->nblk}));
+  int64_t nb = std::min<int64_t>({want, (int64_t)per_sm * h->nsm, (int64_t)h->nblk});
+  if (nb >= h->nsm) nb -= nb % h->nsm;
+  return (int)std::max<int64_t>(1, nb);
 }
 
 // Each launcher returns the number of blocks, i.e. of partial sums per value.
@@ -509,13 +519,13 @@ static int launch_dots(gs2_handle* h, int jc, const double* w, const int* skip) 
   switch (jc) {
 #define GS2_DOTS_CASE(J)                                                          \
   case J:                                                                         \
-    nb = reduction_grid(h, (const void*)k_dots_x<J>);                             \
+    nb = reduction_grid(h, (const void*)k_dots_x<J>, kDotBlocksPerSm);            \
     k_dots_x<J><<<nb, kVecThreads, 0, s>>>(n, h->V, w, h->part, nb, skip);        \
     break;
     GS2_JC_CASES(GS2_DOTS_CASE)
 #undef GS2_DOTS_CASE
     default:
-      nb = reduction_grid(h, (const void*)k_dots<64>);
+      nb = reduction_grid(h, (const void*)k_dots<64>, kDotBlocksPerSm);
       k_dots<64><<<nb, kVecThreads, 0, s>>>(n, h->V, jc, w, h->part, nb, skip);
       break;
   }
@@ -529,16 +539,17 @@ static int launch_update(gs2_handle* h, int jc, double* w, const int* skip) {
   const int n = (int)h->n;
   cudaStream_t s = h->stream;
   int nb = 1;
+  const int cap = NORM ? kNormBlocksPerSm : kUpdBlocksPerSm;
   switch (jc) {
 #define GS2_UPD_CASE(J)                                                                 \
   case J:                                                                               \
-    nb = reduction_grid(h, (const void*)k_update_x<J, NORM>);                           \
+    nb = reduction_grid(h, (const void*)k_update_x<J, NORM>, cap);                      \
     k_update_x<J, NORM><<<nb, kVecThreads, 0, s>>>(n, h->V, h->hbuf, w, h->part, nb, skip); \
     break;
     GS2_JC_CASES(GS2_UPD_CASE)
 #undef GS2_UPD_CASE
     default:
-      nb = reduction_grid(h, (const void*)k_update<64, NORM>);
+      nb = reduction_grid(h, (const void*)k_update<64, NORM>, cap);
       k_update<64, NORM><<<nb, kVecThreads, 0, s>>>(n, h->V, jc, h->hbuf, w, h->part, nb, skip);
       break;
   }
