@@ -20,6 +20,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "amg.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -35,12 +36,12 @@ class OracleError(RuntimeError):
 def build(force: bool = False) -> str:
     """Compile oracle.c into liboracle.so next to it (gcc, -O2, no -march)."""
     stale = (not os.path.exists(_LIB)) or (
-        os.path.getmtime(_LIB) < max(os.path.getmtime(_SRC),
-                                     os.path.getmtime(os.path.join(_HERE, "oracle.h"))))
+        os.path.getmtime(_LIB) < max([os.path.getmtime(f) for f in _SRCS] +
+                                     [os.path.getmtime(os.path.join(_HERE, "oracle.h"))]))
     if force or stale:
         tmp = _LIB + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-               _SRC, "-o", tmp, "-lm"]
+               *_SRCS, "-o", tmp, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
     return _LIB
@@ -82,10 +83,24 @@ def _load():
                                          ctypes.POINTER(_Info)]
             lib.ora_gs2_compact.argtypes = csr + [P, P, I32, I32, I32]
             lib.ora_coloring.argtypes = [I64, P, P, P]
+            lib.ora_amg_build.argtypes = csr + [D, I32, I64]
+            lib.ora_amg_build.restype = P
+            lib.ora_amg_free.argtypes = [P]
+            lib.ora_amg_free.restype = None
+            lib.ora_amg_levels.argtypes = [P]
+            lib.ora_amg_level.argtypes = [P, I32, P, P, P]
+            lib.ora_amg_get_matrix.argtypes = [P, I32, P, P, P]
+            lib.ora_amg_get_prolongator.argtypes = [P, I32, P, P, P]
+            lib.ora_amg_get_aggregates.argtypes = [P, I32, P]
+            lib.ora_amg_vcycle.argtypes = [P, P, P, I32, I32, I32, D, D, I32]
+            lib.ora_gmres_amg.argtypes = csr + [P, P, I32, D, I32, P, I32, I32, I32, D, D,
+                                                I32, ctypes.POINTER(_Info)]
             lib.ora_mtgs.argtypes = csr + [P, P, I32, D, I32]
             for f in ("ora_diag", "ora_gs2", "ora_gs", "ora_jr", "ora_levels",
                       "ora_precond", "ora_gmres", "ora_cg", "ora_gs2_compact",
-                      "ora_coloring", "ora_mtgs"):
+                      "ora_coloring", "ora_mtgs", "ora_amg_levels", "ora_amg_level",
+                      "ora_amg_get_matrix", "ora_amg_get_prolongator",
+                      "ora_amg_get_aggregates", "ora_amg_vcycle", "ora_gmres_amg"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -241,3 +256,80 @@ def gs2_compact(A, b, x, outer=1, inner=1, direction=FORWARD):
     _check(_load().ora_gs2_compact(n, _p(rp), _p(ci), _p(va), _p(b), _p(x), outer,
                                    inner, direction), "ora_gs2_compact")
     return x
+
+
+class AMG:
+    """Smoothed-aggregation hierarchy of A (amg.c) with a GS2 or JR smoother.
+
+    theta: classical strength threshold; max_levels; coarse_size: stop
+    coarsening at this many rows or fewer (the coarsest level is solved
+    exactly)."""
+
+    def __init__(self, A, theta=0.25, max_levels=10, coarse_size=64):
+        n, rp, ci, va = _csr(A)
+        self.n = n
+        self._lib = _load()
+        self._ptr = self._lib.ora_amg_build(n, _p(rp), _p(ci), _p(va), theta, max_levels,
+                                            coarse_size)
+        if not self._ptr:
+            raise OracleError("ora_amg_build failed")
+
+    def __del__(self):
+        if getattr(self, "_ptr", None):
+            self._lib.ora_amg_free(self._ptr)
+            self._ptr = None
+
+    @property
+    def levels(self):
+        return int(self._lib.ora_amg_levels(self._ptr))
+
+    def level(self, l):
+        """(rows, entries of A_l, entries of P_l)"""
+        v = [ctypes.c_int64() for _ in range(3)]
+        _check(self._lib.ora_amg_level(self._ptr, l, *[ctypes.byref(x) for x in v]),
+               "ora_amg_level")
+        return tuple(int(x.value) for x in v)
+
+    def matrix(self, l):
+        n, nnz, _ = self.level(l)
+        rp, ci, va = np.zeros(n + 1, np.int64), np.zeros(nnz, np.int32), np.zeros(nnz)
+        _check(self._lib.ora_amg_get_matrix(self._ptr, l, _p(rp), _p(ci), _p(va)),
+               "ora_amg_get_matrix")
+        return rp, ci, va
+
+    def prolongator(self, l):
+        n, _, pnnz = self.level(l)
+        rp, ci, va = np.zeros(n + 1, np.int64), np.zeros(pnnz, np.int32), np.zeros(pnnz)
+        _check(self._lib.ora_amg_get_prolongator(self._ptr, l, _p(rp), _p(ci), _p(va)),
+               "ora_amg_get_prolongator")
+        return rp, ci, va
+
+    def aggregates(self, l):
+        n = self.level(l)[0]
+        agg = np.zeros(n, np.int32)
+        _check(self._lib.ora_amg_get_aggregates(self._ptr, l, _p(agg)),
+               "ora_amg_get_aggregates")
+        return agg
+
+    def vcycle(self, b, kind=PC_GS2, outer=1, inner=1, omega=1.0, gamma=1.0,
+               direction=SYMMETRIC):
+        """x = M^{-1} b, one V-cycle from zero."""
+        b = _vec(b, self.n)
+        x = np.zeros(self.n)
+        _check(self._lib.ora_amg_vcycle(self._ptr, _p(b), _p(x), kind, outer, inner, omega,
+                                        gamma, direction), "ora_amg_vcycle")
+        return x
+
+    def gmres(self, A, b, x0=None, restart=30, tol=1e-8, max_iters=10000, kind=PC_GS2,
+              outer=1, inner=1, omega=1.0, gamma=1.0, direction=SYMMETRIC):
+        """GMRES(restart) preconditioned by one V-cycle; (x, SolveInfo)."""
+        n, rp, ci, va = _csr(A)
+        b = _vec(b, n)
+        x = np.zeros(n) if x0 is None else _vec(x0, n)
+        info = _Info()
+        st = self._lib.ora_gmres_amg(n, _p(rp), _p(ci), _p(va), _p(b), _p(x), restart, tol,
+                                     max_iters, self._ptr, kind, outer, inner, omega, gamma,
+                                     direction, ctypes.byref(info))
+        if st == 1:
+            raise OracleError("ora_gmres_amg: invalid argument")
+        return x, SolveInfo(info.iters, info.cycles, info.status, info.true_relres)

@@ -286,6 +286,11 @@ int ora_precond(int64_t n, const int64_t* rp, const int32_t* ci,
       return ora_gs(n, rp, ci, va, v, z, outer, omega, dir);
     case ORA_PC_MTGS:
       return ora_mtgs(n, rp, ci, va, v, z, outer, omega, dir);
+    case ORA_PC_AMG:
+    case ORA_PC_AMG_JR:
+      if (!ora_amg_current) return 1;
+      return ora_amg_vcycle(ora_amg_current, v, z, kind == ORA_PC_AMG ? ORA_PC_GS2 : ORA_PC_JR,
+                            outer, inner, omega, gamma, dir);
     default:
       return 1;
   }

@@ -26,7 +26,7 @@ extern "C" {
 
 enum { ORA_FORWARD = 0, ORA_BACKWARD = 1, ORA_SYMMETRIC = 2 };
 enum { ORA_PC_NONE = 0, ORA_PC_GS2 = 1, ORA_PC_JR = 2, ORA_PC_GS = 3,
-       ORA_PC_MTGS = 4 };
+       ORA_PC_MTGS = 4, ORA_PC_AMG = 5, ORA_PC_AMG_JR = 6 };
 
 typedef struct {
   int iters;          /* total Arnoldi steps over all cycles */
@@ -87,7 +87,8 @@ int ora_mtgs(int64_t n, const int64_t* rp, const int32_t* ci, const double* va,
 /* Apply a preconditioner from a zero start: z = M^{-1} v.
  * kind: ORA_PC_NONE (z = v), ORA_PC_GS2, ORA_PC_JR (outer = sweeps),
  * ORA_PC_GS (exact GS, outer = sweeps), ORA_PC_MTGS (multicolour GS,
- * outer = sweeps). */
+ * outer = sweeps), ORA_PC_AMG / ORA_PC_AMG_JR (one V-cycle of the hierarchy
+ * ora_gmres_amg installs, GS2 / JR smoother with these parameters). */
 int ora_precond(int64_t n, const int64_t* rp, const int32_t* ci,
                 const double* va, const double* v, double* z, int kind,
                 int outer, int inner, double omega, double gamma, int dir);
@@ -118,6 +119,42 @@ int ora_cg(int64_t n, const int64_t* rp, const int32_t* ci, const double* va,
 int ora_gs2_compact(int64_t n, const int64_t* rp, const int32_t* ci,
                     const double* va, const double* b, double* x, int outer,
                     int inner, int dir);
+
+/* ------------------------------------------------------------------ */
+/* Smoothed-aggregation AMG with GS2 (or JR) as the smoother of a       */
+/* V-cycle (amg.c; the readings are stated there).                      */
+/* ------------------------------------------------------------------ */
+
+#define ORA_AMG_MAX_LEVELS 16
+typedef struct ora_amg ora_amg;
+
+/* Build the hierarchy of A: strength threshold theta, at most max_levels
+ * levels, stop coarsening at <= coarse_size rows.  NULL on invalid input,
+ * a zero diagonal or a singular coarsest matrix. */
+ora_amg* ora_amg_build(int64_t n, const int64_t* rp, const int32_t* ci, const double* va,
+                       double theta, int max_levels, int64_t coarse_size);
+void ora_amg_free(ora_amg* M);
+int ora_amg_levels(const ora_amg* M);
+/* sizes of level l: rows, entries of A_l, entries of P_l (0 on the coarsest) */
+int ora_amg_level(const ora_amg* M, int l, int64_t* n, int64_t* nnz, int64_t* pnnz);
+/* copies of A_l, P_l (rows of level l, columns of level l+1) and the
+ * aggregate of every row of level l; arrays sized by ora_amg_level */
+int ora_amg_get_matrix(const ora_amg* M, int l, int64_t* rp, int32_t* ci, double* va);
+int ora_amg_get_prolongator(const ora_amg* M, int l, int64_t* rp, int32_t* ci, double* va);
+int ora_amg_get_aggregates(const ora_amg* M, int l, int32_t* agg);
+/* x = M^{-1} b: one V-cycle from a zero start, smoother kind ORA_PC_GS2
+ * (outer, inner, omega, gamma) or ORA_PC_JR (outer sweeps, omega) applied
+ * before and after the coarse correction; direction SYMMETRIC smooths
+ * forward before and backward after. */
+int ora_amg_vcycle(const ora_amg* M, const double* b, double* x, int kind, int outer,
+                   int inner, double omega, double gamma, int dir);
+/* GMRES(restart) right-preconditioned by one V-cycle per application */
+int ora_gmres_amg(int64_t n, const int64_t* rp, const int32_t* ci, const double* va,
+                  const double* b, double* x, int restart, double tol, int max_iters,
+                  const ora_amg* M, int kind, int outer, int inner, double omega,
+                  double gamma, int dir, ora_info* info);
+/* the hierarchy the AMG preconditioner kinds apply (set by ora_gmres_amg) */
+extern _Thread_local const ora_amg* ora_amg_current;
 
 #ifdef __cplusplus
 }

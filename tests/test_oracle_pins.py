@@ -352,6 +352,131 @@ def test_mtgs_red_black_poisson_is_two_jacobi_half_steps():
 
 
 # ---------------------------------------------------------------------------
+# Smoothed-aggregation AMG with a GS2 smoother
+# ---------------------------------------------------------------------------
+
+def _amg_golden():
+    out = {}
+    for line in open(os.path.join(GOLDEN, "amg_aggregates.txt")):
+        if line.strip() and not line.startswith("#"):
+            key, *vals = line.split()
+            out[key] = [int(v) for v in vals]
+    return out
+
+
+def test_amg_aggregates_hand_worked():
+    g = _amg_golden()
+    n = 10
+    L1 = 2 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)
+    M = oracle.AMG(P.dense_to_csr(L1), coarse_size=2, max_levels=2)
+    assert M.aggregates(0).tolist() == g["laplace1d_10"]
+    M = oracle.AMG(P.poisson2d_matrix(4), coarse_size=2, max_levels=2)
+    assert M.aggregates(0).tolist() == g["laplace2d_4x4"]
+
+
+def test_amg_aggregates_are_connected_partitions():
+    A = P.random_csr(400, 12, mean_offdiag=4.0)
+    M = oracle.AMG(A, coarse_size=8, max_levels=3)
+    rp, ci, va = A
+    agg = M.aggregates(0)
+    na = M.level(1)[0]
+    assert sorted(set(agg.tolist())) == list(range(na))
+    # every aggregate is connected in the symmetrised strength graph
+    G = nx.Graph()
+    G.add_nodes_from(range(400))
+    for i in range(400):
+        row = slice(rp[i], rp[i + 1])
+        off = [(int(j), abs(v)) for j, v in zip(ci[row], va[row]) if j != i]
+        mx = max((v for _, v in off), default=0.0)
+        for j, v in off:
+            if mx > 0 and v >= 0.25 * mx:
+                G.add_edge(i, j)
+    for a in range(na):
+        assert nx.is_connected(G.subgraph(np.flatnonzero(agg == a).tolist()))
+
+
+def test_amg_prolongator_maps_aggregate_sizes_to_smoothed_ones():
+    """P0 s = 1 with s_a = sqrt(|aggregate a|), so P s = (I - w D^-1 A) 1 =
+    1 - w (row sums of A) / a_ii with w = 4 / (3 max_i sum_j |a_ij| / |a_ii|)."""
+    for A in (P.poisson2d_matrix(9), P.random_csr(300, 13, mean_offdiag=5.0)):
+        Md = P.csr_to_dense(A)
+        d = np.diag(Md)
+        w = 4.0 / (3.0 * np.max(np.abs(Md).sum(1) / np.abs(d)))
+        M = oracle.AMG(A, coarse_size=4, max_levels=2)
+        agg = M.aggregates(0)
+        s = np.sqrt(np.bincount(agg).astype(float))
+        Pd = _dense(M.prolongator(0), M.level(1)[0])
+        assert np.allclose(Pd @ s, 1.0 - w * Md.sum(1) / d, rtol=0, atol=1e-13)
+
+
+def _dense(csr, ncols):
+    rp, ci, va = csr
+    n = len(rp) - 1
+    D = np.zeros((n, ncols))
+    for i in range(n):
+        for k in range(rp[i], rp[i + 1]):
+            D[i, ci[k]] += va[k]
+    return D
+
+
+def test_amg_coarse_correction_is_a_projection():
+    """Two levels, no smoothing: C = I - P A_c^-1 P^T A is idempotent and
+    A-self-adjoint exactly when A_c is the Galerkin product and the cycle
+    restricts with P^T and prolongs with P."""
+    A = P.poisson2d_matrix(7)
+    Md = P.csr_to_dense(A)
+    M = oracle.AMG(A, coarse_size=30, max_levels=2)
+    assert M.levels == 2
+    n = Md.shape[0]
+    Minv = np.column_stack([M.vcycle(e, outer=0) for e in np.eye(n)])
+    C = np.eye(n) - Minv @ Md
+    assert np.allclose(C @ C, C, atol=1e-12)
+    assert np.allclose(Md @ C, (Md @ C).T, atol=1e-12)
+    # rank of the correction = number of aggregates
+    assert np.linalg.matrix_rank(Minv, tol=1e-10) == M.level(1)[0]
+
+
+def test_amg_symmetric_vcycle_is_spd_and_contracts():
+    """Forward pre- and backward post-smoothing give a symmetric positive
+    definite preconditioner for SPD A; a forward-forward cycle does not, and
+    the error propagator I - M^-1 A contracts in the A-norm."""
+    A = P.poisson2d_matrix(8)
+    Md = P.csr_to_dense(A)
+    n = Md.shape[0]
+    M = oracle.AMG(A, coarse_size=10, max_levels=3)
+    assert M.levels == 3
+    for kw in (dict(kind=oracle.PC_GS2, inner=1, omega=0.9),
+               dict(kind=oracle.PC_GS2, inner=3),
+               dict(kind=oracle.PC_JR, outer=2, omega=0.7)):
+        Minv = np.column_stack([M.vcycle(e, direction=oracle.SYMMETRIC, **kw)
+                                for e in np.eye(n)])
+        assert np.allclose(Minv, Minv.T, atol=1e-12), kw
+        assert np.linalg.eigvalsh((Minv + Minv.T) / 2).min() > 0
+        E = np.eye(n) - Minv @ Md
+        Lc = np.linalg.cholesky(Md)
+        assert np.linalg.norm(Lc.T @ E @ np.linalg.inv(Lc.T), 2) < 1.0
+    Mff = np.column_stack([M.vcycle(e, direction=oracle.FORWARD, inner=1) for e in np.eye(n)])
+    assert not np.allclose(Mff, Mff.T, atol=1e-6)
+
+
+def test_amg_iterations_grid_independent():
+    """Multigrid: GMRES iterations stay flat as the grid is refined, while
+    the one-level SGS2 preconditioner's grow with it."""
+    amg, one = [], []
+    for N in (32, 64, 128):
+        pr = P.poisson2d(N)
+        M = oracle.AMG(pr.A)
+        _, info = M.gmres(pr.A, pr.b, restart=30, tol=1e-8, max_iters=500)
+        assert info.status == 0
+        amg.append(info.iters)
+        _, info = oracle.gmres(pr.A, pr.b, restart=30, tol=1e-8, max_iters=5000,
+                               pc_kind=oracle.PC_GS2, pc_direction=oracle.SYMMETRIC)
+        one.append(info.iters)
+    assert max(amg) - min(amg) <= 3 and max(amg) <= 14, amg
+    assert one[2] > 2 * one[0], one
+
+
+# ---------------------------------------------------------------------------
 # GMRES against the Krylov least-squares minimiser
 # ---------------------------------------------------------------------------
 
