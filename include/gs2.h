@@ -73,7 +73,10 @@ typedef enum {
   GS2_PC_GS2 = 1,  /* two-stage GS, Eq. (4)-(7) with damping */
   GS2_PC_JR = 2,   /* damped Jacobi-Richardson, `outer` sweeps */
   GS2_PC_GS = 3,   /* exact GS/SOR, level-scheduled, `outer` sweeps */
-  GS2_PC_MTGS = 4  /* multicolour GS/SOR, `outer` sweeps (Sec. 5.1.2) */
+  GS2_PC_MTGS = 4, /* multicolour GS/SOR, `outer` sweeps (Sec. 5.1.2) */
+  GS2_PC_AMG = 5,  /* one AMG V-cycle, GS2 smoother (outer, inner, omega,
+                      gamma, precision) on every level */
+  GS2_PC_AMG_JR = 6 /* one AMG V-cycle, JR smoother (outer sweeps, omega) */
 } gs2_pc_kind;
 
 /* Relaxation / preconditioner parameters in the paper's notation:
@@ -209,6 +212,51 @@ gs2_status gs_apply(gs2_handle* h, const double* b, double* x, int sweeps,
  * omega <= 0, bad direction), OOM and CUDA on the first call. */
 gs2_status mtgs_apply(gs2_handle* h, const double* b, double* x, int sweeps,
                       double omega, int direction);
+
+/* ------------------------------------------------------------------------
+ * GS2 as a multigrid smoother.  The paper also applies the two-stage
+ * iteration as the smoother of an AMG V-cycle (its Nalu-Wind runs: one GS2
+ * sweep per level of hypre's C-AMG).  This library builds a
+ * smoothed-aggregation hierarchy: classical strength of connection
+ * |a_ij| >= theta max_{k != i} |a_ik| (symmetrised), greedy aggregation in
+ * natural row order, unit-norm constant tentative prolongator P0, smoothed
+ * prolongator P = (I - w D^{-1} A) P0 with w = 4 / (3 rho) and rho the
+ * Gershgorin bound of rho(D^{-1} A), Galerkin coarse operators P^T A P, and
+ * an exact solve on the coarsest level.  The hierarchy is set up on the host
+ * (once per matrix) and applied on the device.
+ * ---------------------------------------------------------------------- */
+
+#define GS2_AMG_MAX_LEVELS 16
+
+typedef struct {
+  double theta;        /* strength threshold, 0.25 (the paper's C-AMG value) */
+  int max_levels;      /* 1 .. GS2_AMG_MAX_LEVELS, default 10 */
+  int64_t coarse_size; /* stop coarsening at this many rows or fewer (64);
+                          the coarsest level must have at most 2048 rows */
+} gs2_amg_cfg;
+
+/* Build (or rebuild) the handle's hierarchy; cfg NULL = defaults.  A GMRES,
+ * CG or batch solve with an AMG preconditioner kind builds the default
+ * hierarchy itself when the handle has none.  Errors: INVALID_ARG (bad
+ * settings, a coarsest level above 2048 rows, a singular coarsest matrix),
+ * OOM, CUDA. */
+gs2_status gs2_amg_setup(gs2_handle* h, const gs2_amg_cfg* cfg);
+
+/* Levels of the hierarchy (0 if none) and, per level l < levels, its rows,
+ * matrix entries and prolongator entries (0 on the coarsest); each array
+ * (may be NULL) holds GS2_AMG_MAX_LEVELS entries. */
+gs2_status gs2_amg_info(const gs2_handle* h, int* levels, int64_t* rows, int64_t* nnz,
+                        int64_t* pnnz);
+
+/* x = M^{-1} b: one V-cycle from a zero start with the smoother of `p`
+ * (kind GS2_PC_AMG or GS2_PC_AMG_JR).  On each level but the coarsest: x =
+ * `outer` smoother sweeps from zero on b, r = b - A x, coarse right-hand
+ * side P^T r, coarse correction, x += P x_c, `outer` sweeps from x.
+ * Direction SYMMETRIC smooths forward before and backward after the coarse
+ * correction (a symmetric cycle for SPD A); FORWARD / BACKWARD smooth in
+ * that direction both times.  The hierarchy is built with defaults if the
+ * handle has none. */
+gs2_status gs2_amg_vcycle(gs2_handle* h, const double* b, double* x, const gs2_params* p);
 
 /* Damped JR baseline: x += omega D^{-1} (b - A x), `sweeps` times (Sec. 3,
  * zero-inner-sweep case). x in/out. */

@@ -18,9 +18,9 @@ import numpy as np
 
 __all__ = [
     "GS2Error", "Params", "SolveInfo", "Handle", "load", "gs2_setup", "gs2_apply",
-    "gs2_apply_ex", "gs_apply", "mtgs_apply", "jr_apply", "gs2_spmv", "gmres_solve", "cg_solve",
+    "gs2_apply_ex", "gs_apply", "mtgs_apply", "jr_apply", "amg_vcycle", "gs2_spmv", "gmres_solve", "cg_solve",
     "gs2_batch_solve", "params", "FORWARD", "BACKWARD", "SYMMETRIC", "FP64", "FP32",
-    "FP16_ROWSCALED", "PC_NONE", "PC_GS2", "PC_JR", "PC_GS", "PC_MTGS", "NONCOMPACT", "COMPACT",
+    "FP16_ROWSCALED", "PC_NONE", "PC_GS2", "PC_JR", "PC_GS", "PC_MTGS", "PC_AMG", "PC_AMG_JR", "NONCOMPACT", "COMPACT",
     "STATUS",
 ]
 
@@ -29,20 +29,27 @@ LIB_PATH = os.path.join(_HERE, "libgs2.so")
 
 FORWARD, BACKWARD, SYMMETRIC = 0, 1, 2
 FP64, FP32, FP16_ROWSCALED = 0, 1, 2
-PC_NONE, PC_GS2, PC_JR, PC_GS, PC_MTGS = 0, 1, 2, 3, 4
+PC_NONE, PC_GS2, PC_JR, PC_GS, PC_MTGS, PC_AMG, PC_AMG_JR = 0, 1, 2, 3, 4, 5, 6
+AMG_MAX_LEVELS = 16
 NONCOMPACT, COMPACT = 0, 1
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "ZERO_DIAGONAL", 3: "OOM", 4: "CUDA",
           5: "NOT_CONVERGED", 6: "BREAKDOWN", 7: "NAN", 8: "TIMEOUT", 9: "BUSY",
           10: "NOT_FOUND"}
 _DIR = {"forward": FORWARD, "backward": BACKWARD, "symmetric": SYMMETRIC}
 _PREC = {"fp64": FP64, "fp32": FP32, "fp16": FP16_ROWSCALED}
-_KIND = {"none": PC_NONE, "gs2": PC_GS2, "jr": PC_JR, "gs": PC_GS, "mtgs": PC_MTGS}
+_KIND = {"none": PC_NONE, "gs2": PC_GS2, "jr": PC_JR, "gs": PC_GS, "mtgs": PC_MTGS,
+         "amg": PC_AMG, "amg_jr": PC_AMG_JR}
 
 
 class GS2Error(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
         self.status = status
+
+
+class _AmgCfg(ctypes.Structure):
+    _fields_ = [("theta", ctypes.c_double), ("max_levels", ctypes.c_int),
+                ("coarse_size", ctypes.c_int64)]
 
 
 class Params(ctypes.Structure):
@@ -137,6 +144,9 @@ def load(path: str | None = None):
         "gs2_autotune": [P],
         "gs2_profile_read": [P, ctypes.POINTER(_KStat), I, ctypes.POINTER(I)],
         "gs2_profile_reset": [P],
+        "gs2_amg_setup": [P, ctypes.POINTER(_AmgCfg)],
+        "gs2_amg_info": [P, ctypes.POINTER(I), P, P, P],
+        "gs2_amg_vcycle": [P, P, P, ctypes.POINTER(Params)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -240,6 +250,19 @@ class Handle:
         """Pick the fastest tile shape of each matrix (cached by matrix class)."""
         _check(load().gs2_autotune(self.ptr))
 
+    def amg_setup(self, theta: float = 0.25, max_levels: int = 10, coarse_size: int = 64):
+        """Build the smoothed-aggregation hierarchy used by the AMG
+        preconditioner kinds (host setup, device-resident levels)."""
+        _check(load().gs2_amg_setup(self.ptr, ctypes.byref(_AmgCfg(theta, max_levels,
+                                                                    coarse_size))))
+
+    def amg_info(self) -> list:
+        """[(rows, matrix entries, prolongator entries)] per level."""
+        lv = ctypes.c_int()
+        arr = [(ctypes.c_int64 * AMG_MAX_LEVELS)() for _ in range(3)]
+        _check(load().gs2_amg_info(self.ptr, ctypes.byref(lv), *arr))
+        return [(arr[0][i], arr[1][i], arr[2][i]) for i in range(lv.value)]
+
     def set_graph_mode(self, mode: int):
         """0: automatic, 1: always replay Arnoldi steps as a CUDA graph, 2: never."""
         _check(load().gs2_set_graph_mode(self.ptr, mode))
@@ -342,6 +365,14 @@ def mtgs_apply(h, b, x, sweeps=1, omega=1.0, direction=FORWARD):
     px, _kx = _ptr(x, True)
     d = _DIR[direction] if isinstance(direction, str) else direction
     _check(load().mtgs_apply(h.ptr, pb, px, sweeps, omega, d))
+    return x
+
+
+def amg_vcycle(h, b, x, params):
+    """x = M^{-1} b, one V-cycle (params.kind PC_AMG or PC_AMG_JR)."""
+    pb, _kb = _ptr(b)
+    px, _kx = _ptr(x, True)
+    _check(load().gs2_amg_vcycle(h.ptr, pb, px, ctypes.byref(params)))
     return x
 
 

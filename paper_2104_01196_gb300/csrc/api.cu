@@ -405,6 +405,12 @@ void ensure_precond(gs2_handle* h, const gs2_params* p) {
   if (!p) return;
   if (p->kind == GS2_PC_GS) ensure_levels(h);
   if (p->kind == GS2_PC_MTGS) ensure_colors(h);
+  if (p->kind == GS2_PC_AMG || p->kind == GS2_PC_AMG_JR) amg_prepare(h, p);
+}
+
+void upload_matrix(gs2_handle* h, DevCsr& M, int n, const std::vector<int>& rp,
+                   const std::vector<int>& ci, const std::vector<double>& va) {
+  upload_csr(h, M, n, rp, ci, va);
 }
 
 // ---------------------------------------------------------------------------
@@ -499,7 +505,7 @@ struct Staged {
 
 static void check_params(const gs2_params* p) {
   if (!p) return;
-  if (p->kind < GS2_PC_NONE || p->kind > GS2_PC_MTGS)
+  if (p->kind < GS2_PC_NONE || p->kind > GS2_PC_AMG_JR)
     GS2_THROW(GS2_ERR_INVALID_ARG, "unknown preconditioner kind");
   if (p->kind == GS2_PC_NONE) return;
   if (p->outer < 1 || p->outer > 1000) GS2_THROW(GS2_ERR_INVALID_ARG, "outer sweeps < 1");
@@ -546,6 +552,7 @@ void gs2::destroy_handle(gs2_handle* h) {
   cudaSetDevice(h->device);
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->gstream) cudaStreamSynchronize(h->gstream);
+  if (h->amg) amg_free(h);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->gstream) cudaStreamDestroy(h->gstream);
   if (h->gev_in) cudaEventDestroy(h->gev_in);
@@ -739,7 +746,7 @@ gs2_status gs2_get_stats(const gs2_handle* h, gs2_handle_stats* out) {
   out->nnz_upper = h->U.nnz;
   out->levels_lower = h->levels_ready ? (int)h->lev_ptr_L.size() - 1 : 0;
   out->levels_upper = h->levels_ready ? (int)h->lev_ptr_U.size() - 1 : 0;
-  out->device_bytes = h->dev_bytes;
+  out->device_bytes = h->dev_bytes + amg_device_bytes(h);
   out->tpr_a = h->A.tpr;
   out->tpr_tri = h->L.tpr;
   out->rpt_a = h->A.rpt;
@@ -799,6 +806,42 @@ gs2_status mtgs_apply(gs2_handle* h, const double* b, double* x, int sweeps, dou
   ensure_colors(h);
   Staged s(h, b, x, true);
   mtgs_relax(h, s.b, s.x, sweeps, omega, direction);
+  s.finish();
+  return GS2_OK;
+  API_END
+}
+
+gs2_status gs2_amg_setup(gs2_handle* h, const gs2_amg_cfg* cfg) {
+  if (!h) return GS2_ERR_INVALID_ARG;
+  API_BEGIN
+  gs2_amg_cfg c{0.25, 10, 64};
+  if (cfg) c = *cfg;
+  if (h->n == 0) GS2_THROW(GS2_ERR_INVALID_ARG, "AMG of an empty matrix");
+  amg_build(h, c);
+  return GS2_OK;
+  API_END
+}
+
+gs2_status gs2_amg_info(const gs2_handle* h, int* levels, int64_t* rows, int64_t* nnz,
+                        int64_t* pnnz) {
+  if (!h || !levels) return GS2_ERR_INVALID_ARG;
+  amg_info(h, levels, rows, nnz, pnnz);
+  return GS2_OK;
+}
+
+gs2_status gs2_amg_vcycle(gs2_handle* h, const double* b, double* x, const gs2_params* p) {
+  if (!h || !p || (h->n && (!b || !x))) {
+    set_error("NULL argument");
+    return GS2_ERR_INVALID_ARG;
+  }
+  API_BEGIN
+  if (p->kind != GS2_PC_AMG && p->kind != GS2_PC_AMG_JR)
+    GS2_THROW(GS2_ERR_INVALID_ARG, "kind must be GS2_PC_AMG or GS2_PC_AMG_JR");
+  check_params(p);
+  if (h->n == 0) return GS2_OK;
+  amg_prepare(h, p);
+  Staged s(h, b, x, false);
+  amg_vcycle(h, p, s.b, s.x, false, nullptr);
   s.finish();
   return GS2_OK;
   API_END

@@ -87,6 +87,7 @@ struct KrylovState {
 };
 
 struct Profiler;
+struct AmgHierarchy;
 
 }  // namespace gs2
 
@@ -134,6 +135,10 @@ struct gs2_handle {
   int* stop_mapped_dev = nullptr;
 
   gs2::Profiler* prof = nullptr;
+
+  // smoothed-aggregation multigrid hierarchy (gs2_amg_setup, or built with
+  // default settings on first use as a preconditioner)
+  gs2::AmgHierarchy* amg = nullptr;
 
   // CUDA graph of one restart cycle's Arnoldi steps (launch-bound small
   // systems): captured on a private stream, replayed there and joined to
@@ -213,6 +218,10 @@ void launch_level(gs2_handle* h, const DevCsr& T, const int* rows, int r0,
 void launch_color(gs2_handle* h, const DevCsr& C, const int* rows, const double* bhat,
                   double* x, double omega, const int* skip);
 
+// y = M x (accumulate: y += M x) for any tiled matrix M whose columns index x
+void launch_spmv_matrix(gs2_handle* h, const DevCsr& M, const double* x, double* y,
+                        bool accumulate, const int* skip);
+
 void launch_axpy(gs2_handle* h, double* y, double a, const double* x,
                  const int* skip);
 void launch_copy(gs2_handle* h, double* dst, const double* src);
@@ -240,6 +249,25 @@ void ensure_levels(gs2_handle* h);
 void ensure_colors(gs2_handle* h);
 // level sets or colours a preconditioner needs, built on first use
 void ensure_precond(gs2_handle* h, const gs2_params* p);
+// p->outer sweeps of a GS2 or JR smoother (p->kind) on A x = b from the
+// current x, in direction p->direction (AMG post-smoothing)
+void smooth_sweeps(gs2_handle* h, const gs2_params* p, const double* b, double* x,
+                   const int* skip);
+
+// smoothed-aggregation AMG (amg.cu)
+constexpr int64_t kAmgMaxCoarse = 2048;  // rows of the exactly solved coarsest level
+void amg_build(gs2_handle* h, const gs2_amg_cfg& cfg);
+void amg_free(gs2_handle* h);
+// build the default hierarchy if there is none, and the smoother's precision
+void amg_prepare(gs2_handle* h, const gs2_params* p);
+void amg_info(const gs2_handle* h, int* levels, int64_t* rows, int64_t* nnz, int64_t* pnnz);
+int64_t amg_device_bytes(const gs2_handle* h);
+// x = M^{-1} b: one V-cycle from zero (p->kind GS2_PC_AMG or GS2_PC_AMG_JR)
+void amg_vcycle(gs2_handle* h, const gs2_params* p, const double* b, double* x,
+                bool rhat_ready, const int* skip);
+// a tiled CSR matrix on the device, held by h (api.cu)
+void upload_matrix(gs2_handle* h, DevCsr& M, int n, const std::vector<int>& rp,
+                   const std::vector<int>& ci, const std::vector<double>& va);
 void ensure_precision(gs2_handle* h, int prec);
 
 // solvers (krylov.cu)

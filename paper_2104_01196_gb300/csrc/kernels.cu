@@ -329,6 +329,18 @@ struct EpiSpmv {
   __device__ void finish(int i, double s, const Pre&) const { y[i] = s; }
 };
 
+// y += M x (multigrid prolongation)
+struct EpiSpmvAdd {
+  const double* __restrict__ x;
+  double* __restrict__ y;
+  struct Pre {
+    double y;
+  };
+  __device__ Pre pre(int i) const { return Pre{y[i]}; }
+  __device__ double gather(int c) const { return __ldg(x + c); }
+  __device__ void finish(int i, double s, const Pre& p) const { y[i] = p.y + s; }
+};
+
 // x_out = x_in + omega D^{-1} (b - A x_in)   (damped JR, ping-pong buffers)
 struct EpiJr {
   const double* __restrict__ x;
@@ -503,6 +515,19 @@ void launch_spmv(gs2_handle* h, const double* x, double* y, const int* skip) {
   KernelTimer tm(h, "spmv", bytes_csr(h->A, 8) + 16.0 * h->n);
   EpiSpmv e{x, y};
   dispatch<double>(h, h->A, h->A.va, e, skip);
+}
+
+void launch_spmv_matrix(gs2_handle* h, const DevCsr& M, const double* x, double* y,
+                        bool accumulate, const int* skip) {
+  KernelTimer tm(h, accumulate ? "amg_prolong" : "amg_restrict",
+                 bytes_csr(M, 8) + 8.0 * M.n * (accumulate ? 3.0 : 2.0));
+  if (accumulate) {
+    EpiSpmvAdd e{x, y};
+    dispatch<double>(h, M, M.va, e, skip);
+  } else {
+    EpiSpmv e{x, y};
+    dispatch<double>(h, M, M.va, e, skip);
+  }
 }
 
 // Autotuner probe: milliseconds per launch of y = M x over M's FP64 values

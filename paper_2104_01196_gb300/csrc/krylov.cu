@@ -742,7 +742,8 @@ struct GmresRun {
   // only, so a server can do it on a preparation thread.
   void ensure_graph() {
     std::vector<double> key = {(double)m, (double)(uintptr_t)h->V, (double)(uintptr_t)r64,
-                               (double)(uintptr_t)r32, (double)(uintptr_t)h->part};
+                               (double)(uintptr_t)r32, (double)(uintptr_t)h->part,
+                               (double)(uintptr_t)h->amg};
     if (pc) {
       const double pk[] = {(double)pc->kind, (double)pc->outer, (double)pc->inner, pc->omega,
                            pc->gamma, (double)pc->direction, (double)pc->precision,

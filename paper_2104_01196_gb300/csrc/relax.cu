@@ -212,13 +212,36 @@ void jr_relax(gs2_handle* h, const double* b, double* x, int sweeps, double omeg
 
 bool precond_wants_rhat(const gs2_params* p) {
   return p && (p->kind == GS2_PC_GS2 || p->kind == GS2_PC_JR || p->kind == GS2_PC_GS ||
-               p->kind == GS2_PC_MTGS);
+               p->kind == GS2_PC_MTGS || p->kind == GS2_PC_AMG || p->kind == GS2_PC_AMG_JR);
 }
 
+// (the AMG kinds start with the fine-level smoother from zero, which reads
+// D^{-1} v like the stand-alone smoother does)
 void* precond_rhat_buffer(gs2_handle* h, const gs2_params* p) {
   if (!precond_wants_rhat(p)) return nullptr;
-  if (p->kind == GS2_PC_GS2) return rhat_buf(h, p->precision);
+  if (p->kind == GS2_PC_GS2 || p->kind == GS2_PC_AMG) return rhat_buf(h, p->precision);
   return h->rhat;
+}
+
+void smooth_sweeps(gs2_handle* h, const gs2_params* p, const double* b, double* x,
+                   const int* skip) {
+  if (p->kind == GS2_PC_JR) {
+    const double* xin = x;
+    double* xout = h->t;
+    for (int s = 0; s < p->outer; ++s) {
+      launch_jr(h, b, xin, xout, p->omega, skip);
+      xin = xout;
+      xout = (xout == h->t) ? x : h->t;
+    }
+    if (xin != x) launch_copy_skip(h, x, xin, skip);
+    return;
+  }
+  for (int s = 0; s < p->outer; ++s) {
+    if (p->direction == GS2_FORWARD || p->direction == GS2_SYMMETRIC)
+      gs2_half(h, p, h->L, h->U, b, x, false, skip);
+    if (p->direction == GS2_BACKWARD || p->direction == GS2_SYMMETRIC)
+      gs2_half(h, p, h->U, h->L, b, x, false, skip);
+  }
 }
 
 void precond_apply(gs2_handle* h, const gs2_params* p, const double* v, double* z,
@@ -259,6 +282,10 @@ void precond_apply(gs2_handle* h, const gs2_params* p, const double* v, double* 
       xout = (xout == h->t) ? z : h->t;
     }
     if (xin != z) launch_copy_skip(h, z, xin, skip);
+    return;
+  }
+  if (p->kind == GS2_PC_AMG || p->kind == GS2_PC_AMG_JR) {
+    amg_vcycle(h, p, v, z, rhat_ready, skip);
     return;
   }
   if (p->kind == GS2_PC_MTGS) {

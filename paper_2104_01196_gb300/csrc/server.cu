@@ -69,6 +69,12 @@ static int64_t footprint(const gs2_server_cfg& c, int64_t n, int64_t nnz) {
   // pointers and tile descriptors, plus per-colour allocation slack
   if (c.has_precond && c.precond.kind == GS2_PC_MTGS)
     b += 12 * off + 8 * n + 4 * (n / 16 + 16) * 16 + (1 << 18);
+  // multigrid hierarchy: coarse matrices with their triangles and resident
+  // vectors (operator complexity below ~1.6 for the model problems), the
+  // transfer operators P and R (about 6 entries per fine row each), level
+  // vectors and the coarsest inverse
+  if (c.has_precond && (c.precond.kind == GS2_PC_AMG || c.precond.kind == GS2_PC_AMG_JR))
+    b += 40 * nnz + 160 * n + (64 << 20);
   return b + (1 << 20);
 }
 
@@ -285,7 +291,7 @@ gs2_status gs2_server_create(const gs2_server_cfg* cfg, gs2_server** out) {
   }
   if (cfg->has_precond) {
     const gs2_params& p = cfg->precond;
-    if (p.kind < GS2_PC_NONE || p.kind > GS2_PC_MTGS || p.outer < 1 || p.inner < 0 ||
+    if (p.kind < GS2_PC_NONE || p.kind > GS2_PC_AMG_JR || p.outer < 1 || p.inner < 0 ||
         !(p.omega > 0.0) || !(p.gamma > 0.0) || p.direction < 0 || p.direction > 2 ||
         p.precision < 0 || p.precision > 2) {
       set_error("bad preconditioner parameters");

@@ -60,10 +60,12 @@ def _alone(pr, pc):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "mtsgs"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "mtsgs", "amg"])
 def test_results_equal_alone_and_in_the_mix(lib, prec):
     if prec == "mtsgs":
         pc = gs2.params("mtgs", 1, direction="symmetric")
+    elif prec == "amg":
+        pc = gs2.params("amg", 1, 1, direction="symmetric")
     else:
         pc = gs2.params("gs2", 1, 1, direction="symmetric", precision=prec)
     probs = _mix()
