@@ -559,10 +559,15 @@ def comparisons(gs2, torch, pr, stream, b):
         "sgs2_1_1_fp16": gs2.params("gs2", 1, 1, direction="symmetric", precision="fp16"),
         "gs_levels_sym": gs2.params("gs", 1, direction="symmetric"),
         "mtsgs": gs2.params("mtgs", 1, direction="symmetric"),
+        "amg_sgs2_1_1": gs2.params("amg", 1, 1, direction="symmetric"),
         "jr3_w1.0": gs2.params("jr", 3, omega=1.0),
         "jr3_w0.8": gs2.params("jr", 3, omega=0.8),
     }
     h = gs2.gs2_setup(pr.A, precisions=("fp32", "fp16"), stream=stream.cuda_stream)
+    t0 = time.perf_counter()
+    h.amg_setup()  # smoothed-aggregation hierarchy (host setup, once per matrix)
+    res["amg_setup_s"] = round(time.perf_counter() - t0, 3)
+    res["amg_levels"] = [list(lv) for lv in h.amg_info()]
     with torch.cuda.stream(stream):
         x = torch.zeros(pr.n, dtype=torch.float64, device="cuda")
         for name, p in variants.items():

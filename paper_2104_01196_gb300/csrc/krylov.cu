@@ -142,7 +142,9 @@ __global__ void k_reduce_cols(const double* __restrict__ part, int nblk, double*
 // restarts use the MAXK = 64 forms with a runtime bound.
 // ---------------------------------------------------------------------------
 
-// pass 1: part = V[0..JC)^T w
+// pass 1: part = V[0..JC)^T w.  (Splitting the vectors over two block
+// groups, or two rows per iteration per thread, measured no faster: this
+// pass wants every resident warp.)
 template <int JC>
 __global__ void __launch_bounds__(kVecThreads)
 k_dots_x(int n, const double* __restrict__ V, const double* __restrict__ w, double* part,
@@ -161,25 +163,27 @@ k_dots_x(int n, const double* __restrict__ V, const double* __restrict__ w, doub
 
 // pass 2: w -= V h ; part = V^T w          (NORM = false)
 // pass 3: w -= V h ; part[0] = w^T w       (NORM = true)
-// V h is summed in two interleaved partial sums: a shorter FMA chain, and
-// only one extra FP64 add per row (the FP64 pipe is the limit here).
+// w_i - sum_k V_ki h_k is one FMA chain started at w_i with the negated
+// coefficients, so the update issues no FP64 instruction beyond its
+// products.  The FP64 pipe limits these passes, and at its issue interval
+// (one warp instruction per 64 cycles per scheduler) a dependent chain does
+// not stall.
 template <int JC, bool NORM>
 __global__ void __launch_bounds__(kVecThreads)
 k_update_x(int n, const double* __restrict__ V, const double* __restrict__ hcoef,
            double* __restrict__ w, double* part, int nblk, const int* skip) {
   if (skip && *skip) return;
-  __shared__ double hs[JC];
-  for (int k = threadIdx.x; k < JC; k += blockDim.x) hs[k] = hcoef[k];
+  __shared__ double hneg[JC];
+  for (int k = threadIdx.x; k < JC; k += blockDim.x) hneg[k] = -hcoef[k];
   __syncthreads();
   constexpr int NA = NORM ? 1 : JC;
   double acc[NA];
 #pragma unroll
   for (int k = 0; k < NA; ++k) acc[k] = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    double sp[2] = {0.0, 0.0};
+    double wn = w[i];
 #pragma unroll
-    for (int k = 0; k < JC; ++k) sp[k & 1] = fma(__ldg(V + (size_t)k * n + i), hs[k], sp[k & 1]);
-    const double wn = w[i] - (sp[0] + sp[1]);
+    for (int k = 0; k < JC; ++k) wn = fma(__ldg(V + (size_t)k * n + i), hneg[k], wn);
     w[i] = wn;
     if (NORM) {
       acc[0] = fma(wn, wn, acc[0]);

@@ -419,6 +419,7 @@ FULL_PCS = {
     "jr3_w1.0": dict(kind="jr", outer=3, omega=1.0),
     "jr3_w0.8": dict(kind="jr", outer=3, omega=0.8),
     "mtsgs": dict(kind="mtgs", outer=1, direction="symmetric"),
+    "amg_sgs2_1_1": dict(kind="amg", outer=1, inner=1, direction="symmetric"),
 }
 
 

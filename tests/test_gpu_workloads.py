@@ -138,10 +138,84 @@ def test_convdiff_gmres_error_vs_fp64_oracle(g, cd, prec):
         assert abs(info.iters - oinfo.iters) <= max(2, oinfo.iters // 10)
 
 
-def test_convdiff_full_size_sweeps(g):
+# ---------------------------------------------------------------------------
+# full-size configurations
+# ---------------------------------------------------------------------------
+
+def _oracle_count(key):
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "oracle_counts.txt")
+    for line in open(path):
+        if line.split() and line.split()[0] == key:
+            return int(dict(x.split("=") for x in line.split()[1:])["iters"])
+    raise KeyError(key)
+
+
+@pytest.fixture(scope="module")
+def cd192():
+    return P.convdiff3d(192)
+
+
+@pytest.fixture(scope="module")
+def ela64():
+    return P.elasticity3d(64)
+
+
+def test_elasticity_full_size_sweeps_and_solves(g, ela64):
+    """Q1 elasticity on 64^3 nodes (n = 786,432, 60.8M entries, ~77 per row):
+    one SGS2(1,1) sweep at omega = 0.8 in FP64 against the oracle on every
+    entry and with FP32 triangle values within their bound; GMRES(30) with
+    SGS2(1,2), omega = 0.8, within +-1 of the oracle's stored count in FP64
+    and within 5% with FP32 values (Sec. 6.3); true residuals recomputed by
+    the oracle's SpMV."""
+    pr = ela64
+    x0 = P.uniform_pm1(17, pr.n)
+    ref = oracle.gs2(pr.A, pr.b, x0, 1, 1, 0.8, 1.0, 2)
+    h = g.gs2_setup(pr.A, precisions=("fp32",))
+    for prec, bound in (("fp64", TOL), ("fp32", 2e-6)):
+        x = dev(x0)
+        g.gs2_apply_ex(h, dev(pr.b), x, g.params("gs2", 1, 1, omega=0.8,
+                                                  direction="symmetric", precision=prec))
+        assert rel(host(x), ref) <= bound, prec
+    want = _oracle_count("elasticity3d_64_gmres30_sgs2_1_2_w0.8")
+    for prec in ("fp64", "fp32"):
+        x = dev(np.zeros(pr.n))
+        info = g.gmres_solve(h, dev(pr.b), x, 30, 1e-8, 5000,
+                             g.params("gs2", 1, 2, omega=0.8, direction="symmetric",
+                                      precision=prec))
+        assert info.status == 0, prec
+        slack = 1 if prec == "fp64" else max(2, want // 20)
+        assert abs(info.iters - want) <= slack, (prec, info.iters, want)
+        r = np.linalg.norm(pr.b - oracle.spmv(pr.A, host(x))) / np.linalg.norm(pr.b)
+        assert r <= 1e-8 and abs(r - info.true_relres) <= 1e-10, prec
+
+
+def test_convdiff_full_size_gmres_all_precisions(g, cd192):
+    """192^3 upwind convection-diffusion (n = 7,077,888, nonsymmetric),
+    GMRES(30) + SGS2(1,1) to 1e-8 with FP64, FP32 and FP16-row-scaled inner
+    sweeps (residual and Arnoldi FP64): FP64 within +-1 of the oracle's
+    stored count, the others within 10%; every true residual recomputed by
+    the oracle's SpMV, and the error against the generating x_true."""
+    pr = cd192
+    want = _oracle_count("convdiff3d_192_gmres30_sgs2_1_1")
+    h = g.gs2_setup(pr.A, precisions=("fp32", "fp16"))
+    for prec in ("fp64", "fp32", "fp16"):
+        x = dev(np.zeros(pr.n))
+        info = g.gmres_solve(h, dev(pr.b), x, 30, 1e-8, 5000,
+                             g.params("gs2", 1, 1, direction="symmetric", precision=prec))
+        assert info.status == 0, prec
+        slack = 1 if prec == "fp64" else max(2, want // 10)
+        assert abs(info.iters - want) <= slack, (prec, info.iters, want)
+        xg = host(x)
+        r = np.linalg.norm(pr.b - oracle.spmv(pr.A, xg)) / np.linalg.norm(pr.b)
+        assert r <= 1e-8, prec
+        assert rel(xg, pr.x_true) <= 1e-5, prec
+
+
+def test_convdiff_full_size_sweeps(g, cd192):
     """192^3 (n = 7,077,888): one forward GS2(1,1) sweep in FP64 against the
     oracle on every entry, FP32 and FP16 inner sweeps within their bounds."""
-    pr = P.convdiff3d(192)
+    pr = cd192
     x0 = P.uniform_pm1(13, pr.n)
     ref = oracle.gs2(pr.A, pr.b, x0, 1, 1, 1.0, 1.0, 0)
     h = g.gs2_setup(pr.A, precisions=("fp32", "fp16"))
