@@ -338,15 +338,20 @@ def run_ours(args):
         kernels = kernel_table(warm, n, hbm)
         top = max(kernels, key=lambda k: kernels[k]["ms"]) if kernels else None
 
+    if top:
+        # inside the timed region only the dominant kernel is bracketed; one
+        # more untimed solve captures the Arnoldi-step graph with those event
+        # nodes, so no capture happens inside the timed region
+        h.profile_filter(top)
+        h.profile(True)
+        with torch.cuda.stream(stream):
+            solve()
+        stream.synchronize()
+        h.profile_reset()
     sampler = ClockSampler(local) if rank == 0 else None
     if sampler:
         sampler.start()
         time.sleep(0.3)
-    if top:
-        # inside the timed region only the dominant kernel is bracketed
-        h.profile_filter(top)
-        h.profile_reset()
-        h.profile(True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     iters = []

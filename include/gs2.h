@@ -150,11 +150,13 @@ gs2_status gs2_get_stats(const gs2_handle* h, gs2_handle_stats* out);
 gs2_status gs2_autotune(gs2_handle* h);
 
 /* How gmres_solve issues the Arnoldi steps of a restart cycle:
- * 0 (default) = as one replayed CUDA graph for n <= 524,288 and as separate
- * launches above; 1 = always a graph; 2 = never.  A graph is captured once
- * per cycle shape (restart, preconditioner) on a private stream joined to
- * the handle's stream; results are the same either way, bit for bit.
- * Graphs are not used while per-kernel profiling is enabled. */
+ * 0 (default) and 1 = as one replayed CUDA graph; 2 = as separate launches.
+ * A graph is captured once per cycle shape (restart, preconditioner,
+ * profiling settings) on a private stream joined to the handle's stream;
+ * steps after the device has ended the cycle run as no-ops.  Results are
+ * the same either way, bit for bit.  With per-kernel profiling enabled the
+ * graph carries event nodes around the profiled kernels, and only the steps
+ * a cycle ran are counted. */
 gs2_status gs2_set_graph_mode(gs2_handle* h, int mode);
 
 /* Non-compact GS2 relaxation, Eq. (4) with inner JR sweeps Eq. (5)-(7):

@@ -41,9 +41,23 @@ struct Profiler {
     int id;
     cudaEvent_t a, b;
     double bytes;
+    int step;  // Arnoldi step of an eager cycle, -1 outside one
   };
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> pool;
+  // Event pairs captured into an Arnoldi-step graph: recorded as external
+  // event nodes at every replay and read after each replay of a cycle,
+  // counting only the steps the cycle ran (later steps are no-ops).
+  struct Captured {
+    int id;
+    cudaEvent_t a, b;
+    double bytes;
+    int step;
+  };
+  std::vector<Captured> captured;
+  bool capturing = false;
+  int cap_step = -1;  // step of the launches being issued (graph or eager), or -1
+  int epoch = 0;  // changes with enable/filter, so graphs are re-captured
 
   cudaEvent_t get() {
     if (!pool.empty()) {
@@ -80,7 +94,42 @@ struct Profiler {
     }
     pending.clear();
   }
+  void clear_captured() {
+    for (auto& c : captured) {
+      cudaEventDestroy(c.a);
+      cudaEventDestroy(c.b);
+    }
+    captured.clear();
+  }
+  // after an eager cycle that ran `steps` steps: launches of later steps
+  // (issued before the host saw the device stop) ran as no-ops
+  void settle(int steps) {
+    std::vector<Pending> keep;
+    keep.reserve(pending.size());
+    for (auto& p : pending) {
+      if (p.step >= steps) {
+        pool.push_back(p.a);
+        pool.push_back(p.b);
+      } else {
+        p.step = -1;
+        keep.push_back(p);
+      }
+    }
+    pending.swap(keep);
+  }
+  void harvest(int steps) {
+    for (auto& c : captured) {
+      if (c.step >= steps) continue;
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, c.a, c.b) == cudaSuccess) {
+        stats[c.id].launches += 1;
+        stats[c.id].total_ms += ms;
+        stats[c.id].bytes += c.bytes;
+      }
+    }
+  }
   ~Profiler() {
+    clear_captured();
     for (auto& p : pending) {
       cudaEventDestroy(p.a);
       cudaEventDestroy(p.b);
@@ -91,22 +140,62 @@ struct Profiler {
 
 bool profiling_active(const gs2_handle* h) { return h->prof && h->prof->enabled; }
 
+int profile_epoch(const gs2_handle* h) {
+  return profiling_active(h) ? h->prof->epoch : -1;
+}
+
+void profile_capture_begin(gs2_handle* h) {
+  if (!profiling_active(h)) return;
+  h->prof->clear_captured();
+  h->prof->capturing = true;
+}
+
+void profile_capture_step(gs2_handle* h, int step) {
+  if (profiling_active(h)) h->prof->cap_step = step;
+}
+
+void profile_capture_end(gs2_handle* h) {
+  if (!h->prof) return;
+  h->prof->capturing = false;
+  h->prof->cap_step = -1;
+}
+
+void profile_harvest(gs2_handle* h, int steps, bool graph) {
+  if (!profiling_active(h)) return;
+  if (graph) h->prof->harvest(steps);
+  else h->prof->settle(steps);
+}
+
 KernelTimer::KernelTimer(gs2_handle* h_, const char* name, double bytes_)
     : h(h_), id(-1), bytes(bytes_) {
   if (h->prof && h->prof->enabled && (h->prof->only.empty() || h->prof->only == name)) {
     id = h->prof->id_of(name);
-    e0 = h->prof->get();
-    cudaEventRecord(e0, h->stream);
+    if (h->prof->capturing) {
+      cudaEventCreate(&e0);
+      cudaEventRecordWithFlags(e0, h->stream, cudaEventRecordExternal);
+    } else {
+      e0 = h->prof->get();
+      cudaEventRecord(e0, h->stream);
+    }
   }
 }
 
 KernelTimer::~KernelTimer() {
   if (id >= 0 && e0) {
+    if (h->prof->capturing) {
+      cudaEvent_t e1 = nullptr;
+      cudaEventCreate(&e1);
+      cudaEventRecordWithFlags(e1, h->stream, cudaEventRecordExternal);
+      h->prof->captured.push_back({id, e0, e1, bytes, h->prof->cap_step});
+      return;
+    }
     cudaEvent_t e1 = h->prof->get();
     cudaEventRecord(e1, h->stream);
-    h->prof->pending.push_back({id, e0, e1, bytes});
-    // keep the pending list bounded on long runs
-    if (h->prof->pending.size() > 4096) h->prof->resolve(h->stream);
+    h->prof->pending.push_back({id, e0, e1, bytes, h->prof->cap_step});
+    // keep the pending list bounded on long runs (never inside a cycle,
+    // whose trailing launches are settled when it ends)
+    if (h->prof->cap_step < 0 && h->prof->pending.size() > 16384)
+      h->prof->resolve(h->stream);
   }
 }
 
@@ -926,6 +1015,7 @@ gs2_status gs2_profile_enable(gs2_handle* h, int enable) {
   if (!h) return GS2_ERR_INVALID_ARG;
   if (!h->prof) h->prof = new gs2::Profiler();
   h->prof->enabled = enable != 0;
+  h->prof->epoch++;
   return GS2_OK;
 }
 
@@ -974,6 +1064,7 @@ gs2_status gs2_profile_filter(gs2_handle* h, const char* name) {
   if (!h) return GS2_ERR_INVALID_ARG;
   if (!h->prof) h->prof = new gs2::Profiler();
   h->prof->only = name ? name : "";
+  h->prof->epoch++;
   return GS2_OK;
 }
 

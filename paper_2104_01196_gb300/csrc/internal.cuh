@@ -143,7 +143,7 @@ struct gs2_handle {
   // CUDA graph of one restart cycle's Arnoldi steps (launch-bound small
   // systems): captured on a private stream, replayed there and joined to
   // `stream` with events; re-captured when the cycle's shape changes
-  int graph_mode = 0;  // 0: automatic (n <= kGraphMaxRows), 1: always, 2: never
+  int graph_mode = 0;  // 0: automatic (graphs), 1: always, 2: never
   cudaStream_t gstream = nullptr;
   cudaEvent_t gev_in = nullptr, gev_out = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -167,6 +167,17 @@ namespace gs2 {
 // ---------------------------------------------------------------------------
 
 bool profiling_active(const gs2_handle* h);
+// Profiling of restart cycles.  Launches are tagged with the Arnoldi step
+// set by capture_step (-1 outside a cycle).  In a captured graph (between
+// capture_begin and capture_end) they are bracketed by external event
+// nodes; after a cycle that ran `steps` steps, harvest counts only the
+// launches of those steps: from the graph's event nodes, or, for an eager
+// cycle, by dropping the pending launches of later (no-op) steps.
+int profile_epoch(const gs2_handle* h);
+void profile_capture_begin(gs2_handle* h);
+void profile_capture_step(gs2_handle* h, int step);
+void profile_capture_end(gs2_handle* h);
+void profile_harvest(gs2_handle* h, int steps, bool graph);
 
 struct KernelTimer {
   gs2_handle* h;
@@ -309,8 +320,5 @@ int vec_blocks(gs2_handle* h, int64_t n);
 constexpr int kVecThreads = 256;
 constexpr int kRowThreads = 256;
 constexpr int kMaxRestart = 64;
-// systems up to this size replay their Arnoldi steps as a CUDA graph by
-// default; above it the kernels are long enough that launch cost is noise
-constexpr int64_t kGraphMaxRows = 1 << 19;
 
 }  // namespace gs2

@@ -664,10 +664,18 @@ struct GmresRun {
     done = true;
   }
 
+  bool cycle_ran = false;  // a cycle was issued since the last advance
+  bool graph_ran = false;  // ... as a replay of the step graph
+
   // Called with the stream synchronised.
   void advance() {
     if (done) return;
     const KrylovState& hs = *h->st_host;
+    if (cycle_ran) {
+      // before the next replay re-records the graph's events
+      profile_harvest(h, hs.k, graph_ran);
+      cycle_ran = graph_ran = false;
+    }
     if (first) {
       first = false;
       bnorm = hs.bnorm;
@@ -724,10 +732,9 @@ struct GmresRun {
     }
   }
 
-  bool use_graph() const {
-    if (profiling_active(h)) return false;  // event timing needs eager launches
-    return h->graph_mode == 1 || (h->graph_mode == 0 && h->n <= kGraphMaxRows);
-  }
+  // Graphs by default at every size: even at n = 2.1M the launch gaps of
+  // separate launches cost ~6% of a solve.
+  bool use_graph() const { return h->graph_mode != 2; }
 
   // The m steps as one CUDA graph: captured once per cycle shape on the
   // handle's private stream, replayed there between two event joins with
@@ -747,7 +754,7 @@ struct GmresRun {
   void ensure_graph() {
     std::vector<double> key = {(double)m, (double)(uintptr_t)h->V, (double)(uintptr_t)r64,
                                (double)(uintptr_t)r32, (double)(uintptr_t)h->part,
-                               (double)(uintptr_t)h->amg};
+                               (double)(uintptr_t)h->amg, (double)profile_epoch(h)};
     if (pc) {
       const double pk[] = {(double)pc->kind, (double)pc->outer, (double)pc->inner, pc->omega,
                            pc->gamma, (double)pc->direction, (double)pc->precision,
@@ -766,15 +773,21 @@ struct GmresRun {
       h->stream = h->gstream;
       const long long c0 = gs2_launch_count();
       cudaGraph_t g = nullptr;
+      profile_capture_begin(h);
       GS2_CUDA(cudaStreamBeginCapture(h->gstream, cudaStreamCaptureModeThreadLocal));
       try {
-        for (int j = 0; j < m; ++j) enqueue_step(j);
+        for (int j = 0; j < m; ++j) {
+          profile_capture_step(h, j);
+          enqueue_step(j);
+        }
       } catch (...) {
+        profile_capture_end(h);
         cudaStreamEndCapture(h->gstream, &g);
         if (g) cudaGraphDestroy(g);
         h->stream = user;
         throw;
       }
+      profile_capture_end(h);
       h->stream = user;
       GS2_CUDA(cudaStreamEndCapture(h->gstream, &g));
       h->g_launches = gs2_launch_count() - c0;
@@ -795,13 +808,17 @@ struct GmresRun {
     k_cycle_start<<<vec_blocks(h, n), kVecThreads, 0, h->stream>>>(n, h->r, h->V, h->dinv, r64,
                                                                   r32, h->gvec, m, h->st);
     GS2_LAUNCH_CHECK();
+    cycle_ran = true;
     if (use_graph()) {
       graph_steps();
+      graph_ran = true;
     } else {
       for (int j = 0; j < m; ++j) {
         if (*h->stop_mapped) break;  // the device has already ended the cycle
+        profile_capture_step(h, j);
         enqueue_step(j);
       }
+      profile_capture_step(h, -1);
     }
     // x += M^{-1} V y
     k_backsolve<<<1, 64, 0, h->stream>>>(h->H, ldh, h->gvec, h->y, h->st);

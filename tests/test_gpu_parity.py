@@ -475,3 +475,23 @@ def test_graph_and_eager_cycles_agree_bitwise(g, pc):
     for k in (0, 1):
         assert res[(1, k)][0] == res[(2, k)][0]
         assert np.array_equal(res[(1, k)][1], res[(2, k)][1])
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_profiled_launch_counts_in_graph_and_eager_cycles(g, mode):
+    """Per-kernel profiling counts exactly the Arnoldi steps that ran, also
+    when the steps replay as a graph whose trailing steps are no-ops."""
+    pr = P.poisson2d(64)
+    h = g.gs2_setup(pr.A)
+    h.set_graph_mode(mode)
+    h.profile(True)
+    h.profile_reset()
+    x = dev(np.zeros(pr.n))
+    info = g.gmres_solve(h, dev(pr.b), x, 30, 1e-8, 5000,
+                         g.params("gs2", 1, 1, direction="symmetric"))
+    st = h.profile_read()
+    h.profile(False)
+    assert info.status == 0 and info.iters % 30 != 0  # the last cycle stops early
+    assert st["spmv"]["launches"] == info.iters
+    assert st["cgs2_upd_norm"]["launches"] == info.iters
+    assert all(v["total_ms"] > 0 for v in st.values() if v["launches"])
