@@ -202,7 +202,7 @@ def run_reference(args):
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12  # 2 FMA/clk/SM x 2 flop x 152 SMs x 2.07 GHz
 
 
-def kernel_flops(name, st, n):
+def kernel_flops(name, st, n, nnz=None):
     """FP64 flops of a kernel's timed launches, from its algorithmic bytes
     (the CGS2 passes read 8n bytes per basis vector)."""
     L, B = st["launches"], st["bytes"]
@@ -215,7 +215,7 @@ def kernel_flops(name, st, n):
     return None
 
 
-def kernel_table(stats, n, hbm):
+def kernel_table(stats, n, hbm, nnz=None):
     out = {}
     for name, s in stats.items():
         if not s["launches"] or s["total_ms"] <= 0:
@@ -223,7 +223,7 @@ def kernel_table(stats, n, hbm):
         gbs = s["bytes"] / (s["total_ms"] / 1000.0) / 1e9
         row = {"launches": s["launches"], "ms": round(s["total_ms"], 3), "share": None,
                "gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 3)}
-        fl = kernel_flops(name, s, n)
+        fl = kernel_flops(name, s, n, nnz)
         if fl is not None:
             tf = fl / (s["total_ms"] / 1000.0) / 1e12
             row["fp64_tflops"] = round(tf, 3)
@@ -235,14 +235,15 @@ def kernel_table(stats, n, hbm):
     return out
 
 
-def roofline(name, s, n, hbm, peak_kind, grid):
+def roofline(name, s, n, hbm, peak_kind, grid, nnz=None):
     per_launch_bytes = s["bytes"] / s["launches"]
     per_launch_ms = s["total_ms"] / s["launches"]
     gbs = per_launch_bytes / (per_launch_ms / 1000.0) / 1e9
-    fl = kernel_flops(name, s, n)
+    fl = kernel_flops(name, s, n, nnz)
     traffic = stored_traffic(name, per_launch_bytes)
-    if fl is not None:
-        tf = fl / s["launches"] / (per_launch_ms / 1000.0) / 1e12
+    tf = None if fl is None else fl / s["launches"] / (per_launch_ms / 1000.0) / 1e12
+    # the bound reported is the resource the kernel uses the larger share of
+    if tf is not None and tf / FP64_PEAK_TFLOPS >= gbs / hbm:
         return {"bound": "alu", "kernel": name, "achieved": round(tf, 4),
                 "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
                 "frac": round(tf / FP64_PEAK_TFLOPS, 3), "traffic": traffic,
@@ -335,7 +336,7 @@ def run_ours(args):
     if not args.no_profile:
         warm = h.profile_read()
         h.profile(False)
-        kernels = kernel_table(warm, n, hbm)
+        kernels = kernel_table(warm, n, hbm, len(pr.A[1]))
         top = max(kernels, key=lambda k: kernels[k]["ms"]) if kernels else None
 
     if top:
@@ -388,7 +389,7 @@ def run_ours(args):
 
     roof = None
     if top and top in timed and timed[top]["launches"]:
-        roof = roofline(top, timed[top], n, hbm, peak_kind, args.grid)
+        roof = roofline(top, timed[top], n, hbm, peak_kind, args.grid, len(pr.A[1]))
     sweep = {k: kernels[k] for k in ("resid", "inner64") if k in kernels}
 
     out = {

@@ -12,286 +12,15 @@
 // warp-per-row reduction (whose shuffle-add tree runs on every lane) would
 // spend more FP64 issue slots on the tree than on the products.  Rows are
 // therefore reduced sequentially by one thread (or by K contiguous segments
-// for long rows), with the row's values and column indices staged into
-// shared memory by coalesced 128-bit streaming loads, one tile of
-// consecutive rows per block iteration.  x-gathers go through the
-// read-only path and stay L2-resident.
-#include <cuda_fp16.h>
-
-#include <cstdint>
-#include <map>
-#include <mutex>
-#include <utility>
-
-#include "internal.cuh"
+// for long rows), with each tile's row pointers, columns and values staged
+// into shared memory by TMA bulk copies (tiles.cuh).  x-gathers go through
+// the read-only path and stay L2-resident.  (Fusing the SpMV with the first
+// Gram-Schmidt dot pass of an Arnoldi step was measured: the fused kernel
+// reached only ~0.65 of both the HBM and the FP64 rate, 3% faster than the
+// two kernels apart, and is not kept.)
+#include "tiles.cuh"
 
 namespace gs2 {
-
-// ---------------------------------------------------------------------------
-// small device helpers
-// ---------------------------------------------------------------------------
-
-template <int K, typename T>
-__device__ __forceinline__ T group_sum(T s) {
-#pragma unroll
-  for (int o = K / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, K);
-  return s;
-}
-
-template <typename T>
-__device__ __forceinline__ T block_sum(T s, T* red) {
-  // deterministic: fixed shuffle tree inside warps, then warp 0 over warps
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  __syncthreads();
-  if (lane == 0) red[wid] = s;
-  __syncthreads();
-  const int nw = blockDim.x >> 5;
-  if (wid == 0) {
-    s = lane < nw ? red[lane] : T(0);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  }
-  return s;  // valid in thread 0
-}
-
-template <typename VT>
-struct ValTraits;
-template <>
-struct ValTraits<double> {
-  using AT = double;
-  __device__ static double get(const double* p, int k) { return p[k]; }
-};
-template <>
-struct ValTraits<float> {
-  using AT = float;
-  __device__ static float get(const float* p, int k) { return p[k]; }
-};
-template <>
-struct ValTraits<__half> {
-  using AT = float;
-  __device__ static float get(const __half* p, int k) { return __half2float(p[k]); }
-};
-
-// ---------------------------------------------------------------------------
-// TMA bulk copies and mbarriers (inline PTX, sm_90+ / sm_103a)
-// ---------------------------------------------------------------------------
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-               : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-// order this thread's (and, after a barrier, the block's) generic-proxy
-// accesses of shared memory before later async-proxy (TMA) writes
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t tx) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(tx)
-               : "memory");
-}
-__device__ __forceinline__ uint64_t l2_evict_first_policy() {
-  uint64_t pol;
-  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-  return pol;
-}
-// 1-D bulk copy global -> shared, completion counted on `bar` in bytes;
-// src and dst 16-byte aligned, bytes a positive multiple of 16
-__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes,
-                                            uint64_t* bar, uint64_t policy) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
-      "[%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
-      : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait: gives up after ~2 s of SM clock so that a wrong transaction
-// count can never hang the GPU; the caller reports GS2_ERR_TIMEOUT.
-constexpr long long kWaitBudgetCycles = 4LL << 30;
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity))
-    if (clock64() - t0 > kWaitBudgetCycles) return false;
-  return true;
-}
-
-// ---------------------------------------------------------------------------
-// tile engine
-// ---------------------------------------------------------------------------
-
-// Matrix view for the engine.  Tile t = rows [d.x, d.y) with d = desc[t];
-// d.z = first staged entry (rowptr[d.x] rounded down to 8) and d.w =
-// rowptr[d.y]; a tile holding one row longer than `cap` entries has
-// d.z = -1 - rowptr[d.x] and is processed from global memory by the block.
-template <typename VT>
-struct TileMat {
-  int n;
-  int ntiles;
-  int cap;   // max staged entries of a normal tile (multiple of 8)
-  int rcap;  // max rows of a tile
-  const int* __restrict__ rp;
-  const int* __restrict__ ci;
-  const VT* __restrict__ va;
-  const int4* __restrict__ desc;
-  int* err;  // set to GS2_ERR_TIMEOUT if a copy never completes
-};
-
-__host__ __device__ constexpr int round16(int b) { return (b + 15) & ~15; }
-
-template <typename VT>
-struct StageLayout {
-  int rp_off, ci_off, va_off, bytes;
-  __host__ __device__ StageLayout(int rcap, int cap) {
-    rp_off = 0;
-    ci_off = round16((rcap + 8) * 4);
-    va_off = ci_off + round16((cap + 8) * 4);
-    bytes = ((va_off + round16((cap + 8) * (int)sizeof(VT))) + 127) & ~127;
-  }
-};
-
-// Engine: for every row i, acc_i = sum_k va[k] * epi.gather(ci[k]), then
-// epi.finish(i, acc_i).  Double-buffered: while the block reduces tile t
-// from one shared-memory stage, one thread has TMA fill the other stage
-// with tile t + grid (its rowptr slice, columns and values), completion
-// tracked by one mbarrier per stage.  Rows are reduced by one thread each
-// (K = 1) or by K contiguous segments and a K-wide shuffle tree; each group
-// of K lanes takes RPT rows of a tile (RPT * 256 / K rows per tile).  The
-// epilogue's per-row operands are loaded before the gathers.
-template <int K, int RPT, typename VT, class Epi>
-__global__ void __launch_bounds__(kRowThreads)
-k_tiles(TileMat<VT> M, Epi epi, const int* skip) {
-  using AT = typename ValTraits<VT>::AT;
-  if (skip && *skip) return;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bars[2];
-  __shared__ AT red[kRowThreads / 32];
-  const StageLayout<VT> L(M.rcap, M.cap);
-  const int q = threadIdx.x / K;  // row slot inside the tile
-  const int l = threadIdx.x % K;  // segment of the row
-  uint64_t policy = 0;
-
-  // thread 0: describe and start the copies of tile t into stage st
-  auto issue = [&](int t, int st) {
-    const int4 d = M.desc[t];
-    unsigned char* base = smem_raw + (size_t)st * L.bytes;
-    uint32_t tx = 0;
-    uint32_t brp = 0, bci = 0, bva = 0;
-    if (d.z >= 0) {
-      const int rpb = d.x & ~3;
-      brp = (uint32_t)round16((d.y + 1 - rpb) * 4);
-      const int cnt = d.w - d.z;
-      bci = (uint32_t)round16(cnt * 4);
-      bva = cnt > 0 ? (uint32_t)round16(cnt * (int)sizeof(VT)) : 0u;
-      if (cnt == 0) bci = 0;
-      tx = brp + bci + bva;
-    }
-    mbar_arrive_expect_tx(&bars[st], tx);
-    if (d.z >= 0) {
-      tma_load_1d(base + L.rp_off, M.rp + (d.x & ~3), brp, &bars[st], policy);
-      if (bci) tma_load_1d(base + L.ci_off, M.ci + d.z, bci, &bars[st], policy);
-      if (bva) tma_load_1d(base + L.va_off, M.va + d.z, bva, &bars[st], policy);
-    }
-  };
-
-  if (threadIdx.x == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
-    fence_mbar_init();
-    policy = l2_evict_first_policy();
-    if ((int)blockIdx.x < M.ntiles) issue(blockIdx.x, 0);
-  }
-  __syncthreads();
-
-  int it = 0;
-  for (int t = blockIdx.x; t < M.ntiles; t += gridDim.x, ++it) {
-    const int st = it & 1;
-    const int tn = t + gridDim.x;
-    if (threadIdx.x == 0 && tn < M.ntiles) {
-      fence_proxy_async_smem();
-      issue(tn, st ^ 1);
-    }
-    const int4 d = M.desc[t];
-    const bool ok = mbar_wait_bounded(&bars[st], (it >> 1) & 1);
-    if (__syncthreads_or(!ok)) {
-      if (threadIdx.x == 0 && M.err) atomicExch(M.err, (int)GS2_ERR_TIMEOUT);
-      return;
-    }
-    if (d.z < 0) {
-      // one long row: whole block, straight from global memory
-      const int a = -1 - d.z;
-      AT s = AT(0);
-      for (int k = a + threadIdx.x; k < d.w; k += blockDim.x)
-        s = fma((AT)ValTraits<VT>::get(M.va, k), (AT)epi.gather(M.ci[k]), s);
-      s = block_sum<AT>(s, red);
-      if (threadIdx.x == 0) epi.finish(d.x, s, epi.pre(d.x));
-      __syncthreads();
-      continue;
-    }
-    const unsigned char* base = smem_raw + (size_t)st * L.bytes;
-    const int* s_rp = reinterpret_cast<const int*>(base + L.rp_off);
-    const int* s_ci = reinterpret_cast<const int*>(base + L.ci_off);
-    const VT* s_va = reinterpret_cast<const VT*>(base + L.va_off);
-    const int rpb = d.x & ~3;
-#pragma unroll
-    for (int rr = 0; rr < RPT; ++rr) {
-      const int row = d.x + q + rr * (kRowThreads / K);
-      AT s = AT(0);
-      typename Epi::Pre pv{};
-      if (row < d.y) {
-        pv = epi.pre(row);
-        const int rs = s_rp[row - rpb] - d.z, re = s_rp[row + 1 - rpb] - d.z;
-        int ks = rs, ke = re;
-        if (K > 1) {
-          const int seg = (re - rs + K - 1) / K;
-          ks = min(rs + l * seg, re);
-          ke = min(ks + seg, re);
-        }
-        int k = ks;
-        // groups of four: all four gathers are in flight before the FMAs
-        for (; k + 4 <= ke; k += 4) {
-          const AT x0 = (AT)epi.gather(s_ci[k]), x1 = (AT)epi.gather(s_ci[k + 1]);
-          const AT x2 = (AT)epi.gather(s_ci[k + 2]), x3 = (AT)epi.gather(s_ci[k + 3]);
-          s = fma((AT)ValTraits<VT>::get(s_va, k), x0, s);
-          s = fma((AT)ValTraits<VT>::get(s_va, k + 1), x1, s);
-          s = fma((AT)ValTraits<VT>::get(s_va, k + 2), x2, s);
-          s = fma((AT)ValTraits<VT>::get(s_va, k + 3), x3, s);
-        }
-        const int rem = ke - k;
-        if (rem > 0) {
-          const AT x0 = (AT)epi.gather(s_ci[k]);
-          const AT x1 = rem > 1 ? (AT)epi.gather(s_ci[k + 1]) : AT(0);
-          const AT x2 = rem > 2 ? (AT)epi.gather(s_ci[k + 2]) : AT(0);
-          s = fma((AT)ValTraits<VT>::get(s_va, k), x0, s);
-          if (rem > 1) s = fma((AT)ValTraits<VT>::get(s_va, k + 1), x1, s);
-          if (rem > 2) s = fma((AT)ValTraits<VT>::get(s_va, k + 2), x2, s);
-        }
-      }
-      if (K > 1) s = group_sum<K, AT>(s);
-      if (row < d.y && l == 0) epi.finish(row, s, pv);
-    }
-    __syncthreads();
-  }
-}
 
 // ---------------------------------------------------------------------------
 // epilogues: pre(i) loads the row's operands before the gathers, finish(i,
@@ -425,6 +154,7 @@ struct EpiColor {
   }
 };
 
+
 // ---------------------------------------------------------------------------
 // launch plumbing
 // ---------------------------------------------------------------------------
@@ -434,7 +164,7 @@ struct EpiColor {
 // call cost microseconds of host time per launch otherwise).  The dynamic
 // shared-memory limit is one attribute per kernel, so it is only ever
 // raised: matrices with smaller tiles keep launching under the larger limit.
-static int blocks_per_sm(const void* fn, size_t smem) {
+int blocks_per_sm(const void* fn, size_t smem) {
   static std::mutex mu;
   static std::map<std::pair<const void*, size_t>, int> cache;
   static std::map<const void*, size_t> attr;
@@ -455,52 +185,7 @@ static int blocks_per_sm(const void* fn, size_t smem) {
   return per_sm;
 }
 
-template <typename VT>
-static TileMat<VT> view(gs2_handle* h, const DevCsr& M, const VT* va) {
-  TileMat<VT> t;
-  t.n = M.n;
-  t.ntiles = M.ntiles;
-  t.cap = M.cap;
-  t.rcap = M.rpt * kRowThreads / M.tpr;
-  t.rp = M.rp;
-  t.ci = M.ci;
-  t.va = va;
-  t.desc = M.desc;
-  t.err = h->dev_err;
-  return t;
-}
 
-template <int K, int RPT, typename VT, class Epi>
-static void launch_k(gs2_handle* h, const DevCsr& M, const VT* va, const Epi& epi,
-                     const int* skip) {
-  if (M.n == 0 || M.ntiles == 0) return;
-  const size_t smem = 2 * (size_t)StageLayout<VT>(RPT * kRowThreads / K, M.cap).bytes;
-  auto fn = k_tiles<K, RPT, VT, Epi>;
-  const int per_sm = blocks_per_sm((const void*)fn, smem);
-  const int grid = std::min(M.ntiles, per_sm * h->nsm);
-  fn<<<grid, kRowThreads, smem, h->stream>>>(view<VT>(h, M, va), epi, skip);
-  GS2_LAUNCH_CHECK();
-}
-
-// (K, RPT) shapes: RPT = 2 only for short rows (K <= 2), where the per-tile
-// barrier and stage overhead is largest relative to the work per row
-template <typename VT, class Epi>
-static void dispatch(gs2_handle* h, const DevCsr& M, const VT* va, const Epi& epi,
-                     const int* skip) {
-  switch (M.tpr * 4 + (M.rpt == 2 ? 1 : 0)) {
-    case 1 * 4 + 1: launch_k<1, 2, VT, Epi>(h, M, va, epi, skip); break;
-    case 2 * 4 + 1: launch_k<2, 2, VT, Epi>(h, M, va, epi, skip); break;
-    case 1 * 4: launch_k<1, 1, VT, Epi>(h, M, va, epi, skip); break;
-    case 2 * 4: launch_k<2, 1, VT, Epi>(h, M, va, epi, skip); break;
-    case 4 * 4: launch_k<4, 1, VT, Epi>(h, M, va, epi, skip); break;
-    case 8 * 4: launch_k<8, 1, VT, Epi>(h, M, va, epi, skip); break;
-    default: launch_k<16, 1, VT, Epi>(h, M, va, epi, skip); break;
-  }
-}
-
-static double bytes_csr(const DevCsr& M, int vbytes) {
-  return (double)M.nnz * (4.0 + vbytes) + 4.0 * (M.n + 1);
-}
 
 void launch_resid(gs2_handle* h, const double* b, const double* x, double* r_out,
                   double* rhat64, float* rhat32, const int* skip) {

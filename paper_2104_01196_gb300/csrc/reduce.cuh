@@ -1,0 +1,76 @@
+// Fixed-order block reductions of per-thread FP64 partial sums used by the
+// Krylov kernels.  Deterministic: the same shuffle pattern and the same
+// summation order on every run.
+#pragma once
+
+#include "internal.cuh"
+
+namespace gs2 {
+
+__device__ __forceinline__ double warp_sum(double s) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+template <int N>
+struct Pow2 {
+  static constexpr int value = N <= 1 ? 1 : 2 * Pow2<(N + 1) / 2>::value;
+};
+template <>
+struct Pow2<1> {
+  static constexpr int value = 1;
+};
+template <int P>
+struct Log2 {
+  static constexpr int value = P <= 1 ? 0 : 1 + Log2<P / 2>::value;
+};
+template <>
+struct Log2<1> {
+  static constexpr int value = 0;
+};
+
+// Block-wide sums of NV <= 32 per-thread values.  Inside a warp a butterfly
+// transpose-reduction halves the values each lane holds at every exchange,
+// P - 1 adds per lane for P = NV rounded up to a power of two, instead of
+// 5 adds per value of a shuffle tree -- the FP64 pipe is the bottleneck of
+// these kernels.  After it lane l holds the warp's sum of value l >> (5 - p).
+template <int NV>
+__device__ __forceinline__ void block_partials_bf(const double (&acc)[NV], double* part,
+                                                  int nblk) {
+  constexpr int P = Pow2<NV>::value;
+  constexpr int p = Log2<P>::value;
+  static_assert(P <= 32, "butterfly reduction holds at most 32 values");
+  __shared__ double red[kVecThreads / 32][P];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double a[P];
+#pragma unroll
+  for (int k = 0; k < P; ++k) a[k] = k < NV ? acc[k] : 0.0;
+#pragma unroll
+  for (int s = 0; s < p; ++s) {
+    const int off = 16 >> s;
+    const int half = (P >> s) / 2;
+    const bool upper = (lane & off) != 0;
+#pragma unroll
+    for (int j = 0; j < half; ++j) {
+      const double send = upper ? a[j] : a[j + half];
+      const double recv = __shfl_xor_sync(0xffffffffu, send, off);
+      a[j] = (upper ? a[j + half] : a[j]) + recv;
+    }
+  }
+  // lanes that differ only in their low 5 - p bits hold parts of the same
+  // value: finish with a plain tree over those bits
+#pragma unroll
+  for (int o = 16 >> p; o > 0; o >>= 1) a[0] += __shfl_xor_sync(0xffffffffu, a[0], o);
+  const int k = lane >> (5 - p);
+  if ((lane & ((1 << (5 - p)) - 1)) == 0) red[wid][k] = a[0];
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kVecThreads / 32; ++w) s += red[w][threadIdx.x];
+    part[(size_t)threadIdx.x * nblk + blockIdx.x] = s;
+  }
+}
+
+}  // namespace gs2
