@@ -196,3 +196,29 @@ def test_rebuild_replaces_hierarchy_and_rejects_bad_settings(g):
     info = g.gmres_solve(h, dev(pr.b), x, 30, 1e-8, 500,
                          g.params("amg", 1, 1, direction="symmetric"))
     assert info.status == 0 and h.amg_info() == deep
+
+
+def test_degenerate_hierarchies(g):
+    """One row; a diagonal matrix (every row its own aggregate, so nothing
+    coarsens and the single level is solved exactly); an empty matrix."""
+    A1 = (np.array([0, 1]), np.array([0], np.int32), np.array([3.0]))
+    h = g.gs2_setup(A1)
+    x = dev(np.zeros(1))
+    g.amg_vcycle(h, dev(np.array([6.0])), x, g.params("amg", 1, 1, direction="symmetric"))
+    assert host(x)[0] == pytest.approx(2.0, rel=1e-15)
+    assert h.amg_info() == [(1, 1, 0)]
+    n = 500
+    d = 1.0 + P.uniform01(5, n)
+    D = (np.arange(n + 1, dtype=np.int64), np.arange(n, dtype=np.int32), d)
+    h = g.gs2_setup(D)
+    v = P.uniform_pm1(6, n)
+    x = dev(np.zeros(n))
+    g.amg_vcycle(h, dev(v), x, g.params("amg", 1, 1, direction="symmetric"))
+    assert h.amg_info() == [(n, n, 0)]
+    assert rel(host(x), v / d) <= 1e-15
+    assert rel(oracle.AMG(D).vcycle(v), v / d) <= 1e-15
+    E = (np.array([0]), np.zeros(0, np.int32), np.zeros(0))
+    h = g.gs2_setup(E)
+    with pytest.raises(g.GS2Error):
+        h.amg_setup()
+    g.amg_vcycle(h, dev(np.zeros(0)), dev(np.zeros(0)), g.params("amg", 1, 1))
