@@ -220,7 +220,14 @@ k_tiles(TileMat<VT> M, Epi epi, const int* skip) {
     const int4 d = M.desc[t];
     const bool ok = mbar_wait_bounded(&bars[st], (it >> 1) & 1);
     if (__syncthreads_or(!ok)) {
-      if (threadIdx.x == 0 && M.err) atomicExch(M.err, (int)GS2_ERR_TIMEOUT);
+      if (threadIdx.x == 0) {
+        if (M.err) atomicExch(M.err, (int)GS2_ERR_TIMEOUT);
+        // let the copies still in flight (the late tile's and the next
+        // one's) land before the block exits; each wait is bounded too
+        mbar_wait_bounded(&bars[st], (it >> 1) & 1);
+        if (tn < M.ntiles) mbar_wait_bounded(&bars[st ^ 1], ((it + 1) >> 1) & 1);
+      }
+      __syncthreads();
       return;
     }
     if (d.z < 0) {
