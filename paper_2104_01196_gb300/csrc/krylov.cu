@@ -650,17 +650,31 @@ struct GmresRun {
     precond_apply(h, pc, vj, h->z, wants, skip);
     launch_spmv(h, h->z, h->w, skip);
     const int jc = j + 1;
+    // (the column reductions and the Givens step stay separate small
+    // kernels: done instead by the last block of each pass, the tail work
+    // serialises on one SM and the solve got 2% slower)
     int nbr = launch_dots(h, jc, h->w, skip);
-    k_reduce_cols<<<jc, 256, 0, h->stream>>>(h->part, nbr, h->H, ldh, j, h->hbuf, 0, skip);
-    GS2_LAUNCH_CHECK();
+    {
+      KernelTimer tm(h, "reduce_cols", 8.0 * jc * nbr);
+      k_reduce_cols<<<jc, 256, 0, h->stream>>>(h->part, nbr, h->H, ldh, j, h->hbuf, 0, skip);
+      GS2_LAUNCH_CHECK();
+    }
     nbr = launch_update<false>(h, jc, h->w, skip);
-    k_reduce_cols<<<jc, 256, 0, h->stream>>>(h->part, nbr, h->H, ldh, j, h->hbuf, 1, skip);
-    GS2_LAUNCH_CHECK();
+    {
+      KernelTimer tm(h, "reduce_cols", 8.0 * jc * nbr);
+      k_reduce_cols<<<jc, 256, 0, h->stream>>>(h->part, nbr, h->H, ldh, j, h->hbuf, 1, skip);
+      GS2_LAUNCH_CHECK();
+    }
     nbr = launch_update<true>(h, jc, h->w, skip);
-    k_givens<<<1, 256, 0, h->stream>>>(h->part, nbr, h->H, ldh, j, h->cs, h->sn, h->gvec, h->st,
-                                       h->stop_mapped_dev);
-    GS2_LAUNCH_CHECK();
+    {
+      KernelTimer tm(h, "givens", 8.0 * nbr + 8.0 * 4 * (j + 2));
+      k_givens<<<1, 256, 0, h->stream>>>(h->part, nbr, h->H, ldh, j, h->cs, h->sn, h->gvec,
+                                         h->st, h->stop_mapped_dev);
+      GS2_LAUNCH_CHECK();
+    }
     if (j + 1 < m) {
+      // w read, v_{j+1} written, and D^{-1} v_{j+1} (D^{-1} read) when wanted
+      KernelTimer tm(h, "scale_next", 16.0 * n + (r64 ? 16.0 * n : 0.0) + (r32 ? 12.0 * n : 0.0));
       k_scale_next<<<vec_blocks(h, n), kVecThreads, 0, h->stream>>>(
           n, h->w, h->V + (size_t)(j + 1) * n, h->dinv, r64, r32, h->st);
       GS2_LAUNCH_CHECK();
