@@ -3,7 +3,7 @@
  *
  * Two-stage Gauss-Seidel (GS2) replaces the sparse triangular solve of a
  * Gauss-Seidel sweep by a fixed number of inner Jacobi-Richardson (JR)
- * sweeps (Sec. 3, Eq. (4)-(7)); it is used here as a relaxation and as the
+ * sweeps (Sec. 4, Eq. (2)-(5)); it is used here as a relaxation and as the
  * preconditioner of restarted GMRES.  Exact GS through a level-scheduled
  * triangular solve and damped JR are provided beside it as baselines.
  *
@@ -56,7 +56,7 @@ typedef enum { GS2_FORWARD = 0, GS2_BACKWARD = 1, GS2_SYMMETRIC = 2 } gs2_direct
 
 /* Storage and arithmetic of the inner sweeps (the triangles D^{-1}L and
  * D^{-1}U and the inner iterate g).  The residual r = b - A x (outer
- * iteration) is always FP64.  Sec. 6.3 runs the preconditioner in single
+ * iteration) is always FP64.  Sec. 10 runs the preconditioner in single
  * precision; FP16 with a per-row FP32 scale is an extension of that. */
 typedef enum {
   GS2_FP64 = 0,
@@ -64,25 +64,25 @@ typedef enum {
   GS2_FP16_ROWSCALED = 2
 } gs2_precision;
 
-/* Non-compact form Eq. (4) is the paper's default (Sec. 6 setup); the
- * compact form Eq. (11) is x <- Mhat^{-1}(b + N x) (undamped). */
+/* Non-compact form Eq. (2) is the paper's default (Sec. 7 setup); the
+ * compact form Eq. (9) is x <- Mhat^{-1}(b + N x) (undamped). */
 typedef enum { GS2_NONCOMPACT = 0, GS2_COMPACT = 1 } gs2_form;
 
 typedef enum {
   GS2_PC_NONE = 0, /* identity */
-  GS2_PC_GS2 = 1,  /* two-stage GS, Eq. (4)-(7) with damping */
+  GS2_PC_GS2 = 1,  /* two-stage GS, Eq. (2)-(5) with damping */
   GS2_PC_JR = 2,   /* damped Jacobi-Richardson, `outer` sweeps */
   GS2_PC_GS = 3,   /* exact GS/SOR, level-scheduled, `outer` sweeps */
-  GS2_PC_MTGS = 4, /* multicolour GS/SOR, `outer` sweeps (Sec. 5.1.2) */
+  GS2_PC_MTGS = 4, /* multicolour GS/SOR, `outer` sweeps (Sec. 6.1.2) */
   GS2_PC_AMG = 5,  /* one AMG V-cycle, GS2 smoother (outer, inner, omega,
                       gamma, precision) on every level */
   GS2_PC_AMG_JR = 6 /* one AMG V-cycle, JR smoother (outer sweeps, omega) */
 } gs2_pc_kind;
 
 /* Relaxation / preconditioner parameters in the paper's notation:
- * GS2(n_t, n_j) = `outer` global sweeps with `inner` JR sweeps each (Sec. 6
+ * GS2(n_t, n_j) = `outer` global sweeps with `inner` JR sweeps each (Sec. 7
  * setup; the local sweep count n_k is 1 on one GPU).  omega is the outer
- * (SOR-like) damping factor and gamma the inner one (Sec. 3, "Damping
+ * (SOR-like) damping factor and gamma the inner one (Sec. 4, "Damping
  * factor"): an outer sweep computes r = b - A x, g_0 = D^{-1} r,
  *   g_{j+1} = (1 - gamma) g_j + gamma D^{-1} (r - omega T g_j),
  * and x += omega g_{inner}, with T = L (forward) or U (backward).
@@ -116,8 +116,8 @@ typedef struct {
 
 typedef struct gs2_handle gs2_handle;
 
-/* Create a handle for A (Sec. 3 splitting; Sec. 5.1.3 keeps D^{-1}L and
- * D^{-1}U prescaled and explicit; Sec. 5.2 keeps the temporaries resident
+/* Create a handle for A (Sec. 3 splitting; Sec. 6.1.3 keeps D^{-1}L and
+ * D^{-1}U prescaled and explicit; Sec. 6.2 keeps the temporaries resident
  * with A).  Copies A to the current CUDA device, checks it (rowptr
  * monotone with rowptr[0] = 0 and rowptr[n] = nnz, 0 <= col < n, no
  * duplicate (i, j), nonzero a_ii in every row) and prepares the inner-sweep
@@ -159,7 +159,7 @@ gs2_status gs2_autotune(gs2_handle* h);
  * a cycle ran are counted. */
 gs2_status gs2_set_graph_mode(gs2_handle* h, int mode);
 
-/* Non-compact GS2 relaxation, Eq. (4) with inner JR sweeps Eq. (5)-(7):
+/* Non-compact GS2 relaxation, Eq. (2) with inner JR sweeps Eq. (3)-(5):
  * x is read and overwritten (in/out), b is read.  outer_sweeps = n_t >= 0,
  * inner_sweeps = n_j >= 0 (0 gives JR), damping = omega > 0, direction as
  * gs2_direction (symmetric = forward then backward, Sec. 3).  FP64,
@@ -194,13 +194,13 @@ gs2_status gs2_apply_noalloc(int64_t n, const int64_t* rowptr, const int32_t* co
                              int direction, void* stream);
 
 /* Exact GS / SOR baseline: x + omega (D + omega T)^{-1} (b - A x) per half
- * sweep (Sec. 3, "Damping factor"), the triangular solve scheduled by
+ * sweep (Sec. 4, "Damping factor"), the triangular solve scheduled by
  * level sets of T (Sec. 3, level-set scheduling).  Levels are computed on
  * the first call. x in/out. */
 gs2_status gs_apply(gs2_handle* h, const double* b, double* x, int sweeps,
                     double omega, int direction);
 
-/* Multicolour GS / SOR baseline (Sec. 5.1.2, multi-threaded GS): rows are
+/* Multicolour GS / SOR baseline (Sec. 6.1.2, multi-threaded GS): rows are
  * coloured on the host on the first call, first fit in natural row order
  * on the symmetrised pattern (rows i and j differ in colour whenever a_ij
  * or a_ji is stored, i != j); the paper's greedy colouring is parallel and
@@ -217,8 +217,8 @@ gs2_status mtgs_apply(gs2_handle* h, const double* b, double* x, int sweeps,
 
 /* ------------------------------------------------------------------------
  * GS2 as a multigrid smoother.  The paper also applies the two-stage
- * iteration as the smoother of an AMG V-cycle (its Nalu-Wind runs: one GS2
- * sweep per level of hypre's C-AMG).  This library builds a
+ * iteration as the smoother of an AMG V-cycle (its Nalu-Wind runs, Sec. 11.2:
+ * one GS2 sweep per level of hypre's C-AMG).  This library builds a
  * smoothed-aggregation hierarchy: classical strength of connection
  * |a_ij| >= theta max_{k != i} |a_ik| (symmetrised), greedy aggregation in
  * natural row order, unit-norm constant tentative prolongator P0, smoothed
@@ -260,7 +260,7 @@ gs2_status gs2_amg_info(const gs2_handle* h, int* levels, int64_t* rows, int64_t
  * handle has none. */
 gs2_status gs2_amg_vcycle(gs2_handle* h, const double* b, double* x, const gs2_params* p);
 
-/* Damped JR baseline: x += omega D^{-1} (b - A x), `sweeps` times (Sec. 3,
+/* Damped JR baseline: x += omega D^{-1} (b - A x), `sweeps` times (Sec. 4,
  * zero-inner-sweep case). x in/out. */
 gs2_status jr_apply(gs2_handle* h, const double* b, double* x, int sweeps,
                     double omega);
@@ -271,7 +271,7 @@ gs2_status gs2_spmv(gs2_handle* h, const double* x, double* y);
 /* Restarted GMRES(restart), right preconditioned by `precond` (NULL = no
  * preconditioner) applied from a zero start, Arnoldi by classical
  * Gram-Schmidt applied twice (CGS2) in FP64, Givens rotations in FP64 on
- * the device (Sec. 6 uses GMRES with GS2; the paper's stopping rule is a
+ * the device (Sec. 7 uses GMRES with GS2; the paper's stopping rule is a
  * relative residual reduction).  x holds x0 on entry and the solution on
  * exit.  Stops when the implicit residual |g_{j+1}| <= tol ||b|| and the
  * recomputed true residual confirms it, or after max_iters Arnoldi steps.
@@ -281,7 +281,7 @@ gs2_status gmres_solve(gs2_handle* h, const double* b, double* x, int restart,
                        double tol, int max_iters, const gs2_params* precond,
                        gs2_solve_info* info);
 
-/* Preconditioned CG for SPD A (Sec. 6.2 runs CG with SGS2), same
+/* Preconditioned CG for SPD A (Sec. 9 runs CG with SGS2), same
  * conventions as gmres_solve; the preconditioner must be symmetric
  * (GS2/GS/MTGS with direction SYMMETRIC, JR, or none). */
 gs2_status cg_solve(gs2_handle* h, const double* b, double* x, double tol,

@@ -147,7 +147,7 @@ def diag(A):
 
 
 def gs2(A, b, x, outer=1, inner=1, omega=1.0, gamma=1.0, direction=FORWARD):
-    """Non-compact GS2 sweeps (Eq. 4-7, damped); returns the new x."""
+    """Non-compact GS2 sweeps (Eq. 2-5, damped); returns the new x."""
     n, rp, ci, va = _csr(A)
     b, x = _vec(b, n), _vec(x, n)
     _check(_load().ora_gs2(n, _p(rp), _p(ci), _p(va), _p(b), _p(x), outer, inner,
@@ -250,7 +250,7 @@ def cg(A, b, x0=None, tol=1e-8, max_iters=10000, pc_kind=PC_GS2, pc_outer=1,
 
 
 def gs2_compact(A, b, x, outer=1, inner=1, direction=FORWARD):
-    """Compact GS2 (Eq. 11); returns the new x."""
+    """Compact GS2 (Eq. 9); returns the new x."""
     n, rp, ci, va = _csr(A)
     b, x = _vec(b, n), _vec(x, n)
     _check(_load().ora_gs2_compact(n, _p(rp), _p(ci), _p(va), _p(b), _p(x), outer,

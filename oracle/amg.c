@@ -1,8 +1,8 @@
 /*
  * FP64 CPU oracle, part 2: smoothed-aggregation algebraic multigrid with a
  * relaxation smoother, the setting in which the paper also runs GS2 -- as
- * the smoother of an AMG V-cycle (the Nalu-Wind experiments, hypre and
- * Trilinos subsections).  TEST INFRASTRUCTURE ONLY -- see oracle.h.
+ * the smoother of an AMG V-cycle (the Nalu-Wind experiments of Sec. 11,
+ * hypre and Trilinos subsections).  TEST INFRASTRUCTURE ONLY -- see oracle.h.
  *
  * Readings (the paper names the AMG flavours it used but not their steps):
  *  - strength of connection: the classical threshold the paper's C-AMG runs

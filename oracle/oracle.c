@@ -46,7 +46,7 @@ static double dot(int64_t n, const double* a, const double* b) {
 
 static double nrm2(int64_t n, const double* a) { return sqrt(dot(n, a, a)); }
 
-/* r = b - A x  (the residual of Eq. (1) and Eq. (4)) */
+/* r = b - A x  (the residual of Eq. (1) and Eq. (2)) */
 static void residual(int64_t n, const int64_t* rp, const int32_t* ci,
                      const double* va, const double* b, const double* x,
                      double* r) {
@@ -73,18 +73,18 @@ static void tri_mult(int64_t n, const int64_t* rp, const int32_t* ci,
 }
 
 /* ------------------------------------------------------------------ */
-/* GS2: Eq. (4) with inner JR sweeps Eq. (5)-(7) and the damping        */
-/* factors omega (outer) and gamma (inner) of Sec. 3.                   */
+/* GS2: Eq. (2) with inner JR sweeps Eq. (3)-(5) and the damping        */
+/* factors omega (outer) and gamma (inner) of Sec. 4.                   */
 /* ------------------------------------------------------------------ */
 
 /* One non-compact GS2 sweep with triangle T (lower or upper):
  *   r = b - A x
- *   g^(0) = D^{-1} r                                   Eq. (5)
+ *   g^(0) = D^{-1} r                                   Eq. (3)
  *   g^(j+1) = (1-gamma) g^(j) + gamma D^{-1}(r - omega T g^(j))
- *                                     (damped form of Eq. (6)-(7))
+ *                                     (damped form of Eq. (4)-(5))
  *   x = x + omega g^(inner)
  * Reading: the outer damping multiplies the correction, so the inner
- * iteration solves (D + omega T) g = r and omega = 1 gives Eq. (4) exactly.
+ * iteration solves (D + omega T) g = r and omega = 1 gives Eq. (2) exactly.
  * Each inner sweep uses only the previous iterate (Jacobi, not in place). */
 static void gs2_sweep(int64_t n, const int64_t* rp, const int32_t* ci,
                       const double* va, const double* d, const double* b,
@@ -127,7 +127,7 @@ int ora_gs2(int64_t n, const int64_t* rp, const int32_t* ci, const double* va,
 
 /* ------------------------------------------------------------------ */
 /* Exact GS / SOR: compact row recurrence of the sequential GS listing  */
-/* (Sec. 5.1.1); for omega != 1 the SOR form x + omega (D+omega L)^{-1} */
+/* (Sec. 6.1.1); for omega != 1 the SOR form x + omega (D+omega L)^{-1} */
 /* (b - A x) of the "Damping factor" paragraph, written row by row.     */
 /* ------------------------------------------------------------------ */
 
@@ -162,7 +162,7 @@ int ora_gs(int64_t n, const int64_t* rp, const int32_t* ci, const double* va,
 }
 
 /* ------------------------------------------------------------------ */
-/* Multicolour GS (Sec. 5.1.2): greedy colouring, then the sequential   */
+/* Multicolour GS (Sec. 6.1.2): greedy colouring, then the sequential   */
 /* row update visiting the rows colour by colour.                       */
 /* ------------------------------------------------------------------ */
 
@@ -223,7 +223,7 @@ int ora_mtgs(int64_t n, const int64_t* rp, const int32_t* ci, const double* va,
 }
 
 /* ------------------------------------------------------------------ */
-/* Jacobi-Richardson: GS2 with zero inner sweeps (Sec. 3), damped.      */
+/* Jacobi-Richardson: GS2 with zero inner sweeps (Sec. 4), damped.      */
 /* ------------------------------------------------------------------ */
 
 int ora_jr(int64_t n, const int64_t* rp, const int32_t* ci, const double* va,
@@ -267,7 +267,7 @@ int ora_levels(int64_t n, const int64_t* rp, const int32_t* ci, int lower,
 /* Reading: the paper does not state the preconditioner's initial      */
 /* guess; a zero start makes M^{-1} a fixed linear operator, and makes  */
 /* one JR sweep equal omega D^{-1}, which is why the JR(1) row of the   */
-/* elasticity omega table (Sec. 6.1) does not depend on omega.          */
+/* elasticity omega table (Sec. 8) does not depend on omega.            */
 /* ------------------------------------------------------------------ */
 
 int ora_precond(int64_t n, const int64_t* rp, const int32_t* ci,
@@ -428,7 +428,7 @@ done:
 }
 
 /* ------------------------------------------------------------------ */
-/* Preconditioned CG (Sec. 6.2 and 6.3 run CG with SGS2 on SPD          */
+/* Preconditioned CG (Sec. 9 and 10 run CG with SGS2 on SPD            */
 /* matrices; SGS2 from a zero start is a symmetric operator when A is). */
 /* ------------------------------------------------------------------ */
 
@@ -497,7 +497,7 @@ int ora_cg(int64_t n, const int64_t* rp, const int32_t* ci, const double* va,
 }
 
 /* ------------------------------------------------------------------ */
-/* Compact GS2, Eq. (11): x <- Mhat^{-1}(b + N x).                      */
+/* Compact GS2, Eq. (9): x <- Mhat^{-1}(b + N x).                       */
 /* Forward: M = D + L, N = -U; backward: M = D + U, N = -L.             */
 /* ------------------------------------------------------------------ */
 

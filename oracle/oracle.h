@@ -43,8 +43,8 @@ void ora_spmv(int64_t n, const int64_t* rp, const int32_t* ci,
 int ora_diag(int64_t n, const int64_t* rp, const int32_t* ci,
              const double* va, double* d);
 
-/* Non-compact two-stage GS, Eq. (4)-(7) with the damping factors of the
- * "Damping factor" paragraph of Sec. 3: per outer sweep
+/* Non-compact two-stage GS, Eq. (2)-(5) with the damping factors of the
+ * "Damping factor" paragraph of Sec. 4: per outer sweep
  *   r = b - A x;  g0 = D^{-1} r;
  *   g_{j+1} = (1-gamma) g_j + gamma D^{-1} (r - omega T g_j),  j < inner;
  *   x += omega g_inner,
@@ -54,7 +54,7 @@ int ora_gs2(int64_t n, const int64_t* rp, const int32_t* ci, const double* va,
             const double* b, double* x, int outer, int inner, double omega,
             double gamma, int dir);
 
-/* Exact GS / SOR by the compact row recurrence (Sec. 5.1.1, sequential GS):
+/* Exact GS / SOR by the compact row recurrence (Sec. 6.1.1, sequential GS):
  * x_i <- (1-omega) x_i + omega (b_i - sum_{j != i} a_ij x_j) / a_ii in
  * ascending (forward) or descending (backward) row order; symmetric =
  * forward then backward.  x in place. */
@@ -62,7 +62,7 @@ int ora_gs(int64_t n, const int64_t* rp, const int32_t* ci, const double* va,
            const double* b, double* x, int sweeps, double omega, int dir);
 
 /* Damped Jacobi-Richardson: x += omega D^{-1} (b - A x), `sweeps` times
- * (Sec. 3, zero-inner-sweep special case). */
+ * (Sec. 4, zero-inner-sweep special case). */
 int ora_jr(int64_t n, const int64_t* rp, const int32_t* ci, const double* va,
            const double* b, double* x, int sweeps, double omega);
 
@@ -77,7 +77,7 @@ int ora_levels(int64_t n, const int64_t* rp, const int32_t* ci, int lower,
  * Returns the number of colours. */
 int ora_coloring(int64_t n, const int64_t* rp, const int32_t* ci, int32_t* color);
 
-/* Multicolour GS / SOR (Sec. 5.1.2, multi-threaded GS): the compact row
+/* Multicolour GS / SOR (Sec. 6.1.2, multi-threaded GS): the compact row
  * update of ora_gs applied colour by colour, colours ascending (forward) or
  * descending (backward), rows of one colour in natural order; symmetric =
  * forward then backward.  x in place. */
@@ -105,7 +105,7 @@ int ora_gmres(int64_t n, const int64_t* rp, const int32_t* ci,
               int pc_inner, double pc_omega, double pc_gamma, int pc_dir,
               ora_info* info, double* resid_hist);
 
-/* Preconditioned conjugate gradients for SPD A (Sec. 6.2 uses CG with an
+/* Preconditioned conjugate gradients for SPD A (Sec. 9 uses CG with an
  * SGS2 preconditioner).  Same stopping rule on the recursively updated
  * residual, confirmed by the true residual. */
 int ora_cg(int64_t n, const int64_t* rp, const int32_t* ci, const double* va,
@@ -113,7 +113,7 @@ int ora_cg(int64_t n, const int64_t* rp, const int32_t* ci, const double* va,
            int pc_outer, int pc_inner, double pc_omega, double pc_gamma,
            int pc_dir, ora_info* info);
 
-/* Compact two-stage GS, Eq. (11): x <- Mhat^{-1} (b + N x) where
+/* Compact two-stage GS, Eq. (9): x <- Mhat^{-1} (b + N x) where
  * N = -U (forward) or -L (backward) and Mhat^{-1} is `inner` JR sweeps on
  * (D + T) from g0 = D^{-1}(b + N x).  Undamped (omega = gamma = 1). */
 int ora_gs2_compact(int64_t n, const int64_t* rp, const int32_t* ci,

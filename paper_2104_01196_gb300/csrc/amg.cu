@@ -1,6 +1,7 @@
 // Smoothed-aggregation algebraic multigrid with GS2 (or JR) as the smoother
 // of a V-cycle -- the second role the paper gives the two-stage iteration
-// (its Nalu-Wind runs smooth an AMG V-cycle with one GS2 sweep per level).
+// (its Nalu-Wind runs, Sec. 11.2, smooth an AMG V-cycle with one GS2 sweep
+// per level).
 //
 // Setup runs on the host once per matrix: classical strength of connection
 // (j is strong for i if |a_ij| >= theta max_{k != i} |a_ik|, theta = 0.25 as

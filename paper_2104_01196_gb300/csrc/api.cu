@@ -284,7 +284,7 @@ void retile(gs2_handle* h, DevCsr& M, const std::vector<int>& rp, int K, int RPT
 }
 
 // FP32 copy and FP16 copy with per-row scale s_i = max_j |v_ij| of a
-// triangle (Sec. 6.3 single-precision preconditioner; FP16 with row scale
+// triangle (Sec. 10 single-precision preconditioner; FP16 with row scale
 // is an extension of it).
 struct HostTri {
   std::vector<int> rp, ci;
@@ -746,7 +746,7 @@ gs2_handle* gs2::setup_handle(int64_t n, int64_t nnz, const int64_t* rowptr,
     if (!has_diag || diag[i] == 0.0 || !std::isfinite(diag[i]))
       GS2_THROW(GS2_ERR_ZERO_DIAGONAL, "zero or missing diagonal in row " + std::to_string(i));
   }
-  // split A = L + D + U, triangles prescaled by D^{-1} (Sec. 5.1.3)
+  // split A = L + D + U, triangles prescaled by D^{-1} (Sec. 6.1.3)
   std::vector<int> rp32(n + 1);
   for (int64_t i = 0; i <= n; ++i) rp32[i] = (int)rp64[i];
   auto* hs = new gs2_host_side();

@@ -102,7 +102,7 @@ struct gs2_handle {
   int64_t dev_bytes = 0;
   std::vector<void*> allocs;
 
-  // resident temporaries (Sec. 5.2: allocated once per matrix)
+  // resident temporaries (Sec. 6.2: allocated once per matrix)
   double *r = nullptr, *rhat = nullptr, *g0 = nullptr, *g1 = nullptr;
   double *z = nullptr, *t = nullptr, *bstage = nullptr, *xstage = nullptr;
   float *rhat32 = nullptr, *g32a = nullptr, *g32b = nullptr;

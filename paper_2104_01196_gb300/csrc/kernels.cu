@@ -1,11 +1,11 @@
 // Row kernels of the two-stage Gauss-Seidel library (sm_103a).
 //
 // Every sweep is a CSR row reduction followed by a per-row epilogue:
-//   residual      r = b - A x, rhat = D^{-1} r              (Eq. 4, Eq. 5)
-//   inner sweep   g' = (1-gamma) g + gamma (rhat - omega T g)  (Eq. 6-7,
-//                 damped form of Sec. 3), the last one fused with
+//   residual      r = b - A x, rhat = D^{-1} r              (Eq. 2, Eq. 3)
+//   inner sweep   g' = (1-gamma) g + gamma (rhat - omega T g)  (Eq. 4-5,
+//                 damped form of Sec. 4), the last one fused with
 //                 x += omega g'
-//   JR            x' = x + omega D^{-1} (b - A x)           (Sec. 3)
+//   JR            x' = x + omega D^{-1} (b - A x)           (Sec. 4)
 //   SpMV          y = A x
 //
 // Design (GB300): FP64 throughput on this part is ~2 FMA/clk/SM, so a
@@ -27,7 +27,7 @@ namespace gs2 {
 // s, pre) consumes the row sum
 // ---------------------------------------------------------------------------
 
-// r = b - A x;  rhat = D^{-1} r   (Eq. 4 residual and Eq. 5 initial guess)
+// r = b - A x;  rhat = D^{-1} r   (Eq. 2 residual and Eq. 3 initial guess)
 struct EpiResid {
   const double* __restrict__ x;
   const double* __restrict__ b;
@@ -125,7 +125,7 @@ struct EpiInner {
   }
 };
 
-// one colour of multicolour GS (Sec. 5.1.2): the colour matrix holds only
+// one colour of multicolour GS (Sec. 6.1.2): the colour matrix holds only
 // off-diagonal entries prescaled by D^{-1}, none of them inside the colour,
 // so every x_j gathered here belongs to another colour and is not written
 // by this launch; row i of the colour is row rows[i] of A.

@@ -72,7 +72,7 @@ __global__ void k_na_diag(int64_t n, const int64_t* __restrict__ rp,
   }
 }
 
-// rhat = D^{-1} (b - A x)   (Eq. 4 residual, Eq. 5 initial guess)
+// rhat = D^{-1} (b - A x)   (Eq. 2 residual, Eq. 3 initial guess)
 __global__ void k_na_resid(int64_t n, const int64_t* __restrict__ rp,
                            const int32_t* __restrict__ ci, const double* __restrict__ va,
                            const double* __restrict__ b, const double* __restrict__ x,
@@ -86,7 +86,7 @@ __global__ void k_na_resid(int64_t n, const int64_t* __restrict__ rp,
 }
 
 // g_out = rhat - omega D^{-1} T g_in over the strict triangle T of A
-// (Eq. 6-7 with the outer damping); the last sweep adds omega g to x
+// (Eq. 4-5 with the outer damping); the last sweep adds omega g to x
 __global__ void k_na_inner(int64_t n, const int64_t* __restrict__ rp,
                            const int32_t* __restrict__ ci, const double* __restrict__ va,
                            const double* __restrict__ dinv, const double* __restrict__ rhat,

@@ -1,4 +1,4 @@
-// Relaxation drivers: GS2 (non-compact Eq. 4 and compact Eq. 11), exact
+// Relaxation drivers: GS2 (non-compact Eq. 2 and compact Eq. 9), exact
 // GS/SOR by level-scheduled triangular solves, damped JR, and the
 // zero-start preconditioner application used by the Krylov solvers.
 #include <algorithm>
@@ -8,7 +8,7 @@
 namespace gs2 {
 
 // ---------------------------------------------------------------------------
-// compact right-hand side: rhat = D^{-1} (b - T_other x)  (Eq. 11 with
+// compact right-hand side: rhat = D^{-1} (b - T_other x)  (Eq. 9 with
 // N = -U for a forward sweep and N = -L for a backward one)
 // ---------------------------------------------------------------------------
 
@@ -68,14 +68,14 @@ static void* rhat_buf(gs2_handle* h, int prec) {
   return prec == GS2_FP64 ? (void*)h->rhat : (void*)h->rhat32;
 }
 
-// n_j inner JR sweeps (Eq. 6-7, damped), the last one fused with the update
+// n_j inner JR sweeps (Eq. 4-5, damped), the last one fused with the update
 // of x in `last_mode` (x += omega g or x = omega g).
 static void inner_sweeps(gs2_handle* h, const DevCsr& T, int prec, const void* rhat,
                          double* x, double omega, double gamma, int inner, int last_mode,
                          const int* skip) {
   void* bufA = prec == GS2_FP64 ? (void*)h->g0 : (void*)h->g32a;
   void* bufB = prec == GS2_FP64 ? (void*)h->g1 : (void*)h->g32b;
-  const void* gin = rhat;  // g_0 = D^{-1} r  (Eq. 5)
+  const void* gin = rhat;  // g_0 = D^{-1} r  (Eq. 3)
   for (int j = 0; j < inner; ++j) {
     const bool last = j == inner - 1;
     void* gout = last ? nullptr : (j % 2 == 0 ? bufA : bufB);
@@ -165,7 +165,7 @@ void gs_relax(gs2_handle* h, const double* b, double* x, int sweeps, double omeg
 }
 
 // ---------------------------------------------------------------------------
-// multicolour GS / SOR baseline (Sec. 5.1.2): the compact row update of
+// multicolour GS / SOR baseline (Sec. 6.1.2): the compact row update of
 // exact GS, colour by colour (ascending forward, descending backward); rows
 // of one colour are independent, so each colour is one parallel launch.
 // bhat = D^{-1} b must be in h->rhat.

@@ -141,7 +141,7 @@ def test_level_scheduled_gs(g, name, direction):
 @pytest.mark.parametrize("name", list(MATS))
 @pytest.mark.parametrize("direction", [0, 1, 2])
 def test_multicolor_gs(g, name, direction):
-    """Multicolour GS/SOR (Sec. 5.1.2): same colouring as the oracle's first
+    """Multicolour GS/SOR (Sec. 6.1.2): same colouring as the oracle's first
     fit, sweeps equal to the oracle's colour-by-colour recurrence."""
     A = MATS[name]
     b, x0 = rhs_and_x0(A, 29)
@@ -327,7 +327,7 @@ def test_batch_results_equal_alone(g):
 
 
 # ---------------------------------------------------------------------------
-# lower-precision inner sweeps (Sec. 6.3; FP16 row-scaled is an extension)
+# lower-precision inner sweeps (Sec. 10; FP16 row-scaled is an extension)
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("prec,bound", [("fp32", 2e-6), ("fp16", 2e-2)])
@@ -345,7 +345,7 @@ def test_lowprec_sweep_error_vs_fp64_oracle(g, prec, bound):
 
 @pytest.mark.parametrize("prec", ["fp32", "fp16"])
 def test_lowprec_preconditioner_keeps_convergence(g, prec):
-    """Sec. 6.3: the single-precision preconditioner keeps the GMRES
+    """Sec. 10: the single-precision preconditioner keeps the GMRES
     iteration count (6,656 = 6,656 in the paper's table)."""
     pr = P.poisson2d(64)
     h = g.gs2_setup(pr.A, precisions=(prec,))

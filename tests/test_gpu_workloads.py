@@ -66,8 +66,8 @@ def test_elasticity_sgs2_sweeps_fp64(g, ela, inner):
 @pytest.mark.parametrize("inner,omega", [(1, 0.7), (2, 0.8), (3, 0.9)])
 def test_elasticity_gmres_fp32_preconditioner(g, ela, inner, omega):
     """Preconditioner values in FP32, GMRES/Arnoldi FP64: converges to the
-    same tolerance in about the FP64 oracle's iteration count (Sec. 6.3).
-    As in the elasticity omega table of Sec. 6.1, SGS2 with few inner sweeps
+    same tolerance in about the FP64 oracle's iteration count (Sec. 10).
+    As in the elasticity omega table of Sec. 8, SGS2 with few inner sweeps
     needs omega < 1 (here SGS2(1,1) stagnates at omega = 0.8)."""
     h = g.gs2_setup(ela.A, precisions=("fp32",))
     x = dev(np.zeros(ela.n))
@@ -85,7 +85,7 @@ def test_elasticity_gmres_fp32_preconditioner(g, ela, inner, omega):
 
 
 def test_elasticity_stationary_jr_diverges_at_omega_one(g, ela):
-    """Sec. 6.1: with omega = 1 JR diverges on elasticity, while SGS2(1,1) with
+    """Sec. 8: with omega = 1 JR diverges on elasticity, while SGS2(1,1) with
     omega = 0.8 reduces the residual."""
     h = g.gs2_setup(ela.A)
     b = dev(ela.b)
@@ -166,7 +166,7 @@ def test_elasticity_full_size_sweeps_and_solves(g, ela64):
     one SGS2(1,1) sweep at omega = 0.8 in FP64 against the oracle on every
     entry and with FP32 triangle values within their bound; GMRES(30) with
     SGS2(1,2), omega = 0.8, within +-1 of the oracle's stored count in FP64
-    and within 10% with FP32 values (Sec. 6.3); true residuals recomputed by
+    and within 10% with FP32 values (Sec. 10); true residuals recomputed by
     the oracle's SpMV."""
     pr = ela64
     x0 = P.uniform_pm1(17, pr.n)

@@ -35,7 +35,7 @@ def tiny_nonsym(n=7, seed=5):
 
 
 # ---------------------------------------------------------------------------
-# A hand-worked example (Eq. 5-7 applied by hand to a 3x3 tridiagonal system)
+# A hand-worked example (Eq. 3-5 applied by hand to a 3x3 tridiagonal system)
 # ---------------------------------------------------------------------------
 
 def test_hand_worked_gs2_and_gs():
@@ -81,7 +81,7 @@ def test_gs_equals_dense_sor(omega):
 
 
 # ---------------------------------------------------------------------------
-# GS2 against the closed forms of Sec. 3
+# GS2 against the closed forms of Sec. 4
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("inner", [0, 1, 2, 3])
@@ -168,7 +168,7 @@ def test_diagonal_matrix_collapses_everything():
 
 
 def test_residual_propagators_of_sec4():
-    """Sec. 4: one GS2(1) sweep maps r to (I - A D^-1 [I - L D^-1]) r, two JR
+    """Sec. 5.3: one GS2(1) sweep maps r to (I - A D^-1 [I - L D^-1]) r, two JR
     sweeps to (I - A D^-1)^2 r = (I - A D^-1 [I - (L+U) D^-1]) r, SGS2(1) to
     (I - A D^-1 [I - U D^-1])(I - A D^-1 [I - L D^-1]) r."""
     A = tiny_nonsym(8, 13)
@@ -279,7 +279,7 @@ def test_levels_equal_longest_path_brute_force():
 
 
 # ---------------------------------------------------------------------------
-# Multicolour GS (Sec. 5.1.2) against a dense solve in the colour ordering
+# Multicolour GS (Sec. 6.1.2) against a dense solve in the colour ordering
 # ---------------------------------------------------------------------------
 
 def test_coloring_red_black_on_stencils_and_valid_on_random():
@@ -617,7 +617,7 @@ def test_compact_gs2_closed_form_and_exact_limit():
         expect = S @ Di @ (b - U @ x0)
         got = oracle.gs2_compact(A, b, x0, 1, s, oracle.FORWARD)
         assert np.allclose(got, expect, rtol=1e-13, atol=1e-13)
-    # exact inner solve: compact and non-compact GS coincide (Eq. 1 vs Eq. 10)
+    # exact inner solve: compact and non-compact GS coincide (Eq. 1 vs Eq. 8)
     Ap = P.poisson2d_matrix(7)
     bb, xx = rng.standard_normal(49), rng.standard_normal(49)
     assert np.allclose(oracle.gs2_compact(Ap, bb, xx, 1, 12), oracle.gs(Ap, bb, xx, 1),
