@@ -140,9 +140,11 @@ gs2_status gs2_set_stream(gs2_handle* h, void* stream);
 
 gs2_status gs2_get_stats(const gs2_handle* h, gs2_handle_stats* out);
 
-/* Autotune the tile shape of A, D^{-1}L and D^{-1}U: for each matrix, time an
- * SpMV-shaped pass for every candidate (lanes per row K around the row-length
- * heuristic, rows per lane group 1 or 2) and keep the fastest.  Results are
+/* Autotune the tile shape of A, D^{-1}L and D^{-1}U: for each matrix, time
+ * its most frequent kernel (the residual for A, the inner sweep with the x
+ * update for a triangle) for every candidate shape (lanes per row K around
+ * the row-length heuristic, rows per lane group 1 or 2) and keep the
+ * heuristic shape unless another is at least 2% faster.  Results are
  * cached by matrix class (size to a factor sqrt(2), mean row length), so
  * matrices of a class already measured are re-tiled without timing.  The
  * numerical results do not change (rows are reduced in the same order for

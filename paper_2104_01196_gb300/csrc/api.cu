@@ -532,12 +532,15 @@ static void tune_matrix(gs2_handle* h, DevCsr& M, const std::vector<int>& rp, in
     cand.emplace_back(K, 1);
     if (K <= 2) cand.emplace_back(K, 2);
   }
+  // the heuristic shape is timed first; another shape must beat it by 2%,
+  // so timing noise does not flip the choice between near-equal shapes
   std::pair<int, int> best{M.tpr, M.rpt};
-  float best_ms = 1e30f;
+  float best_ms = time_tile_probe(h, M, 5, role);
   for (const auto& c : cand) {
+    if (c == best) continue;
     retile(h, M, rp, c.first, c.second);
-    const float ms = time_tile_probe(h, M, 5);
-    if (ms < best_ms) {
+    const float ms = time_tile_probe(h, M, 5, role);
+    if (ms < 0.98f * best_ms) {
       best_ms = ms;
       best = c;
     }

@@ -217,7 +217,9 @@ void launch_rhat_update(gs2_handle* h, int prec, const void* rhat, double* x,
                         double omega, bool add, const int* skip);
 
 void launch_spmv(gs2_handle* h, const double* x, double* y, const int* skip);
-float time_tile_probe(gs2_handle* h, const DevCsr& M, int reps);
+// autotuner probe: ms per launch of M's most frequent kernel (role 0: A's
+// residual, 1 and 2: a triangle's inner sweep), best of reps
+float time_tile_probe(gs2_handle* h, const DevCsr& M, int reps, int role);
 void launch_jr(gs2_handle* h, const double* b, const double* x_in,
                double* x_out, double omega, const int* skip);
 void launch_level(gs2_handle* h, const DevCsr& T, const int* rows, int r0,

@@ -215,10 +215,12 @@ void launch_spmv_matrix(gs2_handle* h, const DevCsr& M, const double* x, double*
   }
 }
 
-// Autotuner probe: milliseconds per launch of y = M x over M's FP64 values
-// with M's current tile shape (x = h->t, y = h->z), best of `reps`.
-float time_tile_probe(gs2_handle* h, const DevCsr& M, int reps) {
-  EpiSpmv e{h->t, h->z};
+// Autotuner probe: milliseconds per launch of M's most frequent kernel with
+// M's current tile shape, best of `reps`: the residual for A (role 0), the
+// inner sweep with the x update for a triangle (roles 1, 2).  The operands
+// are the handle's temporaries (their values do not matter for the timing).
+template <class Epi>
+static float time_epilogue(gs2_handle* h, const DevCsr& M, const Epi& e, int reps) {
   cudaEvent_t e0, e1;
   GS2_CUDA(cudaEventCreate(&e0));
   GS2_CUDA(cudaEventCreate(&e1));
@@ -236,6 +238,16 @@ float time_tile_probe(gs2_handle* h, const DevCsr& M, int reps) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return best;
+}
+
+float time_tile_probe(gs2_handle* h, const DevCsr& M, int reps, int role) {
+  if (role == 0) {
+    EpiResid e{h->t, h->g1, h->dinv, nullptr, h->rhat, nullptr};
+    return time_epilogue(h, M, e, reps);
+  }
+  EpiInner<double, double, false, false> e{h->g0, h->rhat, nullptr, h->z, nullptr,
+                                           1.0, 1.0, 1.0, INNER_LAST_ADD};
+  return time_epilogue(h, M, e, reps);
 }
 
 void launch_jr(gs2_handle* h, const double* b, const double* x_in, double* x_out,
