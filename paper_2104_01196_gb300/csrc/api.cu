@@ -243,6 +243,66 @@ static void build_tiles(const std::vector<int>& rp, int n, int K, int RPT,
 
 void retile(gs2_handle* h, DevCsr& M, const std::vector<int>& rp, int K, int RPT);
 
+// ---------------------------------------------------------------------------
+// sliced-ELL copies of short-row matrices
+// ---------------------------------------------------------------------------
+
+constexpr int kSellC = 32;              // rows per chunk (one warp)
+constexpr double kSellMaxMeanRow = 24;  // the one-thread-per-row regime
+constexpr double kSellMaxPadding = 1.2; // slots / entries
+
+// chunk offsets: chunk c takes (longest row of the chunk) x 32 slots
+static std::vector<int> sell_layout(const std::vector<int>& rp, int n) {
+  const int nc = (n + kSellC - 1) / kSellC;
+  std::vector<int> cptr(nc + 1, 0);
+  for (int c = 0; c < nc; ++c) {
+    int L = 0;
+    for (int i = c * kSellC; i < std::min(n, (c + 1) * kSellC); ++i)
+      L = std::max(L, rp[i + 1] - rp[i]);
+    cptr[c + 1] = cptr[c] + L * kSellC;
+  }
+  return cptr;
+}
+
+// values of a CSR array in sliced-ELL order; pad fills the padding slots
+template <class T>
+static std::vector<T> to_sell(const std::vector<int>& rp, int n, const std::vector<int>& cptr,
+                              const T* src, T pad) {
+  std::vector<T> out(std::max(cptr.back(), 1), pad);
+  for (int i = 0; i < n; ++i) {
+    const int c = i / kSellC, lane = i % kSellC;
+    for (int k = rp[i]; k < rp[i + 1]; ++k) out[cptr[c] + (k - rp[i]) * kSellC + lane] = src[k];
+  }
+  return out;
+}
+
+static void upload_sell(gs2_handle* h, DevCsr& M, const std::vector<int>& rp,
+                        const std::vector<int>& ci, const std::vector<double>& va) {
+  const int n = M.n;
+  if (n == 0 || M.nnz == 0 || M.mean_row > kSellMaxMeanRow) return;
+  std::vector<int> cptr = sell_layout(rp, n);
+  if (cptr.back() > kSellMaxPadding * M.nnz) return;
+  // padding columns repeat the row's last column (column 0 for empty rows),
+  // so a padded slot gathers an x entry the row already reads
+  std::vector<int> pad_ci = to_sell(rp, n, cptr, ci.data(), 0);
+  for (int i = 0; i < n; ++i) {
+    const int len = rp[i + 1] - rp[i];
+    if (len == 0) continue;
+    const int c = i / kSellC, lane = i % kSellC;
+    int L = (cptr[c + 1] - cptr[c]) / kSellC;
+    for (int k = len; k < L; ++k) pad_ci[cptr[c] + k * kSellC + lane] = ci[rp[i + 1] - 1];
+  }
+  std::vector<double> sv = to_sell(rp, n, cptr, va.data(), 0.0);
+  M.sell_chunks = (int)cptr.size() - 1;
+  M.sell_ptr = (int*)h->dalloc(sizeof(int) * cptr.size());
+  M.sell_ci = (int*)h->dalloc(sizeof(int) * pad_ci.size());
+  M.sell_va = (double*)h->dalloc(sizeof(double) * sv.size());
+  h->h2d(M.sell_ptr, cptr.data(), sizeof(int) * cptr.size());
+  h->h2d(M.sell_ci, pad_ci.data(), sizeof(int) * pad_ci.size());
+  h->h2d(M.sell_va, sv.data(), sizeof(double) * sv.size());
+  M.sell = true;
+}
+
 static void upload_csr(gs2_handle* h, DevCsr& M, int n, const std::vector<int>& rp,
                        const std::vector<int>& ci, const std::vector<double>& va) {
   M.n = n;
@@ -262,6 +322,7 @@ static void upload_csr(gs2_handle* h, DevCsr& M, int n, const std::vector<int>& 
   h->h2d(M.ci, ci.data(), sizeof(int) * M.nnz);
   h->h2d(M.va, va.data(), sizeof(double) * M.nnz);
   retile(h, M, rp, M.tpr, 1);
+  upload_sell(h, M, rp, ci, va);
 }
 
 // (Re)build the row tiles of M for K lanes per row and RPT rows per lane
@@ -298,6 +359,12 @@ static void prepare_lowprec(gs2_handle* h, DevCsr& M, const HostTri& T, int prec
     for (int k = 0; k < M.nnz; ++k) v[k] = (float)T.va[k];
     M.va32 = (float*)h->dalloc(sizeof(float) * nz);
     h->h2d(M.va32, v.data(), sizeof(float) * nz);
+    if (M.sell) {
+      const std::vector<int> cptr = sell_layout(T.rp, M.n);
+      const std::vector<float> sv = to_sell(T.rp, M.n, cptr, v.data(), 0.f);
+      M.sell_va32 = (float*)h->dalloc(sizeof(float) * sv.size());
+      h->h2d(M.sell_va32, sv.data(), sizeof(float) * sv.size());
+    }
   }
   if (prec == GS2_FP16_ROWSCALED && !M.va16) {
     std::vector<__half> v(nz, __float2half(0.f));
@@ -313,6 +380,12 @@ static void prepare_lowprec(gs2_handle* h, DevCsr& M, const HostTri& T, int prec
     M.scale16 = (float*)h->dalloc(sizeof(float) * std::max(M.n, 1));
     h->h2d(M.va16, v.data(), sizeof(__half) * nz);
     h->h2d(M.scale16, s.data(), sizeof(float) * M.n);
+    if (M.sell) {
+      const std::vector<int> cptr = sell_layout(T.rp, M.n);
+      const std::vector<__half> sv = to_sell(T.rp, M.n, cptr, v.data(), __float2half(0.f));
+      M.sell_va16 = (__half*)h->dalloc(sizeof(__half) * sv.size());
+      h->h2d(M.sell_va16, sv.data(), sizeof(__half) * sv.size());
+    }
   }
 }
 

@@ -67,6 +67,17 @@ struct DevCsr {
   int cap = 0;
   int4* desc = nullptr;  // ntiles
   double mean_row = 0.0;
+  // Sliced-ELL copy (short rows): chunk c holds rows 32c .. 32c+31, its
+  // longest row's length L_c times 32 slots, column-major: slot k of row i
+  // at sell_ptr[c] + 32 k + i % 32; padding slots have value 0 and repeat
+  // a column of the row (column 0 for an empty row)
+  bool sell = false;
+  int sell_chunks = 0;
+  int* sell_ptr = nullptr;     // sell_chunks + 1
+  int* sell_ci = nullptr;
+  double* sell_va = nullptr;
+  float* sell_va32 = nullptr;
+  __half* sell_va16 = nullptr;
 };
 
 // Device-resident GMRES / CG state, one per handle.

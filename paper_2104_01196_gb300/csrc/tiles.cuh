@@ -292,6 +292,78 @@ k_tiles(TileMat<VT> M, Epi epi, const int* skip) {
 // launch plumbing
 // ---------------------------------------------------------------------------
 
+// ---------------------------------------------------------------------------
+// sliced-ELL rows (short rows, one thread per row, one warp per chunk of 32
+// rows): slot k of the warp's rows is one coalesced 32-wide load of columns
+// and one of values, streamed with evict-first hints so the gathered vector
+// stays in L2; no shared memory and no block barrier.  Rows are reduced in
+// CSR order, as by the row-tile engine with one lane per row.
+// ---------------------------------------------------------------------------
+
+template <typename VT>
+__device__ __forceinline__ typename ValTraits<VT>::AT stream_val(const VT* p);
+template <>
+__device__ __forceinline__ double stream_val<double>(const double* p) { return __ldcs(p); }
+template <>
+__device__ __forceinline__ float stream_val<float>(const float* p) { return __ldcs(p); }
+template <>
+__device__ __forceinline__ float stream_val<__half>(const __half* p) {
+  return __half2float(__ushort_as_half(__ldcs(reinterpret_cast<const unsigned short*>(p))));
+}
+
+template <typename VT, class Epi>
+__global__ void __launch_bounds__(kRowThreads)
+k_sell(int n, int nchunks, const int* __restrict__ cptr, const int* __restrict__ ci,
+       const VT* __restrict__ va, Epi epi, const int* skip) {
+  using AT = typename ValTraits<VT>::AT;
+  if (skip && *skip) return;
+  const int lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks; c += nw) {
+    const int row = c * 32 + lane;
+    const int base = cptr[c], L = (cptr[c + 1] - base) >> 5;
+    typename Epi::Pre pv{};
+    if (row < n) pv = epi.pre(row);
+    const int* cc = ci + base + lane;
+    const VT* vv = va + base + lane;
+    AT s = AT(0);
+    int k = 0;
+    // groups of four: all loads and gathers are in flight before the FMAs
+    for (; k + 4 <= L; k += 4, cc += 128, vv += 128) {
+      const int c0 = __ldcs(cc), c1 = __ldcs(cc + 32), c2 = __ldcs(cc + 64), c3 = __ldcs(cc + 96);
+      const AT a0 = stream_val<VT>(vv), a1 = stream_val<VT>(vv + 32);
+      const AT a2 = stream_val<VT>(vv + 64), a3 = stream_val<VT>(vv + 96);
+      const AT x0 = (AT)epi.gather(c0), x1 = (AT)epi.gather(c1);
+      const AT x2 = (AT)epi.gather(c2), x3 = (AT)epi.gather(c3);
+      s = fma(a0, x0, s);
+      s = fma(a1, x1, s);
+      s = fma(a2, x2, s);
+      s = fma(a3, x3, s);
+    }
+    // the last one to three slots, also issued together
+    const int rem = L - k;
+    if (rem > 0) {
+      const int c0 = __ldcs(cc);
+      const int c1 = rem > 1 ? __ldcs(cc + 32) : c0;
+      const int c2 = rem > 2 ? __ldcs(cc + 64) : c0;
+      const AT a0 = stream_val<VT>(vv);
+      const AT a1 = rem > 1 ? stream_val<VT>(vv + 32) : AT(0);
+      const AT a2 = rem > 2 ? stream_val<VT>(vv + 64) : AT(0);
+      const AT x0 = (AT)epi.gather(c0);
+      const AT x1 = rem > 1 ? (AT)epi.gather(c1) : AT(0);
+      const AT x2 = rem > 2 ? (AT)epi.gather(c2) : AT(0);
+      s = fma(a0, x0, s);
+      if (rem > 1) s = fma(a1, x1, s);
+      if (rem > 2) s = fma(a2, x2, s);
+    }
+    if (row < n) epi.finish(row, s, pv);
+  }
+}
+
+inline const double* sell_values(const DevCsr& M, const double*) { return M.sell_va; }
+inline const float* sell_values(const DevCsr& M, const float*) { return M.sell_va32; }
+inline const __half* sell_values(const DevCsr& M, const __half*) { return M.sell_va16; }
+
 // Resident blocks per SM of a tile kernel at a dynamic shared-memory size
 // (kernels.cu; cached per kernel and size, the attribute only ever raised).
 int blocks_per_sm(const void* fn, size_t smem);
@@ -323,11 +395,29 @@ inline void launch_k(gs2_handle* h, const DevCsr& M, const VT* va, const Epi& ep
   GS2_LAUNCH_CHECK();
 }
 
+template <typename VT, class Epi>
+inline void launch_sell(gs2_handle* h, const DevCsr& M, const VT* sv, const Epi& epi,
+                        const int* skip) {
+  if (M.n == 0 || M.sell_chunks == 0) return;
+  auto fn = k_sell<VT, Epi>;
+  const int per_sm = blocks_per_sm((const void*)fn, 0);
+  const int warps = kRowThreads / 32;
+  const int grid = std::max(1, std::min((M.sell_chunks + warps - 1) / warps, per_sm * h->nsm));
+  fn<<<grid, kRowThreads, 0, h->stream>>>(M.n, M.sell_chunks, M.sell_ptr, M.sell_ci, sv, epi,
+                                          skip);
+  GS2_LAUNCH_CHECK();
+}
+
 // (K, RPT) shapes: RPT = 2 only for short rows (K <= 2), where the per-tile
 // barrier and stage overhead is largest relative to the work per row
 template <typename VT, class Epi>
 inline void dispatch(gs2_handle* h, const DevCsr& M, const VT* va, const Epi& epi,
                      const int* skip) {
+  const VT* sv = M.sell ? sell_values(M, va) : nullptr;
+  if (sv) {
+    launch_sell<VT, Epi>(h, M, sv, epi, skip);
+    return;
+  }
   switch (M.tpr * 4 + (M.rpt == 2 ? 1 : 0)) {
     case 1 * 4 + 1: launch_k<1, 2, VT, Epi>(h, M, va, epi, skip); break;
     case 2 * 4 + 1: launch_k<2, 2, VT, Epi>(h, M, va, epi, skip); break;
