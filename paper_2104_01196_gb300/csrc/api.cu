@@ -264,42 +264,23 @@ static std::vector<int> sell_layout(const std::vector<int>& rp, int n) {
   return cptr;
 }
 
-// values of a CSR array in sliced-ELL order; pad fills the padding slots
-template <class T>
-static std::vector<T> to_sell(const std::vector<int>& rp, int n, const std::vector<int>& cptr,
-                              const T* src, T pad) {
-  std::vector<T> out(std::max(cptr.back(), 1), pad);
-  for (int i = 0; i < n; ++i) {
-    const int c = i / kSellC, lane = i % kSellC;
-    for (int k = rp[i]; k < rp[i + 1]; ++k) out[cptr[c] + (k - rp[i]) * kSellC + lane] = src[k];
-  }
-  return out;
-}
-
-static void upload_sell(gs2_handle* h, DevCsr& M, const std::vector<int>& rp,
-                        const std::vector<int>& ci, const std::vector<double>& va) {
+// The sliced-ELL arrays are filled on the device from the CSR arrays already
+// there (launch_to_sell); only the chunk offsets are computed here.
+static void upload_sell(gs2_handle* h, DevCsr& M, const std::vector<int>& rp) {
   const int n = M.n;
   if (n == 0 || M.nnz == 0 || M.mean_row > kSellMaxMeanRow) return;
   std::vector<int> cptr = sell_layout(rp, n);
   if (cptr.back() > kSellMaxPadding * M.nnz) return;
-  // padding columns repeat the row's last column (column 0 for empty rows),
-  // so a padded slot gathers an x entry the row already reads
-  std::vector<int> pad_ci = to_sell(rp, n, cptr, ci.data(), 0);
-  for (int i = 0; i < n; ++i) {
-    const int len = rp[i + 1] - rp[i];
-    if (len == 0) continue;
-    const int c = i / kSellC, lane = i % kSellC;
-    int L = (cptr[c + 1] - cptr[c]) / kSellC;
-    for (int k = len; k < L; ++k) pad_ci[cptr[c] + k * kSellC + lane] = ci[rp[i + 1] - 1];
-  }
-  std::vector<double> sv = to_sell(rp, n, cptr, va.data(), 0.0);
+  const size_t slots = std::max(cptr.back(), 1);
   M.sell_chunks = (int)cptr.size() - 1;
+  M.sell_slots = (int)slots;
   M.sell_ptr = (int*)h->dalloc(sizeof(int) * cptr.size());
-  M.sell_ci = (int*)h->dalloc(sizeof(int) * pad_ci.size());
-  M.sell_va = (double*)h->dalloc(sizeof(double) * sv.size());
+  M.sell_ci = (int*)h->dalloc(sizeof(int) * slots);
+  M.sell_va = (double*)h->dalloc(sizeof(double) * slots);
+  h->dzero(M.sell_ci, sizeof(int) * slots);
+  h->dzero(M.sell_va, sizeof(double) * slots);
   h->h2d(M.sell_ptr, cptr.data(), sizeof(int) * cptr.size());
-  h->h2d(M.sell_ci, pad_ci.data(), sizeof(int) * pad_ci.size());
-  h->h2d(M.sell_va, sv.data(), sizeof(double) * sv.size());
+  launch_to_sell(h, M, M.va, M.sell_va, true);
   M.sell = true;
 }
 
@@ -322,7 +303,7 @@ static void upload_csr(gs2_handle* h, DevCsr& M, int n, const std::vector<int>& 
   h->h2d(M.ci, ci.data(), sizeof(int) * M.nnz);
   h->h2d(M.va, va.data(), sizeof(double) * M.nnz);
   retile(h, M, rp, M.tpr, 1);
-  upload_sell(h, M, rp, ci, va);
+  upload_sell(h, M, rp);
 }
 
 // (Re)build the row tiles of M for K lanes per row and RPT rows per lane
@@ -360,10 +341,10 @@ static void prepare_lowprec(gs2_handle* h, DevCsr& M, const HostTri& T, int prec
     M.va32 = (float*)h->dalloc(sizeof(float) * nz);
     h->h2d(M.va32, v.data(), sizeof(float) * nz);
     if (M.sell) {
-      const std::vector<int> cptr = sell_layout(T.rp, M.n);
-      const std::vector<float> sv = to_sell(T.rp, M.n, cptr, v.data(), 0.f);
-      M.sell_va32 = (float*)h->dalloc(sizeof(float) * sv.size());
-      h->h2d(M.sell_va32, sv.data(), sizeof(float) * sv.size());
+      const size_t slots = M.sell_slots;
+      M.sell_va32 = (float*)h->dalloc(sizeof(float) * slots);
+      h->dzero(M.sell_va32, sizeof(float) * slots);
+      launch_to_sell(h, M, M.va32, M.sell_va32, false);
     }
   }
   if (prec == GS2_FP16_ROWSCALED && !M.va16) {
@@ -381,10 +362,10 @@ static void prepare_lowprec(gs2_handle* h, DevCsr& M, const HostTri& T, int prec
     h->h2d(M.va16, v.data(), sizeof(__half) * nz);
     h->h2d(M.scale16, s.data(), sizeof(float) * M.n);
     if (M.sell) {
-      const std::vector<int> cptr = sell_layout(T.rp, M.n);
-      const std::vector<__half> sv = to_sell(T.rp, M.n, cptr, v.data(), __float2half(0.f));
-      M.sell_va16 = (__half*)h->dalloc(sizeof(__half) * sv.size());
-      h->h2d(M.sell_va16, sv.data(), sizeof(__half) * sv.size());
+      const size_t slots = M.sell_slots;
+      M.sell_va16 = (__half*)h->dalloc(sizeof(__half) * slots);
+      h->dzero(M.sell_va16, sizeof(__half) * slots);
+      launch_to_sell(h, M, M.va16, M.sell_va16, false);
     }
   }
 }

@@ -73,6 +73,7 @@ struct DevCsr {
   // a column of the row (column 0 for an empty row)
   bool sell = false;
   int sell_chunks = 0;
+  int sell_slots = 0;          // length of the value and column arrays
   int* sell_ptr = nullptr;     // sell_chunks + 1
   int* sell_ci = nullptr;
   double* sell_va = nullptr;
@@ -241,6 +242,13 @@ void launch_level(gs2_handle* h, const DevCsr& T, const int* rows, int r0,
 // C (original row rows[i]), x_r = (1 - omega) x_r + omega (bhat_r - (C x)_i)
 void launch_color(gs2_handle* h, const DevCsr& C, const int* rows, const double* bhat,
                   double* x, double omega, const int* skip);
+
+// Fill M's sliced-ELL arrays (offsets already in M.sell_ptr, arrays zeroed)
+// from its CSR arrays on the device: values from `va` into `sva`, and the
+// columns too when with_ci.
+void launch_to_sell(gs2_handle* h, const DevCsr& M, const double* va, double* sva, bool with_ci);
+void launch_to_sell(gs2_handle* h, const DevCsr& M, const float* va, float* sva, bool with_ci);
+void launch_to_sell(gs2_handle* h, const DevCsr& M, const __half* va, __half* sva, bool with_ci);
 
 // y = M x (accumulate: y += M x) for any tiled matrix M whose columns index x
 void launch_spmv_matrix(gs2_handle* h, const DevCsr& M, const double* x, double* y,

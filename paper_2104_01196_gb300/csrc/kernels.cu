@@ -215,6 +215,46 @@ void launch_spmv_matrix(gs2_handle* h, const DevCsr& M, const double* x, double*
   }
 }
 
+// CSR rows into the sliced-ELL layout, one thread per row: slot k of row i
+// goes to cptr[c] + 32 k + i % 32 (c = i / 32); value slots past the row's
+// end keep their zero, column slots repeat the row's last column (column 0
+// for an empty row, whose slots stay zero)
+template <typename T>
+__global__ void k_to_sell(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                          const T* __restrict__ va, const int* __restrict__ cptr, int* sci,
+                          T* sva) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int c = i >> 5, lane = i & 31;
+    const int L = (cptr[c + 1] - cptr[c]) >> 5;
+    const int a = rp[i], len = rp[i + 1] - a;
+    for (int k = 0; k < L; ++k) {
+      const int slot = cptr[c] + (k << 5) + lane;
+      if (k < len) {
+        sva[slot] = va[a + k];
+        if (sci) sci[slot] = ci[a + k];
+      } else if (sci && len > 0) {
+        sci[slot] = ci[a + len - 1];
+      }
+    }
+  }
+}
+
+template <typename T>
+static void to_sell(gs2_handle* h, const DevCsr& M, const T* va, T* sva, bool with_ci) {
+  k_to_sell<T><<<vec_blocks(h, M.n), kVecThreads, 0, h->stream>>>(
+      M.n, M.rp, M.ci, va, M.sell_ptr, with_ci ? M.sell_ci : nullptr, sva);
+  GS2_LAUNCH_CHECK();
+}
+void launch_to_sell(gs2_handle* h, const DevCsr& M, const double* va, double* sva, bool with_ci) {
+  to_sell(h, M, va, sva, with_ci);
+}
+void launch_to_sell(gs2_handle* h, const DevCsr& M, const float* va, float* sva, bool with_ci) {
+  to_sell(h, M, va, sva, with_ci);
+}
+void launch_to_sell(gs2_handle* h, const DevCsr& M, const __half* va, __half* sva, bool with_ci) {
+  to_sell(h, M, va, sva, with_ci);
+}
+
 // Autotuner probe: milliseconds per launch of M's most frequent kernel with
 // M's current tile shape, best of `reps`: the residual for A (role 0), the
 // inner sweep with the x update for a triangle (roles 1, 2).  The operands
