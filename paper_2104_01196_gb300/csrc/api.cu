@@ -10,6 +10,7 @@
 #include <limits>
 #include <map>
 #include <mutex>
+#include <thread>
 #include <tuple>
 #include <new>
 #include <string>
@@ -203,6 +204,25 @@ KernelTimer::~KernelTimer() {
 // setup helpers
 // ---------------------------------------------------------------------------
 
+// Host setup loops run over row ranges on up to kHostThreads threads (one
+// range below 64K rows per thread); f(begin, end, thread index) must not
+// throw.
+constexpr int kHostThreads = 16;
+template <class F>
+static void parallel_ranges(int64_t n, F f) {
+  const int64_t per = 65536;
+  const int64_t hw = std::max(1u, std::thread::hardware_concurrency());
+  const int nt = (int)std::max<int64_t>(
+      1, std::min<int64_t>({hw, (int64_t)kHostThreads, (n + per - 1) / per}));
+  if (nt == 1) {
+    f(int64_t(0), n, 0);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (int t = 0; t < nt; ++t) th.emplace_back(f, n * t / nt, n * (t + 1) / nt, t);
+  for (auto& x : th) x.join();
+}
+
 constexpr int kHardCap = 6144;  // staged entries per tile at most
 constexpr int kPad = 16;        // padding entries after every CSR array
 
@@ -285,9 +305,9 @@ static void upload_sell(gs2_handle* h, DevCsr& M, const std::vector<int>& rp) {
 }
 
 static void upload_csr(gs2_handle* h, DevCsr& M, int n, const std::vector<int>& rp,
-                       const std::vector<int>& ci, const std::vector<double>& va) {
+                       const int* ci, const double* va, int nnz) {
   M.n = n;
-  M.nnz = (int)ci.size();
+  M.nnz = nnz;
   M.mean_row = n ? (double)M.nnz / n : 0.0;
   M.tpr = choose_lanes(M.mean_row);
   // every array is padded by kPad entries so that the 16-byte-rounded bulk
@@ -300,8 +320,8 @@ static void upload_csr(gs2_handle* h, DevCsr& M, int n, const std::vector<int>& 
   h->h2d(M.rp, rp.data(), sizeof(int) * (n + 1));
   h->dzero(M.ci, sizeof(int) * nz);
   h->dzero(M.va, sizeof(double) * nz);
-  h->h2d(M.ci, ci.data(), sizeof(int) * M.nnz);
-  h->h2d(M.va, va.data(), sizeof(double) * M.nnz);
+  h->h2d(M.ci, ci, sizeof(int) * M.nnz);
+  h->h2d(M.va, va, sizeof(double) * M.nnz);
   retile(h, M, rp, M.tpr, 1);
   upload_sell(h, M, rp);
 }
@@ -537,7 +557,7 @@ void ensure_colors(gs2_handle* h) {
       }
       rp[q + 1] = (int)ci.size();
     }
-    upload_csr(h, h->colors[c], (int)rr.size(), rp, ci, va);
+    upload_csr(h, h->colors[c], (int)rr.size(), rp, ci.data(), va.data(), (int)ci.size());
     h->color_rows[c] = (int*)h->dalloc(sizeof(int) * std::max<size_t>(rr.size(), 1));
     h->h2d(h->color_rows[c], rr.data(), sizeof(int) * rr.size());
   }
@@ -553,7 +573,7 @@ void ensure_precond(gs2_handle* h, const gs2_params* p) {
 
 void upload_matrix(gs2_handle* h, DevCsr& M, int n, const std::vector<int>& rp,
                    const std::vector<int>& ci, const std::vector<double>& va) {
-  upload_csr(h, M, n, rp, ci, va);
+  upload_csr(h, M, n, rp, ci.data(), va.data(), (int)ci.size());
 }
 
 // ---------------------------------------------------------------------------
@@ -762,70 +782,127 @@ gs2_handle* gs2::setup_handle(int64_t n, int64_t nnz, const int64_t* rowptr,
     GS2_THROW(GS2_ERR_INVALID_ARG, "n or nnz above 2^31 - 1");
   if (!rowptr || (nnz > 0 && (!col || !val)))
     GS2_THROW(GS2_ERR_INVALID_ARG, "NULL CSR array");
-  // host copies of the input
-  std::vector<int64_t> rp64(n + 1);
-  std::vector<int32_t> ci(nnz);
-  std::vector<double> va(nnz);
+  // the input on the host: the caller's arrays, or copies of device arrays
+  std::vector<int64_t> rp_copy;
+  std::vector<int32_t> ci_copy;
+  std::vector<double> va_copy;
+  const int64_t* RP = rowptr;
+  const int32_t* CI = col;
+  const double* VA = val;
   if (on_device) {
-    GS2_CUDA(cudaMemcpy(rp64.data(), rowptr, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost));
+    rp_copy.resize(n + 1);
+    ci_copy.resize(nnz);
+    va_copy.resize(nnz);
+    GS2_CUDA(cudaMemcpy(rp_copy.data(), rowptr, sizeof(int64_t) * (n + 1),
+                        cudaMemcpyDeviceToHost));
     if (nnz) {
-      GS2_CUDA(cudaMemcpy(ci.data(), col, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost));
-      GS2_CUDA(cudaMemcpy(va.data(), val, sizeof(double) * nnz, cudaMemcpyDeviceToHost));
+      GS2_CUDA(cudaMemcpy(ci_copy.data(), col, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost));
+      GS2_CUDA(cudaMemcpy(va_copy.data(), val, sizeof(double) * nnz, cudaMemcpyDeviceToHost));
     }
-  } else {
-    std::memcpy(rp64.data(), rowptr, sizeof(int64_t) * (n + 1));
-    if (nnz) {
-      std::memcpy(ci.data(), col, sizeof(int32_t) * nnz);
-      std::memcpy(va.data(), val, sizeof(double) * nnz);
-    }
+    RP = rp_copy.data();
+    CI = ci_copy.data();
+    VA = va_copy.data();
   }
-  // validation
-  if (rp64[0] != 0 || rp64[n] != nnz)
+  // validation, row ranges in parallel; the first bad row (in row order) is
+  // reported
+  if (RP[0] != 0 || RP[n] != nnz)
     GS2_THROW(GS2_ERR_INVALID_ARG, "rowptr[0] must be 0 and rowptr[n] must be nnz");
   for (int64_t i = 0; i < n; ++i)
-    if (rp64[i + 1] < rp64[i]) GS2_THROW(GS2_ERR_INVALID_ARG, "rowptr is not monotone");
-  std::vector<int> seen(n, -1);
+    if (RP[i + 1] < RP[i]) GS2_THROW(GS2_ERR_INVALID_ARG, "rowptr is not monotone");
   std::vector<double> diag(n, 0.0);
-  for (int64_t i = 0; i < n; ++i) {
-    bool has_diag = false;
-    for (int64_t k = rp64[i]; k < rp64[i + 1]; ++k) {
-      const int64_t j = ci[k];
-      if (j < 0 || j >= n)
-        GS2_THROW(GS2_ERR_INVALID_ARG, "column index out of range in row " + std::to_string(i));
-      if (seen[j] == (int)i)
-        GS2_THROW(GS2_ERR_INVALID_ARG, "duplicate entry in row " + std::to_string(i));
-      seen[j] = (int)i;
-      if (j == i) {
-        has_diag = true;
-        diag[i] = va[k];
+  struct RowError {
+    int64_t row = std::numeric_limits<int64_t>::max();
+    gs2_status st = GS2_OK;
+    const char* what = "";
+  };
+  std::vector<RowError> errs(kHostThreads);
+  parallel_ranges(n, [&](int64_t i0, int64_t i1, int tid) {
+    std::vector<int32_t> cols;
+    for (int64_t i = i0; i < i1; ++i) {
+      const int64_t a = RP[i], e = RP[i + 1];
+      const char* what = nullptr;
+      gs2_status st = GS2_ERR_INVALID_ARG;
+      for (int64_t k = a; k < e && !what; ++k)
+        if (CI[k] < 0 || CI[k] >= n) what = "column index out of range in row ";
+      if (!what) {
+        if (e - a <= 32) {
+          for (int64_t k = a; k < e && !what; ++k)
+            for (int64_t q = k + 1; q < e; ++q)
+              if (CI[q] == CI[k]) {
+                what = "duplicate entry in row ";
+                break;
+              }
+        } else {
+          cols.assign(CI + a, CI + e);
+          std::sort(cols.begin(), cols.end());
+          if (std::adjacent_find(cols.begin(), cols.end()) != cols.end())
+            what = "duplicate entry in row ";
+        }
+      }
+      if (!what) {
+        bool has_diag = false;
+        for (int64_t k = a; k < e; ++k)
+          if (CI[k] == i) {
+            has_diag = true;
+            diag[i] = VA[k];
+          }
+        if (!has_diag || diag[i] == 0.0 || !std::isfinite(diag[i])) {
+          what = "zero or missing diagonal in row ";
+          st = GS2_ERR_ZERO_DIAGONAL;
+        }
+      }
+      if (what) {
+        errs[tid] = RowError{i, st, what};
+        return;
       }
     }
-    if (!has_diag || diag[i] == 0.0 || !std::isfinite(diag[i]))
-      GS2_THROW(GS2_ERR_ZERO_DIAGONAL, "zero or missing diagonal in row " + std::to_string(i));
-  }
-  // split A = L + D + U, triangles prescaled by D^{-1} (Sec. 6.1.3)
+  });
+  const RowError* first = &errs[0];
+  for (const RowError& e : errs)
+    if (e.row < first->row) first = &e;
+  if (first->st != GS2_OK) GS2_THROW(first->st, first->what + std::to_string(first->row));
+  // split A = L + D + U, triangles prescaled by D^{-1} (Sec. 6.1.3): count
+  // per row, prefix sums, fill, row ranges in parallel
   std::vector<int> rp32(n + 1);
-  for (int64_t i = 0; i <= n; ++i) rp32[i] = (int)rp64[i];
+  for (int64_t i = 0; i <= n; ++i) rp32[i] = (int)RP[i];
   auto* hs = new gs2_host_side();
   HostTri& L = hs->L;
   HostTri& U = hs->U;
   L.rp.assign(n + 1, 0);
   U.rp.assign(n + 1, 0);
+  parallel_ranges(n, [&](int64_t i0, int64_t i1, int) {
+    for (int64_t i = i0; i < i1; ++i)
+      for (int64_t k = RP[i]; k < RP[i + 1]; ++k) {
+        if (CI[k] < i) L.rp[i + 1]++;
+        else if (CI[k] > i) U.rp[i + 1]++;
+      }
+  });
   for (int64_t i = 0; i < n; ++i) {
-    const double di = 1.0 / diag[i];
-    for (int64_t k = rp64[i]; k < rp64[i + 1]; ++k) {
-      const int j = ci[k];
-      if (j < i) {
-        L.ci.push_back(j);
-        L.va.push_back(va[k] * di);
-      } else if (j > i) {
-        U.ci.push_back(j);
-        U.va.push_back(va[k] * di);
+    L.rp[i + 1] += L.rp[i];
+    U.rp[i + 1] += U.rp[i];
+  }
+  L.ci.resize(L.rp[n]);
+  L.va.resize(L.rp[n]);
+  U.ci.resize(U.rp[n]);
+  U.va.resize(U.rp[n]);
+  std::vector<double> dinv(n);
+  parallel_ranges(n, [&](int64_t i0, int64_t i1, int) {
+    for (int64_t i = i0; i < i1; ++i) {
+      const double di = 1.0 / diag[i];
+      dinv[i] = di;
+      int ql = L.rp[i], qu = U.rp[i];
+      for (int64_t k = RP[i]; k < RP[i + 1]; ++k) {
+        const int j = CI[k];
+        if (j < i) {
+          L.ci[ql] = j;
+          L.va[ql++] = VA[k] * di;
+        } else if (j > i) {
+          U.ci[qu] = j;
+          U.va[qu++] = VA[k] * di;
+        }
       }
     }
-    L.rp[i + 1] = (int)L.ci.size();
-    U.rp[i + 1] = (int)U.ci.size();
-  }
+  });
   h = new gs2_handle();
   {
     std::lock_guard<std::mutex> g(g_host_mu);
@@ -837,12 +914,10 @@ gs2_handle* gs2::setup_handle(int64_t n, int64_t nnz, const int64_t* rowptr,
   h->async_alloc = async_alloc;
   h->n = n;
   h->nnz = nnz;
-  upload_csr(h, h->A, (int)n, rp32, std::vector<int>(ci.begin(), ci.end()), va);
+  upload_csr(h, h->A, (int)n, rp32, CI, VA, (int)nnz);
   hs->Arp = rp32;
-  upload_csr(h, h->L, (int)n, L.rp, L.ci, L.va);
-  upload_csr(h, h->U, (int)n, U.rp, U.ci, U.va);
-  std::vector<double> dinv(n);
-  for (int64_t i = 0; i < n; ++i) dinv[i] = 1.0 / diag[i];
+  upload_csr(h, h->L, (int)n, L.rp, L.ci.data(), L.va.data(), (int)L.ci.size());
+  upload_csr(h, h->U, (int)n, U.rp, U.ci.data(), U.va.data(), (int)U.ci.size());
   const size_t nv = (size_t)std::max<int64_t>(n, 1);
   h->dinv = (double*)h->dalloc(sizeof(double) * nv);
   h->dev_err = (int*)h->dalloc(sizeof(int));

@@ -86,6 +86,29 @@ def test_setup_rejects_bad_structure(lib):
     assert st == 1
 
 
+def test_setup_reports_the_first_bad_row_of_a_large_matrix(lib):
+    """Validation runs on several host threads over row ranges; the error
+    reported is still the one of the first bad row."""
+    n = 300_000
+    rp = np.arange(n + 1, dtype=np.int64)
+    ci = np.arange(n, dtype=np.int32)
+    va = np.ones(n)
+    bad = ci.copy()
+    bad[250_000] = 7          # row 250000 loses its diagonal
+    bad[280_000] = n + 5      # row 280000: column out of range
+    st, msg = _setup_status(lib, (rp, bad, va))
+    assert st == 2 and msg.endswith("row 250000")
+    bad[200_001] = -1         # an earlier row, out of range
+    st, msg = _setup_status(lib, (rp, bad, va))
+    assert st == 1 and "range" in msg and msg.endswith("row 200001")
+    # a long row with a duplicate (the sorted check) before it all
+    rp2 = np.concatenate([[0, 40], 40 + np.arange(1, n)]).astype(np.int64)
+    ci2 = np.concatenate([np.arange(40), np.arange(1, n)]).astype(np.int32)
+    ci2[39] = 3
+    st, msg = _setup_status(lib, (rp2, ci2, np.ones(len(ci2))))
+    assert st == 1 and "duplicate" in msg and msg.endswith("row 0")
+
+
 def test_null_arguments_are_rejected(lib):
     assert lib.gs2_apply(None, None, None, 1, 1, 1.0, 0) != 0
     assert lib.gmres_solve(None, None, None, 30, 1e-8, 10, None, None) != 0
