@@ -95,12 +95,15 @@ def _load():
             lib.ora_amg_vcycle.argtypes = [P, P, P, I32, I32, I32, D, D, I32]
             lib.ora_gmres_amg.argtypes = csr + [P, P, I32, D, I32, P, I32, I32, I32, D, D,
                                                 I32, ctypes.POINTER(_Info)]
+            lib.ora_cg_amg.argtypes = csr + [P, P, D, I32, P, I32, I32, I32, D, D, I32,
+                                             ctypes.POINTER(_Info)]
             lib.ora_mtgs.argtypes = csr + [P, P, I32, D, I32]
             for f in ("ora_diag", "ora_gs2", "ora_gs", "ora_jr", "ora_levels",
                       "ora_precond", "ora_gmres", "ora_cg", "ora_gs2_compact",
                       "ora_coloring", "ora_mtgs", "ora_amg_levels", "ora_amg_level",
                       "ora_amg_get_matrix", "ora_amg_get_prolongator",
-                      "ora_amg_get_aggregates", "ora_amg_vcycle", "ora_gmres_amg"):
+                      "ora_amg_get_aggregates", "ora_amg_vcycle", "ora_gmres_amg",
+                      "ora_cg_amg"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -332,4 +335,18 @@ class AMG:
                                      direction, ctypes.byref(info))
         if st == 1:
             raise OracleError("ora_gmres_amg: invalid argument")
+        return x, SolveInfo(info.iters, info.cycles, info.status, info.true_relres)
+
+    def cg(self, A, b, x0=None, tol=1e-8, max_iters=10000, kind=PC_GS2, outer=1, inner=1,
+           omega=1.0, gamma=1.0, direction=SYMMETRIC):
+        """CG preconditioned by one symmetric V-cycle; (x, SolveInfo)."""
+        n, rp, ci, va = _csr(A)
+        b = _vec(b, n)
+        x = np.zeros(n) if x0 is None else _vec(x0, n)
+        info = _Info()
+        st = self._lib.ora_cg_amg(n, _p(rp), _p(ci), _p(va), _p(b), _p(x), tol, max_iters,
+                                  self._ptr, kind, outer, inner, omega, gamma, direction,
+                                  ctypes.byref(info))
+        if st == 1:
+            raise OracleError("ora_cg_amg: invalid argument")
         return x, SolveInfo(info.iters, info.cycles, info.status, info.true_relres)

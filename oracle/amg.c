@@ -494,3 +494,18 @@ int ora_gmres_amg(int64_t n, const int64_t* rp, const int32_t* ci, const double*
   ora_amg_current = NULL;
   return st;
 }
+
+/* CG with one symmetric V-cycle as the preconditioner: ora_cg with the AMG
+ * preconditioner kind on the hierarchy set here. */
+int ora_cg_amg(int64_t n, const int64_t* rp, const int32_t* ci, const double* va,
+               const double* b, double* x, double tol, int max_iters, const ora_amg* M,
+               int kind, int outer, int inner, double omega, double gamma, int dir,
+               ora_info* info) {
+  if (!M || M->A[0].n != n || (kind != ORA_PC_GS2 && kind != ORA_PC_JR)) return 1;
+  ora_amg_current = M;
+  const int pc = (kind == ORA_PC_JR) ? ORA_PC_AMG_JR : ORA_PC_AMG;
+  const int st = ora_cg(n, rp, ci, va, b, x, tol, max_iters, pc, outer, inner, omega, gamma,
+                        dir, info);
+  ora_amg_current = NULL;
+  return st;
+}

@@ -153,7 +153,13 @@ int ora_gmres_amg(int64_t n, const int64_t* rp, const int32_t* ci, const double*
                   const double* b, double* x, int restart, double tol, int max_iters,
                   const ora_amg* M, int kind, int outer, int inner, double omega,
                   double gamma, int dir, ora_info* info);
-/* the hierarchy the AMG preconditioner kinds apply (set by ora_gmres_amg) */
+/* CG preconditioned by one V-cycle per application (symmetric smoothing) */
+int ora_cg_amg(int64_t n, const int64_t* rp, const int32_t* ci, const double* va,
+               const double* b, double* x, double tol, int max_iters, const ora_amg* M,
+               int kind, int outer, int inner, double omega, double gamma, int dir,
+               ora_info* info);
+/* the hierarchy the AMG preconditioner kinds apply (set by ora_gmres_amg and
+ * ora_cg_amg) */
 extern _Thread_local const ora_amg* ora_amg_current;
 
 #ifdef __cplusplus

@@ -141,12 +141,16 @@ def test_amg_beats_one_level_sgs2_in_iterations(g):
     assert abs(counts[1] - counts[0]) <= 3
 
 
-def test_cg_with_symmetric_amg(g):
-    pr = P.poisson3d(20)
+@pytest.mark.parametrize("name", ["poisson3d_14", "elasticity3d_6"])
+def test_cg_with_symmetric_amg_matches_oracle(g, name):
+    pr = PROBS[name]
+    gp, op = SMOOTHERS["sgs2_damped" if name.startswith("elasticity") else "sgs2_1_1"]
     h = g.gs2_setup(pr.A)
     x = dev(np.zeros(pr.n))
-    info = g.cg_solve(h, dev(pr.b), x, 1e-8, 200, g.params("amg", 1, 1, direction="symmetric"))
-    assert info.status == 0 and info.iters <= 20
+    info = g.cg_solve(h, dev(pr.b), x, 1e-8, 500, g.params(**gp))
+    _, oinfo = oracle.AMG(pr.A).cg(pr.A, pr.b, tol=1e-8, max_iters=500, **op)
+    assert info.status == 0 and oinfo.status == 0
+    assert abs(info.iters - oinfo.iters) <= 1, (info.iters, oinfo.iters)
     r = np.linalg.norm(pr.b - oracle.spmv(pr.A, host(x))) / np.linalg.norm(pr.b)
     assert r <= 1e-8
 

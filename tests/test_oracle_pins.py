@@ -459,6 +459,19 @@ def test_amg_symmetric_vcycle_is_spd_and_contracts():
     assert not np.allclose(Mff, Mff.T, atol=1e-6)
 
 
+def test_amg_preconditioned_cg_converges_like_gmres():
+    """The symmetric V-cycle is SPD (pinned above), so CG with it converges on
+    an SPD system, in about as many iterations as GMRES with the same cycle."""
+    pr = P.poisson3d(16)
+    M = oracle.AMG(pr.A)
+    xc, ic = M.cg(pr.A, pr.b, tol=1e-8, max_iters=200)
+    _, ig = M.gmres(pr.A, pr.b, restart=30, tol=1e-8, max_iters=200)
+    assert ic.status == 0 and ic.true_relres <= 1e-8
+    assert abs(ic.iters - ig.iters) <= 3 and ic.iters <= 15
+    r = np.linalg.norm(pr.b - oracle.spmv(pr.A, xc)) / np.linalg.norm(pr.b)
+    assert r <= 1e-8
+
+
 def test_amg_iterations_grid_independent():
     """Multigrid: GMRES iterations stay flat as the grid is refined, while
     the one-level SGS2 preconditioner's grow with it."""
