@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the baseline/precision comparison solves")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the elasticity 64^3 and convection-diffusion 192^3 runs")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer e2e timing")
     ap.add_argument("--no-serve", action="store_true", help="skip the request-stream run")
     ap.add_argument("--no-autotune", action="store_true", help="keep the heuristic tile shapes")
@@ -457,6 +459,8 @@ def run_ours(args):
         out["serving"] = serving(gs2, torch, args.serve_requests)
     if rank == 0 and not args.no_extras and world == 1:
         out["small_system"] = small_system(gs2, torch)
+    if rank == 0 and not args.no_extras and not args.no_workloads and world == 1:
+        out["workloads"] = full_workloads(gs2, torch)
     if rank == 0 and world == 1 and not args.no_cpu:
         v, sample = oracle_sample(pr)
         out["cpu_baseline"] = {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
@@ -497,6 +501,68 @@ def small_system(gs2, torch, reps=20):
                      "iters": info.iters, "true_relres": info.true_relres}
         h.close()
     return res
+
+
+def full_workloads(gs2, torch):
+    """The other full-size configurations, device-timed once each (after an
+    untimed restart cycle): Q1 elasticity on 64^3 nodes with SGS2(1, n_j) at
+    the omega its few inner sweeps need (n_j = 2: 0.8, n_j = 3: 0.9; with
+    omega = 1 it stagnates, as the paper's elasticity tables show), FP64 and
+    FP32 triangle values (GMRES FP64), and stationary
+    JR at omega = 1, which diverges on it; 192^3 upwind convection-diffusion
+    with GS2(1,1) inner sweeps in FP64, FP32 and FP16 with a row scale.  Each
+    result carries its iteration count, its true relative residual and, where
+    the right-hand side was generated from one, its error against x_true."""
+    from paper_2104_01196_gb300 import problems as P
+    out = {}
+
+    def timed(h, b, x, pc, max_iters):
+        x.zero_()
+        gs2.gmres_solve(h, b, x, 30, 1e-8, 30, pc)  # warm: one restart cycle
+        x.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        info = gs2.gmres_solve(h, b, x, 30, 1e-8, max_iters, pc)
+        e1.record()
+        e1.synchronize()
+        return info, e0.elapsed_time(e1)
+
+    for name, pr, variants in (
+            ("elasticity3d_64", P.elasticity3d(64),
+             [(f"sgs2_1_{nj}_w{om}_{prec}", gs2.params("gs2", 1, nj, omega=om,
+                                                        direction="symmetric", precision=prec))
+              for nj, om in ((2, 0.8), (3, 0.9)) for prec in ("fp64", "fp32")]),
+            ("convdiff3d_192", P.convdiff3d(192),
+             [(f"sgs2_1_1_{prec}", gs2.params("gs2", 1, 1, direction="symmetric",
+                                               precision=prec))
+              for prec in ("fp64", "fp32", "fp16")])):
+        h = gs2.gs2_setup(pr.A, precisions=("fp32", "fp16"))
+        b = torch.from_numpy(pr.b).cuda()
+        x = torch.zeros(pr.n, dtype=torch.float64, device="cuda")
+        # (the elasticity right-hand side is a body load, with no x_true)
+        xt = torch.from_numpy(pr.x_true).cuda() if pr.x_true is not None else None
+        res = {"n": pr.n, "nnz": int(len(pr.A[1]))}
+        for vname, pc in variants:
+            info, ms = timed(h, b, x, pc, 5000)
+            err = (float(torch.linalg.norm(x - xt) / torch.linalg.norm(xt))
+                   if xt is not None else None)
+            res[vname] = {"status": info.status, "iters": info.iters, "ms": round(ms, 2),
+                          "true_relres": info.true_relres, "rel_err_vs_x_true": err}
+        if name.startswith("elasticity"):
+            # stationary JR, omega = 1 (the paper's elasticity tables): the
+            # residual grows
+            x.zero_()
+            r0 = float(torch.linalg.norm(b))
+            gs2.jr_apply(h, b, x, 50, 1.0)
+            y = torch.zeros_like(x)
+            gs2.gs2_spmv(h, x, y)
+            growth = float(torch.linalg.norm(b - y)) / r0
+            res["jr_stationary_w1.0_50_sweeps_residual_growth"] = \
+                growth if math.isfinite(growth) else None
+        h.close()
+        out[name] = res
+    return out
 
 
 def serving(gs2, torch, count):
