@@ -62,38 +62,60 @@ static HCsr transpose(const HCsr& a) {
 }
 
 // C = A B by rows (Gustavson): a dense accumulator indexed by column and a
-// list of the columns a row touched; columns of each row sorted.
+// list of the columns a row touched; columns of each row sorted.  Row
+// ranges run on parallel host threads (a symbolic pass counts each row's
+// columns, a numeric pass fills them); every row is summed in the same order
+// as a sequential product.
 static HCsr multiply(const HCsr& a, const HCsr& b) {
   HCsr c;
   c.n = a.n;
   c.m = b.m;
   c.rp.assign(c.n + 1, 0);
-  std::vector<int64_t> seen(b.m, -1);
-  std::vector<double> acc(b.m, 0.0);
-  std::vector<int32_t> cols;
-  cols.reserve(256);
-  for (int64_t i = 0; i < a.n; ++i) {
-    cols.clear();
-    for (int64_t k = a.rp[i]; k < a.rp[i + 1]; ++k) {
-      const int64_t r = a.ci[k];
-      const double av = a.va[k];
-      for (int64_t q = b.rp[r]; q < b.rp[r + 1]; ++q) {
-        const int32_t j = b.ci[q];
-        if (seen[j] != i) {
-          seen[j] = i;
-          acc[j] = 0.0;
-          cols.push_back(j);
+  parallel_ranges(a.n, [&](int64_t i0, int64_t i1, int) {
+    std::vector<int64_t> seen(b.m, -1);
+    for (int64_t i = i0; i < i1; ++i) {
+      int64_t cnt = 0;
+      for (int64_t k = a.rp[i]; k < a.rp[i + 1]; ++k) {
+        const int64_t r = a.ci[k];
+        for (int64_t q = b.rp[r]; q < b.rp[r + 1]; ++q)
+          if (seen[b.ci[q]] != i) {
+            seen[b.ci[q]] = i;
+            ++cnt;
+          }
+      }
+      c.rp[i + 1] = cnt;
+    }
+  });
+  for (int64_t i = 0; i < c.n; ++i) c.rp[i + 1] += c.rp[i];
+  c.ci.resize(c.rp[c.n]);
+  c.va.resize(c.rp[c.n]);
+  parallel_ranges(a.n, [&](int64_t i0, int64_t i1, int) {
+    std::vector<int64_t> seen(b.m, -1);
+    std::vector<double> acc(b.m, 0.0);
+    std::vector<int32_t> cols;
+    for (int64_t i = i0; i < i1; ++i) {
+      cols.clear();
+      for (int64_t k = a.rp[i]; k < a.rp[i + 1]; ++k) {
+        const int64_t r = a.ci[k];
+        const double av = a.va[k];
+        for (int64_t q = b.rp[r]; q < b.rp[r + 1]; ++q) {
+          const int32_t j = b.ci[q];
+          if (seen[j] != i) {
+            seen[j] = i;
+            acc[j] = 0.0;
+            cols.push_back(j);
+          }
+          acc[j] += av * b.va[q];
         }
-        acc[j] += av * b.va[q];
+      }
+      std::sort(cols.begin(), cols.end());
+      int64_t o = c.rp[i];
+      for (int32_t j : cols) {
+        c.ci[o] = j;
+        c.va[o++] = acc[j];
       }
     }
-    std::sort(cols.begin(), cols.end());
-    for (int32_t j : cols) {
-      c.ci.push_back(j);
-      c.va.push_back(acc[j]);
-    }
-    c.rp[i + 1] = (int64_t)c.ci.size();
-  }
+  });
   return c;
 }
 
@@ -101,34 +123,63 @@ static HCsr multiply(const HCsr& a, const HCsr& b) {
 // aggregation
 // ---------------------------------------------------------------------------
 
-// Symmetrised strength graph as sorted adjacency lists.
+// Symmetrised strength graph as sorted adjacency lists: the directed strong
+// entries (S), their transpose, and per row the sorted union of both, each
+// step over parallel row ranges except the transpose's counting.
 static void strength(const HCsr& a, double theta, std::vector<int64_t>& gp,
                      std::vector<int32_t>& gi) {
   const int64_t n = a.n;
-  std::vector<std::vector<int32_t>> adj(n);
-  for (int64_t i = 0; i < n; ++i) {
-    double big = 0.0;
-    for (int64_t k = a.rp[i]; k < a.rp[i + 1]; ++k)
-      if (a.ci[k] != i) big = std::max(big, std::fabs(a.va[k]));
-    if (big == 0.0) continue;
-    for (int64_t k = a.rp[i]; k < a.rp[i + 1]; ++k) {
-      const int32_t j = a.ci[k];
-      if (j != i && std::fabs(a.va[k]) >= theta * big) {
-        adj[i].push_back(j);
-        adj[j].push_back((int32_t)i);
-      }
+  HCsr S;
+  S.n = S.m = n;
+  S.rp.assign(n + 1, 0);
+  std::vector<double> big(n, 0.0);
+  parallel_ranges(n, [&](int64_t i0, int64_t i1, int) {
+    for (int64_t i = i0; i < i1; ++i) {
+      double m = 0.0;
+      for (int64_t k = a.rp[i]; k < a.rp[i + 1]; ++k)
+        if (a.ci[k] != i) m = std::max(m, std::fabs(a.va[k]));
+      big[i] = m;
+      int64_t cnt = 0;
+      if (m > 0.0)
+        for (int64_t k = a.rp[i]; k < a.rp[i + 1]; ++k)
+          if (a.ci[k] != i && std::fabs(a.va[k]) >= theta * m) ++cnt;
+      S.rp[i + 1] = cnt;
     }
-  }
+  });
+  for (int64_t i = 0; i < n; ++i) S.rp[i + 1] += S.rp[i];
+  S.ci.resize(S.rp[n]);
+  S.va.assign(S.rp[n], 1.0);
+  parallel_ranges(n, [&](int64_t i0, int64_t i1, int) {
+    for (int64_t i = i0; i < i1; ++i) {
+      int64_t o = S.rp[i];
+      if (big[i] > 0.0)
+        for (int64_t k = a.rp[i]; k < a.rp[i + 1]; ++k)
+          if (a.ci[k] != i && std::fabs(a.va[k]) >= theta * big[i]) S.ci[o++] = a.ci[k];
+    }
+  });
+  const HCsr St = transpose(S);
   gp.assign(n + 1, 0);
-  gi.clear();
-  for (int64_t i = 0; i < n; ++i) {
-    auto& v = adj[i];
-    std::sort(v.begin(), v.end());
-    v.erase(std::unique(v.begin(), v.end()), v.end());
-    gi.insert(gi.end(), v.begin(), v.end());
-    gp[i + 1] = (int64_t)gi.size();
-    std::vector<int32_t>().swap(v);
-  }
+  parallel_ranges(n, [&](int64_t i0, int64_t i1, int) {
+    std::vector<int32_t> v;
+    for (int64_t i = i0; i < i1; ++i) {
+      v.assign(S.ci.begin() + S.rp[i], S.ci.begin() + S.rp[i + 1]);
+      v.insert(v.end(), St.ci.begin() + St.rp[i], St.ci.begin() + St.rp[i + 1]);
+      std::sort(v.begin(), v.end());
+      gp[i + 1] = std::unique(v.begin(), v.end()) - v.begin();
+    }
+  });
+  for (int64_t i = 0; i < n; ++i) gp[i + 1] += gp[i];
+  gi.resize(gp[n]);
+  parallel_ranges(n, [&](int64_t i0, int64_t i1, int) {
+    std::vector<int32_t> v;
+    for (int64_t i = i0; i < i1; ++i) {
+      v.assign(S.ci.begin() + S.rp[i], S.ci.begin() + S.rp[i + 1]);
+      v.insert(v.end(), St.ci.begin() + St.rp[i], St.ci.begin() + St.rp[i + 1]);
+      std::sort(v.begin(), v.end());
+      v.erase(std::unique(v.begin(), v.end()), v.end());
+      std::copy(v.begin(), v.end(), gi.begin() + gp[i]);
+    }
+  });
 }
 
 static int64_t aggregate(const std::vector<int64_t>& gp, const std::vector<int32_t>& gi,

@@ -204,25 +204,6 @@ KernelTimer::~KernelTimer() {
 // setup helpers
 // ---------------------------------------------------------------------------
 
-// Host setup loops run over row ranges on up to kHostThreads threads (one
-// range below 64K rows per thread); f(begin, end, thread index) must not
-// throw.
-constexpr int kHostThreads = 16;
-template <class F>
-static void parallel_ranges(int64_t n, F f) {
-  const int64_t per = 65536;
-  const int64_t hw = std::max(1u, std::thread::hardware_concurrency());
-  const int nt = (int)std::max<int64_t>(
-      1, std::min<int64_t>({hw, (int64_t)kHostThreads, (n + per - 1) / per}));
-  if (nt == 1) {
-    f(int64_t(0), n, 0);
-    return;
-  }
-  std::vector<std::thread> th;
-  for (int t = 0; t < nt; ++t) th.emplace_back(f, n * t / nt, n * (t + 1) / nt, t);
-  for (auto& x : th) x.join();
-}
-
 constexpr int kHardCap = 6144;  // staged entries per tile at most
 constexpr int kPad = 16;        // padding entries after every CSR array
 

@@ -5,8 +5,10 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/gs2.h"
@@ -335,6 +337,25 @@ void destroy_handle(gs2_handle* h);
 // pinned memory synchronises the device)
 void* pinned_get(size_t bytes);
 void pinned_put(void* p, size_t bytes);
+
+// Host setup loops run over row ranges on up to kHostThreads threads (one
+// range below 64K rows per thread); f(begin, end, thread index) must not
+// throw.
+constexpr int kHostThreads = 16;
+template <class F>
+inline void parallel_ranges(int64_t n, F f) {
+  const int64_t per = 65536;
+  const int64_t hw = std::max(1u, std::thread::hardware_concurrency());
+  const int nt = (int)std::max<int64_t>(
+      1, std::min<int64_t>({hw, (int64_t)kHostThreads, (n + per - 1) / per}));
+  if (nt == 1) {
+    f(int64_t(0), n, 0);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (int t = 0; t < nt; ++t) th.emplace_back(f, n * t / nt, n * (t + 1) / nt, t);
+  for (auto& x : th) x.join();
+}
 
 // geometry helpers
 int vec_blocks(gs2_handle* h, int64_t n);
