@@ -495,3 +495,32 @@ def test_profiled_launch_counts_in_graph_and_eager_cycles(g, mode):
     assert st["spmv"]["launches"] == info.iters
     assert st["cgs2_upd_norm"]["launches"] == info.iters
     assert all(v["total_ms"] > 0 for v in st.values() if v["launches"])
+
+
+def test_handles_release_all_device_memory(g):
+    """Handles with every optional structure (lower-precision copies, level
+    sets, colours, an AMG hierarchy, Krylov workspace, captured graphs) give
+    all their device memory back when destroyed."""
+    import torch
+    pr = P.poisson3d(24)
+    torch.cuda.synchronize()
+
+    def cycle():
+        h = g.gs2_setup(pr.A, precisions=("fp32", "fp16"))
+        x = dev(np.zeros(pr.n))
+        for prm in (g.params("gs2", 1, 1, direction="symmetric", precision="fp16"),
+                    g.params("gs", 1, direction="symmetric"),
+                    g.params("mtgs", 1, direction="symmetric"),
+                    g.params("amg", 1, 1, direction="symmetric")):
+            x.zero_()
+            info = g.gmres_solve(h, dev(pr.b), x, 30, 1e-8, 500, prm)
+            assert info.status == 0
+        h.close()
+        torch.cuda.synchronize()
+
+    cycle()  # first use: process-wide caches (pinned pool, kernel attributes)
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(5):
+        cycle()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free0 - free1 < 4 << 20, (free0, free1)
