@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <exception>
 #include <string>
 #include <thread>
 #include <vector>
@@ -339,8 +340,8 @@ void* pinned_get(size_t bytes);
 void pinned_put(void* p, size_t bytes);
 
 // Host setup loops run over row ranges on up to kHostThreads threads (one
-// range below 64K rows per thread); f(begin, end, thread index) must not
-// throw.
+// range below 64K rows per thread).  An exception thrown by f in a worker
+// (a failed host allocation) is rethrown here after every worker has ended.
 constexpr int kHostThreads = 16;
 template <class F>
 inline void parallel_ranges(int64_t n, F f) {
@@ -352,9 +353,19 @@ inline void parallel_ranges(int64_t n, F f) {
     f(int64_t(0), n, 0);
     return;
   }
+  std::vector<std::exception_ptr> err(nt);
   std::vector<std::thread> th;
-  for (int t = 0; t < nt; ++t) th.emplace_back(f, n * t / nt, n * (t + 1) / nt, t);
+  for (int t = 0; t < nt; ++t)
+    th.emplace_back([&, t] {
+      try {
+        f(n * t / nt, n * (t + 1) / nt, t);
+      } catch (...) {
+        err[t] = std::current_exception();
+      }
+    });
   for (auto& x : th) x.join();
+  for (auto& e : err)
+    if (e) std::rethrow_exception(e);
 }
 
 // geometry helpers
