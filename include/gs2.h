@@ -301,6 +301,50 @@ gs2_status gs2_batch_solve(gs2_handle* const* hs, const double* const* bs,
                            double tol, int max_iters, const gs2_params* precond,
                            gs2_solve_info* infos);
 
+/* ---- packs: many independent systems in one set of launches ------------
+ *
+ * A pack holds `count` independent systems A_s x_s = b_s as one handle
+ * whose matrix is their block-diagonal concatenation diag(A_0, ..., A_{S-1})
+ * (system s owns rows offsets[s] .. offsets[s+1]-1).  Every row kernel of a
+ * sweep (residual, inner JR sweeps, SpMV, level-scheduled and multicolour
+ * GS, JR) covers all systems in one launch: a row reads only its own
+ * system's columns, so each system is relaxed exactly as it would be alone
+ * (gs2_apply and the other relaxations work on a pack unchanged, vectors
+ * concatenated).  gs2_pack_gmres runs restarted GMRES for all systems at
+ * once with per-system inner products, Hessenberg matrices, Givens
+ * rotations, stopping tests and iteration counts; each restart cycle is one
+ * replay of the captured Arnoldi steps for every system still running.
+ * Small systems, which alone leave the GPU idle between launches, share the
+ * launches of a pack.  The paper solves one system at a time; packs are a
+ * library extension. */
+
+/* Create a pack from host CSR arrays: n[s] rows, rowptr[s] (int64, n[s]+1,
+ * rowptr[s][0] = 0), col[s] (int32, columns of system s: 0 .. n[s]-1) and
+ * val[s] (double) per system, with the conventions of gs2_setup (diagonal,
+ * duplicates; precisions and stream as there).  Errors name the system and
+ * its row.  The total rows and entries must stay below 2^31. */
+gs2_status gs2_pack_setup(int count, const int64_t* n, const int64_t* const* rowptr,
+                          const int32_t* const* col, const double* const* val,
+                          unsigned precisions, void* stream, gs2_handle** out);
+
+/* Systems of a pack (0 for a handle made by gs2_setup) and, if offsets is
+ * not NULL, their first rows: offsets[count + 1], offsets[count] = n. */
+gs2_status gs2_pack_info(const gs2_handle* h, int* count, int64_t* offsets);
+
+/* Restarted GMRES(restart) on every system of a pack, each with the
+ * semantics of gmres_solve (right preconditioning by `precond` from a zero
+ * start, CGS2, Givens, tol relative to ||b_s||, at most max_iters Arnoldi
+ * steps per system).  b and x are the concatenated vectors (double[n],
+ * device or host as in gmres_solve; x holds every x_s0 on entry).
+ * infos[count] (may be NULL) receives each system's result.  The AMG
+ * preconditioner kinds are refused (a hierarchy of the pack would coarsen
+ * all systems together).  Returns OK if every system converged, else the
+ * first failing system's status.  Per-system results equal gmres_solve's on
+ * the system alone up to the rounding of the inner products (the block
+ * partition of a reduction differs). */
+gs2_status gs2_pack_gmres(gs2_handle* h, const double* b, double* x, int restart, double tol,
+                          int max_iters, const gs2_params* precond, gs2_solve_info* infos);
+
 /* Synchronise the handle's stream and report a sticky device-side error:
  * TIMEOUT if a kernel's bounded wait on its own shared-memory copies gave
  * up (the kernel then returned without touching its outputs further).  The

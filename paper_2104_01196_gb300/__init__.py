@@ -147,6 +147,9 @@ def load(path: str | None = None):
         "gs2_amg_setup": [P, ctypes.POINTER(_AmgCfg)],
         "gs2_amg_info": [P, ctypes.POINTER(I), P, P, P],
         "gs2_amg_vcycle": [P, P, P, ctypes.POINTER(Params)],
+        "gs2_pack_setup": [I, P, P, P, P, U, P, ctypes.POINTER(P)],
+        "gs2_pack_info": [P, ctypes.POINTER(I), P],
+        "gs2_pack_gmres": [P, P, P, I, D, I, ctypes.POINTER(Params), P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -335,6 +338,63 @@ def gs2_setup(A, precisions=(), stream=None) -> Handle:
     _check(load().gs2_setup(n, nnz, ptrs[0], ptrs[1], ptrs[2], on_dev, mask, s or None,
                             ctypes.byref(out)))
     return Handle(out.value, n, nnz, s)
+
+
+class PackHandle(Handle):
+    """A pack: independent systems held as one block-diagonal handle.
+    `offsets[s]` is the first row of system s in the concatenated vectors."""
+
+    def __init__(self, ptr, n, nnz, stream, offsets):
+        super().__init__(ptr, n, nnz, stream)
+        self.offsets = offsets
+        self.count = len(offsets) - 1
+
+    def split(self, v) -> list:
+        """The per-system pieces of a concatenated vector."""
+        return [v[self.offsets[s]:self.offsets[s + 1]] for s in range(self.count)]
+
+
+def pack_setup(As, precisions=(), stream=None) -> PackHandle:
+    """Create a pack from a list of host CSR matrices (rowptr int64, col
+    int32, val float64), each indexed from 0 within its own system."""
+    cnt = len(As)
+    keep = []
+    N = (ctypes.c_int64 * cnt)()
+    R, C, V = (ctypes.c_void_p * cnt)(), (ctypes.c_void_p * cnt)(), (ctypes.c_void_p * cnt)()
+    nnz = 0
+    for s, (rp, ci, va) in enumerate(As):
+        rp = np.ascontiguousarray(rp, dtype=np.int64)
+        ci = np.ascontiguousarray(ci, dtype=np.int32)
+        va = np.ascontiguousarray(va, dtype=np.float64)
+        keep += [rp, ci, va]
+        N[s] = len(rp) - 1
+        R[s], C[s], V[s] = rp.ctypes.data, ci.ctypes.data, va.ctypes.data
+        nnz += int(rp[-1])
+    mask = 0
+    for p in precisions:
+        mask |= 1 << (_PREC[p] if isinstance(p, str) else int(p))
+    st = _current_stream() if stream is None else stream
+    out = ctypes.c_void_p()
+    _check(load().gs2_pack_setup(cnt, N, R, C, V, mask, st or None, ctypes.byref(out)))
+    cnt_out = ctypes.c_int()
+    off = (ctypes.c_int64 * (cnt + 1))()
+    _check(load().gs2_pack_info(out.value, ctypes.byref(cnt_out), off))
+    offsets = [int(off[i]) for i in range(cnt_out.value + 1)]
+    return PackHandle(out.value, offsets[-1], nnz, st, offsets)
+
+
+def pack_gmres(h: PackHandle, b, x, restart=30, tol=1e-8, max_iters=10000,
+               precond: Params | None = None) -> list:
+    """GMRES on every system of a pack (b, x concatenated); a SolveInfo per
+    system."""
+    pb, _kb = _ptr(b)
+    px, _kx = _ptr(x, True)
+    infos = (_Info * h.count)()
+    st = load().gs2_pack_gmres(h.ptr, pb, px, restart, tol, max_iters,
+                               ctypes.byref(precond) if precond is not None else None, infos)
+    if st not in _SOLVER_STATUSES:
+        _err(st)
+    return [SolveInfo(i.iters, i.cycles, i.status, i.true_relres) for i in infos]
 
 
 def gs2_apply(h, b, x, outer_sweeps=1, inner_sweeps=1, damping=1.0, direction=FORWARD):

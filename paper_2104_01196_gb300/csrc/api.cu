@@ -700,6 +700,7 @@ void gs2::destroy_handle(gs2_handle* h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->gstream) cudaStreamSynchronize(h->gstream);
   if (h->amg) amg_free(h);
+  if (h->pack) pack_free(h);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->gstream) cudaStreamDestroy(h->gstream);
   if (h->gev_in) cudaEventDestroy(h->gev_in);
@@ -1121,6 +1122,74 @@ gs2_status gs2_batch_solve(gs2_handle* const* hs, const double* const* bs, doubl
     ensure_precond(hs[i], precond);
   }
   return gmres_batch(hs, bs, xs, count, restart, tol, max_iters, precond, infos);
+  API_END
+}
+
+gs2_status gs2_pack_setup(int count, const int64_t* n, const int64_t* const* rowptr,
+                          const int32_t* const* col, const double* const* val,
+                          unsigned precisions, void* stream, gs2_handle** out) {
+  if (!out) {
+    set_error("out is NULL");
+    return GS2_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  API_BEGIN
+  std::vector<int64_t> off, rp;
+  std::vector<int32_t> ci;
+  std::vector<double> va;
+  pack_concat(count, n, rowptr, col, val, off, rp, ci, va);
+  gs2_handle* h = nullptr;
+  try {
+    h = setup_handle(off.back(), (int64_t)ci.size(), rp.data(), ci.data(), va.data(), 0,
+                     precisions, (cudaStream_t)stream, false);
+  } catch (const gs2::Error& e) {
+    // "... in row <g>": name the system and its own row
+    const size_t sp = e.msg.find_last_of(' ');
+    if (sp != std::string::npos && e.msg.find(" in row ") != std::string::npos) {
+      const int64_t g = std::stoll(e.msg.substr(sp + 1));
+      const int sys = (int)(std::upper_bound(off.begin(), off.end(), g) - off.begin()) - 1;
+      GS2_THROW(e.st, "system " + std::to_string(sys) + ": " + e.msg.substr(0, sp + 1) +
+                          std::to_string(g - off[sys]));
+    }
+    throw;
+  }
+  try {
+    pack_attach(h, off);
+  } catch (...) {
+    destroy_handle(h);
+    throw;
+  }
+  *out = h;
+  return GS2_OK;
+  API_END
+}
+
+gs2_status gs2_pack_info(const gs2_handle* h, int* count, int64_t* offsets) {
+  if (!h || !count) return GS2_ERR_INVALID_ARG;
+  *count = pack_count(h);
+  if (offsets && *count) {
+    const std::vector<int64_t>& off = *pack_offsets(h);
+    std::copy(off.begin(), off.end(), offsets);
+  }
+  return GS2_OK;
+}
+
+gs2_status gs2_pack_gmres(gs2_handle* h, const double* b, double* x, int restart, double tol,
+                          int max_iters, const gs2_params* precond, gs2_solve_info* infos) {
+  if (!h || (h->n && (!b || !x))) return GS2_ERR_INVALID_ARG;
+  API_BEGIN
+  if (!h->pack) GS2_THROW(GS2_ERR_INVALID_ARG, "the handle is not a pack (gs2_pack_setup)");
+  if (restart < 1 || restart > kMaxRestart || !(tol >= 0.0) || max_iters < 0)
+    GS2_THROW(GS2_ERR_INVALID_ARG, "restart must be in [1, 64], tol >= 0, max_iters >= 0");
+  check_params(precond);
+  if (precond && (precond->kind == GS2_PC_AMG || precond->kind == GS2_PC_AMG_JR))
+    GS2_THROW(GS2_ERR_INVALID_ARG, "a pack takes no AMG preconditioner");
+  if (precond && precond->kind == GS2_PC_GS2) ensure_precision(h, precond->precision);
+  ensure_precond(h, precond);
+  Staged s(h, b, x, true);
+  gs2_status st = pack_gmres_run(h, s.b, s.x, restart, tol, max_iters, precond, infos);
+  s.finish();
+  return st;
   API_END
 }
 

@@ -10,6 +10,7 @@
 #include <exception>
 #include <string>
 #include <thread>
+#include <utility>
 #include <vector>
 
 #include "../../include/gs2.h"
@@ -103,6 +104,7 @@ struct KrylovState {
 
 struct Profiler;
 struct AmgHierarchy;
+struct Pack;
 
 }  // namespace gs2
 
@@ -154,6 +156,10 @@ struct gs2_handle {
   // smoothed-aggregation multigrid hierarchy (gs2_amg_setup, or built with
   // default settings on first use as a preconditioner)
   gs2::AmgHierarchy* amg = nullptr;
+
+  // a pack of independent systems (gs2_pack_setup): the matrix is their
+  // block-diagonal concatenation; null for a single system
+  gs2::Pack* pack = nullptr;
 
   // CUDA graph of one restart cycle's Arnoldi steps (launch-bound small
   // systems): captured on a private stream, replayed there and joined to
@@ -315,6 +321,25 @@ gs2_status gmres_batch(gs2_handle* const* hs, const double* const* bs,
                        double* const* xs, int count, int m, double tol,
                        int max_iters, const gs2_params* p, gs2_solve_info* infos);
 void read_state(gs2_handle* h);
+// a kernel gave up a bounded wait: clear the device error word, throw
+void raise_device_error(gs2_handle* h);
+
+// packs of independent systems (pack.cu)
+// block-diagonal CSR of `count` systems; off receives the first row of each
+// system (count + 1 entries)
+void pack_concat(int count, const int64_t* n, const int64_t* const* rowptr,
+                 const int32_t* const* col, const double* const* val, std::vector<int64_t>& off,
+                 std::vector<int64_t>& rp, std::vector<int32_t>& ci, std::vector<double>& va);
+void pack_attach(gs2_handle* h, const std::vector<int64_t>& off);
+void pack_free(gs2_handle* h);
+int pack_count(const gs2_handle* h);
+const std::vector<int64_t>* pack_offsets(const gs2_handle* h);
+// (system, row of that system) of a row of the pack
+std::pair<int, int64_t> pack_locate(const gs2_handle* h, int64_t row);
+// GMRES(m) on every system of the pack; infos[count]; returns OK if every
+// system converged, else the first failing status
+gs2_status pack_gmres_run(gs2_handle* h, const double* b, double* x, int m, double tol,
+                          int max_iters, const gs2_params* p, gs2_solve_info* infos);
 
 // A GMRES solve as a resumable job (used by the server): start enqueues
 // the first work on the handle's stream; advance must be called only once

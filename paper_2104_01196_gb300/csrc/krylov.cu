@@ -14,6 +14,7 @@
 #include <thread>
 #include <vector>
 
+#include "arnoldi.cuh"
 #include "internal.cuh"
 #include "reduce.cuh"
 
@@ -22,29 +23,6 @@ namespace gs2 {
 // ---------------------------------------------------------------------------
 // reductions
 // ---------------------------------------------------------------------------
-
-// Block-wide sums of NV per-thread values, written to part[v * nblk + blk]
-// (general form: one shuffle tree per value; used for NV > 32).
-template <int NV>
-__device__ __forceinline__ void block_partials(const double (&acc)[NV], int nv, double* part,
-                                               int nblk) {
-  __shared__ double red[kVecThreads / 32][NV];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    if (v < nv) {
-      const double s = warp_sum(acc[v]);
-      if (lane == 0) red[wid][v] = s;
-    }
-  }
-  __syncthreads();
-  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
-    double s = 0.0;
-#pragma unroll
-    for (int w = 0; w < kVecThreads / 32; ++w) s += red[w][v];
-    part[(size_t)v * nblk + blockIdx.x] = s;
-  }
-}
 
 // out[v] = sum over blocks of part[v * nblk + b], one block per v, fixed
 // order.  mode 0: H(v, j) = s; mode 1: H(v, j) += s; both also hbuf[v] = s.
@@ -98,11 +76,9 @@ k_dots_x(int n, const double* __restrict__ V, const double* __restrict__ w, doub
 
 // pass 2: w -= V h ; part = V^T w          (NORM = false)
 // pass 3: w -= V h ; part[0] = w^T w       (NORM = true)
-// w_i - sum_k V_ki h_k is one FMA chain started at w_i with the negated
-// coefficients, so the update issues no FP64 instruction beyond its
-// products.  The FP64 pipe limits these passes, and at its issue interval
-// (one warp instruction per 64 cycles per scheduler) a dependent chain does
-// not stall.
+// (the loop bodies of these two kernels are those of dots_rows and
+// update_rows, written out: through the inline functions ptxas allocates
+// more registers, which lowers the resident blocks of the dot pass)
 template <int JC, bool NORM>
 __global__ void __launch_bounds__(kVecThreads)
 k_update_x(int n, const double* __restrict__ V, const double* __restrict__ hcoef,
@@ -178,82 +154,14 @@ k_update(int n, const double* __restrict__ V, int jc, const double* __restrict__
   block_partials<NA>(acc, NORM ? 1 : jc, part, nblk);
 }
 
-// Givens step j: H(j+1, j) = ||w||, earlier rotations applied to column j,
-// new rotation from (H(j,j), H(j+1,j)) with
-//   d = sqrt(f^2 + g^2), c = |f|/d, r = sign(f) d, s = g/r
-// (f = 0: c = 0, s = sign(g), r = |g|; g = 0: c = 1, s = 0, r = f),
-// residual estimate |g_{j+1}|, and the stop decision of the cycle.  The
-// column and the earlier rotations are staged in shared memory by all
-// threads; the sequential rotation chain then runs on shared memory.
+// Givens step j (givens_block) of the single system; a step that ends the
+// cycle also raises the mapped host flag.
 __global__ void k_givens(const double* __restrict__ part, int nblk, double* H, int ldh, int j,
                          double* cs, double* sn, double* gv, KrylovState* st,
                          volatile int* stop_host) {
   if (st->stop) return;
-  __shared__ double red[32];
-  __shared__ double col_s[kMaxRestart + 2], cs_s[kMaxRestart + 1], sn_s[kMaxRestart + 1];
-  double* col = H + (size_t)j * ldh;
-  for (int i = threadIdx.x; i <= j; i += blockDim.x) col_s[i] = col[i];
-  for (int i = threadIdx.x; i < j; i += blockDim.x) {
-    cs_s[i] = cs[i];
-    sn_s[i] = sn[i];
-  }
-  double s = 0.0;
-  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part[b];
-  s = warp_sum(s);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) red[wid] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double nrm2 = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) nrm2 += red[w];
-    const double hn = sqrt(nrm2);
-    col_s[j + 1] = hn;
-    for (int i = 0; i < j; ++i) {
-      const double a = col_s[i], c = col_s[i + 1];
-      col_s[i] = cs_s[i] * a + sn_s[i] * c;
-      col_s[i + 1] = -sn_s[i] * a + cs_s[i] * c;
-    }
-    const double f = col_s[j], g = col_s[j + 1];
-    double c, sgv, r;
-    if (g == 0.0) {
-      c = 1.0; sgv = 0.0; r = f;
-    } else if (f == 0.0) {
-      c = 0.0; sgv = g > 0.0 ? 1.0 : -1.0; r = fabs(g);
-    } else {
-      const double d = sqrt(f * f + g * g);
-      c = fabs(f) / d;
-      r = f > 0.0 ? d : -d;
-      sgv = g / r;
-    }
-    cs[j] = c;
-    sn[j] = sgv;
-    col_s[j] = r;
-    col_s[j + 1] = 0.0;
-    const double gj = gv[j];
-    gv[j + 1] = -sgv * gj;
-    gv[j] = c * gj;
-    st->iters += 1;
-    st->k = j + 1;
-    st->hn = hn;
-    st->inv_hn = 1.0 / hn;
-    const double est = fabs(-sgv * gj);
-    int stop = 0;
-    if (isnan(est) || isnan(hn) || isinf(hn)) {
-      st->status = GS2_ERR_NAN;
-      stop = 1;
-    } else if (hn == 0.0) {
-      st->status = GS2_ERR_BREAKDOWN;
-      stop = 1;
-    } else if (est <= st->tol_abs || st->iters >= st->max_iters) {
-      stop = 1;
-    }
-    if (stop) {
-      st->stop = 1;
-      *stop_host = 1;
-    }
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) col[i] = col_s[i];
+  if (givens_block(part, 0, nblk, H + (size_t)j * ldh, cs, sn, gv, j, st) && threadIdx.x == 0)
+    *stop_host = 1;
 }
 
 // v_{j+1} = w / H(j+1, j), and the preconditioner's D^{-1} v_{j+1}
@@ -261,36 +169,14 @@ __global__ void k_scale_next(int n, const double* __restrict__ w, double* vnext,
                              const double* __restrict__ dinv, double* rhat64, float* rhat32,
                              const KrylovState* st) {
   if (st->stop) return;
-  const double a = st->inv_hn;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const double v = w[i] * a;
-    vnext[i] = v;
-    if (rhat64) rhat64[i] = dinv[i] * v;
-    if (rhat32) rhat32[i] = (float)(dinv[i] * v);
-  }
+  scale_rows(blockIdx.x * blockDim.x + threadIdx.x, n, gridDim.x * blockDim.x, st->inv_hn, w,
+             vnext, dinv, rhat64, rhat32);
 }
 
-// y = R^{-1} g over the k steps of the cycle: column-oriented back
-// substitution, y_i = g_i / R_ii, then every g_l (l < i) -= R_li y_i in
-// parallel; g lives in shared memory.
+// y = R^{-1} g over the k steps of the cycle (backsolve_block)
 __global__ void k_backsolve(const double* __restrict__ H, int ldh, const double* gv, double* y,
                             const KrylovState* st) {
-  __shared__ double g_s[kMaxRestart + 1];
-  __shared__ double yi_s;
-  const int k = st->k;
-  for (int i = threadIdx.x; i < k; i += blockDim.x) g_s[i] = gv[i];
-  __syncthreads();
-  for (int i = k - 1; i >= 0; --i) {
-    const double* ci = H + (size_t)i * ldh;
-    if (threadIdx.x == 0) {
-      yi_s = g_s[i] / ci[i];
-      y[i] = yi_s;
-    }
-    __syncthreads();
-    const double yi = yi_s;
-    for (int l = threadIdx.x; l < i; l += blockDim.x) g_s[l] -= ci[l] * yi;
-    __syncthreads();
-  }
+  backsolve_block(H, ldh, gv, y, st->k);
 }
 
 // u = V[0..k) y and the preconditioner's D^{-1} u
@@ -303,15 +189,8 @@ k_combine(int n, const double* __restrict__ V, const double* __restrict__ y, dou
   const int k = st->k;
   for (int i = threadIdx.x; i < MAXK; i += blockDim.x) ys[i] = i < k ? y[i] : 0.0;
   __syncthreads();
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    double s = 0.0;
-#pragma unroll
-    for (int l = 0; l < MAXK; ++l)
-      if (l < k) s = fma(__ldg(V + (size_t)l * n + i), ys[l], s);
-    u[i] = s;
-    if (rhat64) rhat64[i] = dinv[i] * s;
-    if (rhat32) rhat32[i] = (float)(dinv[i] * s);
-  }
+  combine_rows<MAXK>(blockIdx.x * blockDim.x + threadIdx.x, n, gridDim.x * blockDim.x, n, V, ys,
+                     k, u, dinv, rhat64, rhat32);
 }
 
 // per-block partial sums of x^T x
@@ -346,13 +225,8 @@ __global__ void k_cycle_start(int n, const double* __restrict__ r, double* v0,
                               const double* __restrict__ dinv, double* rhat64, float* rhat32,
                               double* gv, int m, KrylovState* st) {
   const double beta = st->beta;
-  const double a = 1.0 / beta;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const double v = r[i] * a;
-    v0[i] = v;
-    if (rhat64) rhat64[i] = dinv[i] * v;
-    if (rhat32) rhat32[i] = (float)(dinv[i] * v);
-  }
+  scale_rows(blockIdx.x * blockDim.x + threadIdx.x, n, gridDim.x * blockDim.x, 1.0 / beta, r, v0,
+             dinv, rhat64, rhat32);
   if (blockIdx.x == 0)
     for (int i = threadIdx.x; i <= m; i += blockDim.x) gv[i] = i == 0 ? beta : 0.0;
 }
@@ -525,7 +399,7 @@ static void copy_state_async(gs2_handle* h) {
 }
 
 // A kernel gave up a bounded wait: clear the word and fail the call.
-static void raise_device_error(gs2_handle* h) {
+void raise_device_error(gs2_handle* h) {
   const int e = *h->err_host;
   *h->err_host = 0;
   GS2_CUDA(cudaMemsetAsync(h->dev_err, 0, sizeof(int), h->stream));

@@ -73,4 +73,27 @@ __device__ __forceinline__ void block_partials_bf(const double (&acc)[NV], doubl
   }
 }
 
+// Block-wide sums of NV per-thread values, written to part[v * nblk + blk]
+// (general form: one shuffle tree per value; used for NV > 32).
+template <int NV>
+__device__ __forceinline__ void block_partials(const double (&acc)[NV], int nv, double* part,
+                                               int nblk) {
+  __shared__ double red[kVecThreads / 32][NV];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    if (v < nv) {
+      const double s = warp_sum(acc[v]);
+      if (lane == 0) red[wid][v] = s;
+    }
+  }
+  __syncthreads();
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kVecThreads / 32; ++w) s += red[w][v];
+    part[(size_t)v * nblk + blockIdx.x] = s;
+  }
+}
+
 }  // namespace gs2

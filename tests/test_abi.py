@@ -123,3 +123,47 @@ def test_binding_fails_loudly_without_library(tmp_path):
             gs2.load(str(tmp_path / "nope.so"))
     finally:
         gs2._lib = saved
+
+
+def _pack_status(lib, mats):
+    cnt = len(mats)
+    keep = []
+    N = (ctypes.c_int64 * cnt)()
+    R, C, V = (ctypes.c_void_p * cnt)(), (ctypes.c_void_p * cnt)(), (ctypes.c_void_p * cnt)()
+    for s, (rp, ci, va) in enumerate(mats):
+        rp, ci, va = (np.ascontiguousarray(rp, np.int64), np.ascontiguousarray(ci, np.int32),
+                      np.ascontiguousarray(va, np.float64))
+        keep += [rp, ci, va]
+        N[s] = len(rp) - 1
+        R[s], C[s], V[s] = rp.ctypes.data, ci.ctypes.data, va.ctypes.data
+    out = ctypes.c_void_p()
+    st = lib.gs2_pack_setup(cnt, N, R, C, V, 0, None, ctypes.byref(out))
+    return st, lib.gs2_last_error().decode()
+
+
+def test_pack_setup_names_the_bad_system_and_row(lib):
+    """A pack is validated per system before any device work: a column of
+    system s must lie inside system s (so no entry couples two systems), and
+    the errors of the whole-pack checks are reported as (system, its row)."""
+    good = P.poisson2d(4).A
+    # column 16 is inside the 32-row pack but outside system 1 (16 rows)
+    rp, ci, va = (a.copy() for a in good)
+    ci[rp[2]] = 16
+    st, msg = _pack_status(lib, [good, (rp, ci, va), good])
+    assert st == 1 and msg == "system 1: column index out of range in row 2", msg
+    # zero diagonal in row 3 of system 2
+    rp, ci, va = (a.copy() for a in good)
+    va[(ci == 3) & (np.arange(len(ci)) >= rp[3]) & (np.arange(len(ci)) < rp[4])] = 0.0
+    st, msg = _pack_status(lib, [good, good, (rp, ci, va)])
+    assert st == 2 and msg == "system 2: zero or missing diagonal in row 3", msg
+    # duplicate entry in row 0 of system 0
+    rp, ci, va = (a.copy() for a in good)
+    ci[1] = ci[0]
+    st, msg = _pack_status(lib, [(rp, ci, va), good])
+    assert st == 1 and msg == "system 0: duplicate entry in row 0", msg
+    # rowptr not starting at 0
+    st, msg = _pack_status(lib, [good, (good[0] + 1, good[1], good[2])])
+    assert st == 1 and msg.startswith("system 1: rowptr[0]")
+    out = ctypes.c_void_p()
+    assert lib.gs2_pack_setup(0, None, None, None, None, 0, None, ctypes.byref(out)) == 1
+    assert lib.gs2_pack_gmres(None, None, None, 30, 1e-8, 10, None, None) != 0

@@ -1,0 +1,241 @@
+"""GPU parity of packs: independent systems held as one block-diagonal handle.
+
+A relaxation of the pack must equal the relaxation of every system alone
+(1e-12 per system against the oracle); GMRES on the pack must take, for
+every system, the oracle's iteration count within +-1 and reach the true
+relative residual; per-system statuses (converged, not converged, NaN,
+zero right-hand side, warm start at the solution) must be those of the
+system solved alone while the other systems converge.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2104_01196_gb300 import problems as P
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def g():
+    import torch  # noqa: F401
+
+    from paper_2104_01196_gb300 import build as B
+    B.build()
+    import paper_2104_01196_gb300 as gs2
+    gs2.load()
+    return gs2
+
+
+def dev(v):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(v, dtype=np.float64)).cuda()
+
+
+def host(t):
+    import torch
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def _mix():
+    """Uneven systems: 2D and 3D Laplacians, upwind convection-diffusion, a
+    random nonsymmetric system, elasticity and a one-row system."""
+    one = P.Problem("one_row", (np.array([0, 1]), np.array([0], np.int32), np.array([4.0])),
+                    np.array([2.0]), np.array([0.5]))
+    return [P.poisson2d(20), P.poisson3d(9), P.convdiff3d(8),
+            P.random_system(700, 41, mean_offdiag=6.0, dominance=1.1), one,
+            P.poisson2d(33), P.elasticity3d(4)]
+
+
+MIX = _mix()
+
+PCS = {
+    "none": (None, dict(pc_kind=oracle.PC_NONE)),
+    "gs2_fwd_1_1": (dict(kind="gs2", outer=1, inner=1),
+                    dict(pc_kind=oracle.PC_GS2)),
+    "sgs2_1_2_damped": (dict(kind="gs2", outer=1, inner=2, omega=0.9, gamma=0.8,
+                             direction="symmetric"),
+                        dict(pc_kind=oracle.PC_GS2, pc_inner=2, pc_omega=0.9, pc_gamma=0.8,
+                             pc_direction=oracle.SYMMETRIC)),
+    "jr_3_w0.8": (dict(kind="jr", outer=3, omega=0.8),
+                  dict(pc_kind=oracle.PC_JR, pc_outer=3, pc_omega=0.8)),
+    "sgs_levels": (dict(kind="gs", outer=1, direction="symmetric"),
+                   dict(pc_kind=oracle.PC_GS, pc_direction=oracle.SYMMETRIC)),
+    "mtsgs": (dict(kind="mtgs", outer=1, direction="symmetric"),
+              dict(pc_kind=oracle.PC_MTGS, pc_direction=oracle.SYMMETRIC)),
+}
+
+
+def _cat(vs):
+    return np.concatenate([np.asarray(v, dtype=np.float64) for v in vs])
+
+
+@pytest.fixture(scope="module")
+def pack(g):
+    return g.pack_setup([p.A for p in MIX])
+
+
+def test_pack_layout(g, pack):
+    sizes = [p.n for p in MIX]
+    assert pack.count == len(MIX)
+    assert pack.offsets == list(np.concatenate([[0], np.cumsum(sizes)]))
+    assert pack.n == sum(sizes)
+
+
+@pytest.mark.parametrize("direction", ["forward", "backward", "symmetric"])
+def test_relaxation_of_a_pack_is_each_system_alone(g, pack, direction):
+    d = {"forward": oracle.FORWARD, "backward": oracle.BACKWARD,
+         "symmetric": oracle.SYMMETRIC}[direction]
+    bs = [P.uniform_pm1(300 + s, p.n) for s, p in enumerate(MIX)]
+    xs = [P.uniform_pm1(400 + s, p.n) for s, p in enumerate(MIX)]
+    x = dev(_cat(xs))
+    g.gs2_apply(pack, dev(_cat(bs)), x, 2, 2, 0.9, d)
+    for s, piece in enumerate(pack.split(host(x))):
+        xo = oracle.gs2(MIX[s].A, bs[s], xs[s], outer=2, inner=2, omega=0.9, direction=d)
+        assert rel(piece, xo) <= TOL, s
+    # the compact form (Eq. (9)) as well
+    x = dev(_cat(xs))
+    g.gs2_apply_ex(pack, dev(_cat(bs)), x, g.params("gs2", 2, 2, direction=direction,
+                                                  form="compact"))
+    for s, piece in enumerate(pack.split(host(x))):
+        xo = oracle.gs2_compact(MIX[s].A, bs[s], xs[s], 2, 2, d)
+        assert rel(piece, xo) <= TOL, s
+
+
+def test_exact_gs_and_multicolour_of_a_pack(g, pack):
+    """Level sets and first-fit colours of the pack are the systems' own."""
+    bs = [P.uniform_pm1(500 + s, p.n) for s, p in enumerate(MIX)]
+    for fn, ofn in ((g.gs_apply, oracle.gs), (g.mtgs_apply, oracle.mtgs)):
+        x = dev(np.zeros(pack.n))
+        fn(pack, dev(_cat(bs)), x, 1, 1.0, oracle.SYMMETRIC)
+        for s, piece in enumerate(pack.split(host(x))):
+            xo = ofn(MIX[s].A, bs[s], np.zeros(MIX[s].n), sweeps=1, omega=1.0,
+                     direction=oracle.SYMMETRIC)
+            assert rel(piece, xo) <= TOL, (fn.__name__, s)
+
+
+@pytest.mark.parametrize("pc", list(PCS))
+def test_pack_gmres_matches_oracle_per_system(g, pack, pc):
+    gp, op = PCS[pc]
+    x = dev(np.zeros(pack.n))
+    infos = g.pack_gmres(pack, dev(_cat([p.b for p in MIX])), x, restart=30, tol=1e-8,
+                         max_iters=3000, precond=g.params(**gp) if gp else None)
+    xs = pack.split(host(x))
+    for s, pr in enumerate(MIX):
+        if pc == "jr_3_w0.8" and pr.name.startswith("elasticity"):
+            continue  # JR does not converge on elasticity (both sides stall)
+        _, oinfo = oracle.gmres(pr.A, pr.b, restart=30, tol=1e-8, max_iters=3000, **op)
+        assert infos[s].status == 0 and oinfo.status == 0, (s, infos[s], oinfo)
+        assert abs(infos[s].iters - oinfo.iters) <= 1, (s, infos[s].iters, oinfo.iters)
+        r = np.linalg.norm(pr.b - oracle.spmv(pr.A, xs[s])) / np.linalg.norm(pr.b)
+        assert r <= 1e-8 and infos[s].true_relres <= 1e-8, (s, r)
+
+
+def test_pack_gmres_equals_each_system_solved_alone(g, pack):
+    prm = g.params("gs2", 1, 1, direction="symmetric")
+    x = dev(np.zeros(pack.n))
+    infos = g.pack_gmres(pack, dev(_cat([p.b for p in MIX])), x, 30, 1e-8, 3000, prm)
+    xs = pack.split(host(x))
+    for s, pr in enumerate(MIX):
+        h = g.gs2_setup(pr.A)
+        xa = dev(np.zeros(pr.n))
+        ia = g.gmres_solve(h, dev(pr.b), xa, 30, 1e-8, 3000, prm)
+        assert abs(ia.iters - infos[s].iters) <= 1, (s, ia.iters, infos[s].iters)
+        assert rel(xs[s], host(xa)) <= 1e-6, s
+
+
+def test_pack_statuses_are_per_system(g):
+    """In one pack: a system that converges, one whose right-hand side is
+    zero (x = 0, no step), one warm-started at its solution (no step), one
+    with a NaN in b (NAN), and the same matrix with an unreachable tolerance
+    is not tested here since tol is shared; max_iters ends every system that
+    has not converged with NOT_CONVERGED."""
+    a, b = P.poisson2d(24), P.poisson3d(7)
+    pack = g.pack_setup([a.A, a.A, b.A, b.A, a.A])
+    nan_b = b.b.copy()
+    nan_b[3] = np.nan
+    rhs = _cat([a.b, np.zeros(a.n), b.b, nan_b, a.b])
+    x0 = _cat([np.zeros(a.n), np.ones(a.n), b.x_true, np.zeros(b.n), np.zeros(a.n)])
+    x = dev(x0)
+    infos = g.pack_gmres(pack, dev(rhs), x, 30, 1e-8, 3000, g.params("gs2", 1, 1))
+    st = [i.status for i in infos]
+    assert st == [0, 0, 0, 7, 0], st
+    xs = pack.split(host(x))
+    assert np.all(xs[1] == 0.0) and infos[1].iters == 0
+    assert infos[2].iters == 0 and np.array_equal(xs[2], b.x_true)
+    assert infos[0].iters == infos[4].iters and np.array_equal(xs[0], xs[4])
+    # iteration limit: every unconverged system stops at max_iters
+    x = dev(np.zeros(pack.n))
+    infos = g.pack_gmres(pack, dev(_cat([a.b, a.b, b.b, b.b, a.b])), x, 10, 1e-12, 7,
+                         g.params("gs2", 1, 1))
+    assert [i.status for i in infos] == [5] * 5 and [i.iters for i in infos] == [7] * 5
+
+
+def test_pack_graph_and_eager_agree_bitwise_and_host_vectors(g):
+    probs = [P.poisson2d(30), P.random_system(900, 43, dominance=1.1), P.poisson3d(8)]
+    prm = g.params("gs2", 1, 1, direction="symmetric")
+    rhs = _cat([p.b for p in probs])
+    res = {}
+    for mode in (1, 2):
+        pack = g.pack_setup([p.A for p in probs])
+        pack.set_graph_mode(mode)
+        x = dev(np.zeros(pack.n))
+        infos = g.pack_gmres(pack, dev(rhs), x, 30, 1e-8, 3000, prm)
+        res[mode] = ([i.iters for i in infos], host(x))
+    assert res[1][0] == res[2][0]
+    assert np.array_equal(res[1][1], res[2][1])
+    # host vectors through the same call
+    pack = g.pack_setup([p.A for p in probs])
+    xh = np.zeros(pack.n)
+    infos = g.pack_gmres(pack, rhs, xh, 30, 1e-8, 3000, prm)
+    assert [i.iters for i in infos] == res[1][0]
+    assert np.array_equal(xh, res[1][1])
+
+
+def test_pack_lower_precision_and_restart_above_32(g):
+    probs = [P.convdiff3d(10), P.poisson2d(40)]
+    pack = g.pack_setup([p.A for p in probs])
+    rhs = dev(_cat([p.b for p in probs]))
+    for prec in ("fp32", "fp16"):
+        x = dev(np.zeros(pack.n))
+        infos = g.pack_gmres(pack, rhs, x, 30, 1e-8, 3000,
+                             g.params("gs2", 1, 1, direction="symmetric", precision=prec))
+        for s, pr in enumerate(probs):
+            _, oinfo = oracle.gmres(pr.A, pr.b, restart=30, tol=1e-8, max_iters=3000,
+                                    pc_kind=oracle.PC_GS2, pc_direction=oracle.SYMMETRIC)
+            assert infos[s].status == 0
+            assert abs(infos[s].iters - oinfo.iters) <= max(2, oinfo.iters // 10)
+    x = dev(np.zeros(pack.n))
+    infos = g.pack_gmres(pack, rhs, x, 48, 1e-10, 3000, g.params("gs2", 1, 1))
+    for s, pr in enumerate(probs):
+        _, oinfo = oracle.gmres(pr.A, pr.b, restart=48, tol=1e-10, max_iters=3000,
+                                pc_kind=oracle.PC_GS2)
+        assert infos[s].status == 0 and abs(infos[s].iters - oinfo.iters) <= 1
+
+
+def test_pack_refuses_amg_and_plain_handles(g, pack):
+    with pytest.raises(g.GS2Error):
+        g.pack_gmres(pack, dev(np.ones(pack.n)), dev(np.zeros(pack.n)), 30, 1e-8, 10,
+                     g.params("amg", 1, 1))
+    h = g.gs2_setup(P.poisson2d(8).A)
+    h_as_pack = g.PackHandle(h.ptr, h.n, h.nnz, h.stream, [0, h.n])
+    with pytest.raises(g.GS2Error):
+        g.pack_gmres(h_as_pack, dev(np.ones(h.n)), dev(np.zeros(h.n)), 30, 1e-8, 10)
+    h_as_pack._ptr = None  # owned by h
+
+
+def test_pack_with_empty_systems(g):
+    E = (np.array([0]), np.zeros(0, np.int32), np.zeros(0))
+    pr = P.poisson2d(12)
+    pack = g.pack_setup([E, pr.A, E])
+    assert pack.offsets == [0, 0, pr.n, pr.n]
+    x = dev(np.zeros(pr.n))
+    infos = g.pack_gmres(pack, dev(pr.b), x, 30, 1e-8, 500, g.params("gs2", 1, 1))
+    assert [i.status for i in infos] == [0, 0, 0]
+    assert infos[0].iters == 0 and infos[2].iters == 0 and infos[1].iters > 0
