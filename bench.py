@@ -459,6 +459,7 @@ def run_ours(args):
         out["serving"] = serving(gs2, torch, args.serve_requests)
     if rank == 0 and not args.no_extras and world == 1:
         out["small_system"] = small_system(gs2, torch)
+        out["packs"] = packs(gs2, torch)
     if rank == 0 and not args.no_extras and not args.no_workloads and world == 1:
         out["workloads"] = full_workloads(gs2, torch)
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -500,6 +501,67 @@ def small_system(gs2, torch, reps=20):
         res[name] = {"ms_per_solve": round(ms, 3), "solves_per_s": round(1000.0 / ms, 1),
                      "iters": info.iters, "true_relres": info.true_relres}
         h.close()
+    return res
+
+
+def packs(gs2, torch, count=128):
+    """Many small systems of the request stream's kinds (2D/3D Poisson and 3D
+    convection-diffusion, lognormal coefficients), n log-uniform in
+    [1e3, 3.2e4], GMRES(30) + SGS2(1,1) to 1e-8, three ways: one gmres_solve
+    after another, gs2_batch_solve (one stream per system) and one pack
+    (gs2_pack_gmres: every row kernel covers all systems, per-system Krylov
+    state).  Matrices are set up before the clock starts; each way is timed
+    once after an untimed run, wall clock around the call(s) with device
+    vectors.  The pack's per-system iteration counts are compared with the
+    separate solves'."""
+    from paper_2104_01196_gb300 import problems as P
+    recipe = P.request_stream(count, rate_hz=1.0, n_lo=1e3, n_hi=3.2e4, build=False)
+    probs = [P.variable_coefficient_problem(kind, N, seed) for _, kind, N, seed in recipe]
+    res = {"systems": count, "n_total": int(sum(p.n for p in probs)),
+           "n_range": [int(min(p.n for p in probs)), int(max(p.n for p in probs))]}
+    pc = gs2.params("gs2", 1, 1, direction="symmetric")
+    streams = [torch.cuda.Stream() for _ in probs]
+    hs = [gs2.gs2_setup(p.A, stream=s.cuda_stream) for p, s in zip(probs, streams)]
+    bs = [torch.from_numpy(p.b).cuda() for p in probs]
+    xs = [torch.zeros(p.n, dtype=torch.float64, device="cuda") for p in probs]
+    torch.cuda.synchronize()
+
+    def clock(fn):
+        fn()  # untimed: graphs, workspaces
+        for x in xs:
+            x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return out, time.perf_counter() - t0
+
+    seq, dt = clock(lambda: [gs2.gmres_solve(h, b, x, 30, 1e-8, 4000, pc)
+                             for h, b, x in zip(hs, bs, xs)])
+    res["sequential"] = {"solves_per_s": round(count / dt, 1), "s": round(dt, 4),
+                         "failed": sum(i.status != 0 for i in seq)}
+    bat, dt = clock(lambda: gs2.gs2_batch_solve(hs, bs, xs, 30, 1e-8, 4000, pc))
+    res["batch_streams"] = {"solves_per_s": round(count / dt, 1), "s": round(dt, 4),
+                            "failed": sum(i.status != 0 for i in bat)}
+    for h in hs:
+        h.close()
+    pack = gs2.pack_setup([p.A for p in probs], precisions=("fp32",))
+    b = torch.cat(bs)
+    x = torch.zeros(pack.n, dtype=torch.float64, device="cuda")
+    for prec in ("fp64", "fp32"):
+        pcp = gs2.params("gs2", 1, 1, direction="symmetric", precision=prec)
+
+        def run():
+            x.zero_()
+            return gs2.pack_gmres(pack, b, x, 30, 1e-8, 4000, pcp)
+        infos, dt = clock(run)
+        worst = max(i.true_relres for i in infos)
+        res[f"pack_{prec}"] = {
+            "solves_per_s": round(count / dt, 1), "s": round(dt, 4),
+            "failed": sum(i.status != 0 for i in infos), "worst_true_relres": worst,
+            "iters_max_abs_diff_vs_sequential": int(max(abs(a.iters - q.iters)
+                                                        for a, q in zip(infos, seq)))}
+    pack.close()
     return res
 
 
