@@ -160,6 +160,10 @@ struct gs2_handle {
   // a pack of independent systems (gs2_pack_setup): the matrix is their
   // block-diagonal concatenation; null for a single system
   gs2::Pack* pack = nullptr;
+  // per 32-row chunk of A's rows: 0 = the sliced-ELL kernels of A, L and U
+  // skip the chunk (set by a pack's solve while some of its systems have
+  // finished); null = every chunk
+  const int* row_live = nullptr;
 
   // CUDA graph of one restart cycle's Arnoldi steps (launch-bound small
   // systems): captured on a private stream, replayed there and joined to

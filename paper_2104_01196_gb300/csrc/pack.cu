@@ -41,6 +41,13 @@ struct Pack {
   int* active = nullptr;           // device, count: system takes the next cycle
   int* active_host = nullptr;      // pinned
   int* nactive = nullptr;          // device: systems still in the current cycle
+  int* off_dev = nullptr;          // device copy of off (int32)
+  // per 32-row chunk: systems overlapping the chunk that take the current
+  // cycle (live_cycle) and that are still running in it (live_run); the
+  // sliced-ELL row kernels skip chunks at zero
+  int nchunks = 0;
+  int* live_cycle = nullptr;
+  int* live_run = nullptr;
   int m = 0;                       // restart the arrays below are sized for
   double *H = nullptr, *hbuf = nullptr, *gvec = nullptr, *cs = nullptr, *sn = nullptr,
          *y = nullptr, *part = nullptr;
@@ -171,16 +178,56 @@ __global__ void k_preduce(const double* __restrict__ part, int nb, const int* __
 __global__ void k_pgivens(const double* __restrict__ part, const int* __restrict__ seg_blk,
                           KrylovState* st, double* H, size_t hstride, int ldh, int j,
                           double* cs, double* sn, double* gv, int vstride, int* nactive,
-                          KrylovState* pack_st, volatile int* stop_host) {
+                          const int* __restrict__ off, int* live_run, KrylovState* pack_st,
+                          volatile int* stop_host) {
   const int s = blockIdx.x;
   if (st[s].stop) return;
   const size_t o = (size_t)s * vstride;
   const bool ended = givens_block(part, seg_blk[s], seg_blk[s + 1], H + s * hstride + (size_t)j * ldh,
                                   cs + o, sn + o, gv + o, j, st + s);
-  if (ended && threadIdx.x == 0 && atomicSub(nactive, 1) == 1) {
+  if (!ended) return;
+  // the system's rows leave the row kernels for the rest of the cycle
+  for (int c = off[s] / 32 + threadIdx.x; c <= (off[s + 1] - 1) / 32; c += blockDim.x)
+    atomicSub(live_run + c, 1);
+  if (threadIdx.x == 0 && atomicSub(nactive, 1) == 1) {
     pack_st->stop = 1;
     *stop_host = 1;
   }
+}
+
+// system of row r: the last s with off[s] <= r (empty systems share their
+// offset with the next one and hold no row)
+__device__ __forceinline__ int system_of(const int* __restrict__ off, int count, int r) {
+  int lo = 0, hi = count;  // off[lo] <= r < off[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= r) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// chunk liveness at a cycle start: the number of systems overlapping each
+// 32-row chunk that take the cycle
+__global__ void k_plive_init(int nchunks, int n, const int* __restrict__ off, int count,
+                             const int* __restrict__ active, int* live_cycle, int* live_run) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nchunks; c += gridDim.x * blockDim.x) {
+    const int s0 = system_of(off, count, 32 * c);
+    const int s1 = system_of(off, count, min(32 * c + 31, n - 1));
+    int k = 0;
+    for (int s = s0; s <= s1; ++s) k += active[s] != 0;
+    live_cycle[c] = k;
+    live_run[c] = k;
+  }
+}
+
+// x += z over the rows of the systems that took the cycle
+__global__ void __launch_bounds__(kVecThreads)
+k_paxpy(const int4* __restrict__ blk, const int* __restrict__ active, double* x,
+        const double* __restrict__ z) {
+  const int4 b = blk[blockIdx.x];
+  if (!active[b.x]) return;
+  for (int i = b.y + threadIdx.x; i < b.z; i += blockDim.x) x[i] = x[i] + z[i];
 }
 
 // v_{j+1} = w / H(j+1, j) of the block's system, and D^{-1} v_{j+1}
@@ -394,6 +441,12 @@ void pack_attach(gs2_handle* h, const std::vector<int64_t>& off) {
   P->active = (int*)h->dalloc(sizeof(int) * P->count);
   P->active_host = (int*)pinned_get(sizeof(int) * P->count);
   P->nactive = (int*)h->dalloc(sizeof(int));
+  std::vector<int> off32(off.begin(), off.end());
+  P->off_dev = (int*)h->dalloc(sizeof(int) * (P->count + 1));
+  h->h2d(P->off_dev, off32.data(), sizeof(int) * (P->count + 1));
+  P->nchunks = (int)((N + 31) / 32);
+  P->live_cycle = (int*)h->dalloc(sizeof(int) * std::max(1, P->nchunks));
+  P->live_run = (int*)h->dalloc(sizeof(int) * std::max(1, P->nchunks));
   GS2_CUDA(cudaStreamSynchronize(h->stream));
 }
 
@@ -620,10 +673,18 @@ struct PackRun {
     GS2_LAUNCH_CHECK();
   }
 
+  // the row kernels skip chunks of systems outside `live` while it lives
+  struct LiveRows {
+    gs2_handle* h;
+    LiveRows(gs2_handle* h_, const int* live) : h(h_) { h->row_live = live; }
+    ~LiveRows() { h->row_live = nullptr; }
+  };
+
   // Arnoldi step j for every system whose cycle is still running
   void enqueue_step(int j) {
     const int N = (int)h->n;
     const int* skip = &h->st->stop;
+    LiveRows lr(h, P->live_run);
     precond_apply(h, pc, h->V + (size_t)j * N, h->z, wants, skip);
     launch_spmv(h, h->z, h->w, skip);
     const int jc = j + 1;
@@ -636,8 +697,8 @@ struct PackRun {
       KernelTimer tm(h, "givens", 8.0 * P->nb + 8.0 * 4 * (j + 2) * P->count);
       k_pgivens<<<P->count, 128, 0, h->stream>>>(P->part, P->seg_blk, P->st, P->H, P->hstride(),
                                                  ldh(), j, P->cs, P->sn, P->gvec,
-                                                 (int)P->vstride(), P->nactive, h->st,
-                                                 h->stop_mapped_dev);
+                                                 (int)P->vstride(), P->nactive, P->off_dev,
+                                                 P->live_run, h->st, h->stop_mapped_dev);
       GS2_LAUNCH_CHECK();
     }
     if (j + 1 < m) {
@@ -705,6 +766,9 @@ struct PackRun {
                              cudaMemcpyHostToDevice, h->stream));
     k_pcycle_reset<<<1, 1024, 0, h->stream>>>(P->st, P->active, P->count, P->nactive, h->st);
     GS2_LAUNCH_CHECK();
+    k_plive_init<<<(P->nchunks + 255) / 256, 256, 0, h->stream>>>(
+        P->nchunks, (int)h->n, P->off_dev, P->count, P->active, P->live_cycle, P->live_run);
+    GS2_LAUNCH_CHECK();
     k_pcycle_start<<<P->nb, kVecThreads, 0, h->stream>>>(P->blk, P->st, h->r, h->V, h->dinv,
                                                          r64, r32, P->gvec, (int)P->vstride(),
                                                          m);
@@ -749,9 +813,14 @@ struct PackRun {
                                                              h->w, h->dinv, r64, r32);
       GS2_LAUNCH_CHECK();
     }
-    precond_apply(h, pc, h->w, h->z, wants, nullptr);
-    launch_axpy(h, x, 1.0, h->z, nullptr);
-    launch_true_residual();
+    {
+      // systems that took no part in the cycle keep their x and skip the rows
+      LiveRows lr(h, P->live_cycle);
+      precond_apply(h, pc, h->w, h->z, wants, nullptr);
+      k_paxpy<<<P->nb, kVecThreads, 0, h->stream>>>(P->blk, P->active, x, h->z);
+      GS2_LAUNCH_CHECK();
+      launch_true_residual();
+    }
   }
 };
 

@@ -314,12 +314,14 @@ __device__ __forceinline__ float stream_val<__half>(const __half* p) {
 template <typename VT, class Epi>
 __global__ void __launch_bounds__(kRowThreads)
 k_sell(int n, int nchunks, const int* __restrict__ cptr, const int* __restrict__ ci,
-       const VT* __restrict__ va, Epi epi, const int* skip) {
+       const VT* __restrict__ va, Epi epi, const int* skip, const int* __restrict__ live) {
   using AT = typename ValTraits<VT>::AT;
   if (skip && *skip) return;
   const int lane = threadIdx.x & 31;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks; c += nw) {
+    // a chunk whose rows belong only to finished systems of a pack
+    if (live && live[c] == 0) continue;
     const int row = c * 32 + lane;
     const int base = cptr[c], L = (cptr[c + 1] - base) >> 5;
     typename Epi::Pre pv{};
@@ -403,8 +405,11 @@ inline void launch_sell(gs2_handle* h, const DevCsr& M, const VT* sv, const Epi&
   const int per_sm = blocks_per_sm((const void*)fn, 0);
   const int warps = kRowThreads / 32;
   const int grid = std::max(1, std::min((M.sell_chunks + warps - 1) / warps, per_sm * h->nsm));
+  // chunk liveness applies to the matrices whose rows are the handle's rows
+  const int* live =
+      (h->row_live && (&M == &h->A || &M == &h->L || &M == &h->U)) ? h->row_live : nullptr;
   fn<<<grid, kRowThreads, 0, h->stream>>>(M.n, M.sell_chunks, M.sell_ptr, M.sell_ci, sv, epi,
-                                          skip);
+                                          skip, live);
   GS2_LAUNCH_CHECK();
 }
 
