@@ -633,7 +633,9 @@ def serving(gs2, torch, count):
     SGS2(1,1) to 1e-8 (a bounded sample of `count` requests).  Measured:
     one-at-a-time gmres_solve, the server saturated (all submitted at once:
     solves/s) and the server under open-loop Poisson arrivals at 60% of that
-    rate (p50/p99 submit-to-done latency), with FP64 and FP32 inner sweeps."""
+    rate (p50/p99 submit-to-done latency), with FP64 and FP32 inner sweeps,
+    and FP32 with requests of at most 65,536 rows admitted together as packs
+    (up to 32 per pack)."""
     from paper_2104_01196_gb300 import problems as P
     recipe = P.request_stream(count, rate_hz=1.0, build=False)
     probs = [P.variable_coefficient_problem(kind, N, seed) for _, kind, N, seed in recipe]
@@ -652,10 +654,11 @@ def serving(gs2, torch, count):
         h.close()
     res["sequential_fp64"] = {"solves_per_s": count / (time.perf_counter() - t0),
                               "failed": int(seq_fail)}
-    for prec in ("fp64", "fp32"):
+    for name, prec, pack_rows in (("fp64", "fp64", 0), ("fp32", "fp32", 0),
+                                  ("fp32_packed", "fp32", 1 << 16)):
         pc = gs2.params("gs2", 1, 1, direction="symmetric", precision=prec)
         srv = gs2.Server(restart=30, tol=1e-8, max_iters=4000, precond=pc, max_slots=8,
-                         prep_threads=4)
+                         prep_threads=4, pack_rows=pack_rows, pack_max=32)
         t0 = time.perf_counter()
         tickets = [srv.submit(p.A, p.b) for p in probs]
         lat, worst = [], 0.0
@@ -678,7 +681,7 @@ def serving(gs2, torch, count):
             tickets.append(srv.submit(p.A, p.b))
         olat = [srv.wait(t, p.n)[2] for t, p in zip(tickets, probs)]
         srv.close()
-        res[f"served_{prec}"] = {
+        res[f"served_{name}"] = {
             "solves_per_s": rate, "max_active": st["max_active"], "failed": st["failed"],
             "worst_true_relres": worst,
             "saturated_latency_ms": {"p50": float(np.percentile(lat, 50)),

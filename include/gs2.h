@@ -361,7 +361,11 @@ gs2_status gs2_check(gs2_handle* h);
  * budget and the device's free memory; each admitted request gets its own
  * stream, handle and resident Krylov state, so the work of requests that
  * arrive while others are running overlaps on the GPU.  A result is the
- * same, bit for bit, as the same solve run alone through gmres_solve. */
+ * same, bit for bit, as the same solve run alone through gmres_solve; with
+ * pack_rows set, a packed request's result is the same, bit for bit, as that
+ * request solved alone as a pack of one (a pack partitions each system by
+ * its own size), and equal to gmres_solve's up to the rounding of the inner
+ * products. */
 typedef struct gs2_server gs2_server;
 
 typedef struct {
@@ -377,6 +381,12 @@ typedef struct {
   uint64_t fail_ticket;     /* fault-injection hook for tests: the request with
                                this ticket fails its admission with GS2_ERR_OOM
                                as if its allocation had failed (0 = none) */
+  int64_t pack_rows;        /* requests of at most this many rows are admitted
+                               together, up to pack_max of them taken in arrival
+                               order from the front of the queue, and solved as
+                               one pack (gs2_pack_gmres) in one slot; 0 = every
+                               request alone.  Not with an AMG preconditioner. */
+  int pack_max;             /* most requests in one pack (0 = 64) */
 } gs2_server_cfg;
 
 typedef struct {

@@ -82,7 +82,8 @@ class _ServerCfg(ctypes.Structure):
                 ("prep_threads", ctypes.c_int), ("restart", ctypes.c_int),
                 ("tol", ctypes.c_double), ("max_iters", ctypes.c_int),
                 ("has_precond", ctypes.c_int), ("precond", Params),
-                ("fail_ticket", ctypes.c_uint64)]
+                ("fail_ticket", ctypes.c_uint64), ("pack_rows", ctypes.c_int64),
+                ("pack_max", ctypes.c_int)]
 
 
 class _Request(ctypes.Structure):
@@ -505,10 +506,14 @@ class Server:
     gs2_server_* in include/gs2.h).  Matrices and vectors are host numpy."""
 
     def __init__(self, restart=30, tol=1e-8, max_iters=10000, precond: Params | None = None,
-                 max_slots=4, prep_threads=2, hbm_budget_bytes=0, fail_ticket=0):
+                 max_slots=4, prep_threads=2, hbm_budget_bytes=0, fail_ticket=0,
+                 pack_rows=0, pack_max=0):
+        """pack_rows > 0: requests of at most that many rows are admitted
+        together (up to pack_max, 0 = 64) and solved as one pack."""
         self._cfg = _ServerCfg(hbm_budget_bytes, max_slots, prep_threads, restart, tol,
                                max_iters, 1 if precond is not None else 0,
-                               precond if precond is not None else Params(), fail_ticket)
+                               precond if precond is not None else Params(), fail_ticket,
+                               pack_rows, pack_max)
         out = ctypes.c_void_p()
         _check(load().gs2_server_create(ctypes.byref(self._cfg), ctypes.byref(out)))
         self._ptr = out.value

@@ -752,46 +752,17 @@ gs2_status gs2_setup(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_
 
 }  // extern "C"
 
-// Validate A, split it, upload everything and allocate the resident
-// temporaries.  Throws gs2::Error; a partly built handle is released.
-gs2_handle* gs2::setup_handle(int64_t n, int64_t nnz, const int64_t* rowptr,
-                              const int32_t* col, const double* val, int on_device,
-                              unsigned precisions, cudaStream_t stream, bool async_alloc) {
-  gs2_handle* h = nullptr;
-  try {
-  if (n < 0 || nnz < 0) GS2_THROW(GS2_ERR_INVALID_ARG, "negative size");
-  if (n > std::numeric_limits<int>::max() - 1 || nnz > std::numeric_limits<int>::max() - 64)
-    GS2_THROW(GS2_ERR_INVALID_ARG, "n or nnz above 2^31 - 1");
-  if (!rowptr || (nnz > 0 && (!col || !val)))
-    GS2_THROW(GS2_ERR_INVALID_ARG, "NULL CSR array");
-  // the input on the host: the caller's arrays, or copies of device arrays
-  std::vector<int64_t> rp_copy;
-  std::vector<int32_t> ci_copy;
-  std::vector<double> va_copy;
-  const int64_t* RP = rowptr;
-  const int32_t* CI = col;
-  const double* VA = val;
-  if (on_device) {
-    rp_copy.resize(n + 1);
-    ci_copy.resize(nnz);
-    va_copy.resize(nnz);
-    GS2_CUDA(cudaMemcpy(rp_copy.data(), rowptr, sizeof(int64_t) * (n + 1),
-                        cudaMemcpyDeviceToHost));
-    if (nnz) {
-      GS2_CUDA(cudaMemcpy(ci_copy.data(), col, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost));
-      GS2_CUDA(cudaMemcpy(va_copy.data(), val, sizeof(double) * nnz, cudaMemcpyDeviceToHost));
-    }
-    RP = rp_copy.data();
-    CI = ci_copy.data();
-    VA = va_copy.data();
-  }
-  // validation, row ranges in parallel; the first bad row (in row order) is
-  // reported
+// Validate a host CSR matrix (rowptr, column range, duplicates, nonzero
+// finite diagonal) over parallel row ranges and return its diagonal; the
+// first bad row in row order is reported.
+void gs2::validate_csr(int64_t n, int64_t nnz, const int64_t* RP, const int32_t* CI,
+                       const double* VA, std::vector<double>* diag_out) {
   if (RP[0] != 0 || RP[n] != nnz)
     GS2_THROW(GS2_ERR_INVALID_ARG, "rowptr[0] must be 0 and rowptr[n] must be nnz");
   for (int64_t i = 0; i < n; ++i)
     if (RP[i + 1] < RP[i]) GS2_THROW(GS2_ERR_INVALID_ARG, "rowptr is not monotone");
-  std::vector<double> diag(n, 0.0);
+  std::vector<double>& diag = *diag_out;
+  diag.assign(n, 0.0);
   struct RowError {
     int64_t row = std::numeric_limits<int64_t>::max();
     gs2_status st = GS2_OK;
@@ -843,6 +814,45 @@ gs2_handle* gs2::setup_handle(int64_t n, int64_t nnz, const int64_t* rowptr,
   for (const RowError& e : errs)
     if (e.row < first->row) first = &e;
   if (first->st != GS2_OK) GS2_THROW(first->st, first->what + std::to_string(first->row));
+}
+
+// Validate A, split it, upload everything and allocate the resident
+// temporaries.  Throws gs2::Error; a partly built handle is released.
+gs2_handle* gs2::setup_handle(int64_t n, int64_t nnz, const int64_t* rowptr,
+                              const int32_t* col, const double* val, int on_device,
+                              unsigned precisions, cudaStream_t stream, bool async_alloc) {
+  gs2_handle* h = nullptr;
+  try {
+  if (n < 0 || nnz < 0) GS2_THROW(GS2_ERR_INVALID_ARG, "negative size");
+  if (n > std::numeric_limits<int>::max() - 1 || nnz > std::numeric_limits<int>::max() - 64)
+    GS2_THROW(GS2_ERR_INVALID_ARG, "n or nnz above 2^31 - 1");
+  if (!rowptr || (nnz > 0 && (!col || !val)))
+    GS2_THROW(GS2_ERR_INVALID_ARG, "NULL CSR array");
+  // the input on the host: the caller's arrays, or copies of device arrays
+  std::vector<int64_t> rp_copy;
+  std::vector<int32_t> ci_copy;
+  std::vector<double> va_copy;
+  const int64_t* RP = rowptr;
+  const int32_t* CI = col;
+  const double* VA = val;
+  if (on_device) {
+    rp_copy.resize(n + 1);
+    ci_copy.resize(nnz);
+    va_copy.resize(nnz);
+    GS2_CUDA(cudaMemcpy(rp_copy.data(), rowptr, sizeof(int64_t) * (n + 1),
+                        cudaMemcpyDeviceToHost));
+    if (nnz) {
+      GS2_CUDA(cudaMemcpy(ci_copy.data(), col, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost));
+      GS2_CUDA(cudaMemcpy(va_copy.data(), val, sizeof(double) * nnz, cudaMemcpyDeviceToHost));
+    }
+    RP = rp_copy.data();
+    CI = ci_copy.data();
+    VA = va_copy.data();
+  }
+  // validation, row ranges in parallel; the first bad row (in row order) is
+  // reported
+  std::vector<double> diag;
+  validate_csr(n, nnz, RP, CI, VA, &diag);
   // split A = L + D + U, triangles prescaled by D^{-1} (Sec. 6.1.3): count
   // per row, prefix sums, fill, row ranges in parallel
   std::vector<int> rp32(n + 1);

@@ -344,6 +344,15 @@ std::pair<int, int64_t> pack_locate(const gs2_handle* h, int64_t row);
 // system converged, else the first failing status
 gs2_status pack_gmres_run(gs2_handle* h, const double* b, double* x, int m, double tol,
                           int max_iters, const gs2_params* p, gs2_solve_info* infos);
+// the same as a resumable job (as GmresJob); pack_job_info gives system s's
+// result once the job is done
+struct PackJob;
+PackJob* pack_job_start(gs2_handle* h, const double* b, double* x, int m, double tol,
+                        int max_iters, const gs2_params* p);
+void pack_job_prepare(PackJob* j);
+bool pack_job_advance(PackJob* j);
+gs2_solve_info pack_job_info(const PackJob* j, int s);
+void pack_job_free(PackJob* j);
 
 // A GMRES solve as a resumable job (used by the server): start enqueues
 // the first work on the handle's stream; advance must be called only once
@@ -356,6 +365,11 @@ bool gmres_job_advance(GmresJob* j);
 void gmres_job_prepare(GmresJob* j);
 gs2_solve_info gmres_job_info(const GmresJob* j);
 void gmres_job_free(GmresJob* j);
+
+// host validation of a CSR matrix as gs2_setup does it (throws the first
+// bad row's error); *diag receives the diagonal
+void validate_csr(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col,
+                  const double* val, std::vector<double>* diag);
 
 // handle creation / destruction shared by gs2_setup and the server
 gs2_handle* setup_handle(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col,

@@ -409,22 +409,23 @@ std::pair<int, int64_t> pack_locate(const gs2_handle* h, int64_t g) {
   return {s, g - off[s]};
 }
 
-// The block table: about four blocks per SM over the whole pack, at least
-// 512 rows per block, every block inside one system, at least one block per
-// non-empty system.
+// The block table: every block inside one system, at least 512 rows per
+// block and at most 256 blocks per system (at least one per non-empty
+// system).  A system's partition depends on its own size only, so its
+// reductions, and with them its whole solve, do not depend on the other
+// systems of the pack.
 void pack_attach(gs2_handle* h, const std::vector<int64_t>& off) {
   Pack* P = new Pack();
   h->pack = P;
   P->count = (int)off.size() - 1;
   P->off = off;
   const int64_t N = off.back();
-  const int64_t target = 4LL * h->nsm;
-  const int64_t rpb = std::max<int64_t>(2 * kVecThreads, (N + target - 1) / target);
   std::vector<int4> blk;
   std::vector<int> sb(P->count + 1, 0);
   for (int s = 0; s < P->count; ++s) {
     sb[s] = (int)blk.size();
     const int64_t r0 = off[s], ns = off[s + 1] - off[s];
+    const int64_t rpb = std::max<int64_t>(2 * kVecThreads, (ns + 255) / 256);
     const int64_t k = (ns + rpb - 1) / rpb;
     for (int64_t b = 0; b < k; ++b)
       blk.push_back(make_int4(s, (int)(r0 + ns * b / k), (int)(r0 + ns * (b + 1) / k), b == 0));
@@ -823,6 +824,44 @@ struct PackRun {
     }
   }
 };
+
+// A pack solve as a resumable job (the server's packs of small requests):
+// start enqueues the first work on the handle's stream; advance is called
+// only when that stream is idle and returns true once every system is done.
+struct PackJob {
+  gs2_params params{};
+  bool has_params = false;
+  PackRun run;
+};
+
+PackJob* pack_job_start(gs2_handle* h, const double* b, double* x, int m, double tol,
+                        int max_iters, const gs2_params* p) {
+  PackJob* j = new PackJob();
+  if (p) {
+    j->params = *p;
+    j->has_params = true;
+  }
+  try {
+    j->run.start(h, b, x, m, tol, max_iters, j->has_params ? &j->params : nullptr);
+  } catch (...) {
+    delete j;
+    throw;
+  }
+  return j;
+}
+
+void pack_job_prepare(PackJob* j) {
+  if (!j->run.finished && j->run.use_graph()) j->run.ensure_graph();
+}
+
+bool pack_job_advance(PackJob* j) {
+  if (!j->run.finished) j->run.advance();
+  return j->run.finished;
+}
+
+gs2_solve_info pack_job_info(const PackJob* j, int s) { return j->run.loc[s]; }
+
+void pack_job_free(PackJob* j) { delete j; }
 
 gs2_status pack_gmres_run(gs2_handle* h, const double* b, double* x, int m, double tol,
                           int max_iters, const gs2_params* p, gs2_solve_info* infos) {

@@ -10,7 +10,10 @@
 // arrive while others run are therefore admitted as slots and memory free
 // up, and their kernels overlap on the GPU.  Every request runs the same
 // kernels with the same launch geometry as a lone gmres_solve, so its
-// result is bitwise the same alone and in the mix.
+// result is bitwise the same alone and in the mix.  With packing enabled,
+// small requests at the front of the queue are admitted together and solved
+// as one pack (pack.cu) in one slot: one set of launches for all of them,
+// each result independent of its pack-mates.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -45,6 +48,14 @@ struct Request {
   gs2_solve_info info{0, 0, GS2_OK, 0.0};
   gs2_status status = GS2_OK;
   std::vector<double> x;
+};
+
+// Small requests admitted together and solved as one pack in one slot.
+struct Group {
+  std::vector<Request*> members;  // in pack order
+  cudaStream_t stream = nullptr;
+  gs2_handle* h = nullptr;
+  PackJob* job = nullptr;
 };
 
 // Device bytes a request of this size holds once admitted: the matrix, its
@@ -90,6 +101,7 @@ struct gs2_server {
   std::condition_variable cv_loop;  // the progress thread, when idle
   std::deque<gs2::Request*> pending;
   std::vector<gs2::Request*> active;
+  std::vector<gs2::Group*> groups;  // packs on the GPU
   std::unordered_map<uint64_t, gs2::Request*> table;
   uint64_t next_ticket = 1;
   int64_t reserved = 0;
@@ -107,13 +119,20 @@ static bool admissible(gs2_server* s) {
   return s->reserved + s->pending.front()->footprint <= s->budget;
 }
 
-// Called with the lock held: release the request's reservation, record its
-// end and wake everybody who may be waiting on it or on free capacity.
-static void retire_locked(gs2_server* s, Request* r, bool ok) {
+static bool packable(const gs2_server* s, const Request* r) {
+  const bool amg = s->cfg.has_precond &&
+                   (s->cfg.precond.kind == GS2_PC_AMG || s->cfg.precond.kind == GS2_PC_AMG_JR);
+  return s->cfg.pack_rows > 0 && r->n <= s->cfg.pack_rows && !amg;
+}
+
+// Called with the lock held: release the request's reservation (and its
+// slot, unless it was one of a pack's), record its end and wake everybody
+// who may be waiting on it or on free capacity.
+static void retire_locked(gs2_server* s, Request* r, bool ok, bool frees_slot = true) {
   r->state = REQ_DONE;
   r->t_done = Clock::now();
   s->reserved -= r->footprint;
-  s->slots_used -= 1;
+  if (frees_slot) s->slots_used -= 1;
   if (ok) s->completed += 1;
   else s->failed += 1;
   s->cv_done.notify_all();
@@ -178,10 +197,110 @@ static void prepare(gs2_server* s, Request* r) {
   s->cv_loop.notify_one();
 }
 
+// Build one pack from the group's requests and start its job.  Each request
+// is validated on its own first, so a malformed one fails alone.
+static void prepare_group(gs2_server* s, Group* g) {
+  std::vector<std::pair<Request*, gs2_status>> failed;
+  std::vector<Request*> ok;
+  for (Request* r : g->members) {
+    gs2_status st = GS2_OK;
+    try {
+      if (s->cfg.fail_ticket && r->ticket == s->cfg.fail_ticket)
+        GS2_THROW(GS2_ERR_OOM, "injected allocation failure");
+      std::vector<double> d;
+      validate_csr(r->n, r->nnz, r->rp.data(), r->ci.data(), r->va.data(), &d);
+    } catch (const Error& e) {
+      st = e.st;
+    } catch (const std::bad_alloc&) {
+      st = GS2_ERR_OOM;
+    }
+    if (st == GS2_OK) ok.push_back(r);
+    else failed.push_back({r, st});
+  }
+  g->members = ok;
+  gs2_status st = GS2_OK;
+  if (!ok.empty()) {
+    try {
+      GS2_CUDA(cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking));
+      const int cnt = (int)ok.size();
+      std::vector<int64_t> n(cnt);
+      std::vector<const int64_t*> rp(cnt);
+      std::vector<const int32_t*> ci(cnt);
+      std::vector<const double*> va(cnt);
+      std::vector<double> b, x0;
+      for (int k = 0; k < cnt; ++k) {
+        Request* r = ok[k];
+        n[k] = r->n;
+        rp[k] = r->rp.data();
+        ci[k] = r->ci.data();
+        va[k] = r->va.data();
+        b.insert(b.end(), r->b.begin(), r->b.end());
+        if (r->x0.empty()) x0.insert(x0.end(), r->n, 0.0);
+        else x0.insert(x0.end(), r->x0.begin(), r->x0.end());
+      }
+      std::vector<int64_t> off, crp;
+      std::vector<int32_t> cci;
+      std::vector<double> cva;
+      pack_concat(cnt, n.data(), rp.data(), ci.data(), va.data(), off, crp, cci, cva);
+      unsigned prec = 0;
+      const gs2_params* pc = s->cfg.has_precond ? &s->cfg.precond : nullptr;
+      if (pc && pc->kind == GS2_PC_GS2) prec = 1u << pc->precision;
+      g->h = setup_handle(off.back(), (int64_t)cci.size(), crp.data(), cci.data(), cva.data(), 0,
+                          prec, g->stream, true);
+      pack_attach(g->h, off);
+      ensure_precond(g->h, pc);
+      g->h->graph_mode = 1;
+      if (!b.empty()) {
+        g->h->h2d(g->h->bstage, b.data(), sizeof(double) * b.size());
+        g->h->h2d(g->h->xstage, x0.data(), sizeof(double) * x0.size());
+      }
+      g->job = pack_job_start(g->h, g->h->bstage, g->h->xstage, s->cfg.restart, s->cfg.tol,
+                              s->cfg.max_iters, pc);
+      pack_job_prepare(g->job);
+      // the pageable staging copies above have been taken by the driver
+    } catch (const Error& e) {
+      st = e.st;
+    } catch (const std::bad_alloc&) {
+      st = GS2_ERR_OOM;
+    } catch (...) {
+      st = GS2_ERR_CUDA;
+    }
+  }
+  for (Request* r : g->members) {
+    std::vector<int64_t>().swap(r->rp);
+    std::vector<int32_t>().swap(r->ci);
+    std::vector<double>().swap(r->va);
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  for (auto& f : failed) {
+    f.first->status = f.second;
+    f.first->info.status = f.second;
+    retire_locked(s, f.first, false, false);
+  }
+  if (ok.empty() || st != GS2_OK) {
+    if (g->job) pack_job_free(g->job);
+    if (g->h) destroy_handle(g->h);
+    if (g->stream) cudaStreamDestroy(g->stream);
+    for (Request* r : g->members) {
+      r->status = st;
+      r->info.status = st;
+      retire_locked(s, r, false, false);
+    }
+    s->slots_used -= 1;
+    s->cv_prep.notify_all();
+    delete g;
+    return;
+  }
+  for (Request* r : g->members) r->state = REQ_ACTIVE;
+  s->groups.push_back(g);
+  s->cv_loop.notify_one();
+}
+
 static void prep_thread(gs2_server* s) {
   cudaSetDevice(s->device);
   for (;;) {
     Request* r = nullptr;
+    Group* g = nullptr;
     {
       std::unique_lock<std::mutex> lk(s->mu);
       s->cv_prep.wait(lk, [&] { return s->stopping || admissible(s); });
@@ -193,8 +312,24 @@ static void prep_thread(gs2_server* s) {
       s->slots_used += 1;
       s->admitted += 1;
       s->max_active = std::max(s->max_active, s->slots_used);
+      if (packable(s, r)) {
+        // the small requests behind it join its pack while they fit
+        g = new Group();
+        g->members.push_back(r);
+        const int cap = s->cfg.pack_max > 0 ? s->cfg.pack_max : 64;
+        while ((int)g->members.size() < cap && !s->pending.empty()) {
+          Request* q = s->pending.front();
+          if (!packable(s, q) || s->reserved + q->footprint > s->budget) break;
+          s->pending.pop_front();
+          q->state = REQ_PREPARING;
+          s->reserved += q->footprint;
+          s->admitted += 1;
+          g->members.push_back(q);
+        }
+      }
     }
-    prepare(s, r);
+    if (g) prepare_group(s, g);
+    else prepare(s, r);
   }
 }
 
@@ -222,20 +357,81 @@ static void finish(gs2_server* s, Request* r, gs2_status err) {
   retire_locked(s, r, ok && r->status == GS2_OK);
 }
 
+// Copy a finished pack's solutions back and retire its requests (one slot).
+static void finish_group(gs2_server* s, Group* g, gs2_status err) {
+  std::vector<double> xall;
+  if (err == GS2_OK) {
+    xall.resize(g->h->n);
+    if (g->h->n &&
+        cudaMemcpyAsync(xall.data(), g->h->xstage, sizeof(double) * g->h->n,
+                        cudaMemcpyDeviceToHost, g->stream) != cudaSuccess) {
+      cudaGetLastError();
+      err = GS2_ERR_CUDA;
+    }
+    cudaStreamSynchronize(g->stream);
+  }
+  int64_t o = 0;
+  for (size_t k = 0; k < g->members.size(); ++k) {
+    Request* r = g->members[k];
+    if (err == GS2_OK) {
+      r->info = pack_job_info(g->job, (int)k);
+      r->status = (gs2_status)r->info.status;
+      r->x.assign(xall.begin() + o, xall.begin() + o + r->n);
+    } else {
+      r->status = err;
+      r->info.status = err;
+    }
+    o += r->n;
+  }
+  pack_job_free(g->job);
+  destroy_handle(g->h);
+  cudaStreamDestroy(g->stream);
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->groups.erase(std::find(s->groups.begin(), s->groups.end(), g));
+  for (Request* r : g->members) retire_locked(s, r, err == GS2_OK && r->status == GS2_OK, false);
+  s->slots_used -= 1;
+  s->cv_prep.notify_all();
+  delete g;
+}
+
 static void progress_thread(gs2_server* s) {
   cudaSetDevice(s->device);
   std::vector<Request*> snap;
+  std::vector<Group*> gsnap;
   for (;;) {
     {
       std::unique_lock<std::mutex> lk(s->mu);
-      if (s->active.empty()) {
+      if (s->active.empty() && s->groups.empty()) {
         if (s->stopping && s->slots_used == 0) return;
         s->cv_loop.wait_for(lk, std::chrono::milliseconds(2));
         continue;
       }
       snap = s->active;
+      gsnap = s->groups;
     }
     bool progressed = false;
+    for (Group* g : gsnap) {
+      const cudaError_t q = cudaStreamQuery(g->stream);
+      if (q == cudaErrorNotReady) continue;
+      progressed = true;
+      if (q != cudaSuccess) {
+        cudaGetLastError();
+        finish_group(s, g, GS2_ERR_CUDA);
+        continue;
+      }
+      gs2_status err = GS2_OK;
+      bool done = false;
+      try {
+        done = pack_job_advance(g->job);
+      } catch (const Error& e) {
+        err = e.st;
+        done = true;
+      } catch (...) {
+        err = GS2_ERR_CUDA;
+        done = true;
+      }
+      if (done) finish_group(s, g, err);
+    }
     for (Request* r : snap) {
       const cudaError_t q = cudaStreamQuery(r->stream);
       if (q == cudaErrorNotReady) continue;
@@ -285,7 +481,8 @@ gs2_status gs2_server_create(const gs2_server_cfg* cfg, gs2_server** out) {
   if (!cfg || !out) return GS2_ERR_INVALID_ARG;
   *out = nullptr;
   if (cfg->max_slots < 1 || cfg->restart < 1 || cfg->restart > kMaxRestart ||
-      !(cfg->tol >= 0.0) || cfg->max_iters < 0 || cfg->hbm_budget_bytes < 0) {
+      !(cfg->tol >= 0.0) || cfg->max_iters < 0 || cfg->hbm_budget_bytes < 0 ||
+      cfg->pack_rows < 0 || cfg->pack_max < 0) {
     set_error("bad server configuration");
     return GS2_ERR_INVALID_ARG;
   }

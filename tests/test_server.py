@@ -141,3 +141,67 @@ def test_poll_busy_unknown_and_invalid_requests(lib):
     info, _, _ = srv.wait(tb, 2)
     assert info.status == 2
     srv.close()
+
+
+def _pack_of_one(pr, pc):
+    import torch
+    pk = gs2.pack_setup([pr.A])
+    x = torch.zeros(pr.n, dtype=torch.float64, device="cuda")
+    info = gs2.pack_gmres(pk, torch.from_numpy(pr.b).cuda(), x, 30, 1e-8, 4000, pc)[0]
+    torch.cuda.synchronize()
+    out = x.cpu().numpy()
+    pk.close()
+    return info, out
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_packed_requests_are_independent_of_their_pack_mates(lib, prec):
+    """Requests up to pack_rows rows are admitted together and solved as one
+    pack; each result is bitwise that of the request solved as a pack of
+    one, agrees with gmres_solve alone (iterations +-1, x to 1e-6), and the
+    larger requests still run alone, bitwise as gmres_solve."""
+    pc = gs2.params("gs2", 1, 1, direction="symmetric", precision=prec)
+    probs = _mix()
+    limit = 5000
+    srv = gs2.Server(restart=30, tol=1e-8, max_iters=4000, precond=pc, max_slots=2,
+                     prep_threads=2, pack_rows=limit, pack_max=4)
+    tickets = [srv.submit(p.A, p.b) for p in probs]
+    got = [srv.wait(t, p.n) for t, p in zip(tickets, probs)]
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(probs) and st["failed"] == 0 and st["max_active"] <= 2
+    assert st["reserved_bytes"] == 0
+    packed = [p.n <= limit for p in probs]
+    assert 2 <= sum(packed) < len(probs)
+    for p, small, (info, x, lat) in zip(probs, packed, got):
+        assert info.status == 0 and info.true_relres <= 1e-8 and lat > 0.0
+        ainfo, ax = _alone(p, pc)
+        if small:
+            oinfo, ox = _pack_of_one(p, pc)
+            assert info.iters == oinfo.iters and np.array_equal(x, ox), p.name
+            assert abs(info.iters - ainfo.iters) <= 1
+            assert np.linalg.norm(x - ax) <= 1e-6 * np.linalg.norm(ax)
+        else:
+            assert info.iters == ainfo.iters and np.array_equal(x, ax), p.name
+
+
+@pytest.mark.gpu
+def test_a_bad_request_in_a_pack_fails_alone(lib):
+    """Inside one pack: an injected allocation failure and a zero diagonal
+    are reported for their own requests; the others converge."""
+    good = [P.poisson2d(20), P.poisson2d(21), P.poisson2d(22)]
+    bad = P.dense_to_csr(np.array([[1.0, 2.0], [3.0, 0.0]]))
+    srv = gs2.Server(precond=gs2.params("gs2", 1, 1), max_slots=1, pack_rows=10_000,
+                     fail_ticket=1)
+    mats = [(good[0].A, good[0].b), (bad, np.ones(2)), (good[1].A, good[1].b),
+            (good[2].A, good[2].b)]
+    tickets = [srv.submit(A, b) for A, b in mats]
+    out = [srv.wait(t, len(b)) for t, (A, b) in zip(tickets, mats)]
+    st = srv.stats()
+    srv.close()
+    assert [o[0].status for o in out] == [3, 2, 0, 0]
+    assert st["failed"] == 2 and st["completed"] == 2 and st["reserved_bytes"] == 0
+    for (info, x, _), p in zip(out[2:], good[1:]):
+        r = np.linalg.norm(p.b - P.csr_matvec(p.A, x)) / np.linalg.norm(p.b)
+        assert r <= 1e-8
