@@ -20,13 +20,14 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
-_SRCS = [_SRC, os.path.join(_HERE, "amg.c")]
+_SRCS = [_SRC, os.path.join(_HERE, "amg.c"), os.path.join(_HERE, "hybrid.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
 FORWARD, BACKWARD, SYMMETRIC = 0, 1, 2
 PC_NONE, PC_GS2, PC_JR, PC_GS, PC_MTGS = 0, 1, 2, 3, 4
+PC_HYBRID_GS2, PC_HYBRID_JR = 7, 8
 
 
 class OracleError(RuntimeError):
@@ -98,12 +99,15 @@ def _load():
             lib.ora_cg_amg.argtypes = csr + [P, P, D, I32, P, I32, I32, I32, D, D, I32,
                                              ctypes.POINTER(_Info)]
             lib.ora_mtgs.argtypes = csr + [P, P, I32, D, I32]
+            lib.ora_hybrid.argtypes = csr + [P, P, I32, I32, I32, I32, I32, D, D, I32]
+            lib.ora_set_hybrid.argtypes = [I32, I32]
+            lib.ora_set_hybrid.restype = None
             for f in ("ora_diag", "ora_gs2", "ora_gs", "ora_jr", "ora_levels",
                       "ora_precond", "ora_gmres", "ora_cg", "ora_gs2_compact",
                       "ora_coloring", "ora_mtgs", "ora_amg_levels", "ora_amg_level",
                       "ora_amg_get_matrix", "ora_amg_get_prolongator",
                       "ora_amg_get_aggregates", "ora_amg_vcycle", "ora_gmres_amg",
-                      "ora_cg_amg"):
+                      "ora_cg_amg", "ora_hybrid"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -214,12 +218,14 @@ def precond(A, v, kind=PC_GS2, outer=1, inner=1, omega=1.0, gamma=1.0,
 
 def gmres(A, b, x0=None, restart=30, tol=1e-8, max_iters=10000, pc_kind=PC_GS2,
           pc_outer=1, pc_inner=1, pc_omega=1.0, pc_gamma=1.0,
-          pc_direction=FORWARD, history=False):
+          pc_direction=FORWARD, history=False, pc_parts=1, pc_local=1):
     """Restarted right-preconditioned GMRES with CGS2.
 
     Returns (x, SolveInfo[, history]).  A non-converged solve is returned with
-    its status rather than raised, so tests can check the status.
+    its status rather than raised, so tests can check the status.  The
+    hybrid kinds use pc_parts blocks and pc_local local sweeps.
     """
+    _load().ora_set_hybrid(pc_parts, pc_local)
     n, rp, ci, va = _csr(A)
     b = _vec(b, n)
     x = np.zeros(n) if x0 is None else _vec(x0, n)
@@ -238,8 +244,10 @@ def gmres(A, b, x0=None, restart=30, tol=1e-8, max_iters=10000, pc_kind=PC_GS2,
 
 
 def cg(A, b, x0=None, tol=1e-8, max_iters=10000, pc_kind=PC_GS2, pc_outer=1,
-       pc_inner=1, pc_omega=1.0, pc_gamma=1.0, pc_direction=SYMMETRIC):
+       pc_inner=1, pc_omega=1.0, pc_gamma=1.0, pc_direction=SYMMETRIC, pc_parts=1,
+       pc_local=1):
     """Preconditioned CG; returns (x, SolveInfo)."""
+    _load().ora_set_hybrid(pc_parts, pc_local)
     n, rp, ci, va = _csr(A)
     b = _vec(b, n)
     x = np.zeros(n) if x0 is None else _vec(x0, n)
@@ -250,6 +258,18 @@ def cg(A, b, x0=None, tol=1e-8, max_iters=10000, pc_kind=PC_GS2, pc_outer=1,
     if st == 1:
         raise OracleError("ora_cg: invalid argument")
     return x, SolveInfo(info.iters, info.cycles, info.status, info.true_relres)
+
+
+def hybrid(A, b, x, kind=PC_GS2, parts=1, outer=1, local=1, inner=1, omega=1.0, gamma=1.0,
+           direction=FORWARD):
+    """Hybrid (block-Jacobi) relaxation over `parts` contiguous row blocks:
+    `outer` exchanges, `local` local sweeps each (kind PC_GS2, PC_JR or
+    PC_GS); returns the new x."""
+    n, rp, ci, va = _csr(A)
+    b, x = _vec(b, n), _vec(x, n)
+    _check(_load().ora_hybrid(n, _p(rp), _p(ci), _p(va), _p(b), _p(x), kind, parts, outer,
+                              local, inner, omega, gamma, direction), "ora_hybrid")
+    return x
 
 
 def gs2_compact(A, b, x, outer=1, inner=1, direction=FORWARD):

@@ -26,7 +26,8 @@ extern "C" {
 
 enum { ORA_FORWARD = 0, ORA_BACKWARD = 1, ORA_SYMMETRIC = 2 };
 enum { ORA_PC_NONE = 0, ORA_PC_GS2 = 1, ORA_PC_JR = 2, ORA_PC_GS = 3,
-       ORA_PC_MTGS = 4, ORA_PC_AMG = 5, ORA_PC_AMG_JR = 6 };
+       ORA_PC_MTGS = 4, ORA_PC_AMG = 5, ORA_PC_AMG_JR = 6, ORA_PC_HYBRID_GS2 = 7,
+       ORA_PC_HYBRID_JR = 8 };
 
 typedef struct {
   int iters;          /* total Arnoldi steps over all cycles */
@@ -88,7 +89,9 @@ int ora_mtgs(int64_t n, const int64_t* rp, const int32_t* ci, const double* va,
  * kind: ORA_PC_NONE (z = v), ORA_PC_GS2, ORA_PC_JR (outer = sweeps),
  * ORA_PC_GS (exact GS, outer = sweeps), ORA_PC_MTGS (multicolour GS,
  * outer = sweeps), ORA_PC_AMG / ORA_PC_AMG_JR (one V-cycle of the hierarchy
- * ora_gmres_amg installs, GS2 / JR smoother with these parameters). */
+ * ora_gmres_amg installs, GS2 / JR smoother with these parameters),
+ * ORA_PC_HYBRID_GS2 / ORA_PC_HYBRID_JR (ora_hybrid with the partition and
+ * local sweeps set by ora_set_hybrid; outer = n_t). */
 int ora_precond(int64_t n, const int64_t* rp, const int32_t* ci,
                 const double* va, const double* v, double* z, int kind,
                 int outer, int inner, double omega, double gamma, int dir);
@@ -119,6 +122,24 @@ int ora_cg(int64_t n, const int64_t* rp, const int32_t* ci, const double* va,
 int ora_gs2_compact(int64_t n, const int64_t* rp, const int32_t* ci,
                     const double* va, const double* b, double* x, int outer,
                     int inner, int dir);
+
+/* ------------------------------------------------------------------ */
+/* Hybrid (block-Jacobi) relaxation of Sec. 3 with the local sweeps of  */
+/* the two-stage listing (hybrid.c; the readings are stated there).     */
+/* ------------------------------------------------------------------ */
+
+/* Rows in `parts` contiguous blocks; per exchange (outer = n_t times)
+ * c = b - E x with E the couplings between blocks, then `local` = n_k local
+ * sweeps on A_loc x = c: kind ORA_PC_GS2 (half sweeps as ora_gs2 with the
+ * local triangles, `inner` = n_j, dir), ORA_PC_JR (x += omega D^{-1}
+ * (c - A_loc x)) or ORA_PC_GS (exact local SOR, dir).  x in place. */
+int ora_hybrid(int64_t n, const int64_t* rp, const int32_t* ci, const double* va,
+               const double* b, double* x, int kind, int parts, int outer, int local, int inner,
+               double omega, double gamma, int dir);
+/* partition and local sweeps of the hybrid preconditioner kinds */
+void ora_set_hybrid(int parts, int local);
+extern _Thread_local int ora_hybrid_parts;
+extern _Thread_local int ora_hybrid_local;
 
 /* ------------------------------------------------------------------ */
 /* Smoothed-aggregation AMG with GS2 (or JR) as the smoother of a       */

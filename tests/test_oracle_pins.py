@@ -653,3 +653,155 @@ def test_statuses():
     b[3] = np.nan
     _, info = oracle.gmres(pr.A, b, restart=10, tol=1e-8, max_iters=30)
     assert info.status == 7
+
+
+# ---------------------------------------------------------------------------
+# Hybrid (block-Jacobi) relaxation, Sec. 3 with the local sweeps of the
+# two-stage listing: dense block computations, and the special cases that
+# reduce it to the global methods
+# ---------------------------------------------------------------------------
+
+def _blocks(n, parts):
+    blk = np.empty(n, dtype=int)
+    for p in range(parts):
+        blk[p * n // parts:(p + 1) * n // parts] = p
+    return blk
+
+
+def _dense_hybrid(M, b, x, parts, outer, local, sweep):
+    """Dense reference: per exchange c = b - E x (E the couplings between
+    blocks), then `local` sweeps x <- sweep(A_loc, c, x)."""
+    n = len(b)
+    blk = _blocks(n, parts)
+    same = blk[:, None] == blk[None, :]
+    Aloc, E = np.where(same, M, 0.0), np.where(same, 0.0, M)
+    for _ in range(outer):
+        c = b - E @ x
+        for _ in range(local):
+            x = sweep(Aloc, c, x)
+    return x
+
+
+def test_hybrid_gs_is_block_jacobi_with_sor_blocks():
+    """Local exact GS = x + omega (D + omega L_loc)^{-1} (c - A_loc x) per
+    half sweep, with the other blocks' values frozen at the exchange."""
+    A = tiny_nonsym(9, seed=11)
+    M, _, _, _ = dense_parts(A)
+    b = np.linspace(-1.0, 2.0, 9)
+    x0 = np.linspace(0.5, -0.5, 9)
+    om = 0.8
+
+    def fwd(Al, c, x):
+        Dl, Ll = np.diag(np.diag(Al)), np.tril(Al, -1)
+        return x + om * np.linalg.solve(Dl + om * Ll, c - Al @ x)
+
+    def bwd(Al, c, x):
+        Dl, Ul = np.diag(np.diag(Al)), np.triu(Al, 1)
+        return x + om * np.linalg.solve(Dl + om * Ul, c - Al @ x)
+
+    for parts, outer, local in ((3, 1, 1), (3, 2, 3), (4, 1, 2)):
+        want = _dense_hybrid(M, b, x0.copy(), parts, outer, local, lambda Al, c, x: bwd(Al, c, fwd(Al, c, x)))
+        got = oracle.hybrid(A, b, x0, oracle.PC_GS, parts=parts, outer=outer, local=local,
+                            omega=om, direction=oracle.SYMMETRIC)
+        assert np.allclose(got, want, rtol=0, atol=1e-13), (parts, outer, local)
+
+
+def test_hybrid_gs2_is_block_neumann_with_local_triangles():
+    """Local GS2 half sweep: g0 = D^{-1} r, n_j damped JR sweeps with the
+    local triangle, x += omega g (dense, per exchange)."""
+    A = tiny_nonsym(10, seed=12)
+    M, _, _, _ = dense_parts(A)
+    b = np.linspace(1.0, -1.0, 10)
+    x0 = np.cos(np.arange(10.0))
+    om, ga, nj = 0.9, 0.7, 2
+
+    def half(Al, c, x, tri):
+        Dl = np.diag(np.diag(Al))
+        T = tri(Al, -1) if tri is np.tril else tri(Al, 1)
+        r = c - Al @ x
+        g = np.linalg.solve(Dl, r)
+        for _ in range(nj):
+            g = (1 - ga) * g + ga * np.linalg.solve(Dl, r - om * T @ g)
+        return x + om * g
+
+    want = _dense_hybrid(M, b, x0.copy(), 3, 2, 2,
+                         lambda Al, c, x: half(Al, c, half(Al, c, x, np.tril), np.triu))
+    got = oracle.hybrid(A, b, x0, oracle.PC_GS2, parts=3, outer=2, local=2, inner=nj, omega=om,
+                        gamma=ga, direction=oracle.SYMMETRIC)
+    assert np.allclose(got, want, rtol=0, atol=1e-13)
+
+
+def test_hybrid_reduces_to_the_global_methods():
+    pr = P.poisson2d(12)
+    x0 = P.uniform_pm1(3, pr.n)
+    # one block: the global sweeps, n_t * n_k of them
+    for kind, glob in ((oracle.PC_GS2, lambda x: oracle.gs2(pr.A, pr.b, x, outer=6, inner=2,
+                                                             omega=0.9, direction=2)),
+                       (oracle.PC_JR, lambda x: oracle.jr(pr.A, pr.b, x, sweeps=6, omega=0.9)),
+                       (oracle.PC_GS, lambda x: oracle.gs(pr.A, pr.b, x, sweeps=6, omega=0.9,
+                                                          direction=2))):
+        got = oracle.hybrid(pr.A, pr.b, x0, kind, parts=1, outer=2, local=3, inner=2, omega=0.9,
+                            direction=oracle.SYMMETRIC)
+        assert np.abs(got - glob(x0)).max() <= 1e-14 * np.abs(got).max(), kind
+    # one local sweep of JR per exchange is global JR, whatever the blocks
+    for parts in (2, 5, 144):
+        got = oracle.hybrid(pr.A, pr.b, x0, oracle.PC_JR, parts=parts, outer=4, local=1,
+                            omega=0.7)
+        want = oracle.jr(pr.A, pr.b, x0, sweeps=4, omega=0.7)
+        assert np.allclose(got, want, rtol=0, atol=1e-14)
+    # every row its own block: no local triangle, GS2 (and exact GS) is JR
+    for kind in (oracle.PC_GS2, oracle.PC_GS):
+        got = oracle.hybrid(pr.A, pr.b, x0, kind, parts=pr.n, outer=3, local=1, inner=2)
+        want = oracle.jr(pr.A, pr.b, x0, sweeps=3, omega=1.0)
+        assert np.allclose(got, want, rtol=0, atol=1e-14), kind
+
+
+def test_hybrid_on_uncoupled_blocks_is_global():
+    """Two uncoupled systems split exactly at their boundary: no couplings
+    between blocks, so the hybrid sweep is the global one."""
+    a, c = P.poisson2d(8), P.convdiff3d(4)
+    Ma, Mc = P.csr_to_dense(a.A), P.csr_to_dense(c.A)
+    M = np.zeros((a.n + c.n,) * 2)
+    M[:a.n, :a.n], M[a.n:, a.n:] = Ma, Mc
+    A = P.dense_to_csr(M)
+    assert a.n == c.n  # 64 + 64 rows: two equal blocks
+    b = np.concatenate([a.b, c.b])
+    got = oracle.hybrid(A, b, np.zeros(len(b)), oracle.PC_GS2, parts=2, outer=2, local=1,
+                        inner=3, direction=oracle.SYMMETRIC)
+    want = oracle.gs2(A, b, np.zeros(len(b)), outer=2, inner=3, direction=oracle.SYMMETRIC)
+    assert np.array_equal(got, want)
+
+
+def test_hybrid_gs2_reaches_local_exact_gs_at_the_local_depth():
+    """D_loc^{-1} L_loc is nilpotent: n_j at least the depth of the local
+    triangles gives the local exact GS (the nilpotency limit of Sec. 4,
+    block by block)."""
+    pr = P.poisson2d(10)
+    parts = 4
+    depth = max(oracle.levels(P.dense_to_csr(np.where(
+        _blocks(pr.n, parts)[:, None] == _blocks(pr.n, parts)[None, :],
+        P.csr_to_dense(pr.A), 0.0)))[1], 1)
+    x0 = P.uniform_pm1(9, pr.n)
+    got = oracle.hybrid(pr.A, pr.b, x0, oracle.PC_GS2, parts=parts, outer=2, local=2,
+                        inner=depth, direction=oracle.SYMMETRIC)
+    want = oracle.hybrid(pr.A, pr.b, x0, oracle.PC_GS, parts=parts, outer=2, local=2,
+                         direction=oracle.SYMMETRIC)
+    assert np.allclose(got, want, rtol=0, atol=1e-13)
+    less = oracle.hybrid(pr.A, pr.b, x0, oracle.PC_GS2, parts=parts, outer=2, local=2,
+                         inner=depth - 3, direction=oracle.SYMMETRIC)
+    assert np.abs(less - want).max() > 1e-8
+
+
+def test_local_jr_iterations_grow_with_the_blocks_global_stay():
+    """Sec. 8 strong scaling: GMRES with the global JR(4,1) takes the same
+    iterations on any number of blocks; with the local JR(1,4) the count
+    grows with the number of blocks."""
+    pr = P.poisson2d(32)
+    glob, loc = [], []
+    for parts in (1, 4, 16):
+        glob.append(oracle.gmres(pr.A, pr.b, restart=30, tol=1e-8, pc_kind=oracle.PC_HYBRID_JR,
+                                 pc_outer=4, pc_parts=parts, pc_local=1)[1].iters)
+        loc.append(oracle.gmres(pr.A, pr.b, restart=30, tol=1e-8, pc_kind=oracle.PC_HYBRID_JR,
+                                pc_outer=1, pc_parts=parts, pc_local=4)[1].iters)
+    assert glob[0] == glob[1] == glob[2]
+    assert loc[0] == glob[0] and loc[0] < loc[1] < loc[2]
