@@ -96,6 +96,17 @@ typedef struct {
   int direction; /* gs2_direction */
   int precision; /* gs2_precision */
   int form;      /* gs2_form */
+  int parts;     /* hybrid (block-Jacobi) form of Sec. 3 for kinds GS2 and
+                    JR: the rows in `parts` contiguous blocks (block p holds
+                    rows [p n / P, (p+1) n / P), more blocks than rows count
+                    as n); each of the `outer` sweeps (n_t) freezes the other
+                    blocks' values, c = b - E x with E the couplings between
+                    blocks, then runs `local_sweeps` (n_k) local sweeps on
+                    A_loc x = c, GS2 with the local triangles (n_j = inner)
+                    or JR.  It is the preconditioner a 1-D row-block
+                    distribution over `parts` processes applies, run here on
+                    one GPU.  0 or 1 = the global method. Non-compact only. */
+  int local_sweeps; /* n_k >= 1 (0 = 1) */
 } gs2_params;
 
 typedef struct {

@@ -56,7 +56,7 @@ class Params(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("outer", ctypes.c_int), ("inner", ctypes.c_int),
                 ("omega", ctypes.c_double), ("gamma", ctypes.c_double),
                 ("direction", ctypes.c_int), ("precision", ctypes.c_int),
-                ("form", ctypes.c_int)]
+                ("form", ctypes.c_int), ("parts", ctypes.c_int), ("local_sweeps", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -213,13 +213,15 @@ def _ptr(a, writable=False):
 
 
 def params(kind="gs2", outer=1, inner=1, omega=1.0, gamma=1.0, direction="forward",
-           precision="fp64", form="noncompact") -> Params:
-    """gs2_params in the paper's notation: GS2(n_t = outer, n_j = inner)."""
+           precision="fp64", form="noncompact", parts=1, local=1) -> Params:
+    """gs2_params in the paper's notation: GS2(n_t = outer, n_k = local,
+    n_j = inner); parts > 1 is the hybrid (block-Jacobi) form over that many
+    row blocks."""
     k = _KIND[kind] if isinstance(kind, str) else int(kind)
     d = _DIR[direction] if isinstance(direction, str) else int(direction)
     p = _PREC[precision] if isinstance(precision, str) else int(precision)
     f = {"noncompact": NONCOMPACT, "compact": COMPACT}[form] if isinstance(form, str) else int(form)
-    return Params(k, outer, inner, omega, gamma, d, p, f)
+    return Params(k, outer, inner, omega, gamma, d, p, f, parts, local)
 
 
 class Handle:

@@ -377,6 +377,8 @@ static void prepare_lowprec(gs2_handle* h, DevCsr& M, const HostTri& T, int prec
 struct gs2_host_side {
   gs2::HostTri L, U;
   std::vector<int> Arp;  // rowptr of A (re-tiling)
+  // local triangles of each hybrid form (low-precision copies), by parts
+  std::map<int, std::pair<gs2::HostTri, gs2::HostTri>> hyb;
 };
 static std::mutex g_host_mu;
 static std::unordered_map<const gs2_handle*, gs2_host_side*> g_host;
@@ -545,8 +547,85 @@ void ensure_colors(gs2_handle* h) {
   h->colors_ready = true;
 }
 
+Hybrid* find_hybrid(gs2_handle* h, int parts) {
+  for (Hybrid* y : h->hybrids)
+    if (y->parts == parts) return y;
+  return nullptr;
+}
+
+// Build the hybrid form with P = min(parts, n) blocks: A's entries split by
+// whether the column lies in the row's block (A is read back from the
+// device once), the prescaled triangles filtered the same way.
+Hybrid* ensure_hybrid(gs2_handle* h, const gs2_params* p) {
+  if (!p || p->parts <= 1 || h->n == 0) return nullptr;
+  const int n = (int)h->n;
+  const int P = (int)std::min<int64_t>(p->parts, n);
+  gs2_host_side* hs = host_side(h);
+  Hybrid* y = find_hybrid(h, P);
+  if (!y) {
+    std::vector<int> blk(n);
+    for (int q = 0; q < P; ++q)
+      for (int64_t i = (int64_t)q * n / P; i < (int64_t)(q + 1) * n / P; ++i) blk[i] = q;
+    std::vector<int> rp(n + 1), ci(h->A.nnz);
+    std::vector<double> va(h->A.nnz);
+    GS2_CUDA(cudaStreamSynchronize(h->stream));
+    GS2_CUDA(cudaMemcpy(rp.data(), h->A.rp, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost));
+    if (h->A.nnz) {
+      GS2_CUDA(cudaMemcpy(ci.data(), h->A.ci, sizeof(int) * h->A.nnz, cudaMemcpyDeviceToHost));
+      GS2_CUDA(cudaMemcpy(va.data(), h->A.va, sizeof(double) * h->A.nnz,
+                          cudaMemcpyDeviceToHost));
+    }
+    std::vector<int> lrp(n + 1, 0), erp(n + 1, 0), lci, eci;
+    std::vector<double> lva, eva;
+    for (int i = 0; i < n; ++i) {
+      for (int k = rp[i]; k < rp[i + 1]; ++k) {
+        if (blk[ci[k]] == blk[i]) {
+          lci.push_back(ci[k]);
+          lva.push_back(va[k]);
+        } else {
+          eci.push_back(ci[k]);
+          eva.push_back(va[k]);
+        }
+      }
+      lrp[i + 1] = (int)lci.size();
+      erp[i + 1] = (int)eci.size();
+    }
+    auto local_tri = [&](const HostTri& T) {
+      HostTri o;
+      o.rp.assign(n + 1, 0);
+      for (int i = 0; i < n; ++i) {
+        for (int k = T.rp[i]; k < T.rp[i + 1]; ++k)
+          if (blk[T.ci[k]] == blk[i]) {
+            o.ci.push_back(T.ci[k]);
+            o.va.push_back(T.va[k]);
+          }
+        o.rp[i + 1] = (int)o.ci.size();
+      }
+      return o;
+    };
+    auto& tris = hs->hyb[P];
+    tris.first = local_tri(hs->L);
+    tris.second = local_tri(hs->U);
+    y = new Hybrid();
+    y->parts = P;
+    h->hybrids.push_back(y);
+    upload_matrix(h, y->Aloc, n, lrp, lci, lva);
+    upload_matrix(h, y->E, n, erp, eci, eva);
+    upload_matrix(h, y->Lloc, n, tris.first.rp, tris.first.ci, tris.first.va);
+    upload_matrix(h, y->Uloc, n, tris.second.rp, tris.second.ci, tris.second.va);
+    y->c = (double*)h->dalloc(sizeof(double) * n);
+  }
+  if (p->kind == GS2_PC_GS2 && p->precision != GS2_FP64) {
+    auto& tris = hs->hyb[P];
+    prepare_lowprec(h, y->Lloc, tris.first, p->precision);
+    prepare_lowprec(h, y->Uloc, tris.second, p->precision);
+  }
+  return y;
+}
+
 void ensure_precond(gs2_handle* h, const gs2_params* p) {
   if (!p) return;
+  ensure_hybrid(h, p);
   if (p->kind == GS2_PC_GS) ensure_levels(h);
   if (p->kind == GS2_PC_MTGS) ensure_colors(h);
   if (p->kind == GS2_PC_AMG || p->kind == GS2_PC_AMG_JR) amg_prepare(h, p);
@@ -667,6 +746,12 @@ static void check_params(const gs2_params* p) {
     GS2_THROW(GS2_ERR_INVALID_ARG, "form");
   if (p->form == GS2_COMPACT && (p->kind != GS2_PC_GS2 || p->omega != 1.0 || p->gamma != 1.0))
     GS2_THROW(GS2_ERR_INVALID_ARG, "the compact form is undamped GS2 (omega = gamma = 1)");
+  if (p->parts < 0 || p->local_sweeps < 0 || p->local_sweeps > 1000)
+    GS2_THROW(GS2_ERR_INVALID_ARG, "parts and local_sweeps must be >= 0");
+  if ((p->parts > 1 || p->local_sweeps > 1) && p->kind != GS2_PC_GS2 && p->kind != GS2_PC_JR)
+    GS2_THROW(GS2_ERR_INVALID_ARG, "the hybrid form and local sweeps are for GS2 and JR");
+  if (p->parts > 1 && p->form == GS2_COMPACT)
+    GS2_THROW(GS2_ERR_INVALID_ARG, "the hybrid form is non-compact");
 }
 
 }  // namespace gs2
@@ -701,6 +786,7 @@ void gs2::destroy_handle(gs2_handle* h) {
   if (h->gstream) cudaStreamSynchronize(h->gstream);
   if (h->amg) amg_free(h);
   if (h->pack) pack_free(h);
+  for (Hybrid* y : h->hybrids) delete y;
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->gstream) cudaStreamDestroy(h->gstream);
   if (h->gev_in) cudaEventDestroy(h->gev_in);
@@ -1194,6 +1280,9 @@ gs2_status gs2_pack_gmres(gs2_handle* h, const double* b, double* x, int restart
   check_params(precond);
   if (precond && (precond->kind == GS2_PC_AMG || precond->kind == GS2_PC_AMG_JR))
     GS2_THROW(GS2_ERR_INVALID_ARG, "a pack takes no AMG preconditioner");
+  if (precond && precond->parts > 1)
+    GS2_THROW(GS2_ERR_INVALID_ARG, "a pack takes no hybrid preconditioner (its blocks would "
+                                   "cut across the systems)");
   if (precond && precond->kind == GS2_PC_GS2) ensure_precision(h, precond->precision);
   ensure_precond(h, precond);
   Staged s(h, b, x, true);

@@ -106,6 +106,16 @@ struct Profiler;
 struct AmgHierarchy;
 struct Pack;
 
+// Hybrid (block-Jacobi) form of the relaxations (Sec. 3): the rows in
+// `parts` contiguous blocks (block p: rows [p n / P, (p+1) n / P)), A split
+// into the entries inside a row's block (Aloc) and the couplings to other
+// blocks (E), and the local parts of the prescaled triangles.
+struct Hybrid {
+  int parts = 0;
+  DevCsr Aloc, E, Lloc, Uloc;
+  double* c = nullptr;  // b - E x of the current exchange
+};
+
 }  // namespace gs2
 
 struct gs2_handle {
@@ -160,6 +170,9 @@ struct gs2_handle {
   // a pack of independent systems (gs2_pack_setup): the matrix is their
   // block-diagonal concatenation; null for a single system
   gs2::Pack* pack = nullptr;
+  // hybrid forms built so far, one per partition (ensure_precond)
+  std::vector<gs2::Hybrid*> hybrids;
+
   // per 32-row chunk of A's rows: 0 = the sliced-ELL kernels of A, L and U
   // skip the chunk (set by a pack's solve while some of its systems have
   // finished); null = every chunk
@@ -223,6 +236,11 @@ void launch_resid(gs2_handle* h, const double* b, const double* x,
                   double* r_out, double* rhat64, float* rhat32,
                   const int* skip);
 
+// The same with any matrix M over the handle's rows in place of A (the
+// hybrid form's local block and couplings).
+void launch_resid_matrix(gs2_handle* h, const DevCsr& M, const double* b, const double* x,
+                         double* r_out, double* rhat64, float* rhat32, const int* skip);
+
 // Elementwise r-hat = D^{-1} v (v FP64) in the sweep precision.
 void launch_prep_rhat(gs2_handle* h, const double* v, double* rhat64,
                       float* rhat32, const int* skip);
@@ -247,6 +265,8 @@ void launch_spmv(gs2_handle* h, const double* x, double* y, const int* skip);
 float time_tile_probe(gs2_handle* h, const DevCsr& M, int reps, int role);
 void launch_jr(gs2_handle* h, const double* b, const double* x_in,
                double* x_out, double omega, const int* skip);
+void launch_jr_matrix(gs2_handle* h, const DevCsr& M, const double* b, const double* x_in,
+                      double* x_out, double omega, const int* skip);
 void launch_level(gs2_handle* h, const DevCsr& T, const int* rows, int r0,
                   int r1, const double* rhat, double* g, double* x,
                   double omega, const int* skip);
@@ -291,6 +311,10 @@ void jr_relax(gs2_handle* h, const double* b, double* x, int sweeps,
 void mtgs_relax(gs2_handle* h, const double* b, double* x, int sweeps,
                 double omega, int direction);
 void ensure_levels(gs2_handle* h);
+// the hybrid form with p->parts blocks (built on first use, with the
+// low-precision triangles p->precision needs); null for parts <= 1
+Hybrid* ensure_hybrid(gs2_handle* h, const gs2_params* p);
+Hybrid* find_hybrid(gs2_handle* h, int parts);
 void ensure_colors(gs2_handle* h);
 // level sets or colours a preconditioner needs, built on first use
 void ensure_precond(gs2_handle* h, const gs2_params* p);

@@ -189,11 +189,16 @@ int blocks_per_sm(const void* fn, size_t smem) {
 
 void launch_resid(gs2_handle* h, const double* b, const double* x, double* r_out,
                   double* rhat64, float* rhat32, const int* skip) {
-  // algorithmic bytes: A once, x, b, D^{-1} read, r / rhat written
-  KernelTimer tm(h, "resid", bytes_csr(h->A, 8) + 24.0 * h->n + (r_out ? 8.0 * h->n : 0.0) +
+  launch_resid_matrix(h, h->A, b, x, r_out, rhat64, rhat32, skip);
+}
+
+void launch_resid_matrix(gs2_handle* h, const DevCsr& M, const double* b, const double* x,
+                         double* r_out, double* rhat64, float* rhat32, const int* skip) {
+  // algorithmic bytes: M once, x, b, D^{-1} read, r / rhat written
+  KernelTimer tm(h, "resid", bytes_csr(M, 8) + 24.0 * h->n + (r_out ? 8.0 * h->n : 0.0) +
                  (rhat64 ? 8.0 * h->n : 0.0) + (rhat32 ? 4.0 * h->n : 0.0));
   EpiResid e{x, b, h->dinv, r_out, rhat64, rhat32};
-  dispatch<double>(h, h->A, h->A.va, e, skip);
+  dispatch<double>(h, M, M.va, e, skip);
 }
 
 void launch_spmv(gs2_handle* h, const double* x, double* y, const int* skip) {
@@ -292,9 +297,14 @@ float time_tile_probe(gs2_handle* h, const DevCsr& M, int reps, int role) {
 
 void launch_jr(gs2_handle* h, const double* b, const double* x_in, double* x_out,
                double omega, const int* skip) {
-  KernelTimer tm(h, "jr", bytes_csr(h->A, 8) + 32.0 * h->n);
+  launch_jr_matrix(h, h->A, b, x_in, x_out, omega, skip);
+}
+
+void launch_jr_matrix(gs2_handle* h, const DevCsr& M, const double* b, const double* x_in,
+                      double* x_out, double omega, const int* skip) {
+  KernelTimer tm(h, "jr", bytes_csr(M, 8) + 32.0 * h->n);
   EpiJr e{x_in, b, h->dinv, x_out, omega};
-  dispatch<double>(h, h->A, h->A.va, e, skip);
+  dispatch<double>(h, M, M.va, e, skip);
 }
 
 void launch_inner(gs2_handle* h, const DevCsr& T, int prec, const void* rhat,

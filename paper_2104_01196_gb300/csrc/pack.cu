@@ -721,8 +721,8 @@ struct PackRun {
     if (pc) {
       const double pk[] = {(double)pc->kind, (double)pc->outer, (double)pc->inner, pc->omega,
                            pc->gamma, (double)pc->direction, (double)pc->precision,
-                           (double)pc->form};
-      key.insert(key.end(), pk, pk + 8);
+                           (double)pc->form, (double)pc->parts, (double)pc->local_sweeps};
+      key.insert(key.end(), pk, pk + 10);
     }
     if (!h->gstream) {
       GS2_CUDA(cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking));

@@ -85,12 +85,12 @@ static void inner_sweeps(gs2_handle* h, const DevCsr& T, int prec, const void* r
   }
 }
 
-static void resid_into(gs2_handle* h, int prec, const double* b, const double* x,
-                       const int* skip) {
+static void resid_into(gs2_handle* h, const DevCsr& R, int prec, const double* b,
+                       const double* x, const int* skip) {
   if (prec == GS2_FP64)
-    launch_resid(h, b, x, nullptr, h->rhat, nullptr, skip);
+    launch_resid_matrix(h, R, b, x, nullptr, h->rhat, nullptr, skip);
   else
-    launch_resid(h, b, x, nullptr, nullptr, h->rhat32, skip);
+    launch_resid_matrix(h, R, b, x, nullptr, nullptr, h->rhat32, skip);
 }
 
 static void compact_rhs_into(gs2_handle* h, int prec, const DevCsr& Tother, const double* b,
@@ -102,9 +102,11 @@ static void compact_rhs_into(gs2_handle* h, int prec, const DevCsr& Tother, cons
 }
 
 // One half sweep of GS2 on triangle T.  x_zero: x is known to be 0 and the
-// sweep-precision D^{-1} b is already in the rhat buffer.
+// sweep-precision D^{-1} b is already in the rhat buffer.  R: the matrix of
+// the residual (A; the local block in the hybrid form).
 static void gs2_half(gs2_handle* h, const gs2_params* p, const DevCsr& T, const DevCsr& Tother,
-                     const double* b, double* x, bool x_zero, const int* skip) {
+                     const double* b, double* x, bool x_zero, const int* skip,
+                     const DevCsr* R = nullptr) {
   const int prec = p->precision;
   void* rh = rhat_buf(h, prec);
   if (p->form == GS2_COMPACT) {
@@ -117,7 +119,7 @@ static void gs2_half(gs2_handle* h, const gs2_params* p, const DevCsr& T, const 
     return;
   }
   // non-compact: x += omega Mhat^{-1} (b - A x)
-  if (!x_zero) resid_into(h, prec, b, x, skip);
+  if (!x_zero) resid_into(h, R ? *R : h->A, prec, b, x, skip);
   const int mode = x_zero ? INNER_LAST_SET : INNER_LAST_ADD;
   if (p->inner == 0)
     launch_rhat_update(h, prec, rh, x, p->omega, !x_zero, skip);
@@ -125,8 +127,58 @@ static void gs2_half(gs2_handle* h, const gs2_params* p, const DevCsr& T, const 
     inner_sweeps(h, T, prec, rh, x, p->omega, p->gamma, p->inner, mode, skip);
 }
 
+// Sweeps of a GS2 / JR parameter set: n_t = outer exchanges of n_k local
+// sweeps each (one block: n_t n_k global sweeps)
+static int global_sweeps(const gs2_params* p) {
+  return p->outer * std::max(1, p->local_sweeps);
+}
+
+// ---------------------------------------------------------------------------
+// hybrid (block-Jacobi) form, Sec. 3: per exchange c = b - E x with the other
+// blocks' values frozen, then n_k local sweeps on A_loc x = c (GS2 half
+// sweeps with the local triangles, or JR).  x_zero: x = 0 and D^{-1} b is in
+// the rhat buffer of the sweep precision.
+// ---------------------------------------------------------------------------
+
+static void hybrid_apply(gs2_handle* h, const gs2_params* p, const Hybrid& Y, const double* b,
+                         double* x, bool x_zero, const int* skip) {
+  const int nk = std::max(1, p->local_sweeps);
+  bool zero = x_zero;
+  for (int t = 0; t < p->outer; ++t) {
+    const double* c = b;  // E x = 0 while x = 0
+    if (!zero) {
+      launch_resid_matrix(h, Y.E, b, x, Y.c, nullptr, nullptr, skip);
+      c = Y.c;
+    }
+    for (int k = 0; k < nk; ++k) {
+      if (p->kind == GS2_PC_JR) {
+        if (zero) {
+          launch_rhat_update(h, GS2_FP64, h->rhat, x, p->omega, false, skip);
+        } else {
+          launch_jr_matrix(h, Y.Aloc, c, x, h->t, p->omega, skip);
+          launch_copy_skip(h, x, h->t, skip);
+        }
+        zero = false;
+        continue;
+      }
+      if (p->direction == GS2_FORWARD || p->direction == GS2_SYMMETRIC) {
+        gs2_half(h, p, Y.Lloc, Y.Uloc, c, x, zero, skip, &Y.Aloc);
+        zero = false;
+      }
+      if (p->direction == GS2_BACKWARD || p->direction == GS2_SYMMETRIC) {
+        gs2_half(h, p, Y.Uloc, Y.Lloc, c, x, zero, skip, &Y.Aloc);
+        zero = false;
+      }
+    }
+  }
+}
+
 void gs2_relax(gs2_handle* h, const double* b, double* x, const gs2_params* p) {
-  for (int s = 0; s < p->outer; ++s) {
+  if (Hybrid* Y = p->parts > 1 ? ensure_hybrid(h, p) : nullptr) {
+    hybrid_apply(h, p, *Y, b, x, false, nullptr);
+    return;
+  }
+  for (int s = 0; s < global_sweeps(p); ++s) {
     if (p->direction == GS2_FORWARD || p->direction == GS2_SYMMETRIC)
       gs2_half(h, p, h->L, h->U, b, x, false, nullptr);
     if (p->direction == GS2_BACKWARD || p->direction == GS2_SYMMETRIC)
@@ -250,6 +302,18 @@ void precond_apply(gs2_handle* h, const gs2_params* p, const double* v, double* 
     launch_copy_skip(h, z, v, skip);
     return;
   }
+  if ((p->kind == GS2_PC_GS2 || p->kind == GS2_PC_JR) && p->parts > 1) {
+    const Hybrid* Y = find_hybrid(h, (int)std::min<int64_t>(p->parts, h->n));
+    if (!Y) GS2_THROW(GS2_ERR_INVALID_ARG, "hybrid form not prepared (ensure_precond)");
+    if (!rhat_ready) {
+      if (p->kind == GS2_PC_GS2 && p->precision != GS2_FP64)
+        launch_prep_rhat(h, v, nullptr, h->rhat32, skip);
+      else
+        launch_prep_rhat(h, v, h->rhat, nullptr, skip);
+    }
+    hybrid_apply(h, p, *Y, v, z, true, skip);
+    return;
+  }
   if (p->kind == GS2_PC_GS2) {
     const int prec = p->precision;
     if (!rhat_ready) {
@@ -259,7 +323,7 @@ void precond_apply(gs2_handle* h, const gs2_params* p, const double* v, double* 
         launch_prep_rhat(h, v, nullptr, h->rhat32, skip);
     }
     bool zero = true;
-    for (int s = 0; s < p->outer; ++s) {
+    for (int s = 0; s < global_sweeps(p); ++s) {
       if (p->direction == GS2_FORWARD || p->direction == GS2_SYMMETRIC) {
         gs2_half(h, p, h->L, h->U, v, z, zero, skip);
         zero = false;
@@ -276,7 +340,7 @@ void precond_apply(gs2_handle* h, const gs2_params* p, const double* v, double* 
     launch_rhat_update(h, GS2_FP64, h->rhat, z, p->omega, false, skip);
     const double* xin = z;
     double* xout = h->t;
-    for (int s = 1; s < p->outer; ++s) {
+    for (int s = 1; s < global_sweeps(p); ++s) {
       launch_jr(h, v, xin, xout, p->omega, skip);
       xin = xout;
       xout = (xout == h->t) ? z : h->t;

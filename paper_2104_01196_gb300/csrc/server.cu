@@ -76,6 +76,13 @@ static int64_t footprint(const gs2_server_cfg& c, int64_t n, int64_t nnz) {
     if (c.precond.precision == GS2_FP16_ROWSCALED) b += 2 * off + 8 * n + 12 * n;
   }
   if (c.has_precond && c.precond.kind == GS2_PC_GS) b += 8 * n;
+  // hybrid form: the local block of A, the couplings, the local triangles
+  // (with their low-precision copies) and the exchange vector
+  if (c.has_precond && c.precond.parts > 1) {
+    b += 12 * nnz + 12 * off + 4 * 4 * (n + 17) + 8 * n;
+    if (c.precond.precision == GS2_FP32) b += 4 * off;
+    if (c.precond.precision == GS2_FP16_ROWSCALED) b += 2 * off + 4 * n;
+  }
   // colour matrices: the off-diagonal entries again, row lists, row
   // pointers and tile descriptors, plus per-colour allocation slack
   if (c.has_precond && c.precond.kind == GS2_PC_MTGS)
@@ -122,7 +129,8 @@ static bool admissible(gs2_server* s) {
 static bool packable(const gs2_server* s, const Request* r) {
   const bool amg = s->cfg.has_precond &&
                    (s->cfg.precond.kind == GS2_PC_AMG || s->cfg.precond.kind == GS2_PC_AMG_JR);
-  return s->cfg.pack_rows > 0 && r->n <= s->cfg.pack_rows && !amg;
+  const bool hybrid = s->cfg.has_precond && s->cfg.precond.parts > 1;
+  return s->cfg.pack_rows > 0 && r->n <= s->cfg.pack_rows && !amg && !hybrid;
 }
 
 // Called with the lock held: release the request's reservation (and its
@@ -490,7 +498,9 @@ gs2_status gs2_server_create(const gs2_server_cfg* cfg, gs2_server** out) {
     const gs2_params& p = cfg->precond;
     if (p.kind < GS2_PC_NONE || p.kind > GS2_PC_AMG_JR || p.outer < 1 || p.inner < 0 ||
         !(p.omega > 0.0) || !(p.gamma > 0.0) || p.direction < 0 || p.direction > 2 ||
-        p.precision < 0 || p.precision > 2) {
+        p.precision < 0 || p.precision > 2 || p.parts < 0 || p.local_sweeps < 0 ||
+        ((p.parts > 1 || p.local_sweeps > 1) && p.kind != GS2_PC_GS2 && p.kind != GS2_PC_JR) ||
+        (p.parts > 1 && p.form == GS2_COMPACT)) {
       set_error("bad preconditioner parameters");
       return GS2_ERR_INVALID_ARG;
     }
