@@ -455,6 +455,7 @@ def run_ours(args):
 
     if rank == 0 and not args.no_extras and world == 1:
         out["comparisons"] = comparisons(gs2, torch, pr, stream, b)
+        out["hybrid"] = hybrid(gs2, torch, pr, stream, b)
     if rank == 0 and not args.no_serve and world == 1:
         out["serving"] = serving(gs2, torch, args.serve_requests)
     if rank == 0 and not args.no_extras and world == 1:
@@ -689,6 +690,38 @@ def serving(gs2, torch, count):
             "open_loop_rate_hz": 0.6 * rate,
             "open_loop_latency_ms": {"p50": float(np.percentile(olat, 50)),
                                      "p99": float(np.percentile(olat, 99))}}
+    return res
+
+
+def hybrid(gs2, torch, pr, stream, b):
+    """The hybrid (block-Jacobi) preconditioners of the paper's distributed
+    runs on the same workload, P row blocks standing in for P processes:
+    the global JR(4,1), the local JR(1,4) and hybrid SGS2(1,1); GMRES(30)
+    iterations and device time per solve for each P (one untimed solve
+    first, which also builds the blocks' matrices)."""
+    res = {"workload": "GMRES(30) to 1e-8 on the 128^3 Laplacian, P contiguous row blocks"}
+    h = gs2.gs2_setup(pr.A, stream=stream.cuda_stream)
+    with torch.cuda.stream(stream):
+        x = torch.zeros(pr.n, dtype=torch.float64, device="cuda")
+        for parts in (1, 8, 64, 512):
+            row = {}
+            for name, p in (("jr_4_1_global", gs2.params("jr", 4, parts=parts)),
+                            ("jr_1_4_local", gs2.params("jr", 1, parts=parts, local=4)),
+                            ("sgs2_1_1", gs2.params("gs2", 1, 1, direction="symmetric",
+                                                    parts=parts))):
+                x.zero_()
+                gs2.gmres_solve(h, b, x, 30, 1e-8, 5000, p)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                x.zero_()
+                e0.record(stream)
+                info = gs2.gmres_solve(h, b, x, 30, 1e-8, 5000, p)
+                e1.record(stream)
+                e1.synchronize()
+                row[name] = {"status": info.status, "iters": info.iters,
+                             "ms": round(e0.elapsed_time(e1), 2)}
+            res[f"P={parts}"] = row
+    h.close()
     return res
 
 
