@@ -696,7 +696,8 @@ def serving(gs2, torch, count):
 def hybrid(gs2, torch, pr, stream, b):
     """The hybrid (block-Jacobi) preconditioners of the paper's distributed
     runs on the same workload, P row blocks standing in for P processes:
-    the global JR(4,1), the local JR(1,4) and hybrid SGS2(1,1); GMRES(30)
+    the global JR(4,1), the local JR(1,4), hybrid SGS2(1,1) and hybrid exact
+    SGS (local triangular solves by level sets); GMRES(30)
     iterations and device time per solve for each P (one untimed solve
     first, which also builds the blocks' matrices)."""
     res = {"workload": "GMRES(30) to 1e-8 on the 128^3 Laplacian, P contiguous row blocks"}
@@ -708,7 +709,9 @@ def hybrid(gs2, torch, pr, stream, b):
             for name, p in (("jr_4_1_global", gs2.params("jr", 4, parts=parts)),
                             ("jr_1_4_local", gs2.params("jr", 1, parts=parts, local=4)),
                             ("sgs2_1_1", gs2.params("gs2", 1, 1, direction="symmetric",
-                                                    parts=parts))):
+                                                    parts=parts)),
+                            ("sgs_levels", gs2.params("gs", 1, direction="symmetric",
+                                                      parts=parts))):
                 x.zero_()
                 gs2.gmres_solve(h, b, x, 30, 1e-8, 5000, p)
                 e0 = torch.cuda.Event(enable_timing=True)

@@ -273,6 +273,13 @@ gs2_status gs2_amg_info(const gs2_handle* h, int* levels, int64_t* rows, int64_t
  * handle has none. */
 gs2_status gs2_amg_vcycle(gs2_handle* h, const double* b, double* x, const gs2_params* p);
 
+/* The relaxation of p's kind from x (in/out): GS2 (as gs2_apply_ex), JR,
+ * exact GS by level sets or multicolour GS, with `outer` sweeps; for GS2, JR
+ * and GS the hybrid (block-Jacobi) form when p->parts > 1, local exact GS
+ * solving each block's triangle by its own level sets.  Errors: INVALID_ARG
+ * for the other kinds and bad parameters, OOM, CUDA. */
+gs2_status relax_apply(gs2_handle* h, const double* b, double* x, const gs2_params* p);
+
 /* Damped JR baseline: x += omega D^{-1} (b - A x), `sweeps` times (Sec. 4,
  * zero-inner-sweep case). x in/out. */
 gs2_status jr_apply(gs2_handle* h, const double* b, double* x, int sweeps,

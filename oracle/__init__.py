@@ -27,7 +27,7 @@ _lib = None
 
 FORWARD, BACKWARD, SYMMETRIC = 0, 1, 2
 PC_NONE, PC_GS2, PC_JR, PC_GS, PC_MTGS = 0, 1, 2, 3, 4
-PC_HYBRID_GS2, PC_HYBRID_JR = 7, 8
+PC_HYBRID_GS2, PC_HYBRID_JR, PC_HYBRID_GS = 7, 8, 9
 
 
 class OracleError(RuntimeError):

@@ -288,7 +288,11 @@ int ora_precond(int64_t n, const int64_t* rp, const int32_t* ci,
       return ora_mtgs(n, rp, ci, va, v, z, outer, omega, dir);
     case ORA_PC_HYBRID_GS2:
     case ORA_PC_HYBRID_JR:
-      return ora_hybrid(n, rp, ci, va, v, z, kind == ORA_PC_HYBRID_GS2 ? ORA_PC_GS2 : ORA_PC_JR,
+    case ORA_PC_HYBRID_GS:
+      return ora_hybrid(n, rp, ci, va, v, z,
+                        kind == ORA_PC_HYBRID_GS2 ? ORA_PC_GS2
+                                                  : (kind == ORA_PC_HYBRID_JR ? ORA_PC_JR
+                                                                              : ORA_PC_GS),
                         ora_hybrid_parts, outer, ora_hybrid_local, inner, omega, gamma, dir);
     case ORA_PC_AMG:
     case ORA_PC_AMG_JR:

@@ -131,6 +131,7 @@ def load(path: str | None = None):
         "gs2_get_stats": [P, ctypes.POINTER(_Stats)],
         "gs2_apply": [P, P, P, I, I, D, I],
         "gs2_apply_ex": [P, P, P, ctypes.POINTER(Params)],
+        "relax_apply": [P, P, P, ctypes.POINTER(Params)],
         "gs_apply": [P, P, P, I, D, I],
         "mtgs_apply": [P, P, P, I, D, I],
         "jr_apply": [P, P, P, I, D],
@@ -413,6 +414,13 @@ def gs2_apply_ex(h, b, x, p: Params):
     px, _kx = _ptr(x, True)
     _check(load().gs2_apply_ex(h.ptr, pb, px, ctypes.byref(p)))
     return x
+
+
+def relax_apply(h, b, x, p: Params):
+    """The relaxation of p's kind (GS2, JR, GS, MTGS), global or hybrid, from x."""
+    pb, _kb = _ptr(b)
+    px, _kx = _ptr(x, True)
+    _check(load().relax_apply(h.ptr, pb, px, ctypes.byref(p)))
 
 
 def gs_apply(h, b, x, sweeps=1, omega=1.0, direction=FORWARD):

@@ -463,30 +463,34 @@ void ensure_precision(gs2_handle* h, int prec) {
 
 // Level sets of the triangles (level-set scheduling, Sec. 3): level(i) =
 // 1 + max level over row i's dependencies; rows are grouped by level.
+// Level sets of a strict triangle: level(i) = 1 + the largest level of the
+// rows row i depends on (0 without any); rows grouped by level on the device.
+static void build_levels(gs2_handle* h, const HostTri& T, bool lower, std::vector<int>& ptr,
+                         int*& rows_dev) {
+  const int n = (int)h->n;
+  std::vector<int> lev(n, 0);
+  int nlev = n ? 1 : 0;
+  for (int s = 0; s < n; ++s) {
+    const int i = lower ? s : n - 1 - s;
+    int lv = 0;
+    for (int k = T.rp[i]; k < T.rp[i + 1]; ++k) lv = std::max(lv, lev[T.ci[k]] + 1);
+    lev[i] = lv;
+    nlev = std::max(nlev, lv + 1);
+  }
+  ptr.assign(nlev + 1, 0);
+  for (int i = 0; i < n; ++i) ptr[lev[i] + 1]++;
+  for (int l = 0; l < nlev; ++l) ptr[l + 1] += ptr[l];
+  std::vector<int> fill(ptr.begin(), ptr.end() - 1), rows(std::max(n, 1));
+  for (int i = 0; i < n; ++i) rows[fill[lev[i]]++] = i;
+  rows_dev = (int*)h->dalloc(sizeof(int) * std::max(n, 1));
+  h->h2d(rows_dev, rows.data(), sizeof(int) * std::max(n, 1));
+}
+
 void ensure_levels(gs2_handle* h) {
   if (h->levels_ready) return;
   gs2_host_side* hs = host_side(h);
-  const int n = (int)h->n;
-  auto build = [&](const HostTri& T, bool lower, std::vector<int>& ptr, int*& rows_dev) {
-    std::vector<int> lev(n, 0);
-    int nlev = n ? 1 : 0;
-    for (int s = 0; s < n; ++s) {
-      const int i = lower ? s : n - 1 - s;
-      int lv = 0;
-      for (int k = T.rp[i]; k < T.rp[i + 1]; ++k) lv = std::max(lv, lev[T.ci[k]] + 1);
-      lev[i] = lv;
-      nlev = std::max(nlev, lv + 1);
-    }
-    ptr.assign(nlev + 1, 0);
-    for (int i = 0; i < n; ++i) ptr[lev[i] + 1]++;
-    for (int l = 0; l < nlev; ++l) ptr[l + 1] += ptr[l];
-    std::vector<int> fill(ptr.begin(), ptr.end() - 1), rows(std::max(n, 1));
-    for (int i = 0; i < n; ++i) rows[fill[lev[i]]++] = i;
-    rows_dev = (int*)h->dalloc(sizeof(int) * std::max(n, 1));
-    h->h2d(rows_dev, rows.data(), sizeof(int) * std::max(n, 1));
-  };
-  build(hs->L, true, h->lev_ptr_L, h->lev_rows_L);
-  build(hs->U, false, h->lev_ptr_U, h->lev_rows_U);
+  build_levels(h, hs->L, true, h->lev_ptr_L, h->lev_rows_L);
+  build_levels(h, hs->U, false, h->lev_ptr_U, h->lev_rows_U);
   h->levels_ready = true;
 }
 
@@ -620,6 +624,14 @@ Hybrid* ensure_hybrid(gs2_handle* h, const gs2_params* p) {
     prepare_lowprec(h, y->Lloc, tris.first, p->precision);
     prepare_lowprec(h, y->Uloc, tris.second, p->precision);
   }
+  if (p->kind == GS2_PC_GS && !y->levels_ready) {
+    // local exact GS: level sets of the local triangles (each block's own
+    // dependency chains side by side)
+    auto& tris = hs->hyb[P];
+    build_levels(h, tris.first, true, y->lev_ptr_L, y->lev_rows_L);
+    build_levels(h, tris.second, false, y->lev_ptr_U, y->lev_rows_U);
+    y->levels_ready = true;
+  }
   return y;
 }
 
@@ -748,8 +760,9 @@ static void check_params(const gs2_params* p) {
     GS2_THROW(GS2_ERR_INVALID_ARG, "the compact form is undamped GS2 (omega = gamma = 1)");
   if (p->parts < 0 || p->local_sweeps < 0 || p->local_sweeps > 1000)
     GS2_THROW(GS2_ERR_INVALID_ARG, "parts and local_sweeps must be >= 0");
-  if ((p->parts > 1 || p->local_sweeps > 1) && p->kind != GS2_PC_GS2 && p->kind != GS2_PC_JR)
-    GS2_THROW(GS2_ERR_INVALID_ARG, "the hybrid form and local sweeps are for GS2 and JR");
+  if ((p->parts > 1 || p->local_sweeps > 1) && p->kind != GS2_PC_GS2 && p->kind != GS2_PC_JR &&
+      p->kind != GS2_PC_GS)
+    GS2_THROW(GS2_ERR_INVALID_ARG, "the hybrid form and local sweeps are for GS2, JR and GS");
   if (p->parts > 1 && p->form == GS2_COMPACT)
     GS2_THROW(GS2_ERR_INVALID_ARG, "the hybrid form is non-compact");
 }
@@ -1078,6 +1091,26 @@ gs2_status gs2_apply(gs2_handle* h, const double* b, double* x, int outer_sweeps
   gs2_params p{GS2_PC_GS2, outer_sweeps, inner_sweeps, damping, 1.0, direction,
                GS2_FP64, GS2_NONCOMPACT};
   return gs2_apply_ex(h, b, x, &p);
+}
+
+gs2_status relax_apply(gs2_handle* h, const double* b, double* x, const gs2_params* p) {
+  if (!h || !p || (h->n && (!b || !x))) {
+    set_error("NULL argument");
+    return GS2_ERR_INVALID_ARG;
+  }
+  API_BEGIN
+  check_params(p);
+  if (p->kind != GS2_PC_GS2 && p->kind != GS2_PC_JR && p->kind != GS2_PC_GS &&
+      p->kind != GS2_PC_MTGS)
+    GS2_THROW(GS2_ERR_INVALID_ARG, "relax_apply takes kinds GS2, JR, GS and MTGS");
+  if (h->n == 0) return GS2_OK;
+  if (p->kind == GS2_PC_GS2) ensure_precision(h, p->precision);
+  ensure_precond(h, p);
+  Staged s(h, b, x, true);
+  gs2_relax(h, s.b, s.x, p);
+  s.finish();
+  return GS2_OK;
+  API_END
 }
 
 gs2_status gs_apply(gs2_handle* h, const double* b, double* x, int sweeps, double omega,

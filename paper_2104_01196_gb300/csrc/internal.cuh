@@ -114,6 +114,11 @@ struct Hybrid {
   int parts = 0;
   DevCsr Aloc, E, Lloc, Uloc;
   double* c = nullptr;  // b - E x of the current exchange
+  // level sets of the local triangles (local exact GS), built on first use
+  bool levels_ready = false;
+  std::vector<int> lev_ptr_L, lev_ptr_U;
+  int* lev_rows_L = nullptr;
+  int* lev_rows_U = nullptr;
 };
 
 }  // namespace gs2
@@ -303,6 +308,8 @@ void* precond_rhat_buffer(gs2_handle* h, const gs2_params* p);
 bool precond_wants_rhat(const gs2_params* p);
 
 // relaxations (relax.cu)
+// the relaxation of p's kind (GS2, JR, exact GS, multicolour GS), global or
+// in the hybrid form, from x
 void gs2_relax(gs2_handle* h, const double* b, double* x, const gs2_params* p);
 void gs_relax(gs2_handle* h, const double* b, double* x, int sweeps,
               double omega, int direction);

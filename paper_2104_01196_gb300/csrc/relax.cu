@@ -140,6 +140,10 @@ static int global_sweeps(const gs2_params* p) {
 // the rhat buffer of the sweep precision.
 // ---------------------------------------------------------------------------
 
+static void gs_half_levels(gs2_handle* h, const DevCsr& T, const std::vector<int>& ptr,
+                           const int* rows, const DevCsr& R, const double* b, double* x,
+                           double omega, bool x_zero, const int* skip);
+
 static void hybrid_apply(gs2_handle* h, const gs2_params* p, const Hybrid& Y, const double* b,
                          double* x, bool x_zero, const int* skip) {
   const int nk = std::max(1, p->local_sweeps);
@@ -161,6 +165,20 @@ static void hybrid_apply(gs2_handle* h, const gs2_params* p, const Hybrid& Y, co
         zero = false;
         continue;
       }
+      if (p->kind == GS2_PC_GS) {
+        // local exact GS / SOR: the local triangular solves by level sets
+        if (p->direction == GS2_FORWARD || p->direction == GS2_SYMMETRIC) {
+          gs_half_levels(h, Y.Lloc, Y.lev_ptr_L, Y.lev_rows_L, Y.Aloc, c, x, p->omega, zero,
+                         skip);
+          zero = false;
+        }
+        if (p->direction == GS2_BACKWARD || p->direction == GS2_SYMMETRIC) {
+          gs_half_levels(h, Y.Uloc, Y.lev_ptr_U, Y.lev_rows_U, Y.Aloc, c, x, p->omega, zero,
+                         skip);
+          zero = false;
+        }
+        continue;
+      }
       if (p->direction == GS2_FORWARD || p->direction == GS2_SYMMETRIC) {
         gs2_half(h, p, Y.Lloc, Y.Uloc, c, x, zero, skip, &Y.Aloc);
         zero = false;
@@ -178,6 +196,20 @@ void gs2_relax(gs2_handle* h, const double* b, double* x, const gs2_params* p) {
     hybrid_apply(h, p, *Y, b, x, false, nullptr);
     return;
   }
+  if (p->kind == GS2_PC_JR) {
+    jr_relax(h, b, x, global_sweeps(p), p->omega);
+    return;
+  }
+  if (p->kind == GS2_PC_GS) {
+    ensure_levels(h);
+    gs_relax(h, b, x, global_sweeps(p), p->omega, p->direction);
+    return;
+  }
+  if (p->kind == GS2_PC_MTGS) {
+    ensure_colors(h);
+    mtgs_relax(h, b, x, p->outer, p->omega, p->direction);
+    return;
+  }
   for (int s = 0; s < global_sweeps(p); ++s) {
     if (p->direction == GS2_FORWARD || p->direction == GS2_SYMMETRIC)
       gs2_half(h, p, h->L, h->U, b, x, false, nullptr);
@@ -191,19 +223,26 @@ void gs2_relax(gs2_handle* h, const double* b, double* x, const gs2_params* p) {
 // triangular solve by level sets (one launch per level)
 // ---------------------------------------------------------------------------
 
-static void gs_half(gs2_handle* h, bool lower, const double* b, double* x, double omega,
-                    bool x_zero, const int* skip) {
-  const DevCsr& T = lower ? h->L : h->U;
-  const std::vector<int>& ptr = lower ? h->lev_ptr_L : h->lev_ptr_U;
-  const int* rows = lower ? h->lev_rows_L : h->lev_rows_U;
+// One exact half sweep by level sets of T: r-hat = D^{-1} (b - R x) (R = A;
+// the local block in the hybrid form), then the triangular solve level by
+// level with the x update.  x_zero: x = 0 and D^{-1} b is in h->rhat.
+static void gs_half_levels(gs2_handle* h, const DevCsr& T, const std::vector<int>& ptr,
+                           const int* rows, const DevCsr& R, const double* b, double* x,
+                           double omega, bool x_zero, const int* skip) {
   if (x_zero) {
     launch_fill(h, x, 0.0, skip);
   } else {
-    launch_resid(h, b, x, nullptr, h->rhat, nullptr, skip);
+    launch_resid_matrix(h, R, b, x, nullptr, h->rhat, nullptr, skip);
   }
   KernelTimer tm(h, "levels", T.nnz * 12.0 + 4.0 * (h->n + 1) + 32.0 * h->n);
   for (size_t l = 0; l + 1 < ptr.size(); ++l)
     launch_level(h, T, rows, ptr[l], ptr[l + 1], h->rhat, h->g0, x, omega, skip);
+}
+
+static void gs_half(gs2_handle* h, bool lower, const double* b, double* x, double omega,
+                    bool x_zero, const int* skip) {
+  gs_half_levels(h, lower ? h->L : h->U, lower ? h->lev_ptr_L : h->lev_ptr_U,
+                 lower ? h->lev_rows_L : h->lev_rows_U, h->A, b, x, omega, x_zero, skip);
 }
 
 void gs_relax(gs2_handle* h, const double* b, double* x, int sweeps, double omega,
@@ -302,7 +341,7 @@ void precond_apply(gs2_handle* h, const gs2_params* p, const double* v, double* 
     launch_copy_skip(h, z, v, skip);
     return;
   }
-  if ((p->kind == GS2_PC_GS2 || p->kind == GS2_PC_JR) && p->parts > 1) {
+  if ((p->kind == GS2_PC_GS2 || p->kind == GS2_PC_JR || p->kind == GS2_PC_GS) && p->parts > 1) {
     const Hybrid* Y = find_hybrid(h, (int)std::min<int64_t>(p->parts, h->n));
     if (!Y) GS2_THROW(GS2_ERR_INVALID_ARG, "hybrid form not prepared (ensure_precond)");
     if (!rhat_ready) {
@@ -366,7 +405,7 @@ void precond_apply(gs2_handle* h, const gs2_params* p, const double* v, double* 
   // exact GS: the first half sweep from z = 0 solves with r = v
   if (!rhat_ready) launch_prep_rhat(h, v, h->rhat, nullptr, skip);
   bool zero = true;
-  for (int s = 0; s < p->outer; ++s) {
+  for (int s = 0; s < global_sweeps(p); ++s) {
     if (p->direction == GS2_FORWARD || p->direction == GS2_SYMMETRIC) {
       gs_half(h, true, v, z, p->omega, zero, skip);
       zero = false;

@@ -499,7 +499,8 @@ gs2_status gs2_server_create(const gs2_server_cfg* cfg, gs2_server** out) {
     if (p.kind < GS2_PC_NONE || p.kind > GS2_PC_AMG_JR || p.outer < 1 || p.inner < 0 ||
         !(p.omega > 0.0) || !(p.gamma > 0.0) || p.direction < 0 || p.direction > 2 ||
         p.precision < 0 || p.precision > 2 || p.parts < 0 || p.local_sweeps < 0 ||
-        ((p.parts > 1 || p.local_sweeps > 1) && p.kind != GS2_PC_GS2 && p.kind != GS2_PC_JR) ||
+        ((p.parts > 1 || p.local_sweeps > 1) && p.kind != GS2_PC_GS2 && p.kind != GS2_PC_JR &&
+         p.kind != GS2_PC_GS) ||
         (p.parts > 1 && p.form == GS2_COMPACT)) {
       set_error("bad preconditioner parameters");
       return GS2_ERR_INVALID_ARG;

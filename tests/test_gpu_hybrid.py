@@ -171,10 +171,53 @@ def test_hybrid_refusals(g):
     b, x = dev(pr.b), dev(np.zeros(pr.n))
     for bad in (g.params("gs2", 1, 1, form="compact", parts=4),
                 g.params("mtgs", 1, parts=4), g.params("amg", 1, 1, parts=4),
-                g.params("gs", 1, local=2), g.params("gs2", 1, 1, parts=-1)):
+                g.params("mtgs", 1, local=2), g.params("gs2", 1, 1, parts=-1)):
         with pytest.raises(g.GS2Error):
             g.gmres_solve(h, b, x, 30, 1e-8, 10, bad)
     pk = g.pack_setup([pr.A, pr.A])
     with pytest.raises(g.GS2Error):
         g.pack_gmres(pk, dev(np.concatenate([pr.b, pr.b])), dev(np.zeros(2 * pr.n)), 30, 1e-8,
                      10, g.params("gs2", 1, 1, parts=4))
+
+
+@pytest.mark.parametrize("name", list(PROBS))
+@pytest.mark.parametrize("parts", [1, 5, 40])
+def test_relax_apply_every_kind_global_and_hybrid(g, name, parts):
+    """relax_apply: JR, exact GS (the local triangles solved by their own
+    level sets in the hybrid form) and GS2 against the oracle; multicolour
+    GS (global only) against its oracle."""
+    pr = PROBS[name]
+    b = P.uniform_pm1(91, pr.n)
+    x0 = P.uniform_pm1(92, pr.n)
+    h = g.gs2_setup(pr.A)
+    cases = [("jr", oracle.PC_JR, dict(outer=2, omega=0.8, local=2)),
+             ("gs", oracle.PC_GS, dict(outer=2, omega=0.9, direction="symmetric", local=2)),
+             ("gs", oracle.PC_GS, dict(outer=1, direction="backward")),
+             ("gs2", oracle.PC_GS2, dict(outer=1, inner=3, direction="symmetric", local=2))]
+    for kind, okind, kw in cases:
+        x = dev(x0)
+        g.relax_apply(h, dev(b), x, g.params(kind, parts=parts, **kw))
+        want = oracle.hybrid(pr.A, b, x0, okind, parts=parts, outer=kw["outer"],
+                             local=kw.get("local", 1), inner=kw.get("inner", 1),
+                             omega=kw.get("omega", 1.0),
+                             direction=DIRS[kw.get("direction", "forward")])
+        assert rel(host(x), want) <= TOL, (kind, kw)
+    if parts == 1:
+        x = dev(x0)
+        g.relax_apply(h, dev(b), x, g.params("mtgs", 2, omega=0.9, direction="symmetric"))
+        want = oracle.mtgs(pr.A, b, x0, sweeps=2, omega=0.9, direction=oracle.SYMMETRIC)
+        assert rel(host(x), want) <= TOL
+
+
+@pytest.mark.parametrize("name", ["poisson2d_37", "convdiff3d_12"])
+def test_gmres_with_hybrid_exact_sgs_matches_oracle(g, name):
+    pr = PROBS[name]
+    h = g.gs2_setup(pr.A)
+    x = dev(np.zeros(pr.n))
+    info = g.gmres_solve(h, dev(pr.b), x, 30, 1e-8, 4000,
+                         g.params("gs", 1, direction="symmetric", parts=12))
+    _, oinfo = oracle.gmres(pr.A, pr.b, restart=30, tol=1e-8, max_iters=4000,
+                            pc_kind=oracle.PC_HYBRID_GS, pc_direction=oracle.SYMMETRIC,
+                            pc_parts=12)
+    assert info.status == 0 and oinfo.status == 0
+    assert abs(info.iters - oinfo.iters) <= 1, (info.iters, oinfo.iters)
