@@ -53,6 +53,9 @@ def parse():
                     help="requests of the served stream (bounded sample of 2000)")
     ap.add_argument("--no-profile", action="store_true",
                     help="do not time kernels with events inside the timed region")
+    ap.add_argument("--only-extras", default="",
+                    help="comma list: run only these extras (comparisons, hybrid, "
+                         "small_system, packs, workloads, serving)")
     return ap.parse_args()
 
 
@@ -453,15 +456,22 @@ def run_ours(args):
                       "note": "gmres_solve with pinned host b and x: H2D of b and x0, "
                               "solve, D2H of x inside each timed call"}
 
-    if rank == 0 and not args.no_extras and world == 1:
+    only = set(filter(None, args.only_extras.split(",")))
+
+    def want(name, off=False):
+        return rank == 0 and world == 1 and not off and (name in only if only else True)
+
+    if want("comparisons", args.no_extras):
         out["comparisons"] = comparisons(gs2, torch, pr, stream, b)
+    if want("hybrid", args.no_extras):
         out["hybrid"] = hybrid(gs2, torch, pr, stream, b)
-    if rank == 0 and not args.no_serve and world == 1:
+    if want("serving", args.no_serve):
         out["serving"] = serving(gs2, torch, args.serve_requests)
-    if rank == 0 and not args.no_extras and world == 1:
+    if want("small_system", args.no_extras):
         out["small_system"] = small_system(gs2, torch)
+    if want("packs", args.no_extras):
         out["packs"] = packs(gs2, torch)
-    if rank == 0 and not args.no_extras and not args.no_workloads and world == 1:
+    if want("workloads", args.no_extras or args.no_workloads):
         out["workloads"] = full_workloads(gs2, torch)
     if rank == 0 and world == 1 and not args.no_cpu:
         v, sample = oracle_sample(pr)
