@@ -48,6 +48,17 @@ struct Pack {
   int nchunks = 0;
   int* live_cycle = nullptr;
   int* live_run = nullptr;
+  // work lists of the systems taking the current cycle (written by the host
+  // before each cycle): their block-table entries and the systems, with the
+  // two counts in cnt[0], cnt[1]; grids of the kernels looping over them
+  std::vector<int> seg_blk_host;
+  int* items = nullptr;
+  int* sys = nullptr;
+  int* cnt = nullptr;
+  int* items_host = nullptr;
+  int* sys_host = nullptr;
+  int* cnt_host = nullptr;
+  int gb = 1, gs = 1;
   int m = 0;                       // restart the arrays below are sized for
   double *H = nullptr, *hbuf = nullptr, *gvec = nullptr, *cs = nullptr, *sn = nullptr,
          *y = nullptr, *part = nullptr;
@@ -62,136 +73,179 @@ struct Pack {
 
 // ---------------------------------------------------------------------------
 // kernels
+//
+// Work lists: the block-table entries (`items`, count at *nitems) and the
+// systems (`sys`, count at *nsys) of the systems taking the current cycle,
+// written by the host before each cycle.  Kernels run a fixed grid (captured
+// once) and loop over the list, so a cycle in which few systems remain costs
+// one short wave per kernel, not one block per entry of the table.  Whether
+// a block skips an item is uniform over the block; a block that loops runs
+// a barrier before it reuses shared memory.
 // ---------------------------------------------------------------------------
 
-// p = V[0..JC)^T w over the block's rows (a block of a stopped system writes
+// p = V[0..JC)^T w over an item's rows (an item of a stopped system writes
 // nothing: its partial sums are never read)
 template <int JC>
 __global__ void __launch_bounds__(kVecThreads)
-k_pdots(int ld, const int4* __restrict__ blk, const KrylovState* st,
-        const double* __restrict__ V, const double* __restrict__ w, double* part, int nb) {
-  const int4 b = blk[blockIdx.x];
-  if (st[b.x].stop) return;
-  double acc[JC];
+k_pdots(int ld, const int4* __restrict__ blk, const int* __restrict__ items,
+        const int* __restrict__ nitems, const KrylovState* st, const double* __restrict__ V,
+        const double* __restrict__ w, double* part, int nb) {
+  const int nq = *nitems;
+  for (int q = blockIdx.x; q < nq; q += gridDim.x) {
+    const int e = items[q];
+    const int4 b = blk[e];
+    if (st[b.x].stop) continue;
+    double acc[JC];
 #pragma unroll
-  for (int k = 0; k < JC; ++k) acc[k] = 0.0;
-  dots_rows<JC>(b.y + threadIdx.x, b.z, blockDim.x, ld, V, w, acc);
-  block_partials_bf<JC>(acc, part, nb);
+    for (int k = 0; k < JC; ++k) acc[k] = 0.0;
+    dots_rows<JC>(b.y + threadIdx.x, b.z, blockDim.x, ld, V, w, acc);
+    block_partials_bf<JC>(acc, part, nb, e);
+    __syncthreads();
+  }
 }
 
-// w -= V h (h of the block's system); then p = V^T w or p = w^T w
+// w -= V h (h of the item's system); then p = V^T w or p = w^T w
 template <int JC, bool NORM>
 __global__ void __launch_bounds__(kVecThreads)
-k_pupdate(int ld, const int4* __restrict__ blk, const KrylovState* st,
-          const double* __restrict__ V, const double* __restrict__ hbuf, int hb_stride,
-          double* __restrict__ w, double* part, int nb) {
-  const int4 b = blk[blockIdx.x];
-  if (st[b.x].stop) return;
+k_pupdate(int ld, const int4* __restrict__ blk, const int* __restrict__ items,
+          const int* __restrict__ nitems, const KrylovState* st, const double* __restrict__ V,
+          const double* __restrict__ hbuf, int hb_stride, double* __restrict__ w, double* part,
+          int nb) {
   __shared__ double hneg[JC];
-  for (int k = threadIdx.x; k < JC; k += blockDim.x) hneg[k] = -hbuf[(size_t)b.x * hb_stride + k];
-  __syncthreads();
-  constexpr int NA = NORM ? 1 : JC;
-  double acc[NA];
+  const int nq = *nitems;
+  for (int q = blockIdx.x; q < nq; q += gridDim.x) {
+    const int e = items[q];
+    const int4 b = blk[e];
+    if (st[b.x].stop) continue;
+    for (int k = threadIdx.x; k < JC; k += blockDim.x)
+      hneg[k] = -hbuf[(size_t)b.x * hb_stride + k];
+    __syncthreads();
+    constexpr int NA = NORM ? 1 : JC;
+    double acc[NA];
 #pragma unroll
-  for (int k = 0; k < NA; ++k) acc[k] = 0.0;
-  update_rows<JC, NORM>(b.y + threadIdx.x, b.z, blockDim.x, ld, V, hneg, w, acc);
-  block_partials_bf<NA>(acc, part, nb);
+    for (int k = 0; k < NA; ++k) acc[k] = 0.0;
+    update_rows<JC, NORM>(b.y + threadIdx.x, b.z, blockDim.x, ld, V, hneg, w, acc);
+    block_partials_bf<NA>(acc, part, nb, e);
+    __syncthreads();
+  }
 }
 
 // runtime-bounded forms for 32 < jc <= 64 basis vectors
 template <int MAXK>
 __global__ void __launch_bounds__(kVecThreads)
-k_pdots_rt(int ld, const int4* __restrict__ blk, const KrylovState* st,
-           const double* __restrict__ V, int jc, const double* __restrict__ w, double* part,
-           int nb) {
-  const int4 b = blk[blockIdx.x];
-  if (st[b.x].stop) return;
-  double acc[MAXK];
+k_pdots_rt(int ld, const int4* __restrict__ blk, const int* __restrict__ items,
+           const int* __restrict__ nitems, const KrylovState* st, const double* __restrict__ V,
+           int jc, const double* __restrict__ w, double* part, int nb) {
+  const int nq = *nitems;
+  for (int q = blockIdx.x; q < nq; q += gridDim.x) {
+    const int e = items[q];
+    const int4 b = blk[e];
+    if (st[b.x].stop) continue;
+    double acc[MAXK];
 #pragma unroll
-  for (int k = 0; k < MAXK; ++k) acc[k] = 0.0;
-  for (int i = b.y + threadIdx.x; i < b.z; i += blockDim.x) {
-    const double wi = w[i];
+    for (int k = 0; k < MAXK; ++k) acc[k] = 0.0;
+    for (int i = b.y + threadIdx.x; i < b.z; i += blockDim.x) {
+      const double wi = w[i];
 #pragma unroll
-    for (int k = 0; k < MAXK; ++k)
-      if (k < jc) acc[k] = fma(__ldg(V + (size_t)k * ld + i), wi, acc[k]);
+      for (int k = 0; k < MAXK; ++k)
+        if (k < jc) acc[k] = fma(__ldg(V + (size_t)k * ld + i), wi, acc[k]);
+    }
+    block_partials<MAXK>(acc, jc, part, nb, e);
+    __syncthreads();
   }
-  block_partials<MAXK>(acc, jc, part, nb);
 }
 
 template <int MAXK, bool NORM>
 __global__ void __launch_bounds__(kVecThreads)
-k_pupdate_rt(int ld, const int4* __restrict__ blk, const KrylovState* st,
+k_pupdate_rt(int ld, const int4* __restrict__ blk, const int* __restrict__ items,
+             const int* __restrict__ nitems, const KrylovState* st,
              const double* __restrict__ V, int jc, const double* __restrict__ hbuf,
              int hb_stride, double* w, double* part, int nb) {
-  const int4 b = blk[blockIdx.x];
-  if (st[b.x].stop) return;
   __shared__ double hneg[MAXK];
-  for (int k = threadIdx.x; k < MAXK; k += blockDim.x)
-    hneg[k] = k < jc ? -hbuf[(size_t)b.x * hb_stride + k] : 0.0;
-  __syncthreads();
-  constexpr int NA = NORM ? 1 : MAXK;
-  double acc[NA];
+  const int nq = *nitems;
+  for (int q = blockIdx.x; q < nq; q += gridDim.x) {
+    const int e = items[q];
+    const int4 b = blk[e];
+    if (st[b.x].stop) continue;
+    for (int k = threadIdx.x; k < MAXK; k += blockDim.x)
+      hneg[k] = k < jc ? -hbuf[(size_t)b.x * hb_stride + k] : 0.0;
+    __syncthreads();
+    constexpr int NA = NORM ? 1 : MAXK;
+    double acc[NA];
 #pragma unroll
-  for (int k = 0; k < NA; ++k) acc[k] = 0.0;
-  for (int i = b.y + threadIdx.x; i < b.z; i += blockDim.x) {
-    double wn = w[i];
+    for (int k = 0; k < NA; ++k) acc[k] = 0.0;
+    for (int i = b.y + threadIdx.x; i < b.z; i += blockDim.x) {
+      double wn = w[i];
 #pragma unroll
-    for (int k = 0; k < MAXK; ++k)
-      if (k < jc) wn = fma(__ldg(V + (size_t)k * ld + i), hneg[k], wn);
-    w[i] = wn;
-    if (NORM) {
-      acc[0] = fma(wn, wn, acc[0]);
-    } else {
+      for (int k = 0; k < MAXK; ++k)
+        if (k < jc) wn = fma(__ldg(V + (size_t)k * ld + i), hneg[k], wn);
+      w[i] = wn;
+      if (NORM) {
+        acc[0] = fma(wn, wn, acc[0]);
+      } else {
 #pragma unroll
-      for (int k = 0; k < NA; ++k)
-        if (k < jc) acc[k] = fma(__ldg(V + (size_t)k * ld + i), wn, acc[k]);
+        for (int k = 0; k < NA; ++k)
+          if (k < jc) acc[k] = fma(__ldg(V + (size_t)k * ld + i), wn, acc[k]);
+      }
     }
+    block_partials<NA>(acc, NORM ? 1 : jc, part, nb, e);
+    __syncthreads();
   }
-  block_partials<NA>(acc, NORM ? 1 : jc, part, nb);
 }
 
-// One block per system: coefficient v of column j is the fixed-order sum of
-// the system's block partials (warps over coefficients, lanes over blocks).
+// Per system: coefficient v of column j is the fixed-order sum of the
+// system's block partials (warps over coefficients, lanes over blocks).
 // mode 0: H(v, j) = s; mode 1: H(v, j) += s; both also hbuf[v] = s.
 __global__ void k_preduce(const double* __restrict__ part, int nb, const int* __restrict__ seg_blk,
+                          const int* __restrict__ sys, const int* __restrict__ nsys,
                           const KrylovState* st, double* H, size_t hstride, int ldh, int j,
                           double* hbuf, int hb_stride, int mode, int jc) {
-  const int s = blockIdx.x;
-  if (st[s].stop) return;
-  const int b0 = seg_blk[s], b1 = seg_blk[s + 1];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  double* col = H + s * hstride + (size_t)j * ldh;
-  for (int v = wid; v < jc; v += nw) {
-    double t = 0.0;
-    for (int b = b0 + lane; b < b1; b += 32) t += part[(size_t)v * nb + b];
-    t = warp_sum(t);
-    if (lane == 0) {
-      if (mode == 0) col[v] = t;
-      else col[v] += t;
-      hbuf[(size_t)s * hb_stride + v] = t;
+  const int nq = *nsys;
+  for (int q = blockIdx.x; q < nq; q += gridDim.x) {
+    const int s = sys[q];
+    if (st[s].stop) continue;
+    const int b0 = seg_blk[s], b1 = seg_blk[s + 1];
+    double* col = H + s * hstride + (size_t)j * ldh;
+    for (int v = wid; v < jc; v += nw) {
+      double t = 0.0;
+      for (int b = b0 + lane; b < b1; b += 32) t += part[(size_t)v * nb + b];
+      t = warp_sum(t);
+      if (lane == 0) {
+        if (mode == 0) col[v] = t;
+        else col[v] += t;
+        hbuf[(size_t)s * hb_stride + v] = t;
+      }
     }
   }
 }
 
-// One block per system: the Givens step (givens_block).  The last system to
-// end its cycle stops the pack's row kernels and raises the host flag.
+// Per system: the Givens step (givens_block).  A system that stops takes its
+// rows out of the row kernels for the rest of the cycle; the last one to
+// stop stops the pack's row kernels and raises the host flag.
 __global__ void k_pgivens(const double* __restrict__ part, const int* __restrict__ seg_blk,
+                          const int* __restrict__ sys, const int* __restrict__ nsys,
                           KrylovState* st, double* H, size_t hstride, int ldh, int j,
                           double* cs, double* sn, double* gv, int vstride, int* nactive,
                           const int* __restrict__ off, int* live_run, KrylovState* pack_st,
                           volatile int* stop_host) {
-  const int s = blockIdx.x;
-  if (st[s].stop) return;
-  const size_t o = (size_t)s * vstride;
-  const bool ended = givens_block(part, seg_blk[s], seg_blk[s + 1], H + s * hstride + (size_t)j * ldh,
-                                  cs + o, sn + o, gv + o, j, st + s);
-  if (!ended) return;
-  // the system's rows leave the row kernels for the rest of the cycle
-  for (int c = off[s] / 32 + threadIdx.x; c <= (off[s + 1] - 1) / 32; c += blockDim.x)
-    atomicSub(live_run + c, 1);
-  if (threadIdx.x == 0 && atomicSub(nactive, 1) == 1) {
-    pack_st->stop = 1;
-    *stop_host = 1;
+  const int nq = *nsys;
+  for (int q = blockIdx.x; q < nq; q += gridDim.x) {
+    const int s = sys[q];
+    if (st[s].stop) continue;
+    const size_t o = (size_t)s * vstride;
+    const bool ended = givens_block(part, seg_blk[s], seg_blk[s + 1],
+                                    H + s * hstride + (size_t)j * ldh, cs + o, sn + o, gv + o, j,
+                                    st + s);
+    if (ended) {
+      for (int c = off[s] / 32 + threadIdx.x; c <= (off[s + 1] - 1) / 32; c += blockDim.x)
+        atomicSub(live_run + c, 1);
+      if (threadIdx.x == 0 && atomicSub(nactive, 1) == 1) {
+        pack_st->stop = 1;
+        *stop_host = 1;
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -221,50 +275,70 @@ __global__ void k_plive_init(int nchunks, int n, const int* __restrict__ off, in
   }
 }
 
-// x += z over the rows of the systems that took the cycle
+// x += z over the items (the systems that took the cycle)
 __global__ void __launch_bounds__(kVecThreads)
-k_paxpy(const int4* __restrict__ blk, const int* __restrict__ active, double* x,
-        const double* __restrict__ z) {
-  const int4 b = blk[blockIdx.x];
-  if (!active[b.x]) return;
-  for (int i = b.y + threadIdx.x; i < b.z; i += blockDim.x) x[i] = x[i] + z[i];
+k_paxpy(const int4* __restrict__ blk, const int* __restrict__ items,
+        const int* __restrict__ nitems, double* x, const double* __restrict__ z) {
+  const int nq = *nitems;
+  for (int q = blockIdx.x; q < nq; q += gridDim.x) {
+    const int4 b = blk[items[q]];
+    for (int i = b.y + threadIdx.x; i < b.z; i += blockDim.x) x[i] = x[i] + z[i];
+  }
 }
 
-// v_{j+1} = w / H(j+1, j) of the block's system, and D^{-1} v_{j+1}
+// v_{j+1} = w / H(j+1, j) of the item's system, and D^{-1} v_{j+1}
 __global__ void __launch_bounds__(kVecThreads)
-k_pscale_next(const int4* __restrict__ blk, const KrylovState* st, const double* __restrict__ w,
-              double* vnext, const double* __restrict__ dinv, double* rhat64, float* rhat32) {
-  const int4 b = blk[blockIdx.x];
-  if (st[b.x].stop) return;
-  scale_rows(b.y + threadIdx.x, b.z, blockDim.x, st[b.x].inv_hn, w, vnext, dinv, rhat64, rhat32);
+k_pscale_next(const int4* __restrict__ blk, const int* __restrict__ items,
+              const int* __restrict__ nitems, const KrylovState* st,
+              const double* __restrict__ w, double* vnext, const double* __restrict__ dinv,
+              double* rhat64, float* rhat32) {
+  const int nq = *nitems;
+  for (int q = blockIdx.x; q < nq; q += gridDim.x) {
+    const int4 b = blk[items[q]];
+    if (st[b.x].stop) continue;
+    scale_rows(b.y + threadIdx.x, b.z, blockDim.x, st[b.x].inv_hn, w, vnext, dinv, rhat64,
+               rhat32);
+  }
 }
 
-// per-block partial sums of x^T x over the block's rows
+// per-item partial sums of x^T x
 __global__ void __launch_bounds__(kVecThreads)
-k_pnorm_part(const int4* __restrict__ blk, const double* __restrict__ x, double* part, int nb) {
-  const int4 b = blk[blockIdx.x];
-  double acc[1] = {0.0};
-  for (int i = b.y + threadIdx.x; i < b.z; i += blockDim.x) acc[0] = fma(x[i], x[i], acc[0]);
-  block_partials_bf<1>(acc, part, nb);
+k_pnorm_part(const int4* __restrict__ blk, const int* __restrict__ items,
+             const int* __restrict__ nitems, const double* __restrict__ x, double* part,
+             int nb) {
+  const int nq = *nitems;
+  for (int q = blockIdx.x; q < nq; q += gridDim.x) {
+    const int e = items[q];
+    const int4 b = blk[e];
+    double acc[1] = {0.0};
+    for (int i = b.y + threadIdx.x; i < b.z; i += blockDim.x) acc[0] = fma(x[i], x[i], acc[0]);
+    block_partials_bf<1>(acc, part, nb, e);
+    __syncthreads();
+  }
 }
 
-// one block per system: sqrt of the sum of its partials into st.beta
-// (which = 0) or st.bnorm (which = 1)
+// per system: sqrt of the sum of its partials into st.beta (which = 0) or
+// st.bnorm (which = 1)
 __global__ void k_pnorm_final(const double* __restrict__ part, const int* __restrict__ seg_blk,
+                              const int* __restrict__ sys, const int* __restrict__ nsys,
                               KrylovState* st, int which) {
-  const int s = blockIdx.x;
   __shared__ double red[32];
-  double t = 0.0;
-  for (int b = seg_blk[s] + threadIdx.x; b < seg_blk[s + 1]; b += blockDim.x) t += part[b];
-  t = warp_sum(t);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) red[wid] = t;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double u = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) u += red[w];
-    if (which == 0) st[s].beta = sqrt(u);
-    else st[s].bnorm = sqrt(u);
+  const int nq = *nsys;
+  for (int q = blockIdx.x; q < nq; q += gridDim.x) {
+    const int s = sys[q];
+    double t = 0.0;
+    for (int b = seg_blk[s] + threadIdx.x; b < seg_blk[s + 1]; b += blockDim.x) t += part[b];
+    t = warp_sum(t);
+    if (lane == 0) red[wid] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double u = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) u += red[w];
+      if (which == 0) st[s].beta = sqrt(u);
+      else st[s].bnorm = sqrt(u);
+    }
+    __syncthreads();
   }
 }
 
@@ -302,44 +376,59 @@ __global__ void k_pcycle_reset(KrylovState* st, const int* __restrict__ active, 
   }
 }
 
-// cycle start of the block's system: v_0 = r / beta, D^{-1} v_0, and (its
+// cycle start of the item's system: v_0 = r / beta, D^{-1} v_0, and (its
 // first block) g = (beta, 0, ..., 0)
 __global__ void __launch_bounds__(kVecThreads)
-k_pcycle_start(const int4* __restrict__ blk, const KrylovState* st, const double* __restrict__ r,
-               double* v0, const double* __restrict__ dinv, double* rhat64, float* rhat32,
-               double* gv, int vstride, int m) {
-  const int4 b = blk[blockIdx.x];
-  if (st[b.x].stop) return;
-  const double beta = st[b.x].beta;
-  scale_rows(b.y + threadIdx.x, b.z, blockDim.x, 1.0 / beta, r, v0, dinv, rhat64, rhat32);
-  if (b.w)
-    for (int i = threadIdx.x; i <= m; i += blockDim.x)
-      gv[(size_t)b.x * vstride + i] = i == 0 ? beta : 0.0;
+k_pcycle_start(const int4* __restrict__ blk, const int* __restrict__ items,
+               const int* __restrict__ nitems, const KrylovState* st,
+               const double* __restrict__ r, double* v0, const double* __restrict__ dinv,
+               double* rhat64, float* rhat32, double* gv, int vstride, int m) {
+  const int nq = *nitems;
+  for (int q = blockIdx.x; q < nq; q += gridDim.x) {
+    const int4 b = blk[items[q]];
+    if (st[b.x].stop) continue;
+    const double beta = st[b.x].beta;
+    scale_rows(b.y + threadIdx.x, b.z, blockDim.x, 1.0 / beta, r, v0, dinv, rhat64, rhat32);
+    if (b.w)
+      for (int i = threadIdx.x; i <= m; i += blockDim.x)
+        gv[(size_t)b.x * vstride + i] = i == 0 ? beta : 0.0;
+  }
 }
 
-// one block per system: y = R^{-1} g over the steps its cycle took
+// per system: y = R^{-1} g over the steps its cycle took
 __global__ void k_pbacksolve(const double* __restrict__ H, size_t hstride, int ldh,
-                             const double* gv, double* y, int vstride, const KrylovState* st) {
-  const int s = blockIdx.x;
-  backsolve_block(H + s * hstride, ldh, gv + (size_t)s * vstride, y + (size_t)s * vstride, st[s].k);
+                             const double* gv, double* y, int vstride,
+                             const int* __restrict__ sys, const int* __restrict__ nsys,
+                             const KrylovState* st) {
+  const int nq = *nsys;
+  for (int q = blockIdx.x; q < nq; q += gridDim.x) {
+    const int s = sys[q];
+    backsolve_block(H + s * hstride, ldh, gv + (size_t)s * vstride, y + (size_t)s * vstride,
+                    st[s].k);
+    __syncthreads();
+  }
 }
 
-// u = V[0..k) y of the block's system (zero for a system whose cycle took no
-// step) and D^{-1} u
+// u = V[0..k) y of the item's system and D^{-1} u
 template <int MAXK>
 __global__ void __launch_bounds__(kVecThreads)
-k_pcombine(int ld, const int4* __restrict__ blk, const KrylovState* st,
+k_pcombine(int ld, const int4* __restrict__ blk, const int* __restrict__ items,
+           const int* __restrict__ nitems, const KrylovState* st,
            const double* __restrict__ V, const double* __restrict__ y, int vstride, double* u,
            const double* __restrict__ dinv, double* rhat64, float* rhat32) {
-  const int4 b = blk[blockIdx.x];
   __shared__ double ys[MAXK];
-  const int k = st[b.x].k;
-  for (int i = threadIdx.x; i < MAXK; i += blockDim.x)
-    ys[i] = i < k ? y[(size_t)b.x * vstride + i] : 0.0;
-  __syncthreads();
-  combine_rows<MAXK>(b.y + threadIdx.x, b.z, blockDim.x, ld, V, ys, k, u, dinv, rhat64, rhat32);
+  const int nq = *nitems;
+  for (int q = blockIdx.x; q < nq; q += gridDim.x) {
+    const int4 b = blk[items[q]];
+    const int k = st[b.x].k;
+    for (int i = threadIdx.x; i < MAXK; i += blockDim.x)
+      ys[i] = i < k ? y[(size_t)b.x * vstride + i] : 0.0;
+    __syncthreads();
+    combine_rows<MAXK>(b.y + threadIdx.x, b.z, blockDim.x, ld, V, ys, k, u, dinv, rhat64,
+                       rhat32);
+    __syncthreads();
+  }
 }
-
 
 // ---------------------------------------------------------------------------
 // host side
@@ -436,6 +525,15 @@ void pack_attach(gs2_handle* h, const std::vector<int64_t>& off) {
   P->seg_blk = (int*)h->dalloc(sizeof(int) * (P->count + 1));
   h->h2d(P->blk, blk.data(), sizeof(int4) * P->nb);
   h->h2d(P->seg_blk, sb.data(), sizeof(int) * (P->count + 1));
+  P->seg_blk_host = sb;
+  P->items = (int*)h->dalloc(sizeof(int) * std::max(1, P->nb));
+  P->sys = (int*)h->dalloc(sizeof(int) * P->count);
+  P->cnt = (int*)h->dalloc(sizeof(int) * 2);
+  P->items_host = (int*)pinned_get(sizeof(int) * std::max(1, P->nb));
+  P->sys_host = (int*)pinned_get(sizeof(int) * P->count);
+  P->cnt_host = (int*)pinned_get(sizeof(int) * 2);
+  P->gb = std::max(1, std::min(P->nb, 4 * h->nsm));
+  P->gs = std::max(1, std::min(P->count, 2 * h->nsm));
   P->st = (KrylovState*)h->dalloc(sizeof(KrylovState) * P->count);
   h->dzero(P->st, sizeof(KrylovState) * P->count);
   P->st_host = (KrylovState*)pinned_get(sizeof(KrylovState) * P->count);
@@ -457,6 +555,9 @@ void pack_free(gs2_handle* h) {
   if (P->gexec) cudaGraphExecDestroy(P->gexec);
   pinned_put(P->st_host, sizeof(KrylovState) * P->count);
   pinned_put(P->active_host, sizeof(int) * P->count);
+  pinned_put(P->items_host, sizeof(int) * std::max(1, P->nb));
+  pinned_put(P->sys_host, sizeof(int) * P->count);
+  pinned_put(P->cnt_host, sizeof(int) * 2);
   delete P;
   h->pack = nullptr;
 }
@@ -533,18 +634,42 @@ struct PackRun {
       if (rb == (void*)h->rhat32) r32 = h->rhat32;
       else r64 = (double*)rb;
     }
+    upload_lists();  // every system
     launch_norms(b, 1);
     k_pstate_init<<<(P->count + 255) / 256, 256, 0, h->stream>>>(P->st, P->count, tol, max_iters);
     GS2_LAUNCH_CHECK();
     launch_true_residual();
   }
 
+  // the work lists of the systems not done yet (all of them before the
+  // first advance), copied to the device on the handle's stream
+  void upload_lists() {
+    int ni = 0, ns = 0;
+    for (int s = 0; s < P->count; ++s) {
+      if (done[s]) continue;
+      P->sys_host[ns++] = s;
+      for (int e = P->seg_blk_host[s]; e < P->seg_blk_host[s + 1]; ++e) P->items_host[ni++] = e;
+    }
+    P->cnt_host[0] = ni;
+    P->cnt_host[1] = ns;
+    if (ni)
+      GS2_CUDA(cudaMemcpyAsync(P->items, P->items_host, sizeof(int) * ni,
+                               cudaMemcpyHostToDevice, h->stream));
+    if (ns)
+      GS2_CUDA(cudaMemcpyAsync(P->sys, P->sys_host, sizeof(int) * ns, cudaMemcpyHostToDevice,
+                               h->stream));
+    GS2_CUDA(cudaMemcpyAsync(P->cnt, P->cnt_host, sizeof(int) * 2, cudaMemcpyHostToDevice,
+                             h->stream));
+  }
+
   // per-system ||v|| into st.beta (which = 0) or st.bnorm (which = 1)
   void launch_norms(const double* v, int which) {
     KernelTimer tm(h, "norm", 8.0 * h->n);
-    k_pnorm_part<<<P->nb, kVecThreads, 0, h->stream>>>(P->blk, v, P->part, P->nb);
+    k_pnorm_part<<<P->gb, kVecThreads, 0, h->stream>>>(P->blk, P->items, P->cnt, v, P->part,
+                                                       P->nb);
     GS2_LAUNCH_CHECK();
-    k_pnorm_final<<<P->count, 256, 0, h->stream>>>(P->part, P->seg_blk, P->st, which);
+    k_pnorm_final<<<P->gs, 256, 0, h->stream>>>(P->part, P->seg_blk, P->sys, P->cnt + 1, P->st,
+                                                which);
     GS2_LAUNCH_CHECK();
   }
 
@@ -622,6 +747,7 @@ struct PackRun {
       return;
     }
     for (int s = 0; s < P->count; ++s) P->active_host[s] = !done[s];
+    upload_lists();
     launch_cycle();
   }
 
@@ -631,14 +757,15 @@ struct PackRun {
     switch (jc) {
 #define GS2_PDOTS_CASE(J)                                                               \
   case J:                                                                               \
-    k_pdots<J><<<P->nb, kVecThreads, 0, h->stream>>>(N, P->blk, P->st, h->V, h->w,      \
-                                                     P->part, P->nb);                   \
+    k_pdots<J><<<P->gb, kVecThreads, 0, h->stream>>>(N, P->blk, P->items, P->cnt, P->st, \
+                                                     h->V, h->w, P->part, P->nb);       \
     break;
       GS2_PJC_CASES(GS2_PDOTS_CASE)
 #undef GS2_PDOTS_CASE
       default:
-        k_pdots_rt<64><<<P->nb, kVecThreads, 0, h->stream>>>(N, P->blk, P->st, h->V, jc, h->w,
-                                                             P->part, P->nb);
+        k_pdots_rt<64><<<P->gb, kVecThreads, 0, h->stream>>>(N, P->blk, P->items, P->cnt,
+                                                             P->st, h->V, jc, h->w, P->part,
+                                                             P->nb);
         break;
     }
     GS2_LAUNCH_CHECK();
@@ -652,15 +779,14 @@ struct PackRun {
     switch (jc) {
 #define GS2_PUPD_CASE(J)                                                                \
   case J:                                                                               \
-    k_pupdate<J, NORM><<<P->nb, kVecThreads, 0, h->stream>>>(N, P->blk, P->st, h->V,    \
-                                                             P->hbuf, hs, h->w,         \
-                                                             P->part, P->nb);           \
+    k_pupdate<J, NORM><<<P->gb, kVecThreads, 0, h->stream>>>(                           \
+        N, P->blk, P->items, P->cnt, P->st, h->V, P->hbuf, hs, h->w, P->part, P->nb);   \
     break;
       GS2_PJC_CASES(GS2_PUPD_CASE)
 #undef GS2_PUPD_CASE
       default:
-        k_pupdate_rt<64, NORM><<<P->nb, kVecThreads, 0, h->stream>>>(
-            N, P->blk, P->st, h->V, jc, P->hbuf, hs, h->w, P->part, P->nb);
+        k_pupdate_rt<64, NORM><<<P->gb, kVecThreads, 0, h->stream>>>(
+            N, P->blk, P->items, P->cnt, P->st, h->V, jc, P->hbuf, hs, h->w, P->part, P->nb);
         break;
     }
     GS2_LAUNCH_CHECK();
@@ -668,9 +794,9 @@ struct PackRun {
 
   void launch_reduce(int j, int jc, int mode) {
     KernelTimer tm(h, "reduce_cols", 8.0 * jc * P->nb);
-    k_preduce<<<P->count, 256, 0, h->stream>>>(P->part, P->nb, P->seg_blk, P->st, P->H,
-                                               P->hstride(), ldh(), j, P->hbuf,
-                                               (int)P->vstride(), mode, jc);
+    k_preduce<<<P->gs, 256, 0, h->stream>>>(P->part, P->nb, P->seg_blk, P->sys, P->cnt + 1,
+                                            P->st, P->H, P->hstride(), ldh(), j, P->hbuf,
+                                            (int)P->vstride(), mode, jc);
     GS2_LAUNCH_CHECK();
   }
 
@@ -696,18 +822,19 @@ struct PackRun {
     launch_update<true>(jc);
     {
       KernelTimer tm(h, "givens", 8.0 * P->nb + 8.0 * 4 * (j + 2) * P->count);
-      k_pgivens<<<P->count, 128, 0, h->stream>>>(P->part, P->seg_blk, P->st, P->H, P->hstride(),
-                                                 ldh(), j, P->cs, P->sn, P->gvec,
-                                                 (int)P->vstride(), P->nactive, P->off_dev,
-                                                 P->live_run, h->st, h->stop_mapped_dev);
+      k_pgivens<<<P->gs, 128, 0, h->stream>>>(P->part, P->seg_blk, P->sys, P->cnt + 1, P->st,
+                                              P->H, P->hstride(), ldh(), j, P->cs, P->sn,
+                                              P->gvec, (int)P->vstride(), P->nactive,
+                                              P->off_dev, P->live_run, h->st,
+                                              h->stop_mapped_dev);
       GS2_LAUNCH_CHECK();
     }
     if (j + 1 < m) {
       KernelTimer tm(h, "scale_next",
                      16.0 * N + (r64 ? 16.0 * N : 0.0) + (r32 ? 12.0 * N : 0.0));
-      k_pscale_next<<<P->nb, kVecThreads, 0, h->stream>>>(P->blk, P->st, h->w,
-                                                          h->V + (size_t)(j + 1) * N, h->dinv,
-                                                          r64, r32);
+      k_pscale_next<<<P->gb, kVecThreads, 0, h->stream>>>(P->blk, P->items, P->cnt, P->st,
+                                                          h->w, h->V + (size_t)(j + 1) * N,
+                                                          h->dinv, r64, r32);
       GS2_LAUNCH_CHECK();
     }
   }
@@ -770,9 +897,9 @@ struct PackRun {
     k_plive_init<<<(P->nchunks + 255) / 256, 256, 0, h->stream>>>(
         P->nchunks, (int)h->n, P->off_dev, P->count, P->active, P->live_cycle, P->live_run);
     GS2_LAUNCH_CHECK();
-    k_pcycle_start<<<P->nb, kVecThreads, 0, h->stream>>>(P->blk, P->st, h->r, h->V, h->dinv,
-                                                         r64, r32, P->gvec, (int)P->vstride(),
-                                                         m);
+    k_pcycle_start<<<P->gb, kVecThreads, 0, h->stream>>>(P->blk, P->items, P->cnt, P->st, h->r,
+                                                         h->V, h->dinv, r64, r32, P->gvec,
+                                                         (int)P->vstride(), m);
     GS2_LAUNCH_CHECK();
     cycle_ran = true;
     if (use_graph()) {
@@ -793,32 +920,29 @@ struct PackRun {
       profile_capture_step(h, -1);
     }
     // x += M^{-1} V y per system (u = 0 for systems without a step)
-    k_pbacksolve<<<P->count, 64, 0, h->stream>>>(P->H, P->hstride(), ldh(), P->gvec, P->y,
-                                                 (int)P->vstride(), P->st);
+    k_pbacksolve<<<P->gs, 64, 0, h->stream>>>(P->H, P->hstride(), ldh(), P->gvec, P->y,
+                                              (int)P->vstride(), P->sys, P->cnt + 1, P->st);
     GS2_LAUNCH_CHECK();
     {
       KernelTimer tm(h, "combine", 8.0 * h->n * (m + 1));
       const int N = (int)h->n;
       const int vs = (int)P->vstride();
-      if (m <= 8)
-        k_pcombine<8><<<P->nb, kVecThreads, 0, h->stream>>>(N, P->blk, P->st, h->V, P->y, vs,
-                                                            h->w, h->dinv, r64, r32);
-      else if (m <= 16)
-        k_pcombine<16><<<P->nb, kVecThreads, 0, h->stream>>>(N, P->blk, P->st, h->V, P->y, vs,
-                                                             h->w, h->dinv, r64, r32);
-      else if (m <= 32)
-        k_pcombine<32><<<P->nb, kVecThreads, 0, h->stream>>>(N, P->blk, P->st, h->V, P->y, vs,
-                                                             h->w, h->dinv, r64, r32);
-      else
-        k_pcombine<64><<<P->nb, kVecThreads, 0, h->stream>>>(N, P->blk, P->st, h->V, P->y, vs,
-                                                             h->w, h->dinv, r64, r32);
+#define GS2_PCOMBINE(M)                                                                  \
+  k_pcombine<M><<<P->gb, kVecThreads, 0, h->stream>>>(N, P->blk, P->items, P->cnt, P->st, \
+                                                      h->V, P->y, vs, h->w, h->dinv, r64,  \
+                                                      r32)
+      if (m <= 8) GS2_PCOMBINE(8);
+      else if (m <= 16) GS2_PCOMBINE(16);
+      else if (m <= 32) GS2_PCOMBINE(32);
+      else GS2_PCOMBINE(64);
+#undef GS2_PCOMBINE
       GS2_LAUNCH_CHECK();
     }
     {
       // systems that took no part in the cycle keep their x and skip the rows
       LiveRows lr(h, P->live_cycle);
       precond_apply(h, pc, h->w, h->z, wants, nullptr);
-      k_paxpy<<<P->nb, kVecThreads, 0, h->stream>>>(P->blk, P->active, x, h->z);
+      k_paxpy<<<P->gb, kVecThreads, 0, h->stream>>>(P->blk, P->items, P->cnt, x, h->z);
       GS2_LAUNCH_CHECK();
       launch_true_residual();
     }

@@ -35,9 +35,11 @@ struct Log2<1> {
 // P - 1 adds per lane for P = NV rounded up to a power of two, instead of
 // 5 adds per value of a shuffle tree -- the FP64 pipe is the bottleneck of
 // these kernels.  After it lane l holds the warp's sum of value l >> (5 - p).
+// The block's sums go to column `col` of part (the block index by default;
+// a block that loops over several work items passes the item).
 template <int NV>
 __device__ __forceinline__ void block_partials_bf(const double (&acc)[NV], double* part,
-                                                  int nblk) {
+                                                  int nblk, int col) {
   constexpr int P = Pow2<NV>::value;
   constexpr int p = Log2<P>::value;
   static_assert(P <= 32, "butterfly reduction holds at most 32 values");
@@ -69,15 +71,21 @@ __device__ __forceinline__ void block_partials_bf(const double (&acc)[NV], doubl
     double s = 0.0;
 #pragma unroll
     for (int w = 0; w < kVecThreads / 32; ++w) s += red[w][threadIdx.x];
-    part[(size_t)threadIdx.x * nblk + blockIdx.x] = s;
+    part[(size_t)threadIdx.x * nblk + col] = s;
   }
+}
+
+template <int NV>
+__device__ __forceinline__ void block_partials_bf(const double (&acc)[NV], double* part,
+                                                  int nblk) {
+  block_partials_bf<NV>(acc, part, nblk, (int)blockIdx.x);
 }
 
 // Block-wide sums of NV per-thread values, written to part[v * nblk + blk]
 // (general form: one shuffle tree per value; used for NV > 32).
 template <int NV>
 __device__ __forceinline__ void block_partials(const double (&acc)[NV], int nv, double* part,
-                                               int nblk) {
+                                               int nblk, int col) {
   __shared__ double red[kVecThreads / 32][NV];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -92,8 +100,14 @@ __device__ __forceinline__ void block_partials(const double (&acc)[NV], int nv, 
     double s = 0.0;
 #pragma unroll
     for (int w = 0; w < kVecThreads / 32; ++w) s += red[w][v];
-    part[(size_t)v * nblk + blockIdx.x] = s;
+    part[(size_t)v * nblk + col] = s;
   }
+}
+
+template <int NV>
+__device__ __forceinline__ void block_partials(const double (&acc)[NV], int nv, double* part,
+                                               int nblk) {
+  block_partials<NV>(acc, nv, part, nblk, (int)blockIdx.x);
 }
 
 }  // namespace gs2
