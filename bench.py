@@ -740,7 +740,9 @@ def hybrid(gs2, torch, pr, stream, b):
 
 def comparisons(gs2, torch, pr, stream, b):
     """One solve each of the paper's baselines and the precision variants on
-    the same workload (untimed by the headline; device-timed here)."""
+    the same workload (untimed by the headline; device-timed here), and CG
+    with SGS2 and with the AMG cycle (the Laplacian is SPD; Sec. 9 runs CG
+    with SGS2)."""
     res = {}
     variants = {
         "sgs2_1_2": gs2.params("gs2", 1, 2, direction="symmetric"),
@@ -752,6 +754,8 @@ def comparisons(gs2, torch, pr, stream, b):
         "amg_sgs2_1_1": gs2.params("amg", 1, 1, direction="symmetric"),
         "jr3_w1.0": gs2.params("jr", 3, omega=1.0),
         "jr3_w0.8": gs2.params("jr", 3, omega=0.8),
+        "cg_sgs2_1_1": gs2.params("gs2", 1, 1, direction="symmetric"),
+        "cg_amg_sgs2_1_1": gs2.params("amg", 1, 1, direction="symmetric"),
     }
     h = gs2.gs2_setup(pr.A, precisions=("fp32", "fp16"), stream=stream.cuda_stream)
     t0 = time.perf_counter()
@@ -761,13 +765,19 @@ def comparisons(gs2, torch, pr, stream, b):
     with torch.cuda.stream(stream):
         x = torch.zeros(pr.n, dtype=torch.float64, device="cuda")
         for name, p in variants.items():
+            # (the Laplacian is SPD: the cg_ variants run CG with the
+            # symmetric preconditioner instead of GMRES)
+            def solve():
+                if name.startswith("cg_"):
+                    return gs2.cg_solve(h, b, x, 1e-8, 3000, p)
+                return gs2.gmres_solve(h, b, x, 30, 1e-8, 3000, p)
             x.zero_()
-            gs2.gmres_solve(h, b, x, 30, 1e-8, 3000, p)  # warm (levels, workspace)
+            solve()  # warm (levels, workspace)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             x.zero_()
             e0.record(stream)
-            info = gs2.gmres_solve(h, b, x, 30, 1e-8, 3000, p)
+            info = solve()
             e1.record(stream)
             e1.synchronize()
             ms = e0.elapsed_time(e1)

@@ -801,6 +801,7 @@ void gs2::destroy_handle(gs2_handle* h) {
   if (h->pack) pack_free(h);
   for (Hybrid* y : h->hybrids) delete y;
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->cg_gexec) cudaGraphExecDestroy(h->cg_gexec);
   if (h->gstream) cudaStreamDestroy(h->gstream);
   if (h->gev_in) cudaEventDestroy(h->gev_in);
   if (h->gev_out) cudaEventDestroy(h->gev_out);
@@ -1350,6 +1351,12 @@ gs2_status gs2_autotune(gs2_handle* h) {
     h->gexec = nullptr;
     h->gkey.clear();
   }
+  if (h->cg_gexec) {
+    cudaGraphExecDestroy(h->cg_gexec);
+    h->cg_gexec = nullptr;
+    h->cg_gkey.clear();
+  }
+  pack_drop_graph(h);
   return GS2_OK;
   API_END
 }

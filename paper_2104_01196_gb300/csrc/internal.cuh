@@ -191,6 +191,10 @@ struct gs2_handle {
   cudaEvent_t gev_in = nullptr, gev_out = nullptr;
   cudaGraphExec_t gexec = nullptr;
   std::vector<double> gkey;
+  // CG: a chunk of iterations as one graph (same stream and events)
+  cudaGraphExec_t cg_gexec = nullptr;
+  std::vector<double> cg_gkey;
+  int64_t cg_launches = 0;
   int64_t g_launches = 0;  // kernel launches per replay
 
   // stream-ordered allocation (cudaMallocAsync / cudaFreeAsync on `stream`):
@@ -367,6 +371,8 @@ void pack_concat(int count, const int64_t* n, const int64_t* const* rowptr,
                  std::vector<int64_t>& rp, std::vector<int32_t>& ci, std::vector<double>& va);
 void pack_attach(gs2_handle* h, const std::vector<int64_t>& off);
 void pack_free(gs2_handle* h);
+// drop the pack's captured cycle (tile shapes changed)
+void pack_drop_graph(gs2_handle* h);
 int pack_count(const gs2_handle* h);
 const std::vector<int64_t>* pack_offsets(const gs2_handle* h);
 // (system, row of that system) of a row of the pack

@@ -781,10 +781,12 @@ __global__ void k_cg_scalar(const double* __restrict__ part, int nblk, KrylovSta
   }
 }
 
-// x += alpha p ; r -= alpha q ; part = r.r
+// x += alpha p ; r -= alpha q ; part = r.r ; and the preconditioner's
+// D^{-1} r in its sweep precision (whichever of rhat64, rhat32 is non-null)
 __global__ void __launch_bounds__(kVecThreads)
 k_cg_xr(int n, double* x, double* r, const double* __restrict__ p, const double* __restrict__ q,
-        double* part, int nblk, const KrylovState* st, const int* skip) {
+        double* part, int nblk, const KrylovState* st, const int* skip,
+        const double* __restrict__ dinv, double* rhat64, float* rhat32) {
   if (skip && *skip) return;
   const double a = st->alpha;
   double acc[1] = {0.0};
@@ -793,6 +795,8 @@ k_cg_xr(int n, double* x, double* r, const double* __restrict__ p, const double*
     const double ri = fma(-a, q[i], r[i]);
     r[i] = ri;
     acc[0] = fma(ri, ri, acc[0]);
+    if (rhat64) rhat64[i] = dinv[i] * ri;
+    if (rhat32) rhat32[i] = (float)(dinv[i] * ri);
   }
   block_partials<1>(acc, 1, part, nblk);
 }
@@ -859,8 +863,85 @@ gs2_status cg_run(gs2_handle* h, const double* b, double* x, double tol, int max
     return GS2_OK;
   }
   gs2_status st = GS2_OK;
-  launch_resid(h, b, x, r, nullptr, nullptr, nullptr);
+  // the preconditioner's D^{-1} r comes from the kernel that updates r
+  const bool wants = precond_wants_rhat(pc);
+  double* r64 = nullptr;
+  float* r32 = nullptr;
+  if (wants) {
+    void* rb = precond_rhat_buffer(h, pc);
+    if (rb == (void*)h->rhat32) r32 = h->rhat32;
+    else r64 = (double*)rb;
+  }
+  // one CG iteration (every kernel a no-op once the device has stopped)
+  auto enqueue_iter = [&]() {
+    launch_spmv(h, pv, q, skip);
+    k_dot_part<<<nb, kVecThreads, 0, h->stream>>>(n, pv, q, h->part, nb, skip);
+    k_cg_scalar<<<1, 256, 0, h->stream>>>(h->part, nb, h->st, 0, skip);
+    k_cg_xr<<<nb, kVecThreads, 0, h->stream>>>(n, x, r, pv, q, h->part, nb, h->st, skip,
+                                               h->dinv, r64, r32);
+    k_cg_check<<<1, 256, 0, h->stream>>>(h->part, nb, h->st, h->stop_mapped_dev, skip);
+    precond_apply(h, pc, r, z, wants, skip);
+    k_dot_part<<<nb, kVecThreads, 0, h->stream>>>(n, r, z, h->part, nb, skip);
+    k_cg_scalar<<<1, 256, 0, h->stream>>>(h->part, nb, h->st, 1, skip);
+    k_cg_p<<<vec_blocks(h, n), kVecThreads, 0, h->stream>>>(n, pv, z, h->st, skip);
+    GS2_LAUNCH_CHECK();
+  };
   constexpr int kCheckEvery = 16;
+  // graphs (default): kCheckEvery iterations captured once, replayed on the
+  // handle's graph stream; x is the handle's own accumulator so that the
+  // graph does not depend on the caller's pointer
+  const bool graph = h->graph_mode != 2;
+  double* xu = x;
+  if (graph) {
+    x = h->w;
+    launch_copy(h, x, xu);
+    std::vector<double> key = {(double)(uintptr_t)x, (double)(uintptr_t)r64,
+                               (double)(uintptr_t)r32, (double)(uintptr_t)h->part,
+                               (double)profile_epoch(h)};
+    if (pc) {
+      const double pk[] = {(double)pc->kind, (double)pc->outer, (double)pc->inner, pc->omega,
+                           pc->gamma, (double)pc->direction, (double)pc->precision,
+                           (double)pc->form, (double)pc->parts, (double)pc->local_sweeps};
+      key.insert(key.end(), pk, pk + 10);
+    }
+    if (!h->gstream) {
+      GS2_CUDA(cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking));
+      GS2_CUDA(cudaEventCreateWithFlags(&h->gev_in, cudaEventDisableTiming));
+      GS2_CUDA(cudaEventCreateWithFlags(&h->gev_out, cudaEventDisableTiming));
+    }
+    if (!h->cg_gexec || h->cg_gkey != key) {
+      if (h->cg_gexec) cudaGraphExecDestroy(h->cg_gexec);
+      h->cg_gexec = nullptr;
+      cudaStream_t user = h->stream;
+      h->stream = h->gstream;
+      const long long c0 = gs2_launch_count();
+      cudaGraph_t g = nullptr;
+      profile_capture_begin(h);
+      GS2_CUDA(cudaStreamBeginCapture(h->gstream, cudaStreamCaptureModeThreadLocal));
+      try {
+        for (int it = 0; it < kCheckEvery; ++it) {
+          profile_capture_step(h, it);
+          enqueue_iter();
+        }
+      } catch (...) {
+        profile_capture_end(h);
+        cudaStreamEndCapture(h->gstream, &g);
+        if (g) cudaGraphDestroy(g);
+        h->stream = user;
+        throw;
+      }
+      profile_capture_end(h);
+      h->stream = user;
+      GS2_CUDA(cudaStreamEndCapture(h->gstream, &g));
+      h->cg_launches = gs2_launch_count() - c0;
+      add_launches(-h->cg_launches);  // captured, not run
+      cudaError_t e = cudaGraphInstantiate(&h->cg_gexec, g, 0);
+      cudaGraphDestroy(g);
+      GS2_CUDA(e);
+      h->cg_gkey = key;
+    }
+  }
+  launch_resid(h, b, x, r, nullptr, nullptr, nullptr);
   for (;;) {
     // (re)start the search direction from the current residual
     launch_norm(h, r, 0);
@@ -893,20 +974,25 @@ gs2_status cg_run(gs2_handle* h, const double* b, double* x, double tol, int max
     k_cg_scalar<<<1, 256, 0, h->stream>>>(h->part, nb, h->st, 2, nullptr);
     GS2_LAUNCH_CHECK();
     for (;;) {
-      for (int it = 0; it < kCheckEvery; ++it) {
-        if (*h->stop_mapped) break;
-        launch_spmv(h, pv, q, skip);
-        k_dot_part<<<nb, kVecThreads, 0, h->stream>>>(n, pv, q, h->part, nb, skip);
-        k_cg_scalar<<<1, 256, 0, h->stream>>>(h->part, nb, h->st, 0, skip);
-        k_cg_xr<<<nb, kVecThreads, 0, h->stream>>>(n, x, r, pv, q, h->part, nb, h->st, skip);
-        k_cg_check<<<1, 256, 0, h->stream>>>(h->part, nb, h->st, h->stop_mapped_dev, skip);
-        precond_apply(h, pc, r, z, false, skip);
-        k_dot_part<<<nb, kVecThreads, 0, h->stream>>>(n, r, z, h->part, nb, skip);
-        k_cg_scalar<<<1, 256, 0, h->stream>>>(h->part, nb, h->st, 1, skip);
-        k_cg_p<<<vec_blocks(h, n), kVecThreads, 0, h->stream>>>(n, pv, z, h->st, skip);
-        GS2_LAUNCH_CHECK();
+      const int before = h->st_host->iters;
+      if (graph) {
+        GS2_CUDA(cudaEventRecord(h->gev_in, h->stream));
+        GS2_CUDA(cudaStreamWaitEvent(h->gstream, h->gev_in, 0));
+        GS2_CUDA(cudaGraphLaunch(h->cg_gexec, h->gstream));
+        GS2_CUDA(cudaEventRecord(h->gev_out, h->gstream));
+        GS2_CUDA(cudaStreamWaitEvent(h->stream, h->gev_out, 0));
+        add_launches(h->cg_launches);
+      } else {
+        for (int it = 0; it < kCheckEvery; ++it) {
+          if (*h->stop_mapped) break;
+          profile_capture_step(h, it);
+          enqueue_iter();
+        }
+        profile_capture_step(h, -1);
       }
       read_state(h);
+      // launches of the iterations that ran (the rest were no-ops)
+      profile_harvest(h, h->st_host->iters - before, graph);
       if (h->st_host->stop) break;
     }
     if (h->st_host->status == GS2_ERR_NAN) {
@@ -922,6 +1008,7 @@ gs2_status cg_run(gs2_handle* h, const double* b, double* x, double tol, int max
   }
   launch_resid(h, b, x, h->t, nullptr, nullptr, nullptr);
   launch_norm(h, h->t, 0);
+  if (x != xu) launch_copy(h, xu, x);
   read_state(h);
   loc.true_relres = h->st_host->beta / bnorm;
   loc.status = st;

@@ -562,6 +562,13 @@ void pack_free(gs2_handle* h) {
   h->pack = nullptr;
 }
 
+void pack_drop_graph(gs2_handle* h) {
+  if (!h->pack || !h->pack->gexec) return;
+  cudaGraphExecDestroy(h->pack->gexec);
+  h->pack->gexec = nullptr;
+  h->pack->gkey.clear();
+}
+
 int pack_count(const gs2_handle* h) { return h->pack ? h->pack->count : 0; }
 const std::vector<int64_t>* pack_offsets(const gs2_handle* h) {
   return h->pack ? &h->pack->off : nullptr;

@@ -60,12 +60,14 @@ def _alone(pr, pc):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "mtsgs", "amg"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "mtsgs", "amg", "hybrid"])
 def test_results_equal_alone_and_in_the_mix(lib, prec):
     if prec == "mtsgs":
         pc = gs2.params("mtgs", 1, direction="symmetric")
     elif prec == "amg":
         pc = gs2.params("amg", 1, 1, direction="symmetric")
+    elif prec == "hybrid":
+        pc = gs2.params("gs2", 1, 1, direction="symmetric", parts=6, local=2)
     else:
         pc = gs2.params("gs2", 1, 1, direction="symmetric", precision=prec)
     probs = _mix()
