@@ -448,6 +448,32 @@ inline void parallel_ranges(int64_t n, F f) {
     if (e) std::rethrow_exception(e);
 }
 
+// Programmatic dependent launch: a kernel launched with launch_pdl may be
+// scheduled while the previous kernel of its stream is finishing; it must
+// call pdl_wait() before it touches global memory (the wait returns once the
+// previous grid has completed and its writes are visible, and at once for a
+// kernel launched without the attribute).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// (No kernel triggers its dependents early: a trigger at the start of each
+// kernel made the GMRES(30) solve 0.9% slower, one after each main loop
+// 0.3% slower, than the implicit trigger at completion.)
+
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t stream, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  GS2_CUDA(cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...));
+}
+
 // geometry helpers
 int vec_blocks(gs2_handle* h, int64_t n);
 constexpr int kVecThreads = 256;

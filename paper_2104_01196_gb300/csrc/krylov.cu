@@ -28,6 +28,7 @@ namespace gs2 {
 // order.  mode 0: H(v, j) = s; mode 1: H(v, j) += s; both also hbuf[v] = s.
 __global__ void k_reduce_cols(const double* __restrict__ part, int nblk, double* H, int ldh,
                               int j, double* hbuf, int mode, const int* skip) {
+  pdl_wait();
   if (skip && *skip) return;
   const int v = blockIdx.x;
   double s = 0.0;
@@ -62,6 +63,7 @@ template <int JC>
 __global__ void __launch_bounds__(kVecThreads)
 k_dots_x(int n, const double* __restrict__ V, const double* __restrict__ w, double* part,
          int nblk, const int* skip) {
+  pdl_wait();
   if (skip && *skip) return;
   double acc[JC];
 #pragma unroll
@@ -83,6 +85,7 @@ template <int JC, bool NORM>
 __global__ void __launch_bounds__(kVecThreads)
 k_update_x(int n, const double* __restrict__ V, const double* __restrict__ hcoef,
            double* __restrict__ w, double* part, int nblk, const int* skip) {
+  pdl_wait();
   if (skip && *skip) return;
   __shared__ double hneg[JC];
   for (int k = threadIdx.x; k < JC; k += blockDim.x) hneg[k] = -hcoef[k];
@@ -159,6 +162,7 @@ k_update(int n, const double* __restrict__ V, int jc, const double* __restrict__
 __global__ void k_givens(const double* __restrict__ part, int nblk, double* H, int ldh, int j,
                          double* cs, double* sn, double* gv, KrylovState* st,
                          volatile int* stop_host) {
+  pdl_wait();
   if (st->stop) return;
   if (givens_block(part, 0, nblk, H + (size_t)j * ldh, cs, sn, gv, j, st) && threadIdx.x == 0)
     *stop_host = 1;
@@ -168,6 +172,7 @@ __global__ void k_givens(const double* __restrict__ part, int nblk, double* H, i
 __global__ void k_scale_next(int n, const double* __restrict__ w, double* vnext,
                              const double* __restrict__ dinv, double* rhat64, float* rhat32,
                              const KrylovState* st) {
+  pdl_wait();
   if (st->stop) return;
   scale_rows(blockIdx.x * blockDim.x + threadIdx.x, n, gridDim.x * blockDim.x, st->inv_hn, w,
              vnext, dinv, rhat64, rhat32);
@@ -333,7 +338,8 @@ static int launch_dots(gs2_handle* h, int jc, const double* w, const int* skip) 
 #define GS2_DOTS_CASE(J)                                                          \
   case J:                                                                         \
     nb = reduction_grid(h, (const void*)k_dots_x<J>, kDotBlocksPerSm);            \
-    k_dots_x<J><<<nb, kVecThreads, 0, s>>>(n, h->V, w, h->part, nb, skip);        \
+    launch_pdl(k_dots_x<J>, nb, kVecThreads, 0, s, n, (const double*)h->V, w,     \
+               h->part, nb, skip);                                                \
     break;
     GS2_JC_CASES(GS2_DOTS_CASE)
 #undef GS2_DOTS_CASE
@@ -357,7 +363,8 @@ static int launch_update(gs2_handle* h, int jc, double* w, const int* skip) {
 #define GS2_UPD_CASE(J)                                                                 \
   case J:                                                                               \
     nb = reduction_grid(h, (const void*)k_update_x<J, NORM>, cap);                      \
-    k_update_x<J, NORM><<<nb, kVecThreads, 0, s>>>(n, h->V, h->hbuf, w, h->part, nb, skip); \
+    launch_pdl(k_update_x<J, NORM>, nb, kVecThreads, 0, s, n, (const double*)h->V,      \
+               (const double*)h->hbuf, w, h->part, nb, skip);                           \
     break;
     GS2_JC_CASES(GS2_UPD_CASE)
 #undef GS2_UPD_CASE
@@ -530,27 +537,30 @@ struct GmresRun {
     int nbr = launch_dots(h, jc, h->w, skip);
     {
       KernelTimer tm(h, "reduce_cols", 8.0 * jc * nbr);
-      k_reduce_cols<<<jc, 256, 0, h->stream>>>(h->part, nbr, h->H, ldh, j, h->hbuf, 0, skip);
+      launch_pdl(k_reduce_cols, jc, 256, 0, h->stream, (const double*)h->part, nbr, h->H, ldh, j,
+                 h->hbuf, 0, skip);
       GS2_LAUNCH_CHECK();
     }
     nbr = launch_update<false>(h, jc, h->w, skip);
     {
       KernelTimer tm(h, "reduce_cols", 8.0 * jc * nbr);
-      k_reduce_cols<<<jc, 256, 0, h->stream>>>(h->part, nbr, h->H, ldh, j, h->hbuf, 1, skip);
+      launch_pdl(k_reduce_cols, jc, 256, 0, h->stream, (const double*)h->part, nbr, h->H, ldh, j,
+                 h->hbuf, 1, skip);
       GS2_LAUNCH_CHECK();
     }
     nbr = launch_update<true>(h, jc, h->w, skip);
     {
       KernelTimer tm(h, "givens", 8.0 * nbr + 8.0 * 4 * (j + 2));
-      k_givens<<<1, 256, 0, h->stream>>>(h->part, nbr, h->H, ldh, j, h->cs, h->sn, h->gvec,
-                                         h->st, h->stop_mapped_dev);
+      launch_pdl(k_givens, 1, 256, 0, h->stream, (const double*)h->part, nbr, h->H, ldh, j, h->cs,
+                 h->sn, h->gvec, h->st, (volatile int*)h->stop_mapped_dev);
       GS2_LAUNCH_CHECK();
     }
     if (j + 1 < m) {
       // w read, v_{j+1} written, and D^{-1} v_{j+1} (D^{-1} read) when wanted
       KernelTimer tm(h, "scale_next", 16.0 * n + (r64 ? 16.0 * n : 0.0) + (r32 ? 12.0 * n : 0.0));
-      k_scale_next<<<vec_blocks(h, n), kVecThreads, 0, h->stream>>>(
-          n, h->w, h->V + (size_t)(j + 1) * n, h->dinv, r64, r32, h->st);
+      launch_pdl(k_scale_next, vec_blocks(h, n), kVecThreads, 0, h->stream, n,
+                 (const double*)h->w, h->V + (size_t)(j + 1) * n, (const double*)h->dinv, r64,
+                 r32, (const KrylovState*)h->st);
       GS2_LAUNCH_CHECK();
     }
   }

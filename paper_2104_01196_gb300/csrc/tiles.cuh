@@ -168,6 +168,7 @@ template <int K, int RPT, typename VT, class Epi>
 __global__ void __launch_bounds__(kRowThreads)
 k_tiles(TileMat<VT> M, Epi epi, const int* skip) {
   using AT = typename ValTraits<VT>::AT;
+  pdl_wait();
   if (skip && *skip) return;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bars[2];
@@ -316,6 +317,7 @@ __global__ void __launch_bounds__(kRowThreads)
 k_sell(int n, int nchunks, const int* __restrict__ cptr, const int* __restrict__ ci,
        const VT* __restrict__ va, Epi epi, const int* skip, const int* __restrict__ live) {
   using AT = typename ValTraits<VT>::AT;
+  pdl_wait();
   if (skip && *skip) return;
   const int lane = threadIdx.x & 31;
   const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -393,7 +395,7 @@ inline void launch_k(gs2_handle* h, const DevCsr& M, const VT* va, const Epi& ep
   auto fn = k_tiles<K, RPT, VT, Epi>;
   const int per_sm = blocks_per_sm((const void*)fn, smem);
   const int grid = std::min(M.ntiles, per_sm * h->nsm);
-  fn<<<grid, kRowThreads, smem, h->stream>>>(view<VT>(h, M, va), epi, skip);
+  launch_pdl(fn, grid, kRowThreads, smem, h->stream, view<VT>(h, M, va), epi, skip);
   GS2_LAUNCH_CHECK();
 }
 
@@ -408,8 +410,8 @@ inline void launch_sell(gs2_handle* h, const DevCsr& M, const VT* sv, const Epi&
   // chunk liveness applies to the matrices whose rows are the handle's rows
   const int* live =
       (h->row_live && (&M == &h->A || &M == &h->L || &M == &h->U)) ? h->row_live : nullptr;
-  fn<<<grid, kRowThreads, 0, h->stream>>>(M.n, M.sell_chunks, M.sell_ptr, M.sell_ci, sv, epi,
-                                          skip, live);
+  launch_pdl(fn, grid, kRowThreads, 0, h->stream, M.n, M.sell_chunks,
+             (const int*)M.sell_ptr, (const int*)M.sell_ci, sv, epi, skip, live);
   GS2_LAUNCH_CHECK();
 }
 
