@@ -747,6 +747,7 @@ def comparisons(gs2, torch, pr, stream, b):
     variants = {
         "sgs2_1_2": gs2.params("gs2", 1, 2, direction="symmetric"),
         "sgs2_1_3": gs2.params("gs2", 1, 3, direction="symmetric"),
+        "compact_sgs2_1_2": gs2.params("gs2", 1, 2, direction="symmetric", form="compact"),
         "sgs2_1_1_fp32": gs2.params("gs2", 1, 1, direction="symmetric", precision="fp32"),
         "sgs2_1_1_fp16": gs2.params("gs2", 1, 1, direction="symmetric", precision="fp16"),
         "gs_levels_sym": gs2.params("gs", 1, direction="symmetric"),

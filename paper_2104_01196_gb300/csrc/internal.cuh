@@ -264,6 +264,11 @@ void launch_inner(gs2_handle* h, const DevCsr& T, int prec, const void* rhat,
                   const void* g_in, void* g_out, double* x, double omega,
                   double gamma, int mode, const int* skip);
 
+// compact right-hand side of Eq. (9): rhat = D^{-1} b - Tother x with the
+// other prescaled triangle, in the sweep precision
+void launch_compact_rhs(gs2_handle* h, const DevCsr& Tother, const double* b, const double* x,
+                        double* rhat64, float* rhat32, const int* skip);
+
 // x = omega * rhat (zero inner sweeps from a zero start) or x += omega*rhat.
 void launch_rhat_update(gs2_handle* h, int prec, const void* rhat, double* x,
                         double omega, bool add, const int* skip);

@@ -125,6 +125,26 @@ struct EpiInner {
   }
 };
 
+// compact right-hand side of Eq. (9) on the other prescaled triangle
+// T' = D^{-1} U (forward) or D^{-1} L (backward):  rhat = D^{-1} b - T' x
+struct EpiCompact {
+  const double* __restrict__ x;
+  const double* __restrict__ b;
+  const double* __restrict__ dinv;
+  double* __restrict__ rhat64;
+  float* __restrict__ rhat32;
+  struct Pre {
+    double b, d;
+  };
+  __device__ Pre pre(int i) const { return Pre{b[i], dinv[i]}; }
+  __device__ double gather(int c) const { return __ldg(x + c); }
+  __device__ void finish(int i, double s, const Pre& p) const {
+    const double rh = p.d * p.b - s;
+    if (rhat64) rhat64[i] = rh;
+    if (rhat32) rhat32[i] = (float)rh;
+  }
+};
+
 // one colour of multicolour GS (Sec. 6.1.2): the colour matrix holds only
 // off-diagonal entries prescaled by D^{-1}, none of them inside the colour,
 // so every x_j gathered here belongs to another colour and is not written
@@ -293,6 +313,14 @@ float time_tile_probe(gs2_handle* h, const DevCsr& M, int reps, int role) {
   EpiInner<double, double, false, false> e{h->g0, h->rhat, nullptr, h->z, nullptr,
                                            1.0, 1.0, 1.0, INNER_LAST_ADD};
   return time_epilogue(h, M, e, reps);
+}
+
+void launch_compact_rhs(gs2_handle* h, const DevCsr& Tother, const double* b, const double* x,
+                        double* rhat64, float* rhat32, const int* skip) {
+  KernelTimer tm(h, "compact_rhs", bytes_csr(Tother, 8) + 24.0 * h->n +
+                                       (rhat64 ? 8.0 : 4.0) * h->n);
+  EpiCompact e{x, b, h->dinv, rhat64, rhat32};
+  dispatch<double>(h, Tother, Tother.va, e, skip);
 }
 
 void launch_jr(gs2_handle* h, const double* b, const double* x_in, double* x_out,

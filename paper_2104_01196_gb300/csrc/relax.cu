@@ -7,26 +7,6 @@
 
 namespace gs2 {
 
-// ---------------------------------------------------------------------------
-// compact right-hand side: rhat = D^{-1} (b - T_other x)  (Eq. 9 with
-// N = -U for a forward sweep and N = -L for a backward one)
-// ---------------------------------------------------------------------------
-
-__global__ void k_compact_rhs(int n, const int* __restrict__ rp, const int* __restrict__ ci,
-                              const double* __restrict__ va, const double* __restrict__ b,
-                              const double* __restrict__ x, const double* __restrict__ dinv,
-                              double* rhat64, float* rhat32, const int* skip) {
-  if (skip && *skip) return;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int k = rp[i]; k < rp[i + 1]; ++k) s = fma(va[k], __ldg(x + ci[k]), s);
-    // the triangle is prescaled: sum = (D^{-1} T x)_i
-    const double rh = dinv[i] * b[i] - s;
-    if (rhat64) rhat64[i] = rh;
-    if (rhat32) rhat32[i] = (float)rh;
-  }
-}
-
 __global__ void k_fill(int n, double* y, double v, const int* skip) {
   if (skip && *skip) return;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
@@ -37,16 +17,6 @@ __global__ void k_copy(int n, double* y, const double* __restrict__ x, const int
   if (skip && *skip) return;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     y[i] = x[i];
-}
-
-static void launch_compact_rhs(gs2_handle* h, const DevCsr& Tother, const double* b,
-                               const double* x, double* rhat64, float* rhat32,
-                               const int* skip) {
-  KernelTimer tm(h, "compact_rhs",
-                 Tother.nnz * 12.0 + 4.0 * (h->n + 1) + 24.0 * h->n + (rhat64 ? 8.0 : 4.0) * h->n);
-  k_compact_rhs<<<vec_blocks(h, h->n), kVecThreads, 0, h->stream>>>(
-      (int)h->n, Tother.rp, Tother.ci, Tother.va, b, x, h->dinv, rhat64, rhat32, skip);
-  GS2_LAUNCH_CHECK();
 }
 
 static void launch_fill(gs2_handle* h, double* y, double v, const int* skip) {
