@@ -163,7 +163,13 @@ gs2_status gs2_get_stats(const gs2_handle* h, gs2_handle_stats* out);
 gs2_status gs2_autotune(gs2_handle* h);
 
 /* How gmres_solve issues the Arnoldi steps of a restart cycle:
- * 0 (default) and 1 = as one replayed CUDA graph; 2 = as separate launches.
+ * 0 (default): the whole solve as one cooperative launch for a small system
+ * (n <= 16,384, restart <= 32, no preconditioner, JR or FP64 non-compact
+ * GS2, per-kernel profiling off: every restart cycle, preconditioner
+ * application and Givens step inside one kernel whose blocks meet at
+ * bounded grid barriers), else as in mode 1; 1 = each restart cycle's steps
+ * as one replayed CUDA graph; 2 = as separate launches; 3 = the one-launch
+ * solver, up to n = 65,536 (INVALID_ARG when the solve does not qualify).
  * A graph is captured once per cycle shape (restart, preconditioner,
  * profiling settings) on a private stream joined to the handle's stream;
  * steps after the device has ended the cycle run as no-ops.  Results are
@@ -171,6 +177,12 @@ gs2_status gs2_autotune(gs2_handle* h);
  * graph carries event nodes around the profiled kernels, and only the steps
  * a cycle ran are counted. */
 gs2_status gs2_set_graph_mode(gs2_handle* h, int mode);
+
+/* Test hook for the bounded waits of the one-launch solver: the next such
+ * solve on this handle starts with a grid barrier that can never open, so
+ * every block gives up after its wait limit (about two seconds), the kernel
+ * returns, and the solve reports GS2_ERR_TIMEOUT; the handle stays usable. */
+gs2_status gs2_test_stall_barrier(gs2_handle* h);
 
 /* Non-compact GS2 relaxation, Eq. (2) with inner JR sweeps Eq. (3)-(5):
  * x is read and overwritten (in/out), b is read.  outer_sweeps = n_t >= 0,
@@ -313,7 +325,8 @@ gs2_status cg_solve(gs2_handle* h, const double* b, double* x, double tol,
  * max_iters and preconditioner.  The systems' kernels are interleaved on
  * the first handle's stream so that small systems share the GPU.
  * infos[count] receives each system's result; the return value is OK if
- * every system converged, else the first failing status. */
+ * every system converged, else the first failing status.  Each system runs
+ * the restart-cycle graphs of gmres_solve's graph mode 1. */
 gs2_status gs2_batch_solve(gs2_handle* const* hs, const double* const* bs,
                            double* const* xs, int count, int restart,
                            double tol, int max_iters, const gs2_params* precond,
@@ -379,7 +392,9 @@ gs2_status gs2_check(gs2_handle* h);
  * budget and the device's free memory; each admitted request gets its own
  * stream, handle and resident Krylov state, so the work of requests that
  * arrive while others are running overlaps on the GPU.  A result is the
- * same, bit for bit, as the same solve run alone through gmres_solve; with
+ * same, bit for bit, as the same solve run alone through gmres_solve with
+ * graph mode 1 (the one-launch solver gmres_solve picks by default for a
+ * small system sums its inner products in another order); with
  * pack_rows set, a packed request's result is the same, bit for bit, as that
  * request solved alone as a pack of one (a pack partitions each system by
  * its own size), and equal to gmres_solve's up to the rounding of the inner

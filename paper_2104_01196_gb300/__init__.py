@@ -143,6 +143,7 @@ def load(path: str | None = None):
         "gs2_profile_filter": [P, ctypes.c_char_p],
         "gs2_check": [P],
         "gs2_set_graph_mode": [P, I],
+        "gs2_test_stall_barrier": [P],
         "gs2_autotune": [P],
         "gs2_profile_read": [P, ctypes.POINTER(_KStat), I, ctypes.POINTER(I)],
         "gs2_profile_reset": [P],
@@ -271,8 +272,13 @@ class Handle:
         return [(arr[0][i], arr[1][i], arr[2][i]) for i in range(lv.value)]
 
     def set_graph_mode(self, mode: int):
-        """0: automatic, 1: always replay Arnoldi steps as a CUDA graph, 2: never."""
+        """0: automatic (one launch for small systems, else graphs), 1: restart
+        cycles as CUDA graphs, 2: separate launches, 3: one launch."""
         _check(load().gs2_set_graph_mode(self.ptr, mode))
+
+    def test_stall_barrier(self):
+        """Test hook: the next one-launch solve's barrier never opens."""
+        _check(load().gs2_test_stall_barrier(self.ptr))
 
     def check(self):
         """Synchronise and raise if a kernel reported a device-side error."""

@@ -1362,8 +1362,14 @@ gs2_status gs2_autotune(gs2_handle* h) {
 }
 
 gs2_status gs2_set_graph_mode(gs2_handle* h, int mode) {
-  if (!h || mode < 0 || mode > 2) return GS2_ERR_INVALID_ARG;
+  if (!h || mode < 0 || mode > 3) return GS2_ERR_INVALID_ARG;
   h->graph_mode = mode;
+  return GS2_OK;
+}
+
+gs2_status gs2_test_stall_barrier(gs2_handle* h) {
+  if (!h) return GS2_ERR_INVALID_ARG;
+  h->stall_barrier = true;
   return GS2_OK;
 }
 

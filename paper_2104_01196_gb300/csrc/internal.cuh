@@ -92,7 +92,7 @@ struct KrylovState {
   int k;         // Arnoldi steps taken in the current cycle
   int iters;     // total Arnoldi steps
   int max_iters;
-  int pad_;
+  int cycles;    // restart cycles started (single-launch solver)
   double tol_abs;  // tol * ||b||
   double bnorm;
   double beta;     // ||r0|| of the cycle
@@ -186,7 +186,10 @@ struct gs2_handle {
   // CUDA graph of one restart cycle's Arnoldi steps (launch-bound small
   // systems): captured on a private stream, replayed there and joined to
   // `stream` with events; re-captured when the cycle's shape changes
-  int graph_mode = 0;  // 0: automatic (graphs), 1: always, 2: never
+  int graph_mode = 0;  // 0: automatic, 1: graphs, 2: separate launches, 3: one launch
+  unsigned* persist_bar = nullptr;  // grid barrier of the single-launch solver
+  double* persist_part = nullptr;   // its partial sums
+  bool stall_barrier = false;       // test hook: next one-launch solve's barrier never opens
   cudaStream_t gstream = nullptr;
   cudaEvent_t gev_in = nullptr, gev_out = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -365,6 +368,13 @@ gs2_status gmres_batch(gs2_handle* const* hs, const double* const* bs,
                        double* const* xs, int count, int m, double tol,
                        int max_iters, const gs2_params* p, gs2_solve_info* infos);
 void read_state(gs2_handle* h);
+
+// GMRES(m) of a small system as one cooperative launch (persist.cu): n up
+// to 65,536 rows (16,384 when chosen automatically), m <= 32, no
+// preconditioner, FP64 non-compact GS2 or JR
+bool persistent_eligible(const gs2_handle* h, int m, const gs2_params* p, bool automatic);
+gs2_status gmres_persistent(gs2_handle* h, const double* b, double* x, int m, double tol,
+                            int max_iters, const gs2_params* p, gs2_solve_info* info);
 // a kernel gave up a bounded wait: clear the device error word, throw
 void raise_device_error(gs2_handle* h);
 

@@ -665,6 +665,15 @@ struct GmresRun {
 
 gs2_status gmres_run(gs2_handle* h, const double* b, double* x, int m, double tol,
                      int max_iters, const gs2_params* p, gs2_solve_info* info) {
+  // small systems: the whole solve in one launch (automatic unless per-kernel
+  // profiling is on; graph mode 3 asks for it)
+  const bool forced = h->graph_mode == 3;
+  const bool automatic = h->graph_mode == 0 && !profiling_active(h);
+  if ((forced || automatic) && persistent_eligible(h, m, p, !forced))
+    return gmres_persistent(h, b, x, m, tol, max_iters, p, info);
+  if (h->graph_mode == 3)
+    GS2_THROW(GS2_ERR_INVALID_ARG, "the one-launch solver takes n <= 65536, restart <= 32 and "
+                                   "no, JR or FP64 non-compact GS2 preconditioning");
   GmresRun g;
   g.start(h, b, x, m, tol, max_iters, p);
   while (!g.done) {

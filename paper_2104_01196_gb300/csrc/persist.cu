@@ -1,0 +1,578 @@
+// Restarted GMRES(m) for small systems as one cooperative launch.
+//
+// A small system (a few thousand rows) runs the multi-kernel solve at the
+// launch rate: each of the ~11 kernels of an Arnoldi step costs a few
+// microseconds of launch and drain however little work it holds.  Here the
+// whole solve -- every restart cycle, the GS2 or JR preconditioner, the CGS2
+// Arnoldi steps, the Givens rotations and the true-residual checks -- runs in
+// one launch of at most 64 co-resident blocks (cooperative launch).  Rows are
+// owned by threads for the whole solve, so a phase that only touches its own
+// rows needs no synchronisation; a phase that gathers other rows' values
+// waits at a grid barrier first.  Inner products are block partial sums
+// followed by a barrier, after which every block sums all partials in the
+// same fixed order, so every block holds bitwise the same scalars: the
+// Hessenberg matrix, the rotations and the stopping decisions are computed
+// by every block in its own shared memory, and control flow is uniform over
+// the grid.  The barrier is a counter and a generation word in device
+// memory, spun with a bound: a block that waits too long records
+// GS2_ERR_TIMEOUT and every block leaves at its next barrier.
+#include <algorithm>
+#include <cmath>
+
+#include "arnoldi.cuh"
+#include "internal.cuh"
+#include "reduce.cuh"
+
+namespace gs2 {
+
+// Small blocks spread the rows over many SMs: one SM issues only 2 FP64
+// FMAs per clock, so rows per SM, not threads, set the time of a phase.
+constexpr int kPerThreads = 128;
+constexpr int kPerMaxBlocks = 128;
+constexpr long long kBarrierCycles = 4LL << 30;  // ~2 s at 2.07 GHz
+constexpr int64_t kPersistMaxRows = 1 << 16;
+// chosen automatically up to this size: measured on the 2D Laplacian with
+// GS2(1,1), GMRES(30): 4,096 rows 10.1 ms one launch vs 15.3 ms replayed
+// graphs, 16,384 rows 25.7 vs 27.9 ms, 62,500 rows 82 vs 76 ms
+constexpr int64_t kPersistAutoRows = 1 << 14;
+
+struct PersistArgs {
+  int n;
+  const int* Arp;
+  const int* Aci;
+  const double* Ava;
+  const int* Lrp;  // D^{-1} L
+  const int* Lci;
+  const double* Lva;
+  const int* Urp;  // D^{-1} U
+  const int* Uci;
+  const double* Uva;
+  const double* dinv;
+  const double* b;
+  double* x;
+  double* V;
+  double *w, *z, *r, *rh, *g0, *g1;
+  double* part;  // partial sums, value v of block k at part[v * nb + k]
+  int m;
+  double tol;
+  int max_iters;
+  int kind;  // GS2_PC_NONE, GS2_PC_GS2 or GS2_PC_JR
+  int outer, inner, dir;
+  double omega, gamma;
+  unsigned* bar;  // {arrivals, generation}
+  int* err;       // device error word
+  KrylovState* out;
+};
+
+// grid barrier (all blocks co-resident by the cooperative launch); false
+// when this block gave up waiting or another block had given up before
+__device__ bool grid_sync(const PersistArgs& a) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned* gen = a.bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    if (atomicAdd(a.bar, 1u) == gridDim.x - 1) {
+      a.bar[0] = 0;
+      __threadfence();
+      atomicAdd(a.bar + 1, 1u);
+    } else {
+      // tight spin (a sleep between polls delays the wake-up by more than
+      // the barrier itself costs), bounded by the clock
+      const long long t0 = clock64();
+      while (*gen == g) {
+        if (clock64() - t0 > kBarrierCycles || *(volatile int*)a.err) {
+          atomicCAS(a.err, 0, (int)GS2_ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+#define PSYNC()             \
+  do {                      \
+    if (!grid_sync(a)) return; \
+  } while (0)
+
+// rows owned by this thread
+#define FOR_ROWS(i) \
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x)
+
+// sum over the grid of one value per thread: block partial at `slot`, a
+// barrier, then every thread sums the partials in block order
+__device__ bool grid_sum1(const PersistArgs& a, double v, int slot, double* out) {
+  __shared__ double red[kPerThreads / 32];
+  __shared__ double tot;
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int q = 0; q < kPerThreads / 32; ++q) s += red[q];
+    a.part[(size_t)slot * gridDim.x + blockIdx.x] = s;
+  }
+  if (!grid_sync(a)) return false;
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < (int)gridDim.x; ++k) s += a.part[(size_t)slot * gridDim.x + k];
+    tot = s;
+  }
+  __syncthreads();
+  *out = tot;
+  return true;
+}
+
+// Block sums of nv <= NV per-thread values to part[v * nb + block]
+template <int NV>
+__device__ __forceinline__ void block_partials_p(const double (&acc)[NV], int nv, double* part,
+                                                 int nb) {
+  __shared__ double red[kPerThreads / 32][NV];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    if (v < nv) {
+      const double s = warp_sum(acc[v]);
+      if (lane == 0) red[wid][v] = s;
+    }
+  }
+  __syncthreads();
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < kPerThreads / 32; ++q) s += red[q][v];
+    part[(size_t)v * nb + blockIdx.x] = s;
+  }
+}
+
+// y_i = sum_k M_ik u_k for a CSR row
+__device__ __forceinline__ double row_dot(const int* rp, const int* ci, const double* va, int i,
+                                          const double* u) {
+  double s = 0.0;
+  for (int k = rp[i]; k < rp[i + 1]; ++k) s = fma(va[k], u[ci[k]], s);
+  return s;
+}
+
+// value slots of the partial-sum buffer
+constexpr int kSlotDots1 = 0, kSlotDots2 = 32, kSlotNorm = 64, kSlotB = 65, kSlotR = 66;
+constexpr int kPerSlots = 67;
+
+// CGS2 phases over the thread's rows, for jc <= JB basis vectors (JB a
+// multiple of 8, so at most 7 predicated-off products per row and vector)
+// w = A z and part = V^T w
+template <int JB>
+__device__ void phase_spmv_dots(const PersistArgs& a, int jc, double* part) {
+  double acc[JB];
+#pragma unroll
+  for (int q = 0; q < JB; ++q) acc[q] = 0.0;
+  FOR_ROWS(i) {
+    const double wi = row_dot(a.Arp, a.Aci, a.Ava, i, a.z);
+    a.w[i] = wi;
+#pragma unroll
+    for (int q = 0; q < JB; ++q)
+      if (q < jc) acc[q] = fma(a.V[(size_t)q * a.n + i], wi, acc[q]);
+  }
+  block_partials_p<JB>(acc, jc, part, gridDim.x);
+}
+
+// w -= V h and part = V^T w
+template <int JB>
+__device__ void phase_update_dots(const PersistArgs& a, int jc, const double* h, double* part) {
+  double acc[JB];
+#pragma unroll
+  for (int q = 0; q < JB; ++q) acc[q] = 0.0;
+  FOR_ROWS(i) {
+    double wn = a.w[i];
+#pragma unroll
+    for (int q = 0; q < JB; ++q)
+      if (q < jc) wn = fma(a.V[(size_t)q * a.n + i], -h[q], wn);
+    a.w[i] = wn;
+#pragma unroll
+    for (int q = 0; q < JB; ++q)
+      if (q < jc) acc[q] = fma(a.V[(size_t)q * a.n + i], wn, acc[q]);
+  }
+  block_partials_p<JB>(acc, jc, part, gridDim.x);
+}
+
+// w -= V h; returns this thread's sum of w_i^2
+template <int JB>
+__device__ double phase_update_norm(const PersistArgs& a, int jc, const double* h) {
+  double t = 0.0;
+  FOR_ROWS(i) {
+    double wn = a.w[i];
+#pragma unroll
+    for (int q = 0; q < JB; ++q)
+      if (q < jc) wn = fma(a.V[(size_t)q * a.n + i], -h[q], wn);
+    a.w[i] = wn;
+    t = fma(wn, wn, t);
+  }
+  return t;
+}
+
+#define PHASE_JB(jc, CALL8, CALL16, CALL24, CALL32) \
+  switch (((jc) + 7) >> 3) {                        \
+    case 1: CALL8; break;                           \
+    case 2: CALL16; break;                          \
+    case 3: CALL24; break;                          \
+    default: CALL32; break;                         \
+  }
+
+// z = M^{-1} v from z = 0: GS2 half sweeps (Eq. (2)-(5), damped) or JR
+// sweeps, the arithmetic of the multi-kernel path row for row.  v complete
+// on entry; z complete on a true return.
+__device__ bool precond(const PersistArgs& a, const double* v, double* z) {
+  if (a.kind == GS2_PC_NONE) {
+    FOR_ROWS(i) z[i] = v[i];
+    return grid_sync(a);
+  }
+  FOR_ROWS(i) a.rh[i] = a.dinv[i] * v[i];
+  if (a.kind == GS2_PC_JR) {
+    // first sweep from zero: z = omega D^{-1} v; then z + omega D^{-1} (v - A z)
+    double* cur = z;
+    double* nxt = a.g0;
+    FOR_ROWS(i) cur[i] = a.omega * a.rh[i];
+    for (int s = 1; s < a.outer; ++s) {
+      if (!grid_sync(a)) return false;
+      FOR_ROWS(i) {
+        const double t = row_dot(a.Arp, a.Aci, a.Ava, i, cur);
+        nxt[i] = cur[i] + a.omega * (a.dinv[i] * (v[i] - t));
+      }
+      double* tmp = cur;
+      cur = nxt;
+      nxt = tmp;
+    }
+    if (cur != z) {
+      // every block must be done gathering from z before it is overwritten
+      if (!grid_sync(a)) return false;
+      FOR_ROWS(i) z[i] = cur[i];
+    }
+    return grid_sync(a);
+  }
+  const bool damped = a.gamma != 1.0;
+  bool zero = true;
+  for (int s = 0; s < a.outer; ++s) {
+    for (int half = 0; half < 2; ++half) {
+      const bool fwd = half == 0;
+      if (fwd && a.dir == GS2_BACKWARD) continue;
+      if (!fwd && a.dir == GS2_FORWARD) continue;
+      const int* Tp = fwd ? a.Lrp : a.Urp;
+      const int* Tc = fwd ? a.Lci : a.Uci;
+      const double* Tv = fwd ? a.Lva : a.Uva;
+      if (!zero) {
+        if (!grid_sync(a)) return false;  // z complete
+        FOR_ROWS(i) a.rh[i] = a.dinv[i] * (v[i] - row_dot(a.Arp, a.Aci, a.Ava, i, z));
+      }
+      if (!grid_sync(a)) return false;  // rh complete
+      if (a.inner == 0) {
+        FOR_ROWS(i) z[i] = zero ? a.omega * a.rh[i] : z[i] + a.omega * a.rh[i];
+      }
+      const double* gin = a.rh;
+      for (int k = 0; k < a.inner; ++k) {
+        const bool last = k == a.inner - 1;
+        double* gout = (k % 2 == 0) ? a.g0 : a.g1;
+        FOR_ROWS(i) {
+          const double t = row_dot(Tp, Tc, Tv, i, gin);
+          double go = a.rh[i] - a.omega * t;
+          if (damped) go = (1.0 - a.gamma) * gin[i] + a.gamma * go;
+          if (!last) gout[i] = go;
+          else z[i] = zero ? a.omega * go : z[i] + a.omega * go;
+        }
+        if (!last) {
+          if (!grid_sync(a)) return false;
+          gin = gout;
+        }
+      }
+      zero = false;
+    }
+  }
+  return grid_sync(a);
+}
+
+template <int MAXK>
+__global__ void __launch_bounds__(kPerThreads, 1)
+k_gmres_persistent(PersistArgs a) {
+  // Krylov scalars, identical in every block
+  __shared__ double Hs[(MAXK + 1) * MAXK];  // column j at Hs[j * (m + 1)]
+  __shared__ double cs_s[MAXK + 1], sn_s[MAXK + 1], g_s[MAXK + 1], y_s[MAXK + 1];
+  __shared__ double h1[MAXK], h2[MAXK];
+  __shared__ int sh_flag;
+  const int n = a.n, m = a.m, ldh = m + 1;
+  const int nb = gridDim.x;
+  double* part = a.part;
+  int iters = 0, cycles = 0, status = GS2_OK;
+  double bnorm = 0.0, beta = 0.0;
+
+  // ||b||
+  double t = 0.0;
+  FOR_ROWS(i) t = fma(a.b[i], a.b[i], t);
+  if (!grid_sum1(a, t, kSlotB, &t)) return;
+  bnorm = sqrt(t);
+  if (bnorm == 0.0 || isnan(bnorm) || isinf(bnorm)) {
+    if (bnorm == 0.0) FOR_ROWS(i) a.x[i] = 0.0;
+    else status = GS2_ERR_NAN;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      a.out->iters = 0;
+      a.out->cycles = 0;
+      a.out->status = status;
+      a.out->bnorm = bnorm;
+      a.out->beta = bnorm == 0.0 ? 0.0 : NAN;
+    }
+    return;
+  }
+  const double tol_abs = a.tol * bnorm;
+  bool breakdown = false;
+  for (;;) {
+    // true residual r = b - A x and its norm (x complete here)
+    t = 0.0;
+    FOR_ROWS(i) {
+      const double ri = a.b[i] - row_dot(a.Arp, a.Aci, a.Ava, i, a.x);
+      a.r[i] = ri;
+      t = fma(ri, ri, t);
+    }
+    if (!grid_sum1(a, t, kSlotR, &t)) return;
+    beta = sqrt(t);
+    const double relres = beta / bnorm;
+    if (isnan(beta) || isinf(beta) || status == GS2_ERR_NAN) {
+      status = GS2_ERR_NAN;
+      break;
+    }
+    if (relres <= a.tol) {
+      status = GS2_OK;
+      break;
+    }
+    if (breakdown) {
+      status = GS2_ERR_BREAKDOWN;
+      break;
+    }
+    if (iters >= a.max_iters) {
+      status = GS2_ERR_NOT_CONVERGED;
+      break;
+    }
+    ++cycles;
+    // cycle start: v_0 = r / beta, g = (beta, 0, ...)
+    const double ib = 1.0 / beta;
+    FOR_ROWS(i) a.V[i] = a.r[i] * ib;
+    if (threadIdx.x <= m) g_s[threadIdx.x] = threadIdx.x == 0 ? beta : 0.0;
+    int k = 0;
+    for (int j = 0; j < m; ++j) {
+      const double* vj = a.V + (size_t)j * n;
+      if (!precond(a, vj, a.z)) return;
+      const int jc = j + 1;
+      // w = A z and the first Gram-Schmidt pass V^T w
+      double* p1 = part + (size_t)kSlotDots1 * nb;
+      PHASE_JB(jc, phase_spmv_dots<8>(a, jc, p1), phase_spmv_dots<16>(a, jc, p1),
+               phase_spmv_dots<24>(a, jc, p1), phase_spmv_dots<32>(a, jc, p1));
+      if (!grid_sync(a)) return;
+      if (threadIdx.x < jc) {
+        double s = 0.0;
+        for (int b = 0; b < nb; ++b) s += part[(size_t)(kSlotDots1 + threadIdx.x) * nb + b];
+        h1[threadIdx.x] = s;
+      }
+      __syncthreads();
+      // w -= V h1 and the second pass V^T w
+      double* p2 = part + (size_t)kSlotDots2 * nb;
+      PHASE_JB(jc, phase_update_dots<8>(a, jc, h1, p2), phase_update_dots<16>(a, jc, h1, p2),
+               phase_update_dots<24>(a, jc, h1, p2), phase_update_dots<32>(a, jc, h1, p2));
+      if (!grid_sync(a)) return;
+      if (threadIdx.x < jc) {
+        double s = 0.0;
+        for (int b = 0; b < nb; ++b) s += part[(size_t)(kSlotDots2 + threadIdx.x) * nb + b];
+        h2[threadIdx.x] = s;
+      }
+      __syncthreads();
+      // w -= V h2 and ||w||^2
+      PHASE_JB(jc, t = phase_update_norm<8>(a, jc, h2), t = phase_update_norm<16>(a, jc, h2),
+               t = phase_update_norm<24>(a, jc, h2), t = phase_update_norm<32>(a, jc, h2));
+      if (!grid_sum1(a, t, kSlotNorm, &t)) return;
+      // Givens step j (every block, thread 0, on its own copies)
+      if (threadIdx.x == 0) {
+        double* col = Hs + (size_t)j * ldh;
+        for (int q = 0; q < jc; ++q) col[q] = h1[q] + h2[q];
+        const double hn = sqrt(t);
+        col[j + 1] = hn;
+        for (int q = 0; q < j; ++q) {
+          const double u = col[q], v = col[q + 1];
+          col[q] = cs_s[q] * u + sn_s[q] * v;
+          col[q + 1] = -sn_s[q] * u + cs_s[q] * v;
+        }
+        const double f = col[j], g = col[j + 1];
+        double c, sg, rr;
+        if (g == 0.0) {
+          c = 1.0; sg = 0.0; rr = f;
+        } else if (f == 0.0) {
+          c = 0.0; sg = g > 0.0 ? 1.0 : -1.0; rr = fabs(g);
+        } else {
+          const double d = sqrt(f * f + g * g);
+          c = fabs(f) / d;
+          rr = f > 0.0 ? d : -d;
+          sg = g / rr;
+        }
+        cs_s[j] = c;
+        sn_s[j] = sg;
+        col[j] = rr;
+        col[j + 1] = 0.0;
+        const double gj = g_s[j];
+        g_s[j + 1] = -sg * gj;
+        g_s[j] = c * gj;
+        const double est = fabs(-sg * gj);
+        int stop = 0;
+        if (isnan(est) || isnan(hn) || isinf(hn)) {
+          status = GS2_ERR_NAN;
+          stop = 1;
+        } else if (hn == 0.0) {
+          breakdown = true;
+          stop = 1;
+        } else if (est <= tol_abs || iters + 1 >= a.max_iters) {
+          stop = 1;
+        }
+        sh_flag = stop | (status == GS2_ERR_NAN ? 2 : 0) | (breakdown ? 4 : 0);
+        y_s[0] = 1.0 / hn;  // scratch: H(j+1, j)^{-1}
+      }
+      __syncthreads();
+      ++iters;
+      k = jc;
+      const int fl = sh_flag;
+      if (fl & 2) status = GS2_ERR_NAN;
+      if (fl & 4) breakdown = true;
+      if (fl & 1) break;
+      if (j + 1 < m) {
+        const double ih = y_s[0];
+        double* vn = a.V + (size_t)(j + 1) * n;
+        FOR_ROWS(i) vn[i] = a.w[i] * ih;
+      }
+    }
+    // x += M^{-1} V y, y = R^{-1} g over the k steps
+    if (threadIdx.x == 0) {
+      for (int q = 0; q < k; ++q) y_s[q] = g_s[q];
+      for (int q = k - 1; q >= 0; --q) {
+        const double* cq = Hs + (size_t)q * ldh;
+        const double yq = y_s[q] / cq[q];
+        y_s[q] = yq;
+        for (int l = 0; l < q; ++l) y_s[l] -= cq[l] * yq;
+      }
+    }
+    __syncthreads();
+    FOR_ROWS(i) {
+      double s = 0.0;
+      for (int q = 0; q < k; ++q) s = fma(a.V[(size_t)q * n + i], y_s[q], s);
+      a.w[i] = s;
+    }
+    if (!precond(a, a.w, a.z)) return;
+    FOR_ROWS(i) a.x[i] = a.x[i] + a.z[i];
+    if (!grid_sync(a)) return;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.out->iters = iters;
+    a.out->cycles = cycles;
+    a.out->status = status;
+    a.out->bnorm = bnorm;
+    a.out->beta = beta;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+bool persistent_eligible(const gs2_handle* h, int m, const gs2_params* p, bool automatic) {
+  if (h->n == 0 || h->n > (automatic ? kPersistAutoRows : kPersistMaxRows) || m > 32)
+    return false;
+  if (!p || p->kind == GS2_PC_NONE) return true;
+  if (p->parts > 1 || p->local_sweeps > 1) return false;
+  if (p->kind == GS2_PC_JR) return true;
+  return p->kind == GS2_PC_GS2 && p->precision == GS2_FP64 && p->form == GS2_NONCOMPACT;
+}
+
+template <int MAXK>
+static void launch_persistent(gs2_handle* h, PersistArgs& a, int nb) {
+  void* args[] = {&a};
+  GS2_CUDA(cudaLaunchCooperativeKernel((const void*)k_gmres_persistent<MAXK>, nb, kPerThreads,
+                                       args, 0, h->stream));
+  GS2_LAUNCH_CHECK();
+}
+
+gs2_status gmres_persistent(gs2_handle* h, const double* b, double* x, int m, double tol,
+                            int max_iters, const gs2_params* p, gs2_solve_info* info) {
+  ensure_krylov(h, m);
+  if (!h->persist_bar) {
+    h->persist_bar = (unsigned*)h->dalloc(4 * sizeof(unsigned));
+    // its own partial-sum buffer: kPerSlots values per block, for the most
+    // blocks a launch can have (the handle's buffer is sized for the
+    // multi-kernel path's grids, which a small system keeps small)
+    h->persist_part = (double*)h->dalloc(sizeof(double) * kPerSlots * kPerMaxBlocks);
+  }
+  const gs2_params* pc = (p && p->kind != GS2_PC_NONE) ? p : nullptr;
+  const int n = (int)h->n;
+  // blocks: one row per thread up to 128 blocks, at most what stays resident
+  int nb = (int)std::min<int64_t>(kPerMaxBlocks, (h->n + kPerThreads - 1) / kPerThreads);
+  {
+    int per_sm = 0;
+    const void* fn = m <= 8 ? (const void*)k_gmres_persistent<8>
+                            : (m <= 16 ? (const void*)k_gmres_persistent<16>
+                                       : (const void*)k_gmres_persistent<32>);
+    GS2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPerThreads, 0));
+    nb = std::max(1, std::min(nb, per_sm * h->nsm));
+  }
+  PersistArgs a{};
+  a.n = n;
+  a.Arp = h->A.rp;
+  a.Aci = h->A.ci;
+  a.Ava = h->A.va;
+  a.Lrp = h->L.rp;
+  a.Lci = h->L.ci;
+  a.Lva = h->L.va;
+  a.Urp = h->U.rp;
+  a.Uci = h->U.ci;
+  a.Uva = h->U.va;
+  a.dinv = h->dinv;
+  a.b = b;
+  a.x = x;
+  a.V = h->V;
+  a.w = h->w;
+  a.z = h->z;
+  a.r = h->r;
+  a.rh = h->rhat;
+  a.g0 = h->g0;
+  a.g1 = h->g1;
+  a.part = h->persist_part;
+  if (nb > kPerMaxBlocks) GS2_THROW(GS2_ERR_CUDA, "one-launch grid above its partial-sum buffer");
+  a.m = m;
+  a.tol = tol;
+  a.max_iters = max_iters;
+  a.kind = pc ? pc->kind : GS2_PC_NONE;
+  a.outer = pc ? std::max(1, pc->outer) : 1;
+  a.inner = pc ? pc->inner : 0;
+  a.dir = pc ? pc->direction : GS2_FORWARD;
+  a.omega = pc ? pc->omega : 1.0;
+  a.gamma = pc ? pc->gamma : 1.0;
+  a.bar = h->persist_bar;
+  a.err = h->dev_err;
+  a.out = h->st;
+  GS2_CUDA(cudaMemsetAsync(h->persist_bar, 0, 4 * sizeof(unsigned), h->stream));
+  if (h->stall_barrier) {
+    // test hook: an arrival count no block can complete, so every block's
+    // bounded wait runs out and the solve reports GS2_ERR_TIMEOUT
+    h->stall_barrier = false;
+    GS2_CUDA(cudaMemsetAsync((char*)h->persist_bar + 3, 0x40, 1, h->stream));  // 2^30
+  }
+  {
+    KernelTimer tm(h, "gmres_persistent", 0.0);
+    if (m <= 8) launch_persistent<8>(h, a, nb);
+    else if (m <= 16) launch_persistent<16>(h, a, nb);
+    else launch_persistent<32>(h, a, nb);
+  }
+  read_state(h);  // raises GS2_ERR_TIMEOUT if a barrier gave up
+  const KrylovState& st = *h->st_host;
+  gs2_solve_info loc{st.iters, st.cycles, st.status, 0.0};
+  loc.true_relres = st.bnorm == 0.0 ? 0.0 : st.beta / st.bnorm;
+  if (info) *info = loc;
+  return (gs2_status)st.status;
+}
+
+}  // namespace gs2

@@ -315,7 +315,9 @@ def test_batch_results_equal_alone(g):
     for h, p in zip(hs, probs):
         x = dev(np.zeros(p.n))
         torch.cuda.synchronize()
+        h.set_graph_mode(1)  # the cycle-graph path a batch runs (not the one-launch solver)
         info = g.gmres_solve(h, dev(p.b), x, 30, 1e-8, 3000, pc)
+        h.set_graph_mode(0)
         alone.append((info, host(x)))
     bs = [dev(p.b) for p in probs]
     xs = [dev(np.zeros(p.n)) for p in probs]

@@ -1,0 +1,161 @@
+"""GPU parity of the one-launch GMRES solver for small systems (the whole
+restarted solve in one cooperative launch): iteration counts within +-1 of
+the oracle and of the multi-kernel path for every preconditioner it takes,
+the solver statuses, run-to-run reproducibility, automatic selection, and
+the bounded grid barrier giving up with GS2_ERR_TIMEOUT instead of hanging.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2104_01196_gb300 import problems as P
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    import torch  # noqa: F401
+
+    from paper_2104_01196_gb300 import build as B
+    B.build()
+    import paper_2104_01196_gb300 as gs2
+    gs2.load()
+    return gs2
+
+
+def dev(v):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(v, dtype=np.float64)).cuda()
+
+
+def host(t):
+    import torch
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+PROBS = {
+    "poisson2d_64": P.poisson2d(64),
+    "random_3000": P.random_system(3000, 61, mean_offdiag=6.0, dominance=1.1),
+    "convdiff3d_12": P.convdiff3d(12),
+    "elasticity3d_4": P.elasticity3d(4),
+    "poisson3d_40": P.poisson3d(40),
+}
+PCS = {
+    "none": (None, dict(pc_kind=oracle.PC_NONE)),
+    "gs2_fwd_1_1": (dict(kind="gs2", outer=1, inner=1), dict(pc_kind=oracle.PC_GS2)),
+    "sgs2_1_2_damped": (dict(kind="gs2", outer=1, inner=2, omega=0.9, gamma=0.8,
+                             direction="symmetric"),
+                        dict(pc_kind=oracle.PC_GS2, pc_inner=2, pc_omega=0.9, pc_gamma=0.8,
+                             pc_direction=oracle.SYMMETRIC)),
+    "gs2_bwd_2_0": (dict(kind="gs2", outer=2, inner=0, direction="backward"),
+                    dict(pc_kind=oracle.PC_GS2, pc_outer=2, pc_inner=0,
+                         pc_direction=oracle.BACKWARD)),
+    "jr_3_w0.8": (dict(kind="jr", outer=3, omega=0.8),
+                  dict(pc_kind=oracle.PC_JR, pc_outer=3, pc_omega=0.8)),
+    # an even number of JR sweeps ends in the second buffer (a copy back)
+    "jr_4": (dict(kind="jr", outer=4), dict(pc_kind=oracle.PC_JR, pc_outer=4)),
+    "jr_2_w0.9": (dict(kind="jr", outer=2, omega=0.9),
+                  dict(pc_kind=oracle.PC_JR, pc_outer=2, pc_omega=0.9)),
+}
+
+
+@pytest.mark.parametrize("name", list(PROBS))
+@pytest.mark.parametrize("pc", list(PCS))
+@pytest.mark.parametrize("restart", [5, 30])
+def test_one_launch_matches_oracle_and_multi_kernel_path(g, name, pc, restart):
+    pr = PROBS[name]
+    gp, op = PCS[pc]
+    if name.startswith("elasticity") and (pc in ("none", "gs2_fwd_1_1", "jr_3_w0.8", "jr_4",
+                                                "jr_2_w0.9")
+                                          or restart == 5):
+        # stagnation; and GMRES(5) on elasticity is rounding-sensitive: the
+        # multi-kernel path takes 517 steps there, the oracle 374
+        pytest.skip("stagnating or rounding-sensitive on elasticity")
+    prm = g.params(**gp) if gp else None
+    h = g.gs2_setup(pr.A)
+    h.set_graph_mode(3)
+    x = dev(np.zeros(pr.n))
+    info = g.gmres_solve(h, dev(pr.b), x, restart, 1e-8, 6000, prm)
+    _, oinfo = oracle.gmres(pr.A, pr.b, restart=restart, tol=1e-8, max_iters=6000, **op)
+    assert info.status == 0 and oinfo.status == 0
+    assert abs(info.iters - oinfo.iters) <= 1, (info.iters, oinfo.iters)
+    r = np.linalg.norm(pr.b - oracle.spmv(pr.A, host(x))) / np.linalg.norm(pr.b)
+    assert r <= 1e-8 and abs(info.true_relres - r) <= 1e-12
+    h.set_graph_mode(1)
+    xg = dev(np.zeros(pr.n))
+    ig = g.gmres_solve(h, dev(pr.b), xg, restart, 1e-8, 6000, prm)
+    assert abs(ig.iters - info.iters) <= 1
+    assert np.linalg.norm(host(xg) - host(x)) <= 1e-6 * np.linalg.norm(host(x))
+
+
+def test_one_launch_statuses_and_reproducibility(g):
+    pr = P.poisson2d(40)
+    h = g.gs2_setup(pr.A)
+    h.set_graph_mode(3)
+    prm = g.params("gs2", 1, 1)
+    x1, x2 = dev(np.zeros(pr.n)), dev(np.zeros(pr.n))
+    i1 = g.gmres_solve(h, dev(pr.b), x1, 30, 1e-8, 3000, prm)
+    i2 = g.gmres_solve(h, dev(pr.b), x2, 30, 1e-8, 3000, prm)
+    assert i1.iters == i2.iters and i1.cycles == i2.cycles
+    assert np.array_equal(host(x1), host(x2))
+    # iteration limit
+    info = g.gmres_solve(h, dev(pr.b), dev(np.zeros(pr.n)), 10, 1e-12, 7, prm)
+    assert info.status == 5 and info.iters == 7
+    # NaN in b
+    b = pr.b.copy()
+    b[3] = np.nan
+    assert g.gmres_solve(h, dev(b), dev(np.zeros(pr.n)), 10, 1e-8, 50, prm).status == 7
+    # zero right-hand side: x = 0, no step
+    x = dev(np.ones(pr.n))
+    info = g.gmres_solve(h, dev(np.zeros(pr.n)), x, 10, 1e-8, 50, prm)
+    assert info.status == 0 and info.iters == 0 and np.all(host(x) == 0.0)
+    # warm start at the solution: no step
+    info = g.gmres_solve(h, dev(pr.b), dev(pr.x_true), 10, 1e-8, 50, prm)
+    assert info.status == 0 and info.iters == 0
+    # a diagonal matrix with JR(1): M^{-1} = D^{-1} = A^{-1}, so the first
+    # step is a lucky breakdown (H(1,0) = 0) and the solve has converged
+    n = 300
+    d = 1.0 + P.uniform01(9, n)
+    D = (np.arange(n + 1, dtype=np.int64), np.arange(n, dtype=np.int32), d)
+    hd = g.gs2_setup(D)
+    hd.set_graph_mode(3)
+    v = P.uniform_pm1(10, n)
+    x = dev(np.zeros(n))
+    info = g.gmres_solve(hd, dev(v), x, 30, 1e-10, 100, g.params("jr", 1))
+    assert info.status == 0 and info.iters == 1
+    assert np.linalg.norm(host(x) - v / d) <= 1e-12 * np.linalg.norm(v / d)
+
+
+def test_automatic_selection_uses_one_launch_for_small_systems(g):
+    pr = P.poisson2d(64)
+    h = g.gs2_setup(pr.A)
+    b, x = dev(pr.b), dev(np.zeros(pr.n))
+    g.gmres_solve(h, b, x, 30, 1e-8, 3000, g.params("gs2", 1, 1))  # warm
+    c0 = g.launch_count()
+    info = g.gmres_solve(h, b, dev(np.zeros(pr.n)), 30, 1e-8, 3000, g.params("gs2", 1, 1))
+    assert info.status == 0 and info.iters > 100
+    assert g.launch_count() - c0 <= 2, g.launch_count() - c0
+    # not eligible: restart above 32, FP32 sweeps; mode 3 refuses them
+    h.set_graph_mode(3)
+    with pytest.raises(g.GS2Error):
+        g.gmres_solve(h, b, x, 40, 1e-8, 100, g.params("gs2", 1, 1))
+    with pytest.raises(g.GS2Error):
+        g.gmres_solve(h, b, x, 30, 1e-8, 100, g.params("gs2", 1, 1, precision="fp32"))
+
+
+def test_stalled_barrier_times_out_and_the_handle_recovers(g):
+    """The grid barrier's wait is bounded: with an arrival count no block can
+    complete, every block gives up (about two seconds), the solve reports
+    GS2_ERR_TIMEOUT, and the next solve on the handle is normal."""
+    pr = P.poisson2d(32)
+    h = g.gs2_setup(pr.A)
+    h.set_graph_mode(3)
+    h.test_stall_barrier()
+    with pytest.raises(g.GS2Error) as e:
+        g.gmres_solve(h, dev(pr.b), dev(np.zeros(pr.n)), 30, 1e-8, 500, g.params("gs2", 1, 1))
+    assert e.value.status == 8
+    info = g.gmres_solve(h, dev(pr.b), dev(np.zeros(pr.n)), 30, 1e-8, 500,
+                         g.params("gs2", 1, 1))
+    assert info.status == 0

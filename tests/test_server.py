@@ -50,6 +50,7 @@ def _mix():
 def _alone(pr, pc):
     import torch
     h = gs2.gs2_setup(pr.A)
+    h.set_graph_mode(1)  # the cycle-graph path the server runs
     x = torch.zeros(pr.n, dtype=torch.float64, device="cuda")
     b = torch.from_numpy(pr.b).cuda()
     info = gs2.gmres_solve(h, b, x, 30, 1e-8, 4000, pc)
