@@ -21,7 +21,6 @@
 #include <cmath>
 #include <cstring>
 #include <limits>
-#include <mutex>
 #include <string>
 
 #include "arnoldi.cuh"

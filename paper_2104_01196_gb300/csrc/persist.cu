@@ -96,11 +96,6 @@ __device__ bool grid_sync(const PersistArgs& a) {
   return ok != 0;
 }
 
-#define PSYNC()             \
-  do {                      \
-    if (!grid_sync(a)) return; \
-  } while (0)
-
 // rows owned by this thread
 #define FOR_ROWS(i) \
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x)
