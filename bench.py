@@ -326,7 +326,7 @@ def run_ours(args):
     h = gs2.gs2_setup(pr.A, stream=stream.cuda_stream)
     if not args.no_autotune:
         h.autotune()  # tile shapes of A and the triangles (setup time, untimed)
-    shapes = {k: v for k, v in h.stats().items() if k.startswith(("tpr", "rpt"))}
+    shapes = {k: v for k, v in h.stats().items() if k.startswith(("tpr", "rpt", "sell"))}
     pc = gs2.params("gs2", 1, 1, direction="symmetric")
     with torch.cuda.stream(stream):
         b = torch.from_numpy(pr.b).cuda()

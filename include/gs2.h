@@ -123,6 +123,7 @@ typedef struct {
   int tpr_a, tpr_tri;             /* lanes per row of the tile kernels (A, D^-1 L) */
   int rpt_a, rpt_tri;             /* rows per lane group of the tile kernels */
   int colors;                     /* 0 until a multicolour call */
+  int sell_a, sell_tri;           /* 1: A / the triangles run on the sliced-ELL layout */
 } gs2_handle_stats;
 
 typedef struct gs2_handle gs2_handle;
@@ -151,11 +152,13 @@ gs2_status gs2_set_stream(gs2_handle* h, void* stream);
 
 gs2_status gs2_get_stats(const gs2_handle* h, gs2_handle_stats* out);
 
-/* Autotune the tile shape of A, D^{-1}L and D^{-1}U: for each matrix, time
+/* Autotune the row kernels of A, D^{-1}L and D^{-1}U: for each matrix, time
  * its most frequent kernel (the residual for A, the inner sweep with the x
- * update for a triangle) for every candidate shape (lanes per row K around
- * the row-length heuristic, rows per lane group 1 or 2) and keep the
- * heuristic shape unless another is at least 2% faster.  Results are
+ * update for a triangle) for every candidate row-tile shape (lanes per row
+ * K around the row-length heuristic, rows per lane group 1 or 2), keeping
+ * the heuristic shape unless another is at least 2% faster, and, for a
+ * matrix with a sliced-ELL copy, keep that layout unless the best tile
+ * shape beats it by 2%.  Results are
  * cached by matrix class (size to a factor sqrt(2), mean row length), so
  * matrices of a class already measured are re-tiled without timing.  The
  * numerical results do not change (rows are reduced in the same order for

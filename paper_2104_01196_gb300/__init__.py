@@ -69,7 +69,8 @@ class _Stats(ctypes.Structure):
                 ("nnz_upper", ctypes.c_int64), ("levels_lower", ctypes.c_int),
                 ("levels_upper", ctypes.c_int), ("device_bytes", ctypes.c_int64),
                 ("tpr_a", ctypes.c_int), ("tpr_tri", ctypes.c_int),
-                ("rpt_a", ctypes.c_int), ("rpt_tri", ctypes.c_int), ("colors", ctypes.c_int)]
+                ("rpt_a", ctypes.c_int), ("rpt_tri", ctypes.c_int), ("colors", ctypes.c_int),
+                ("sell_a", ctypes.c_int), ("sell_tri", ctypes.c_int)]
 
 
 class _KStat(ctypes.Structure):

@@ -341,7 +341,7 @@ static void prepare_lowprec(gs2_handle* h, DevCsr& M, const HostTri& T, int prec
     for (int k = 0; k < M.nnz; ++k) v[k] = (float)T.va[k];
     M.va32 = (float*)h->dalloc(sizeof(float) * nz);
     h->h2d(M.va32, v.data(), sizeof(float) * nz);
-    if (M.sell) {
+    if (M.sell_chunks > 0) {  // the layout exists (the autotuner may turn it off and on)
       const size_t slots = M.sell_slots;
       M.sell_va32 = (float*)h->dalloc(sizeof(float) * slots);
       h->dzero(M.sell_va32, sizeof(float) * slots);
@@ -362,7 +362,7 @@ static void prepare_lowprec(gs2_handle* h, DevCsr& M, const HostTri& T, int prec
     M.scale16 = (float*)h->dalloc(sizeof(float) * std::max(M.n, 1));
     h->h2d(M.va16, v.data(), sizeof(__half) * nz);
     h->h2d(M.scale16, s.data(), sizeof(float) * M.n);
-    if (M.sell) {
+    if (M.sell_chunks > 0) {  // the layout exists (the autotuner may turn it off and on)
       const size_t slots = M.sell_slots;
       M.sell_va16 = (__half*)h->dalloc(sizeof(__half) * slots);
       h->dzero(M.sell_va16, sizeof(__half) * slots);
@@ -652,23 +652,39 @@ void upload_matrix(gs2_handle* h, DevCsr& M, int n, const std::vector<int>& rp,
 // autotuner: tile shape (lanes per row K, rows per lane group RPT) per matrix
 // ---------------------------------------------------------------------------
 
-// Best shapes found so far, by (matrix role, n to a factor sqrt(2), mean row
-// length to a quarter): matrices of the same class reuse a measurement.
+// Best choices found so far -- row-tile shape (K, RPT) and whether the
+// sliced-ELL layout is used -- by (matrix role, n to a factor sqrt(2), mean
+// row length to a quarter): matrices of the same class reuse a measurement.
+struct TuneChoice {
+  int K, RPT;
+  bool sell;
+};
 static std::mutex g_tune_mu;
-static std::map<std::tuple<int, int, int>, std::pair<int, int>> g_tune;
+static std::map<std::tuple<int, int, int>, TuneChoice> g_tune;
 
 static void tune_matrix(gs2_handle* h, DevCsr& M, const std::vector<int>& rp, int role) {
   if (M.n == 0 || M.nnz == 0) return;
   const auto key = std::make_tuple(role, (int)std::lround(2.0 * std::log2((double)M.n)),
                                    (int)std::lround(4.0 * M.mean_row));
+  // whether M has a sliced-ELL copy at all (qualifying short rows)
+  const bool has_sell = M.sell_chunks > 0;
   {
     std::lock_guard<std::mutex> g(g_tune_mu);
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
-      if (it->second != std::make_pair(M.tpr, M.rpt))
-        retile(h, M, rp, it->second.first, it->second.second);
+      const TuneChoice& c = it->second;
+      if (c.K != M.tpr || c.RPT != M.rpt) retile(h, M, rp, c.K, c.RPT);
+      M.sell = has_sell && c.sell;
       return;
     }
+  }
+  // the sliced-ELL layout against the best row-tile shape: SELL is kept
+  // unless the tiles are at least 2% faster
+  float sell_ms = 0.f;
+  if (has_sell) {
+    M.sell = true;
+    sell_ms = time_tile_probe(h, M, 5, role);
+    M.sell = false;
   }
   // candidates around the mean-row-length heuristic
   const int kh = choose_lanes(M.mean_row);
@@ -692,8 +708,9 @@ static void tune_matrix(gs2_handle* h, DevCsr& M, const std::vector<int>& rp, in
     }
   }
   retile(h, M, rp, best.first, best.second);
+  M.sell = has_sell && !(best_ms < 0.98f * sell_ms);
   std::lock_guard<std::mutex> g(g_tune_mu);
-  g_tune[key] = best;
+  g_tune[key] = TuneChoice{best.first, best.second, M.sell};
 }
 
 static bool is_device_ptr(const void* p) {
@@ -1065,6 +1082,8 @@ gs2_status gs2_get_stats(const gs2_handle* h, gs2_handle_stats* out) {
   out->rpt_a = h->A.rpt;
   out->rpt_tri = h->L.rpt;
   out->colors = h->colors_ready ? (int)h->colors.size() : 0;
+  out->sell_a = h->A.sell ? 1 : 0;
+  out->sell_tri = h->L.sell ? 1 : 0;
   return GS2_OK;
 }
 
