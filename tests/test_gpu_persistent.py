@@ -159,3 +159,45 @@ def test_stalled_barrier_times_out_and_the_handle_recovers(g):
     info = g.gmres_solve(h, dev(pr.b), dev(np.zeros(pr.n)), 30, 1e-8, 500,
                          g.params("gs2", 1, 1))
     assert info.status == 0
+
+
+@pytest.mark.parametrize("restart", [1, 2, 8, 9, 32])
+def test_one_launch_restart_edges(g, restart):
+    """Restart lengths at and around the register-block boundaries (the CGS2
+    phases round the basis size up to a multiple of 8; m <= 32)."""
+    pr = P.random_system(1500, 71, mean_offdiag=5.0, dominance=1.2)
+    h = g.gs2_setup(pr.A)
+    h.set_graph_mode(3)
+    x = dev(np.zeros(pr.n))
+    info = g.gmres_solve(h, dev(pr.b), x, restart, 1e-9, 4000, g.params("gs2", 1, 1))
+    _, oinfo = oracle.gmres(pr.A, pr.b, restart=restart, tol=1e-9, max_iters=4000,
+                            pc_kind=oracle.PC_GS2)
+    assert info.status == 0 and oinfo.status == 0
+    assert abs(info.iters - oinfo.iters) <= 1, (info.iters, oinfo.iters)
+
+
+def test_one_launch_tiny_systems(g):
+    """One row, two rows, and a system smaller than one block."""
+    one = (np.array([0, 1]), np.array([0], np.int32), np.array([4.0]))
+    h = g.gs2_setup(one)
+    h.set_graph_mode(3)
+    x = dev(np.zeros(1))
+    info = g.gmres_solve(h, dev(np.array([2.0])), x, 30, 1e-12, 10, g.params("gs2", 1, 1))
+    assert info.status == 0 and host(x)[0] == pytest.approx(0.5, rel=1e-15)
+    two = P.dense_to_csr(np.array([[3.0, 1.0], [-1.0, 2.0]]))
+    h = g.gs2_setup(two)
+    h.set_graph_mode(3)
+    x = dev(np.zeros(2))
+    info = g.gmres_solve(h, dev(np.array([1.0, 1.0])), x, 30, 1e-12, 10, None)
+    assert info.status == 0 and info.iters <= 2
+    assert np.allclose(host(x), np.linalg.solve([[3.0, 1.0], [-1.0, 2.0]], [1.0, 1.0]),
+                       rtol=1e-12)
+    pr = P.poisson2d(9)  # 81 rows
+    h = g.gs2_setup(pr.A)
+    h.set_graph_mode(3)
+    x = dev(np.zeros(pr.n))
+    info = g.gmres_solve(h, dev(pr.b), x, 30, 1e-10, 500, g.params("gs2", 1, 2,
+                                                                     direction="symmetric"))
+    _, oinfo = oracle.gmres(pr.A, pr.b, restart=30, tol=1e-10, max_iters=500,
+                            pc_kind=oracle.PC_GS2, pc_inner=2, pc_direction=oracle.SYMMETRIC)
+    assert info.status == 0 and abs(info.iters - oinfo.iters) <= 1
