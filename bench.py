@@ -514,6 +514,27 @@ def small_system(gs2, torch, reps=20):
         res[name] = {"ms_per_solve": round(ms, 3), "solves_per_s": round(1000.0 / ms, 1),
                      "iters": info.iters, "true_relres": info.true_relres}
         h.close()
+    # CG with SGS2(1,1) on the same SPD system, one launch vs graphs of 16 iterations
+    pcs = gs2.params("gs2", 1, 1, direction="symmetric")
+    for name, mode in (("cg_one_launch", 3), ("cg_graph", 1)):
+        h = gs2.gs2_setup(pr.A)
+        h.set_graph_mode(mode)
+        for _ in range(3):
+            x.zero_()
+            info = gs2.cg_solve(h, b, x, 1e-8, 4000, pcs)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            x.zero_()
+            info = gs2.cg_solve(h, b, x, 1e-8, 4000, pcs)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        res[name] = {"ms_per_solve": round(ms, 3), "solves_per_s": round(1000.0 / ms, 1),
+                     "iters": info.iters, "true_relres": info.true_relres}
+        h.close()
     return res
 
 

@@ -375,6 +375,9 @@ void read_state(gs2_handle* h);
 bool persistent_eligible(const gs2_handle* h, int m, const gs2_params* p, bool automatic);
 gs2_status gmres_persistent(gs2_handle* h, const double* b, double* x, int m, double tol,
                             int max_iters, const gs2_params* p, gs2_solve_info* info);
+// preconditioned CG the same way (same eligibility with m = 1)
+gs2_status cg_persistent(gs2_handle* h, const double* b, double* x, double tol, int max_iters,
+                         const gs2_params* p, gs2_solve_info* info);
 // a kernel gave up a bounded wait: clear the device error word, throw
 void raise_device_error(gs2_handle* h);
 

@@ -862,6 +862,15 @@ gs2_status cg_run(gs2_handle* h, const double* b, double* x, double tol, int max
     if (info) *info = loc;
     return GS2_OK;
   }
+  {
+    const bool forced = h->graph_mode == 3;
+    const bool automatic = h->graph_mode == 0 && !profiling_active(h);
+    if ((forced || automatic) && persistent_eligible(h, 1, p, !forced))
+      return cg_persistent(h, b, x, tol, max_iters, p, info);
+    if (forced)
+      GS2_THROW(GS2_ERR_INVALID_ARG, "the one-launch solver takes n <= 65536 and no, JR or "
+                                     "FP64 non-compact GS2 preconditioning");
+  }
   ensure_krylov(h, 1);
   const gs2_params* pc = (p && p->kind != GS2_PC_NONE) ? p : nullptr;
   const int n = (int)h->n, nb = h->nblk_dot;

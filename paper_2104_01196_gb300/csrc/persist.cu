@@ -155,8 +155,9 @@ __device__ __forceinline__ double row_dot(const int* rp, const int* ci, const do
 }
 
 // value slots of the partial-sum buffer
-constexpr int kSlotDots1 = 0, kSlotDots2 = 32, kSlotNorm = 64, kSlotB = 65, kSlotR = 66;
-constexpr int kPerSlots = 67;
+constexpr int kSlotDots1 = 0, kSlotDots2 = 32, kSlotNorm = 64, kSlotB = 65, kSlotR = 66,
+              kSlotFinal = 67;
+constexpr int kPerSlots = 68;
 
 // CGS2 phases over the thread's rows, for jc <= JB basis vectors (JB a
 // multiple of 8, so at most 7 predicated-off products per row and vector)
@@ -471,6 +472,132 @@ k_gmres_persistent(PersistArgs a) {
   }
 }
 
+
+// Preconditioned CG of a small SPD system in one launch: the iteration of
+// krylov.cu's cg_run (restart of the search direction when the recursive
+// residual has converged but the true residual disagrees), every scalar
+// summed identically by every block.
+__global__ void __launch_bounds__(kPerThreads, 1)
+k_cg_persistent(PersistArgs a) {
+  double* p = a.w;           // search direction
+  double* q = a.V;           // A p (first basis vector slot)
+  double* t = a.V + a.n;     // true-residual scratch
+  int iters = 0, cycles = 0, status = GS2_OK;
+  double s = 0.0;
+  FOR_ROWS(i) s = fma(a.b[i], a.b[i], s);
+  if (!grid_sum1(a, s, kSlotB, &s)) return;
+  const double bnorm = sqrt(s);
+  double beta = 0.0;
+  if (bnorm == 0.0 || isnan(bnorm) || isinf(bnorm)) {
+    if (bnorm == 0.0) FOR_ROWS(i) a.x[i] = 0.0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      a.out->iters = 0;
+      a.out->cycles = 0;
+      a.out->status = bnorm == 0.0 ? GS2_OK : GS2_ERR_NAN;
+      a.out->bnorm = bnorm;
+      a.out->beta = bnorm == 0.0 ? 0.0 : NAN;
+    }
+    return;
+  }
+  const double tol_abs = a.tol * bnorm;
+  FOR_ROWS(i) a.r[i] = a.b[i] - row_dot(a.Arp, a.Aci, a.Ava, i, a.x);
+  for (;;) {
+    // ||r|| of the recursive residual; confirmed on the true one
+    s = 0.0;
+    FOR_ROWS(i) s = fma(a.r[i], a.r[i], s);
+    if (!grid_sum1(a, s, kSlotR, &s)) return;
+    double rn = sqrt(s);
+    beta = rn;
+    if (isnan(rn) || isinf(rn)) {
+      status = GS2_ERR_NAN;
+      break;
+    }
+    if (rn <= tol_abs) {
+      s = 0.0;
+      FOR_ROWS(i) {
+        const double ti = a.b[i] - row_dot(a.Arp, a.Aci, a.Ava, i, a.x);
+        t[i] = ti;
+        s = fma(ti, ti, s);
+      }
+      if (!grid_sum1(a, s, kSlotNorm, &s)) return;
+      beta = sqrt(s);
+      if (beta <= tol_abs) break;
+      FOR_ROWS(i) a.r[i] = t[i];
+    }
+    if (iters >= a.max_iters) {
+      status = GS2_ERR_NOT_CONVERGED;
+      break;
+    }
+    ++cycles;
+    // z = M^{-1} r, p = z, rz = r.z
+    if (!precond(a, a.r, a.z)) return;
+    s = 0.0;
+    FOR_ROWS(i) {
+      p[i] = a.z[i];
+      s = fma(a.r[i], a.z[i], s);
+    }
+    double rz;
+    if (!grid_sum1(a, s, kSlotDots1, &rz)) return;
+    bool stop = false;
+    while (!stop) {
+      // q = A p (p complete: the last sum's barrier) and p.q
+      s = 0.0;
+      FOR_ROWS(i) {
+        const double qi = row_dot(a.Arp, a.Aci, a.Ava, i, p);
+        q[i] = qi;
+        s = fma(p[i], qi, s);
+      }
+      double pq;
+      if (!grid_sum1(a, s, kSlotDots2, &pq)) return;
+      if (pq == 0.0) {
+        status = GS2_ERR_BREAKDOWN;
+        break;
+      }
+      const double alpha = rz / pq;
+      s = 0.0;
+      FOR_ROWS(i) {
+        a.x[i] = fma(alpha, p[i], a.x[i]);
+        const double ri = fma(-alpha, q[i], a.r[i]);
+        a.r[i] = ri;
+        s = fma(ri, ri, s);
+      }
+      if (!grid_sum1(a, s, kSlotNorm, &s)) return;
+      ++iters;
+      const double rr = sqrt(s);
+      if (isnan(rr) || isinf(rr)) {
+        status = GS2_ERR_NAN;
+        break;
+      }
+      if (rr <= tol_abs || iters >= a.max_iters) break;
+      // z = M^{-1} r, beta = r.z / rz, p = z + beta p
+      if (!precond(a, a.r, a.z)) return;
+      s = 0.0;
+      FOR_ROWS(i) s = fma(a.r[i], a.z[i], s);
+      double rz_new;
+      if (!grid_sum1(a, s, kSlotDots1 + 1, &rz_new)) return;
+      const double bt = rz_new / rz;
+      rz = rz_new;
+      FOR_ROWS(i) p[i] = fma(bt, p[i], a.z[i]);
+      if (!grid_sync(a)) return;
+    }
+    if (status == GS2_ERR_NAN || status == GS2_ERR_BREAKDOWN) break;
+  }
+  // the true residual at exit
+  s = 0.0;
+  FOR_ROWS(i) {
+    const double ti = a.b[i] - row_dot(a.Arp, a.Aci, a.Ava, i, a.x);
+    s = fma(ti, ti, s);
+  }
+  if (!grid_sum1(a, s, kSlotFinal, &s)) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.out->iters = iters;
+    a.out->cycles = cycles;
+    a.out->status = status;
+    a.out->bnorm = bnorm;
+    a.out->beta = sqrt(s);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -563,6 +690,71 @@ gs2_status gmres_persistent(gs2_handle* h, const double* b, double* x, int m, do
     else launch_persistent<32>(h, a, nb);
   }
   read_state(h);  // raises GS2_ERR_TIMEOUT if a barrier gave up
+  const KrylovState& st = *h->st_host;
+  gs2_solve_info loc{st.iters, st.cycles, st.status, 0.0};
+  loc.true_relres = st.bnorm == 0.0 ? 0.0 : st.beta / st.bnorm;
+  if (info) *info = loc;
+  return (gs2_status)st.status;
+}
+
+gs2_status cg_persistent(gs2_handle* h, const double* b, double* x, double tol, int max_iters,
+                         const gs2_params* p, gs2_solve_info* info) {
+  ensure_krylov(h, 2);  // V holds q and a residual scratch vector
+  if (!h->persist_bar) {
+    h->persist_bar = (unsigned*)h->dalloc(4 * sizeof(unsigned));
+    h->persist_part = (double*)h->dalloc(sizeof(double) * kPerSlots * kPerMaxBlocks);
+  }
+  const gs2_params* pc = (p && p->kind != GS2_PC_NONE) ? p : nullptr;
+  int nb = (int)std::min<int64_t>(kPerMaxBlocks, (h->n + kPerThreads - 1) / kPerThreads);
+  {
+    int per_sm = 0;
+    GS2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k_cg_persistent,
+                                                           kPerThreads, 0));
+    nb = std::max(1, std::min(nb, per_sm * h->nsm));
+  }
+  PersistArgs a{};
+  a.n = (int)h->n;
+  a.Arp = h->A.rp;
+  a.Aci = h->A.ci;
+  a.Ava = h->A.va;
+  a.Lrp = h->L.rp;
+  a.Lci = h->L.ci;
+  a.Lva = h->L.va;
+  a.Urp = h->U.rp;
+  a.Uci = h->U.ci;
+  a.Uva = h->U.va;
+  a.dinv = h->dinv;
+  a.b = b;
+  a.x = x;
+  a.V = h->V;
+  a.w = h->w;
+  a.z = h->z;
+  a.r = h->r;
+  a.rh = h->rhat;
+  a.g0 = h->g0;
+  a.g1 = h->g1;
+  a.part = h->persist_part;
+  a.m = 1;
+  a.tol = tol;
+  a.max_iters = max_iters;
+  a.kind = pc ? pc->kind : GS2_PC_NONE;
+  a.outer = pc ? std::max(1, pc->outer) : 1;
+  a.inner = pc ? pc->inner : 0;
+  a.dir = pc ? pc->direction : GS2_SYMMETRIC;
+  a.omega = pc ? pc->omega : 1.0;
+  a.gamma = pc ? pc->gamma : 1.0;
+  a.bar = h->persist_bar;
+  a.err = h->dev_err;
+  a.out = h->st;
+  GS2_CUDA(cudaMemsetAsync(h->persist_bar, 0, 4 * sizeof(unsigned), h->stream));
+  {
+    KernelTimer tm(h, "cg_persistent", 0.0);
+    void* args[] = {&a};
+    GS2_CUDA(cudaLaunchCooperativeKernel((const void*)k_cg_persistent, nb, kPerThreads, args, 0,
+                                         h->stream));
+    GS2_LAUNCH_CHECK();
+  }
+  read_state(h);
   const KrylovState& st = *h->st_host;
   gs2_solve_info loc{st.iters, st.cycles, st.status, 0.0};
   loc.true_relres = st.bnorm == 0.0 ? 0.0 : st.beta / st.bnorm;

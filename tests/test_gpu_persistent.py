@@ -201,3 +201,63 @@ def test_one_launch_tiny_systems(g):
     _, oinfo = oracle.gmres(pr.A, pr.b, restart=30, tol=1e-10, max_iters=500,
                             pc_kind=oracle.PC_GS2, pc_inner=2, pc_direction=oracle.SYMMETRIC)
     assert info.status == 0 and abs(info.iters - oinfo.iters) <= 1
+
+
+SPD = {
+    "poisson2d_64": P.poisson2d(64),
+    "poisson3d_24": P.poisson3d(24),
+    "elasticity3d_4": P.elasticity3d(4),
+}
+CG_PCS = {
+    "none": (None, dict(pc_kind=oracle.PC_NONE)),
+    "sgs2_1_1": (dict(kind="gs2", outer=1, inner=1, direction="symmetric"),
+                 dict(pc_kind=oracle.PC_GS2, pc_direction=oracle.SYMMETRIC)),
+    "sgs2_1_2_w0.9": (dict(kind="gs2", outer=1, inner=2, omega=0.9, direction="symmetric"),
+                      dict(pc_kind=oracle.PC_GS2, pc_inner=2, pc_omega=0.9,
+                           pc_direction=oracle.SYMMETRIC)),
+    "jr_2_w0.7": (dict(kind="jr", outer=2, omega=0.7),
+                  dict(pc_kind=oracle.PC_JR, pc_outer=2, pc_omega=0.7)),
+}
+
+
+@pytest.mark.parametrize("name", list(SPD))
+@pytest.mark.parametrize("pc", list(CG_PCS))
+def test_one_launch_cg_matches_oracle(g, name, pc):
+    pr = SPD[name]
+    gp, op = CG_PCS[pc]
+    prm = g.params(**gp) if gp else None
+    h = g.gs2_setup(pr.A)
+    h.set_graph_mode(3)
+    x = dev(np.zeros(pr.n))
+    info = g.cg_solve(h, dev(pr.b), x, 1e-8, 5000, prm)
+    _, oinfo = oracle.cg(pr.A, pr.b, tol=1e-8, max_iters=5000, **op)
+    assert info.status == 0 and oinfo.status == 0, (info, oinfo)
+    assert abs(info.iters - oinfo.iters) <= 1, (info.iters, oinfo.iters)
+    r = np.linalg.norm(pr.b - oracle.spmv(pr.A, host(x))) / np.linalg.norm(pr.b)
+    assert r <= 1e-8 and abs(info.true_relres - r) <= 1e-12
+    h.set_graph_mode(1)
+    ig = g.cg_solve(h, dev(pr.b), dev(np.zeros(pr.n)), 1e-8, 5000, prm)
+    assert abs(ig.iters - info.iters) <= 1
+
+
+def test_one_launch_cg_statuses_and_selection(g):
+    pr = P.poisson2d(40)
+    h = g.gs2_setup(pr.A)
+    prm = g.params("gs2", 1, 1, direction="symmetric")
+    b = dev(pr.b)
+    g.cg_solve(h, b, dev(np.zeros(pr.n)), 1e-8, 500, prm)  # warm
+    c0 = g.launch_count()
+    info = g.cg_solve(h, b, dev(np.zeros(pr.n)), 1e-8, 500, prm)
+    assert info.status == 0 and g.launch_count() - c0 <= 2
+    h.set_graph_mode(3)
+    info = g.cg_solve(h, b, dev(np.zeros(pr.n)), 1e-14, 9, prm)
+    assert info.status == 5 and info.iters == 9
+    x = dev(np.ones(pr.n))
+    info = g.cg_solve(h, dev(np.zeros(pr.n)), x, 1e-8, 50, prm)
+    assert info.status == 0 and info.iters == 0 and np.all(host(x) == 0.0)
+    bn = pr.b.copy()
+    bn[7] = np.nan
+    assert g.cg_solve(h, dev(bn), dev(np.zeros(pr.n)), 1e-8, 50, prm).status == 7
+    with pytest.raises(g.GS2Error):
+        g.cg_solve(h, b, dev(np.zeros(pr.n)), 1e-8, 50,
+                   g.params("gs2", 1, 1, direction="symmetric", precision="fp32"))
