@@ -861,6 +861,7 @@ gs2_status gs2_setup(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_
   }
   *out = nullptr;
   API_BEGIN
+  NvtxRange nvtx_("gs2_setup");
   *out = setup_handle(n, nnz, rowptr, col, val, on_device, precisions, (cudaStream_t)stream,
                       false);
   return GS2_OK;
@@ -1093,6 +1094,7 @@ gs2_status gs2_apply_ex(gs2_handle* h, const double* b, double* x, const gs2_par
     return GS2_ERR_INVALID_ARG;
   }
   API_BEGIN
+  NvtxRange nvtx_("gs2_apply_ex");
   gs2_params q = *p;
   q.kind = GS2_PC_GS2;
   check_params(&q);
@@ -1119,6 +1121,7 @@ gs2_status relax_apply(gs2_handle* h, const double* b, double* x, const gs2_para
     return GS2_ERR_INVALID_ARG;
   }
   API_BEGIN
+  NvtxRange nvtx_("relax_apply");
   check_params(p);
   if (p->kind != GS2_PC_GS2 && p->kind != GS2_PC_JR && p->kind != GS2_PC_GS &&
       p->kind != GS2_PC_MTGS)
@@ -1137,6 +1140,7 @@ gs2_status gs_apply(gs2_handle* h, const double* b, double* x, int sweeps, doubl
                     int direction) {
   if (!h || (h->n && (!b || !x))) return GS2_ERR_INVALID_ARG;
   API_BEGIN
+  NvtxRange nvtx_("gs_apply");
   if (sweeps < 0 || !(omega > 0.0) || direction < 0 || direction > 2)
     GS2_THROW(GS2_ERR_INVALID_ARG, "bad sweeps/omega/direction");
   if (sweeps == 0 || h->n == 0) return GS2_OK;
@@ -1152,6 +1156,7 @@ gs2_status mtgs_apply(gs2_handle* h, const double* b, double* x, int sweeps, dou
                       int direction) {
   if (!h || (h->n && (!b || !x))) return GS2_ERR_INVALID_ARG;
   API_BEGIN
+  NvtxRange nvtx_("mtgs_apply");
   if (sweeps < 0 || !(omega > 0.0) || direction < 0 || direction > 2)
     GS2_THROW(GS2_ERR_INVALID_ARG, "bad sweeps/omega/direction");
   if (sweeps == 0 || h->n == 0) return GS2_OK;
@@ -1166,6 +1171,7 @@ gs2_status mtgs_apply(gs2_handle* h, const double* b, double* x, int sweeps, dou
 gs2_status gs2_amg_setup(gs2_handle* h, const gs2_amg_cfg* cfg) {
   if (!h) return GS2_ERR_INVALID_ARG;
   API_BEGIN
+  NvtxRange nvtx_("gs2_amg_setup");
   gs2_amg_cfg c{0.25, 10, 64};
   if (cfg) c = *cfg;
   if (h->n == 0) GS2_THROW(GS2_ERR_INVALID_ARG, "AMG of an empty matrix");
@@ -1187,6 +1193,7 @@ gs2_status gs2_amg_vcycle(gs2_handle* h, const double* b, double* x, const gs2_p
     return GS2_ERR_INVALID_ARG;
   }
   API_BEGIN
+  NvtxRange nvtx_("gs2_amg_vcycle");
   if (p->kind != GS2_PC_AMG && p->kind != GS2_PC_AMG_JR)
     GS2_THROW(GS2_ERR_INVALID_ARG, "kind must be GS2_PC_AMG or GS2_PC_AMG_JR");
   check_params(p);
@@ -1202,6 +1209,7 @@ gs2_status gs2_amg_vcycle(gs2_handle* h, const double* b, double* x, const gs2_p
 gs2_status jr_apply(gs2_handle* h, const double* b, double* x, int sweeps, double omega) {
   if (!h || (h->n && (!b || !x))) return GS2_ERR_INVALID_ARG;
   API_BEGIN
+  NvtxRange nvtx_("jr_apply");
   if (sweeps < 0 || !(omega > 0.0)) GS2_THROW(GS2_ERR_INVALID_ARG, "bad sweeps/omega");
   if (sweeps == 0 || h->n == 0) return GS2_OK;
   Staged s(h, b, x, true);
@@ -1214,6 +1222,7 @@ gs2_status jr_apply(gs2_handle* h, const double* b, double* x, int sweeps, doubl
 gs2_status gs2_spmv(gs2_handle* h, const double* x, double* y) {
   if (!h || (h->n && (!x || !y))) return GS2_ERR_INVALID_ARG;
   API_BEGIN
+  NvtxRange nvtx_("gs2_spmv");
   if (h->n == 0) return GS2_OK;
   Staged s(h, x, y, false);
   launch_spmv(h, s.b, s.x, nullptr);
@@ -1226,6 +1235,7 @@ gs2_status gmres_solve(gs2_handle* h, const double* b, double* x, int restart, d
                        int max_iters, const gs2_params* precond, gs2_solve_info* info) {
   if (!h || (h->n && (!b || !x))) return GS2_ERR_INVALID_ARG;
   API_BEGIN
+  NvtxRange nvtx_("gmres_solve");
   if (restart < 1 || restart > kMaxRestart || !(tol >= 0.0) || max_iters < 0)
     GS2_THROW(GS2_ERR_INVALID_ARG, "restart must be in [1, 64], tol >= 0, max_iters >= 0");
   check_params(precond);
@@ -1242,6 +1252,7 @@ gs2_status cg_solve(gs2_handle* h, const double* b, double* x, double tol, int m
                     const gs2_params* precond, gs2_solve_info* info) {
   if (!h || (h->n && (!b || !x))) return GS2_ERR_INVALID_ARG;
   API_BEGIN
+  NvtxRange nvtx_("cg_solve");
   if (!(tol >= 0.0) || max_iters < 0) GS2_THROW(GS2_ERR_INVALID_ARG, "tol/max_iters");
   check_params(precond);
   if (precond && precond->kind == GS2_PC_GS2) ensure_precision(h, precond->precision);
@@ -1258,6 +1269,7 @@ gs2_status gs2_batch_solve(gs2_handle* const* hs, const double* const* bs, doubl
                            const gs2_params* precond, gs2_solve_info* infos) {
   if (count < 0 || (count > 0 && (!hs || !bs || !xs))) return GS2_ERR_INVALID_ARG;
   API_BEGIN
+  NvtxRange nvtx_("gs2_batch_solve");
   if (restart < 1 || restart > kMaxRestart || !(tol >= 0.0) || max_iters < 0)
     GS2_THROW(GS2_ERR_INVALID_ARG, "restart must be in [1, 64], tol >= 0, max_iters >= 0");
   check_params(precond);
@@ -1283,6 +1295,7 @@ gs2_status gs2_pack_setup(int count, const int64_t* n, const int64_t* const* row
   }
   *out = nullptr;
   API_BEGIN
+  NvtxRange nvtx_("gs2_pack_setup");
   std::vector<int64_t> off, rp;
   std::vector<int32_t> ci;
   std::vector<double> va;
@@ -1327,6 +1340,7 @@ gs2_status gs2_pack_gmres(gs2_handle* h, const double* b, double* x, int restart
                           int max_iters, const gs2_params* precond, gs2_solve_info* infos) {
   if (!h || (h->n && (!b || !x))) return GS2_ERR_INVALID_ARG;
   API_BEGIN
+  NvtxRange nvtx_("gs2_pack_gmres");
   if (!h->pack) GS2_THROW(GS2_ERR_INVALID_ARG, "the handle is not a pack (gs2_pack_setup)");
   if (restart < 1 || restart > kMaxRestart || !(tol >= 0.0) || max_iters < 0)
     GS2_THROW(GS2_ERR_INVALID_ARG, "restart must be in [1, 64], tol >= 0, max_iters >= 0");
@@ -1356,6 +1370,7 @@ gs2_status gs2_profile_enable(gs2_handle* h, int enable) {
 gs2_status gs2_autotune(gs2_handle* h) {
   if (!h) return GS2_ERR_INVALID_ARG;
   API_BEGIN
+  NvtxRange nvtx_("gs2_autotune");
   if (h->n == 0) return GS2_OK;
   gs2_host_side* hs = host_side(h);
   h->dzero(h->t, sizeof(double) * h->n);

@@ -4,6 +4,7 @@
 
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cstdint>
@@ -45,6 +46,15 @@ void add_launches(long long delta);
     ::gs2::count_launch();          \
     GS2_CUDA(cudaGetLastError());   \
   } while (0)
+
+// NVTX range over a library call: shows each call on the timeline of
+// Nsight Systems; without a tool attached it costs a branch
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ---------------------------------------------------------------------------
 // device storage
