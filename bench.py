@@ -639,12 +639,21 @@ def full_workloads(gs2, torch):
         # (the elasticity right-hand side is a body load, with no x_true)
         xt = torch.from_numpy(pr.x_true).cuda() if pr.x_true is not None else None
         res = {"n": pr.n, "nnz": int(len(pr.A[1]))}
+        x64 = {}
         for vname, pc in variants:
             info, ms = timed(h, b, x, pc, 5000)
             err = (float(torch.linalg.norm(x - xt) / torch.linalg.norm(xt))
                    if xt is not None else None)
             res[vname] = {"status": info.status, "iters": info.iters, "ms": round(ms, 2),
                           "true_relres": info.true_relres, "rel_err_vs_x_true": err}
+            # lower-precision sweeps: error against the FP64-sweep solution of
+            # the same system (itself within the parity bound of the oracle)
+            stem = vname.rsplit("_", 1)[0]
+            if vname.endswith("_fp64"):
+                x64[stem] = x.clone()
+            elif stem in x64:
+                res[vname]["rel_err_vs_fp64_solution"] = float(
+                    torch.linalg.norm(x - x64[stem]) / torch.linalg.norm(x64[stem]))
         if name.startswith("elasticity"):
             # stationary JR, omega = 1 (the paper's elasticity tables): the
             # residual grows
@@ -788,6 +797,10 @@ def comparisons(gs2, torch, pr, stream, b):
     res["amg_levels"] = [list(lv) for lv in h.amg_info()]
     with torch.cuda.stream(stream):
         x = torch.zeros(pr.n, dtype=torch.float64, device="cuda")
+        # the FP64 SGS2(1,1) solution, the reference of the precision variants
+        x_ref = torch.zeros_like(x)
+        gs2.gmres_solve(h, b, x_ref, 30, 1e-8, 3000,
+                        gs2.params("gs2", 1, 1, direction="symmetric"))
         for name, p in variants.items():
             # (the Laplacian is SPD: the cg_ variants run CG with the
             # symmetric preconditioner instead of GMRES)
@@ -810,6 +823,9 @@ def comparisons(gs2, torch, pr, stream, b):
             res[name] = {"status": info.status, "iters": info.iters, "ms": round(ms, 2),
                          "solves_per_s": round(1000.0 / ms, 3),
                          "true_relres": info.true_relres, "rms_err_vs_x_true": err}
+            if name in ("sgs2_1_1_fp32", "sgs2_1_1_fp16") and x_ref is not None:
+                res[name]["rel_err_vs_fp64_solution"] = float(
+                    torch.linalg.norm(x - x_ref) / torch.linalg.norm(x_ref))
     h.close()
     return res
 
