@@ -191,6 +191,58 @@ def oracle_sample(pr, target_s=12.0):
                                      f"full-solve count {full}")
 
 
+def sweep_cpu_vs_gpu(gs2, torch, pr, h, stream):
+    """One SGS2(1,1) relaxation sweep from x = 0 on the benchmark matrix (the
+    work of one preconditioner application): the oracle's sequential build on
+    one core, the same oracle built with -fopenmp on every host core (row
+    loops spread, bitwise the same result; inner products and exact-GS
+    recurrences stay sequential), and the GPU (gs2_apply, CUDA events on the
+    handle's stream, mean of 20 after 3 untimed).  Each CPU figure is the mean
+    of the sweeps that fit in about 2 s (at least one, after one untimed)."""
+    import oracle
+    x0 = np.zeros(pr.n)
+    res = {"sweep": "SGS2(1,1) from x = 0, FP64, gs2_apply vs the oracle's ora_gs2"}
+    ref = None
+    for omp in (False, True):
+        key = "oracle_all_cores" if omp else "oracle_1_core"
+        try:
+            oracle.build(openmp=omp)
+        except Exception as e:  # no OpenMP in the host compiler
+            res[key] = {"unavailable": str(e).splitlines()[0][:200]}
+            continue
+        run = lambda: oracle.gs2(pr.A, pr.b, x0, 1, 1, 1.0, 1.0, oracle.SYMMETRIC,  # noqa: E731
+                                 openmp=omp)
+        ref = run()
+        reps, t0 = 0, time.perf_counter()
+        while reps < 1 or (time.perf_counter() - t0 < 2.0 and reps < 20):
+            run()
+            reps += 1
+        res[key] = {"ms": round(1000 * (time.perf_counter() - t0) / reps, 2),
+                    "threads": oracle.threads(openmp=omp), "sweeps_timed": reps}
+    b = torch.from_numpy(pr.b).cuda()
+    x = torch.zeros(pr.n, dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            x.zero_()
+            gs2.gs2_apply(h, b, x, 1, 1, 1.0, "symmetric")
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        ms = 0.0
+        for _ in range(20):
+            x.zero_()
+            e0.record(stream)
+            gs2.gs2_apply(h, b, x, 1, 1, 1.0, "symmetric")
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+    res["gpu"] = {"ms": round(ms / 20, 4)}
+    if ref is not None:
+        xr = torch.from_numpy(ref).cuda()
+        res["gpu"]["rel_diff_vs_oracle"] = float(torch.linalg.norm(x - xr) /
+                                                 torch.linalg.norm(xr))
+    return res
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -476,7 +528,9 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu:
         v, sample = oracle_sample(pr)
         out["cpu_baseline"] = {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                               "sample": sample}
+                               "sample": sample,
+                               "sweep_1_vs_all_cores": sweep_cpu_vs_gpu(gs2, torch, pr, h,
+                                                                        stream)}
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist:

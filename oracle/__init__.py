@@ -22,8 +22,11 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _SRCS = [_SRC, os.path.join(_HERE, "amg.c"), os.path.join(_HERE, "hybrid.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
+# the same sources built with -fopenmp: the row loops spread over the host
+# cores, bitwise the same results (the multi-core CPU timing)
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 FORWARD, BACKWARD, SYMMETRIC = 0, 1, 2
 PC_NONE, PC_GS2, PC_JR, PC_GS, PC_MTGS = 0, 1, 2, 3, 4
@@ -34,18 +37,20 @@ class OracleError(RuntimeError):
     pass
 
 
-def build(force: bool = False) -> str:
-    """Compile oracle.c into liboracle.so next to it (gcc, -O2, no -march)."""
-    stale = (not os.path.exists(_LIB)) or (
-        os.path.getmtime(_LIB) < max([os.path.getmtime(f) for f in _SRCS] +
-                                     [os.path.getmtime(os.path.join(_HERE, "oracle.h"))]))
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile oracle.c into liboracle.so next to it (gcc, -O2, no -march);
+    with openmp=True into liboracle_omp.so with -fopenmp."""
+    lib = _LIB_OMP if openmp else _LIB
+    stale = (not os.path.exists(lib)) or (
+        os.path.getmtime(lib) < max([os.path.getmtime(f) for f in _SRCS] +
+                                    [os.path.getmtime(os.path.join(_HERE, "oracle.h"))]))
     if force or stale:
-        tmp = _LIB + f".tmp{os.getpid()}"
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-               *_SRCS, "-o", tmp, "-lm"]
+               *(["-fopenmp"] if openmp else []), *_SRCS, "-o", tmp, "-lm"]
         subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB)
-    return _LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 class _Info(ctypes.Structure):
@@ -61,12 +66,10 @@ class SolveInfo:
     true_relres: float
 
 
-def _load():
-    global _lib
+def _load(openmp: bool = False):
     with _lock:
-        if _lib is None:
-            build()
-            lib = ctypes.CDLL(_LIB)
+        if openmp not in _libs:
+            lib = ctypes.CDLL(build(openmp=openmp))
             P = ctypes.c_void_p
             I64, I32, D = ctypes.c_int64, ctypes.c_int, ctypes.c_double
             csr = [I64, P, P, P]
@@ -102,15 +105,21 @@ def _load():
             lib.ora_hybrid.argtypes = csr + [P, P, I32, I32, I32, I32, I32, D, D, I32]
             lib.ora_set_hybrid.argtypes = [I32, I32]
             lib.ora_set_hybrid.restype = None
+            lib.ora_threads.argtypes = []
             for f in ("ora_diag", "ora_gs2", "ora_gs", "ora_jr", "ora_levels",
                       "ora_precond", "ora_gmres", "ora_cg", "ora_gs2_compact",
                       "ora_coloring", "ora_mtgs", "ora_amg_levels", "ora_amg_level",
                       "ora_amg_get_matrix", "ora_amg_get_prolongator",
                       "ora_amg_get_aggregates", "ora_amg_vcycle", "ora_gmres_amg",
-                      "ora_cg_amg", "ora_hybrid"):
+                      "ora_cg_amg", "ora_hybrid", "ora_threads"):
                 getattr(lib, f).restype = ctypes.c_int
-            _lib = lib
-    return _lib
+            _libs[openmp] = lib
+    return _libs[openmp]
+
+
+def threads(openmp: bool = False) -> int:
+    """Threads the row loops of that build run on."""
+    return int(_load(openmp).ora_threads())
 
 
 def _csr(A):
@@ -138,11 +147,11 @@ def _check(st, what):
         raise OracleError(f"{what} returned status {st}")
 
 
-def spmv(A, x):
+def spmv(A, x, openmp=False):
     n, rp, ci, va = _csr(A)
     x = _vec(x, n)
     y = np.empty(n)
-    _load().ora_spmv(n, _p(rp), _p(ci), _p(va), _p(x), _p(y))
+    _load(openmp).ora_spmv(n, _p(rp), _p(ci), _p(va), _p(x), _p(y))
     return y
 
 
@@ -153,11 +162,11 @@ def diag(A):
     return d
 
 
-def gs2(A, b, x, outer=1, inner=1, omega=1.0, gamma=1.0, direction=FORWARD):
+def gs2(A, b, x, outer=1, inner=1, omega=1.0, gamma=1.0, direction=FORWARD, openmp=False):
     """Non-compact GS2 sweeps (Eq. 2-5, damped); returns the new x."""
     n, rp, ci, va = _csr(A)
     b, x = _vec(b, n), _vec(x, n)
-    _check(_load().ora_gs2(n, _p(rp), _p(ci), _p(va), _p(b), _p(x), outer, inner,
+    _check(_load(openmp).ora_gs2(n, _p(rp), _p(ci), _p(va), _p(b), _p(x), outer, inner,
                            omega, gamma, direction), "ora_gs2")
     return x
 
@@ -171,11 +180,11 @@ def gs(A, b, x, sweeps=1, omega=1.0, direction=FORWARD):
     return x
 
 
-def jr(A, b, x, sweeps=1, omega=1.0):
+def jr(A, b, x, sweeps=1, omega=1.0, openmp=False):
     """Damped Jacobi-Richardson; returns the new x."""
     n, rp, ci, va = _csr(A)
     b, x = _vec(b, n), _vec(x, n)
-    _check(_load().ora_jr(n, _p(rp), _p(ci), _p(va), _p(b), _p(x), sweeps, omega),
+    _check(_load(openmp).ora_jr(n, _p(rp), _p(ci), _p(va), _p(b), _p(x), sweeps, omega),
            "ora_jr")
     return x
 

@@ -13,12 +13,34 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Loops over rows (or vector entries) in which every iteration writes only
+ * its own entry, from the same code in the same order, carry an OpenMP
+ * parallel-for: a build with -fopenmp spreads them over the host cores (the
+ * multi-core CPU timing), a build without it ignores the pragma, and both
+ * give bitwise the same results.  Reductions (inner products, norms) and the
+ * recurrences of exact GS stay sequential in every build. */
+#ifdef _OPENMP
+#include <omp.h>
+#define ORA_ROWS_PARALLEL _Pragma("omp parallel for schedule(static)")
+#else
+#define ORA_ROWS_PARALLEL
+#endif
+
+int ora_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
 /* ------------------------------------------------------------------ */
 /* Basic pieces                                                         */
 /* ------------------------------------------------------------------ */
 
 void ora_spmv(int64_t n, const int64_t* rp, const int32_t* ci,
               const double* va, const double* x, double* y) {
+  ORA_ROWS_PARALLEL
   for (int64_t i = 0; i < n; ++i) {
     double s = 0.0;
     for (int64_t k = rp[i]; k < rp[i + 1]; ++k) s += va[k] * x[ci[k]];
@@ -50,6 +72,7 @@ static double nrm2(int64_t n, const double* a) { return sqrt(dot(n, a, a)); }
 static void residual(int64_t n, const int64_t* rp, const int32_t* ci,
                      const double* va, const double* b, const double* x,
                      double* r) {
+  ORA_ROWS_PARALLEL
   for (int64_t i = 0; i < n; ++i) {
     double s = 0.0;
     for (int64_t k = rp[i]; k < rp[i + 1]; ++k) s += va[k] * x[ci[k]];
@@ -62,6 +85,7 @@ static void residual(int64_t n, const int64_t* rp, const int32_t* ci,
 static void tri_mult(int64_t n, const int64_t* rp, const int32_t* ci,
                      const double* va, int lower, const double* g,
                      double* t) {
+  ORA_ROWS_PARALLEL
   for (int64_t i = 0; i < n; ++i) {
     double s = 0.0;
     for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
@@ -92,13 +116,16 @@ static void gs2_sweep(int64_t n, const int64_t* rp, const int32_t* ci,
                       int lower, double* r, double* g, double* gn,
                       double* t) {
   residual(n, rp, ci, va, b, x, r);
+  ORA_ROWS_PARALLEL
   for (int64_t i = 0; i < n; ++i) g[i] = r[i] / d[i];
   for (int j = 0; j < inner; ++j) {
     tri_mult(n, rp, ci, va, lower, g, t);
+    ORA_ROWS_PARALLEL
     for (int64_t i = 0; i < n; ++i)
       gn[i] = (1.0 - gamma) * g[i] + gamma * (r[i] - omega * t[i]) / d[i];
     memcpy(g, gn, (size_t)n * sizeof(double));
   }
+  ORA_ROWS_PARALLEL
   for (int64_t i = 0; i < n; ++i) x[i] = x[i] + omega * g[i];
 }
 
@@ -235,6 +262,7 @@ int ora_jr(int64_t n, const int64_t* rp, const int32_t* ci, const double* va,
   int st = ora_diag(n, rp, ci, va, d);
   for (int s = 0; st == 0 && s < sweeps; ++s) {
     residual(n, rp, ci, va, b, x, r);
+    ORA_ROWS_PARALLEL
     for (int64_t i = 0; i < n; ++i) x[i] = x[i] + omega * r[i] / d[i];
   }
   free(d); free(r);

@@ -138,6 +138,10 @@ int ora_hybrid(int64_t n, const int64_t* rp, const int32_t* ci, const double* va
                double omega, double gamma, int dir);
 /* partition and local sweeps of the hybrid preconditioner kinds */
 void ora_set_hybrid(int parts, int local);
+
+/* Threads the row loops run on: the OpenMP thread count in a build with
+ * -fopenmp, else 1. */
+int ora_threads(void);
 extern _Thread_local int ora_hybrid_parts;
 extern _Thread_local int ora_hybrid_local;
 

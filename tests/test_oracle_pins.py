@@ -805,3 +805,25 @@ def test_local_jr_iterations_grow_with_the_blocks_global_stay():
                                 pc_outer=1, pc_parts=parts, pc_local=4)[1].iters)
     assert glob[0] == glob[1] == glob[2]
     assert loc[0] == glob[0] and loc[0] < loc[1] < loc[2]
+
+
+def test_openmp_build_is_bitwise_the_sequential_oracle():
+    """The -fopenmp build of the oracle (the multi-core CPU timing) spreads
+    only loops whose iterations write their own entry; it must give bitwise
+    the results of the sequential build on a nonsymmetric system."""
+    try:
+        oracle.build(openmp=True)
+    except Exception as e:  # a host compiler without OpenMP
+        pytest.skip(f"no OpenMP build: {e}")
+    pr = P.convdiff3d(12)
+    rng = np.random.default_rng(3)
+    x0 = rng.uniform(-1, 1, pr.n)
+    assert oracle.threads(openmp=False) == 1
+    assert oracle.threads(openmp=True) >= 1
+    for direction in (oracle.FORWARD, oracle.BACKWARD, oracle.SYMMETRIC):
+        a = oracle.gs2(pr.A, pr.b, x0, 2, 2, 0.9, 0.8, direction)
+        b = oracle.gs2(pr.A, pr.b, x0, 2, 2, 0.9, 0.8, direction, openmp=True)
+        assert np.array_equal(a, b)
+    assert np.array_equal(oracle.jr(pr.A, pr.b, x0, 3, 0.7),
+                          oracle.jr(pr.A, pr.b, x0, 3, 0.7, openmp=True))
+    assert np.array_equal(oracle.spmv(pr.A, x0), oracle.spmv(pr.A, x0, openmp=True))
