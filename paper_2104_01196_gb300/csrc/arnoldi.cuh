@@ -56,12 +56,27 @@ __device__ __forceinline__ void update_rows(int i, int end, int step, int ld,
 // column and the earlier rotations are staged in shared memory by all
 // threads; the sequential rotation chain runs on thread 0.  Returns (to
 // every thread) whether this step ended the system's cycle.
+// Every global value the step needs (the column, the rotations, the norm
+// partials, g_j and the state fields) is loaded before the first use of any
+// of them, so the loads share one round trip instead of following the
+// rotation chain one after another.  With skip_if non-null the block returns
+// false without side effects when *skip_if is set (read with the others).
 __device__ __forceinline__ bool givens_block(const double* __restrict__ part, int p0, int p1,
                                              double* col, double* cs, double* sn, double* gv,
-                                             int j, KrylovState* st) {
+                                             int j, KrylovState* st,
+                                             const int* skip_if = nullptr) {
   __shared__ double red[32];
   __shared__ double col_s[kMaxRestart + 2], cs_s[kMaxRestart + 1], sn_s[kMaxRestart + 1];
   __shared__ int stopped;
+  const int skip = skip_if ? *skip_if : 0;
+  double gj = 0.0, tol_abs = 0.0;
+  int iters = 0, max_iters = 0;
+  if (threadIdx.x == 0) {
+    gj = gv[j];
+    iters = st->iters;
+    max_iters = st->max_iters;
+    tol_abs = st->tol_abs;
+  }
   for (int i = threadIdx.x; i <= j; i += blockDim.x) col_s[i] = col[i];
   for (int i = threadIdx.x; i < j; i += blockDim.x) {
     cs_s[i] = cs[i];
@@ -69,6 +84,7 @@ __device__ __forceinline__ bool givens_block(const double* __restrict__ part, in
   }
   double s = 0.0;
   for (int b = p0 + threadIdx.x; b < p1; b += blockDim.x) s += part[b];
+  if (skip) return false;  // the same value in every thread: a uniform exit
   s = warp_sum(s);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) red[wid] = s;
@@ -99,10 +115,9 @@ __device__ __forceinline__ bool givens_block(const double* __restrict__ part, in
     sn[j] = sgv;
     col_s[j] = r;
     col_s[j + 1] = 0.0;
-    const double gj = gv[j];
     gv[j + 1] = -sgv * gj;
     gv[j] = c * gj;
-    st->iters += 1;
+    st->iters = iters + 1;
     st->k = j + 1;
     st->hn = hn;
     st->inv_hn = 1.0 / hn;
@@ -114,7 +129,7 @@ __device__ __forceinline__ bool givens_block(const double* __restrict__ part, in
     } else if (hn == 0.0) {
       st->status = GS2_ERR_BREAKDOWN;
       stop = 1;
-    } else if (est <= st->tol_abs || st->iters >= st->max_iters) {
+    } else if (est <= tol_abs || iters + 1 >= max_iters) {
       stop = 1;
     }
     if (stop) st->stop = 1;

@@ -29,10 +29,11 @@ namespace gs2 {
 __global__ void k_reduce_cols(const double* __restrict__ part, int nblk, double* H, int ldh,
                               int j, double* hbuf, int mode, const int* skip) {
   pdl_wait();
-  if (skip && *skip) return;
+  // the skip flag is read after the partials' loads are issued: one round trip
   const int v = blockIdx.x;
   double s = 0.0;
   for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part[(size_t)v * nblk + b];
+  if (skip && *skip) return;
   __shared__ double red[32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   s = warp_sum(s);
@@ -163,8 +164,8 @@ __global__ void k_givens(const double* __restrict__ part, int nblk, double* H, i
                          double* cs, double* sn, double* gv, KrylovState* st,
                          volatile int* stop_host) {
   pdl_wait();
-  if (st->stop) return;
-  if (givens_block(part, 0, nblk, H + (size_t)j * ldh, cs, sn, gv, j, st) && threadIdx.x == 0)
+  if (givens_block(part, 0, nblk, H + (size_t)j * ldh, cs, sn, gv, j, st, &st->stop) &&
+      threadIdx.x == 0)
     *stop_host = 1;
 }
 
