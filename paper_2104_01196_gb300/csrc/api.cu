@@ -245,22 +245,36 @@ static void build_tiles(const std::vector<int>& rp, int n, int K, int RPT,
 void retile(gs2_handle* h, DevCsr& M, const std::vector<int>& rp, int K, int RPT);
 
 // ---------------------------------------------------------------------------
-// sliced-ELL copies of short-row matrices
+// sliced-ELL copies
 // ---------------------------------------------------------------------------
 
-constexpr int kSellC = 32;              // rows per chunk (one warp)
-constexpr double kSellMaxMeanRow = 24;  // the one-thread-per-row regime
-constexpr double kSellMaxPadding = 1.2; // slots / entries
+// A matrix whose sliced-ELL layout pads by at most 20% gets the copy when
+// its rows are short (one lane per row is the natural width) or when it is
+// streamed from HBM (its CSR larger than the 129 MB L2): there one lane per
+// row issues only the row's FMAs, with no segment reduction and no idle
+// lanes, which matters on this part's FP64 pipe (on the 81-entry rows of Q1
+// elasticity the residual went from 2.8 to 5.0 TB/s against the best
+// row-tile shape, 8 lanes per row).  Smaller long-row matrices (coarse
+// multigrid levels) are latency-bound and keep the row tiles, whose K lanes
+// per row shorten each row's chain of dependent gathers.
+constexpr int kSellC = 32;                       // rows per chunk (one warp)
+constexpr double kSellMaxPadding = 1.2;          // slots / entries
+constexpr double kSellShortRow = 24;             // mean entries per row
+constexpr double kSellStreamBytes = 128.0 * (1 << 20);  // CSR bytes beyond L2
 
-// chunk offsets: chunk c takes (longest row of the chunk) x 32 slots
+// chunk offsets: chunk c takes (longest row of the chunk) x 32 slots; empty
+// when the slots would not fit 32-bit offsets
 static std::vector<int> sell_layout(const std::vector<int>& rp, int n) {
   const int nc = (n + kSellC - 1) / kSellC;
   std::vector<int> cptr(nc + 1, 0);
+  int64_t total = 0;
   for (int c = 0; c < nc; ++c) {
     int L = 0;
     for (int i = c * kSellC; i < std::min(n, (c + 1) * kSellC); ++i)
       L = std::max(L, rp[i + 1] - rp[i]);
-    cptr[c + 1] = cptr[c] + L * kSellC;
+    total += (int64_t)L * kSellC;
+    if (total > INT32_MAX) return {};
+    cptr[c + 1] = (int)total;
   }
   return cptr;
 }
@@ -269,9 +283,10 @@ static std::vector<int> sell_layout(const std::vector<int>& rp, int n) {
 // there (launch_to_sell); only the chunk offsets are computed here.
 static void upload_sell(gs2_handle* h, DevCsr& M, const std::vector<int>& rp) {
   const int n = M.n;
-  if (n == 0 || M.nnz == 0 || M.mean_row > kSellMaxMeanRow) return;
+  if (n == 0 || M.nnz == 0) return;
+  if (M.mean_row > kSellShortRow && 12.0 * M.nnz < kSellStreamBytes) return;
   std::vector<int> cptr = sell_layout(rp, n);
-  if (cptr.back() > kSellMaxPadding * M.nnz) return;
+  if (cptr.empty() || cptr.back() > kSellMaxPadding * M.nnz) return;
   const size_t slots = std::max(cptr.back(), 1);
   M.sell_chunks = (int)cptr.size() - 1;
   M.sell_slots = (int)slots;
@@ -666,7 +681,7 @@ static void tune_matrix(gs2_handle* h, DevCsr& M, const std::vector<int>& rp, in
   if (M.n == 0 || M.nnz == 0) return;
   const auto key = std::make_tuple(role, (int)std::lround(2.0 * std::log2((double)M.n)),
                                    (int)std::lround(4.0 * M.mean_row));
-  // whether M has a sliced-ELL copy at all (qualifying short rows)
+  // whether M has a sliced-ELL copy at all (padding of at most 20%)
   const bool has_sell = M.sell_chunks > 0;
   {
     std::lock_guard<std::mutex> g(g_tune_mu);

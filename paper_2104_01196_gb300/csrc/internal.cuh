@@ -81,7 +81,7 @@ struct DevCsr {
   int cap = 0;
   int4* desc = nullptr;  // ntiles
   double mean_row = 0.0;
-  // Sliced-ELL copy (short rows): chunk c holds rows 32c .. 32c+31, its
+  // Sliced-ELL copy (rows of similar length): chunk c holds rows 32c .. 32c+31, its
   // longest row's length L_c times 32 slots, column-major: slot k of row i
   // at sell_ptr[c] + 32 k + i % 32; padding slots have value 0 and repeat
   // a column of the row (column 0 for an empty row)

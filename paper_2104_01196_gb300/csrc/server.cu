@@ -58,41 +58,51 @@ struct Group {
   PackJob* job = nullptr;
 };
 
+// Bytes of the sliced-ELL copy of a matrix with this many entries (at most
+// 1.2 slots per entry, else no copy is made) holding vbytes-byte values, with
+// its chunk offsets.
+static int64_t sell_bytes(int64_t entries, int64_t n, int vbytes) {
+  return (entries * 6 / 5 + 1) * (4 + vbytes) + 4 * (n / 32 + 2);
+}
+
 // Device bytes a request of this size holds once admitted: the matrix, its
-// two prescaled triangles, the resident vectors, the Krylov basis and the
-// optional lower-precision, level-set and colour storage (mirrors
-// setup_handle, ensure_precision, ensure_levels, ensure_colors and
-// ensure_krylov).
+// two prescaled triangles, their sliced-ELL copies, the resident vectors,
+// the Krylov basis and the optional lower-precision, level-set and colour
+// storage (mirrors setup_handle, upload_sell, ensure_precision,
+// ensure_levels, ensure_colors and ensure_krylov).
 static int64_t footprint(const gs2_server_cfg& c, int64_t n, int64_t nnz) {
   const int64_t off = std::max<int64_t>(nnz - n, 0);
   const int64_t m = std::max(c.restart, 1);
   int64_t b = 12 * nnz + 12 * off + 3 * 4 * (n + 17) + 3 * (n / 16 + 16) * 16;
+  b += sell_bytes(nnz, n, 8) + 2 * sell_bytes(off / 2 + 1, n, 8);
   b += 8 * n * 9;                     // D^{-1} and eight resident temporaries
   b += 8 * (int64_t)8 * 152 * 66;     // per-block partial sums (upper bound)
   b += 8 * n * (m + 1) + 3 * 8 * n;   // Krylov basis, w, p, q
   b += 8 * (m + 1) * (m + 6);         // Hessenberg, rotations, y
   if (c.has_precond && c.precond.kind == GS2_PC_GS2) {
-    if (c.precond.precision == GS2_FP32) b += 4 * off + 12 * n;
-    if (c.precond.precision == GS2_FP16_ROWSCALED) b += 2 * off + 8 * n + 12 * n;
+    if (c.precond.precision == GS2_FP32) b += 4 * off + 12 * n + 4 * (off * 6 / 5 + 2);
+    if (c.precond.precision == GS2_FP16_ROWSCALED)
+      b += 2 * off + 8 * n + 12 * n + 2 * (off * 6 / 5 + 2);
   }
   if (c.has_precond && c.precond.kind == GS2_PC_GS) b += 8 * n;
   // hybrid form: the local block of A, the couplings, the local triangles
   // (with their low-precision copies) and the exchange vector
   if (c.has_precond && c.precond.parts > 1) {
     b += 12 * nnz + 12 * off + 4 * 4 * (n + 17) + 8 * n;
-    if (c.precond.precision == GS2_FP32) b += 4 * off;
-    if (c.precond.precision == GS2_FP16_ROWSCALED) b += 2 * off + 4 * n;
+    b += sell_bytes(nnz, n, 8) + 2 * sell_bytes(off / 2 + 1, n, 8) + 4 * (n / 32 + 2);
+    if (c.precond.precision == GS2_FP32) b += 4 * off + 4 * (off * 6 / 5 + 2);
+    if (c.precond.precision == GS2_FP16_ROWSCALED) b += 2 * off + 4 * n + 2 * (off * 6 / 5 + 2);
   }
   // colour matrices: the off-diagonal entries again, row lists, row
   // pointers and tile descriptors, plus per-colour allocation slack
   if (c.has_precond && c.precond.kind == GS2_PC_MTGS)
-    b += 12 * off + 8 * n + 4 * (n / 16 + 16) * 16 + (1 << 18);
+    b += 12 * off + 8 * n + 4 * (n / 16 + 16) * 16 + (1 << 18) + sell_bytes(off, n, 8);
   // multigrid hierarchy: coarse matrices with their triangles and resident
   // vectors (operator complexity below ~1.6 for the model problems), the
   // transfer operators P and R (about 6 entries per fine row each), level
   // vectors and the coarsest inverse
   if (c.has_precond && (c.precond.kind == GS2_PC_AMG || c.precond.kind == GS2_PC_AMG_JR))
-    b += 40 * nnz + 160 * n + (64 << 20);
+    b += 60 * nnz + 160 * n + (64 << 20);
   return b + (1 << 20);
 }
 

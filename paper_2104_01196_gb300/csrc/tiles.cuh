@@ -294,7 +294,7 @@ k_tiles(TileMat<VT> M, Epi epi, const int* skip) {
 // ---------------------------------------------------------------------------
 
 // ---------------------------------------------------------------------------
-// sliced-ELL rows (short rows, one thread per row, one warp per chunk of 32
+// sliced-ELL rows (one thread per row, one warp per chunk of 32
 // rows): slot k of the warp's rows is one coalesced 32-wide load of columns
 // and one of values, streamed with evict-first hints so the gathered vector
 // stays in L2; no shared memory and no block barrier.  Rows are reduced in

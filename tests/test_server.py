@@ -208,3 +208,37 @@ def test_a_bad_request_in_a_pack_fails_alone(lib):
     for (info, x, _), p in zip(out[2:], good[1:]):
         r = np.linalg.norm(p.b - P.csr_matvec(p.A, x)) / np.linalg.norm(p.b)
         assert r <= 1e-8
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("pc_name", ["sgs2", "sgs2_fp32", "sgs2_fp16", "mtgs", "gs", "jr",
+                                     "hybrid4", "amg"])
+def test_footprint_bounds_what_a_handle_allocates(lib, pc_name):
+    """The admission estimate is an upper bound of the device bytes a handle
+    holds after solving with that preconditioner (matrix, triangles, their
+    sliced-ELL and lower-precision copies, level sets or colours, the
+    hierarchy, the Krylov workspace), on short- and long-row matrices."""
+    import torch
+    pcs = {
+        "sgs2": gs2.params("gs2", 1, 1, direction="symmetric"),
+        "sgs2_fp32": gs2.params("gs2", 1, 1, direction="symmetric", precision="fp32"),
+        "sgs2_fp16": gs2.params("gs2", 1, 1, direction="symmetric", precision="fp16"),
+        "mtgs": gs2.params("mtgs", 1, direction="symmetric"),
+        "gs": gs2.params("gs", 1, direction="symmetric"),
+        "jr": gs2.params("jr", 2, omega=0.7),
+        "hybrid4": gs2.params("gs2", 1, 1, direction="symmetric", parts=4),
+        "amg": gs2.params("amg", 1, 1, direction="symmetric"),
+    }
+    pc = pcs[pc_name]
+    for pr in (P.poisson2d(40), P.poisson3d(16), P.convdiff3d(12), P.elasticity3d(6)):
+        prec = {"sgs2_fp32": ("fp32",), "sgs2_fp16": ("fp16",)}.get(pc_name, ())
+        h = gs2.gs2_setup(pr.A, precisions=prec)
+        if pc_name == "amg":
+            h.amg_setup()
+        b = torch.from_numpy(pr.b).cuda()
+        x = torch.zeros(pr.n, dtype=torch.float64, device="cuda")
+        gs2.gmres_solve(h, b, x, 30, 1e-8, 60, pc)
+        used = h.stats()["device_bytes"]
+        h.close()
+        fp = gs2.server_footprint(pr.n, pr.nnz, restart=30, precond=pc)
+        assert used <= fp, (pr.name, pc_name, used, fp)
