@@ -312,7 +312,11 @@ __device__ __forceinline__ float stream_val<__half>(const __half* p) {
   return __half2float(__ushort_as_half(__ldcs(reinterpret_cast<const unsigned short*>(p))));
 }
 
-template <typename VT, class Epi>
+// LONG (matrices with long rows): the next group's slots are loaded while
+// the current group's gathers are in flight, one dependent round trip per
+// group of four instead of two.  Its extra registers would cost short-row
+// matrices occupancy, so it is a separate instantiation.
+template <typename VT, class Epi, bool LONG>
 __global__ void __launch_bounds__(kRowThreads)
 k_sell(int n, int nchunks, const int* __restrict__ cptr, const int* __restrict__ ci,
        const VT* __restrict__ va, Epi epi, const int* skip, const int* __restrict__ live) {
@@ -332,6 +336,36 @@ k_sell(int n, int nchunks, const int* __restrict__ cptr, const int* __restrict__
     const VT* vv = va + base + lane;
     AT s = AT(0);
     int k = 0;
+    if (LONG && L >= 8) {
+      int c0 = __ldcs(cc), c1 = __ldcs(cc + 32), c2 = __ldcs(cc + 64), c3 = __ldcs(cc + 96);
+      AT a0 = stream_val<VT>(vv), a1 = stream_val<VT>(vv + 32);
+      AT a2 = stream_val<VT>(vv + 64), a3 = stream_val<VT>(vv + 96);
+      for (; k + 8 <= L; k += 4) {
+        cc += 128;
+        vv += 128;
+        const AT x0 = (AT)epi.gather(c0), x1 = (AT)epi.gather(c1);
+        const AT x2 = (AT)epi.gather(c2), x3 = (AT)epi.gather(c3);
+        const int n0 = __ldcs(cc), n1 = __ldcs(cc + 32), n2 = __ldcs(cc + 64), n3 = __ldcs(cc + 96);
+        const AT b0 = stream_val<VT>(vv), b1 = stream_val<VT>(vv + 32);
+        const AT b2 = stream_val<VT>(vv + 64), b3 = stream_val<VT>(vv + 96);
+        s = fma(a0, x0, s);
+        s = fma(a1, x1, s);
+        s = fma(a2, x2, s);
+        s = fma(a3, x3, s);
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        a0 = b0; a1 = b1; a2 = b2; a3 = b3;
+      }
+      // the last preloaded group
+      const AT x0 = (AT)epi.gather(c0), x1 = (AT)epi.gather(c1);
+      const AT x2 = (AT)epi.gather(c2), x3 = (AT)epi.gather(c3);
+      s = fma(a0, x0, s);
+      s = fma(a1, x1, s);
+      s = fma(a2, x2, s);
+      s = fma(a3, x3, s);
+      k += 4;
+      cc += 128;
+      vv += 128;
+    }
     // groups of four: all loads and gathers are in flight before the FMAs
     for (; k + 4 <= L; k += 4, cc += 128, vv += 128) {
       const int c0 = __ldcs(cc), c1 = __ldcs(cc + 32), c2 = __ldcs(cc + 64), c3 = __ldcs(cc + 96);
@@ -403,7 +437,10 @@ template <typename VT, class Epi>
 inline void launch_sell(gs2_handle* h, const DevCsr& M, const VT* sv, const Epi& epi,
                         const int* skip) {
   if (M.n == 0 || M.sell_chunks == 0) return;
-  auto fn = k_sell<VT, Epi>;
+  // mean rows longer than 24 entries take the software-pipelined form
+  // (Q1 elasticity, 77 per row: GMRES+SGS2(1,2) 90.3 -> 81.8 ms per 120
+  // iterations; on 7-entry rows it was 2% slower)
+  auto fn = M.mean_row > 24.0 ? k_sell<VT, Epi, true> : k_sell<VT, Epi, false>;
   const int per_sm = blocks_per_sm((const void*)fn, 0);
   const int warps = kRowThreads / 32;
   const int grid = std::max(1, std::min((M.sell_chunks + warps - 1) / warps, per_sm * h->nsm));
