@@ -1,7 +1,9 @@
 """GPU parity on the elasticity and convection-diffusion model problems.
 
-Q1 hexahedral elasticity (SPD, ~81 entries per row: the K-lane row path)
-with SGS2 in FP64 and with FP32 triangle values; 3D first-order upwind
+Q1 hexahedral elasticity (SPD, ~81 entries per row: the K-lane row tiles at
+10^3 nodes; at 64^3 nodes, whose CSR streams from HBM, the software-pipelined
+one-lane-per-row sliced-ELL path) with SGS2 in FP64 and with FP32 triangle
+values; 3D first-order upwind
 convection-diffusion (nonsymmetric) with GS2 inner sweeps in FP64, FP32 and
 FP16 with a per-row scale, outer residual and Arnoldi in FP64.  FP64 sweeps
 match the oracle to 1e-12; lower-precision results are compared with the
