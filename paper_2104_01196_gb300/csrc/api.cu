@@ -259,7 +259,6 @@ void retile(gs2_handle* h, DevCsr& M, const std::vector<int>& rp, int K, int RPT
 // per row shorten each row's chain of dependent gathers.
 constexpr int kSellC = 32;                       // rows per chunk (one warp)
 constexpr double kSellMaxPadding = 1.2;          // slots / entries
-constexpr double kSellShortRow = 24;             // mean entries per row
 constexpr double kSellStreamBytes = 128.0 * (1 << 20);  // CSR bytes beyond L2
 
 // chunk offsets: chunk c takes (longest row of the chunk) x 32 slots; empty
@@ -284,7 +283,7 @@ static std::vector<int> sell_layout(const std::vector<int>& rp, int n) {
 static void upload_sell(gs2_handle* h, DevCsr& M, const std::vector<int>& rp) {
   const int n = M.n;
   if (n == 0 || M.nnz == 0) return;
-  if (M.mean_row > kSellShortRow && 12.0 * M.nnz < kSellStreamBytes) return;
+  if (M.mean_row > kShortRowMean && 12.0 * M.nnz < kSellStreamBytes) return;
   std::vector<int> cptr = sell_layout(rp, n);
   if (cptr.empty() || cptr.back() > kSellMaxPadding * M.nnz) return;
   const size_t slots = std::max(cptr.back(), 1);

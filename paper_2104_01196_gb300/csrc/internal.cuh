@@ -506,6 +506,10 @@ inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
 int vec_blocks(gs2_handle* h, int64_t n);
 constexpr int kVecThreads = 256;
 constexpr int kRowThreads = 256;
+// Mean row length up to which one lane per row is the natural width: such
+// matrices always get a sliced-ELL copy (when it pads little), longer rows
+// only when they stream from HBM, and then take the pipelined instantiation.
+constexpr double kShortRowMean = 24.0;
 constexpr int kMaxRestart = 64;
 
 }  // namespace gs2

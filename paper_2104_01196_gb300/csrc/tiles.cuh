@@ -440,7 +440,7 @@ inline void launch_sell(gs2_handle* h, const DevCsr& M, const VT* sv, const Epi&
   // mean rows longer than 24 entries take the software-pipelined form
   // (Q1 elasticity, 77 per row: GMRES+SGS2(1,2) 90.3 -> 81.8 ms per 120
   // iterations; on 7-entry rows it was 2% slower)
-  auto fn = M.mean_row > 24.0 ? k_sell<VT, Epi, true> : k_sell<VT, Epi, false>;
+  auto fn = M.mean_row > kShortRowMean ? k_sell<VT, Epi, true> : k_sell<VT, Epi, false>;
   const int per_sm = blocks_per_sm((const void*)fn, 0);
   const int warps = kRowThreads / 32;
   const int grid = std::max(1, std::min((M.sell_chunks + warps - 1) / warps, per_sm * h->nsm));
