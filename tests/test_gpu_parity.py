@@ -526,3 +526,42 @@ def test_handles_release_all_device_memory(g):
         cycle()
     free1 = torch.cuda.mem_get_info()[0]
     assert free0 - free1 < 4 << 20, (free0, free1)
+
+
+def _long_row_stream_matrix(n=400_000, seed=29):
+    """Rows of 25..32 entries, the length constant inside each 32-row chunk and
+    cycling over chunks (every remainder mod 4 of the chunk length, no
+    padding), CSR of ~137 MB: above the L2, so A takes the pipelined
+    long-row sliced-ELL path.  Columns i + 997 k (mod n), diagonally dominant."""
+    rng = np.random.default_rng(seed)
+    lens = 25 + (np.arange(n) // 32) % 8
+    rp = np.zeros(n + 1, dtype=np.int64)
+    rp[1:] = np.cumsum(lens)
+    rows = np.repeat(np.arange(n), lens)
+    k = np.arange(rp[-1]) - np.repeat(rp[:-1], lens)  # slot inside the row
+    ci = np.where(k == 0, rows, (rows + 997 * k) % n).astype(np.int32)
+    va = rng.uniform(-1.0, 1.0, rp[-1])
+    off = np.abs(va)
+    off[k == 0] = 0.0
+    rowsum = np.add.reduceat(off, rp[:-1])
+    va[k == 0] = rowsum + 1.0
+    return rp, ci, va
+
+
+def test_long_rows_streamed_from_hbm_match_oracle(g):
+    A = _long_row_stream_matrix()
+    n = len(A[0]) - 1
+    assert 12 * len(A[1]) > 128 * (1 << 20)
+    h = g.gs2_setup(A)
+    assert h.stats()["sell_a"] == 1
+    x0 = P.uniform_pm1(31, n)
+    b = P.uniform_pm1(32, n)
+    y = dev(np.zeros(n))
+    g.gs2_spmv(h, dev(x0), y)
+    assert rel(host(y), oracle.spmv(A, x0)) <= TOL
+    for direction, dname in ((oracle.FORWARD, "forward"), (oracle.SYMMETRIC, "symmetric")):
+        x = dev(x0)
+        g.gs2_apply_ex(h, dev(b), x, g.params("gs2", 1, 2, omega=0.9, direction=dname))
+        ref = oracle.gs2(A, b, x0, 1, 2, 0.9, 1.0, direction)
+        assert rel(host(x), ref) <= TOL, dname
+    h.close()
