@@ -20,7 +20,8 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
-_SRCS = [_SRC, os.path.join(_HERE, "amg.c"), os.path.join(_HERE, "hybrid.c")]
+_SRCS = [_SRC, os.path.join(_HERE, "amg.c"), os.path.join(_HERE, "hybrid.c"),
+         os.path.join(_HERE, "lowprec.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 # the same sources built with -fopenmp: the row loops spread over the host
 # cores, bitwise the same results (the multi-core CPU timing)
@@ -31,6 +32,8 @@ _libs = {}
 FORWARD, BACKWARD, SYMMETRIC = 0, 1, 2
 PC_NONE, PC_GS2, PC_JR, PC_GS, PC_MTGS = 0, 1, 2, 3, 4
 PC_HYBRID_GS2, PC_HYBRID_JR, PC_HYBRID_GS = 7, 8, 9
+# inner-sweep precision of GS2 (lowprec.c)
+PREC = {"fp64": 0, "fp32": 1, "fp16": 2}
 
 
 class OracleError(RuntimeError):
@@ -106,15 +109,25 @@ def _load(openmp: bool = False):
             lib.ora_set_hybrid.argtypes = [I32, I32]
             lib.ora_set_hybrid.restype = None
             lib.ora_threads.argtypes = []
+            lib.ora_gs2_lp.argtypes = csr + [P, P, I32, I32, D, D, I32, I32]
+            lib.ora_round_half.argtypes = [D]
+            lib.ora_round_half.restype = D
+            lib.ora_set_precision.argtypes = [I32]
+            lib.ora_set_precision.restype = None
             for f in ("ora_diag", "ora_gs2", "ora_gs", "ora_jr", "ora_levels",
                       "ora_precond", "ora_gmres", "ora_cg", "ora_gs2_compact",
                       "ora_coloring", "ora_mtgs", "ora_amg_levels", "ora_amg_level",
                       "ora_amg_get_matrix", "ora_amg_get_prolongator",
                       "ora_amg_get_aggregates", "ora_amg_vcycle", "ora_gmres_amg",
-                      "ora_cg_amg", "ora_hybrid", "ora_threads"):
+                      "ora_cg_amg", "ora_hybrid", "ora_threads", "ora_gs2_lp"):
                 getattr(lib, f).restype = ctypes.c_int
             _libs[openmp] = lib
     return _libs[openmp]
+
+
+def round_half(v: float) -> float:
+    """IEEE binary16 round-to-nearest-even of v (the oracle's own rounding)."""
+    return float(_load().ora_round_half(float(v)))
 
 
 def threads(openmp: bool = False) -> int:
@@ -162,10 +175,18 @@ def diag(A):
     return d
 
 
-def gs2(A, b, x, outer=1, inner=1, omega=1.0, gamma=1.0, direction=FORWARD, openmp=False):
-    """Non-compact GS2 sweeps (Eq. 2-5, damped); returns the new x."""
+def gs2(A, b, x, outer=1, inner=1, omega=1.0, gamma=1.0, direction=FORWARD, openmp=False,
+        precision="fp64"):
+    """Non-compact GS2 sweeps (Eq. 2-5, damped); returns the new x.  With
+    precision "fp32" or "fp16" the inner sweeps run in that precision
+    (lowprec.c: FP32 values, or FP16 values with a per-row scale; FP32
+    vectors and accumulation; residual and update FP64)."""
     n, rp, ci, va = _csr(A)
     b, x = _vec(b, n), _vec(x, n)
+    if precision != "fp64":
+        _check(_load().ora_gs2_lp(n, _p(rp), _p(ci), _p(va), _p(b), _p(x), outer, inner,
+                                  omega, gamma, direction, PREC[precision]), "ora_gs2_lp")
+        return x
     _check(_load(openmp).ora_gs2(n, _p(rp), _p(ci), _p(va), _p(b), _p(x), outer, inner,
                            omega, gamma, direction), "ora_gs2")
     return x
@@ -227,14 +248,17 @@ def precond(A, v, kind=PC_GS2, outer=1, inner=1, omega=1.0, gamma=1.0,
 
 def gmres(A, b, x0=None, restart=30, tol=1e-8, max_iters=10000, pc_kind=PC_GS2,
           pc_outer=1, pc_inner=1, pc_omega=1.0, pc_gamma=1.0,
-          pc_direction=FORWARD, history=False, pc_parts=1, pc_local=1):
+          pc_direction=FORWARD, history=False, pc_parts=1, pc_local=1,
+          pc_precision="fp64"):
     """Restarted right-preconditioned GMRES with CGS2.
 
     Returns (x, SolveInfo[, history]).  A non-converged solve is returned with
     its status rather than raised, so tests can check the status.  The
-    hybrid kinds use pc_parts blocks and pc_local local sweeps.
+    hybrid kinds use pc_parts blocks and pc_local local sweeps; the GS2 kind
+    runs its inner sweeps in pc_precision ("fp64", "fp32", "fp16").
     """
     _load().ora_set_hybrid(pc_parts, pc_local)
+    _load().ora_set_precision(PREC[pc_precision])
     n, rp, ci, va = _csr(A)
     b = _vec(b, n)
     x = np.zeros(n) if x0 is None else _vec(x0, n)
@@ -254,9 +278,11 @@ def gmres(A, b, x0=None, restart=30, tol=1e-8, max_iters=10000, pc_kind=PC_GS2,
 
 def cg(A, b, x0=None, tol=1e-8, max_iters=10000, pc_kind=PC_GS2, pc_outer=1,
        pc_inner=1, pc_omega=1.0, pc_gamma=1.0, pc_direction=SYMMETRIC, pc_parts=1,
-       pc_local=1):
-    """Preconditioned CG; returns (x, SolveInfo)."""
+       pc_local=1, pc_precision="fp64"):
+    """Preconditioned CG; returns (x, SolveInfo).  The GS2 kind runs its
+    inner sweeps in pc_precision ("fp64", "fp32", "fp16")."""
     _load().ora_set_hybrid(pc_parts, pc_local)
+    _load().ora_set_precision(PREC[pc_precision])
     n, rp, ci, va = _csr(A)
     b = _vec(b, n)
     x = np.zeros(n) if x0 is None else _vec(x0, n)

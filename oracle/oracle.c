@@ -307,6 +307,9 @@ int ora_precond(int64_t n, const int64_t* rp, const int32_t* ci,
       memcpy(z, v, (size_t)n * sizeof(double));
       return 0;
     case ORA_PC_GS2:
+      if (ora_precision != ORA_PREC_FP64)
+        return ora_gs2_lp(n, rp, ci, va, v, z, outer, inner, omega, gamma, dir,
+                          ora_precision);
       return ora_gs2(n, rp, ci, va, v, z, outer, inner, omega, gamma, dir);
     case ORA_PC_JR:
       return ora_jr(n, rp, ci, va, v, z, outer, omega);

@@ -139,6 +139,25 @@ int ora_hybrid(int64_t n, const int64_t* rp, const int32_t* ci, const double* va
 /* partition and local sweeps of the hybrid preconditioner kinds */
 void ora_set_hybrid(int parts, int local);
 
+/* ------------------------------------------------------------------ */
+/* GS2 with lower-precision inner sweeps (lowprec.c; the definitions    */
+/* are stated there): FP32 values and vectors, or FP16 values with a    */
+/* per-row FP32 scale, FP32 accumulation; residual and update in FP64.  */
+/* ------------------------------------------------------------------ */
+
+enum { ORA_PREC_FP64 = 0, ORA_PREC_FP32 = 1, ORA_PREC_FP16_ROWSCALED = 2 };
+
+/* GS2 sweeps as ora_gs2 with the inner sweeps in precision `prec`
+ * (ORA_PREC_FP64 is ora_gs2 itself).  x in place. */
+int ora_gs2_lp(int64_t n, const int64_t* rp, const int32_t* ci, const double* va,
+               const double* b, double* x, int outer, int inner, double omega,
+               double gamma, int dir, int prec);
+/* IEEE binary16 round-to-nearest-even of v (returned exactly as a double) */
+double ora_round_half(double v);
+/* inner-sweep precision of the ORA_PC_GS2 preconditioner kind */
+void ora_set_precision(int prec);
+extern _Thread_local int ora_precision;
+
 /* Threads the row loops run on: the OpenMP thread count in a build with
  * -fopenmp, else 1. */
 int ora_threads(void);

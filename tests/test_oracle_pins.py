@@ -827,3 +827,131 @@ def test_openmp_build_is_bitwise_the_sequential_oracle():
     assert np.array_equal(oracle.jr(pr.A, pr.b, x0, 3, 0.7),
                           oracle.jr(pr.A, pr.b, x0, 3, 0.7, openmp=True))
     assert np.array_equal(oracle.spmv(pr.A, x0), oracle.spmv(pr.A, x0, openmp=True))
+
+
+# ---------------------------------------------------------------------------
+# Lower-precision inner sweeps (Sec. 10; the FP16 row-scaled form of this
+# library): IEEE binary16 rounding, exactness where every value is
+# representable, the error bounds of the value precision, and the per-row
+# scale that keeps FP16 in range
+# ---------------------------------------------------------------------------
+
+def test_round_half_is_ieee_binary16():
+    rng = np.random.default_rng(3)
+    v = np.concatenate([
+        rng.choice([-1.0, 1.0], 4000) * 10.0 ** rng.uniform(-9, 5, 4000),
+        [0.0, 1.0, 65504.0, 65519.99, 65520.0, 70000.0, 2.0 ** -24, 2.0 ** -25,
+         3 * 2.0 ** -26, 2.0 ** -14, 2.0 ** -14 - 2.0 ** -25],
+    ])
+    # exact halfway points between consecutive binary16 values (ties to even)
+    h = np.float16(rng.uniform(-1000, 1000, 2000))
+    up = np.nextafter(h, np.float16(np.inf))
+    mid = (h.astype(np.float64) + up.astype(np.float64)) / 2
+    v = np.concatenate([v, mid])
+    with np.errstate(over="ignore"):
+        want = v.astype(np.float16).astype(np.float64)
+    got = np.array([oracle.round_half(t) for t in v])
+    assert np.array_equal(got, want)
+
+
+def dyadic_nonsym_csr(N=6, seed=4):
+    """A nonsymmetric 2D-pattern matrix with diagonal 16 and off-diagonals
+    from {-1, -2, -4}: D^{-1}T entries are -1/16, -1/8, -1/4 and their ratio to
+    the row maximum is a power of two, so every stored value is exact in
+    FP32 and in row-scaled FP16."""
+    rng = np.random.default_rng(seed)
+    n = N * N
+    M = np.zeros((n, n))
+    for i in range(N):
+        for j in range(N):
+            r = i * N + j
+            M[r, r] = 16.0
+            for di, dj in ((-1, 0), (1, 0), (0, -1), (0, 1)):
+                a, c = i + di, j + dj
+                if 0 <= a < N and 0 <= c < N:
+                    M[r, a * N + c] = -float(rng.choice([1, 2, 4]))
+    return P.dense_to_csr(M), n
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_lowprec_gs2_exact_when_every_value_is_representable(prec):
+    """With dyadic data whose every intermediate fits in 24 bits the
+    lower-precision sweep performs exactly the FP64 sweep's arithmetic, so
+    it must equal the FP64 oracle bitwise: a dropped row scale, a wrong
+    triangle, sign or damping placement breaks the equality."""
+    A, n = dyadic_nonsym_csr()
+    rng = np.random.default_rng(8)
+    b = rng.integers(-32, 33, n) / 16.0
+    x0 = rng.integers(-64, 65, n) / 64.0
+    for kw in (dict(outer=1, inner=2, omega=0.75, gamma=0.5, direction=oracle.FORWARD),
+               dict(outer=1, inner=2, omega=1.0, gamma=1.0, direction=oracle.BACKWARD),
+               dict(outer=1, inner=1, omega=1.0, gamma=1.0, direction=oracle.SYMMETRIC),
+               dict(outer=1, inner=0, omega=0.5, gamma=1.0, direction=oracle.FORWARD)):
+        ref = oracle.gs2(A, b, x0, **kw)
+        got = oracle.gs2(A, b, x0, precision=prec, **kw)
+        assert np.array_equal(got, ref), kw
+
+
+def test_lowprec_gs2_error_within_the_value_precision():
+    """Non-dyadic data: FP32 sweeps differ from FP64 by a few FP32 rounding
+    units (u = 2^-24), FP16 values by a few FP16 units (2^-11), and both do
+    differ (the rounding is really applied)."""
+    A = tiny_nonsym(n=60, seed=12)
+    rng = np.random.default_rng(2)
+    b, x0 = rng.uniform(-1, 1, 60), rng.uniform(-1, 1, 60)
+    for d in (oracle.FORWARD, oracle.SYMMETRIC):
+        ref = oracle.gs2(A, b, x0, 1, 2, 0.9, 0.8, d)
+        dx = np.linalg.norm(ref - x0)
+        e32 = np.linalg.norm(oracle.gs2(A, b, x0, 1, 2, 0.9, 0.8, d, precision="fp32") - ref)
+        e16 = np.linalg.norm(oracle.gs2(A, b, x0, 1, 2, 0.9, 0.8, d, precision="fp16") - ref)
+        assert 1e-10 * dx < e32 < 40 * 2.0 ** -24 * dx
+        assert 40 * 2.0 ** -24 * dx < e16 < 40 * 2.0 ** -11 * dx
+
+
+def test_lowprec_fp16_row_scale_keeps_far_out_of_range_values():
+    """A 10x10 grid whose rows alternate (checkerboard) between a diagonal
+    of the off-diagonal size and one 2^28 times larger: the heavy rows have
+    prescaled entries D^{-1}T near 2^-28 = 3.7e-9, below binary16's
+    smallest subnormal (6e-8), and couple to light rows whose iterates are
+    2^28 times their own, so those couplings decide the heavy rows' result.
+    Stored unscaled they would vanish; the per-row scale keeps them, so the
+    FP16 sweep matches the FP64 sweep to FP16 accuracy (errors measured in
+    the balanced quantity D x) in a forward sweep, while dropping the
+    couplings (zero inner sweeps) is far off."""
+    N = 10
+    rng = np.random.default_rng(5)
+    n = N * N
+    M = np.zeros((n, n))
+    for i in range(N):
+        for j in range(N):
+            r = i * N + j
+            for di, dj in ((-1, 0), (1, 0), (0, -1), (0, 1)):
+                a, c = i + di, j + dj
+                if 0 <= a < N and 0 <= c < N:
+                    M[r, a * N + c] = -rng.uniform(0.2, 1.0)
+            M[r, r] = (np.abs(M[r]).sum() + 1.0) * (2.0 ** 28 if (i + j) % 2 else 1.0)
+    d = np.diag(M).copy()
+    A = P.dense_to_csr(M)
+    b = rng.uniform(-1, 1, n)
+    ref = oracle.gs2(A, b, np.zeros(n), 1, 2, 1.0, 1.0, oracle.FORWARD)
+    got = oracle.gs2(A, b, np.zeros(n), 1, 2, 1.0, 1.0, oracle.FORWARD, precision="fp16")
+    assert np.all(np.isfinite(got))
+    assert np.linalg.norm(d * (got - ref)) <= 5e-3 * np.linalg.norm(d * ref)
+    jr = oracle.gs2(A, b, np.zeros(n), 1, 0, 1.0, 1.0, oracle.FORWARD)
+    assert np.linalg.norm(d * (jr - ref)) >= 0.1 * np.linalg.norm(d * ref)
+
+
+def test_lowprec_gmres_keeps_the_iteration_count():
+    """Sec. 10: a single-precision preconditioner leaves the GMRES iteration
+    count of the double-precision solve essentially unchanged; the FP16
+    row-scaled form stays close as well on a well-conditioned problem."""
+    pr = P.poisson2d(48)
+    _, i64 = oracle.gmres(pr.A, pr.b, restart=30, tol=1e-8, max_iters=3000,
+                          pc_kind=oracle.PC_GS2, pc_direction=oracle.SYMMETRIC)
+    for prec, slack in (("fp32", 1), ("fp16", 3)):
+        x, i = oracle.gmres(pr.A, pr.b, restart=30, tol=1e-8, max_iters=3000,
+                            pc_kind=oracle.PC_GS2, pc_direction=oracle.SYMMETRIC,
+                            pc_precision=prec)
+        assert i.status == 0 and abs(i.iters - i64.iters) <= slack, (prec, i, i64)
+        r = np.linalg.norm(pr.b - oracle.spmv(pr.A, x)) / np.linalg.norm(pr.b)
+        assert r <= 1e-8
