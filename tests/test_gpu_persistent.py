@@ -61,33 +61,94 @@ PCS = {
 }
 
 
+# Restarted GMRES with a 5-vector basis on the small Q1 elasticity problem is
+# rounding-sensitive: perturbing b by one unit in the last place changes the
+# oracle's own iteration count over a wide range (gs2_bwd_2_0: 301..681, jr_4:
+# 287..489), because every restart keeps only a 5-dimensional Krylov space and
+# the tiny differences between two runs grow by about 1e14 within 10 to 40
+# steps.  There an iteration count agreeing to +-1 is not a property of the
+# method but of one rounding sequence, so these cases assert instead that (1)
+# the oracle itself is sensitive (a one-ulp ensemble spreads by more than 2),
+# (2) the GPU tracks the oracle's true residual step by step to 1e-10 for as
+# long as the oracle tracks itself to 1e-12, and (3) the GPU's count lies in
+# the ensemble's range widened by 15%.  Two settings stagnate at restart 5 on
+# elasticity in every run: both sides must return NOT_CONVERGED.
+SENSITIVE = {("elasticity3d_4", 5, pc) for pc in ("none", "gs2_bwd_2_0", "jr_3_w0.8", "jr_4")}
+STAGNATING = {("elasticity3d_4", 5, pc) for pc in ("gs2_fwd_1_1", "jr_2_w0.9")}
+ULP = 2.0 ** -52
+
+
+def oracle_ensemble(pr, restart, op, members=12, seed=7):
+    """The oracle's solve of A x = b(1 + e), e_i ~ one ulp (seeded), for
+    `members` perturbations: their iteration counts and statuses."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(members):
+        bp = pr.b * (1.0 + ULP * rng.standard_normal(pr.n))
+        _, oi = oracle.gmres(pr.A, bp, restart=restart, tol=1e-8, max_iters=6000, **op)
+        out.append(oi)
+    return out
+
+
+def tracking_horizon(pr, restart, op, kmax=40, members=4, seed=11):
+    """Per step k <= kmax the oracle's true relative residual after k Arnoldi
+    steps (a solve stopped by max_iters = k), and the largest k up to which
+    one-ulp perturbations of b leave it within 1e-12 (the steps over which the
+    oracle agrees with itself)."""
+    rng = np.random.default_rng(seed)
+    pert = [pr.b * (1.0 + ULP * rng.standard_normal(pr.n)) for _ in range(members)]
+    base, horizon = [], 0
+    for k in range(1, kmax + 1):
+        _, oi = oracle.gmres(pr.A, pr.b, restart=restart, tol=1e-8, max_iters=k, **op)
+        base.append(oi.true_relres)
+        spread = max(abs(oracle.gmres(pr.A, bp, restart=restart, tol=1e-8, max_iters=k,
+                                      **op)[1].true_relres - oi.true_relres) / oi.true_relres
+                     for bp in pert)
+        if spread <= 1e-12 and horizon == k - 1:
+            horizon = k
+    return base, horizon
+
+
+def check_sensitive(g, h, pr, restart, prm, op, info):
+    ens = oracle_ensemble(pr, restart, op)
+    counts = [e.iters for e in ens]
+    assert all(e.status == 0 for e in ens)
+    assert max(counts) - min(counts) > 2, counts  # the case is rounding-sensitive
+    lo, hi = 0.85 * min(counts), 1.15 * max(counts)
+    assert info.status == 0 and lo <= info.iters <= hi, (info.iters, counts)
+    base, horizon = tracking_horizon(pr, restart, op)
+    assert horizon >= 5, horizon  # at least one whole restart cycle
+    for k in range(1, horizon + 1):
+        x = dev(np.zeros(pr.n))
+        ik = g.gmres_solve(h, dev(pr.b), x, restart, 1e-8, k, prm)
+        assert abs(ik.true_relres - base[k - 1]) <= 1e-10 * base[k - 1], (k, ik, base[k - 1])
+
+
 @pytest.mark.parametrize("name", list(PROBS))
 @pytest.mark.parametrize("pc", list(PCS))
 @pytest.mark.parametrize("restart", [5, 30])
 def test_one_launch_matches_oracle_and_multi_kernel_path(g, name, pc, restart):
     pr = PROBS[name]
     gp, op = PCS[pc]
-    if name.startswith("elasticity") and (pc in ("none", "gs2_fwd_1_1", "jr_3_w0.8", "jr_4",
-                                                "jr_2_w0.9")
-                                          or restart == 5):
-        # stagnation; and GMRES(5) on elasticity is rounding-sensitive: the
-        # multi-kernel path takes 517 steps there, the oracle 374
-        pytest.skip("stagnating or rounding-sensitive on elasticity")
+    case = (name, restart, pc)
     prm = g.params(**gp) if gp else None
     h = g.gs2_setup(pr.A)
-    h.set_graph_mode(3)
-    x = dev(np.zeros(pr.n))
-    info = g.gmres_solve(h, dev(pr.b), x, restart, 1e-8, 6000, prm)
     _, oinfo = oracle.gmres(pr.A, pr.b, restart=restart, tol=1e-8, max_iters=6000, **op)
-    assert info.status == 0 and oinfo.status == 0
-    assert abs(info.iters - oinfo.iters) <= 1, (info.iters, oinfo.iters)
-    r = np.linalg.norm(pr.b - oracle.spmv(pr.A, host(x))) / np.linalg.norm(pr.b)
-    assert r <= 1e-8 and abs(info.true_relres - r) <= 1e-12
-    h.set_graph_mode(1)
-    xg = dev(np.zeros(pr.n))
-    ig = g.gmres_solve(h, dev(pr.b), xg, restart, 1e-8, 6000, prm)
-    assert abs(ig.iters - info.iters) <= 1
-    assert np.linalg.norm(host(xg) - host(x)) <= 1e-6 * np.linalg.norm(host(x))
+    for mode in (3, 1):  # the one-launch solver, then the multi-kernel path (graphs)
+        h.set_graph_mode(mode)
+        x = dev(np.zeros(pr.n))
+        info = g.gmres_solve(h, dev(pr.b), x, restart, 1e-8, 6000, prm)
+        if case in STAGNATING:
+            assert oinfo.status == 5 and info.status == 5, (info, oinfo)
+            assert info.iters == oinfo.iters == 6000
+            continue
+        if case in SENSITIVE:
+            check_sensitive(g, h, pr, restart, prm, op, info)
+        else:
+            assert info.status == 0 and oinfo.status == 0, (info, oinfo)
+            assert abs(info.iters - oinfo.iters) <= 1, (mode, info.iters, oinfo.iters)
+        r = np.linalg.norm(pr.b - oracle.spmv(pr.A, host(x))) / np.linalg.norm(pr.b)
+        assert r <= 1e-8 and abs(info.true_relres - r) <= 1e-12
 
 
 def test_one_launch_statuses_and_reproducibility(g):
