@@ -11,7 +11,8 @@
  *   rhat  = fl32(D^{-1} r)                           rounded once, at the boundary
  *   FP32:  t_ij = fl32((D^{-1} T)_ij)
  *   FP16:  m_i = max_j |(D^{-1} T)_ij|,  sigma_i = fl32(m_i),
- *          q_ij = fl16((D^{-1} T)_ij / m_i),  t_ij = sigma_i q_ij
+ *          q_ij = fl16((D^{-1} T)_ij / m_i)  (0 when m_i = 0: a row whose
+ *          stored triangle entries are all zero),  t_ij = sigma_i q_ij
  *   g^(0) = rhat
  *   s_i   = sum_j t_ij g_j          FP32 operations, the row's stored order
  *           (FP16: sigma_i (sum_j q_ij g_j), the scale applied once per row)
@@ -92,7 +93,7 @@ static void lp_half(int64_t n, const int64_t* rp, const int32_t* ci, const doubl
         const double t64 = va[k] / d[i];
         float t;
         if (prec == ORA_PREC_FP32) t = (float)t64;
-        else t = (float)ora_round_half(t64 / m);  /* q_ij (m > 0 here) */
+        else t = m > 0.0 ? (float)ora_round_half(t64 / m) : 0.0f;  /* q_ij */
         const float p = t * g[c];
         s = s + p;
       }

@@ -325,6 +325,8 @@ int ora_precond(int64_t n, const int64_t* rp, const int32_t* ci,
                                                   : (kind == ORA_PC_HYBRID_JR ? ORA_PC_JR
                                                                               : ORA_PC_GS),
                         ora_hybrid_parts, outer, ora_hybrid_local, inner, omega, gamma, dir);
+    case ORA_PC_GS2_COMPACT:
+      return ora_gs2_compact(n, rp, ci, va, v, z, outer, inner, dir);
     case ORA_PC_AMG:
     case ORA_PC_AMG_JR:
       if (!ora_amg_current) return 1;

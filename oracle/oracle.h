@@ -27,7 +27,7 @@ extern "C" {
 enum { ORA_FORWARD = 0, ORA_BACKWARD = 1, ORA_SYMMETRIC = 2 };
 enum { ORA_PC_NONE = 0, ORA_PC_GS2 = 1, ORA_PC_JR = 2, ORA_PC_GS = 3,
        ORA_PC_MTGS = 4, ORA_PC_AMG = 5, ORA_PC_AMG_JR = 6, ORA_PC_HYBRID_GS2 = 7,
-       ORA_PC_HYBRID_JR = 8, ORA_PC_HYBRID_GS = 9 };
+       ORA_PC_HYBRID_JR = 8, ORA_PC_HYBRID_GS = 9, ORA_PC_GS2_COMPACT = 10 };
 
 typedef struct {
   int iters;          /* total Arnoldi steps over all cycles */
@@ -91,7 +91,8 @@ int ora_mtgs(int64_t n, const int64_t* rp, const int32_t* ci, const double* va,
  * outer = sweeps), ORA_PC_AMG / ORA_PC_AMG_JR (one V-cycle of the hierarchy
  * ora_gmres_amg installs, GS2 / JR smoother with these parameters),
  * ORA_PC_HYBRID_GS2 / ORA_PC_HYBRID_JR / ORA_PC_HYBRID_GS (ora_hybrid with
- * the partition and local sweeps set by ora_set_hybrid; outer = n_t). */
+ * the partition and local sweeps set by ora_set_hybrid; outer = n_t),
+ * ORA_PC_GS2_COMPACT (compact GS2 of Eq. (9), undamped). */
 int ora_precond(int64_t n, const int64_t* rp, const int32_t* ci,
                 const double* va, const double* v, double* z, int kind,
                 int outer, int inner, double omega, double gamma, int dir);

@@ -7,6 +7,10 @@ scale factor that turns a timed sample of oracle Arnoldi steps into solves/s.
 
     python tests/golden/make_oracle_counts.py            # every case
     python tests/golden/make_oracle_counts.py KEY ...    # recompute these keys only
+    python tests/golden/make_oracle_counts.py --jobs 6 [KEY ...]   # cases in parallel
+
+Keys ending in _fp32 / _fp16 run the GS2 preconditioner's inner sweeps in
+that precision (the oracle's lowprec.c definitions), everything else FP64.
 """
 import os
 import sys
@@ -42,40 +46,84 @@ CASES = [
      dict(pc_kind=oracle.PC_GS2, pc_inner=2, pc_omega=0.8, pc_direction=oracle.SYMMETRIC)),
     ("convdiff3d_192_gmres30_sgs2_1_1", lambda: P.convdiff3d(192),
      dict(pc_kind=oracle.PC_GS2, pc_inner=1, pc_direction=oracle.SYMMETRIC)),
+    # lower-precision inner sweeps (Sec. 10) and the second elasticity setting
+    ("poisson3d_128_gmres30_sgs2_1_1_fp32", lambda: P.poisson3d(128),
+     dict(pc_kind=oracle.PC_GS2, pc_inner=1, pc_direction=oracle.SYMMETRIC,
+          pc_precision="fp32")),
+    ("poisson3d_128_gmres30_sgs2_1_1_fp16", lambda: P.poisson3d(128),
+     dict(pc_kind=oracle.PC_GS2, pc_inner=1, pc_direction=oracle.SYMMETRIC,
+          pc_precision="fp16")),
+    ("elasticity3d_64_gmres30_sgs2_1_2_w0.8_fp32", lambda: P.elasticity3d(64),
+     dict(pc_kind=oracle.PC_GS2, pc_inner=2, pc_omega=0.8, pc_direction=oracle.SYMMETRIC,
+          pc_precision="fp32")),
+    ("elasticity3d_64_gmres30_sgs2_1_3_w0.9", lambda: P.elasticity3d(64),
+     dict(pc_kind=oracle.PC_GS2, pc_inner=3, pc_omega=0.9, pc_direction=oracle.SYMMETRIC)),
+    ("elasticity3d_64_gmres30_sgs2_1_3_w0.9_fp32", lambda: P.elasticity3d(64),
+     dict(pc_kind=oracle.PC_GS2, pc_inner=3, pc_omega=0.9, pc_direction=oracle.SYMMETRIC,
+          pc_precision="fp32")),
+    ("convdiff3d_192_gmres30_sgs2_1_1_fp32", lambda: P.convdiff3d(192),
+     dict(pc_kind=oracle.PC_GS2, pc_inner=1, pc_direction=oracle.SYMMETRIC,
+          pc_precision="fp32")),
+    ("convdiff3d_192_gmres30_sgs2_1_1_fp16", lambda: P.convdiff3d(192),
+     dict(pc_kind=oracle.PC_GS2, pc_inner=1, pc_direction=oracle.SYMMETRIC,
+          pc_precision="fp16")),
+    # compact GS2 of Eq. (9) as the GMRES preconditioner; CG (tol 1e-8) with
+    # SGS2(1,1) and with the AMG V-cycle
+    ("poisson3d_128_gmres30_compact_sgs2_1_2", lambda: P.poisson3d(128),
+     dict(pc_kind=oracle.PC_GS2_COMPACT, pc_inner=2, pc_direction=oracle.SYMMETRIC)),
+    ("poisson3d_128_cg_sgs2_1_1", lambda: P.poisson3d(128),
+     dict(cg=True, pc_kind=oracle.PC_GS2, pc_inner=1, pc_direction=oracle.SYMMETRIC)),
+    ("poisson3d_128_cg_amg_sgs2_1_1", lambda: P.poisson3d(128),
+     dict(cg=True, amg=True, kind=oracle.PC_GS2, inner=1, direction=oracle.SYMMETRIC)),
 ]
 
 
-def main(only=(), out=os.path.join(HERE, "oracle_counts.txt")):
+def run_case(key):
+    """One case through the oracle: its line of oracle_counts.txt."""
     oracle.build()
-    header = ["# GMRES(30), x0 = 0, rel. residual 1e-8, max 5000 iterations; FP64 CPU oracle",
+    _, mk, pc = next(c for c in CASES if c[0] == key)
+    pr = mk()
+    t0 = time.time()
+    kw = {k: v for k, v in pc.items() if k not in ("amg", "cg")}
+    if pc.get("amg"):
+        # smoothed-aggregation hierarchy with the default settings
+        # (theta 0.25, 10 levels, coarsest <= 64 rows), one V-cycle
+        M = oracle.AMG(pr.A)
+        if pc.get("cg"):
+            _, info = M.cg(pr.A, pr.b, tol=1e-8, max_iters=5000, **kw)
+        else:
+            _, info = M.gmres(pr.A, pr.b, restart=30, tol=1e-8, max_iters=5000, **kw)
+    elif pc.get("cg"):
+        _, info = oracle.cg(pr.A, pr.b, tol=1e-8, max_iters=5000, **kw)
+    else:
+        _, info = oracle.gmres(pr.A, pr.b, restart=30, tol=1e-8, max_iters=5000, **kw)
+    dt = time.time() - t0
+    line = (f"{key} iters={info.iters} cycles={info.cycles} status={info.status} "
+            f"true_relres={info.true_relres:.6e} seconds={dt:.1f}")
+    print(line, flush=True)
+    return line
+
+
+def main(only=(), out=os.path.join(HERE, "oracle_counts.txt"), jobs=1):
+    oracle.build()
+    header = ["# GMRES(30) (CG where the key says cg), x0 = 0, rel. residual 1e-8, "
+              "max 5000 iterations; FP64 CPU oracle",
+              "# (keys ending _fp32 / _fp16: GS2 inner sweeps in that precision)",
               "# written by tests/golden/make_oracle_counts.py"]
     kept = {}
     if only and os.path.exists(out):
         for line in open(out):
             if line.strip() and not line.startswith("#"):
                 kept[line.split()[0]] = line.rstrip("\n")
-    cache = {}
-    for key, mk, pc in CASES:
-        if only and key not in only:
-            continue
-        name = key.split("_gmres")[0]
-        if name not in cache:
-            cache = {name: mk()}
-        pr = cache[name]
-        t0 = time.time()
-        if pc.get("amg"):
-            # smoothed-aggregation hierarchy with the default settings
-            # (theta 0.25, 10 levels, coarsest <= 64 rows), one V-cycle
-            kw = {k: v for k, v in pc.items() if k != "amg"}
-            _, info = oracle.AMG(pr.A).gmres(pr.A, pr.b, restart=30, tol=1e-8,
-                                             max_iters=5000, **kw)
-        else:
-            _, info = oracle.gmres(pr.A, pr.b, restart=30, tol=1e-8, max_iters=5000, **pc)
-        dt = time.time() - t0
-        line = (f"{key} iters={info.iters} cycles={info.cycles} status={info.status} "
-                f"true_relres={info.true_relres:.6e} seconds={dt:.1f}")
-        print(line, flush=True)
-        kept[key] = line
+    keys = [k for k, _, _ in CASES if not only or k in only]
+    if jobs > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(jobs) as pool:
+            lines = pool.map(run_case, keys, chunksize=1)
+    else:
+        lines = [run_case(k) for k in keys]
+    for k, line in zip(keys, lines):
+        kept[k] = line
     order = [k for k, _, _ in CASES]
     lines = header + [kept[k] for k in order if k in kept]
     with open(out, "w") as f:
@@ -83,4 +131,8 @@ def main(only=(), out=os.path.join(HERE, "oracle_counts.txt")):
 
 
 if __name__ == "__main__":
-    main(tuple(sys.argv[1:]))
+    args = sys.argv[1:]
+    jobs = 1
+    if args[:1] == ["--jobs"]:
+        jobs, args = int(args[1]), args[2:]
+    main(tuple(args), jobs=jobs)
