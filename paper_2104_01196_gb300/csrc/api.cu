@@ -261,40 +261,92 @@ constexpr int kSellC = 32;                       // rows per chunk (one warp)
 constexpr double kSellMaxPadding = 1.2;          // slots / entries
 constexpr double kSellStreamBytes = 128.0 * (1 << 20);  // CSR bytes beyond L2
 
-// chunk offsets: chunk c takes (longest row of the chunk) x 32 slots; empty
-// when the slots would not fit 32-bit offsets
-static std::vector<int> sell_layout(const std::vector<int>& rp, int n) {
+// Chunk layout: chunk c takes width_c x 32 slots, width_c its longest row
+// (explicit columns) or, for an offset chunk, the number of distinct column
+// offsets j - i over its rows.  A chunk is an offset chunk when that union is
+// at most its longest row + kOffsetSlack and at most 32 (stencil rows: the
+// rows at a grid boundary miss some offsets and get zero slots there).
+// Consecutive chunks with the same offset list share one copy.  Returns
+// false when the slots would not fit 32-bit offsets.
+constexpr int kOffsetSlack = 2;
+constexpr int kOffsetMax = 32;
+
+struct SellLayout {
+  std::vector<int> cptr, coff, offs;
+  int offset_chunks = 0;
+};
+
+static bool sell_layout(const std::vector<int>& rp, const int* ci, int n, SellLayout& out) {
   const int nc = (n + kSellC - 1) / kSellC;
-  std::vector<int> cptr(nc + 1, 0);
+  out.cptr.assign(nc + 1, 0);
+  out.coff.assign(nc, -1);
+  out.offs.clear();
+  out.offset_chunks = 0;
   int64_t total = 0;
+  std::vector<int> u;
+  int prev = -1, prev_len = 0;
   for (int c = 0; c < nc; ++c) {
     int L = 0;
-    for (int i = c * kSellC; i < std::min(n, (c + 1) * kSellC); ++i)
+    u.clear();
+    bool regular = true;
+    for (int i = c * kSellC; i < std::min(n, (c + 1) * kSellC); ++i) {
       L = std::max(L, rp[i + 1] - rp[i]);
-    total += (int64_t)L * kSellC;
-    if (total > INT32_MAX) return {};
-    cptr[c + 1] = (int)total;
+      for (int k = rp[i]; regular && k < rp[i + 1]; ++k) {
+        const int o = ci[k] - i;
+        if (std::find(u.begin(), u.end(), o) == u.end()) {
+          u.push_back(o);
+          if ((int)u.size() > kOffsetMax) regular = false;
+        }
+      }
+    }
+    int width = L;
+    if (regular && L > 0 && (int)u.size() <= L + kOffsetSlack) {
+      std::sort(u.begin(), u.end());
+      width = (int)u.size();
+      if (prev >= 0 && prev_len == width &&
+          std::equal(u.begin(), u.end(), out.offs.begin() + prev)) {
+        out.coff[c] = prev;
+      } else {
+        prev = (int)out.offs.size();
+        prev_len = width;
+        out.offs.insert(out.offs.end(), u.begin(), u.end());
+        out.coff[c] = prev;
+      }
+      out.offset_chunks++;
+    }
+    total += (int64_t)width * kSellC;
+    if (total > INT32_MAX) return false;
+    out.cptr[c + 1] = (int)total;
   }
-  return cptr;
+  return true;
 }
 
 // The sliced-ELL arrays are filled on the device from the CSR arrays already
-// there (launch_to_sell); only the chunk offsets are computed here.
-static void upload_sell(gs2_handle* h, DevCsr& M, const std::vector<int>& rp) {
+// there (launch_to_sell); only the chunk layout is computed here.
+static void upload_sell(gs2_handle* h, DevCsr& M, const std::vector<int>& rp, const int* ci) {
   const int n = M.n;
   if (n == 0 || M.nnz == 0) return;
   if (M.mean_row > kShortRowMean && 12.0 * M.nnz < kSellStreamBytes) return;
-  std::vector<int> cptr = sell_layout(rp, n);
-  if (cptr.empty() || cptr.back() > kSellMaxPadding * M.nnz) return;
+  SellLayout lay;
+  if (!sell_layout(rp, ci, n, lay) || lay.cptr.back() > kSellMaxPadding * M.nnz) return;
+  const std::vector<int>& cptr = lay.cptr;
   const size_t slots = std::max(cptr.back(), 1);
+  int ncols = 1;
+  for (int k = 0; k < M.nnz; ++k) ncols = std::max(ncols, ci[k] + 1);
   M.sell_chunks = (int)cptr.size() - 1;
   M.sell_slots = (int)slots;
+  M.sell_ncols = ncols;
+  M.sell_offset_chunks = lay.offset_chunks;
   M.sell_ptr = (int*)h->dalloc(sizeof(int) * cptr.size());
   M.sell_ci = (int*)h->dalloc(sizeof(int) * slots);
   M.sell_va = (double*)h->dalloc(sizeof(double) * slots);
+  M.sell_coff = (int*)h->dalloc(sizeof(int) * std::max<size_t>(lay.coff.size(), 1));
+  M.sell_off = (int*)h->dalloc(sizeof(int) * std::max<size_t>(lay.offs.size(), 1));
   h->dzero(M.sell_ci, sizeof(int) * slots);
   h->dzero(M.sell_va, sizeof(double) * slots);
   h->h2d(M.sell_ptr, cptr.data(), sizeof(int) * cptr.size());
+  h->h2d(M.sell_coff, lay.coff.data(), sizeof(int) * lay.coff.size());
+  if (!lay.offs.empty()) h->h2d(M.sell_off, lay.offs.data(), sizeof(int) * lay.offs.size());
   launch_to_sell(h, M, M.va, M.sell_va, true);
   M.sell = true;
 }
@@ -318,7 +370,7 @@ static void upload_csr(gs2_handle* h, DevCsr& M, int n, const std::vector<int>& 
   h->h2d(M.ci, ci, sizeof(int) * M.nnz);
   h->h2d(M.va, va, sizeof(double) * M.nnz);
   retile(h, M, rp, M.tpr, 1);
-  upload_sell(h, M, rp);
+  upload_sell(h, M, rp, ci);
 }
 
 // (Re)build the row tiles of M for K lanes per row and RPT rows per lane
@@ -370,7 +422,7 @@ static void prepare_lowprec(gs2_handle* h, DevCsr& M, const HostTri& T, int prec
       for (int k = T.rp[i]; k < T.rp[i + 1]; ++k) m = std::max(m, std::fabs(T.va[k]));
       s[i] = (float)m;
       for (int k = T.rp[i]; k < T.rp[i + 1]; ++k)
-        v[k] = __float2half(m > 0 ? (float)(T.va[k] / m) : 0.f);
+        v[k] = __double2half(m > 0 ? T.va[k] / m : 0.0);  // one rounding, to nearest
     }
     M.va16 = (__half*)h->dalloc(sizeof(__half) * nz);
     M.scale16 = (float*)h->dalloc(sizeof(float) * std::max(M.n, 1));
@@ -1099,6 +1151,10 @@ gs2_status gs2_get_stats(const gs2_handle* h, gs2_handle_stats* out) {
   out->colors = h->colors_ready ? (int)h->colors.size() : 0;
   out->sell_a = h->A.sell ? 1 : 0;
   out->sell_tri = h->L.sell ? 1 : 0;
+  out->offset_frac_a =
+      h->A.sell_chunks ? (double)h->A.sell_offset_chunks / h->A.sell_chunks : 0.0;
+  out->offset_frac_tri =
+      h->L.sell_chunks ? (double)h->L.sell_offset_chunks / h->L.sell_chunks : 0.0;
   return GS2_OK;
 }
 

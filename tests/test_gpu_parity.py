@@ -345,6 +345,31 @@ def test_lowprec_sweep_error_vs_fp64_oracle(g, prec, bound):
     assert e <= bound, e
 
 
+LOWPREC_TOL = 1e-6
+
+
+@pytest.mark.parametrize("name", list(MATS))
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_lowprec_sweeps_match_lowprec_oracle(g, name, prec):
+    """FP32 and row-scaled FP16 inner sweeps against the oracle's definition
+    of the same precision (FP64 residual, r-hat rounded to FP32, values in
+    the sweep precision, FP32 accumulation): the two differ only in FP32
+    rounding order (FMA, the order of a row's partial sums), a few units of
+    2^-24 per inner sweep, so 1e-6 relative per vector; every kernel path,
+    direction and damping."""
+    A = MATS[name]
+    b, x0 = rhs_and_x0(A, 11)
+    h = g.gs2_setup(A, precisions=(prec,))
+    for d in (0, 1, 2):
+        for outer, inner, omega, gamma in ((1, 1, 1.0, 1.0), (2, 3, 0.8, 0.7), (1, 0, 1.0, 1.0),
+                                           (1, 2, 1.2, 1.0)):
+            x = dev(x0)
+            g.gs2_apply_ex(h, dev(b), x, g.params("gs2", outer, inner, omega=omega, gamma=gamma,
+                                                  direction=d, precision=prec))
+            ref = oracle.gs2(A, b, x0, outer, inner, omega, gamma, d, precision=prec)
+            assert rel(host(x), ref) <= LOWPREC_TOL, (d, outer, inner, omega, gamma)
+
+
 @pytest.mark.parametrize("prec", ["fp32", "fp16"])
 def test_lowprec_preconditioner_keeps_convergence(g, prec):
     """Sec. 10: the single-precision preconditioner keeps the GMRES
