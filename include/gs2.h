@@ -124,6 +124,8 @@ typedef struct {
   int rpt_a, rpt_tri;             /* rows per lane group of the tile kernels */
   int colors;                     /* 0 until a multicolour call */
   int sell_a, sell_tri;           /* 1: A / the triangles run on the sliced-ELL layout */
+  double offset_frac_a;           /* share of A's sliced-ELL chunks that store column */
+  double offset_frac_tri;         /* offsets instead of columns (stencil rows); D^{-1}L */
 } gs2_handle_stats;
 
 typedef struct gs2_handle gs2_handle;
@@ -210,11 +212,17 @@ gs2_status gs2_apply_ex(gs2_handle* h, const double* b, double* x,
  * by every GPU that loads the library until the process exits.
  *   n <= 262,144 rows, else GS2_ERR_INVALID_ARG; rowptr int64[n+1],
  *   col int32[nnz], val, b (read) and x (read and overwritten) are device
- *   pointers of the current device; stream as in gs2_setup.  The matrix is
- *   not validated: a zero or missing diagonal gives inf/NaN in x.
+ *   pointers of the current device; stream as in gs2_setup.  Sweep counts
+ *   and damping are bounded as in gs2_apply (outer 0..1000, inner
+ *   0..100000, damping finite and > 0), else GS2_ERR_INVALID_ARG.  The
+ *   matrix is not validated: a zero or missing diagonal gives inf/NaN in x;
+ *   duplicate entries are not detected, and duplicated diagonal entries are
+ *   summed (as an SpMV would use them).
  * Every call uses the same array, so calls that overlap on the GPU race:
- * serialise them.  The first call on a device looks the array up (with that
- * device current); make it before any stream capture.  Results match
+ * serialise them.  Each call outside stream capture looks the array's
+ * device address up on the current device and remembers it; a call on a
+ * capturing stream uses the remembered address, so make one uncaptured call
+ * on the device before capturing (else GS2_ERR_INVALID_ARG).  Results match
  * gs2_apply to rounding (FP64, gamma = 1). */
 gs2_status gs2_apply_noalloc(int64_t n, const int64_t* rowptr, const int32_t* col,
                              const double* val, const double* b, double* x,

@@ -70,7 +70,8 @@ class _Stats(ctypes.Structure):
                 ("levels_upper", ctypes.c_int), ("device_bytes", ctypes.c_int64),
                 ("tpr_a", ctypes.c_int), ("tpr_tri", ctypes.c_int),
                 ("rpt_a", ctypes.c_int), ("rpt_tri", ctypes.c_int), ("colors", ctypes.c_int),
-                ("sell_a", ctypes.c_int), ("sell_tri", ctypes.c_int)]
+                ("sell_a", ctypes.c_int), ("sell_tri", ctypes.c_int),
+                ("offset_frac_a", ctypes.c_double), ("offset_frac_tri", ctypes.c_double)]
 
 
 class _KStat(ctypes.Structure):

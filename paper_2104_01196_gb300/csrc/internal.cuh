@@ -85,11 +85,23 @@ struct DevCsr {
   // longest row's length L_c times 32 slots, column-major: slot k of row i
   // at sell_ptr[c] + 32 k + i % 32; padding slots have value 0 and repeat
   // a column of the row (column 0 for an empty row)
+  //
+  // Offset chunks: a chunk whose rows' entries lie on a few diagonals (a
+  // stencil's rows: the union of the column offsets j - i over its 32 rows is
+  // at most its longest row + 2, and at most 32) stores no columns: slot k of
+  // row i is the entry at column i + sell_off[sell_coff[c] + k] (value 0 where
+  // row i has no such entry; the column is then clamped into [0, sell_ncols)),
+  // the offsets ascending.  sell_coff[c] = -1 marks a chunk with explicit
+  // columns in sell_ci.
   bool sell = false;
   int sell_chunks = 0;
   int sell_slots = 0;          // length of the value and column arrays
   int* sell_ptr = nullptr;     // sell_chunks + 1
   int* sell_ci = nullptr;
+  int* sell_coff = nullptr;    // sell_chunks: first offset, or -1
+  int* sell_off = nullptr;     // the offset lists (chunks with equal lists share one)
+  int sell_offset_chunks = 0;  // chunks without explicit columns
+  int sell_ncols = 0;          // 1 + the largest column (the gathered vector's length)
   double* sell_va = nullptr;
   float* sell_va32 = nullptr;
   __half* sell_va16 = nullptr;

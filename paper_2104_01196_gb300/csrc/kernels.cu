@@ -240,18 +240,39 @@ void launch_spmv_matrix(gs2_handle* h, const DevCsr& M, const double* x, double*
   }
 }
 
-// CSR rows into the sliced-ELL layout, one thread per row: slot k of row i
-// goes to cptr[c] + 32 k + i % 32 (c = i / 32); value slots past the row's
-// end keep their zero, column slots repeat the row's last column (column 0
-// for an empty row, whose slots stay zero)
+__device__ __forceinline__ void add_to(double* p, double v) { *p += v; }
+__device__ __forceinline__ void add_to(float* p, float v) { *p += v; }
+__device__ __forceinline__ void add_to(__half* p, __half v) {
+  *p = __float2half(__half2float(*p) + __half2float(v));
+}
+
+// CSR rows into the sliced-ELL layout, one thread per row (c = i / 32).
+// Explicit chunk: slot k of row i goes to cptr[c] + 32 k + i % 32; value
+// slots past the row's end keep their zero, column slots repeat the row's
+// last column (column 0 for an empty row, whose slots stay zero).  Offset
+// chunk: the entry at column j goes to the slot of offset j - i in the
+// chunk's offset list (added, so duplicate entries of an unvalidated matrix
+// sum as in an SpMV); the other slots keep their zero, and no column is
+// stored.
 template <typename T>
 __global__ void k_to_sell(int n, const int* __restrict__ rp, const int* __restrict__ ci,
-                          const T* __restrict__ va, const int* __restrict__ cptr, int* sci,
+                          const T* __restrict__ va, const int* __restrict__ cptr,
+                          const int* __restrict__ coff, const int* __restrict__ offs, int* sci,
                           T* sva) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int c = i >> 5, lane = i & 31;
     const int L = (cptr[c + 1] - cptr[c]) >> 5;
     const int a = rp[i], len = rp[i + 1] - a;
+    const int ob = coff[c];
+    if (ob >= 0) {
+      for (int k = 0; k < len; ++k) {
+        const int o = ci[a + k] - i;
+        int p = 0;
+        while (p < L && offs[ob + p] != o) ++p;  // present by construction
+        if (p < L) add_to(sva + cptr[c] + (p << 5) + lane, va[a + k]);
+      }
+      continue;
+    }
     for (int k = 0; k < L; ++k) {
       const int slot = cptr[c] + (k << 5) + lane;
       if (k < len) {
@@ -267,7 +288,8 @@ __global__ void k_to_sell(int n, const int* __restrict__ rp, const int* __restri
 template <typename T>
 static void to_sell(gs2_handle* h, const DevCsr& M, const T* va, T* sva, bool with_ci) {
   k_to_sell<T><<<vec_blocks(h, M.n), kVecThreads, 0, h->stream>>>(
-      M.n, M.rp, M.ci, va, M.sell_ptr, with_ci ? M.sell_ci : nullptr, sva);
+      M.n, M.rp, M.ci, va, M.sell_ptr, M.sell_coff, M.sell_off, with_ci ? M.sell_ci : nullptr,
+      sva);
   GS2_LAUNCH_CHECK();
 }
 void launch_to_sell(gs2_handle* h, const DevCsr& M, const double* va, double* sva, bool with_ci) {

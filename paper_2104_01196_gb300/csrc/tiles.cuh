@@ -316,15 +316,21 @@ __device__ __forceinline__ float stream_val<__half>(const __half* p) {
 // the current group's gathers are in flight, one dependent round trip per
 // group of four instead of two.  Its extra registers would cost short-row
 // matrices occupancy, so it is a separate instantiation.
+//
+// Offset chunks (stencil rows) store no columns: the warp reads the chunk's
+// offset list (one broadcast load per slot) and forms column row + o, so a
+// slot moves only its value; the gathers of consecutive rows are contiguous.
 template <typename VT, class Epi, bool LONG>
 __global__ void __launch_bounds__(kRowThreads)
 k_sell(int n, int nchunks, const int* __restrict__ cptr, const int* __restrict__ ci,
-       const VT* __restrict__ va, Epi epi, const int* skip, const int* __restrict__ live) {
+       const VT* __restrict__ va, Epi epi, const int* skip, const int* __restrict__ live,
+       const int* __restrict__ coff, const int* __restrict__ offs, int ncols) {
   using AT = typename ValTraits<VT>::AT;
   pdl_wait();
   if (skip && *skip) return;
   const int lane = threadIdx.x & 31;
   const int nw = (gridDim.x * blockDim.x) >> 5;
+  const int cmax = ncols - 1;
   for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks; c += nw) {
     // a chunk whose rows belong only to finished systems of a pack
     if (live && live[c] == 0) continue;
@@ -332,10 +338,47 @@ k_sell(int n, int nchunks, const int* __restrict__ cptr, const int* __restrict__
     const int base = cptr[c], L = (cptr[c + 1] - base) >> 5;
     typename Epi::Pre pv{};
     if (row < n) pv = epi.pre(row);
-    const int* cc = ci + base + lane;
     const VT* vv = va + base + lane;
     AT s = AT(0);
     int k = 0;
+    const int ob = __ldg(coff + c);
+    if (ob >= 0) {
+      // columns row + o, clamped into [0, ncols) for the zero slots of rows
+      // at a boundary (and the rows past n of the last chunk)
+      const int* oo = offs + ob;
+      for (; k + 4 <= L; k += 4, vv += 128) {
+        const int c0 = min(max(row + __ldg(oo + k), 0), cmax);
+        const int c1 = min(max(row + __ldg(oo + k + 1), 0), cmax);
+        const int c2 = min(max(row + __ldg(oo + k + 2), 0), cmax);
+        const int c3 = min(max(row + __ldg(oo + k + 3), 0), cmax);
+        const AT a0 = stream_val<VT>(vv), a1 = stream_val<VT>(vv + 32);
+        const AT a2 = stream_val<VT>(vv + 64), a3 = stream_val<VT>(vv + 96);
+        const AT x0 = (AT)epi.gather(c0), x1 = (AT)epi.gather(c1);
+        const AT x2 = (AT)epi.gather(c2), x3 = (AT)epi.gather(c3);
+        s = fma(a0, x0, s);
+        s = fma(a1, x1, s);
+        s = fma(a2, x2, s);
+        s = fma(a3, x3, s);
+      }
+      const int rem = L - k;
+      if (rem > 0) {
+        const int c0 = min(max(row + __ldg(oo + k), 0), cmax);
+        const int c1 = rem > 1 ? min(max(row + __ldg(oo + k + 1), 0), cmax) : c0;
+        const int c2 = rem > 2 ? min(max(row + __ldg(oo + k + 2), 0), cmax) : c0;
+        const AT a0 = stream_val<VT>(vv);
+        const AT a1 = rem > 1 ? stream_val<VT>(vv + 32) : AT(0);
+        const AT a2 = rem > 2 ? stream_val<VT>(vv + 64) : AT(0);
+        const AT x0 = (AT)epi.gather(c0);
+        const AT x1 = rem > 1 ? (AT)epi.gather(c1) : AT(0);
+        const AT x2 = rem > 2 ? (AT)epi.gather(c2) : AT(0);
+        s = fma(a0, x0, s);
+        if (rem > 1) s = fma(a1, x1, s);
+        if (rem > 2) s = fma(a2, x2, s);
+      }
+      if (row < n) epi.finish(row, s, pv);
+      continue;
+    }
+    const int* cc = ci + base + lane;
     if (LONG && L >= 8) {
       int c0 = __ldcs(cc), c1 = __ldcs(cc + 32), c2 = __ldcs(cc + 64), c3 = __ldcs(cc + 96);
       AT a0 = stream_val<VT>(vv), a1 = stream_val<VT>(vv + 32);
@@ -448,7 +491,8 @@ inline void launch_sell(gs2_handle* h, const DevCsr& M, const VT* sv, const Epi&
   const int* live =
       (h->row_live && (&M == &h->A || &M == &h->L || &M == &h->U)) ? h->row_live : nullptr;
   launch_pdl(fn, grid, kRowThreads, 0, h->stream, M.n, M.sell_chunks,
-             (const int*)M.sell_ptr, (const int*)M.sell_ci, sv, epi, skip, live);
+             (const int*)M.sell_ptr, (const int*)M.sell_ci, sv, epi, skip, live,
+             (const int*)M.sell_coff, (const int*)M.sell_off, M.sell_ncols);
   GS2_LAUNCH_CHECK();
 }
 
