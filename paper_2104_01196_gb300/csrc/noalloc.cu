@@ -19,12 +19,16 @@
 //    sweep reads from it is written earlier in the same call, so nothing has
 //    to start at zero, but calls that overlap on the GPU (different streams,
 //    or different host threads on one device) race on it: serialise them;
-//  - the first call on a device looks the array's device address up with
-//    cudaGetSymbolAddress while that device is current; make that first call
-//    before any stream capture.
+//  - every call outside stream capture looks the array's device address up
+//    with cudaGetSymbolAddress on the current device (cheap) and remembers it
+//    per device; a call made while its stream is being captured uses the
+//    remembered address, so make one call on that device before capturing
+//    (a capture with none before it is refused).  Looking the address up
+//    again on every uncaptured call keeps it right after a device reset.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 #include <string>
 
@@ -43,23 +47,32 @@ static double* g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
 
 // Device address of the scratch array on the current device.  In host code
 // the array's name is only a host-side stand-in, so the address must come
-// from cudaGetSymbolAddress, once per device, with that device current.
-static double* noalloc_scratch() {
+// from cudaGetSymbolAddress with the device current.  Outside capture it is
+// looked up on every call (and remembered); inside a capture the remembered
+// address of an earlier call on this device is used.
+static double* noalloc_scratch(cudaStream_t stream) {
   int dev = 0;
   GS2_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kNoAllocMaxDevices)
     GS2_THROW(GS2_ERR_INVALID_ARG, "device index out of range for the no-allocation path");
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  GS2_CUDA(cudaStreamIsCapturing(stream, &cap));
   std::lock_guard<std::mutex> g(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
+  if (cap == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     GS2_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
     g_noalloc_ptr[dev] = static_cast<double*>(p);
+  } else if (!g_noalloc_ptr[dev]) {
+    GS2_THROW(GS2_ERR_INVALID_ARG,
+              "the no-allocation path needs one uncaptured call on this device before a "
+              "stream capture");
   }
   return g_noalloc_ptr[dev];
 }
 
-// dinv_i = 1 / a_ii (a missing or zero diagonal gives inf, and the sweep
-// then produces inf / NaN in x)
+// dinv_i = 1 / a_ii, a_ii the sum of the row's stored diagonal entries (as
+// an SpMV would use them; a missing or zero diagonal gives inf, and the
+// sweep then produces inf / NaN in x)
 __global__ void k_na_diag(int64_t n, const int64_t* __restrict__ rp,
                           const int32_t* __restrict__ ci, const double* __restrict__ va,
                           double* dinv) {
@@ -67,7 +80,7 @@ __global__ void k_na_diag(int64_t n, const int64_t* __restrict__ rp,
        i += (int64_t)gridDim.x * blockDim.x) {
     double d = 0.0;
     for (int64_t k = rp[i]; k < rp[i + 1]; ++k)
-      if (ci[k] == i) d = va[k];
+      if (ci[k] == i) d += va[k];
     dinv[i] = 1.0 / d;
   }
 }
@@ -121,8 +134,11 @@ extern "C" gs2_status gs2_apply_noalloc(int64_t n, const int64_t* rowptr, const 
                                         int outer_sweeps, int inner_sweeps, double damping,
                                         int direction, void* stream) {
   try {
-    if (n < 0 || outer_sweeps < 0 || inner_sweeps < 0 || !(damping > 0.0) || direction < 0 ||
-        direction > 2)
+    // the bounds gs2_apply checks: 0..1000 outer and 0..100000 inner sweeps,
+    // a finite positive damping, a known direction
+    if (n < 0 || outer_sweeps < 0 || outer_sweeps > 1000 || inner_sweeps < 0 ||
+        inner_sweeps > 100000 || !(damping > 0.0) || !std::isfinite(damping) ||
+        direction < 0 || direction > 2)
       GS2_THROW(GS2_ERR_INVALID_ARG, "bad size, sweep count, damping or direction");
     if (n > kNoAllocMaxRows)
       GS2_THROW(GS2_ERR_INVALID_ARG,
@@ -130,12 +146,12 @@ extern "C" gs2_status gs2_apply_noalloc(int64_t n, const int64_t* rowptr, const 
                     std::to_string(kNoAllocMaxRows) + " rows");
     if (n == 0 || outer_sweeps == 0) return GS2_OK;
     if (!rowptr || !col || !val || !b || !x) GS2_THROW(GS2_ERR_INVALID_ARG, "NULL pointer");
-    double* base = noalloc_scratch();
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double* base = noalloc_scratch(s);
     double* dinv = base;
     double* rhat = base + kNoAllocMaxRows;
     double* ga = base + 2 * kNoAllocMaxRows;
     double* gb = base + 3 * kNoAllocMaxRows;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     int dev = 0, nsm = 0;
     GS2_CUDA(cudaGetDevice(&dev));
     GS2_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));

@@ -6,7 +6,9 @@ they pass device pointers to their matrix and vectors, and the library's
 working memory is a fixed array in its own device image.  This file checks
 it against the ordinary entry point gs2_apply on two calls in a row (the
 array keeps the previous call's contents, so the second call must not
-depend on them), and that too large a system is refused.
+depend on them), against the FP64 oracle for every inner-sweep count and
+direction and at the documented size limit, and that too large a system
+and out-of-range arguments are refused.
 
 Kept in a file of its own, collected last, so that a run stopping at the
 first failure has already run every other test.
@@ -16,6 +18,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 from paper_2104_01196_gb300 import problems as P
 
 pytestmark = pytest.mark.gpu
@@ -87,7 +90,65 @@ def test_noalloc_matches_gs2_apply_on_two_calls_in_a_row(lib):
     assert _rel(got2, _reference(A2, b2, x2, 1, 3, 1.0, 0)) <= TOL
 
 
+MATS = {"poisson3d_16": P.poisson3d_matrix(16),
+        "random_3000": P.random_csr(3000, 17, mean_offdiag=5.0)}
+
+
+@pytest.mark.parametrize("name", list(MATS))
+@pytest.mark.parametrize("inner", [0, 1, 2, 3])
+@pytest.mark.parametrize("direction", [0, 1, 2])
+def test_noalloc_matches_oracle_and_gs2_apply(lib, name, inner, direction):
+    """Every inner-sweep count (0: the update alone; 1: the last sweep reads
+    r-hat) and direction (backward alone runs only the upper triangle),
+    against the FP64 oracle and the handle-based entry point."""
+    A = MATS[name]
+    n = len(A[0]) - 1
+    b, x0 = P.uniform_pm1(200 + inner, n), P.uniform_pm1(300 + direction, n)
+    got = _noalloc(lib, A, b, x0, 2, inner, 0.85, direction)
+    assert _rel(got, oracle.gs2(A, b, x0, 2, inner, 0.85, 1.0, direction)) <= TOL
+    assert _rel(got, _reference(A, b, x0, 2, inner, 0.85, direction)) <= TOL
+
+
+def test_noalloc_at_the_size_limit_matches_oracle(lib):
+    """n = 262,144 (64^3) exactly: the four slices of the array are full and
+    abut; a symmetric sweep with two inner sweeps uses all of them."""
+    A = P.poisson3d_matrix(64)
+    assert len(A[0]) - 1 == MAX_ROWS
+    b, x0 = P.uniform_pm1(401, MAX_ROWS), P.uniform_pm1(402, MAX_ROWS)
+    got = _noalloc(lib, A, b, x0, 1, 2, 1.0, 2)
+    assert _rel(got, oracle.gs2(A, b, x0, 1, 2, 1.0, 1.0, oracle.SYMMETRIC)) <= TOL
+
+
+def test_noalloc_sums_duplicate_diagonal_entries(lib):
+    """A row whose diagonal is stored as two entries: D is their sum, as the
+    oracle (and an SpMV) takes it."""
+    M = P.csr_to_dense(P.poisson3d_matrix(6))
+    rp, ci, va = P.dense_to_csr(M)
+    rows = [[(int(c), float(v)) for c, v in zip(ci[rp[i]:rp[i + 1]], va[rp[i]:rp[i + 1]])]
+            for i in range(len(rp) - 1)]
+    for i in (0, 17, 100):  # split the diagonal 6 into 2.5 + 3.5
+        rows[i] = [(c, v) for c, v in rows[i] if c != i] + [(i, 2.5), (i, 3.5)]
+    rp2 = np.cumsum([0] + [len(r) for r in rows]).astype(np.int64)
+    ci2 = np.array([c for r in rows for c, _ in r], np.int32)
+    va2 = np.array([v for r in rows for _, v in r])
+    A = (rp2, ci2, va2)
+    n = len(rp2) - 1
+    b, x0 = P.uniform_pm1(501, n), P.uniform_pm1(502, n)
+    got = _noalloc(lib, A, b, x0, 1, 2, 1.0, 2)
+    assert _rel(got, oracle.gs2(A, b, x0, 1, 2, 1.0, 1.0, oracle.SYMMETRIC)) <= TOL
+
+
 def test_noalloc_refuses_systems_above_its_limit(lib):
     st = lib.gs2_apply_noalloc(MAX_ROWS + 1, 1, 1, 1, 1, 1, 1, 1, 1.0, 0, None)
     assert st == 1
     assert b"no-allocation limit" in lib.gs2_last_error()
+
+
+@pytest.mark.parametrize("outer,inner,damping,direction", [
+    (1, 1, float("inf"), 0), (1, 1, float("nan"), 0), (1, 1, 0.0, 0),
+    (1001, 1, 1.0, 0), (1, 100001, 1.0, 0), (-1, 1, 1.0, 0), (1, 1, 1.0, 3)])
+def test_noalloc_refuses_out_of_range_arguments(lib, outer, inner, damping, direction):
+    """The bounds gs2_apply enforces; nothing is launched (the pointers are
+    never touched when the arguments are refused)."""
+    st = lib.gs2_apply_noalloc(100, 1, 1, 1, 1, 1, outer, inner, damping, direction, None)
+    assert st == 1
