@@ -1,10 +1,17 @@
 """Benchmark: GS2-preconditioned restarted GMRES on one GB300.
 
-One step = one full solve A x = b from x0 = 0 of the 3D 7-point Laplacian
-on a 128^3 grid (n = 2,097,152, nnz = 14,581,760, FP64 CSR, b = A x_true,
-x_true ~ U[-1,1] from the seed), GMRES(30) right preconditioned by one
-symmetric GS2 sweep with one inner JR sweep (SGS2(1,1)), relative residual
-1e-8.  Inputs are synthetic (the paper's Galeri Laplacian, re-synthesised).
+One step = one full solve A x = b from x0 = 0 of the 3D nonsymmetric
+convection-diffusion system on a 192^3 grid (first-order upwind, rotating
+wind, lognormal cell Peclet numbers, mass term 1; n = 7,077,888,
+nnz = 49,324,032, FP64 CSR, b = A x_true, x_true ~ U[-1,1] from the seed),
+GMRES(30) right preconditioned by one symmetric GS2 sweep with one inner JR
+sweep (SGS2(1,1)), relative residual 1e-8.  Inputs are synthetic (the
+paper's model problems, re-synthesised).  The timed region runs with
+profiling off; the per-kernel table and the dominant kernel's roofline come
+from a second, identical pass.  Extras on the same line: the same workload
+with FP32 and FP16 inner sweeps, the 128^3 Laplacian with the same
+measurement, the paper's baselines, packs, serving and the elasticity
+workload.
 
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
 on the host cores on a bounded sample of the same workload instead.
@@ -28,8 +35,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "GS2 sweep HBM GB/s (% peak); GMRES solves/s, p50/p99 latency vs plain FP64"
-WORKLOAD = ("3D 7-point Laplacian 128^3 (n=2,097,152, nnz=14,581,760), CSR FP64, "
-            "b = A x_true, x_true ~ U[-1,1]; GMRES(30) + SGS2(1,1), rel. residual 1e-8")
+WORKLOAD = ("3D upwind convection-diffusion 192^3 (n=7,077,888, nnz=49,324,032), rotating "
+            "wind, cell Peclet lognormal in [0.1, 10], CSR FP64, b = A x_true, "
+            "x_true ~ U[-1,1]; GMRES(30) + SGS2(1,1) FP64, rel. residual 1e-8")
 COUNTS_FILE = os.path.join(ROOT, "tests", "golden", "oracle_counts.txt")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.txt")
 
@@ -40,7 +48,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--grid", type=int, default=128, help="N of the N^3 Laplacian")
+    ap.add_argument("--grid", type=int, default=192,
+                    help="N of the N^3 convection-diffusion grid")
+    ap.add_argument("--no-cpu-table", action="store_true",
+                    help="skip the oracle's per-configuration sweep and solve table")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the baseline/precision comparison solves")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
@@ -54,8 +65,8 @@ def parse():
     ap.add_argument("--no-profile", action="store_true",
                     help="do not time kernels with events inside the timed region")
     ap.add_argument("--only-extras", default="",
-                    help="comma list: run only these extras (comparisons, hybrid, "
-                         "small_system, packs, workloads, serving)")
+                    help="comma list: run only these extras (precision, laplacian128, "
+                         "comparisons, hybrid, small_system, packs, workloads, serving)")
     return ap.parse_args()
 
 
@@ -158,12 +169,13 @@ class ClockSampler:
 # reference arm: the FP64 CPU oracle
 # ---------------------------------------------------------------------------
 
-def oracle_sample(pr, target_s=12.0):
+def oracle_sample(pr, key, target_s=12.0):
     """Time the oracle's GMRES(30)+SGS2(1,1) on a bounded sample of about
-    `target_s` seconds: a 3-step probe sets how many Arnoldi steps fit; if the
+    `target_s` seconds: a 2-step probe sets how many Arnoldi steps fit; if the
     whole solve fits, it is run to convergence and timed as it is, else that
     many steps are timed and scaled to one full solve by the oracle's own
-    full-solve iteration count.  Returns (solves/s, description)."""
+    full-solve iteration count (stored under `key`).  Returns (solves/s,
+    description)."""
     import oracle
     oracle.build()
 
@@ -174,10 +186,10 @@ def oracle_sample(pr, target_s=12.0):
                                pc_direction=oracle.SYMMETRIC)
         return time.perf_counter() - t0, info
 
-    dt, info = run(3)
+    dt, info = run(2)
     per_iter = dt / max(info.iters, 1)
-    full = stored_count(f"poisson3d_{int(round(pr.n ** (1 / 3)))}_gmres30_sgs2_1_1")
-    steps = max(3, int(target_s / per_iter))
+    full = stored_count(key)
+    steps = max(2, int(target_s / per_iter))
     if full and steps >= full:
         dt, info = run(5000)
         return 1.0 / dt, (f"the whole GMRES(30)+SGS2(1,1) solve ({info.iters} Arnoldi steps, "
@@ -248,10 +260,11 @@ def run_reference(args):
     if rank != 0:
         return
     from paper_2104_01196_gb300 import problems as P
-    pr = P.poisson3d(args.grid)
+    pr = P.convdiff3d(args.grid)
+    key = f"convdiff3d_{args.grid}_gmres30_sgs2_1_1"
     values, sample = [], ""
     for s in range(args.warmup + args.steps):
-        v, sample = oracle_sample(pr)
+        v, sample = oracle_sample(pr, key, target_s=5.0)
         if s >= args.warmup and v is not None:
             values.append(v)
     value = float(np.mean(values)) if values else None
@@ -351,6 +364,59 @@ def whole_job_rate(world, steps, slowest_ms):
     return world * steps / (slowest_ms / 1000.0)
 
 
+def timed_solves(torch, stream, solve, steps):
+    """Device time of `steps` back-to-back solves on `stream` (CUDA events on
+    that stream around the whole run and around every solve); returns
+    (total ms, per-solve ms, infos)."""
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    infos = []
+    with torch.cuda.stream(stream):
+        t0.record(stream)
+        for k in range(steps):
+            ev[k][0].record(stream)
+            infos.append(solve())
+            ev[k][1].record(stream)
+        t1.record(stream)
+    torch.cuda.synchronize()
+    return t0.elapsed_time(t1), [a.elapsed_time(b) for a, b in ev], infos
+
+
+def profiled(h, torch, stream, solve, steps, hbm, n, nnz, peak_kind="measured"):
+    """The kernel table of one solve (an event pair around every launch),
+    then a second pass of `steps` identical solves with only the dominant
+    kernel bracketed: its roofline.  Kept out of the timed region."""
+    with torch.cuda.stream(stream):
+        h.profile_filter(None)
+        h.profile(True)
+        h.profile_reset()
+        solve()
+    stream.synchronize()
+    table = kernel_table(h.profile_read(), n, hbm, nnz)
+    h.profile(False)
+    top = max(table, key=lambda k: table[k]["ms"]) if table else None
+    roof = None
+    if top:
+        h.profile_filter(top)
+        h.profile(True)
+        with torch.cuda.stream(stream):
+            solve()  # captures the Arnoldi-step graph with the event nodes
+        stream.synchronize()
+        h.profile_reset()
+        with torch.cuda.stream(stream):
+            for _ in range(steps):
+                solve()
+        stream.synchronize()
+        st = h.profile_read()
+        h.profile(False)
+        h.profile_filter(None)
+        if top in st and st[top]["launches"]:
+            roof = roofline(top, st[top], n, hbm, peak_kind, None, nnz)
+    return table, roof
+
+
 def run_ours(args):
     import torch
 
@@ -372,10 +438,10 @@ def run_ours(args):
         dist.barrier()
     gs2.load()
 
-    pr = P.poisson3d(args.grid)
-    n = pr.n
+    pr = P.convdiff3d(args.grid)
+    n, nnz = pr.n, pr.nnz
     stream = torch.cuda.Stream()
-    h = gs2.gs2_setup(pr.A, stream=stream.cuda_stream)
+    h = gs2.gs2_setup(pr.A, precisions=("fp32", "fp16"), stream=stream.cuda_stream)
     if not args.no_autotune:
         h.autotune()  # tile shapes of A and the triangles (setup time, untimed)
     shapes = {k: v for k, v in h.stats().items() if k.startswith(("tpr", "rpt", "sell"))}
@@ -385,138 +451,144 @@ def run_ours(args):
         x = torch.zeros(n, dtype=torch.float64, device="cuda")
     stream.synchronize()
 
-    def solve():
-        x.zero_()
-        return gs2.gmres_solve(h, b, x, 30, 1e-8, 5000, pc)
+    def solver(prm):
+        def solve():
+            x.zero_()
+            return gs2.gmres_solve(h, b, x, 30, 1e-8, 5000, prm)
+        return solve
+    solve = solver(pc)
 
-    # warm-up; the last warm-up solve is timed kernel by kernel (event pair
-    # around every launch) for the table of shares
+    # warm-up (graph capture, workspaces); no profiling anywhere before or in
+    # the timed region
     with torch.cuda.stream(stream):
-        for w in range(args.warmup):
-            if w == args.warmup - 1 and not args.no_profile:
-                h.profile_filter(None)
-                h.profile(True)
-                h.profile_reset()
+        for _ in range(args.warmup):
             info = solve()
     stream.synchronize()
     if info.status != 0:
         raise RuntimeError(f"warm-up solve failed: {info}")
     hbm, peak_kind = peaks()
-    kernels = {}
-    top = None
-    if not args.no_profile:
-        warm = h.profile_read()
-        h.profile(False)
-        kernels = kernel_table(warm, n, hbm, len(pr.A[1]))
-        top = max(kernels, key=lambda k: kernels[k]["ms"]) if kernels else None
 
-    if top:
-        # inside the timed region only the dominant kernel is bracketed; one
-        # more untimed solve captures the Arnoldi-step graph with those event
-        # nodes, so no capture happens inside the timed region
-        h.profile_filter(top)
-        h.profile(True)
-        with torch.cuda.stream(stream):
-            solve()
-        stream.synchronize()
-        h.profile_reset()
     sampler = ClockSampler(local) if rank == 0 else None
     if sampler:
         sampler.start()
         time.sleep(0.3)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    iters = []
     launches0 = gs2.launch_count()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
-    with torch.cuda.stream(stream):
-        t_start.record(stream)
-        for k in range(args.steps):
-            ev[k][0].record(stream)
-            info = solve()
-            ev[k][1].record(stream)
-            iters.append(info.iters)
-            if info.status != 0:
-                raise RuntimeError(f"timed solve failed: {info}")
-        t_end.record(stream)
-    torch.cuda.synchronize()
+    total_ms, step_ms, infos = timed_solves(torch, stream, solve, args.steps)
     if dist:
         dist.barrier()
     launches = gs2.launch_count() - launches0
-    total_ms = t_start.elapsed_time(t_end)
-    step_ms = [a.elapsed_time(bb) for a, bb in ev]
-    timed = h.profile_read() if top else {}
-    h.profile(False)
-    h.profile_filter(None)
     clocks = sampler.stop() if sampler else None
+    for inf in infos:
+        if inf.status != 0:
+            raise RuntimeError(f"timed solve failed: {inf}")
     if dist:
         total_ms = slowest_rank(dist, total_ms, "cuda")
     ms_per_step = total_ms / args.steps
     value = whole_job_rate(world, args.steps, total_ms)
-
-    roof = None
-    if top and top in timed and timed[top]["launches"]:
-        roof = roofline(top, timed[top], n, hbm, peak_kind, args.grid, len(pr.A[1]))
-    sweep = {k: kernels[k] for k in ("resid", "inner64") if k in kernels}
+    iters = [inf.iters for inf in infos]
+    xt = torch.from_numpy(pr.x_true).cuda()
+    err = float(torch.linalg.norm(x - xt) / torch.linalg.norm(xt))
+    x64 = x.clone()
 
     out = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": args.grid, "n": n, "nnz": pr.nnz,
+        "config": {"workload": WORKLOAD, "grid": args.grid, "n": n, "nnz": nnz,
                    "restart": 30, "tol": 1e-8, "precond": "SGS2(1,1) FP64",
                    "tile_shapes": shapes,
                    "parallelism": f"replicas x{world}",
-                   "l2": "no flush: per-step working set (A 175 MB, D^-1L/D^-1U 2x75 MB, "
-                         "Krylov basis 520 MB) exceeds the 129 MB L2"},
+                   "l2": "no flush: per-step working set (A 592 MB, D^-1L/D^-1U 2x253 MB, "
+                         "Krylov basis 1.75 GB) exceeds the 129 MB L2"},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                        "p99": float(np.percentile(step_ms, 99)),
                        "per_step": [round(t, 3) for t in step_ms]},
         "iters": iters,
+        "oracle_iters": stored_count(f"convdiff3d_{args.grid}_gmres30_sgs2_1_1"),
+        "rel_err_vs_x_true": err,
+        "true_relres": infos[-1].true_relres,
         "gpu_launches": int(launches),
-        "roofline": roof,
-        "sweep_kernels": sweep,
-        "kernels": kernels,
         "clocks": clocks,
     }
 
     # ---- e2e: the public C-ABI call with host (pinned) buffers ------------
     # the library copies b and x0 to the device, solves and copies x back
-    # inside every timed call
+    # inside every timed call; all `steps` solves are timed
     out["e2e"] = None
     if not args.no_e2e:
         bh = torch.from_numpy(pr.b.copy()).pin_memory().numpy()
         xh = torch.zeros(n, dtype=torch.float64).pin_memory().numpy()
-        xh[:] = 0.0
         gs2.gmres_solve(h, bh, xh, 30, 1e-8, 5000, pc)
         e2e_t = []
-        for _ in range(max(1, min(args.steps, 3))):
+        for _ in range(args.steps):
             xh[:] = 0.0
             t0 = time.perf_counter()
             inf = gs2.gmres_solve(h, bh, xh, 30, 1e-8, 5000, pc)
             e2e_t.append(time.perf_counter() - t0)
             assert inf.status == 0
+        tot = float(np.sum(e2e_t))
         if dist:
-            e2e_t = [slowest_rank(dist, float(np.mean(e2e_t)), "cuda")]
-        out["e2e"] = {"value": world / float(np.mean(e2e_t)), "unit": "solves/s",
+            tot = slowest_rank(dist, tot, "cuda")
+        out["e2e"] = {"value": world * args.steps / tot, "unit": "solves/s",
                       "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 8 * n,
+                      "steps": args.steps,
                       "note": "gmres_solve with pinned host b and x: H2D of b and x0, "
-                              "solve, D2H of x inside each timed call"}
+                              "solve, D2H of x inside each timed call (wall clock)"}
+
+    # ---- roofline: a second, identical pass with the dominant kernel ------
+    # bracketed by events (and the per-kernel table of one solve before it)
+    if not args.no_profile:
+        kernels, roof = profiled(h, torch, stream, solve, args.steps, hbm, n, nnz, peak_kind)
+        out["roofline"] = roof
+        out["kernels"] = kernels
+        out["sweep_kernels"] = {k: kernels[k] for k in ("resid", "inner64", "spmv")
+                                if k in kernels}
 
     only = set(filter(None, args.only_extras.split(",")))
 
     def want(name, off=False):
         return rank == 0 and world == 1 and not off and (name in only if only else True)
 
+    # ---- the same workload with lower-precision inner sweeps --------------
+    if want("precision", args.no_extras):
+        res = {}
+        for prec in ("fp32", "fp16"):
+            pp = gs2.params("gs2", 1, 1, direction="symmetric", precision=prec)
+            sp = solver(pp)
+            with torch.cuda.stream(stream):
+                sp()
+            stream.synchronize()
+            tot, per, inf = timed_solves(torch, stream, sp, args.steps)
+            row = {"solves_per_s": args.steps / (tot / 1000.0), "ms_per_solve": tot / args.steps,
+                   "iters": inf[-1].iters, "status": inf[-1].status,
+                   "oracle_iters": stored_count(
+                       f"convdiff3d_{args.grid}_gmres30_sgs2_1_1_{prec}"),
+                   "true_relres": inf[-1].true_relres,
+                   "rel_err_vs_x_true": float(torch.linalg.norm(x - xt) / torch.linalg.norm(xt)),
+                   "rel_err_vs_fp64_solution": float(torch.linalg.norm(x - x64) /
+                                                     torch.linalg.norm(x64)),
+                   "speedup_vs_fp64": (args.steps / (tot / 1000.0)) / value}
+            if not args.no_profile:
+                tab, _ = profiled(h, torch, stream, sp, 0, hbm, n, nnz)
+                row["kernels"] = {k: v for k, v in tab.items()
+                                  if k.startswith(("inner", "resid", "spmv"))}
+            res[prec] = row
+        out["precision"] = res
+    h.close()
+
+    if want("laplacian128", args.no_extras):
+        out["laplacian128"] = laplacian_line(gs2, torch, P, args, hbm)
     if want("comparisons", args.no_extras):
-        out["comparisons"] = comparisons(gs2, torch, pr, stream, b)
-    if want("hybrid", args.no_extras):
-        out["hybrid"] = hybrid(gs2, torch, pr, stream, b)
+        lap = P.poisson3d(128)
+        out["comparisons"] = comparisons(gs2, torch, lap, stream,
+                                         torch.from_numpy(lap.b).cuda())
+        if want("hybrid", args.no_extras):
+            out["hybrid"] = hybrid(gs2, torch, lap, stream, torch.from_numpy(lap.b).cuda())
+        del lap
     if want("serving", args.no_serve):
         out["serving"] = serving(gs2, torch, args.serve_requests)
     if want("small_system", args.no_extras):
@@ -526,15 +598,57 @@ def run_ours(args):
     if want("workloads", args.no_extras or args.no_workloads):
         out["workloads"] = full_workloads(gs2, torch)
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, sample = oracle_sample(pr)
+        v, sample = oracle_sample(pr, f"convdiff3d_{args.grid}_gmres30_sgs2_1_1")
+        hh = gs2.gs2_setup(pr.A, stream=stream.cuda_stream)
         out["cpu_baseline"] = {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
                                "sample": sample,
-                               "sweep_1_vs_all_cores": sweep_cpu_vs_gpu(gs2, torch, pr, h,
+                               "sweep_1_vs_all_cores": sweep_cpu_vs_gpu(gs2, torch, pr, hh,
                                                                         stream)}
+        hh.close()
+        if not args.no_cpu_table:
+            out["cpu_baseline"]["table"] = cpu_table(gs2, torch, P)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def laplacian_line(gs2, torch, P, args, hbm):
+    """The 3D 7-point Laplacian 128^3 with GMRES(30) + SGS2(1,1) FP64, the
+    same measurement as the headline: device-timed solves with profiling
+    off, then the kernel table and the dominant kernel's roofline from a
+    second pass."""
+    pr = P.poisson3d(128)
+    stream = torch.cuda.Stream()
+    h = gs2.gs2_setup(pr.A, stream=stream.cuda_stream)
+    if not args.no_autotune:
+        h.autotune()
+    pc = gs2.params("gs2", 1, 1, direction="symmetric")
+    with torch.cuda.stream(stream):
+        b = torch.from_numpy(pr.b).cuda()
+        x = torch.zeros(pr.n, dtype=torch.float64, device="cuda")
+
+    def solve():
+        x.zero_()
+        return gs2.gmres_solve(h, b, x, 30, 1e-8, 5000, pc)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            solve()
+    stream.synchronize()
+    tot, per, infos = timed_solves(torch, stream, solve, args.steps)
+    res = {"workload": "3D 7-point Laplacian 128^3 (n=2,097,152, nnz=14,581,760), "
+                       "GMRES(30) + SGS2(1,1) FP64, 1e-8",
+           "solves_per_s": args.steps / (tot / 1000.0), "ms_per_solve": tot / args.steps,
+           "iters": infos[-1].iters,
+           "oracle_iters": stored_count("poisson3d_128_gmres30_sgs2_1_1"),
+           "true_relres": infos[-1].true_relres}
+    if not args.no_profile:
+        tab, roof = profiled(h, torch, stream, solve, args.steps, hbm, pr.n, pr.nnz,
+                             peaks()[1])
+        res["kernels"] = tab
+        res["roofline"] = roof
+    h.close()
+    return res
 
 
 def small_system(gs2, torch, reps=20):
@@ -654,15 +768,14 @@ def packs(gs2, torch, count=128):
 
 
 def full_workloads(gs2, torch):
-    """The other full-size configurations, device-timed once each (after an
-    untimed restart cycle): Q1 elasticity on 64^3 nodes with SGS2(1, n_j) at
-    the omega its few inner sweeps need (n_j = 2: 0.8, n_j = 3: 0.9; with
+    """The Q1 elasticity configuration at full size (64^3 nodes), device-timed
+    once per setting (after an untimed restart cycle): SGS2(1, n_j) at the
+    omega its few inner sweeps need (n_j = 2: 0.8, n_j = 3: 0.9; with
     omega = 1 it stagnates, as the paper's elasticity tables show), FP64 and
-    FP32 triangle values (GMRES FP64), and stationary
-    JR at omega = 1, which diverges on it; 192^3 upwind convection-diffusion
-    with GS2(1,1) inner sweeps in FP64, FP32 and FP16 with a row scale.  Each
-    result carries its iteration count, its true relative residual and, where
-    the right-hand side was generated from one, its error against x_true."""
+    FP32 triangle values (GMRES FP64), each beside the oracle's count for the
+    same setting and precision; and stationary JR at omega = 1, which
+    diverges on it.  (The 192^3 convection-diffusion configuration is the
+    headline, with its precision variants.)"""
     from paper_2104_01196_gb300 import problems as P
     out = {}
 
@@ -678,50 +791,157 @@ def full_workloads(gs2, torch):
         e1.synchronize()
         return info, e0.elapsed_time(e1)
 
-    for name, pr, variants in (
-            ("elasticity3d_64", P.elasticity3d(64),
-             [(f"sgs2_1_{nj}_w{om}_{prec}", gs2.params("gs2", 1, nj, omega=om,
-                                                        direction="symmetric", precision=prec))
-              for nj, om in ((2, 0.8), (3, 0.9)) for prec in ("fp64", "fp32")]),
-            ("convdiff3d_192", P.convdiff3d(192),
-             [(f"sgs2_1_1_{prec}", gs2.params("gs2", 1, 1, direction="symmetric",
-                                               precision=prec))
-              for prec in ("fp64", "fp32", "fp16")])):
-        h = gs2.gs2_setup(pr.A, precisions=("fp32", "fp16"))
-        b = torch.from_numpy(pr.b).cuda()
-        x = torch.zeros(pr.n, dtype=torch.float64, device="cuda")
-        # (the elasticity right-hand side is a body load, with no x_true)
-        xt = torch.from_numpy(pr.x_true).cuda() if pr.x_true is not None else None
-        res = {"n": pr.n, "nnz": int(len(pr.A[1]))}
-        x64 = {}
-        for vname, pc in variants:
+    pr = P.elasticity3d(64)
+    h = gs2.gs2_setup(pr.A, precisions=("fp32",))
+    b = torch.from_numpy(pr.b).cuda()
+    x = torch.zeros(pr.n, dtype=torch.float64, device="cuda")
+    res = {"n": pr.n, "nnz": int(len(pr.A[1]))}
+    x64 = {}
+    for nj, om in ((2, 0.8), (3, 0.9)):
+        for prec in ("fp64", "fp32"):
+            stem = f"sgs2_1_{nj}_w{om}"
+            vname = f"{stem}_{prec}"
+            pc = gs2.params("gs2", 1, nj, omega=om, direction="symmetric", precision=prec)
             info, ms = timed(h, b, x, pc, 5000)
-            err = (float(torch.linalg.norm(x - xt) / torch.linalg.norm(xt))
-                   if xt is not None else None)
-            res[vname] = {"status": info.status, "iters": info.iters, "ms": round(ms, 2),
-                          "true_relres": info.true_relres, "rel_err_vs_x_true": err}
-            # lower-precision sweeps: error against the FP64-sweep solution of
-            # the same system (itself within the parity bound of the oracle)
-            stem = vname.rsplit("_", 1)[0]
-            if vname.endswith("_fp64"):
+            key = f"elasticity3d_64_gmres30_{stem}" + ("" if prec == "fp64" else f"_{prec}")
+            res[vname] = {"status": info.status, "iters": info.iters,
+                          "oracle_iters": stored_count(key), "ms": round(ms, 2),
+                          "true_relres": info.true_relres}
+            # FP32 values: error against the FP64-value solution of the same
+            # system (itself within the parity bound of the oracle)
+            if prec == "fp64":
                 x64[stem] = x.clone()
-            elif stem in x64:
+            else:
                 res[vname]["rel_err_vs_fp64_solution"] = float(
                     torch.linalg.norm(x - x64[stem]) / torch.linalg.norm(x64[stem]))
-        if name.startswith("elasticity"):
-            # stationary JR, omega = 1 (the paper's elasticity tables): the
-            # residual grows
-            x.zero_()
-            r0 = float(torch.linalg.norm(b))
-            gs2.jr_apply(h, b, x, 50, 1.0)
-            y = torch.zeros_like(x)
-            gs2.gs2_spmv(h, x, y)
-            growth = float(torch.linalg.norm(b - y)) / r0
-            res["jr_stationary_w1.0_50_sweeps_residual_growth"] = \
-                growth if math.isfinite(growth) else None
-        h.close()
-        out[name] = res
+    # stationary JR, omega = 1 (the paper's elasticity tables): the residual grows
+    x.zero_()
+    r0 = float(torch.linalg.norm(b))
+    gs2.jr_apply(h, b, x, 50, 1.0)
+    y = torch.zeros_like(x)
+    gs2.gs2_spmv(h, x, y)
+    growth = float(torch.linalg.norm(b - y)) / r0
+    res["jr_stationary_w1.0_50_sweeps_residual_growth"] = \
+        growth if math.isfinite(growth) else None
+    h.close()
+    out["elasticity3d_64"] = res
     return out
+
+
+def cpu_table(gs2, torch, P, reps=10, solve_budget_s=30.0):
+    """The oracle on the host cores for every single-GPU configuration (2D
+    Poisson 64^2, 3D Laplacian 128^3, Q1 elasticity 64^3, convection-diffusion
+    192^3): each sweep type as the median of `reps` runs on one core and,
+    where its loop is row-parallel, on every core (the -fopenmp build of the
+    same source, bitwise the same result), with the GPU's mean over `reps`
+    beside it; and one full GMRES(30) solve on one core with the
+    configuration's preconditioner -- run to convergence when it fits in
+    `solve_budget_s`, else that many Arnoldi steps timed and scaled by the
+    oracle's stored full-solve count (labelled "extrapolated")."""
+    import platform
+
+    import oracle
+    oracle.build()
+    oracle.build(openmp=True)
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    res = {"nproc": os.cpu_count(), "cpu": model, "threads_all_cores": oracle.threads(True),
+           "configs": {}}
+    confs = [
+        ("poisson2d_64", lambda: P.poisson2d(64), 1, 1.0, oracle.FORWARD,
+         "poisson2d_64_gmres30_gs2_1_1"),
+        ("poisson3d_128", lambda: P.poisson3d(128), 1, 1.0, oracle.SYMMETRIC,
+         "poisson3d_128_gmres30_sgs2_1_1"),
+        ("elasticity3d_64", lambda: P.elasticity3d(64), 2, 0.8, oracle.SYMMETRIC,
+         "elasticity3d_64_gmres30_sgs2_1_2_w0.8"),
+        ("convdiff3d_192", lambda: P.convdiff3d(192), 1, 1.0, oracle.SYMMETRIC,
+         "convdiff3d_192_gmres30_sgs2_1_1"),
+    ]
+
+    def med(fn):
+        fn()
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            fn()
+            ts.append(time.perf_counter() - t0)
+        return round(1000 * float(np.median(ts)), 3)
+
+    for name, mk, nj, om, dirn, key in confs:
+        pr = mk()
+        A, bb = pr.A, pr.b
+        x0 = P.uniform_pm1(99, pr.n)
+        row = {"n": pr.n, "nnz": int(len(A[1])), "sweeps_ms": {}}
+        sweeps = {
+            "spmv": (lambda o: oracle.spmv(A, x0, openmp=o), True),
+            "jr_1": (lambda o: oracle.jr(A, bb, x0, 1, 1.0, openmp=o), True),
+            "resid_scale_update_gs2_fwd_1_0": (
+                lambda o: oracle.gs2(A, bb, x0, 1, 0, 1.0, 1.0, oracle.FORWARD, openmp=o), True),
+            "gs2_fwd_1_1": (
+                lambda o: oracle.gs2(A, bb, x0, 1, 1, 1.0, 1.0, oracle.FORWARD, openmp=o), True),
+            "sgs2_1_1": (
+                lambda o: oracle.gs2(A, bb, x0, 1, 1, 1.0, 1.0, oracle.SYMMETRIC, openmp=o), True),
+            "sgs_exact": (lambda o: oracle.gs(A, bb, x0, 1, 1.0, oracle.SYMMETRIC), False),
+        }
+        h = gs2.gs2_setup(A)
+        bd = torch.from_numpy(bb).cuda()
+        x0d = torch.from_numpy(x0).cuda()
+        xd = torch.zeros_like(x0d)
+        gpu = {
+            "spmv": lambda: gs2.gs2_spmv(h, x0d, xd),
+            "jr_1": lambda: (xd.copy_(x0d), gs2.jr_apply(h, bd, xd, 1, 1.0)),
+            "resid_scale_update_gs2_fwd_1_0": lambda: (xd.copy_(x0d),
+                                                       gs2.gs2_apply(h, bd, xd, 1, 0, 1.0, 0)),
+            "gs2_fwd_1_1": lambda: (xd.copy_(x0d), gs2.gs2_apply(h, bd, xd, 1, 1, 1.0, 0)),
+            "sgs2_1_1": lambda: (xd.copy_(x0d), gs2.gs2_apply(h, bd, xd, 1, 1, 1.0, 2)),
+            "sgs_exact": lambda: (xd.copy_(x0d), gs2.gs_apply(h, bd, xd, 1, 1.0, 2)),
+        }
+        for sname, (fn, par) in sweeps.items():
+            r = {"oracle_1_core_ms": med(lambda: fn(False))}
+            if par:
+                r["oracle_all_cores_ms"] = med(lambda: fn(True))
+            g = gpu[sname]
+            g()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                g()
+            e1.record()
+            e1.synchronize()
+            r["gpu_ms"] = round(e0.elapsed_time(e1) / reps, 4)
+            row["sweeps_ms"][sname] = r
+        h.close()
+        # one full GMRES solve on one core (or a scaled sample of it)
+        kw = dict(pc_kind=oracle.PC_GS2, pc_inner=nj, pc_omega=om, pc_direction=dirn)
+        t0 = time.perf_counter()
+        _, info = oracle.gmres(A, bb, restart=30, tol=1e-8, max_iters=2, **kw)
+        per = (time.perf_counter() - t0) / max(info.iters, 1)
+        full = stored_count(key)
+        if full and per * full <= solve_budget_s:
+            t0 = time.perf_counter()
+            _, info = oracle.gmres(A, bb, restart=30, tol=1e-8, max_iters=5000, **kw)
+            dt = time.perf_counter() - t0
+            row["gmres_1_core"] = {"s": round(dt, 2), "iters": info.iters, "extrapolated": False}
+        elif full:
+            steps = max(2, int(solve_budget_s / per))
+            t0 = time.perf_counter()
+            _, info = oracle.gmres(A, bb, restart=30, tol=1e-8, max_iters=steps, **kw)
+            dt = time.perf_counter() - t0
+            row["gmres_1_core"] = {"s": round(dt / info.iters * full, 2), "iters": full,
+                                   "extrapolated": True,
+                                   "sample": f"{info.iters} Arnoldi steps in {dt:.1f} s"}
+        res["configs"][name] = row
+        del pr, A, bb
+    return res
 
 
 def serving(gs2, torch, count):
@@ -824,6 +1044,23 @@ def hybrid(gs2, torch, pr, stream, b):
     return res
 
 
+# the oracle's stored full-solve counts of the comparison solves
+ORACLE_KEYS = {
+    "sgs2_1_2": "poisson3d_128_gmres30_sgs2_1_2",
+    "sgs2_1_3": "poisson3d_128_gmres30_sgs2_1_3",
+    "compact_sgs2_1_2": "poisson3d_128_gmres30_compact_sgs2_1_2",
+    "sgs2_1_1_fp32": "poisson3d_128_gmres30_sgs2_1_1_fp32",
+    "sgs2_1_1_fp16": "poisson3d_128_gmres30_sgs2_1_1_fp16",
+    "gs_levels_sym": "poisson3d_128_gmres30_sgs_exact",
+    "mtsgs": "poisson3d_128_gmres30_mtsgs",
+    "amg_sgs2_1_1": "poisson3d_128_gmres30_amg_sgs2_1_1",
+    "jr3_w1.0": "poisson3d_128_gmres30_jr3_w1.0",
+    "jr3_w0.8": "poisson3d_128_gmres30_jr3_w0.8",
+    "cg_sgs2_1_1": "poisson3d_128_cg_sgs2_1_1",
+    "cg_amg_sgs2_1_1": "poisson3d_128_cg_amg_sgs2_1_1",
+}
+
+
 def comparisons(gs2, torch, pr, stream, b):
     """One solve each of the paper's baselines and the precision variants on
     the same workload (untimed by the headline; device-timed here), and CG
@@ -874,8 +1111,9 @@ def comparisons(gs2, torch, pr, stream, b):
             ms = e0.elapsed_time(e1)
             err = float(torch.linalg.norm(x - torch.from_numpy(pr.x_true).cuda()) /
                         math.sqrt(pr.n))
-            res[name] = {"status": info.status, "iters": info.iters, "ms": round(ms, 2),
-                         "solves_per_s": round(1000.0 / ms, 3),
+            res[name] = {"status": info.status, "iters": info.iters,
+                         "oracle_iters": stored_count(ORACLE_KEYS.get(name, "")),
+                         "ms": round(ms, 2), "solves_per_s": round(1000.0 / ms, 3),
                          "true_relres": info.true_relres, "rms_err_vs_x_true": err}
             if name in ("sgs2_1_1_fp32", "sgs2_1_1_fp16") and x_ref is not None:
                 res[name]["rel_err_vs_fp64_solution"] = float(
