@@ -91,20 +91,24 @@ def stored_count(key):
     return None
 
 
-def stored_traffic(kernel, algorithmic_bytes_per_launch):
+def stored_traffic(kernel, algorithmic_bytes_per_launch, workload=None):
     """Per-launch DRAM bytes of a kernel: the ratio of DRAM bytes to
     algorithmic bytes captured by ncu on a smaller case of the same kernel
-    (profiles/traffic.txt), scaled to this launch's algorithmic bytes (the
-    kernels stream their inputs once, so traffic grows in proportion)."""
+    (profiles/traffic.txt; a capture of the same workload family first),
+    scaled to this launch's algorithmic bytes (the kernels stream their
+    inputs once, so traffic grows in proportion)."""
     if not os.path.exists(TRAFFIC_FILE):
         return None
+    found = {}
     with open(TRAFFIC_FILE) as f:
         for line in f:
+            if line.startswith("#"):
+                continue
             parts = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
             if parts.get("kernel") == kernel and "dram_over_algorithmic" in parts:
-                return round(float(parts["dram_over_algorithmic"]) *
-                             algorithmic_bytes_per_launch)
-    return None
+                found.setdefault(parts.get("workload"), float(parts["dram_over_algorithmic"]))
+    ratio = found.get(workload, found.get(None))
+    return None if ratio is None else round(ratio * algorithmic_bytes_per_launch)
 
 
 # ---------------------------------------------------------------------------
