@@ -60,8 +60,14 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer e2e timing")
     ap.add_argument("--no-serve", action="store_true", help="skip the request-stream run")
     ap.add_argument("--no-autotune", action="store_true", help="keep the heuristic tile shapes")
-    ap.add_argument("--serve-requests", type=int, default=40,
-                    help="requests of the served stream (bounded sample of 2000)")
+    ap.add_argument("--serve-requests", type=int, default=2000,
+                    help="requests of the served stream")
+    ap.add_argument("--serve-rates", default="50,200,1000",
+                    help="open-loop Poisson arrival rates (requests/s), comma list")
+    ap.add_argument("--serve-forms", default="fp64,fp32,fp16,fp32_packed",
+                    help="server forms (inner-sweep precision, packing), comma list")
+    ap.add_argument("--serve-sweep-forms", default="fp64,fp32_packed",
+                    help="forms that also run the open-loop rate sweep, comma list")
     ap.add_argument("--no-profile", action="store_true",
                     help="do not time kernels with events inside the timed region")
     ap.add_argument("--only-extras", default="",
@@ -594,7 +600,10 @@ def run_ours(args):
             out["hybrid"] = hybrid(gs2, torch, lap, stream, torch.from_numpy(lap.b).cuda())
         del lap
     if want("serving", args.no_serve):
-        out["serving"] = serving(gs2, torch, args.serve_requests)
+        out["serving"] = serving(gs2, torch, args.serve_requests,
+                                 [float(r) for r in args.serve_rates.split(",") if r],
+                                 [f for f in args.serve_forms.split(",") if f],
+                                 [f for f in args.serve_sweep_forms.split(",") if f])
     if want("small_system", args.no_extras):
         out["small_system"] = small_system(gs2, torch)
     if want("packs", args.no_extras):
@@ -948,68 +957,108 @@ def cpu_table(gs2, torch, P, reps=10, solve_budget_s=30.0):
     return res
 
 
-def serving(gs2, torch, count):
-    """The request stream: 2D/3D Poisson and 3D convection-diffusion systems,
+def _make_request(rec):
+    """One request of the stream (spawned worker): its CSR and right-hand side."""
+    from paper_2104_01196_gb300 import problems as P
+    _, kind, N, seed = rec
+    pr = P.variable_coefficient_problem(kind, N, seed)
+    return pr.A, pr.b
+
+
+SERVE_FORMS = {
+    # name: (inner-sweep precision, rows up to which requests are packed)
+    "fp64": ("fp64", 0),
+    "fp32": ("fp32", 0),
+    "fp16": ("fp16", 0),
+    "fp32_packed": ("fp32", 1 << 16),
+}
+
+
+def serving(gs2, torch, count, rates, forms, sweep_forms, workers=0):
+    """The request stream of the serving configuration: `count` requests,
+    each a 2D/3D Poisson or 3D convection-diffusion system (type uniform),
     n log-uniform in [1e3, 2e6], lognormal(0,1) coefficients, GMRES(30) +
-    SGS2(1,1) to 1e-8 (a bounded sample of `count` requests).  Measured:
-    one-at-a-time gmres_solve, the server saturated (all submitted at once:
-    solves/s) and the server under open-loop Poisson arrivals at 60% of that
-    rate (p50/p99 submit-to-done latency), with FP64 and FP32 inner sweeps,
-    and FP32 with requests of at most 65,536 rows admitted together as packs
-    (up to 32 per pack)."""
+    SGS2(1,1) to 1e-8, served by the continuous-batching server (8 slots,
+    admission by device memory).  Per form (inner sweeps FP64, FP32, FP16, or
+    FP32 with requests of at most 65,536 rows admitted together as packs):
+    the server saturated (every request submitted at once: solves/s and
+    submit-to-done latency); for the forms in `sweep_forms` also open-loop
+    Poisson arrivals at each rate in `rates` (the stream's seeded
+    inter-arrival gaps rescaled; p50/p99 latency over all requests and per
+    size tercile, throughput achieved).
+    The requests are generated once, before any clock starts, by spawned
+    worker processes; the server copies each request's inputs at submit."""
+    import multiprocessing as mp
+
     from paper_2104_01196_gb300 import problems as P
     recipe = P.request_stream(count, rate_hz=1.0, build=False)
-    probs = [P.variable_coefficient_problem(kind, N, seed) for _, kind, N, seed in recipe]
-    res = {"requests": count, "n_total": int(sum(p.n for p in probs)),
-           "n_range": [int(min(p.n for p in probs)), int(max(p.n for p in probs))]}
-    torch.cuda.synchronize()
-    # one at a time, FP64, through gmres_solve on fresh handles
     t0 = time.perf_counter()
-    seq_fail = 0
-    for p in probs:
-        h = gs2.gs2_setup(p.A)
-        x = np.zeros(p.n)
-        info = gs2.gmres_solve(h, p.b.copy(), x, 30, 1e-8, 4000,
-                               gs2.params("gs2", 1, 1, direction="symmetric"))
-        seq_fail += info.status != 0
-        h.close()
-    res["sequential_fp64"] = {"solves_per_s": count / (time.perf_counter() - t0),
-                              "failed": int(seq_fail)}
-    for name, prec, pack_rows in (("fp64", "fp64", 0), ("fp32", "fp32", 0),
-                                  ("fp32_packed", "fp32", 1 << 16)):
+    nw = workers or max(1, min(16, (os.cpu_count() or 2) - 1))
+    with mp.get_context("spawn").Pool(nw) as pool:
+        reqs = pool.map(_make_request, recipe, chunksize=4)
+    gen_s = time.perf_counter() - t0
+    ns = np.array([len(A[0]) - 1 for A, _ in reqs])
+    gaps = np.diff(np.concatenate([[0.0], [r[0] for r in recipe]]))  # rate 1/s
+    terc = np.quantile(ns, [1 / 3, 2 / 3])
+    tercile = np.digitize(ns, terc)  # 0, 1, 2
+    res = {"requests": count, "n_total": int(ns.sum()), "n_range": [int(ns.min()), int(ns.max())],
+           "size_terciles_rows": [[int(ns.min()), int(terc[0])], [int(terc[0]), int(terc[1])],
+                                  [int(terc[1]), int(ns.max())]],
+           "generate_s": round(gen_s, 1), "workers": nw}
+
+    def pct(v):
+        return {"p50": round(float(np.percentile(v, 50)), 2),
+                "p99": round(float(np.percentile(v, 99)), 2)} if len(v) else None
+
+    for name in forms:
+        prec, pack_rows = SERVE_FORMS[name]
         pc = gs2.params("gs2", 1, 1, direction="symmetric", precision=prec)
-        srv = gs2.Server(restart=30, tol=1e-8, max_iters=4000, precond=pc, max_slots=8,
+        srv = gs2.Server(restart=30, tol=1e-8, max_iters=10000, precond=pc, max_slots=8,
                          prep_threads=4, pack_rows=pack_rows, pack_max=32)
+        row = {}
+        # saturated: everything queued at once
         t0 = time.perf_counter()
-        tickets = [srv.submit(p.A, p.b) for p in probs]
-        lat, worst = [], 0.0
-        for t, p in zip(tickets, probs):
-            info, x, ms = srv.wait(t, p.n)
+        tickets = [srv.submit(A, b) for A, b in reqs]
+        lat, iters, bad, worst = [], [], 0, 0.0
+        for t in tickets:
+            info, _, ms = srv.wait(t, 0, timeout=3600.0)
             lat.append(ms)
-            worst = max(worst, info.true_relres if info.status == 0 else float("inf"))
+            iters.append(info.iters)
+            if info.status != 0:
+                bad += 1
+            else:
+                worst = max(worst, info.true_relres)
         dt = time.perf_counter() - t0
+        sat = count / dt
         st = srv.stats()
-        rate = count / dt
-        # open loop: Poisson arrivals at 60% of the saturated rate
-        gaps = -np.log(1.0 - P.uniform01(P.SEED_BASE + 77, count)) / (0.6 * rate)
-        arrivals = np.cumsum(gaps)
-        t0 = time.perf_counter()
-        tickets = []
-        for a, p in zip(arrivals, probs):
-            delay = a - (time.perf_counter() - t0)
-            if delay > 0:
-                time.sleep(delay)
-            tickets.append(srv.submit(p.A, p.b))
-        olat = [srv.wait(t, p.n)[2] for t, p in zip(tickets, probs)]
+        row["saturated"] = {"solves_per_s": round(sat, 2), "s": round(dt, 2),
+                            "latency_ms": pct(lat), "failed": bad,
+                            "worst_true_relres": worst, "max_active": st["max_active"],
+                            "iters_total": int(np.sum(iters)),
+                            "iters_median": int(np.median(iters)),
+                            "iters_max": int(np.max(iters))}
+        for rate in (rates if name in sweep_forms else []):
+            arrivals = np.cumsum(gaps / rate)
+            t0 = time.perf_counter()
+            tickets = []
+            for a, (A, b) in zip(arrivals, reqs):
+                delay = a - (time.perf_counter() - t0)
+                if delay > 0:
+                    time.sleep(delay)
+                tickets.append(srv.submit(A, b))
+            lat = np.array([srv.wait(t, 0, timeout=3600.0)[2] for t in tickets])
+            dt = time.perf_counter() - t0
+            row[f"open_loop_{rate:g}_per_s"] = {
+                "offered_per_s": rate, "achieved_per_s": round(count / dt, 2),
+                "s": round(dt, 2), "latency_ms": pct(lat),
+                "latency_ms_by_size_tercile": [pct(lat[tercile == k]) for k in range(3)]}
         srv.close()
-        res[f"served_{name}"] = {
-            "solves_per_s": rate, "max_active": st["max_active"], "failed": st["failed"],
-            "worst_true_relres": worst,
-            "saturated_latency_ms": {"p50": float(np.percentile(lat, 50)),
-                                     "p99": float(np.percentile(lat, 99))},
-            "open_loop_rate_hz": 0.6 * rate,
-            "open_loop_latency_ms": {"p50": float(np.percentile(olat, 50)),
-                                     "p99": float(np.percentile(olat, 99))}}
+        res[name] = row
+    base = res.get("fp64", {}).get("saturated", {}).get("solves_per_s")
+    if base:
+        res["saturated_speedup_vs_fp64"] = {
+            k: round(res[k]["saturated"]["solves_per_s"] / base, 3)
+            for k in forms if k != "fp64"}
     return res
 
 

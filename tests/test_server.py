@@ -47,13 +47,13 @@ def _mix():
     return reqs
 
 
-def _alone(pr, pc):
+def _alone(pr, pc, max_iters=4000):
     import torch
     h = gs2.gs2_setup(pr.A)
     h.set_graph_mode(1)  # the cycle-graph path the server runs
     x = torch.zeros(pr.n, dtype=torch.float64, device="cuda")
     b = torch.from_numpy(pr.b).cuda()
-    info = gs2.gmres_solve(h, b, x, 30, 1e-8, 4000, pc)
+    info = gs2.gmres_solve(h, b, x, 30, 1e-8, max_iters, pc)
     torch.cuda.synchronize()
     out = x.cpu().numpy()
     h.close()
@@ -242,3 +242,37 @@ def test_footprint_bounds_what_a_handle_allocates(lib, pc_name):
         h.close()
         fp = gs2.server_footprint(pr.n, pr.nnz, restart=30, precond=pc)
         assert used <= fp, (pr.name, pc_name, used, fp)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["fp64", "fp16"])
+def test_staggered_arrivals_equal_alone(lib, prec):
+    """Requests submitted while earlier ones are on the GPU (each submitted
+    after the previous one was admitted and has run for a while, and one
+    large request keeps a slot busy throughout) are admitted into free slots
+    as they arrive; every result is still bitwise the one it gets alone."""
+    import time
+    pc = gs2.params("gs2", 1, 1, direction="symmetric", precision=prec)
+    big = P.variable_coefficient_problem("poisson2d", 1200, 21)  # a long solve
+    probs = [big] + _mix()
+    srv = gs2.Server(restart=30, tol=1e-8, max_iters=8000, precond=pc, max_slots=3,
+                     prep_threads=2)
+    t_sub = [time.perf_counter()]
+    tickets = [srv.submit(big.A, big.b)]
+    running_seen = 0
+    for p in probs[1:]:
+        time.sleep(0.01)
+        running_seen = max(running_seen, srv.stats()["active"])
+        t_sub.append(time.perf_counter())
+        tickets.append(srv.submit(p.A, p.b))
+    got = [srv.wait(t, p.n) for t, p in zip(tickets, probs)]
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(probs) and st["failed"] == 0
+    assert running_seen >= 1 and st["max_active"] > 1
+    # the large request was still running when the last one arrived
+    assert t_sub[0] + got[0][2] / 1000.0 > t_sub[-1]
+    for p, (info, x, lat) in zip(probs, got):
+        ainfo, ax = _alone(p, pc, 8000)
+        assert info.status == 0 and info.iters == ainfo.iters, p.name
+        assert np.array_equal(x, ax), p.name
