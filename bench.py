@@ -451,7 +451,8 @@ def run_ours(args):
     pr = P.convdiff3d(args.grid)
     n, nnz = pr.n, pr.nnz
     stream = torch.cuda.Stream()
-    h = gs2.gs2_setup(pr.A, precisions=("fp32", "fp16"), stream=stream.cuda_stream)
+    h = gs2.gs2_setup(pr.A, precisions=("fp32", "fp16", "fp32_sweep", "fp16_sweep"),
+                      stream=stream.cuda_stream)
     if not args.no_autotune:
         h.autotune()  # tile shapes of A and the triangles (setup time, untimed)
     shapes = {k: v for k, v in h.stats().items() if k.startswith(("tpr", "rpt", "sell"))}
@@ -566,7 +567,7 @@ def run_ours(args):
     # ---- the same workload with lower-precision inner sweeps --------------
     if want("precision", args.no_extras):
         res = {}
-        for prec in ("fp32", "fp16"):
+        for prec in ("fp32", "fp16", "fp32_sweep", "fp16_sweep"):
             pp = gs2.params("gs2", 1, 1, direction="symmetric", precision=prec)
             sp = solver(pp)
             with torch.cuda.stream(stream):
@@ -585,7 +586,7 @@ def run_ours(args):
             if not args.no_profile:
                 tab, _ = profiled(h, torch, stream, sp, 0, hbm, n, nnz)
                 row["kernels"] = {k: v for k, v in tab.items()
-                                  if k.startswith(("inner", "resid", "spmv"))}
+                                  if k.startswith(("inner", "resid", "spmv", "rhat", "to32"))}
             res[prec] = row
         out["precision"] = res
     h.close()
@@ -966,11 +967,14 @@ def _make_request(rec):
 
 
 SERVE_FORMS = {
-    # name: (inner-sweep precision, rows up to which requests are packed)
+    # name: (sweep precision, rows up to which requests are packed)
     "fp64": ("fp64", 0),
     "fp32": ("fp32", 0),
     "fp16": ("fp16", 0),
     "fp32_packed": ("fp32", 1 << 16),
+    "fp32_sweep": ("fp32_sweep", 0),
+    "fp16_sweep": ("fp16_sweep", 0),
+    "fp32_sweep_packed": ("fp32_sweep", 1 << 16),
 }
 
 
@@ -1134,7 +1138,8 @@ def comparisons(gs2, torch, pr, stream, b):
         "cg_sgs2_1_1": gs2.params("gs2", 1, 1, direction="symmetric"),
         "cg_amg_sgs2_1_1": gs2.params("amg", 1, 1, direction="symmetric"),
     }
-    h = gs2.gs2_setup(pr.A, precisions=("fp32", "fp16"), stream=stream.cuda_stream)
+    h = gs2.gs2_setup(pr.A, precisions=("fp32", "fp16", "fp32_sweep", "fp16_sweep"),
+                      stream=stream.cuda_stream)
     t0 = time.perf_counter()
     h.amg_setup()  # smoothed-aggregation hierarchy (host setup, once per matrix)
     res["amg_setup_s"] = round(time.perf_counter() - t0, 3)

@@ -54,14 +54,25 @@ typedef enum {
 
 typedef enum { GS2_FORWARD = 0, GS2_BACKWARD = 1, GS2_SYMMETRIC = 2 } gs2_direction;
 
-/* Storage and arithmetic of the inner sweeps (the triangles D^{-1}L and
- * D^{-1}U and the inner iterate g).  The residual r = b - A x (outer
- * iteration) is always FP64.  Sec. 10 runs the preconditioner in single
- * precision; FP16 with a per-row FP32 scale is an extension of that. */
+/* Storage and arithmetic of a GS2 sweep.  Sec. 10 runs the preconditioner
+ * in single precision (its outer GS and inner JR iterations); FP16 values
+ * with a per-row power-of-two scale are an extension of that.
+ *   GS2_FP32, GS2_FP16_ROWSCALED: the inner sweeps only (the triangles
+ *     D^{-1}L, D^{-1}U and the inner iterate g); the residual r = b - A x
+ *     and the iterate x stay FP64.
+ *   GS2_FP32_SWEEP, GS2_FP16_SWEEP: the whole sweep: the iterate x32 =
+ *     fl32(x), the residual rhat = fl32(D^{-1}b) - x32 - (D^{-1}(L+U)) x32
+ *     from FP32 (or row-scaled FP16) values of the prescaled off-diagonal
+ *     entries in FP32 arithmetic, the inner sweeps as above, x32 += omega g
+ *     in FP32; x = (double) x32 at the end of the call.  GS2 preconditioner
+ *     (GMRES, CG, batch, packs, server) and gs2_apply_ex; not with the AMG,
+ *     hybrid or compact forms. */
 typedef enum {
   GS2_FP64 = 0,
   GS2_FP32 = 1,
-  GS2_FP16_ROWSCALED = 2
+  GS2_FP16_ROWSCALED = 2,
+  GS2_FP32_SWEEP = 3,
+  GS2_FP16_SWEEP = 4
 } gs2_precision;
 
 /* Non-compact form Eq. (2) is the paper's default (Sec. 7 setup); the

@@ -34,7 +34,7 @@ PC_NONE, PC_GS2, PC_JR, PC_GS, PC_MTGS = 0, 1, 2, 3, 4
 PC_HYBRID_GS2, PC_HYBRID_JR, PC_HYBRID_GS = 7, 8, 9
 PC_GS2_COMPACT = 10
 # inner-sweep precision of GS2 (lowprec.c)
-PREC = {"fp64": 0, "fp32": 1, "fp16": 2}
+PREC = {"fp64": 0, "fp32": 1, "fp16": 2, "fp32_sweep": 3, "fp16_sweep": 4}
 
 
 class OracleError(RuntimeError):

@@ -143,10 +143,12 @@ void ora_set_hybrid(int parts, int local);
 /* ------------------------------------------------------------------ */
 /* GS2 with lower-precision inner sweeps (lowprec.c; the definitions    */
 /* are stated there): FP32 values and vectors, or FP16 values with a    */
-/* per-row FP32 scale, FP32 accumulation; residual and update in FP64.  */
+/* per-row power-of-two scale, FP32 accumulation; residual and update   */
+/* in FP64 -- or, in the whole-sweep precisions, in FP32 as well.       */
 /* ------------------------------------------------------------------ */
 
-enum { ORA_PREC_FP64 = 0, ORA_PREC_FP32 = 1, ORA_PREC_FP16_ROWSCALED = 2 };
+enum { ORA_PREC_FP64 = 0, ORA_PREC_FP32 = 1, ORA_PREC_FP16_ROWSCALED = 2,
+       ORA_PREC_FP32_SWEEP = 3, ORA_PREC_FP16_SWEEP = 4 };
 
 /* GS2 sweeps as ora_gs2 with the inner sweeps in precision `prec`
  * (ORA_PREC_FP64 is ora_gs2 itself).  x in place. */

@@ -28,7 +28,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgs2.so")
 
 FORWARD, BACKWARD, SYMMETRIC = 0, 1, 2
-FP64, FP32, FP16_ROWSCALED = 0, 1, 2
+FP64, FP32, FP16_ROWSCALED, FP32_SWEEP, FP16_SWEEP = 0, 1, 2, 3, 4
 PC_NONE, PC_GS2, PC_JR, PC_GS, PC_MTGS, PC_AMG, PC_AMG_JR = 0, 1, 2, 3, 4, 5, 6
 AMG_MAX_LEVELS = 16
 NONCOMPACT, COMPACT = 0, 1
@@ -36,7 +36,8 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "ZERO_DIAGONAL", 3: "OOM", 4: "CUDA",
           5: "NOT_CONVERGED", 6: "BREAKDOWN", 7: "NAN", 8: "TIMEOUT", 9: "BUSY",
           10: "NOT_FOUND"}
 _DIR = {"forward": FORWARD, "backward": BACKWARD, "symmetric": SYMMETRIC}
-_PREC = {"fp64": FP64, "fp32": FP32, "fp16": FP16_ROWSCALED}
+_PREC = {"fp64": FP64, "fp32": FP32, "fp16": FP16_ROWSCALED, "fp32_sweep": FP32_SWEEP,
+         "fp16_sweep": FP16_SWEEP}
 _KIND = {"none": PC_NONE, "gs2": PC_GS2, "jr": PC_JR, "gs": PC_GS, "mtgs": PC_MTGS,
          "amg": PC_AMG, "amg_jr": PC_AMG_JR}
 

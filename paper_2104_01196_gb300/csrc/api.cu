@@ -415,19 +415,27 @@ static void prepare_lowprec(gs2_handle* h, DevCsr& M, const HostTri& T, int prec
     }
   }
   if (prec == GS2_FP16_ROWSCALED && !M.va16) {
+    // row scale 2^e_i with max_j |v_ij| / 2^e_i in [1/2, 1): scaling by a
+    // power of two is exact, so q_ij = fl16(v_ij 2^-e_i) is the only rounding
+    // and the row keeps binary16's full precision at any magnitude; e_i is
+    // stored in one byte (clamped to [-126, 127], the exponents of a normal
+    // FP32 power of two)
     std::vector<__half> v(nz, __float2half(0.f));
-    std::vector<float> s(M.n, 0.f);
+    std::vector<signed char> s(M.n, 0);
     for (int i = 0; i < M.n; ++i) {
       double m = 0.0;
       for (int k = T.rp[i]; k < T.rp[i + 1]; ++k) m = std::max(m, std::fabs(T.va[k]));
-      s[i] = (float)m;
+      int e = 0;
+      if (m > 0) std::frexp(m, &e);
+      e = std::min(127, std::max(-126, e));
+      s[i] = (signed char)e;
       for (int k = T.rp[i]; k < T.rp[i + 1]; ++k)
-        v[k] = __double2half(m > 0 ? T.va[k] / m : 0.0);  // one rounding, to nearest
+        v[k] = __double2half(std::ldexp(T.va[k], -e));  // one rounding, to nearest
     }
     M.va16 = (__half*)h->dalloc(sizeof(__half) * nz);
-    M.scale16 = (float*)h->dalloc(sizeof(float) * std::max(M.n, 1));
+    M.scale16 = (signed char*)h->dalloc(sizeof(signed char) * std::max(M.n, 1));
     h->h2d(M.va16, v.data(), sizeof(__half) * nz);
-    h->h2d(M.scale16, s.data(), sizeof(float) * M.n);
+    h->h2d(M.scale16, s.data(), sizeof(signed char) * M.n);
     if (M.sell_chunks > 0) {  // the layout exists (the autotuner may turn it off and on)
       const size_t slots = M.sell_slots;
       M.sell_va16 = (__half*)h->dalloc(sizeof(__half) * slots);
@@ -442,6 +450,7 @@ static void prepare_lowprec(gs2_handle* h, DevCsr& M, const HostTri& T, int prec
 // host copies of the triangles, kept for lazy precision / level setup
 struct gs2_host_side {
   gs2::HostTri L, U;
+  gs2::HostTri O;  // D^{-1}(L + U): row i's L entries, then its U entries (built lazily)
   std::vector<int> Arp;  // rowptr of A (re-tiling)
   // local triangles of each hybrid form (low-precision copies), by parts
   std::map<int, std::pair<gs2::HostTri, gs2::HostTri>> hyb;
@@ -514,16 +523,46 @@ static gs2_host_side* host_side(const gs2_handle* h) {
 
 void ensure_precision(gs2_handle* h, int prec) {
   if (prec == GS2_FP64) return;
-  if (prec != GS2_FP32 && prec != GS2_FP16_ROWSCALED)
+  if (prec != GS2_FP32 && prec != GS2_FP16_ROWSCALED && !is_sweep_precision(prec))
     GS2_THROW(GS2_ERR_INVALID_ARG, "unknown precision");
   gs2_host_side* hs = host_side(h);
-  prepare_lowprec(h, h->L, hs->L, prec);
-  prepare_lowprec(h, h->U, hs->U, prec);
+  const int vprec = value_precision(prec);
+  prepare_lowprec(h, h->L, hs->L, vprec);
+  prepare_lowprec(h, h->U, hs->U, vprec);
+  const size_t n = std::max<int64_t>(h->n, 1);
   if (!h->rhat32) {
-    const size_t n = std::max<int64_t>(h->n, 1);
     h->rhat32 = (float*)h->dalloc(sizeof(float) * n);
     h->g32a = (float*)h->dalloc(sizeof(float) * n);
     h->g32b = (float*)h->dalloc(sizeof(float) * n);
+  }
+  if (!is_sweep_precision(prec)) return;
+  // the whole-sweep precisions: the prescaled off-diagonal matrix O =
+  // D^{-1}(L + U) in the value precision, fl32(D^{-1} b) and the FP32 iterate
+  if (h->O.rp == nullptr) {
+    HostTri& O = hs->O;
+    const int nn = (int)h->n;
+    O.rp.assign(nn + 1, 0);
+    for (int i = 0; i < nn; ++i)
+      O.rp[i + 1] = O.rp[i] + (hs->L.rp[i + 1] - hs->L.rp[i]) + (hs->U.rp[i + 1] - hs->U.rp[i]);
+    O.ci.resize(O.rp[nn]);
+    O.va.resize(O.rp[nn]);
+    for (int i = 0; i < nn; ++i) {
+      int k = O.rp[i];
+      for (int q = hs->L.rp[i]; q < hs->L.rp[i + 1]; ++q, ++k) {
+        O.ci[k] = hs->L.ci[q];
+        O.va[k] = hs->L.va[q];
+      }
+      for (int q = hs->U.rp[i]; q < hs->U.rp[i + 1]; ++q, ++k) {
+        O.ci[k] = hs->U.ci[q];
+        O.va[k] = hs->U.va[q];
+      }
+    }
+    upload_csr(h, h->O, nn, O.rp, O.ci.data(), O.va.data(), (int)O.ci.size());
+  }
+  prepare_lowprec(h, h->O, hs->O, vprec);
+  if (!h->bhat32) {
+    h->bhat32 = (float*)h->dalloc(sizeof(float) * n);
+    h->x32 = (float*)h->dalloc(sizeof(float) * n);
   }
 }
 
@@ -836,7 +875,11 @@ static void check_params(const gs2_params* p) {
   if (!(p->gamma > 0.0) || !std::isfinite(p->gamma))
     GS2_THROW(GS2_ERR_INVALID_ARG, "gamma must be > 0");
   if (p->direction < 0 || p->direction > 2) GS2_THROW(GS2_ERR_INVALID_ARG, "direction");
-  if (p->precision < 0 || p->precision > 2) GS2_THROW(GS2_ERR_INVALID_ARG, "precision");
+  if (p->precision < 0 || p->precision > 4) GS2_THROW(GS2_ERR_INVALID_ARG, "precision");
+  if (is_sweep_precision(p->precision) &&
+      (p->kind != GS2_PC_GS2 || p->form != GS2_NONCOMPACT || p->parts > 1))
+    GS2_THROW(GS2_ERR_INVALID_ARG,
+              "the whole-sweep precisions are for non-compact, non-hybrid GS2");
   if (p->form != GS2_NONCOMPACT && p->form != GS2_COMPACT)
     GS2_THROW(GS2_ERR_INVALID_ARG, "form");
   if (p->form == GS2_COMPACT && (p->kind != GS2_PC_GS2 || p->omega != 1.0 || p->gamma != 1.0))
@@ -1115,7 +1158,7 @@ gs2_handle* gs2::setup_handle(int64_t n, int64_t nnz, const int64_t* rowptr,
       1, std::min<int64_t>((n + kVecThreads * 16 - 1) / (kVecThreads * 16), h->nsm));
   h->part_cap = h->nblk * (kMaxRestart + 2);
   h->part = (double*)h->dalloc(sizeof(double) * h->part_cap);
-  for (int p = 1; p <= 2; ++p)
+  for (int p = 1; p <= 4; ++p)
     if (precisions & (1u << p)) ensure_precision(h, p);
   GS2_CUDA(cudaStreamSynchronize(h->stream));
   return h;

@@ -71,7 +71,7 @@ struct DevCsr {
   double* va = nullptr;    // nnz (padded)
   float* va32 = nullptr;   // FP32 copy (triangles)
   __half* va16 = nullptr;  // FP16 scaled copy (triangles)
-  float* scale16 = nullptr;
+  signed char* scale16 = nullptr;  // FP16 copy: row scale exponent e_i (scale 2^e_i)
   int tpr = 1;             // lanes per row (K) of the tile kernels
   int rpt = 1;             // rows per group of K lanes (RPT), 1 or 2 (K <= 2)
   // row tiles: desc[t] = {first row, end row, first staged entry (rowptr
@@ -151,6 +151,9 @@ struct gs2_handle {
   cudaStream_t stream = nullptr;
   int64_t n = 0, nnz = 0;
   gs2::DevCsr A, L, U;  // L, U prescaled: D^{-1} L and D^{-1} U
+  // D^{-1}(L + U), prescaled off-diagonal entries (whole-sweep FP32/FP16
+  // precisions only: the residual of the single-precision sweep)
+  gs2::DevCsr O;
   double* dinv = nullptr;
   int* dev_err = nullptr;  // sticky device error word (bounded waits)
   int64_t dev_bytes = 0;
@@ -160,6 +163,8 @@ struct gs2_handle {
   double *r = nullptr, *rhat = nullptr, *g0 = nullptr, *g1 = nullptr;
   double *z = nullptr, *t = nullptr, *bstage = nullptr, *xstage = nullptr;
   float *rhat32 = nullptr, *g32a = nullptr, *g32b = nullptr;
+  // whole-sweep precisions: fl32(D^{-1} b) and the FP32 iterate
+  float *bhat32 = nullptr, *x32 = nullptr;
   double* part = nullptr;  // per-block partial sums
   int nblk = 0;            // blocks of the elementwise vector kernels
   int nblk_dot = 0;        // blocks of the reduction kernels (<= nblk)
@@ -279,7 +284,26 @@ void launch_resid_matrix(gs2_handle* h, const DevCsr& M, const double* b, const 
 void launch_prep_rhat(gs2_handle* h, const double* v, double* rhat64,
                       float* rhat32, const int* skip);
 
-enum InnerMode { INNER_MID = 0, INNER_LAST_ADD = 1, INNER_LAST_SET = 2 };
+// INNER_MID: g' to g_out.  LAST_ADD / LAST_SET: x += omega g' / x = omega g'
+// in FP64.  Whole-sweep precisions (FP32 iterate x32): LAST_ADD32 /
+// LAST_SET32 write x32 + omega g' / omega g' to x32, LAST_ADD32_OUT /
+// LAST_SET32_OUT write the same FP32 value, converted, to the FP64 x (the
+// last half sweep of a call).
+enum InnerMode {
+  INNER_MID = 0,
+  INNER_LAST_ADD = 1,
+  INNER_LAST_SET = 2,
+  INNER_LAST_ADD32 = 3,
+  INNER_LAST_SET32 = 4,
+  INNER_LAST_ADD32_OUT = 5,
+  INNER_LAST_SET32_OUT = 6
+};
+
+// whole-sweep precisions and the value precision of their matrices
+inline bool is_sweep_precision(int prec) { return prec == GS2_FP32_SWEEP || prec == GS2_FP16_SWEEP; }
+inline int value_precision(int prec) {
+  return prec == GS2_FP32_SWEEP ? GS2_FP32 : (prec == GS2_FP16_SWEEP ? GS2_FP16_ROWSCALED : prec);
+}
 
 // One inner JR sweep on triangle T (h->L or h->U):
 //   g_out = (1-gamma) g_in + gamma (rhat - omega T g_in)
@@ -297,6 +321,16 @@ void launch_compact_rhs(gs2_handle* h, const DevCsr& Tother, const double* b, co
 // x = omega * rhat (zero inner sweeps from a zero start) or x += omega*rhat.
 void launch_rhat_update(gs2_handle* h, int prec, const void* rhat, double* x,
                         double omega, bool add, const int* skip);
+
+// Whole-sweep precisions (vprec: the value precision, GS2_FP32 or
+// GS2_FP16_ROWSCALED): rhat32 = fl32(D^{-1} b) - x32 - O x32 in FP32 (bhat32
+// and x32 of the handle, O = D^{-1}(L + U)); the update of a sweep with no
+// inner sweep, x32 / x from rhat (mode: one of the x32 InnerModes); and the
+// conversion x32 = fl32(x).
+void launch_resid_sweep(gs2_handle* h, int vprec, const int* skip);
+void launch_rhat_update32(gs2_handle* h, const float* rhat, double* x, double omega, int mode,
+                          const int* skip);
+void launch_to32(gs2_handle* h, const double* x, float* x32, const int* skip);
 
 void launch_spmv(gs2_handle* h, const double* x, double* y, const int* skip);
 // autotuner probe: ms per launch of M's most frequent kernel (role 0: A's

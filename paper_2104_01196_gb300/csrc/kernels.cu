@@ -98,20 +98,23 @@ struct EpiInner {
   const GT* __restrict__ rhat;
   GT* __restrict__ g_out;
   double* __restrict__ x;
-  const float* __restrict__ rowscale;  // FP16 triangles only
+  const signed char* __restrict__ rowscale;  // FP16 triangles only: scale 2^e_i
   AT omega, gamma;
   double omega64;
   int mode;
+  float* __restrict__ x32;  // whole-sweep precisions: the FP32 iterate
   struct Pre {
     AT rh, gi, sc;
     double xi;
+    float x32i;
   };
   __device__ Pre pre(int i) const {
     Pre p;
     p.rh = (AT)rhat[i];
     p.gi = DAMPED ? (AT)g_in[i] : AT(0);
-    p.sc = SCALED ? (AT)rowscale[i] : AT(1);
+    p.sc = SCALED ? (AT)__int_as_float(((int)rowscale[i] + 127) << 23) : AT(1);
     p.xi = mode == INNER_LAST_ADD ? x[i] : 0.0;
+    p.x32i = (mode == INNER_LAST_ADD32 || mode == INNER_LAST_ADD32_OUT) ? x32[i] : 0.f;
     return p;
   }
   __device__ AT gather(int c) const { return (AT)__ldg(g_in + c); }
@@ -119,9 +122,44 @@ struct EpiInner {
     if (SCALED) s *= p.sc;
     AT go = p.rh - omega * s;
     if (DAMPED) go = (AT(1) - gamma) * p.gi + gamma * go;
-    if (mode == INNER_MID) g_out[i] = (GT)go;
-    else if (mode == INNER_LAST_ADD) x[i] = p.xi + omega64 * (double)go;
-    else x[i] = omega64 * (double)go;
+    if (mode == INNER_MID) {
+      g_out[i] = (GT)go;
+    } else if (mode == INNER_LAST_ADD) {
+      x[i] = p.xi + omega64 * (double)go;
+    } else if (mode == INNER_LAST_SET) {
+      x[i] = omega64 * (double)go;
+    } else {
+      // FP32 iterate: x32 + omega g (or omega g) in FP32 arithmetic
+      const float u = (float)omega * (float)go;
+      const float xn = (mode == INNER_LAST_ADD32 || mode == INNER_LAST_ADD32_OUT) ? p.x32i + u : u;
+      if (mode == INNER_LAST_ADD32 || mode == INNER_LAST_SET32) x32[i] = xn;
+      else x[i] = (double)xn;
+    }
+  }
+};
+
+// residual of the whole-sweep precisions on the prescaled off-diagonal
+// matrix O = D^{-1}(L + U), FP32 arithmetic:
+//   rhat32 = (fl32(D^{-1} b) - x32) - O x32
+template <bool SCALED>
+struct EpiResidSweep {
+  const float* __restrict__ bhat;
+  const float* __restrict__ x32;
+  const signed char* __restrict__ rowscale;
+  float* __restrict__ rhat32;
+  struct Pre {
+    float bx, sc;
+  };
+  __device__ Pre pre(int i) const {
+    Pre p;
+    p.bx = bhat[i] - x32[i];
+    p.sc = SCALED ? __int_as_float(((int)rowscale[i] + 127) << 23) : 1.f;
+    return p;
+  }
+  __device__ float gather(int c) const { return __ldg(x32 + c); }
+  __device__ void finish(int i, float s, const Pre& p) const {
+    if (SCALED) s *= p.sc;
+    rhat32[i] = p.bx - s;
   }
 };
 
@@ -365,7 +403,7 @@ void launch_inner(gs2_handle* h, const DevCsr& T, int prec, const void* rhat,
   const double gb = prec == GS2_FP64 ? 8.0 : 4.0;
   double bytes = bytes_csr(T, (int)vb) + gb * T.n * (2 + (damped ? 1 : 0)) +
                  (mode == INNER_MID ? gb * T.n : (mode == INNER_LAST_ADD ? 16.0 : 8.0) * T.n) +
-                 (prec == GS2_FP16_ROWSCALED ? 4.0 * T.n : 0.0);
+                 (prec == GS2_FP16_ROWSCALED ? 1.0 * T.n : 0.0);
   KernelTimer tm(h, prec == GS2_FP64 ? "inner64" : (prec == GS2_FP32 ? "inner32" : "inner16"),
                  bytes);
   if (prec == GS2_FP64) {
@@ -384,26 +422,43 @@ void launch_inner(gs2_handle* h, const DevCsr& T, int prec, const void* rhat,
     if (damped) {
       EpiInner<float, float, true, false> e{(const float*)g_in, (const float*)rhat,
                                             (float*)g_out, x, nullptr, (float)omega,
-                                            (float)gamma, omega, mode};
+                                            (float)gamma, omega, mode, h->x32};
       dispatch<float>(h, T, T.va32, e, skip);
     } else {
       EpiInner<float, float, false, false> e{(const float*)g_in, (const float*)rhat,
                                              (float*)g_out, x, nullptr, (float)omega,
-                                             (float)gamma, omega, mode};
+                                             (float)gamma, omega, mode, h->x32};
       dispatch<float>(h, T, T.va32, e, skip);
     }
   } else {
     if (damped) {
       EpiInner<float, float, true, true> e{(const float*)g_in, (const float*)rhat,
                                            (float*)g_out, x, T.scale16, (float)omega,
-                                           (float)gamma, omega, mode};
+                                           (float)gamma, omega, mode, h->x32};
       dispatch<__half>(h, T, T.va16, e, skip);
     } else {
       EpiInner<float, float, false, true> e{(const float*)g_in, (const float*)rhat,
                                             (float*)g_out, x, T.scale16, (float)omega,
-                                            (float)gamma, omega, mode};
+                                            (float)gamma, omega, mode, h->x32};
       dispatch<__half>(h, T, T.va16, e, skip);
     }
+  }
+}
+
+void launch_resid_sweep(gs2_handle* h, int vprec, const int* skip) {
+  const DevCsr& O = h->O;
+  if (O.n == 0) return;
+  // O once (FP32 or FP16 values and a one-byte row scale), bhat32 and x32
+  // read, rhat32 written
+  const bool half = vprec == GS2_FP16_ROWSCALED;
+  KernelTimer tm(h, half ? "resid16" : "resid32",
+                 bytes_csr(O, half ? 2 : 4) + 12.0 * O.n + (half ? 1.0 * O.n : 0.0));
+  if (half) {
+    EpiResidSweep<true> e{h->bhat32, h->x32, O.scale16, h->rhat32};
+    dispatch<__half>(h, O, O.va16, e, skip);
+  } else {
+    EpiResidSweep<false> e{h->bhat32, h->x32, nullptr, h->rhat32};
+    dispatch<float>(h, O, O.va32, e, skip);
   }
 }
 
@@ -447,6 +502,26 @@ __global__ void k_rhat_update(int n, const GT* __restrict__ rhat, double* x, dou
   }
 }
 
+// update of a whole-sweep-precision sweep without inner sweeps: the FP32
+// iterate x32 + omega rhat (or omega rhat), to x32 or converted to x
+__global__ void k_rhat_update32(int n, const float* __restrict__ rhat, float* x32, double* x,
+                                float omega, int mode, const int* skip) {
+  if (skip && *skip) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float u = omega * rhat[i];
+    const bool add = mode == INNER_LAST_ADD32 || mode == INNER_LAST_ADD32_OUT;
+    const float xn = add ? x32[i] + u : u;
+    if (mode == INNER_LAST_ADD32 || mode == INNER_LAST_SET32) x32[i] = xn;
+    else x[i] = (double)xn;
+  }
+}
+
+__global__ void k_to32(int n, const double* __restrict__ x, float* x32, const int* skip) {
+  if (skip && *skip) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    x32[i] = (float)x[i];
+}
+
 __global__ void k_axpy(int n, double* y, double a, const double* __restrict__ x,
                        const int* skip) {
   if (skip && *skip) return;
@@ -480,6 +555,25 @@ void launch_rhat_update(gs2_handle* h, int prec, const void* rhat, double* x, do
   else
     k_rhat_update<float><<<vec_blocks(h, h->n), kVecThreads, 0, h->stream>>>(
         (int)h->n, (const float*)rhat, x, omega, add ? 1 : 0, skip);
+  GS2_LAUNCH_CHECK();
+}
+
+void launch_rhat_update32(gs2_handle* h, const float* rhat, double* x, double omega, int mode,
+                          const int* skip) {
+  if (h->n == 0) return;
+  const bool add = mode == INNER_LAST_ADD32 || mode == INNER_LAST_ADD32_OUT;
+  const bool out = mode == INNER_LAST_ADD32_OUT || mode == INNER_LAST_SET32_OUT;
+  KernelTimer tm(h, "rhat_update", 4.0 * h->n + (add ? 4.0 : 0.0) * h->n +
+                 (out ? 8.0 : 4.0) * h->n);
+  k_rhat_update32<<<vec_blocks(h, h->n), kVecThreads, 0, h->stream>>>(
+      (int)h->n, rhat, h->x32, x, (float)omega, mode, skip);
+  GS2_LAUNCH_CHECK();
+}
+
+void launch_to32(gs2_handle* h, const double* x, float* x32, const int* skip) {
+  if (h->n == 0) return;
+  KernelTimer tm(h, "to32", 12.0 * h->n);
+  k_to32<<<vec_blocks(h, h->n), kVecThreads, 0, h->stream>>>((int)h->n, x, x32, skip);
   GS2_LAUNCH_CHECK();
 }
 

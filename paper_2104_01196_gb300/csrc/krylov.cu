@@ -459,7 +459,7 @@ struct GmresRun {
     wants = precond_wants_rhat(pc);
     if (wants) {
       void* rb = precond_rhat_buffer(h, pc);
-      if (rb == (void*)h->rhat32) r32 = h->rhat32;
+      if (rb == (void*)h->rhat32 || rb == (void*)h->bhat32) r32 = (float*)rb;
       else r64 = (double*)rb;
     }
     launch_norm(h, b, 1);
@@ -898,7 +898,7 @@ gs2_status cg_run(gs2_handle* h, const double* b, double* x, double tol, int max
   float* r32 = nullptr;
   if (wants) {
     void* rb = precond_rhat_buffer(h, pc);
-    if (rb == (void*)h->rhat32) r32 = h->rhat32;
+    if (rb == (void*)h->rhat32 || rb == (void*)h->bhat32) r32 = (float*)rb;
     else r64 = (double*)rb;
   }
   // one CG iteration (every kernel a no-op once the device has stopped)

@@ -637,7 +637,7 @@ struct PackRun {
     wants = precond_wants_rhat(pc);
     if (wants) {
       void* rb = precond_rhat_buffer(h, pc);
-      if (rb == (void*)h->rhat32) r32 = h->rhat32;
+      if (rb == (void*)h->rhat32 || rb == (void*)h->bhat32) r32 = (float*)rb;
       else r64 = (double*)rb;
     }
     upload_lists();  // every system

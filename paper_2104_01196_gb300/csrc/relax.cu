@@ -97,6 +97,50 @@ static void gs2_half(gs2_handle* h, const gs2_params* p, const DevCsr& T, const 
     inner_sweeps(h, T, prec, rh, x, p->omega, p->gamma, p->inner, mode, skip);
 }
 
+// One half sweep of a whole-sweep precision (GS2_FP32_SWEEP,
+// GS2_FP16_SWEEP) on triangle T, all in FP32 arithmetic on the iterate x32:
+//   rhat = fl32(D^{-1} b) - x32 - O x32   (O = D^{-1}(L + U); skipped from
+//                                          x32 = 0, where rhat = bhat32)
+//   n_j inner sweeps on T from g_0 = rhat, x32 (+)= omega g
+// bhat32 = fl32(D^{-1} b) must be prepared.  last: the final half sweep of
+// the call, which writes the FP64 x = (double) x32 instead of x32.
+static void gs2_half_sweep32(gs2_handle* h, const gs2_params* p, const DevCsr& T, double* x,
+                             bool x_zero, bool last, const int* skip) {
+  const int vprec = value_precision(p->precision);
+  if (!x_zero) launch_resid_sweep(h, vprec, skip);
+  const float* rh = x_zero ? h->bhat32 : h->rhat32;
+  const int mode = last ? (x_zero ? INNER_LAST_SET32_OUT : INNER_LAST_ADD32_OUT)
+                        : (x_zero ? INNER_LAST_SET32 : INNER_LAST_ADD32);
+  if (p->inner == 0)
+    launch_rhat_update32(h, rh, x, p->omega, mode, skip);
+  else
+    inner_sweeps(h, T, vprec, rh, x, p->omega, p->gamma, p->inner, mode, skip);
+}
+
+// The half sweeps of a whole-sweep-precision application in order; x_zero:
+// x = 0 and bhat32 is prepared (the preconditioner), else x32 = fl32(x) and
+// bhat32 = fl32(D^{-1} b) are formed first.
+static void sweep32_relax(gs2_handle* h, const gs2_params* p, const double* b, double* x,
+                          bool x_zero, int sweeps, const int* skip) {
+  if (!x_zero) {
+    launch_to32(h, x, h->x32, skip);
+    launch_prep_rhat(h, b, nullptr, h->bhat32, skip);
+  }
+  const bool fwd = p->direction == GS2_FORWARD || p->direction == GS2_SYMMETRIC;
+  const bool bwd = p->direction == GS2_BACKWARD || p->direction == GS2_SYMMETRIC;
+  bool zero = x_zero;
+  for (int s = 0; s < sweeps; ++s) {
+    if (fwd) {
+      gs2_half_sweep32(h, p, h->L, x, zero, s == sweeps - 1 && !bwd, skip);
+      zero = false;
+    }
+    if (bwd) {
+      gs2_half_sweep32(h, p, h->U, x, zero, s == sweeps - 1, skip);
+      zero = false;
+    }
+  }
+}
+
 // Sweeps of a GS2 / JR parameter set: n_t = outer exchanges of n_k local
 // sweeps each (one block: n_t n_k global sweeps)
 static int global_sweeps(const gs2_params* p) {
@@ -178,6 +222,10 @@ void gs2_relax(gs2_handle* h, const double* b, double* x, const gs2_params* p) {
   if (p->kind == GS2_PC_MTGS) {
     ensure_colors(h);
     mtgs_relax(h, b, x, p->outer, p->omega, p->direction);
+    return;
+  }
+  if (is_sweep_precision(p->precision)) {
+    sweep32_relax(h, p, b, x, false, global_sweeps(p), nullptr);
     return;
   }
   for (int s = 0; s < global_sweeps(p); ++s) {
@@ -280,6 +328,7 @@ bool precond_wants_rhat(const gs2_params* p) {
 // D^{-1} v like the stand-alone smoother does)
 void* precond_rhat_buffer(gs2_handle* h, const gs2_params* p) {
   if (!precond_wants_rhat(p)) return nullptr;
+  if (p->kind == GS2_PC_GS2 && is_sweep_precision(p->precision)) return h->bhat32;
   if (p->kind == GS2_PC_GS2 || p->kind == GS2_PC_AMG) return rhat_buf(h, p->precision);
   return h->rhat;
 }
@@ -321,6 +370,11 @@ void precond_apply(gs2_handle* h, const gs2_params* p, const double* v, double* 
         launch_prep_rhat(h, v, h->rhat, nullptr, skip);
     }
     hybrid_apply(h, p, *Y, v, z, true, skip);
+    return;
+  }
+  if (p->kind == GS2_PC_GS2 && is_sweep_precision(p->precision)) {
+    if (!rhat_ready) launch_prep_rhat(h, v, nullptr, h->bhat32, skip);
+    sweep32_relax(h, p, v, z, true, global_sweeps(p), skip);
     return;
   }
   if (p->kind == GS2_PC_GS2) {

@@ -80,9 +80,14 @@ static int64_t footprint(const gs2_server_cfg& c, int64_t n, int64_t nnz) {
   b += 8 * n * (m + 1) + 3 * 8 * n;   // Krylov basis, w, p, q
   b += 8 * (m + 1) * (m + 6);         // Hessenberg, rotations, y
   if (c.has_precond && c.precond.kind == GS2_PC_GS2) {
-    if (c.precond.precision == GS2_FP32) b += 4 * off + 12 * n + 4 * (off * 6 / 5 + 2);
-    if (c.precond.precision == GS2_FP16_ROWSCALED)
-      b += 2 * off + 8 * n + 12 * n + 2 * (off * 6 / 5 + 2);
+    const int vp = value_precision(c.precond.precision);
+    if (vp == GS2_FP32) b += 4 * off + 12 * n + 4 * (off * 6 / 5 + 2);
+    if (vp == GS2_FP16_ROWSCALED) b += 2 * off + 8 * n + 12 * n + 2 * (off * 6 / 5 + 2);
+    // whole-sweep precisions: the off-diagonal matrix O (its CSR, its
+    // sliced-ELL copy, its value-precision copies) and two FP32 vectors
+    if (is_sweep_precision(c.precond.precision))
+      b += 12 * off + 4 * (n + 17) + (n / 16 + 16) * 16 + sell_bytes(off, n, 8) +
+           (vp == GS2_FP32 ? 8 : 4) * off + 2 * n + 8 * n + 4 * (n / 32 + 2);
   }
   if (c.has_precond && c.precond.kind == GS2_PC_GS) b += 8 * n;
   // hybrid form: the local block of A, the couplings, the local triangles
@@ -508,7 +513,9 @@ gs2_status gs2_server_create(const gs2_server_cfg* cfg, gs2_server** out) {
     const gs2_params& p = cfg->precond;
     if (p.kind < GS2_PC_NONE || p.kind > GS2_PC_AMG_JR || p.outer < 1 || p.inner < 0 ||
         !(p.omega > 0.0) || !(p.gamma > 0.0) || p.direction < 0 || p.direction > 2 ||
-        p.precision < 0 || p.precision > 2 || p.parts < 0 || p.local_sweeps < 0 ||
+        p.precision < 0 || p.precision > 4 || p.parts < 0 || p.local_sweeps < 0 ||
+        (is_sweep_precision(p.precision) &&
+         (p.kind != GS2_PC_GS2 || p.form != GS2_NONCOMPACT || p.parts > 1)) ||
         ((p.parts > 1 || p.local_sweeps > 1) && p.kind != GS2_PC_GS2 && p.kind != GS2_PC_JR &&
          p.kind != GS2_PC_GS) ||
         (p.parts > 1 && p.form == GS2_COMPACT)) {

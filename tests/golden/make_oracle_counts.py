@@ -10,7 +10,8 @@ scale factor that turns a timed sample of oracle Arnoldi steps into solves/s.
     python tests/golden/make_oracle_counts.py --jobs 6 [KEY ...]   # cases in parallel
 
 Keys ending in _fp32 / _fp16 run the GS2 preconditioner's inner sweeps in
-that precision (the oracle's lowprec.c definitions), everything else FP64.
+that precision, _fp32_sweep / _fp16_sweep the whole sweep (the oracle's
+lowprec.c definitions); everything else is FP64.
 """
 import os
 import sys
@@ -67,6 +68,19 @@ CASES = [
     ("convdiff3d_192_gmres30_sgs2_1_1_fp16", lambda: P.convdiff3d(192),
      dict(pc_kind=oracle.PC_GS2, pc_inner=1, pc_direction=oracle.SYMMETRIC,
           pc_precision="fp16")),
+    # the whole sweep in single precision (residual and iterate too)
+    ("poisson3d_128_gmres30_sgs2_1_1_fp32_sweep", lambda: P.poisson3d(128),
+     dict(pc_kind=oracle.PC_GS2, pc_inner=1, pc_direction=oracle.SYMMETRIC,
+          pc_precision="fp32_sweep")),
+    ("poisson3d_128_gmres30_sgs2_1_1_fp16_sweep", lambda: P.poisson3d(128),
+     dict(pc_kind=oracle.PC_GS2, pc_inner=1, pc_direction=oracle.SYMMETRIC,
+          pc_precision="fp16_sweep")),
+    ("convdiff3d_192_gmres30_sgs2_1_1_fp32_sweep", lambda: P.convdiff3d(192),
+     dict(pc_kind=oracle.PC_GS2, pc_inner=1, pc_direction=oracle.SYMMETRIC,
+          pc_precision="fp32_sweep")),
+    ("convdiff3d_192_gmres30_sgs2_1_1_fp16_sweep", lambda: P.convdiff3d(192),
+     dict(pc_kind=oracle.PC_GS2, pc_inner=1, pc_direction=oracle.SYMMETRIC,
+          pc_precision="fp16_sweep")),
     # compact GS2 of Eq. (9) as the GMRES preconditioner; CG (tol 1e-8) with
     # SGS2(1,1) and with the AMG V-cycle
     ("poisson3d_128_gmres30_compact_sgs2_1_2", lambda: P.poisson3d(128),

@@ -349,14 +349,15 @@ LOWPREC_TOL = 1e-6
 
 
 @pytest.mark.parametrize("name", list(MATS))
-@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+@pytest.mark.parametrize("prec", ["fp32", "fp16", "fp32_sweep", "fp16_sweep"])
 def test_lowprec_sweeps_match_lowprec_oracle(g, name, prec):
-    """FP32 and row-scaled FP16 inner sweeps against the oracle's definition
-    of the same precision (FP64 residual, r-hat rounded to FP32, values in
-    the sweep precision, FP32 accumulation): the two differ only in FP32
-    rounding order (FMA, the order of a row's partial sums), a few units of
-    2^-24 per inner sweep, so 1e-6 relative per vector; every kernel path,
-    direction and damping."""
+    """FP32 and row-scaled FP16 inner sweeps (FP64 residual, r-hat rounded to
+    FP32, values in the sweep precision, FP32 accumulation), and the whole
+    sweep in single precision (FP32 residual on the prescaled off-diagonal
+    values and FP32 iterate as well), against the oracle's definition of the
+    same precision: the two differ only in FP32 rounding order (FMA, the
+    order of a row's partial sums), a few units of 2^-24 per sweep, so 1e-6
+    relative per vector; every kernel path, direction and damping."""
     A = MATS[name]
     b, x0 = rhs_and_x0(A, 11)
     h = g.gs2_setup(A, precisions=(prec,))
@@ -370,7 +371,7 @@ def test_lowprec_sweeps_match_lowprec_oracle(g, name, prec):
             assert rel(host(x), ref) <= LOWPREC_TOL, (d, outer, inner, omega, gamma)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+@pytest.mark.parametrize("prec", ["fp32", "fp16", "fp32_sweep", "fp16_sweep"])
 def test_lowprec_preconditioner_keeps_convergence(g, prec):
     """Sec. 10: the single-precision preconditioner keeps the GMRES
     iteration count (6,656 = 6,656 in the paper's table)."""
@@ -382,7 +383,12 @@ def test_lowprec_preconditioner_keeps_convergence(g, prec):
     ilo = g.gmres_solve(h, dev(pr.b), x, 30, 1e-8, 5000,
                         g.params("gs2", 1, 1, direction="symmetric", precision=prec))
     assert ilo.status == 0 and ilo.true_relres <= 1e-8
-    assert abs(ilo.iters - i64.iters) <= (1 if prec == "fp32" else 3), (ilo.iters, i64.iters)
+    assert abs(ilo.iters - i64.iters) <= (1 if prec.startswith("fp32") else 3), \
+        (ilo.iters, i64.iters)
+    # and the oracle's count for the same precision
+    _, oi = oracle.gmres(pr.A, pr.b, restart=30, tol=1e-8, max_iters=5000,
+                         pc_kind=oracle.PC_GS2, pc_direction=oracle.SYMMETRIC, pc_precision=prec)
+    assert abs(ilo.iters - oi.iters) <= 1, (ilo.iters, oi.iters)
 
 
 # ---------------------------------------------------------------------------

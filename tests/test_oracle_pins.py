@@ -955,3 +955,73 @@ def test_lowprec_gmres_keeps_the_iteration_count():
         assert i.status == 0 and abs(i.iters - i64.iters) <= slack, (prec, i, i64)
         r = np.linalg.norm(pr.b - oracle.spmv(pr.A, x)) / np.linalg.norm(pr.b)
         assert r <= 1e-8
+
+
+# ---------------------------------------------------------------------------
+# Whole-sweep single precision (Sec. 10: the outer GS iteration in single
+# precision as well): residual, inner sweeps and iterate in FP32
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["fp32_sweep", "fp16_sweep"])
+def test_sweep_precision_exact_when_every_value_is_representable(prec):
+    """Dyadic data whose every intermediate (FP32 residual from the
+    prescaled off-diagonal values, inner sweeps, FP32 iterate) fits in 24
+    bits: the single-precision sweep performs the FP64 sweep's arithmetic
+    exactly and must equal it bitwise; a dropped x or D^{-1}b term, a wrong
+    sign, a wrong triangle or scale breaks the equality."""
+    A, n = dyadic_nonsym_csr()
+    rng = np.random.default_rng(8)
+    b = rng.integers(-32, 33, n) / 16.0
+    x0 = rng.integers(-64, 65, n) / 64.0
+    for kw in (dict(outer=1, inner=2, omega=1.0, gamma=1.0, direction=oracle.BACKWARD),
+               dict(outer=1, inner=1, omega=1.0, gamma=1.0, direction=oracle.SYMMETRIC),
+               dict(outer=1, inner=0, omega=0.5, gamma=1.0, direction=oracle.FORWARD),
+               dict(outer=2, inner=0, omega=1.0, gamma=1.0, direction=oracle.SYMMETRIC)):
+        ref = oracle.gs2(A, b, x0, **kw)
+        got = oracle.gs2(A, b, x0, precision=prec, **kw)
+        assert np.array_equal(got, ref), kw
+
+
+def test_sweep_precision_error_within_the_value_precision():
+    """Non-dyadic data: the whole single-precision sweep differs from FP64
+    by a few units of 2^-24 (FP32 values) or 2^-11 (FP16 values), and does
+    differ."""
+    A = tiny_nonsym(n=60, seed=12)
+    rng = np.random.default_rng(2)
+    b, x0 = rng.uniform(-1, 1, 60), rng.uniform(-1, 1, 60)
+    for d in (oracle.FORWARD, oracle.SYMMETRIC):
+        ref = oracle.gs2(A, b, x0, 1, 2, 0.9, 0.8, d)
+        dx = np.linalg.norm(ref - x0)
+        e32 = np.linalg.norm(oracle.gs2(A, b, x0, 1, 2, 0.9, 0.8, d, precision="fp32_sweep")
+                             - ref)
+        e16 = np.linalg.norm(oracle.gs2(A, b, x0, 1, 2, 0.9, 0.8, d, precision="fp16_sweep")
+                             - ref)
+        assert 1e-10 * dx < e32 < 40 * 2.0 ** -24 * dx
+        assert 40 * 2.0 ** -24 * dx < e16 < 40 * 2.0 ** -11 * dx
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_sweep_precision_from_zero_equals_inner_only_form(prec):
+    """One half sweep from x = 0 with omega = 1: the residual is b in both
+    forms, the inner sweeps are the same FP32 ones, and x = 1 * g is exact in
+    FP32 and FP64 alike, so the whole-sweep form equals the inner-only form
+    of the same value precision bitwise."""
+    pr = P.poisson2d(20)
+    for d in (oracle.FORWARD, oracle.BACKWARD):
+        a = oracle.gs2(pr.A, pr.b, np.zeros(pr.n), 1, 2, 1.0, 0.7, d, precision=prec)
+        c = oracle.gs2(pr.A, pr.b, np.zeros(pr.n), 1, 2, 1.0, 0.7, d, precision=prec + "_sweep")
+        assert np.array_equal(a, c)
+
+
+def test_sweep_precision_gmres_keeps_the_iteration_count():
+    """Sec. 10: the single-precision preconditioner keeps the count."""
+    pr = P.poisson2d(48)
+    _, i64 = oracle.gmres(pr.A, pr.b, restart=30, tol=1e-8, max_iters=3000,
+                          pc_kind=oracle.PC_GS2, pc_direction=oracle.SYMMETRIC)
+    for prec, slack in (("fp32_sweep", 1), ("fp16_sweep", 3)):
+        x, i = oracle.gmres(pr.A, pr.b, restart=30, tol=1e-8, max_iters=3000,
+                            pc_kind=oracle.PC_GS2, pc_direction=oracle.SYMMETRIC,
+                            pc_precision=prec)
+        assert i.status == 0 and abs(i.iters - i64.iters) <= slack, (prec, i, i64)
+        r = np.linalg.norm(pr.b - oracle.spmv(pr.A, x)) / np.linalg.norm(pr.b)
+        assert r <= 1e-8
