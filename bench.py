@@ -723,10 +723,12 @@ def small_system(gs2, torch, reps=20):
 def packs(gs2, torch, count=128):
     """Many small systems of the request stream's kinds (2D/3D Poisson and 3D
     convection-diffusion, lognormal coefficients), n log-uniform in
-    [1e3, 3.2e4], GMRES(30) + SGS2(1,1) to 1e-8, three ways: one gmres_solve
-    after another, gs2_batch_solve (one stream per system) and one pack
-    (gs2_pack_gmres: every row kernel covers all systems, per-system Krylov
-    state).  Matrices are set up before the clock starts; each way is timed
+    [1e3, 3.2e4], GMRES(30) + SGS2(1,1) to 1e-8, several ways: one
+    gmres_solve after another, gs2_batch_solve (one stream per system), one
+    pack (gs2_pack_gmres: every row kernel covers all systems, per-system
+    Krylov state; each restart cycle one graph replay) with FP64, FP32 and
+    whole-sweep FP32 preconditioning, and the pack as one cooperative launch
+    (every system's blocks run its whole solve).  Matrices are set up before the clock starts; each way is timed
     once after an untimed run, wall clock around the call(s) with device
     vectors.  The pack's per-system iteration counts are compared with the
     separate solves'."""
@@ -761,11 +763,13 @@ def packs(gs2, torch, count=128):
                             "failed": sum(i.status != 0 for i in bat)}
     for h in hs:
         h.close()
-    pack = gs2.pack_setup([p.A for p in probs], precisions=("fp32",))
+    pack = gs2.pack_setup([p.A for p in probs], precisions=("fp32", "fp32_sweep"))
     b = torch.cat(bs)
     x = torch.zeros(pack.n, dtype=torch.float64, device="cuda")
-    for prec in ("fp64", "fp32"):
-        pcp = gs2.params("gs2", 1, 1, direction="symmetric", precision=prec)
+    for prec in ("fp64", "fp32", "fp32_sweep", "one_launch_fp64"):
+        pack.set_graph_mode(3 if prec.startswith("one_launch") else 0)
+        pcp = gs2.params("gs2", 1, 1, direction="symmetric",
+                         precision=prec.replace("one_launch_", ""))
 
         def run():
             x.zero_()
@@ -778,6 +782,29 @@ def packs(gs2, torch, count=128):
             "iters_max_abs_diff_vs_sequential": int(max(abs(a.iters - q.iters)
                                                         for a, q in zip(infos, seq)))}
     pack.close()
+    # a pack of 32 tiny systems (n in [500, 2000]; ~35K rows in all, about
+    # one row per thread of the co-resident blocks): replayed cycle graphs
+    # against the whole pack in one cooperative launch
+    recipe = P.request_stream(32, rate_hz=1.0, n_lo=5e2, n_hi=2e3, seed=P.SEED_BASE + 500,
+                              build=False)
+    tiny = [P.variable_coefficient_problem(kind, N, seed) for _, kind, N, seed in recipe]
+    tp = gs2.pack_setup([q.A for q in tiny])
+    tb = torch.cat([torch.from_numpy(q.b).cuda() for q in tiny])
+    tx = torch.zeros(tp.n, dtype=torch.float64, device="cuda")
+    pc1 = gs2.params("gs2", 1, 1, direction="symmetric")
+    row = {"systems": len(tiny), "n_total": int(tp.n)}
+    for name, mode in (("graphs", 0), ("one_launch", 3)):
+        tp.set_graph_mode(mode)
+
+        def run():
+            tx.zero_()
+            return gs2.pack_gmres(tp, tb, tx, 30, 1e-8, 4000, pc1)
+        infos, dt = clock(run)
+        row[name] = {"solves_per_s": round(len(tiny) / dt, 1), "ms": round(1000 * dt, 3),
+                     "failed": sum(i.status != 0 for i in infos),
+                     "iters_max": int(max(i.iters for i in infos))}
+    tp.close()
+    res["tiny_pack"] = row
     return res
 
 

@@ -217,6 +217,15 @@ struct gs2_handle {
   unsigned* persist_bar = nullptr;  // grid barrier of the single-launch solver
   double* persist_part = nullptr;   // its partial sums
   bool stall_barrier = false;       // test hook: next one-launch solve's barrier never opens
+  // one-launch solve of a pack: per-system argument table, block -> system
+  // map, barriers, partial sums and results (grown on demand)
+  void* pp_args = nullptr;
+  int* pp_bsys = nullptr;
+  unsigned* pp_bar = nullptr;
+  double* pp_part = nullptr;
+  gs2::KrylovState* pp_st = nullptr;
+  gs2::KrylovState* pp_st_host = nullptr;
+  int pp_cap_sys = 0, pp_cap_blocks = 0;
   cudaStream_t gstream = nullptr;
   cudaEvent_t gev_in = nullptr, gev_out = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -429,6 +438,12 @@ void read_state(gs2_handle* h);
 // to 65,536 rows (16,384 when chosen automatically), m <= 32, no
 // preconditioner, FP64 non-compact GS2 or JR
 bool persistent_eligible(const gs2_handle* h, int m, const gs2_params* p, bool automatic);
+// every system of a pack in one cooperative launch (per-system blocks,
+// barriers and Krylov scalars); eligible like a single system, and when the
+// systems' blocks fit the co-resident limit
+bool pack_persistent_eligible(const gs2_handle* h, int m, const gs2_params* p, bool automatic);
+gs2_status pack_gmres_persistent(gs2_handle* h, const double* b, double* x, int m, double tol,
+                                 int max_iters, const gs2_params* p, gs2_solve_info* infos);
 gs2_status gmres_persistent(gs2_handle* h, const double* b, double* x, int m, double tol,
                             int max_iters, const gs2_params* p, gs2_solve_info* info);
 // preconditioned CG the same way (same eligibility with m = 1)

@@ -995,6 +995,17 @@ void pack_job_free(PackJob* j) { delete j; }
 
 gs2_status pack_gmres_run(gs2_handle* h, const double* b, double* x, int m, double tol,
                           int max_iters, const gs2_params* p, gs2_solve_info* infos) {
+  // every system in one cooperative launch (persist.cu): graph mode 3, or
+  // automatically for packs small enough (pack_persistent_eligible)
+  if (h->graph_mode == 0 && !profiling_active(h) && pack_persistent_eligible(h, m, p, true))
+    return pack_gmres_persistent(h, b, x, m, tol, max_iters, p, infos);
+  if (h->graph_mode == 3) {
+    if (!pack_persistent_eligible(h, m, p, false))
+      GS2_THROW(GS2_ERR_INVALID_ARG,
+                "one launch: systems of at most 65,536 rows, restart <= 32, no, JR or FP64 "
+                "non-compact GS2 preconditioning, and every system a co-resident block");
+    return pack_gmres_persistent(h, b, x, m, tol, max_iters, p, infos);
+  }
   PackRun r;
   r.start(h, b, x, m, tol, max_iters, p);
   while (!r.finished) {

@@ -149,6 +149,7 @@ def test_poll_busy_unknown_and_invalid_requests(lib):
 def _pack_of_one(pr, pc):
     import torch
     pk = gs2.pack_setup([pr.A])
+    pk.set_graph_mode(1)  # the cycle-graph path the server runs packs on
     x = torch.zeros(pr.n, dtype=torch.float64, device="cuda")
     info = gs2.pack_gmres(pk, torch.from_numpy(pr.b).cuda(), x, 30, 1e-8, 4000, pc)[0]
     torch.cuda.synchronize()
