@@ -64,9 +64,9 @@ def parse():
                     help="requests of the served stream")
     ap.add_argument("--serve-rates", default="50,200,1000",
                     help="open-loop Poisson arrival rates (requests/s), comma list")
-    ap.add_argument("--serve-forms", default="fp64,fp32,fp16,fp32_packed",
+    ap.add_argument("--serve-forms", default="fp64,fp32,fp32_sweep,fp16_sweep,fp32_sweep_packed",
                     help="server forms (inner-sweep precision, packing), comma list")
-    ap.add_argument("--serve-sweep-forms", default="fp64,fp32_packed",
+    ap.add_argument("--serve-sweep-forms", default="fp64,fp32_sweep_packed",
                     help="forms that also run the open-loop rate sweep, comma list")
     ap.add_argument("--no-profile", action="store_true",
                     help="do not time kernels with events inside the timed region")
@@ -455,8 +455,11 @@ def run_ours(args):
                       stream=stream.cuda_stream)
     if not args.no_autotune:
         h.autotune()  # tile shapes of A and the triangles (setup time, untimed)
-    shapes = {k: v for k, v in h.stats().items() if k.startswith(("tpr", "rpt", "sell"))}
     pc = gs2.params("gs2", 1, 1, direction="symmetric")
+    if not args.no_autotune:
+        h.autotune_gmres(30, pc)  # solve structure: separate launches or cycle graphs
+    shapes = {k: v for k, v in h.stats().items()
+              if k.startswith(("tpr", "rpt", "sell", "offset", "solve_mode"))}
     with torch.cuda.stream(stream):
         b = torch.from_numpy(pr.b).cuda()
         x = torch.zeros(n, dtype=torch.float64, device="cuda")
@@ -677,9 +680,11 @@ def small_system(gs2, torch, reps=20):
     b = torch.from_numpy(pr.b).cuda()
     x = torch.zeros(pr.n, dtype=torch.float64, device="cuda")
     res = {"workload": "2D 5-point Poisson 64x64, GMRES(30) + GS2(1,1) forward, 1e-8"}
-    for name, mode in (("one_launch", 3), ("graph", 1), ("launches", 2)):
+    for name, mode in (("one_launch", 3), ("graph", 1), ("launches", 2), ("autotuned", 0)):
         h = gs2.gs2_setup(pr.A)
         h.set_graph_mode(mode)
+        if mode == 0:
+            res["autotuned_mode"] = h.autotune_gmres(30, pc)
         for _ in range(3):
             x.zero_()
             info = gs2.gmres_solve(h, b, x, 30, 1e-8, 4000, pc)
@@ -793,7 +798,7 @@ def packs(gs2, torch, count=128):
     tx = torch.zeros(tp.n, dtype=torch.float64, device="cuda")
     pc1 = gs2.params("gs2", 1, 1, direction="symmetric")
     row = {"systems": len(tiny), "n_total": int(tp.n)}
-    for name, mode in (("graphs", 0), ("one_launch", 3)):
+    for name, mode in (("graphs", 1), ("one_launch", 3)):
         tp.set_graph_mode(mode)
 
         def run():

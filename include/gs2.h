@@ -137,6 +137,8 @@ typedef struct {
   int sell_a, sell_tri;           /* 1: A / the triangles run on the sliced-ELL layout */
   double offset_frac_a;           /* share of A's sliced-ELL chunks that store column */
   double offset_frac_tri;         /* offsets instead of columns (stencil rows); D^{-1}L */
+  int solve_mode;                 /* gs2_autotune_gmres's choice (1, 2, 3); 0 = not tuned */
+  int solve_modes_timed;          /* candidates it timed */
 } gs2_handle_stats;
 
 typedef struct gs2_handle gs2_handle;
@@ -193,6 +195,20 @@ gs2_status gs2_autotune(gs2_handle* h);
  * graph carries event nodes around the profiled kernels, and only the steps
  * a cycle ran are counted. */
 gs2_status gs2_set_graph_mode(gs2_handle* h, int mode);
+
+/* Autotune how much of a GMRES(restart) solve with this preconditioner is
+ * fused into one launch -- the fusion depth: every kernel of an Arnoldi
+ * step launched on its own (mode 2), a restart cycle's steps replayed as
+ * one CUDA graph (mode 1), or the whole solve as one cooperative launch
+ * (mode 3, where the solve qualifies) -- by timing one restart cycle of each
+ * candidate on this matrix (the right-hand side is the handle's scratch, the
+ * caller's vectors are not touched).  The fastest becomes the handle's
+ * automatic choice (graph mode 0), cached by matrix class (size to a factor
+ * sqrt(2), mean row length) and preconditioner; *mode_out (may be NULL)
+ * receives it.  Results do not change with the choice beyond rounding (the
+ * one-launch solver reduces in another order). */
+gs2_status gs2_autotune_gmres(gs2_handle* h, int restart, const gs2_params* precond,
+                              int* mode_out);
 
 /* Test hook for the bounded waits of the one-launch solver: the next such
  * solve on this handle starts with a grid barrier that can never open, so

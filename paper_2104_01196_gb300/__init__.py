@@ -72,7 +72,8 @@ class _Stats(ctypes.Structure):
                 ("tpr_a", ctypes.c_int), ("tpr_tri", ctypes.c_int),
                 ("rpt_a", ctypes.c_int), ("rpt_tri", ctypes.c_int), ("colors", ctypes.c_int),
                 ("sell_a", ctypes.c_int), ("sell_tri", ctypes.c_int),
-                ("offset_frac_a", ctypes.c_double), ("offset_frac_tri", ctypes.c_double)]
+                ("offset_frac_a", ctypes.c_double), ("offset_frac_tri", ctypes.c_double),
+                ("solve_mode", ctypes.c_int), ("solve_modes_timed", ctypes.c_int)]
 
 
 class _KStat(ctypes.Structure):
@@ -148,6 +149,7 @@ def load(path: str | None = None):
         "gs2_set_graph_mode": [P, I],
         "gs2_test_stall_barrier": [P],
         "gs2_autotune": [P],
+        "gs2_autotune_gmres": [P, I, ctypes.POINTER(Params), ctypes.POINTER(I)],
         "gs2_profile_read": [P, ctypes.POINTER(_KStat), I, ctypes.POINTER(I)],
         "gs2_profile_reset": [P],
         "gs2_amg_setup": [P, ctypes.POINTER(_AmgCfg)],
@@ -256,6 +258,16 @@ class Handle:
 
     def profile(self, enable: bool):
         _check(load().gs2_profile_enable(self.ptr, 1 if enable else 0))
+
+    def autotune_gmres(self, restart: int = 30, precond: Params | None = None) -> int:
+        """Time one restart cycle per solve structure (separate launches,
+        cycle graphs, one launch) and make the fastest the automatic
+        choice; returns it (gs2_autotune_gmres)."""
+        mode = ctypes.c_int()
+        _check(load().gs2_autotune_gmres(self.ptr, restart,
+                                         ctypes.byref(precond) if precond is not None else None,
+                                         ctypes.byref(mode)))
+        return int(mode.value)
 
     def autotune(self):
         """Pick the fastest tile shape of each matrix (cached by matrix class)."""

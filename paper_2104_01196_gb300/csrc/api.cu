@@ -1198,6 +1198,8 @@ gs2_status gs2_get_stats(const gs2_handle* h, gs2_handle_stats* out) {
       h->A.sell_chunks ? (double)h->A.sell_offset_chunks / h->A.sell_chunks : 0.0;
   out->offset_frac_tri =
       h->L.sell_chunks ? (double)h->L.sell_offset_chunks / h->L.sell_chunks : 0.0;
+  out->solve_mode = h->tuned_mode;
+  out->solve_modes_timed = h->tuned_candidates;
   return GS2_OK;
 }
 
@@ -1504,6 +1506,22 @@ gs2_status gs2_autotune(gs2_handle* h) {
     h->cg_gkey.clear();
   }
   pack_drop_graph(h);
+  return GS2_OK;
+  API_END
+}
+
+gs2_status gs2_autotune_gmres(gs2_handle* h, int restart, const gs2_params* precond,
+                              int* mode_out) {
+  if (!h) return GS2_ERR_INVALID_ARG;
+  API_BEGIN
+  NvtxRange nvtx_("gs2_autotune_gmres");
+  if (restart < 1 || restart > kMaxRestart)
+    GS2_THROW(GS2_ERR_INVALID_ARG, "restart must be in [1, 64]");
+  check_params(precond);
+  if (precond && precond->kind == GS2_PC_GS2) ensure_precision(h, precond->precision);
+  ensure_precond(h, precond);
+  const int mode = h->n ? autotune_gmres(h, restart, precond) : 1;
+  if (mode_out) *mode_out = mode;
   return GS2_OK;
   API_END
 }

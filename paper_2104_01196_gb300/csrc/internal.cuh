@@ -214,6 +214,11 @@ struct gs2_handle {
   // systems): captured on a private stream, replayed there and joined to
   // `stream` with events; re-captured when the cycle's shape changes
   int graph_mode = 0;  // 0: automatic, 1: graphs, 2: separate launches, 3: one launch
+  // gs2_autotune_gmres: the automatic mode's tuned choice for (restart,
+  // preconditioner) tune_key (0 = not tuned: the size rule)
+  int tuned_mode = 0, tuned_candidates = 0;
+  std::vector<double> tuned_key;
+  double *tune_b = nullptr, *tune_x = nullptr;  // its scratch right-hand side and iterate
   unsigned* persist_bar = nullptr;  // grid barrier of the single-launch solver
   double* persist_part = nullptr;   // its partial sums
   bool stall_barrier = false;       // test hook: next one-launch solve's barrier never opens
@@ -438,6 +443,9 @@ void read_state(gs2_handle* h);
 // to 65,536 rows (16,384 when chosen automatically), m <= 32, no
 // preconditioner, FP64 non-compact GS2 or JR
 bool persistent_eligible(const gs2_handle* h, int m, const gs2_params* p, bool automatic);
+// gs2_autotune_gmres: the fastest solve structure (1, 2, 3) for (m, p)
+int autotune_gmres(gs2_handle* h, int m, const gs2_params* p);
+void launch_fill_value(gs2_handle* h, double* y, double v);
 // every system of a pack in one cooperative launch (per-system blocks,
 // barriers and Krylov scalars); eligible like a single system, and when the
 // systems' blocks fit the co-resident limit

@@ -664,8 +664,111 @@ struct GmresRun {
   }
 };
 
+// the key of a tuned solve structure: restart and preconditioner
+static std::vector<double> solve_key(int m, const gs2_params* p) {
+  if (!p || p->kind == GS2_PC_NONE) return {(double)m, -1.0};
+  return {(double)m, (double)p->kind, (double)p->outer, (double)p->inner, p->omega, p->gamma,
+          (double)p->direction, (double)p->precision, (double)p->form, (double)p->parts,
+          (double)p->local_sweeps};
+}
+
+static gs2_status gmres_run_mode(gs2_handle* h, const double* b, double* x, int m, double tol,
+                                 int max_iters, const gs2_params* p, gs2_solve_info* info);
+
 gs2_status gmres_run(gs2_handle* h, const double* b, double* x, int m, double tol,
                      int max_iters, const gs2_params* p, gs2_solve_info* info) {
+  // automatic mode with a structure tuned for this restart and preconditioner
+  // (gs2_autotune_gmres): run that structure
+  if (h->graph_mode == 0 && h->tuned_mode != 0 && !profiling_active(h) &&
+      h->tuned_key == solve_key(m, p)) {
+    h->graph_mode = h->tuned_mode;
+    gs2_status st;
+    try {
+      st = gmres_run_mode(h, b, x, m, tol, max_iters, p, info);
+    } catch (...) {
+      h->graph_mode = 0;
+      throw;
+    }
+    h->graph_mode = 0;
+    return st;
+  }
+  return gmres_run_mode(h, b, x, m, tol, max_iters, p, info);
+}
+
+// Time one restart cycle per candidate structure (mode 2: separate
+// launches; 1: cycle graphs; 3: one launch, where eligible) on scratch
+// vectors (b = 1, x = 0; tolerance 0 so that every cycle runs all m steps),
+// best of two after one untimed run; the fastest becomes the automatic
+// choice for (m, p).  Cached by matrix class and (m, p).
+static std::mutex g_solve_tune_mu;
+static std::map<std::vector<double>, int> g_solve_tune;
+
+int autotune_gmres(gs2_handle* h, int m, const gs2_params* p) {
+  std::vector<double> key = solve_key(m, p);
+  std::vector<double> ckey = key;
+  ckey.push_back(std::lround(2.0 * std::log2((double)std::max<int64_t>(h->n, 1))));
+  ckey.push_back(std::lround(4.0 * h->A.mean_row));
+  {
+    std::lock_guard<std::mutex> g(g_solve_tune_mu);
+    auto it = g_solve_tune.find(ckey);
+    if (it != g_solve_tune.end()) {
+      h->tuned_mode = it->second;
+      h->tuned_key = key;
+      return it->second;
+    }
+  }
+  if (!h->tune_b) {
+    const size_t n = std::max<int64_t>(h->n, 1);
+    h->tune_b = (double*)h->dalloc(sizeof(double) * n);
+    h->tune_x = (double*)h->dalloc(sizeof(double) * n);
+  }
+  launch_fill_value(h, h->tune_b, 1.0);
+  std::vector<int> cand = {2, 1};
+  if (persistent_eligible(h, m, p, false)) cand.push_back(3);
+  const int saved = h->graph_mode;
+  cudaEvent_t e0, e1;
+  GS2_CUDA(cudaEventCreate(&e0));
+  GS2_CUDA(cudaEventCreate(&e1));
+  int best = 1;
+  float best_ms = 0.f;
+  try {
+    for (int mode : cand) {
+      h->graph_mode = mode;
+      float ms = 0.f;
+      for (int rep = 0; rep < 3; ++rep) {
+        GS2_CUDA(cudaMemsetAsync(h->tune_x, 0, sizeof(double) * h->n, h->stream));
+        GS2_CUDA(cudaEventRecord(e0, h->stream));
+        gmres_run_mode(h, h->tune_b, h->tune_x, m, 0.0, m, p, nullptr);
+        GS2_CUDA(cudaEventRecord(e1, h->stream));
+        GS2_CUDA(cudaEventSynchronize(e1));
+        float t = 0.f;
+        GS2_CUDA(cudaEventElapsedTime(&t, e0, e1));
+        if (rep == 1 || (rep == 2 && t < ms)) ms = t;
+      }
+      if (mode == cand.front() || ms < best_ms) {
+        best = mode;
+        best_ms = ms;
+      }
+    }
+  } catch (...) {
+    h->graph_mode = saved;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    throw;
+  }
+  h->graph_mode = saved;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->tuned_mode = best;
+  h->tuned_candidates = (int)cand.size();
+  h->tuned_key = key;
+  std::lock_guard<std::mutex> g(g_solve_tune_mu);
+  g_solve_tune[ckey] = best;
+  return best;
+}
+
+static gs2_status gmres_run_mode(gs2_handle* h, const double* b, double* x, int m, double tol,
+                                 int max_iters, const gs2_params* p, gs2_solve_info* info) {
   // small systems: the whole solve in one launch (automatic unless per-kernel
   // profiling is on; graph mode 3 asks for it)
   const bool forced = h->graph_mode == 3;

@@ -24,6 +24,8 @@ static void launch_fill(gs2_handle* h, double* y, double v, const int* skip) {
   GS2_LAUNCH_CHECK();
 }
 
+void launch_fill_value(gs2_handle* h, double* y, double v) { launch_fill(h, y, v, nullptr); }
+
 static void launch_copy_skip(gs2_handle* h, double* y, const double* x, const int* skip) {
   KernelTimer tm(h, "copy", 16.0 * h->n);
   k_copy<<<vec_blocks(h, h->n), kVecThreads, 0, h->stream>>>((int)h->n, y, x, skip);

@@ -322,3 +322,34 @@ def test_one_launch_cg_statuses_and_selection(g):
     with pytest.raises(g.GS2Error):
         g.cg_solve(h, b, dev(np.zeros(pr.n)), 1e-8, 50,
                    g.params("gs2", 1, 1, direction="symmetric", precision="fp32"))
+
+
+def test_autotune_gmres_picks_a_structure_and_keeps_the_results(g):
+    """gs2_autotune_gmres times one restart cycle per solve structure
+    (separate launches, cycle graphs, one launch where eligible), makes the
+    fastest the automatic choice for that restart and preconditioner, reports
+    it in the handle's stats, and the tuned automatic solve keeps the
+    oracle's count; a different preconditioner falls back to the size rule."""
+    prm = g.params("gs2", 1, 1, direction="symmetric")
+    for pr, candidates in ((P.poisson2d(64), 3), (P.poisson3d(40), 3)):
+        h = g.gs2_setup(pr.A)
+        mode = h.autotune_gmres(30, prm)
+        st = h.stats()
+        assert mode in (1, 2, 3) and st["solve_mode"] == mode
+        assert st["solve_modes_timed"] == candidates
+        x = dev(np.zeros(pr.n))
+        info = g.gmres_solve(h, dev(pr.b), x, 30, 1e-8, 3000, prm)
+        _, oinfo = oracle.gmres(pr.A, pr.b, restart=30, tol=1e-8, max_iters=3000,
+                                pc_kind=oracle.PC_GS2, pc_direction=oracle.SYMMETRIC)
+        assert info.status == 0 and abs(info.iters - oinfo.iters) <= 1
+        r = np.linalg.norm(pr.b - oracle.spmv(pr.A, host(x))) / np.linalg.norm(pr.b)
+        assert r <= 1e-8
+        # another preconditioner: untuned, the size rule applies
+        info2 = g.gmres_solve(h, dev(pr.b), dev(np.zeros(pr.n)), 30, 1e-8, 3000,
+                              g.params("jr", 3, omega=0.8))
+        assert info2.status == 0
+    # lower-precision sweeps: the one-launch solver does not take them
+    pr = P.poisson2d(40)
+    h = g.gs2_setup(pr.A, precisions=("fp32",))
+    mode = h.autotune_gmres(30, g.params("gs2", 1, 1, precision="fp32"))
+    assert mode in (1, 2) and h.stats()["solve_modes_timed"] == 2
