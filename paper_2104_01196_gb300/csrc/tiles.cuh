@@ -320,7 +320,53 @@ __device__ __forceinline__ float stream_val<__half>(const __half* p) {
 // Offset chunks (stencil rows) store no columns: the warp reads the chunk's
 // offset list (one broadcast load per slot) and forms column row + o, so a
 // slot moves only its value; the gathers of consecutive rows are contiguous.
-template <typename VT, class Epi, bool LONG>
+
+// Two consecutive offset chunks of the same short width (<= 8 slots) at once,
+// one row of each per lane: with FP32 / FP16 values a single chunk leaves
+// too few bytes in flight per warp (the inner sweeps were latency-bound, 20
+// long-scoreboard stalls per issue at 92% of the maximum warps), so both
+// chunks' slots and gathers are issued before their FMAs.  Rows are reduced
+// in the same slot order as one chunk at a time.  False (nothing done) when
+// the pair does not qualify.
+template <typename VT, class Epi>
+__device__ __forceinline__ bool sell_pair(int n, int c, const int* __restrict__ cptr,
+                                          const VT* __restrict__ va, const Epi& epi,
+                                          const int* __restrict__ live,
+                                          const int* __restrict__ coff,
+                                          const int* __restrict__ offs, int cmax, int lane) {
+  using AT = typename ValTraits<VT>::AT;
+  const int ob0 = __ldg(coff + c), ob1 = __ldg(coff + c + 1);
+  if (ob0 < 0 || ob1 < 0) return false;
+  const int b0 = cptr[c], b1 = cptr[c + 1], b2 = cptr[c + 2];
+  const int L = (b1 - b0) >> 5;
+  if (L > 8 || ((b2 - b1) >> 5) != L) return false;
+  if (live && (live[c] == 0 || live[c + 1] == 0)) return false;
+  const int r0 = c * 32 + lane, r1 = r0 + 32;
+  typename Epi::Pre p0{}, p1{};
+  if (r0 < n) p0 = epi.pre(r0);
+  if (r1 < n) p1 = epi.pre(r1);
+  const VT* v0 = va + b0 + lane;
+  const VT* v1 = va + b1 + lane;
+  const int* o0 = offs + ob0;
+  const int* o1 = offs + ob1;
+  AT s0 = AT(0), s1 = AT(0);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    if (k < L) {
+      const int ca = min(max(r0 + __ldg(o0 + k), 0), cmax);
+      const int cb = min(max(r1 + __ldg(o1 + k), 0), cmax);
+      const AT a = stream_val<VT>(v0 + 32 * k), b = stream_val<VT>(v1 + 32 * k);
+      const AT xa = (AT)epi.gather(ca), xb = (AT)epi.gather(cb);
+      s0 = fma(a, xa, s0);
+      s1 = fma(b, xb, s1);
+    }
+  }
+  if (r0 < n) epi.finish(r0, s0, p0);
+  if (r1 < n) epi.finish(r1, s1, p1);
+  return true;
+}
+
+template <typename VT, class Epi, bool LONG, bool PAIR>
 __global__ void __launch_bounds__(kRowThreads)
 k_sell(int n, int nchunks, const int* __restrict__ cptr, const int* __restrict__ ci,
        const VT* __restrict__ va, Epi epi, const int* skip, const int* __restrict__ live,
@@ -331,7 +377,13 @@ k_sell(int n, int nchunks, const int* __restrict__ cptr, const int* __restrict__
   const int lane = threadIdx.x & 31;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   const int cmax = ncols - 1;
-  for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks; c += nw) {
+  // PAIR: a warp takes two chunks per iteration (sell_pair)
+  constexpr int STEP = PAIR ? 2 : 1;
+  for (int cw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; cw * STEP < nchunks; cw += nw) {
+  if (STEP == 2 && cw * 2 + 1 < nchunks &&
+      sell_pair<VT, Epi>(n, cw * 2, cptr, va, epi, live, coff, offs, cmax, lane))
+    continue;
+  for (int c = cw * STEP; c < min(cw * STEP + STEP, nchunks); ++c) {
     // a chunk whose rows belong only to finished systems of a pack
     if (live && live[c] == 0) continue;
     const int row = c * 32 + lane;
@@ -439,6 +491,7 @@ k_sell(int n, int nchunks, const int* __restrict__ cptr, const int* __restrict__
     }
     if (row < n) epi.finish(row, s, pv);
   }
+  }
 }
 
 inline const double* sell_values(const DevCsr& M, const double*) { return M.sell_va; }
@@ -483,10 +536,24 @@ inline void launch_sell(gs2_handle* h, const DevCsr& M, const VT* sv, const Epi&
   // mean rows longer than 24 entries take the software-pipelined form
   // (Q1 elasticity, 77 per row: GMRES+SGS2(1,2) 90.3 -> 81.8 ms per 120
   // iterations; on 7-entry rows it was 2% slower)
-  auto fn = M.mean_row > kShortRowMean ? k_sell<VT, Epi, true> : k_sell<VT, Epi, false>;
+  // FP32 / FP16 values on rows of 5-8 entries (the whole-sweep residual's
+  // off-diagonal matrix): two chunks per warp iteration (FP32 residual on
+  // the 192^3 convection-diffusion matrix 59 -> 51 us).  Rows of 3 entries
+  // (the inner sweeps' triangles) lost occupancy to it (51 -> 57 us), and
+  // FP64 rows are bound by the FP64 pipe, so they keep one chunk.
+  bool pair = false;
+  auto fn = M.mean_row > kShortRowMean ? k_sell<VT, Epi, true, false> : k_sell<VT, Epi, false, false>;
+  if constexpr (sizeof(VT) < sizeof(double)) {
+    if (M.mean_row >= 4.5 && M.mean_row <= 8.0) {
+      pair = true;
+      fn = k_sell<VT, Epi, false, true>;
+    }
+  }
   const int per_sm = blocks_per_sm((const void*)fn, 0);
   const int warps = kRowThreads / 32;
-  const int grid = std::max(1, std::min((M.sell_chunks + warps - 1) / warps, per_sm * h->nsm));
+  // (FP32 / FP16 values: a warp takes chunks in pairs)
+  const int tasks = pair ? (M.sell_chunks + 1) / 2 : M.sell_chunks;
+  const int grid = std::max(1, std::min((tasks + warps - 1) / warps, per_sm * h->nsm));
   // chunk liveness applies to the matrices whose rows are the handle's rows
   const int* live =
       (h->row_live && (&M == &h->A || &M == &h->L || &M == &h->U)) ? h->row_live : nullptr;
