@@ -699,7 +699,8 @@ def small_system(gs2, torch, reps=20):
         e1.synchronize()
         ms = e0.elapsed_time(e1) / reps
         res[name] = {"ms_per_solve": round(ms, 3), "solves_per_s": round(1000.0 / ms, 1),
-                     "iters": info.iters, "true_relres": info.true_relres}
+                     "iters": info.iters, "oracle_iters": stored_count("poisson2d_64_gmres30_gs2_1_1"),
+                     "true_relres": info.true_relres}
         h.close()
     # CG with SGS2(1,1) on the same SPD system, one launch vs graphs of 16 iterations
     pcs = gs2.params("gs2", 1, 1, direction="symmetric")
@@ -720,7 +721,8 @@ def small_system(gs2, torch, reps=20):
         e1.synchronize()
         ms = e0.elapsed_time(e1) / reps
         res[name] = {"ms_per_solve": round(ms, 3), "solves_per_s": round(1000.0 / ms, 1),
-                     "iters": info.iters, "true_relres": info.true_relres}
+                     "iters": info.iters, "oracle_iters": stored_count("poisson2d_64_cg_sgs2_1_1"),
+                     "true_relres": info.true_relres}
         h.close()
     return res
 
@@ -1126,7 +1128,11 @@ def hybrid(gs2, torch, pr, stream, b):
                 info = gs2.gmres_solve(h, b, x, 30, 1e-8, 5000, p)
                 e1.record(stream)
                 e1.synchronize()
+                okey = {"jr_4_1_global": "jr_4_1", "jr_1_4_local": "jr_1_4",
+                        "sgs2_1_1": "sgs2_1_1", "sgs_levels": "sgs"}[name]
                 row[name] = {"status": info.status, "iters": info.iters,
+                             "oracle_iters": stored_count(
+                                 f"poisson3d_128_gmres30_hybrid_{okey}_P{parts}"),
                              "ms": round(e0.elapsed_time(e1), 2)}
             res[f"P={parts}"] = row
     h.close()

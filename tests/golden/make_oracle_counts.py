@@ -91,6 +91,36 @@ CASES = [
      dict(cg=True, amg=True, kind=oracle.PC_GS2, inner=1, direction=oracle.SYMMETRIC)),
 ]
 
+# the hybrid (block-Jacobi) preconditioners of Sec. 3 on the 128^3 Laplacian,
+# P contiguous row blocks: global JR(4,1), local JR(1,4), hybrid SGS2(1,1)
+# and hybrid exact SGS
+for _P in (1, 8, 64, 512):
+    CASES += [
+        (f"poisson3d_128_gmres30_hybrid_jr_4_1_P{_P}", lambda: P.poisson3d(128),
+         dict(pc_kind=oracle.PC_HYBRID_JR, pc_outer=4, pc_parts=_P, pc_local=1)),
+        (f"poisson3d_128_gmres30_hybrid_jr_1_4_P{_P}", lambda: P.poisson3d(128),
+         dict(pc_kind=oracle.PC_HYBRID_JR, pc_outer=1, pc_parts=_P, pc_local=4)),
+        (f"poisson3d_128_gmres30_hybrid_sgs2_1_1_P{_P}", lambda: P.poisson3d(128),
+         dict(pc_kind=oracle.PC_HYBRID_GS2, pc_inner=1, pc_direction=oracle.SYMMETRIC,
+              pc_parts=_P)),
+        (f"poisson3d_128_gmres30_hybrid_sgs_P{_P}", lambda: P.poisson3d(128),
+         dict(pc_kind=oracle.PC_HYBRID_GS, pc_direction=oracle.SYMMETRIC, pc_parts=_P)),
+    ]
+CASES.append(("poisson2d_64_cg_sgs2_1_1", lambda: P.poisson2d(64),
+              dict(cg=True, pc_kind=oracle.PC_GS2, pc_inner=1,
+                   pc_direction=oracle.SYMMETRIC)))
+
+# One-ulp ensembles: the same solve with b multiplied entrywise by
+# (1 + 2^-52 e), e ~ N(0, 1) from numpy's seeded generator (seed = member),
+# where the count is sensitive to rounding (FP32 preconditioning of the 64^3
+# elasticity problem): keys <case>_ens<member>.
+ENSEMBLE_MEMBERS = 8
+for _base in ("elasticity3d_64_gmres30_sgs2_1_2_w0.8_fp32",
+              "elasticity3d_64_gmres30_sgs2_1_3_w0.9_fp32"):
+    _, _mk, _pc = next(c for c in CASES if c[0] == _base)
+    for _m in range(1, ENSEMBLE_MEMBERS + 1):
+        CASES.append((f"{_base}_ens{_m}", _mk, dict(_pc, perturb=_m)))
+
 
 def run_case(key):
     """One case through the oracle: its line of oracle_counts.txt."""
@@ -98,7 +128,11 @@ def run_case(key):
     _, mk, pc = next(c for c in CASES if c[0] == key)
     pr = mk()
     t0 = time.time()
-    kw = {k: v for k, v in pc.items() if k not in ("amg", "cg")}
+    kw = {k: v for k, v in pc.items() if k not in ("amg", "cg", "perturb")}
+    if pc.get("perturb"):
+        import numpy as np
+        rng = np.random.default_rng(pc["perturb"])
+        pr.b = pr.b * (1.0 + 2.0 ** -52 * rng.standard_normal(pr.n))
     if pc.get("amg"):
         # smoothed-aggregation hierarchy with the default settings
         # (theta 0.25, 10 levels, coarsest <= 64 rows), one V-cycle
