@@ -603,6 +603,9 @@ k_level(const int* __restrict__ rows, int r0, int r1, const int* __restrict__ rp
         const int* __restrict__ ci, const double* __restrict__ va,
         const double* __restrict__ rhat, double* g, double* x, double omega,
         const int* skip) {
+  // launched with programmatic dependent launch: the next level's launch
+  // overlaps this one; its rows wait here for the previous level's results
+  pdl_wait();
   if (skip && *skip) return;
   const int q = threadIdx.x / K, l = threadIdx.x % K;
   constexpr int G = kRowThreads / K;
@@ -632,11 +635,11 @@ void launch_level(gs2_handle* h, const DevCsr& T, const int* rows, int r0, int r
   const int G = kRowThreads / K;
   const int grid = std::max(1, std::min((cnt + G - 1) / G, h->nsm * 8));
   if (K == 8)
-    k_level<8><<<grid, kRowThreads, 0, h->stream>>>(rows, r0, r1, T.rp, T.ci, T.va, rhat, g,
-                                                    x, omega, skip);
+    launch_pdl(k_level<8>, grid, kRowThreads, 0, h->stream, rows, r0, r1, (const int*)T.rp,
+               (const int*)T.ci, (const double*)T.va, rhat, g, x, omega, skip);
   else
-    k_level<1><<<grid, kRowThreads, 0, h->stream>>>(rows, r0, r1, T.rp, T.ci, T.va, rhat, g,
-                                                    x, omega, skip);
+    launch_pdl(k_level<1>, grid, kRowThreads, 0, h->stream, rows, r0, r1, (const int*)T.rp,
+               (const int*)T.ci, (const double*)T.va, rhat, g, x, omega, skip);
   GS2_LAUNCH_CHECK();
 }
 
