@@ -5,10 +5,11 @@ Q1 hexahedral elasticity (SPD, ~81 entries per row: the K-lane row tiles at
 one-lane-per-row sliced-ELL path) with SGS2 in FP64 and with FP32 triangle
 values; 3D first-order upwind
 convection-diffusion (nonsymmetric) with GS2 inner sweeps in FP64, FP32 and
-FP16 with a per-row scale, outer residual and Arnoldi in FP64.  FP64 sweeps
-match the oracle to 1e-12; lower-precision results are compared with the
-FP64 oracle and the error bound each precision implies is written in the
-test (FP32 values: ~1e-7 relative per entry; FP16 scaled values: ~5e-4).
+FP16 with a per-row scale, and with the whole sweep in FP32 / FP16; Arnoldi
+in FP64.  FP64 sweeps match the oracle to 1e-12; lower-precision results
+match the oracle's definition of the same precision to 1e-6 and the FP64
+oracle within the bound each value precision implies (FP32 values: ~1e-7
+relative per entry; FP16 scaled values: ~5e-4).
 """
 import numpy as np
 import pytest
@@ -104,28 +105,40 @@ def test_elasticity_stationary_jr_diverges_at_omega_one(g, ela):
     assert res(x) < r0
 
 
+LOWP = ("fp32", "fp16", "fp32_sweep", "fp16_sweep")
+
+
 @pytest.mark.parametrize("direction", [0, 1, 2])
 def test_convdiff_sweeps_all_precisions(g, cd, direction):
+    """Every precision against the oracle's definition of the same precision
+    (1e-6: FP32 rounding order only), and against the FP64 oracle within the
+    value precision's bound."""
     x0 = P.uniform_pm1(9, cd.n)
     ref = oracle.gs2(cd.A, cd.b, x0, 1, 2, 1.0, 1.0, direction)
-    h = g.gs2_setup(cd.A, precisions=("fp32", "fp16"))
+    h = g.gs2_setup(cd.A, precisions=LOWP)
     errs = {}
-    for prec in ("fp64", "fp32", "fp16"):
+    for prec in ("fp64",) + LOWP:
         x = dev(x0)
         g.gs2_apply_ex(h, dev(cd.b), x, g.params("gs2", 1, 2, direction=direction,
                                                  precision=prec))
         errs[prec] = rel(host(x), ref)
+        if prec != "fp64":
+            lp = oracle.gs2(cd.A, cd.b, x0, 1, 2, 1.0, 1.0, direction, precision=prec)
+            assert rel(host(x), lp) <= 1e-6, prec
     assert errs["fp64"] <= TOL
-    assert errs["fp32"] <= 2e-6
-    assert errs["fp16"] <= 2e-3
+    assert errs["fp32"] <= 2e-6 and errs["fp32_sweep"] <= 2e-6
+    assert errs["fp16"] <= 2e-3 and errs["fp16_sweep"] <= 2e-3
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16", "fp32_sweep", "fp16_sweep"])
 def test_convdiff_gmres_error_vs_fp64_oracle(g, cd, prec):
-    """GS2(1,1) inner sweeps in each precision, FP64 outer: the true residual
-    meets 1e-8 and the solution is within the FP64 oracle's own error."""
-    xo, oinfo = oracle.gmres(cd.A, cd.b, restart=30, tol=1e-8, max_iters=5000,
-                             pc_kind=oracle.PC_GS2, pc_inner=1)
+    """GS2(1,1) in each precision, FP64 Arnoldi: the true residual meets
+    1e-8, the solution is within the FP64 oracle's own error, and the count
+    is the oracle's for the same precision within +-1."""
+    xo, _ = oracle.gmres(cd.A, cd.b, restart=30, tol=1e-8, max_iters=5000,
+                         pc_kind=oracle.PC_GS2, pc_inner=1)
+    _, oinfo = oracle.gmres(cd.A, cd.b, restart=30, tol=1e-8, max_iters=5000,
+                            pc_kind=oracle.PC_GS2, pc_inner=1, pc_precision=prec)
     h = g.gs2_setup(cd.A, precisions=(prec,) if prec != "fp64" else ())
     x = dev(np.zeros(cd.n))
     info = g.gmres_solve(h, dev(cd.b), x, 30, 1e-8, 5000,
@@ -134,23 +147,32 @@ def test_convdiff_gmres_error_vs_fp64_oracle(g, cd, prec):
     xg = host(x)
     err_ora = rel(xo, cd.x_true)
     assert rel(xg, cd.x_true) <= 10 * err_ora + 1e-12
-    if prec == "fp64":
-        assert abs(info.iters - oinfo.iters) <= 1
-    else:
-        assert abs(info.iters - oinfo.iters) <= max(2, oinfo.iters // 10)
+    assert abs(info.iters - oinfo.iters) <= 1, (info.iters, oinfo.iters)
 
 
 # ---------------------------------------------------------------------------
 # full-size configurations
 # ---------------------------------------------------------------------------
 
-def _oracle_count(key):
+def _oracle_lines():
     import os
     path = os.path.join(os.path.dirname(__file__), "golden", "oracle_counts.txt")
+    out = {}
     for line in open(path):
-        if line.split() and line.split()[0] == key:
-            return int(dict(x.split("=") for x in line.split()[1:])["iters"])
-    raise KeyError(key)
+        if line.split() and not line.startswith("#"):
+            out[line.split()[0]] = int(dict(x.split("=") for x in line.split()[1:])["iters"])
+    return out
+
+
+def _oracle_count(key):
+    return _oracle_lines()[key]
+
+
+def _oracle_ensemble(key):
+    """The stored counts of the unperturbed solve and of its one-ulp
+    ensemble members (keys <key>_ens<m>)."""
+    lines = _oracle_lines()
+    return [lines[key]] + [v for k, v in lines.items() if k.startswith(key + "_ens")]
 
 
 @pytest.fixture(scope="module")
@@ -179,37 +201,48 @@ def test_elasticity_full_size_sweeps_and_solves(g, ela64):
         g.gs2_apply_ex(h, dev(pr.b), x, g.params("gs2", 1, 1, omega=0.8,
                                                   direction="symmetric", precision=prec))
         assert rel(host(x), ref) <= bound, prec
-    want = _oracle_count("elasticity3d_64_gmres30_sgs2_1_2_w0.8")
-    for prec in ("fp64", "fp32"):
-        x = dev(np.zeros(pr.n))
-        info = g.gmres_solve(h, dev(pr.b), x, 30, 1e-8, 5000,
-                             g.params("gs2", 1, 2, omega=0.8, direction="symmetric",
-                                      precision=prec))
-        assert info.status == 0, prec
-        # FP32 values change the preconditioner itself; over ~1000 restarted
-        # iterations its count moves by several percent with rounding order
-        slack = 1 if prec == "fp64" else max(2, want // 10)
-        assert abs(info.iters - want) <= slack, (prec, info.iters, want)
-        r = np.linalg.norm(pr.b - oracle.spmv(pr.A, host(x))) / np.linalg.norm(pr.b)
-        assert r <= 1e-8 and abs(r - info.true_relres) <= 1e-10, prec
+    for stem, nj, om in (("sgs2_1_2_w0.8", 2, 0.8), ("sgs2_1_3_w0.9", 3, 0.9)):
+        for prec in ("fp64", "fp32"):
+            x = dev(np.zeros(pr.n))
+            info = g.gmres_solve(h, dev(pr.b), x, 30, 1e-8, 5000,
+                                 g.params("gs2", 1, nj, omega=om, direction="symmetric",
+                                          precision=prec))
+            assert info.status == 0, (stem, prec)
+            key = f"elasticity3d_64_gmres30_{stem}"
+            if prec == "fp64":
+                # stable under one-ulp changes of b: the oracle's count +-1
+                want = _oracle_count(key)
+                assert abs(info.iters - want) <= 1, (stem, prec, info.iters, want)
+            else:
+                # an FP32 preconditioner makes the count of this 38-cycle
+                # solve sensitive to rounding: the oracle's own FP32 count
+                # moves with one-ulp changes of b (the stored ensemble), so
+                # the GPU's must lie in that ensemble's range widened by 15%
+                ens = _oracle_ensemble(key + "_fp32")
+                assert len(ens) >= 8 and max(ens) - min(ens) > 2, ens
+                lo, hi = 0.85 * min(ens), 1.15 * max(ens)
+                assert lo <= info.iters <= hi, (stem, info.iters, ens)
+            r = np.linalg.norm(pr.b - oracle.spmv(pr.A, host(x))) / np.linalg.norm(pr.b)
+            assert r <= 1e-8 and abs(r - info.true_relres) <= 1e-10, (stem, prec)
 
 
 def test_convdiff_full_size_gmres_all_precisions(g, cd192):
     """192^3 upwind convection-diffusion (n = 7,077,888, nonsymmetric),
-    GMRES(30) + SGS2(1,1) to 1e-8 with FP64, FP32 and FP16-row-scaled inner
-    sweeps (residual and Arnoldi FP64): FP64 within +-1 of the oracle's
-    stored count, the others within 10%; every true residual recomputed by
-    the oracle's SpMV, and the error against the generating x_true."""
+    GMRES(30) + SGS2(1,1) to 1e-8 in FP64, with FP32 and FP16-row-scaled
+    inner sweeps, and with the whole sweep in FP32 / FP16 (Arnoldi FP64):
+    each within +-1 of the oracle's stored count for the same precision;
+    every true residual recomputed by the oracle's SpMV, and the error
+    against the generating x_true."""
     pr = cd192
-    want = _oracle_count("convdiff3d_192_gmres30_sgs2_1_1")
-    h = g.gs2_setup(pr.A, precisions=("fp32", "fp16"))
-    for prec in ("fp64", "fp32", "fp16"):
+    h = g.gs2_setup(pr.A, precisions=LOWP)
+    for prec in ("fp64",) + LOWP:
         x = dev(np.zeros(pr.n))
         info = g.gmres_solve(h, dev(pr.b), x, 30, 1e-8, 5000,
                              g.params("gs2", 1, 1, direction="symmetric", precision=prec))
         assert info.status == 0, prec
-        slack = 1 if prec == "fp64" else max(2, want // 10)
-        assert abs(info.iters - want) <= slack, (prec, info.iters, want)
+        want = _oracle_count("convdiff3d_192_gmres30_sgs2_1_1" +
+                             ("" if prec == "fp64" else "_" + prec))
+        assert abs(info.iters - want) <= 1, (prec, info.iters, want)
         xg = host(x)
         r = np.linalg.norm(pr.b - oracle.spmv(pr.A, xg)) / np.linalg.norm(pr.b)
         assert r <= 1e-8, prec
@@ -218,12 +251,18 @@ def test_convdiff_full_size_gmres_all_precisions(g, cd192):
 
 def test_convdiff_full_size_sweeps(g, cd192):
     """192^3 (n = 7,077,888): one forward GS2(1,1) sweep in FP64 against the
-    oracle on every entry, FP32 and FP16 inner sweeps within their bounds."""
+    oracle on every entry, the lower precisions against the oracle's
+    definition of the same precision (1e-6) and within their bounds of the
+    FP64 oracle."""
     pr = cd192
     x0 = P.uniform_pm1(13, pr.n)
     ref = oracle.gs2(pr.A, pr.b, x0, 1, 1, 1.0, 1.0, 0)
-    h = g.gs2_setup(pr.A, precisions=("fp32", "fp16"))
-    for prec, bound in (("fp64", TOL), ("fp32", 2e-6), ("fp16", 2e-3)):
+    h = g.gs2_setup(pr.A, precisions=LOWP)
+    for prec, bound in (("fp64", TOL), ("fp32", 2e-6), ("fp16", 2e-3), ("fp32_sweep", 2e-6),
+                        ("fp16_sweep", 2e-3)):
         x = dev(x0)
         g.gs2_apply_ex(h, dev(pr.b), x, g.params("gs2", 1, 1, precision=prec))
         assert rel(host(x), ref) <= bound, prec
+        if prec != "fp64":
+            lp = oracle.gs2(pr.A, pr.b, x0, 1, 1, 1.0, 1.0, 0, precision=prec)
+            assert rel(host(x), lp) <= 1e-6, prec

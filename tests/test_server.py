@@ -61,7 +61,7 @@ def _alone(pr, pc, max_iters=4000):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "mtsgs", "amg", "hybrid"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16_sweep", "mtsgs", "amg", "hybrid"])
 def test_results_equal_alone_and_in_the_mix(lib, prec):
     if prec == "mtsgs":
         pc = gs2.params("mtgs", 1, direction="symmetric")
@@ -159,7 +159,7 @@ def _pack_of_one(pr, pc):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32_sweep"])
 def test_packed_requests_are_independent_of_their_pack_mates(lib, prec):
     """Requests up to pack_rows rows are admitted together and solved as one
     pack; each result is bitwise that of the request solved as a pack of
