@@ -400,13 +400,13 @@ struct HostTri {
   std::vector<double> va;
 };
 
-static void prepare_lowprec(gs2_handle* h, DevCsr& M, const HostTri& T, int prec) {
+static void prepare_lowprec(gs2_handle* h, DevCsr& M, const HostTri&, int prec) {
   const size_t nz = (size_t)M.nnz + kPad;
   if (prec == GS2_FP32 && !M.va32) {
-    std::vector<float> v(nz, 0.f);
-    for (int k = 0; k < M.nnz; ++k) v[k] = (float)T.va[k];
+    // converted on the device from the resident FP64 values (the host loop
+    // and the upload were most of a lower-precision request's setup)
     M.va32 = (float*)h->dalloc(sizeof(float) * nz);
-    h->h2d(M.va32, v.data(), sizeof(float) * nz);
+    launch_values_to_fp32(h, M, (int64_t)nz);
     if (M.sell_chunks > 0) {  // the layout exists (the autotuner may turn it off and on)
       const size_t slots = M.sell_slots;
       M.sell_va32 = (float*)h->dalloc(sizeof(float) * slots);
@@ -419,23 +419,11 @@ static void prepare_lowprec(gs2_handle* h, DevCsr& M, const HostTri& T, int prec
     // power of two is exact, so q_ij = fl16(v_ij 2^-e_i) is the only rounding
     // and the row keeps binary16's full precision at any magnitude; e_i is
     // stored in one byte (clamped to [-126, 127], the exponents of a normal
-    // FP32 power of two)
-    std::vector<__half> v(nz, __float2half(0.f));
-    std::vector<signed char> s(M.n, 0);
-    for (int i = 0; i < M.n; ++i) {
-      double m = 0.0;
-      for (int k = T.rp[i]; k < T.rp[i + 1]; ++k) m = std::max(m, std::fabs(T.va[k]));
-      int e = 0;
-      if (m > 0) std::frexp(m, &e);
-      e = std::min(127, std::max(-126, e));
-      s[i] = (signed char)e;
-      for (int k = T.rp[i]; k < T.rp[i + 1]; ++k)
-        v[k] = __double2half(std::ldexp(T.va[k], -e));  // one rounding, to nearest
-    }
+    // FP32 power of two); converted on the device
     M.va16 = (__half*)h->dalloc(sizeof(__half) * nz);
     M.scale16 = (signed char*)h->dalloc(sizeof(signed char) * std::max(M.n, 1));
-    h->h2d(M.va16, v.data(), sizeof(__half) * nz);
-    h->h2d(M.scale16, s.data(), sizeof(signed char) * M.n);
+    h->dzero(M.va16, sizeof(__half) * nz);
+    launch_values_to_fp16(h, M);
     if (M.sell_chunks > 0) {  // the layout exists (the autotuner may turn it off and on)
       const size_t slots = M.sell_slots;
       M.sell_va16 = (__half*)h->dalloc(sizeof(__half) * slots);

@@ -345,6 +345,11 @@ void launch_resid_sweep(gs2_handle* h, int vprec, const int* skip);
 void launch_rhat_update32(gs2_handle* h, const float* rhat, double* x, double omega, int mode,
                           const int* skip);
 void launch_to32(gs2_handle* h, const double* x, float* x32, const int* skip);
+// M's FP64 values (the nz entries of va, padding included) to M.va32; to
+// M.va16 with the per-row power-of-two scale exponents M.scale16 (the FP16
+// row-scaled precision)
+void launch_values_to_fp32(gs2_handle* h, const DevCsr& M, int64_t nz);
+void launch_values_to_fp16(gs2_handle* h, const DevCsr& M);
 
 void launch_spmv(gs2_handle* h, const double* x, double* y, const int* skip);
 // autotuner probe: ms per launch of M's most frequent kernel (role 0: A's

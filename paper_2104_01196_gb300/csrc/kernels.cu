@@ -522,6 +522,32 @@ __global__ void k_to32(int n, const double* __restrict__ x, float* x32, const in
     x32[i] = (float)x[i];
 }
 
+__global__ void k_values_to_fp32(int64_t nz, const double* __restrict__ va, float* va32) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nz;
+       k += (int64_t)gridDim.x * blockDim.x)
+    va32[k] = (float)va[k];
+}
+
+// Row i: e_i such that max_j |v_ij| = f 2^e_i with f in [1/2, 1) (e_i = 0 for a
+// row of zeros; clamped to [-126, 127]), read off the exponent field of the
+// maximum; q_ij = fl16(v_ij 2^-e_i), the power of two applied exactly.
+__global__ void k_values_to_fp16(int n, const int* __restrict__ rp, const double* __restrict__ va,
+                                 __half* va16, signed char* scale) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double m = 0.0;
+    for (int k = rp[i]; k < rp[i + 1]; ++k) m = fmax(m, fabs(va[k]));
+    int e = 0;
+    if (m > 0.0) {
+      const int E = (int)((__double_as_longlong(m) >> 52) & 0x7ff);
+      e = E == 0 ? -1022 : E - 1022;
+      e = min(127, max(-126, e));
+    }
+    scale[i] = (signed char)e;
+    const double inv = __longlong_as_double((long long)(1023 - e) << 52);  // 2^-e
+    for (int k = rp[i]; k < rp[i + 1]; ++k) va16[k] = __double2half(va[k] * inv);
+  }
+}
+
 __global__ void k_axpy(int n, double* y, double a, const double* __restrict__ x,
                        const int* skip) {
   if (skip && *skip) return;
@@ -567,6 +593,18 @@ void launch_rhat_update32(gs2_handle* h, const float* rhat, double* x, double om
                  (out ? 8.0 : 4.0) * h->n);
   k_rhat_update32<<<vec_blocks(h, h->n), kVecThreads, 0, h->stream>>>(
       (int)h->n, rhat, h->x32, x, (float)omega, mode, skip);
+  GS2_LAUNCH_CHECK();
+}
+
+void launch_values_to_fp32(gs2_handle* h, const DevCsr& M, int64_t nz) {
+  k_values_to_fp32<<<vec_blocks(h, nz), kVecThreads, 0, h->stream>>>(nz, M.va, M.va32);
+  GS2_LAUNCH_CHECK();
+}
+
+void launch_values_to_fp16(gs2_handle* h, const DevCsr& M) {
+  if (M.n == 0) return;
+  k_values_to_fp16<<<vec_blocks(h, M.n), kVecThreads, 0, h->stream>>>(M.n, M.rp, M.va, M.va16,
+                                                                      M.scale16);
   GS2_LAUNCH_CHECK();
 }
 
