@@ -64,9 +64,13 @@ def parse():
                     help="requests of the served stream")
     ap.add_argument("--serve-rates", default="50,200,1000",
                     help="open-loop Poisson arrival rates (requests/s), comma list")
-    ap.add_argument("--serve-forms", default="fp64,fp32,fp32_sweep,fp16_sweep,fp32_sweep_packed",
-                    help="server forms (inner-sweep precision, packing), comma list")
-    ap.add_argument("--serve-sweep-forms", default="fp64,fp32_sweep_packed",
+    ap.add_argument("--serve-forms",
+                    default="fp64,fp32,fp32_sweep,fp16_sweep,fp32_sweep_packed,"
+                            "fp32_sweep_packed_lanes",
+                    help="server forms (inner-sweep precision, packing, small-request "
+                         "slots), comma list")
+    ap.add_argument("--serve-sweep-forms",
+                    default="fp64,fp32_sweep_packed,fp32_sweep_packed_lanes",
                     help="forms that also run the open-loop rate sweep, comma list")
     ap.add_argument("--no-profile", action="store_true",
                     help="do not time kernels with events inside the timed region")
@@ -1001,14 +1005,16 @@ def _make_request(rec):
 
 
 SERVE_FORMS = {
-    # name: (sweep precision, rows up to which requests are packed)
-    "fp64": ("fp64", 0),
-    "fp32": ("fp32", 0),
-    "fp16": ("fp16", 0),
-    "fp32_packed": ("fp32", 1 << 16),
-    "fp32_sweep": ("fp32_sweep", 0),
-    "fp16_sweep": ("fp16_sweep", 0),
-    "fp32_sweep_packed": ("fp32_sweep", 1 << 16),
+    # name: (sweep precision, rows up to which requests are packed, slots
+    # kept for requests of at most 65,536 rows)
+    "fp64": ("fp64", 0, 0),
+    "fp32": ("fp32", 0, 0),
+    "fp16": ("fp16", 0, 0),
+    "fp32_packed": ("fp32", 1 << 16, 0),
+    "fp32_sweep": ("fp32_sweep", 0, 0),
+    "fp16_sweep": ("fp16_sweep", 0, 0),
+    "fp32_sweep_packed": ("fp32_sweep", 1 << 16, 0),
+    "fp32_sweep_packed_lanes": ("fp32_sweep", 1 << 16, 2),
 }
 
 
@@ -1018,7 +1024,8 @@ def serving(gs2, torch, count, rates, forms, sweep_forms, workers=0):
     n log-uniform in [1e3, 2e6], lognormal(0,1) coefficients, GMRES(30) +
     SGS2(1,1) to 1e-8, served by the continuous-batching server (8 slots,
     admission by device memory).  Per form (inner sweeps FP64, FP32, FP16, or
-    FP32 with requests of at most 65,536 rows admitted together as packs):
+    FP32 with requests of at most 65,536 rows admitted together as packs,
+    optionally with two of the slots kept for those requests):
     the server saturated (every request submitted at once: solves/s and
     submit-to-done latency); for the forms in `sweep_forms` also open-loop
     Poisson arrivals at each rate in `rates` (the stream's seeded
@@ -1049,10 +1056,11 @@ def serving(gs2, torch, count, rates, forms, sweep_forms, workers=0):
                 "p99": round(float(np.percentile(v, 99)), 2)} if len(v) else None
 
     for name in forms:
-        prec, pack_rows = SERVE_FORMS[name]
+        prec, pack_rows, small_slots = SERVE_FORMS[name]
         pc = gs2.params("gs2", 1, 1, direction="symmetric", precision=prec)
         srv = gs2.Server(restart=30, tol=1e-8, max_iters=10000, precond=pc, max_slots=8,
-                         prep_threads=4, pack_rows=pack_rows, pack_max=32)
+                         prep_threads=4, pack_rows=pack_rows, pack_max=32,
+                         small_rows=1 << 16, small_slots=small_slots)
         row = {}
         # saturated: everything queued at once
         t0 = time.perf_counter()

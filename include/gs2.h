@@ -458,6 +458,14 @@ typedef struct {
                                one pack (gs2_pack_gmres) in one slot; 0 = every
                                request alone.  Not with an AMG preconditioner. */
   int pack_max;             /* most requests in one pack (0 = 64) */
+  int64_t small_rows;       /* with small_slots > 0: requests of at most this */
+  int small_slots;          /* many rows are small, and small_slots of the
+                               max_slots slots are kept for them -- larger
+                               requests hold at most max_slots - small_slots
+                               at once, and a small request is admitted before
+                               larger ones that wait for their slots (arrival
+                               order within each class); 0 = arrival order for
+                               all.  small_slots < max_slots. */
 } gs2_server_cfg;
 
 typedef struct {

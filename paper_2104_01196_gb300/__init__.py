@@ -87,7 +87,8 @@ class _ServerCfg(ctypes.Structure):
                 ("tol", ctypes.c_double), ("max_iters", ctypes.c_int),
                 ("has_precond", ctypes.c_int), ("precond", Params),
                 ("fail_ticket", ctypes.c_uint64), ("pack_rows", ctypes.c_int64),
-                ("pack_max", ctypes.c_int)]
+                ("pack_max", ctypes.c_int), ("small_rows", ctypes.c_int64),
+                ("small_slots", ctypes.c_int)]
 
 
 class _Request(ctypes.Structure):
@@ -538,13 +539,16 @@ class Server:
 
     def __init__(self, restart=30, tol=1e-8, max_iters=10000, precond: Params | None = None,
                  max_slots=4, prep_threads=2, hbm_budget_bytes=0, fail_ticket=0,
-                 pack_rows=0, pack_max=0):
+                 pack_rows=0, pack_max=0, small_rows=0, small_slots=0):
         """pack_rows > 0: requests of at most that many rows are admitted
-        together (up to pack_max, 0 = 64) and solved as one pack."""
+        together (up to pack_max, 0 = 64) and solved as one pack.
+        small_slots > 0: that many of the max_slots slots are kept for
+        requests of at most small_rows rows, which pass larger ones waiting
+        for a slot."""
         self._cfg = _ServerCfg(hbm_budget_bytes, max_slots, prep_threads, restart, tol,
                                max_iters, 1 if precond is not None else 0,
                                precond if precond is not None else Params(), fail_ticket,
-                               pack_rows, pack_max)
+                               pack_rows, pack_max, small_rows, small_slots)
         out = ctypes.c_void_p()
         _check(load().gs2_server_create(ctypes.byref(self._cfg), ctypes.byref(out)))
         self._ptr = out.value

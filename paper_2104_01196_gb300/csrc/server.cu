@@ -41,6 +41,7 @@ struct Request {
   std::vector<int32_t> ci;
   std::vector<double> va, b, x0;
   int64_t footprint = 0;
+  bool large = false;  // holds one of the slots not reserved for small requests
   Clock::time_point t_submit, t_done;
   cudaStream_t stream = nullptr;
   gs2_handle* h = nullptr;
@@ -53,6 +54,7 @@ struct Request {
 // Small requests admitted together and solved as one pack in one slot.
 struct Group {
   std::vector<Request*> members;  // in pack order
+  bool large = false;             // its slot is one of the large requests'
   cudaStream_t stream = nullptr;
   gs2_handle* h = nullptr;
   PackJob* job = nullptr;
@@ -128,6 +130,7 @@ struct gs2_server {
   uint64_t next_ticket = 1;
   int64_t reserved = 0;
   int64_t slots_used = 0;  // preparing + active
+  int64_t large_used = 0;  // of them, slots held by large requests (small_slots > 0)
   int64_t submitted = 0, admitted = 0, completed = 0, failed = 0, max_active = 0;
   bool stopping = false;
   std::vector<std::thread> prep;
@@ -136,9 +139,28 @@ struct gs2_server {
 
 using namespace gs2;
 
-static bool admissible(gs2_server* s) {
-  if (s->pending.empty() || s->slots_used >= s->cfg.max_slots) return false;
-  return s->reserved + s->pending.front()->footprint <= s->budget;
+// A request is large when small_slots slots are reserved for requests of at
+// most small_rows rows and it has more; large requests hold at most
+// max_slots - small_slots slots at once.
+static bool is_large(const gs2_server* s, const Request* r) {
+  return s->cfg.small_slots > 0 && r->n > s->cfg.small_rows;
+}
+
+// The queue position of the request to admit next, or -1: the first request
+// in arrival order that may take a slot -- every request without reserved
+// slots, else large ones only while their slots are not all taken, so that a
+// small request passes the large ones waiting for those -- provided it fits
+// the memory budget (a request that does not fit holds the queue, as it
+// would in arrival order).
+static int next_admissible(gs2_server* s) {
+  if (s->slots_used >= s->cfg.max_slots) return -1;
+  const int64_t large_cap = s->cfg.max_slots - s->cfg.small_slots;
+  for (size_t k = 0; k < s->pending.size(); ++k) {
+    const Request* r = s->pending[k];
+    if (is_large(s, r) && s->large_used >= large_cap) continue;
+    return s->reserved + r->footprint <= s->budget ? (int)k : -1;
+  }
+  return -1;
 }
 
 static bool packable(const gs2_server* s, const Request* r) {
@@ -155,7 +177,10 @@ static void retire_locked(gs2_server* s, Request* r, bool ok, bool frees_slot = 
   r->state = REQ_DONE;
   r->t_done = Clock::now();
   s->reserved -= r->footprint;
-  if (frees_slot) s->slots_used -= 1;
+  if (frees_slot) {
+    s->slots_used -= 1;
+    if (r->large) s->large_used -= 1;
+  }
   if (ok) s->completed += 1;
   else s->failed += 1;
   s->cv_done.notify_all();
@@ -310,6 +335,7 @@ static void prepare_group(gs2_server* s, Group* g) {
       retire_locked(s, r, false, false);
     }
     s->slots_used -= 1;
+    if (g->large) s->large_used -= 1;
     s->cv_prep.notify_all();
     delete g;
     return;
@@ -326,28 +352,39 @@ static void prep_thread(gs2_server* s) {
     Group* g = nullptr;
     {
       std::unique_lock<std::mutex> lk(s->mu);
-      s->cv_prep.wait(lk, [&] { return s->stopping || admissible(s); });
+      int k = -1;
+      s->cv_prep.wait(lk, [&] { return s->stopping || (k = next_admissible(s)) >= 0; });
       if (s->stopping) return;
-      r = s->pending.front();
-      s->pending.pop_front();
+      r = s->pending[k];
+      s->pending.erase(s->pending.begin() + k);
       r->state = REQ_PREPARING;
+      r->large = is_large(s, r);
       s->reserved += r->footprint;
       s->slots_used += 1;
+      if (r->large) s->large_used += 1;
       s->admitted += 1;
       s->max_active = std::max(s->max_active, s->slots_used);
       if (packable(s, r)) {
-        // the small requests behind it join its pack while they fit
+        // the small requests behind it join its pack while they fit: the
+        // next ones in arrival order, or with reserved small slots the next
+        // ones of its own size class, passing the others
         g = new Group();
+        g->large = r->large;
         g->members.push_back(r);
         const int cap = s->cfg.pack_max > 0 ? s->cfg.pack_max : 64;
-        while ((int)g->members.size() < cap && !s->pending.empty()) {
-          Request* q = s->pending.front();
-          if (!packable(s, q) || s->reserved + q->footprint > s->budget) break;
-          s->pending.pop_front();
-          q->state = REQ_PREPARING;
-          s->reserved += q->footprint;
+        for (size_t q = k; (int)g->members.size() < cap && q < s->pending.size();) {
+          Request* c = s->pending[q];
+          if (!packable(s, c) || is_large(s, c) != r->large) {
+            if (s->cfg.small_slots == 0) break;
+            ++q;
+            continue;
+          }
+          if (s->reserved + c->footprint > s->budget) break;
+          s->pending.erase(s->pending.begin() + q);
+          c->state = REQ_PREPARING;
+          s->reserved += c->footprint;
           s->admitted += 1;
-          g->members.push_back(q);
+          g->members.push_back(c);
         }
       }
     }
@@ -413,6 +450,7 @@ static void finish_group(gs2_server* s, Group* g, gs2_status err) {
   s->groups.erase(std::find(s->groups.begin(), s->groups.end(), g));
   for (Request* r : g->members) retire_locked(s, r, err == GS2_OK && r->status == GS2_OK, false);
   s->slots_used -= 1;
+  if (g->large) s->large_used -= 1;
   s->cv_prep.notify_all();
   delete g;
 }
@@ -505,7 +543,8 @@ gs2_status gs2_server_create(const gs2_server_cfg* cfg, gs2_server** out) {
   *out = nullptr;
   if (cfg->max_slots < 1 || cfg->restart < 1 || cfg->restart > kMaxRestart ||
       !(cfg->tol >= 0.0) || cfg->max_iters < 0 || cfg->hbm_budget_bytes < 0 ||
-      cfg->pack_rows < 0 || cfg->pack_max < 0) {
+      cfg->pack_rows < 0 || cfg->pack_max < 0 || cfg->small_rows < 0 || cfg->small_slots < 0 ||
+      cfg->small_slots >= cfg->max_slots) {
     set_error("bad server configuration");
     return GS2_ERR_INVALID_ARG;
   }

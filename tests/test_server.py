@@ -277,3 +277,54 @@ def test_staggered_arrivals_equal_alone(lib, prec):
         ainfo, ax = _alone(p, pc, 8000)
         assert info.status == 0 and info.iters == ainfo.iters, p.name
         assert np.array_equal(x, ax), p.name
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("pack_rows", [0, 5000])
+def test_small_requests_pass_large_ones_waiting_for_a_slot(lib, pack_rows):
+    """With one of two slots kept for requests of at most 5,000 rows, large
+    requests run one at a time and the small requests submitted behind two
+    large ones are admitted before the second: each finishes before the
+    first large one does, the second large one only starts after the first
+    ends, and every result is still bitwise the one it gets alone (or as a
+    pack of one, when packed)."""
+    import time
+    pc = gs2.params("gs2", 1, 1, direction="symmetric")
+    bigs = [P.variable_coefficient_problem("poisson2d", 1000, 31),
+            P.variable_coefficient_problem("poisson2d", 1000, 32)]
+    smalls = [p for p in _mix() if p.n <= 5000]
+    assert len(smalls) >= 3
+    srv = gs2.Server(restart=30, tol=1e-8, max_iters=8000, precond=pc, max_slots=2,
+                     prep_threads=2, pack_rows=pack_rows, pack_max=4, small_rows=5000,
+                     small_slots=1)
+    t0 = time.perf_counter()
+    subs, tickets = [], []
+    for p in bigs + smalls:
+        subs.append(time.perf_counter() - t0)
+        tickets.append(srv.submit(p.A, p.b))
+    got = [srv.wait(t, p.n) for t, p in zip(tickets, bigs + smalls)]
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(tickets) and st["failed"] == 0 and st["reserved_bytes"] == 0
+    done = [s + lat / 1000.0 for s, (_, _, lat) in zip(subs, got)]
+    # the two large requests are alike: run one after the other, the second
+    # ends about one solve after the first (side by side, both would end
+    # at about the same time)
+    assert done[1] - done[0] > 0.5 * (done[0] - subs[0]), "the large requests ran side by side"
+    for d in done[2:]:
+        assert d < done[0], "a small request waited behind the large ones"
+    for p, (info, x, _) in zip(bigs + smalls, got):
+        assert info.status == 0 and info.true_relres <= 1e-8
+        if pack_rows and p.n <= pack_rows:
+            oinfo, ox = _pack_of_one(p, pc)
+        else:
+            oinfo, ox = _alone(p, pc, 8000)
+        assert info.iters == oinfo.iters and np.array_equal(x, ox), p.name
+
+
+def test_server_refuses_reserving_every_slot(lib):
+    """The configuration is checked before any device work."""
+    with pytest.raises(gs2.GS2Error, match="bad server configuration"):
+        gs2.Server(max_slots=2, small_rows=100, small_slots=2)
+    with pytest.raises(gs2.GS2Error, match="bad server configuration"):
+        gs2.Server(max_slots=2, small_rows=-1, small_slots=1)
