@@ -137,7 +137,7 @@ typedef struct {
   int sell_a, sell_tri;           /* 1: A / the triangles run on the sliced-ELL layout */
   double offset_frac_a;           /* share of A's sliced-ELL chunks that store column */
   double offset_frac_tri;         /* offsets instead of columns (stencil rows); D^{-1}L */
-  int solve_mode;                 /* gs2_autotune_gmres's choice (1, 2, 3); 0 = not tuned */
+  int solve_mode;                 /* gs2_autotune_gmres's choice (1, 2, 3, 4); 0 = not tuned */
   int solve_modes_timed;          /* candidates it timed */
 } gs2_handle_stats;
 
@@ -181,13 +181,23 @@ gs2_status gs2_get_stats(const gs2_handle* h, gs2_handle_stats* out);
 gs2_status gs2_autotune(gs2_handle* h);
 
 /* How gmres_solve issues the Arnoldi steps of a restart cycle:
- * 0 (default): the whole solve as one cooperative launch for a small system
- * (n <= 16,384, restart <= 32, no preconditioner, JR or FP64 non-compact
- * GS2, per-kernel profiling off: every restart cycle, preconditioner
- * application and Givens step inside one kernel whose blocks meet at
- * bounded grid barriers), else as in mode 1; 1 = each restart cycle's steps
+ * 0 (default): for a small system (restart <= 32, no preconditioner, JR or
+ * FP64 non-compact GS2, per-kernel profiling off) the whole solve in one
+ * kernel -- inside one thread-block cluster as in mode 4 when the system's
+ * rows fit its shared memory, else as one cooperative launch whose blocks
+ * meet at bounded grid barriers (n <= 16,384) -- every restart cycle,
+ * preconditioner application and Givens step included; otherwise as in
+ * mode 1; 1 = each restart cycle's steps
  * as one replayed CUDA graph; 2 = as separate launches; 3 = the one-launch
- * solver, up to n = 65,536 (INVALID_ARG when the solve does not qualify).
+ * solver, up to n = 65,536 (INVALID_ARG when the solve does not qualify);
+ * 4 = the one-cluster solver: the whole GMRES solve inside one cluster of
+ * at most 16 CTAs, every row's vectors, Krylov basis entries and matrix
+ * entries in the shared memory of the CTA that owns it, other rows' entries
+ * read through distributed shared memory, the CTAs meeting at bounded
+ * cluster barriers (restart <= 32, no, JR or FP64 non-compact GS2
+ * preconditioning, and a system whose rows fit: about 8,000 rows of a
+ * 5-point stencil at restart 30; INVALID_ARG otherwise; CG and packs run
+ * as in mode 1).
  * A graph is captured once per cycle shape (restart, preconditioner,
  * profiling settings) on a private stream joined to the handle's stream;
  * steps after the device has ended the cycle run as no-ops.  Results are
@@ -199,21 +209,24 @@ gs2_status gs2_set_graph_mode(gs2_handle* h, int mode);
 /* Autotune how much of a GMRES(restart) solve with this preconditioner is
  * fused into one launch -- the fusion depth: every kernel of an Arnoldi
  * step launched on its own (mode 2), a restart cycle's steps replayed as
- * one CUDA graph (mode 1), or the whole solve as one cooperative launch
- * (mode 3, where the solve qualifies) -- by timing one restart cycle of each
+ * one CUDA graph (mode 1), the whole solve as one cooperative launch
+ * (mode 3) or inside one thread-block cluster (mode 4), where the solve
+ * qualifies -- by timing one restart cycle of each
  * candidate on this matrix (the right-hand side is the handle's scratch, the
  * caller's vectors are not touched).  The fastest becomes the handle's
  * automatic choice (graph mode 0), cached by matrix class (size to a factor
  * sqrt(2), mean row length) and preconditioner; *mode_out (may be NULL)
  * receives it.  Results do not change with the choice beyond rounding (the
- * one-launch solver reduces in another order). */
+ * one-launch and one-cluster solvers reduce in another order). */
 gs2_status gs2_autotune_gmres(gs2_handle* h, int restart, const gs2_params* precond,
                               int* mode_out);
 
-/* Test hook for the bounded waits of the one-launch solver: the next such
- * solve on this handle starts with a grid barrier that can never open, so
- * every block gives up after its wait limit (about two seconds), the kernel
- * returns, and the solve reports GS2_ERR_TIMEOUT; the handle stays usable. */
+/* Test hook for the bounded waits of the one-launch and one-cluster
+ * solvers: the next such solve on this handle starts with a grid barrier
+ * that can never open (one launch) or with one CTA that never arrives at the
+ * cluster barriers (one cluster), so every block gives up after its wait
+ * limit (about two seconds), the kernel returns, and the solve reports
+ * GS2_ERR_TIMEOUT; the handle stays usable. */
 gs2_status gs2_test_stall_barrier(gs2_handle* h);
 
 /* Non-compact GS2 relaxation, Eq. (2) with inner JR sweeps Eq. (3)-(5):

@@ -289,7 +289,8 @@ class Handle:
 
     def set_graph_mode(self, mode: int):
         """0: automatic (one launch for small systems, else graphs), 1: restart
-        cycles as CUDA graphs, 2: separate launches, 3: one launch."""
+        cycles as CUDA graphs, 2: separate launches, 3: one launch, 4: one
+        thread-block cluster (GMRES of a system that fits its shared memory)."""
         _check(load().gs2_set_graph_mode(self.ptr, mode))
 
     def test_stall_barrier(self):

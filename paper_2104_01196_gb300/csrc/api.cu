@@ -509,6 +509,21 @@ static gs2_host_side* host_side(const gs2_handle* h) {
   return it == g_host.end() ? nullptr : it->second;
 }
 
+// the longest rows of A, D^{-1}L and D^{-1}U, from the host copies of their
+// row pointers (cached in the handle)
+void longest_rows(gs2_handle* h) {
+  if (h->cl_wa >= 0) return;
+  const gs2_host_side* hs = host_side(h);
+  auto widest = [](const std::vector<int>& rp) {
+    int w = 0;
+    for (size_t i = 0; i + 1 < rp.size(); ++i) w = std::max(w, rp[i + 1] - rp[i]);
+    return w;
+  };
+  h->cl_wa = widest(hs->Arp);
+  h->cl_wl = widest(hs->L.rp);
+  h->cl_wu = widest(hs->U.rp);
+}
+
 void ensure_precision(gs2_handle* h, int prec) {
   if (prec == GS2_FP64) return;
   if (prec != GS2_FP32 && prec != GS2_FP16_ROWSCALED && !is_sweep_precision(prec))
@@ -1515,7 +1530,7 @@ gs2_status gs2_autotune_gmres(gs2_handle* h, int restart, const gs2_params* prec
 }
 
 gs2_status gs2_set_graph_mode(gs2_handle* h, int mode) {
-  if (!h || mode < 0 || mode > 3) return GS2_ERR_INVALID_ARG;
+  if (!h || mode < 0 || mode > 4) return GS2_ERR_INVALID_ARG;
   h->graph_mode = mode;
   return GS2_OK;
 }

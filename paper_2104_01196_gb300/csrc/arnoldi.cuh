@@ -47,6 +47,40 @@ __device__ __forceinline__ void update_rows(int i, int end, int step, int ld,
   }
 }
 
+// Givens step j on one thread's own copies (the solvers whose every block
+// or CTA holds the Krylov scalars): col = column j of H with H(j+1, j)
+// already in col[j + 1]; the earlier rotations cs/sn[0 .. j) are applied to
+// it, the new rotation is formed by the rules of givens_block below and
+// applied to col and to g.  Returns the residual estimate |g_{j+1}|.
+__device__ __forceinline__ double givens_column(double* col, double* cs, double* sn, double* g,
+                                                int j) {
+  for (int q = 0; q < j; ++q) {
+    const double u = col[q], v = col[q + 1];
+    col[q] = cs[q] * u + sn[q] * v;
+    col[q + 1] = -sn[q] * u + cs[q] * v;
+  }
+  const double f = col[j], gg = col[j + 1];
+  double c, sg, rr;
+  if (gg == 0.0) {
+    c = 1.0; sg = 0.0; rr = f;
+  } else if (f == 0.0) {
+    c = 0.0; sg = gg > 0.0 ? 1.0 : -1.0; rr = fabs(gg);
+  } else {
+    const double d = sqrt(f * f + gg * gg);
+    c = fabs(f) / d;
+    rr = f > 0.0 ? d : -d;
+    sg = gg / rr;
+  }
+  cs[j] = c;
+  sn[j] = sg;
+  col[j] = rr;
+  col[j + 1] = 0.0;
+  const double gj = g[j];
+  g[j + 1] = -sg * gj;
+  g[j] = c * gj;
+  return fabs(-sg * gj);
+}
+
 // Givens step j of one system, run by a whole block: H(j+1, j) = ||w|| from
 // the partial sums part[p0 .. p1), the earlier rotations applied to column
 // j, the new rotation from (H(j,j), H(j+1,j)) with

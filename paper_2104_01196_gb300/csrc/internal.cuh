@@ -213,7 +213,8 @@ struct gs2_handle {
   // CUDA graph of one restart cycle's Arnoldi steps (launch-bound small
   // systems): captured on a private stream, replayed there and joined to
   // `stream` with events; re-captured when the cycle's shape changes
-  int graph_mode = 0;  // 0: automatic, 1: graphs, 2: separate launches, 3: one launch
+  int graph_mode = 0;  // 0: automatic, 1: graphs, 2: separate launches, 3: one launch,
+                       // 4: one cluster
   // gs2_autotune_gmres: the automatic mode's tuned choice for (restart,
   // preconditioner) tune_key (0 = not tuned: the size rule)
   int tuned_mode = 0, tuned_candidates = 0;
@@ -222,6 +223,7 @@ struct gs2_handle {
   unsigned* persist_bar = nullptr;  // grid barrier of the single-launch solver
   double* persist_part = nullptr;   // its partial sums
   bool stall_barrier = false;       // test hook: next one-launch solve's barrier never opens
+  int cl_wa = -1, cl_wl = -1, cl_wu = -1;  // longest rows of A, L, U (longest_rows)
   // one-launch solve of a pack: per-system argument table, block -> system
   // map, barriers, partial sums and results (grown on demand)
   void* pp_args = nullptr;
@@ -448,6 +450,10 @@ void read_state(gs2_handle* h);
 // to 65,536 rows (16,384 when chosen automatically), m <= 32, no
 // preconditioner, FP64 non-compact GS2 or JR
 bool persistent_eligible(const gs2_handle* h, int m, const gs2_params* p, bool automatic);
+void longest_rows(gs2_handle* h);
+bool cluster_eligible(gs2_handle* h, int m, const gs2_params* p);
+gs2_status gmres_cluster(gs2_handle* h, const double* b, double* x, int m, double tol,
+                         int max_iters, const gs2_params* p, gs2_solve_info* info);
 // gs2_autotune_gmres: the fastest solve structure (1, 2, 3) for (m, p)
 int autotune_gmres(gs2_handle* h, int m, const gs2_params* p);
 void launch_fill_value(gs2_handle* h, double* y, double v);

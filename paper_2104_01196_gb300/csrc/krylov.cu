@@ -696,7 +696,8 @@ gs2_status gmres_run(gs2_handle* h, const double* b, double* x, int m, double to
 }
 
 // Time one restart cycle per candidate structure (mode 2: separate
-// launches; 1: cycle graphs; 3: one launch, where eligible) on scratch
+// launches; 1: cycle graphs; 3: one launch and 4: one cluster, where
+// eligible) on scratch
 // vectors (b = 1, x = 0; tolerance 0 so that every cycle runs all m steps),
 // best of two after one untimed run; the fastest becomes the automatic
 // choice for (m, p).  Cached by matrix class and (m, p).
@@ -725,6 +726,7 @@ int autotune_gmres(gs2_handle* h, int m, const gs2_params* p) {
   launch_fill_value(h, h->tune_b, 1.0);
   std::vector<int> cand = {2, 1};
   if (persistent_eligible(h, m, p, false)) cand.push_back(3);
+  if (cluster_eligible(h, m, p)) cand.push_back(4);
   const int saved = h->graph_mode;
   cudaEvent_t e0, e1;
   GS2_CUDA(cudaEventCreate(&e0));
@@ -769,10 +771,13 @@ int autotune_gmres(gs2_handle* h, int m, const gs2_params* p) {
 
 static gs2_status gmres_run_mode(gs2_handle* h, const double* b, double* x, int m, double tol,
                                  int max_iters, const gs2_params* p, gs2_solve_info* info) {
-  // small systems: the whole solve in one launch (automatic unless per-kernel
-  // profiling is on; graph mode 3 asks for it)
-  const bool forced = h->graph_mode == 3;
+  // small systems: the whole solve inside one cluster when its rows fit the
+  // cluster's shared memory (automatic unless per-kernel profiling is on;
+  // graph mode 4 asks for it), else in one cooperative launch
   const bool automatic = h->graph_mode == 0 && !profiling_active(h);
+  if (h->graph_mode == 4 || (automatic && cluster_eligible(h, m, p)))
+    return gmres_cluster(h, b, x, m, tol, max_iters, p, info);
+  const bool forced = h->graph_mode == 3;
   if ((forced || automatic) && persistent_eligible(h, m, p, !forced))
     return gmres_persistent(h, b, x, m, tol, max_iters, p, info);
   if (h->graph_mode == 3)

@@ -450,31 +450,7 @@ k_gmres_persistent(PersistArgs a0, const PersistArgs* sys, const int* bsys) {
         for (int q = 0; q < jc; ++q) col[q] = h1[q] + h2[q];
         const double hn = sqrt(t);
         col[j + 1] = hn;
-        for (int q = 0; q < j; ++q) {
-          const double u = col[q], v = col[q + 1];
-          col[q] = cs_s[q] * u + sn_s[q] * v;
-          col[q + 1] = -sn_s[q] * u + cs_s[q] * v;
-        }
-        const double f = col[j], g = col[j + 1];
-        double c, sg, rr;
-        if (g == 0.0) {
-          c = 1.0; sg = 0.0; rr = f;
-        } else if (f == 0.0) {
-          c = 0.0; sg = g > 0.0 ? 1.0 : -1.0; rr = fabs(g);
-        } else {
-          const double d = sqrt(f * f + g * g);
-          c = fabs(f) / d;
-          rr = f > 0.0 ? d : -d;
-          sg = g / rr;
-        }
-        cs_s[j] = c;
-        sn_s[j] = sg;
-        col[j] = rr;
-        col[j + 1] = 0.0;
-        const double gj = g_s[j];
-        g_s[j + 1] = -sg * gj;
-        g_s[j] = c * gj;
-        const double est = fabs(-sg * gj);
+        const double est = givens_column(col, cs_s, sn_s, g_s, j);
         int stop = 0;
         if (isnan(est) || isnan(hn) || isinf(hn)) {
           status = GS2_ERR_NAN;

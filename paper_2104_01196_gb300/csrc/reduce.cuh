@@ -30,21 +30,18 @@ struct Log2<1> {
   static constexpr int value = 0;
 };
 
-// Block-wide sums of NV <= 32 per-thread values.  Inside a warp a butterfly
-// transpose-reduction halves the values each lane holds at every exchange,
-// P - 1 adds per lane for P = NV rounded up to a power of two, instead of
-// 5 adds per value of a shuffle tree -- the FP64 pipe is the bottleneck of
-// these kernels.  After it lane l holds the warp's sum of value l >> (5 - p).
-// The block's sums go to column `col` of part (the block index by default;
-// a block that loops over several work items passes the item).
+// Warp sums of NV <= 32 per-thread values.  A butterfly transpose-reduction
+// halves the values each lane holds at every exchange, P - 1 adds per lane
+// for P = NV rounded up to a power of two, instead of 5 adds per value of a
+// shuffle tree -- the FP64 pipe is the bottleneck of these kernels.  Returns
+// this lane's share: the lanes whose low 5 - p bits are zero (p = log2 P)
+// hold the warp's sum of value lane >> (5 - p).
 template <int NV>
-__device__ __forceinline__ void block_partials_bf(const double (&acc)[NV], double* part,
-                                                  int nblk, int col) {
+__device__ __forceinline__ double warp_butterfly(const double (&acc)[NV]) {
   constexpr int P = Pow2<NV>::value;
   constexpr int p = Log2<P>::value;
   static_assert(P <= 32, "butterfly reduction holds at most 32 values");
-  __shared__ double red[kVecThreads / 32][P];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
   double a[P];
 #pragma unroll
   for (int k = 0; k < P; ++k) a[k] = k < NV ? acc[k] : 0.0;
@@ -64,8 +61,23 @@ __device__ __forceinline__ void block_partials_bf(const double (&acc)[NV], doubl
   // value: finish with a plain tree over those bits
 #pragma unroll
   for (int o = 16 >> p; o > 0; o >>= 1) a[0] += __shfl_xor_sync(0xffffffffu, a[0], o);
+  return a[0];
+}
+
+// Block-wide sums of NV <= 32 per-thread values (warp_butterfly, then the
+// warps' sums in warp order).  The block's sums go to column `col` of part
+// (the block index by default; a block that loops over several work items
+// passes the item).
+template <int NV>
+__device__ __forceinline__ void block_partials_bf(const double (&acc)[NV], double* part,
+                                                  int nblk, int col) {
+  constexpr int P = Pow2<NV>::value;
+  constexpr int p = Log2<P>::value;
+  __shared__ double red[kVecThreads / 32][P];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const double a0 = warp_butterfly<NV>(acc);
   const int k = lane >> (5 - p);
-  if ((lane & ((1 << (5 - p)) - 1)) == 0) red[wid][k] = a[0];
+  if ((lane & ((1 << (5 - p)) - 1)) == 0) red[wid][k] = a0;
   __syncthreads();
   if (threadIdx.x < NV) {
     double s = 0.0;

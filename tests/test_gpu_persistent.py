@@ -1,8 +1,11 @@
-"""GPU parity of the one-launch GMRES solver for small systems (the whole
-restarted solve in one cooperative launch): iteration counts within +-1 of
-the oracle and of the multi-kernel path for every preconditioner it takes,
-the solver statuses, run-to-run reproducibility, automatic selection, and
-the bounded grid barrier giving up with GS2_ERR_TIMEOUT instead of hanging.
+"""GPU parity of the small-system GMRES solvers -- the one-launch solver
+(the whole restarted solve in one cooperative launch, graph mode 3) and the
+one-cluster solver (the whole solve inside one thread-block cluster, the
+system in its CTAs' shared memory, graph mode 4): iteration counts within +-1
+of the oracle and of the multi-kernel path for every preconditioner they
+take, the solver statuses, run-to-run reproducibility, automatic selection,
+and the bounded grid and cluster barriers giving up with GS2_ERR_TIMEOUT
+instead of hanging.
 """
 import numpy as np
 import pytest
@@ -71,23 +74,41 @@ PCS = {
 # the oracle itself is sensitive (a one-ulp ensemble spreads by more than 2),
 # (2) the GPU tracks the oracle's true residual step by step to 1e-10 for as
 # long as the oracle tracks itself to 1e-12, and (3) the GPU's count lies in
-# the ensemble's range widened by 15%.  Two settings stagnate at restart 5 on
-# elasticity in every run: both sides must return NOT_CONVERGED.
-SENSITIVE = {("elasticity3d_4", 5, pc) for pc in ("none", "gs2_bwd_2_0", "jr_3_w0.8", "jr_4")}
-STAGNATING = {("elasticity3d_4", 5, pc) for pc in ("gs2_fwd_1_1", "jr_2_w0.9")}
+# the ensemble's range widened by 15%.  JR(2) with omega = 0.9 is sensitive in
+# its outcome as well: 16 of 48 one-ulp perturbations converge (in 3,369 to
+# 5,999 steps) and the others stop at the 6,000-step limit, so there the GPU
+# must reach an outcome the ensemble shows.  Forward GS2(1,1) stagnates at
+# restart 5 on elasticity in every run (relative residual 0.84 in all 48):
+# both sides must return NOT_CONVERGED.
+SENSITIVE = {("elasticity3d_4", 5, pc)
+             for pc in ("none", "gs2_bwd_2_0", "jr_3_w0.8", "jr_4", "jr_2_w0.9")}
+# the systems whose rows fit one cluster's shared memory (the 40^3 Laplacian,
+# 64,000 rows, does not)
+CLUSTER_FITS = {"poisson2d_64", "random_3000", "convdiff3d_12", "elasticity3d_4"}
+STAGNATING = {("elasticity3d_4", 5, "gs2_fwd_1_1")}
 ULP = 2.0 ** -52
 
 
-def oracle_ensemble(pr, restart, op, members=12, seed=7):
+_ENSEMBLES = {}
+
+
+def oracle_ensemble(pr, restart, op, members=48, seed=7):
     """The oracle's solve of A x = b(1 + e), e_i ~ one ulp (seeded), for
-    `members` perturbations: their iteration counts and statuses."""
-    rng = np.random.default_rng(seed)
-    out = []
-    for _ in range(members):
-        bp = pr.b * (1.0 + ULP * rng.standard_normal(pr.n))
-        _, oi = oracle.gmres(pr.A, bp, restart=restart, tol=1e-8, max_iters=6000, **op)
-        out.append(oi)
-    return out
+    `members` perturbations: their iteration counts and statuses (computed
+    once per case; every solver mode is checked against the same sample).
+    The sample must be large enough to show the spread's tails: twelve
+    members of backward GS2(2,0) at restart 5 spanned 334..484 iterations,
+    while the spread of such perturbations reaches 301..681."""
+    key = (pr.name, restart, tuple(sorted(op.items())), members, seed)
+    if key not in _ENSEMBLES:
+        rng = np.random.default_rng(seed)
+        out = []
+        for _ in range(members):
+            bp = pr.b * (1.0 + ULP * rng.standard_normal(pr.n))
+            _, oi = oracle.gmres(pr.A, bp, restart=restart, tol=1e-8, max_iters=6000, **op)
+            out.append(oi)
+        _ENSEMBLES[key] = out
+    return _ENSEMBLES[key]
 
 
 def tracking_horizon(pr, restart, op, kmax=40, members=4, seed=11):
@@ -111,11 +132,21 @@ def tracking_horizon(pr, restart, op, kmax=40, members=4, seed=11):
 
 def check_sensitive(g, h, pr, restart, prm, op, info):
     ens = oracle_ensemble(pr, restart, op)
-    counts = [e.iters for e in ens]
-    assert all(e.status == 0 for e in ens)
-    assert max(counts) - min(counts) > 2, counts  # the case is rounding-sensitive
-    lo, hi = 0.85 * min(counts), 1.15 * max(counts)
-    assert info.status == 0 and lo <= info.iters <= hi, (info.iters, counts)
+    counts = [e.iters for e in ens if e.status == 0]
+    stopped = [e for e in ens if e.status != 0]
+    assert all(e.status in (0, 5) for e in ens)
+    # the case is rounding-sensitive: both outcomes occur, or the counts spread
+    if stopped:
+        assert counts, "every perturbation stops: a stagnating case"
+    else:
+        assert max(counts) - min(counts) > 2, counts
+    if info.status == 0:
+        # a converged outcome, in the range of the ensemble's converged ones
+        assert counts, "the GPU converged where no perturbation of the oracle does"
+        lo, hi = 0.85 * min(counts), 1.15 * max(counts)
+        assert lo <= info.iters <= hi, (info.iters, sorted(counts))
+    else:
+        assert info.status == 5 and stopped, (info, len(stopped))
     base, horizon = tracking_horizon(pr, restart, op)
     assert horizon >= 5, horizon  # at least one whole restart cycle
     for k in range(1, horizon + 1):
@@ -134,7 +165,14 @@ def test_one_launch_matches_oracle_and_multi_kernel_path(g, name, pc, restart):
     prm = g.params(**gp) if gp else None
     h = g.gs2_setup(pr.A)
     _, oinfo = oracle.gmres(pr.A, pr.b, restart=restart, tol=1e-8, max_iters=6000, **op)
-    for mode in (3, 1):  # the one-launch solver, then the multi-kernel path (graphs)
+    # the one-launch solver, the one-cluster solver, the multi-kernel path
+    for mode in (3, 4, 1):
+        if mode == 4 and name not in CLUSTER_FITS:
+            h.set_graph_mode(4)
+            with pytest.raises(g.GS2Error) as e:
+                g.gmres_solve(h, dev(pr.b), dev(np.zeros(pr.n)), restart, 1e-8, 10, prm)
+            assert e.value.status == 1
+            continue
         h.set_graph_mode(mode)
         x = dev(np.zeros(pr.n))
         info = g.gmres_solve(h, dev(pr.b), x, restart, 1e-8, 6000, prm)
@@ -148,13 +186,15 @@ def test_one_launch_matches_oracle_and_multi_kernel_path(g, name, pc, restart):
             assert info.status == 0 and oinfo.status == 0, (info, oinfo)
             assert abs(info.iters - oinfo.iters) <= 1, (mode, info.iters, oinfo.iters)
         r = np.linalg.norm(pr.b - oracle.spmv(pr.A, host(x))) / np.linalg.norm(pr.b)
-        assert r <= 1e-8 and abs(info.true_relres - r) <= 1e-12
+        assert abs(info.true_relres - r) <= 1e-12
+        assert info.status != 0 or r <= 1e-8
 
 
-def test_one_launch_statuses_and_reproducibility(g):
+@pytest.mark.parametrize("mode", [3, 4])
+def test_one_launch_statuses_and_reproducibility(g, mode):
     pr = P.poisson2d(40)
     h = g.gs2_setup(pr.A)
-    h.set_graph_mode(3)
+    h.set_graph_mode(mode)
     prm = g.params("gs2", 1, 1)
     x1, x2 = dev(np.zeros(pr.n)), dev(np.zeros(pr.n))
     i1 = g.gmres_solve(h, dev(pr.b), x1, 30, 1e-8, 3000, prm)
@@ -181,7 +221,7 @@ def test_one_launch_statuses_and_reproducibility(g):
     d = 1.0 + P.uniform01(9, n)
     D = (np.arange(n + 1, dtype=np.int64), np.arange(n, dtype=np.int32), d)
     hd = g.gs2_setup(D)
-    hd.set_graph_mode(3)
+    hd.set_graph_mode(mode)
     v = P.uniform_pm1(10, n)
     x = dev(np.zeros(n))
     info = g.gmres_solve(hd, dev(v), x, 30, 1e-10, 100, g.params("jr", 1))
@@ -206,13 +246,15 @@ def test_automatic_selection_uses_one_launch_for_small_systems(g):
         g.gmres_solve(h, b, x, 30, 1e-8, 100, g.params("gs2", 1, 1, precision="fp32"))
 
 
-def test_stalled_barrier_times_out_and_the_handle_recovers(g):
-    """The grid barrier's wait is bounded: with an arrival count no block can
-    complete, every block gives up (about two seconds), the solve reports
-    GS2_ERR_TIMEOUT, and the next solve on the handle is normal."""
+@pytest.mark.parametrize("mode", [3, 4])
+def test_stalled_barrier_times_out_and_the_handle_recovers(g, mode):
+    """The grid and cluster barriers' waits are bounded: with an arrival
+    count no block can complete (one launch) or a CTA that never arrives
+    (one cluster), every block gives up (about two seconds), the solve
+    reports GS2_ERR_TIMEOUT, and the next solve on the handle is normal."""
     pr = P.poisson2d(32)
     h = g.gs2_setup(pr.A)
-    h.set_graph_mode(3)
+    h.set_graph_mode(mode)
     h.test_stall_barrier()
     with pytest.raises(g.GS2Error) as e:
         g.gmres_solve(h, dev(pr.b), dev(np.zeros(pr.n)), 30, 1e-8, 500, g.params("gs2", 1, 1))
@@ -222,13 +264,14 @@ def test_stalled_barrier_times_out_and_the_handle_recovers(g):
     assert info.status == 0
 
 
+@pytest.mark.parametrize("mode", [3, 4])
 @pytest.mark.parametrize("restart", [1, 2, 8, 9, 32])
-def test_one_launch_restart_edges(g, restart):
+def test_one_launch_restart_edges(g, restart, mode):
     """Restart lengths at and around the register-block boundaries (the CGS2
     phases round the basis size up to a multiple of 8; m <= 32)."""
     pr = P.random_system(1500, 71, mean_offdiag=5.0, dominance=1.2)
     h = g.gs2_setup(pr.A)
-    h.set_graph_mode(3)
+    h.set_graph_mode(mode)
     x = dev(np.zeros(pr.n))
     info = g.gmres_solve(h, dev(pr.b), x, restart, 1e-9, 4000, g.params("gs2", 1, 1))
     _, oinfo = oracle.gmres(pr.A, pr.b, restart=restart, tol=1e-9, max_iters=4000,
@@ -237,17 +280,18 @@ def test_one_launch_restart_edges(g, restart):
     assert abs(info.iters - oinfo.iters) <= 1, (info.iters, oinfo.iters)
 
 
-def test_one_launch_tiny_systems(g):
+@pytest.mark.parametrize("mode", [3, 4])
+def test_one_launch_tiny_systems(g, mode):
     """One row, two rows, and a system smaller than one block."""
     one = (np.array([0, 1]), np.array([0], np.int32), np.array([4.0]))
     h = g.gs2_setup(one)
-    h.set_graph_mode(3)
+    h.set_graph_mode(mode)
     x = dev(np.zeros(1))
     info = g.gmres_solve(h, dev(np.array([2.0])), x, 30, 1e-12, 10, g.params("gs2", 1, 1))
     assert info.status == 0 and host(x)[0] == pytest.approx(0.5, rel=1e-15)
     two = P.dense_to_csr(np.array([[3.0, 1.0], [-1.0, 2.0]]))
     h = g.gs2_setup(two)
-    h.set_graph_mode(3)
+    h.set_graph_mode(mode)
     x = dev(np.zeros(2))
     info = g.gmres_solve(h, dev(np.array([1.0, 1.0])), x, 30, 1e-12, 10, None)
     assert info.status == 0 and info.iters <= 2
@@ -255,7 +299,7 @@ def test_one_launch_tiny_systems(g):
                        rtol=1e-12)
     pr = P.poisson2d(9)  # 81 rows
     h = g.gs2_setup(pr.A)
-    h.set_graph_mode(3)
+    h.set_graph_mode(mode)
     x = dev(np.zeros(pr.n))
     info = g.gmres_solve(h, dev(pr.b), x, 30, 1e-10, 500, g.params("gs2", 1, 2,
                                                                      direction="symmetric"))
@@ -326,16 +370,18 @@ def test_one_launch_cg_statuses_and_selection(g):
 
 def test_autotune_gmres_picks_a_structure_and_keeps_the_results(g):
     """gs2_autotune_gmres times one restart cycle per solve structure
-    (separate launches, cycle graphs, one launch where eligible), makes the
-    fastest the automatic choice for that restart and preconditioner, reports
+    (separate launches, cycle graphs, one launch or one cluster where
+    eligible), makes the fastest the automatic choice for that restart and
+    preconditioner, reports
     it in the handle's stats, and the tuned automatic solve keeps the
     oracle's count; a different preconditioner falls back to the size rule."""
     prm = g.params("gs2", 1, 1, direction="symmetric")
-    for pr, candidates in ((P.poisson2d(64), 3), (P.poisson3d(40), 3)):
+    # the 64^2 system also fits one cluster; the 40^3 one does not
+    for pr, candidates in ((P.poisson2d(64), 4), (P.poisson3d(40), 3)):
         h = g.gs2_setup(pr.A)
         mode = h.autotune_gmres(30, prm)
         st = h.stats()
-        assert mode in (1, 2, 3) and st["solve_mode"] == mode
+        assert mode in (1, 2, 3, 4) and st["solve_mode"] == mode
         assert st["solve_modes_timed"] == candidates
         x = dev(np.zeros(pr.n))
         info = g.gmres_solve(h, dev(pr.b), x, 30, 1e-8, 3000, prm)
