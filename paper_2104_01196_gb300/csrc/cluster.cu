@@ -164,6 +164,7 @@ struct ClSync {
   int pb;                          // partial-sum buffer of the next sum
   int ok;
   int mute;                        // test hook: this CTA does not arrive
+  double (*red)[32];               // the warps' sums of a cluster sum (every width)
 };
 
 // Bounded cluster barrier: false when this CTA gave up waiting (it records
@@ -278,7 +279,7 @@ __device__ bool cl_sums(ClSync& S, const double (&acc)[NV], int nv, double* out,
                         int* err, double (*part)[32]) {
   constexpr int P = Pow2<NV>::value;
   constexpr int p = Log2<P>::value;
-  __shared__ double red[kClMaxThreads / 32][P];
+  double (*red)[32] = S.red;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const double a0 = warp_butterfly<NV>(acc);
   if ((lane & ((1 << (5 - p)) - 1)) == 0) red[wid][lane >> (5 - p)] = a0;
@@ -721,6 +722,9 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
   extern __shared__ __align__(16) unsigned char cl_smem[];
   __shared__ ClSync S;
   __shared__ double part[2][32];
+  // one buffer for the warp sums of every width, declared here and reached
+  // through S (declared at namespace scope instead, the solve went wrong)
+  __shared__ double red[kClMaxThreads / 32][32];
   // the arguments and the row view in shared memory, where every phase
   // reads them (held in registers they would crowd out the row loops')
   __shared__ ClusterArgs a;
@@ -750,6 +754,7 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
     S.pb = 0;
     S.ok = 1;
     S.mute = a0.stall && (int)rank == a0.C - 1;
+    S.red = red;
   }
   if ((int)threadIdx.x < a0.C) {
     S.peer_mbar[threadIdx.x] = cl_map(smem_u32(&S.mbar), threadIdx.x);
