@@ -723,9 +723,10 @@ def small_system(gs2, torch, reps=20):
                      "iters": info.iters, "oracle_iters": stored_count("poisson2d_64_gmres30_gs2_1_1"),
                      "true_relres": info.true_relres}
         h.close()
-    # CG with SGS2(1,1) on the same SPD system, one launch vs graphs of 16 iterations
+    # CG with SGS2(1,1) on the same SPD system: one cluster, one launch, graphs of 16
+    # iterations
     pcs = gs2.params("gs2", 1, 1, direction="symmetric")
-    for name, mode in (("cg_one_launch", 3), ("cg_graph", 1)):
+    for name, mode in (("cg_one_cluster", 4), ("cg_one_launch", 3), ("cg_graph", 1)):
         h = gs2.gs2_setup(pr.A)
         h.set_graph_mode(mode)
         for _ in range(3):

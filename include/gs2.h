@@ -196,8 +196,8 @@ gs2_status gs2_autotune(gs2_handle* h);
  * read through distributed shared memory, the CTAs meeting at bounded
  * cluster barriers (restart <= 32, no, JR or FP64 non-compact GS2
  * preconditioning, and a system whose rows fit: about 8,000 rows of a
- * 5-point stencil at restart 30; INVALID_ARG otherwise; CG and packs run
- * as in mode 1).
+ * 5-point stencil at restart 30; INVALID_ARG otherwise); cg_solve runs the
+ * same way in modes 3 and 4, and packs run as in mode 1 in mode 4.
  * A graph is captured once per cycle shape (restart, preconditioner,
  * profiling settings) on a private stream joined to the handle's stream;
  * steps after the device has ended the cycle run as no-ops.  Results are

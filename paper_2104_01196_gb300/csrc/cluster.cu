@@ -1,4 +1,5 @@
-// Restarted GMRES(m) of a small system inside one thread-block cluster.
+// Restarted GMRES(m), or CG, of a small system inside one thread-block
+// cluster.
 //
 // A system of a few thousand rows spends its one-launch solve (persist.cu)
 // waiting: on a GB300 a grid barrier through device memory costs 1.3 us and
@@ -117,6 +118,7 @@ struct ClusterArgs {
   int* err;  // device error word
   KrylovState* out;
   int stall;  // test hook: the last CTA never arrives, so every wait runs out
+  int cg;     // 1: preconditioned CG (basis slots 0, 1, 2: p, A p, a residual)
 };
 
 // ---------------------------------------------------------------------------
@@ -717,6 +719,138 @@ __device__ bool cl_solve(const ClRows& c, const ClusterArgs& a, ClSync& S, doubl
   return true;
 }
 
+// Preconditioned CG on loaded rows: the iteration of the one-launch CG
+// solver (restart of the search direction when the recursive residual has
+// converged but the true residual disagrees), every scalar summed alike by
+// every CTA.  p, q = A p and the true-residual scratch t are basis slots
+// 0, 1, 2; r takes w's slot.  False when a barrier gave up.
+__device__ bool cl_cg_solve(const ClRows& c, const ClusterArgs& a, ClSync& S,
+                            double (*part)[32], unsigned rank) {
+  __shared__ double tot;
+  const int C = a.C;
+  double* x = c.v(kVX);
+  double* r = c.v(kVW);
+  const double* z = c.v(kVZ);
+  const double* bb = c.v(kVB);
+  double* p = c.V;
+  double* q = c.V + c.Rp;
+  double* t = c.V + 2 * c.Rp;
+  const unsigned poff = a.lay.V - a.lay.vec;  // p's offset from vector 0
+  int iters = 0, cycles = 0, status = GS2_OK;
+  double sm = 0.0;
+  CL_ROWS(l) sm = fma(bb[l], bb[l], sm);
+  if (!cl_sum1(S, sm, &tot, C, a.err, part)) return false;
+  const double bnorm = sqrt(tot);
+  double beta = 0.0;
+  if (bnorm == 0.0 || isnan(bnorm) || isinf(bnorm)) {
+    if (bnorm == 0.0) CL_ROWS(l) x[l] = 0.0;
+    if (rank == 0 && threadIdx.x == 0) {
+      a.out->iters = 0;
+      a.out->cycles = 0;
+      a.out->status = bnorm == 0.0 ? GS2_OK : GS2_ERR_NAN;
+      a.out->bnorm = bnorm;
+      a.out->beta = bnorm == 0.0 ? 0.0 : NAN;
+    }
+    return true;
+  }
+  const double tol_abs = a.tol * bnorm;
+  CL_ROWS(l) r[l] = bb[l] - cl_dotA(c, l, kVX);
+  for (;;) {
+    // ||r|| of the recursive residual; confirmed on the true one
+    sm = 0.0;
+    CL_ROWS(l) sm = fma(r[l], r[l], sm);
+    if (!cl_sum1(S, sm, &tot, C, a.err, part)) return false;
+    const double rn = sqrt(tot);
+    beta = rn;
+    if (isnan(rn) || isinf(rn)) {
+      status = GS2_ERR_NAN;
+      break;
+    }
+    if (rn <= tol_abs) {
+      sm = 0.0;
+      CL_ROWS(l) {
+        const double ti = bb[l] - cl_dotA(c, l, kVX);
+        t[l] = ti;
+        sm = fma(ti, ti, sm);
+      }
+      if (!cl_sum1(S, sm, &tot, C, a.err, part)) return false;
+      beta = sqrt(tot);
+      if (beta <= tol_abs) break;
+      CL_ROWS(l) r[l] = t[l];
+    }
+    if (iters >= a.max_iters) {
+      status = GS2_ERR_NOT_CONVERGED;
+      break;
+    }
+    ++cycles;
+    // z = M^{-1} r, p = z, rz = r.z
+    if (!cl_precond(c, a, S, r)) return false;
+    sm = 0.0;
+    CL_ROWS(l) {
+      p[l] = z[l];
+      sm = fma(r[l], z[l], sm);
+    }
+    if (!cl_sum1(S, sm, &tot, C, a.err, part)) return false;
+    double rz = tot;
+    for (;;) {
+      // q = A p (p complete: the last sum's barrier) and p.q
+      sm = 0.0;
+      CL_ROWS(l) {
+        const double qi = cl_row_dot(c.Av, c.Aa, c.WA, c.Rp, l, poff);
+        q[l] = qi;
+        sm = fma(p[l], qi, sm);
+      }
+      if (!cl_sum1(S, sm, &tot, C, a.err, part)) return false;
+      const double pq = tot;
+      if (pq == 0.0) {
+        status = GS2_ERR_BREAKDOWN;
+        break;
+      }
+      const double alpha = rz / pq;
+      sm = 0.0;
+      CL_ROWS(l) {
+        x[l] = fma(alpha, p[l], x[l]);
+        const double ri = fma(-alpha, q[l], r[l]);
+        r[l] = ri;
+        sm = fma(ri, ri, sm);
+      }
+      if (!cl_sum1(S, sm, &tot, C, a.err, part)) return false;
+      ++iters;
+      const double rr = sqrt(tot);
+      if (isnan(rr) || isinf(rr)) {
+        status = GS2_ERR_NAN;
+        break;
+      }
+      if (rr <= tol_abs || iters >= a.max_iters) break;
+      // z = M^{-1} r, beta = r.z / rz, p = z + beta p
+      if (!cl_precond(c, a, S, r)) return false;
+      sm = 0.0;
+      CL_ROWS(l) sm = fma(r[l], z[l], sm);
+      if (!cl_sum1(S, sm, &tot, C, a.err, part)) return false;
+      const double bt = tot / rz;
+      rz = tot;
+      CL_ROWS(l) p[l] = fma(bt, p[l], z[l]);
+      if (!cl_sync(S, C, a.err)) return false;
+    }
+    if (status == GS2_ERR_NAN || status == GS2_ERR_BREAKDOWN) break;
+  }
+  // the true residual at exit
+  sm = 0.0;
+  CL_ROWS(l) {
+    const double ti = bb[l] - cl_dotA(c, l, kVX);
+    sm = fma(ti, ti, sm);
+  }
+  if (!cl_sum1(S, sm, &tot, C, a.err, part)) return false;
+  if (rank == 0 && threadIdx.x == 0) {
+    a.out->iters = iters;
+    a.out->cycles = cycles;
+    a.out->status = status;
+    a.out->bnorm = bnorm;
+    a.out->beta = sqrt(tot);
+  }
+  return true;
+}
+
 __global__ void __launch_bounds__(kClMaxThreads, 1)
     k_gmres_cluster(const __grid_constant__ ClusterArgs a0) {
   extern __shared__ __align__(16) unsigned char cl_smem[];
@@ -780,7 +914,8 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
                (double*)(cl_smem + L.Uv), (unsigned*)(cl_smem + L.Ua));
   // every CTA's rows loaded and barrier initialised
   cluster_barrier_hw();
-  cl_solve(c, a, S, part, rank);
+  if (a.cg) cl_cg_solve(c, a, S, part, rank);
+  else cl_solve(c, a, S, part, rank);
   const double* x = c.v(kVX);
   CL_ROWS(l) a.x[row0 + l] = x[l];
   // no CTA leaves while another may still read its shared memory
@@ -873,8 +1008,10 @@ bool cluster_eligible(gs2_handle* h, int m, const gs2_params* p) {
   return cluster_plan(h, m, p, &pl);
 }
 
-gs2_status gmres_cluster(gs2_handle* h, const double* b, double* x, int m, double tol,
-                         int max_iters, const gs2_params* p, gs2_solve_info* info) {
+// GMRES(m) (cg = false) or CG (cg = true: three basis slots) in one cluster
+static gs2_status cluster_run(gs2_handle* h, const double* b, double* x, int m, double tol,
+                              int max_iters, const gs2_params* p, gs2_solve_info* info,
+                              bool cg) {
   ClPlan pl;
   if (!cluster_plan(h, m, p, &pl))
     GS2_THROW(GS2_ERR_INVALID_ARG, "the one-cluster solver takes restart <= 32, no, JR or FP64 "
@@ -905,12 +1042,13 @@ gs2_status gmres_cluster(gs2_handle* h, const double* b, double* x, int m, doubl
   a.kind = pc ? pc->kind : GS2_PC_NONE;
   a.outer = pc ? std::max(1, pc->outer) : 1;
   a.inner = pc ? pc->inner : 0;
-  a.dir = pc ? pc->direction : GS2_FORWARD;
+  a.dir = pc ? pc->direction : (cg ? GS2_SYMMETRIC : GS2_FORWARD);
   a.omega = pc ? pc->omega : 1.0;
   a.gamma = pc ? pc->gamma : 1.0;
   a.err = h->dev_err;
   a.out = h->st;
   a.stall = h->stall_barrier ? 1 : 0;
+  a.cg = cg ? 1 : 0;
   h->stall_barrier = false;
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3((unsigned)pl.C);
@@ -925,7 +1063,7 @@ gs2_status gmres_cluster(gs2_handle* h, const double* b, double* x, int m, doubl
   cfg.attrs = at;
   cfg.numAttrs = 1;
   {
-    KernelTimer tm(h, "gmres_cluster", 0.0);
+    KernelTimer tm(h, cg ? "cg_cluster" : "gmres_cluster", 0.0);
     GS2_CUDA(cudaLaunchKernelEx(&cfg, k_gmres_cluster, a));
     GS2_LAUNCH_CHECK();
   }
@@ -935,6 +1073,16 @@ gs2_status gmres_cluster(gs2_handle* h, const double* b, double* x, int m, doubl
   loc.true_relres = st.bnorm == 0.0 ? 0.0 : st.beta / st.bnorm;
   if (info) *info = loc;
   return (gs2_status)st.status;
+}
+
+gs2_status gmres_cluster(gs2_handle* h, const double* b, double* x, int m, double tol,
+                         int max_iters, const gs2_params* p, gs2_solve_info* info) {
+  return cluster_run(h, b, x, m, tol, max_iters, p, info, false);
+}
+
+gs2_status cg_cluster(gs2_handle* h, const double* b, double* x, double tol, int max_iters,
+                      const gs2_params* p, gs2_solve_info* info) {
+  return cluster_run(h, b, x, 2, tol, max_iters, p, info, true);
 }
 
 }  // namespace gs2

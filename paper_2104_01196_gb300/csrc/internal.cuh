@@ -454,6 +454,8 @@ void longest_rows(gs2_handle* h);
 bool cluster_eligible(gs2_handle* h, int m, const gs2_params* p);
 gs2_status gmres_cluster(gs2_handle* h, const double* b, double* x, int m, double tol,
                          int max_iters, const gs2_params* p, gs2_solve_info* info);
+gs2_status cg_cluster(gs2_handle* h, const double* b, double* x, double tol, int max_iters,
+                      const gs2_params* p, gs2_solve_info* info);
 // gs2_autotune_gmres: the fastest solve structure (1, 2, 3) for (m, p)
 int autotune_gmres(gs2_handle* h, int m, const gs2_params* p);
 void launch_fill_value(gs2_handle* h, double* y, double v);

@@ -972,8 +972,12 @@ gs2_status cg_run(gs2_handle* h, const double* b, double* x, double tol, int max
     return GS2_OK;
   }
   {
-    const bool forced = h->graph_mode == 3;
+    // small systems: inside one cluster where the rows fit (graph mode 4 or
+    // automatic), else in one cooperative launch (graph mode 3 or automatic)
     const bool automatic = h->graph_mode == 0 && !profiling_active(h);
+    if (h->graph_mode == 4 || (automatic && cluster_eligible(h, 2, p)))
+      return cg_cluster(h, b, x, tol, max_iters, p, info);
+    const bool forced = h->graph_mode == 3;
     if ((forced || automatic) && persistent_eligible(h, 1, p, !forced))
       return cg_persistent(h, b, x, tol, max_iters, p, info);
     if (forced)

@@ -325,14 +325,15 @@ CG_PCS = {
 }
 
 
+@pytest.mark.parametrize("mode", [3, 4])
 @pytest.mark.parametrize("name", list(SPD))
 @pytest.mark.parametrize("pc", list(CG_PCS))
-def test_one_launch_cg_matches_oracle(g, name, pc):
+def test_one_launch_cg_matches_oracle(g, name, pc, mode):
     pr = SPD[name]
     gp, op = CG_PCS[pc]
     prm = g.params(**gp) if gp else None
     h = g.gs2_setup(pr.A)
-    h.set_graph_mode(3)
+    h.set_graph_mode(mode)
     x = dev(np.zeros(pr.n))
     info = g.cg_solve(h, dev(pr.b), x, 1e-8, 5000, prm)
     _, oinfo = oracle.cg(pr.A, pr.b, tol=1e-8, max_iters=5000, **op)
@@ -345,7 +346,8 @@ def test_one_launch_cg_matches_oracle(g, name, pc):
     assert abs(ig.iters - info.iters) <= 1
 
 
-def test_one_launch_cg_statuses_and_selection(g):
+@pytest.mark.parametrize("mode", [3, 4])
+def test_one_launch_cg_statuses_and_selection(g, mode):
     pr = P.poisson2d(40)
     h = g.gs2_setup(pr.A)
     prm = g.params("gs2", 1, 1, direction="symmetric")
@@ -354,7 +356,7 @@ def test_one_launch_cg_statuses_and_selection(g):
     c0 = g.launch_count()
     info = g.cg_solve(h, b, dev(np.zeros(pr.n)), 1e-8, 500, prm)
     assert info.status == 0 and g.launch_count() - c0 <= 2
-    h.set_graph_mode(3)
+    h.set_graph_mode(mode)
     info = g.cg_solve(h, b, dev(np.zeros(pr.n)), 1e-14, 9, prm)
     assert info.status == 5 and info.iters == 9
     x = dev(np.ones(pr.n))
