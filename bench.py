@@ -812,8 +812,9 @@ def packs(gs2, torch, count=128):
                                                         for a, q in zip(infos, seq)))}
     pack.close()
     # a pack of 32 tiny systems (n in [500, 2000]; ~35K rows in all, about
-    # one row per thread of the co-resident blocks): replayed cycle graphs
-    # against the whole pack in one cooperative launch
+    # one row per thread of the co-resident blocks): replayed cycle graphs,
+    # the whole pack in one cooperative launch, and one thread-block cluster
+    # per system
     recipe = P.request_stream(32, rate_hz=1.0, n_lo=5e2, n_hi=2e3, seed=P.SEED_BASE + 500,
                               build=False)
     tiny = [P.variable_coefficient_problem(kind, N, seed) for _, kind, N, seed in recipe]
@@ -822,7 +823,7 @@ def packs(gs2, torch, count=128):
     tx = torch.zeros(tp.n, dtype=torch.float64, device="cuda")
     pc1 = gs2.params("gs2", 1, 1, direction="symmetric")
     row = {"systems": len(tiny), "n_total": int(tp.n)}
-    for name, mode in (("graphs", 1), ("one_launch", 3)):
+    for name, mode in (("graphs", 1), ("one_launch", 3), ("one_cluster", 4)):
         tp.set_graph_mode(mode)
 
         def run():

@@ -197,7 +197,9 @@ gs2_status gs2_autotune(gs2_handle* h);
  * cluster barriers (restart <= 32, no, JR or FP64 non-compact GS2
  * preconditioning, and a system whose rows fit: about 8,000 rows of a
  * 5-point stencil at restart 30; INVALID_ARG otherwise); cg_solve runs the
- * same way in modes 3 and 4, and packs run as in mode 1 in mode 4.
+ * same way in modes 3 and 4; a pack (gs2_pack_gmres) in mode 4 gives every
+ * system a cluster of its own, of one shape chosen for the pack (the most
+ * systems resident at once against the rows each CTA holds).
  * A graph is captured once per cycle shape (restart, preconditioner,
  * profiling settings) on a private stream joined to the handle's stream;
  * steps after the device has ended the cycle run as no-ops.  Results are
@@ -397,7 +399,11 @@ gs2_status gs2_batch_solve(gs2_handle* const* hs, const double* const* bs,
  * rotations, stopping tests and iteration counts; each restart cycle is one
  * replay of the captured Arnoldi steps for every system still running.
  * Small systems, which alone leave the GPU idle between launches, share the
- * launches of a pack.  The paper solves one system at a time; packs are a
+ * launches of a pack.  A pack small enough to give every row a thread of
+ * the co-resident blocks runs in one launch instead: one thread-block
+ * cluster per system where every system fits a cluster's shared memory,
+ * else every system on its own blocks of one cooperative launch (graph
+ * modes 4 and 3 ask for these).  The paper solves one system at a time; packs are a
  * library extension. */
 
 /* Create a pack from host CSR arrays: n[s] rows, rowptr[s] (int64, n[s]+1,

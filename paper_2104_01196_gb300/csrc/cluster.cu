@@ -92,10 +92,19 @@ __host__ __device__ inline ClLayout cl_layout(int Rp, int WA, int WL, int WU, in
   return L;
 }
 
+// One system of a pack: its rows [base, base + n) of the pack's vectors and
+// block-diagonal matrix, R rows a CTA, its result slot.
+struct ClSys {
+  int base, n, R;
+  KrylovState* out;
+};
+
 struct ClusterArgs {
-  int n;  // rows
-  int R;  // rows per CTA (the last CTA may hold fewer, at least one)
-  int C;  // CTAs of the cluster
+  int n;     // rows
+  int R;     // rows per CTA (the last CTA may hold fewer, at least one)
+  int C;     // CTAs of the cluster
+  int base;  // the system's first row in the vectors and the matrix
+  const ClSys* sys;  // a pack: cluster k solves system sys[k] (base, n, R, out)
   ClLayout lay;
   const int* Arp;
   const int* Aci;
@@ -406,10 +415,11 @@ __device__ bool cl_precond(const ClRows& c, const ClusterArgs& a, ClSync& S, con
 // entries' values and gather addresses (of vector 0 in the owning CTA) in
 // stored order, then padding slots of value 0 that point at the row itself
 // (W is at least the longest row; a matrix the solve does not use has
-// W = 0)
+// W = 0).  row0: the CTA's first row in the matrix; base: the system's
+// first row, which column numbers are taken relative to.
 __device__ void cl_load_rows(const int* rp, const int* ci, const double* va, int W, int Rp,
-                             int row0, int Rk, int R, unsigned vec0, unsigned rank, double* val,
-                             unsigned* adr) {
+                             int row0, int Rk, int R, int base, unsigned vec0, unsigned rank,
+                             double* val, unsigned* adr) {
   for (int l = threadIdx.x; l < Rp; l += blockDim.x) {
     const bool own = l < Rk;
     const int k0 = own ? rp[row0 + l] : 0;
@@ -417,7 +427,7 @@ __device__ void cl_load_rows(const int* rp, const int* ci, const double* va, int
     const unsigned self = cl_map(vec0 + 8u * (unsigned)l, rank);
     for (int q = 0; q < W; ++q) {
       if (q < ln) {
-        const int col = ci[k0 + q];
+        const int col = ci[k0 + q] - base;
         const int o = col / R;
         val[q * Rp + l] = va[k0 + q];
         adr[q * Rp + l] = cl_map(vec0 + 8u * (unsigned)(col - o * R), (unsigned)o);
@@ -863,11 +873,21 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
   // reads them (held in registers they would crowd out the row loops')
   __shared__ ClusterArgs a;
   __shared__ ClRows c;
+  __shared__ int row0_s;  // this CTA's first row in the vectors and the matrix
   const unsigned rank = cl_rank();
   const ClLayout& L = a0.lay;
-  const int row0 = (int)rank * a0.R;
   if (threadIdx.x == 0) {
     a = a0;
+    if (a0.sys) {
+      // a pack: this cluster's system
+      const ClSys q = a0.sys[blockIdx.x / a0.C];
+      a.base = q.base;
+      a.n = q.n;
+      a.R = q.R;
+      a.out = q.out;
+    }
+    const int r0 = (int)rank * a.R;
+    row0_s = a.base + r0;
     c.vec = (double*)(cl_smem + L.vec);
     c.V = (double*)(cl_smem + L.V);
     c.Av = (const double*)(cl_smem + L.Av);
@@ -880,7 +900,7 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
     c.WL = L.WL;
     c.WU = L.WU;
     c.Rp = L.Rp;
-    c.Rk = max(0, min(a0.R, a0.n - row0));
+    c.Rk = max(0, min(a.R, a.n - r0));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&S.mbar)), "r"(a0.C)
                  : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -895,22 +915,23 @@ __global__ void __launch_bounds__(kClMaxThreads, 1)
     S.peer_part[threadIdx.x] = cl_map(smem_u32(&part[0][0]), threadIdx.x);
   }
   __syncthreads();
+  const int row0 = row0_s;
   // this CTA's rows: x0, b, D^{-1}; the other vectors zero
   for (int l = threadIdx.x; l < L.Rp; l += blockDim.x) {
     const bool own = l < c.Rk;
     for (int k = 0; k < kClVecs; ++k) c.vec[k * L.Rp + l] = 0.0;
     if (own) {
-      c.vec[kVX * L.Rp + l] = a0.x[row0 + l];
-      c.vec[kVB * L.Rp + l] = a0.b[row0 + l];
-      c.vec[kVD * L.Rp + l] = a0.dinv[row0 + l];
+      c.vec[kVX * L.Rp + l] = a.x[row0 + l];
+      c.vec[kVB * L.Rp + l] = a.b[row0 + l];
+      c.vec[kVD * L.Rp + l] = a.dinv[row0 + l];
     }
   }
   const unsigned vec0 = smem_u32(c.vec);
-  cl_load_rows(a.Arp, a.Aci, a.Ava, L.WA, L.Rp, row0, c.Rk, a.R, vec0, rank,
+  cl_load_rows(a.Arp, a.Aci, a.Ava, L.WA, L.Rp, row0, c.Rk, a.R, a.base, vec0, rank,
                (double*)(cl_smem + L.Av), (unsigned*)(cl_smem + L.Aa));
-  cl_load_rows(a.Lrp, a.Lci, a.Lva, L.WL, L.Rp, row0, c.Rk, a.R, vec0, rank,
+  cl_load_rows(a.Lrp, a.Lci, a.Lva, L.WL, L.Rp, row0, c.Rk, a.R, a.base, vec0, rank,
                (double*)(cl_smem + L.Lv), (unsigned*)(cl_smem + L.La));
-  cl_load_rows(a.Urp, a.Uci, a.Uva, L.WU, L.Rp, row0, c.Rk, a.R, vec0, rank,
+  cl_load_rows(a.Urp, a.Uci, a.Uva, L.WU, L.Rp, row0, c.Rk, a.R, a.base, vec0, rank,
                (double*)(cl_smem + L.Uv), (unsigned*)(cl_smem + L.Ua));
   // every CTA's rows loaded and barrier initialised
   cluster_barrier_hw();
@@ -1078,6 +1099,165 @@ static gs2_status cluster_run(gs2_handle* h, const double* b, double* x, int m, 
 gs2_status gmres_cluster(gs2_handle* h, const double* b, double* x, int m, double tol,
                          int max_iters, const gs2_params* p, gs2_solve_info* info) {
   return cluster_run(h, b, x, m, tol, max_iters, p, info, false);
+}
+
+// ---------------------------------------------------------------------------
+// a pack: one cluster per system, every cluster of the same shape (the
+// largest system's rows per CTA), each solving its system's whole GMRES on
+// its own -- clusters never wait for one another
+// ---------------------------------------------------------------------------
+
+static bool pack_cluster_plan(gs2_handle* h, int m, const gs2_params* p, ClPlan* out,
+                              std::vector<ClSys>* sys) {
+  const std::vector<int64_t>* offp = pack_offsets(h);
+  if (!offp || offp->size() < 2 || !cl_kind_ok(m, p)) return false;
+  const std::vector<int64_t>& off = *offp;
+  const int S = (int)off.size() - 1;
+  int64_t maxn = 0;
+  for (int s = 0; s < S; ++s) maxn = std::max(maxn, off[s + 1] - off[s]);
+  if (maxn < 1 || maxn > (int64_t)kClMaxCtas * 4096) return false;
+  const bool tri = p && p->kind == GS2_PC_GS2;
+  longest_rows(h);
+  const size_t limit = cl_smem_limit(h);
+  // The cluster shape that finishes the pack first: an Arnoldi step takes
+  // about 17.4 us + 0.021 us per row of a CTA (measured from 64 to 256
+  // rows a CTA), and the systems run in ceil(S / clusters resident at once)
+  // waves -- more CTAs a system shorten a step but may hold fewer systems
+  // on the GPU at once.
+  double best = 0.0;
+  bool found = false;
+  for (int C = 1; C <= kClMaxCtas; ++C) {
+    const int Rmax = (int)((maxn + C - 1) / C);
+    const int Rp = (Rmax + 1) & ~1;
+    const ClLayout lay = cl_layout(Rp, h->cl_wa, tri ? h->cl_wl : 0, tri ? h->cl_wu : 0, m);
+    if (lay.bytes > limit) continue;
+    const int T = Rmax <= 64 ? 64 : (Rmax <= 128 ? 128 : 256);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)C);
+    cfg.blockDim = dim3((unsigned)T);
+    cfg.dynamicSmemBytes = lay.bytes;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    GS2_CUDA(cudaOccupancyMaxActiveClusters(&clusters, (const void*)k_gmres_cluster, &cfg));
+    if (clusters < 1) continue;
+    const double waves = std::ceil((double)S / clusters);
+    const double cost = waves * (17.4 + 0.021 * Rmax);
+    if (!found || cost < best) {
+      found = true;
+      best = cost;
+      out->C = C;
+      out->R = Rmax;
+      out->T = T;
+      out->lay = lay;
+    }
+  }
+  if (!found) return false;
+  const int C = out->C;
+  sys->resize(S);
+  for (int s = 0; s < S; ++s) {
+    const int n = (int)(off[s + 1] - off[s]);
+    (*sys)[s] = ClSys{(int)off[s], n, std::max(1, (n + C - 1) / C), nullptr};
+  }
+  return true;
+}
+
+bool pack_cluster_eligible(gs2_handle* h, int m, const gs2_params* p) {
+  ClPlan pl;
+  std::vector<ClSys> sys;
+  return pack_cluster_plan(h, m, p, &pl, &sys);
+}
+
+gs2_status pack_gmres_cluster(gs2_handle* h, const double* b, double* x, int m, double tol,
+                              int max_iters, const gs2_params* p, gs2_solve_info* infos) {
+  ClPlan pl;
+  std::vector<ClSys> sys;
+  if (!pack_cluster_plan(h, m, p, &pl, &sys))
+    GS2_THROW(GS2_ERR_INVALID_ARG, "one cluster per system: restart <= 32, no, JR or FP64 "
+                                   "non-compact GS2 preconditioning, and systems whose rows "
+                                   "fit the shared memory of 16 CTAs");
+  ensure_krylov(h, m);
+  const int S = (int)sys.size();
+  if (S > h->pp_cap_sys || !h->cl_sys) {
+    const int cs = std::max(S, h->pp_cap_sys);
+    if (S > h->pp_cap_sys) {
+      h->pp_st = (KrylovState*)h->dalloc(sizeof(KrylovState) * cs);
+      if (h->pp_st_host) pinned_put(h->pp_st_host, sizeof(KrylovState) * h->pp_cap_sys);
+      h->pp_st_host = (KrylovState*)pinned_get(sizeof(KrylovState) * cs);
+      h->pp_cap_sys = cs;
+    }
+  }
+  if (S > h->cl_sys_cap) {
+    h->cl_sys = h->dalloc(sizeof(ClSys) * S);
+    h->cl_sys_cap = S;
+  }
+  for (int s = 0; s < S; ++s) sys[s].out = h->pp_st + s;
+  h->h2d(h->cl_sys, sys.data(), sizeof(ClSys) * S);
+  const gs2_params* pc = (p && p->kind != GS2_PC_NONE) ? p : nullptr;
+  ClusterArgs a{};
+  a.C = pl.C;
+  a.lay = pl.lay;
+  a.sys = (const ClSys*)h->cl_sys;
+  a.Arp = h->A.rp;
+  a.Aci = h->A.ci;
+  a.Ava = h->A.va;
+  a.Lrp = h->L.rp;
+  a.Lci = h->L.ci;
+  a.Lva = h->L.va;
+  a.Urp = h->U.rp;
+  a.Uci = h->U.ci;
+  a.Uva = h->U.va;
+  a.dinv = h->dinv;
+  a.b = b;
+  a.x = x;
+  a.m = m;
+  a.tol = tol;
+  a.max_iters = max_iters;
+  a.kind = pc ? pc->kind : GS2_PC_NONE;
+  a.outer = pc ? std::max(1, pc->outer) : 1;
+  a.inner = pc ? pc->inner : 0;
+  a.dir = pc ? pc->direction : GS2_FORWARD;
+  a.omega = pc ? pc->omega : 1.0;
+  a.gamma = pc ? pc->gamma : 1.0;
+  a.err = h->dev_err;
+  a.out = h->pp_st;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)(pl.C * S));
+  cfg.blockDim = dim3((unsigned)pl.T);
+  cfg.dynamicSmemBytes = pl.lay.bytes;
+  cfg.stream = h->stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)pl.C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  {
+    KernelTimer tm(h, "gmres_cluster", 0.0);
+    GS2_CUDA(cudaLaunchKernelEx(&cfg, k_gmres_cluster, a));
+    GS2_LAUNCH_CHECK();
+  }
+  GS2_CUDA(cudaMemcpyAsync(h->pp_st_host, h->pp_st, sizeof(KrylovState) * S,
+                           cudaMemcpyDeviceToHost, h->stream));
+  GS2_CUDA(cudaMemcpyAsync(h->err_host, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost,
+                           h->stream));
+  GS2_CUDA(cudaStreamSynchronize(h->stream));
+  if (*h->err_host) raise_device_error(h);  // a barrier gave up
+  gs2_status first_bad = GS2_OK;
+  for (int s = 0; s < S; ++s) {
+    const KrylovState& st = h->pp_st_host[s];
+    gs2_solve_info loc{st.iters, st.cycles, st.status, 0.0};
+    loc.true_relres = st.bnorm == 0.0 ? 0.0 : st.beta / st.bnorm;
+    if (infos) infos[s] = loc;
+    if (loc.status != GS2_OK && first_bad == GS2_OK) first_bad = (gs2_status)loc.status;
+  }
+  return first_bad;
 }
 
 gs2_status cg_cluster(gs2_handle* h, const double* b, double* x, double tol, int max_iters,

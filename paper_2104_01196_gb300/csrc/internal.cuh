@@ -224,6 +224,8 @@ struct gs2_handle {
   double* persist_part = nullptr;   // its partial sums
   bool stall_barrier = false;       // test hook: next one-launch solve's barrier never opens
   int cl_wa = -1, cl_wl = -1, cl_wu = -1;  // longest rows of A, L, U (longest_rows)
+  void* cl_sys = nullptr;  // a pack in clusters: its per-system table (device)
+  int cl_sys_cap = 0;
   // one-launch solve of a pack: per-system argument table, block -> system
   // map, barriers, partial sums and results (grown on demand)
   void* pp_args = nullptr;
@@ -456,6 +458,9 @@ gs2_status gmres_cluster(gs2_handle* h, const double* b, double* x, int m, doubl
                          int max_iters, const gs2_params* p, gs2_solve_info* info);
 gs2_status cg_cluster(gs2_handle* h, const double* b, double* x, double tol, int max_iters,
                       const gs2_params* p, gs2_solve_info* info);
+bool pack_cluster_eligible(gs2_handle* h, int m, const gs2_params* p);
+gs2_status pack_gmres_cluster(gs2_handle* h, const double* b, double* x, int m, double tol,
+                              int max_iters, const gs2_params* p, gs2_solve_info* infos);
 // gs2_autotune_gmres: the fastest solve structure (1, 2, 3) for (m, p)
 int autotune_gmres(gs2_handle* h, int m, const gs2_params* p);
 void launch_fill_value(gs2_handle* h, double* y, double v);

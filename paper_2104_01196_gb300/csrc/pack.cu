@@ -995,10 +995,16 @@ void pack_job_free(PackJob* j) { delete j; }
 
 gs2_status pack_gmres_run(gs2_handle* h, const double* b, double* x, int m, double tol,
                           int max_iters, const gs2_params* p, gs2_solve_info* infos) {
-  // every system in one cooperative launch (persist.cu): graph mode 3, or
-  // automatically for packs small enough (pack_persistent_eligible)
-  if (h->graph_mode == 0 && !profiling_active(h) && pack_persistent_eligible(h, m, p, true))
+  // one cluster per system (cluster.cu): graph mode 4, or automatically for
+  // packs small enough (pack_persistent_eligible) whose systems fit a
+  // cluster; else every system in one cooperative launch (persist.cu):
+  // graph mode 3, or automatically for packs small enough
+  if (h->graph_mode == 4) return pack_gmres_cluster(h, b, x, m, tol, max_iters, p, infos);
+  if (h->graph_mode == 0 && !profiling_active(h) && pack_persistent_eligible(h, m, p, true)) {
+    if (pack_cluster_eligible(h, m, p))
+      return pack_gmres_cluster(h, b, x, m, tol, max_iters, p, infos);
     return pack_gmres_persistent(h, b, x, m, tol, max_iters, p, infos);
+  }
   if (h->graph_mode == 3) {
     if (!pack_persistent_eligible(h, m, p, false))
       GS2_THROW(GS2_ERR_INVALID_ARG,

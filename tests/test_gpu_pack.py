@@ -245,15 +245,17 @@ def test_pack_with_empty_systems(g):
 ONE_LAUNCH_PCS = ["none", "gs2_fwd_1_1", "sgs2_1_2_damped", "jr_3_w0.8"]
 
 
+@pytest.mark.parametrize("mode", [3, 4])
 @pytest.mark.parametrize("pc", ONE_LAUNCH_PCS)
-def test_pack_one_launch_matches_oracle_per_system(g, pc):
+def test_pack_one_launch_matches_oracle_per_system(g, pc, mode):
     """Graph mode 3: every system of the pack in one cooperative launch, its
-    own blocks, barrier and Krylov scalars; per system the oracle's count
-    within +-1, the true residual reached, and a single library launch (plus
-    the copies) for the whole pack."""
+    own blocks, barrier and Krylov scalars; graph mode 4: one thread-block
+    cluster per system, the system in its shared memory.  Per system the
+    oracle's count within +-1, the true residual reached, and a single
+    library launch (plus the copies) for the whole pack."""
     gp, op = PCS[pc]
     pack = g.pack_setup([p.A for p in MIX])
-    pack.set_graph_mode(3)
+    pack.set_graph_mode(mode)
     prm = g.params(**gp) if gp else None
     rhs = dev(_cat([p.b for p in MIX]))
     x = dev(np.zeros(pack.n))
@@ -273,24 +275,25 @@ def test_pack_one_launch_matches_oracle_per_system(g, pc):
         assert r <= 1e-8 and abs(infos[s].true_relres - r) <= 1e-12, (s, r)
 
 
-def test_pack_one_launch_statuses_and_graph_agreement(g):
-    """Per-system statuses in one launch (zero right-hand side, warm start at
-    the solution, NaN, iteration limit) while the other systems converge, as
-    the replayed-graph pack gives them; counts within +-1 of the graph
-    pack's; empty systems."""
+@pytest.mark.parametrize("mode", [3, 4])
+def test_pack_one_launch_statuses_and_graph_agreement(g, mode):
+    """Per-system statuses in one launch or one cluster per system (zero
+    right-hand side, warm start at the solution, NaN, iteration limit) while
+    the other systems converge, as the replayed-graph pack gives them;
+    counts within +-1 of the graph pack's; empty systems."""
     a, b = P.poisson2d(24), P.poisson3d(7)
     nan_b = b.b.copy()
     nan_b[3] = np.nan
     rhs = _cat([a.b, np.zeros(a.n), b.b, nan_b, a.b])
     x0 = _cat([np.zeros(a.n), np.ones(a.n), b.x_true, np.zeros(b.n), np.zeros(a.n)])
     res = {}
-    for mode in (1, 3):
+    for md in (1, mode):
         pack = g.pack_setup([a.A, a.A, b.A, b.A, a.A])
-        pack.set_graph_mode(mode)
+        pack.set_graph_mode(md)
         x = dev(x0)
         infos = g.pack_gmres(pack, dev(rhs), x, 30, 1e-8, 3000, g.params("gs2", 1, 1))
-        res[mode] = (infos, pack.split(host(x)))
-    infos, xs = res[3]
+        res[md] = (infos, pack.split(host(x)))
+    infos, xs = res[mode]
     assert [i.status for i in infos] == [0, 0, 0, 7, 0]
     assert np.all(xs[1] == 0.0) and infos[1].iters == 0
     assert infos[2].iters == 0 and np.array_equal(xs[2], b.x_true)
@@ -299,13 +302,13 @@ def test_pack_one_launch_statuses_and_graph_agreement(g):
         assert abs(infos[s].iters - res[1][0][s].iters) <= 1
         assert rel(xs[s], res[1][1][s]) <= 1e-6
     pack = g.pack_setup([a.A, a.A, b.A])
-    pack.set_graph_mode(3)
+    pack.set_graph_mode(mode)
     infos = g.pack_gmres(pack, dev(_cat([a.b, a.b, b.b])), dev(np.zeros(pack.n)), 10, 1e-12,
                          7, g.params("gs2", 1, 1))
     assert [i.status for i in infos] == [5] * 3 and [i.iters for i in infos] == [7] * 3
     E = (np.array([0]), np.zeros(0, np.int32), np.zeros(0))
     pack = g.pack_setup([E, a.A, E])
-    pack.set_graph_mode(3)
+    pack.set_graph_mode(mode)
     infos = g.pack_gmres(pack, dev(a.b), dev(np.zeros(a.n)), 30, 1e-8, 500,
                          g.params("gs2", 1, 1))
     assert [i.status for i in infos] == [0, 0, 0] and infos[1].iters > 0
