@@ -288,9 +288,10 @@ class Handle:
         return [(arr[0][i], arr[1][i], arr[2][i]) for i in range(lv.value)]
 
     def set_graph_mode(self, mode: int):
-        """0: automatic (one launch for small systems, else graphs), 1: restart
-        cycles as CUDA graphs, 2: separate launches, 3: one launch, 4: one
-        thread-block cluster (GMRES of a system that fits its shared memory)."""
+        """0: automatic (one thread-block cluster for a small system that fits
+        its shared memory, else one launch for small systems, else graphs), 1:
+        restart cycles as CUDA graphs, 2: separate launches, 3: one launch, 4:
+        one thread-block cluster (GMRES, CG, or a pack: one cluster a system)."""
         _check(load().gs2_set_graph_mode(self.ptr, mode))
 
     def test_stall_barrier(self):

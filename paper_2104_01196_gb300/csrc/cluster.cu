@@ -19,12 +19,16 @@
 // CTA's barrier (release, cluster scope) and waits on its own (acquire),
 // with a bound -- 0.45 us at 16 CTAs against 1.3 us for the grid barrier.
 // Inner products are CTA partial sums (the warps' butterfly sums, then the
-// warps in order) that every CTA reads from all CTAs in rank order, so that
-// every CTA holds bitwise the same Krylov scalars and takes the same
-// decisions, as in the one-launch solver.  The arithmetic of each row --
-// residuals, inner sweeps, the CGS2 updates -- is that of the multi-kernel
-// path, entry for entry in stored order; only the grouping of the inner
-// products' partial sums differs.
+// warps as a fixed pairwise tree) that every CTA reads from all CTAs and
+// adds as a fixed pairwise tree, so that every CTA holds bitwise the same
+// Krylov scalars and takes the same decisions, as in the one-launch solver.
+// The arithmetic of each row -- residuals, inner sweeps, the CGS2 updates --
+// is that of the multi-kernel path, entry for entry in stored order (the
+// padding slots add exact zeros); the grouping of the inner products'
+// partial sums differs, and the Givens rotations are formed with explicit
+// FMAs.  A pack gives every system a cluster of its own: a table of
+// systems, cluster k solving system k with columns taken relative to the
+// system's first row.
 //
 // The CTAs meet once with the hardware cluster barrier after loading their
 // rows (so that no CTA arrives on a barrier that is not initialised yet) and
@@ -281,8 +285,9 @@ __device__ __forceinline__ double cl_dotA(const ClRows& c, int l, int k) {
 
 // Sums over the cluster of nv <= NV per-thread values into out[0 .. nv)
 // (shared memory), bitwise the same in every CTA: each warp's butterfly
-// sums, the warps in order, this CTA's sums to its partial buffer, the
-// barrier, then value q summed over the CTAs in rank order.  The buffers
+// sums, the warps as a fixed pairwise tree, this CTA's sums to its partial
+// buffer, the barrier, then value q summed over the CTAs as a fixed
+// pairwise tree in rank order.  The buffers
 // alternate, so a buffer is written again only after the barrier that
 // follows every CTA's reads of it.
 template <int NV>
@@ -307,7 +312,7 @@ __device__ bool cl_sums(ClSync& S, const double (&acc)[NV], int nv, double* out,
   if (!cl_sync(S, C, err)) return false;
   if ((int)threadIdx.x < nv) {
     // all CTAs' partials in flight at once (a CTA beyond C re-reads the
-    // last one), then summed in rank order
+    // last one), then summed
     const unsigned o = 8u * (unsigned)(pb * 32 + threadIdx.x);
     double pv[kClMaxCtas];
 #pragma unroll
