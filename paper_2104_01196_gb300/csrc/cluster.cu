@@ -1034,7 +1034,20 @@ bool cluster_eligible(gs2_handle* h, int m, const gs2_params* p) {
   return cluster_plan(h, m, p, &pl);
 }
 
-// GMRES(m) (cg = false) or CG (cg = true: three basis slots) in one cluster
+// The outcome of a one-cluster solve from the handle's host copy of the
+// device state (read_state, or the asynchronous copy of gmres_cluster_async
+// once the stream is idle).
+gs2_status cluster_result(gs2_handle* h, gs2_solve_info* info) {
+  if (*h->err_host) raise_device_error(h);  // a barrier gave up
+  const KrylovState& st = *h->st_host;
+  gs2_solve_info loc{st.iters, st.cycles, st.status, 0.0};
+  loc.true_relres = st.bnorm == 0.0 ? 0.0 : st.beta / st.bnorm;
+  if (info) *info = loc;
+  return (gs2_status)st.status;
+}
+
+// GMRES(m) (cg = false) or CG (cg = true: three basis slots) in one cluster;
+// with info = nullptr only enqueued (the caller copies the state back)
 static gs2_status cluster_run(gs2_handle* h, const double* b, double* x, int m, double tol,
                               int max_iters, const gs2_params* p, gs2_solve_info* info,
                               bool cg) {
@@ -1093,17 +1106,23 @@ static gs2_status cluster_run(gs2_handle* h, const double* b, double* x, int m, 
     GS2_CUDA(cudaLaunchKernelEx(&cfg, k_gmres_cluster, a));
     GS2_LAUNCH_CHECK();
   }
-  read_state(h);  // raises GS2_ERR_TIMEOUT if a barrier gave up
-  const KrylovState& st = *h->st_host;
-  gs2_solve_info loc{st.iters, st.cycles, st.status, 0.0};
-  loc.true_relres = st.bnorm == 0.0 ? 0.0 : st.beta / st.bnorm;
-  if (info) *info = loc;
-  return (gs2_status)st.status;
+  if (!info) return GS2_OK;  // asynchronous: cluster_result once the stream is idle
+  read_state(h);             // raises GS2_ERR_TIMEOUT if a barrier gave up
+  return cluster_result(h, info);
 }
 
 gs2_status gmres_cluster(gs2_handle* h, const double* b, double* x, int m, double tol,
                          int max_iters, const gs2_params* p, gs2_solve_info* info) {
-  return cluster_run(h, b, x, m, tol, max_iters, p, info, false);
+  gs2_solve_info loc{};
+  const gs2_status st = cluster_run(h, b, x, m, tol, max_iters, p, &loc, false);
+  if (info) *info = loc;
+  return st;
+}
+
+void gmres_cluster_async(gs2_handle* h, const double* b, double* x, int m, double tol,
+                         int max_iters, const gs2_params* p) {
+  cluster_run(h, b, x, m, tol, max_iters, p, nullptr, false);
+  copy_state_async(h);
 }
 
 // ---------------------------------------------------------------------------
@@ -1267,7 +1286,10 @@ gs2_status pack_gmres_cluster(gs2_handle* h, const double* b, double* x, int m, 
 
 gs2_status cg_cluster(gs2_handle* h, const double* b, double* x, double tol, int max_iters,
                       const gs2_params* p, gs2_solve_info* info) {
-  return cluster_run(h, b, x, 2, tol, max_iters, p, info, true);
+  gs2_solve_info loc{};
+  const gs2_status st = cluster_run(h, b, x, 2, tol, max_iters, p, &loc, true);
+  if (info) *info = loc;
+  return st;
 }
 
 }  // namespace gs2

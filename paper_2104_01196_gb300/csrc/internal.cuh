@@ -458,6 +458,10 @@ gs2_status gmres_cluster(gs2_handle* h, const double* b, double* x, int m, doubl
                          int max_iters, const gs2_params* p, gs2_solve_info* info);
 gs2_status cg_cluster(gs2_handle* h, const double* b, double* x, double tol, int max_iters,
                       const gs2_params* p, gs2_solve_info* info);
+void gmres_cluster_async(gs2_handle* h, const double* b, double* x, int m, double tol,
+                         int max_iters, const gs2_params* p);
+gs2_status cluster_result(gs2_handle* h, gs2_solve_info* info);
+void copy_state_async(gs2_handle* h);
 bool pack_cluster_eligible(gs2_handle* h, int m, const gs2_params* p);
 gs2_status pack_gmres_cluster(gs2_handle* h, const double* b, double* x, int m, double tol,
                               int max_iters, const gs2_params* p, gs2_solve_info* infos);
@@ -507,8 +511,9 @@ gs2_solve_info pack_job_info(const PackJob* j, int s);
 void pack_job_free(PackJob* j);
 
 // A GMRES solve as a resumable job (used by the server): start enqueues
-// the first work on the handle's stream; advance must be called only once
-// that stream is idle and returns true when the solve has finished.
+// the first work on the handle's stream (graph mode 4: the whole solve in
+// one cluster launch); advance must be called only once that stream is idle
+// and returns true when the solve has finished.
 struct GmresJob;
 GmresJob* gmres_job_start(gs2_handle* h, const double* b, double* x, int m, double tol,
                           int max_iters, const gs2_params* p);

@@ -399,7 +399,7 @@ static void launch_norm(gs2_handle* h, const double* x, int which) {
 }
 
 // Copy the device state and the sticky error word to pinned host memory.
-static void copy_state_async(gs2_handle* h) {
+void copy_state_async(gs2_handle* h) {
   GS2_CUDA(cudaMemcpyAsync(h->st_host, h->st, sizeof(KrylovState), cudaMemcpyDeviceToHost,
                            h->stream));
   GS2_CUDA(cudaMemcpyAsync(h->err_host, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost,
@@ -799,6 +799,11 @@ struct GmresJob {
   gs2_params params{};
   bool has_params = false;
   GmresRun run;
+  // graph mode 4: the whole solve was enqueued as one cluster launch; its
+  // outcome is read once the stream is idle
+  gs2_handle* cluster = nullptr;
+  gs2_solve_info loc{};
+  bool done = false;
 };
 
 GmresJob* gmres_job_start(gs2_handle* h, const double* b, double* x, int m, double tol,
@@ -809,7 +814,13 @@ GmresJob* gmres_job_start(gs2_handle* h, const double* b, double* x, int m, doub
     j->has_params = true;
   }
   try {
-    j->run.start(h, b, x, m, tol, max_iters, j->has_params ? &j->params : nullptr);
+    if (h->graph_mode == 4) {
+      // the whole solve in one cluster launch, the state copied back behind it
+      gmres_cluster_async(h, b, x, m, tol, max_iters, j->has_params ? &j->params : nullptr);
+      j->cluster = h;
+    } else {
+      j->run.start(h, b, x, m, tol, max_iters, j->has_params ? &j->params : nullptr);
+    }
   } catch (...) {
     delete j;
     throw;
@@ -818,15 +829,23 @@ GmresJob* gmres_job_start(gs2_handle* h, const double* b, double* x, int m, doub
 }
 
 void gmres_job_prepare(GmresJob* j) {
-  if (!j->run.done && j->run.use_graph()) j->run.ensure_graph();
+  if (!j->cluster && !j->run.done && j->run.use_graph()) j->run.ensure_graph();
 }
 
 bool gmres_job_advance(GmresJob* j) {
+  if (j->cluster) {
+    if (!j->done) {
+      j->done = true;
+      cluster_result(j->cluster, &j->loc);  // raises if a barrier gave up
+    }
+    return true;
+  }
   if (!j->run.done) j->run.advance();
   return j->run.done;
 }
 
 gs2_solve_info gmres_job_info(const GmresJob* j) {
+  if (j->cluster) return j->loc;
   gs2_solve_info i = j->run.loc;
   i.status = j->run.st;
   return i;

@@ -2,15 +2,19 @@
 //
 // Requests are queued on submission and admitted in arrival order as soon as
 // a slot is free and their estimated device footprint fits the server's
-// budget (by default 90% of the device memory free when the server starts).
-// A preparation thread builds an admitted request's handle on a stream of
-// its own, with stream-ordered allocations, and starts its GMRES job; the
-// progress thread then polls every running job's stream and advances the
-// job by one restart cycle whenever that stream is idle.  Requests that
+// budget (by default 90% of the device memory free when the server starts;
+// optionally some slots kept for small requests).  A preparation thread
+// builds an admitted request's handle on a stream of its own, with
+// stream-ordered allocations, and starts its GMRES job: a system that fits
+// one cluster's shared memory is solved by one cluster launch, any other by
+// one replayed graph per restart cycle.  The progress thread polls every
+// running job's stream and advances the job by one restart cycle (or reads
+// the cluster solve's outcome) whenever that stream is idle.  Requests that
 // arrive while others run are therefore admitted as slots and memory free
 // up, and their kernels overlap on the GPU.  Every request runs the same
-// kernels with the same launch geometry as a lone gmres_solve, so its
-// result is bitwise the same alone and in the mix.  With packing enabled,
+// kernels with the same launch geometry as a lone gmres_solve in the same
+// graph mode (4 or 1), so its result is bitwise the same alone and in the
+// mix.  With packing enabled,
 // small requests at the front of the queue are admitted together and solved
 // as one pack (pack.cu) in one slot: one set of launches for all of them,
 // each result independent of its pack-mates.
@@ -211,9 +215,12 @@ static void prepare(gs2_server* s, Request* r) {
     r->h = setup_handle(r->n, r->nnz, r->rp.data(), r->ci.data(), r->va.data(), 0, prec,
                         r->stream, true);
     ensure_precond(r->h, pc);
-    // every request replays its cycles as a graph captured by this thread,
-    // so the single progress thread only ever launches whole cycles
-    r->h->graph_mode = 1;
+    // a request whose rows fit one cluster's shared memory is solved by one
+    // cluster launch (clusters never wait for one another, so requests on
+    // other streams cannot hold it up); every other request replays its
+    // cycles as a graph captured by this thread, so the single progress
+    // thread only ever launches whole cycles
+    r->h->graph_mode = cluster_eligible(r->h, s->cfg.restart, pc) ? 4 : 1;
     r->h->h2d(r->h->bstage, r->b.data(), sizeof(double) * r->n);
     if (r->x0.empty()) r->h->dzero(r->h->xstage, sizeof(double) * r->n);
     else r->h->h2d(r->h->xstage, r->x0.data(), sizeof(double) * r->n);

@@ -1,7 +1,9 @@
 """The solve server: continuous batching of independent systems.
 
 GPU tests check that every result is the same, bit for bit, alone and in the
-mix; that admission follows the memory budget; and that a failure injected
+mix (small requests are solved in one cluster, the others with per-cycle
+graphs, as gmres_solve does in those graph modes); that admission follows
+the memory budget; and that a failure injected
 on the host (a request whose allocation "fails") is reported for that
 request while the others complete.  The CPU test checks the admission
 estimate, which needs no GPU.
@@ -48,12 +50,19 @@ def _mix():
 
 
 def _alone(pr, pc, max_iters=4000):
+    """gmres_solve alone, on the path the server takes: one cluster where the
+    system fits (graph mode 4), else the per-cycle graphs (mode 1)."""
     import torch
     h = gs2.gs2_setup(pr.A)
-    h.set_graph_mode(1)  # the cycle-graph path the server runs
     x = torch.zeros(pr.n, dtype=torch.float64, device="cuda")
     b = torch.from_numpy(pr.b).cuda()
-    info = gs2.gmres_solve(h, b, x, 30, 1e-8, max_iters, pc)
+    h.set_graph_mode(4)
+    try:
+        info = gs2.gmres_solve(h, b, x, 30, 1e-8, max_iters, pc)
+    except gs2.GS2Error as e:
+        assert e.status == 1  # does not fit one cluster: refused before any work
+        h.set_graph_mode(1)
+        info = gs2.gmres_solve(h, b, x, 30, 1e-8, max_iters, pc)
     torch.cuda.synchronize()
     out = x.cpu().numpy()
     h.close()
