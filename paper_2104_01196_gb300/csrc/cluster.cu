@@ -38,6 +38,10 @@
 // barrier, and so does every other CTA at its next wait.
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
 #include <vector>
 
 #include "arnoldi.cuh"
@@ -957,24 +961,63 @@ struct ClPlan {
   ClLayout lay{};
 };
 
+// the dynamic shared memory a CTA may take (the opt-in limit less the
+// kernel's static shared memory), set on the kernel once per process
 static size_t cl_smem_limit(gs2_handle* h) {
+  static std::once_flag once;
   static size_t limit = 0;
-  static size_t stat = 0;
-  if (!limit) {
+  static cudaError_t failed = cudaSuccess;
+  std::call_once(once, [] {
     int dev = 0, optin = 0;
-    GS2_CUDA(cudaGetDevice(&dev));
-    GS2_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     cudaFuncAttributes fa{};
-    GS2_CUDA(cudaFuncGetAttributes(&fa, (const void*)k_gmres_cluster));
-    stat = fa.sharedSizeBytes;
-    limit = (size_t)optin > stat ? (size_t)optin - stat : 0;
-    GS2_CUDA(cudaFuncSetAttribute((const void*)k_gmres_cluster,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit));
-    GS2_CUDA(cudaFuncSetAttribute((const void*)k_gmres_cluster,
-                                  cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-  }
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+      e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, (const void*)k_gmres_cluster);
+    const size_t lim = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes
+                                                          : 0;
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute((const void*)k_gmres_cluster,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute((const void*)k_gmres_cluster,
+                               cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess) limit = lim;
+    else failed = e;
+  });
   (void)h;
+  if (failed != cudaSuccess)
+    GS2_THROW(GS2_ERR_CUDA, std::string("cluster kernel setup: ") + cudaGetErrorString(failed));
   return limit;
+}
+
+// clusters of C CTAs of T threads with `bytes` of dynamic shared memory that
+// fit the GPU at once (cached: the query is made once per shape)
+static int cl_resident_clusters(int C, int T, unsigned bytes) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, unsigned>, int> known;
+  const auto key = std::make_tuple(C, T, bytes);
+  {
+    std::lock_guard<std::mutex> g(mu);
+    auto it = known.find(key);
+    if (it != known.end()) return it->second;
+  }
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)C);
+  cfg.blockDim = dim3((unsigned)T);
+  cfg.dynamicSmemBytes = bytes;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int clusters = 0;
+  GS2_CUDA(cudaOccupancyMaxActiveClusters(&clusters, (const void*)k_gmres_cluster, &cfg));
+  std::lock_guard<std::mutex> g(mu);
+  known[key] = clusters;
+  return clusters;
 }
 
 static bool cl_kind_ok(int m, const gs2_params* p) {
@@ -1011,20 +1054,7 @@ static bool cluster_plan(gs2_handle* h, int m, const gs2_params* p, ClPlan* out)
     out->lay = lay;
     // one cluster of this shape must fit the GPU (its CTAs on SMs of one
     // GPC, each with this much shared memory)
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3((unsigned)Cn);
-    cfg.blockDim = dim3((unsigned)out->T);
-    cfg.dynamicSmemBytes = lay.bytes;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = (unsigned)Cn;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    int clusters = 0;
-    GS2_CUDA(cudaOccupancyMaxActiveClusters(&clusters, (const void*)k_gmres_cluster, &cfg));
-    return clusters >= 1;
+    return cl_resident_clusters(Cn, out->T, lay.bytes) >= 1;
   }
   return false;
 }
@@ -1156,19 +1186,7 @@ static bool pack_cluster_plan(gs2_handle* h, int m, const gs2_params* p, ClPlan*
     const ClLayout lay = cl_layout(Rp, h->cl_wa, tri ? h->cl_wl : 0, tri ? h->cl_wu : 0, m);
     if (lay.bytes > limit) continue;
     const int T = Rmax <= 64 ? 64 : (Rmax <= 128 ? 128 : 256);
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3((unsigned)C);
-    cfg.blockDim = dim3((unsigned)T);
-    cfg.dynamicSmemBytes = lay.bytes;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = (unsigned)C;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    int clusters = 0;
-    GS2_CUDA(cudaOccupancyMaxActiveClusters(&clusters, (const void*)k_gmres_cluster, &cfg));
+    const int clusters = cl_resident_clusters(C, T, lay.bytes);
     if (clusters < 1) continue;
     const double waves = std::ceil((double)S / clusters);
     const double cost = waves * (17.4 + 0.021 * Rmax);
