@@ -312,7 +312,7 @@ static void prepare_group(gs2_server* s, Group* g) {
       g->job = pack_job_start(g->h, g->h->bstage, g->h->xstage, s->cfg.restart, s->cfg.tol,
                               s->cfg.max_iters, pc);
       pack_job_prepare(g->job);
-      // the pageable staging copies above have been taken by the driver
+      // the pageable staging copies above have been taken by the CUDA driver
     } catch (const Error& e) {
       st = e.st;
     } catch (const std::bad_alloc&) {
