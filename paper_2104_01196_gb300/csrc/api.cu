@@ -462,7 +462,7 @@ void* gs2_handle::dalloc(size_t bytes) {
 }
 
 // setup copies are ordered on the handle's stream (pageable sources are
-// staged by the driver before the call returns)
+// staged by the CUDA driver before the call returns)
 void gs2_handle::h2d(void* dst, const void* src, size_t bytes) {
   if (bytes) GS2_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, stream));
 }
